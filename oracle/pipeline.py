@@ -1,0 +1,57 @@
+"""FastCauchyRegression end to end, FP64 oracle side (Figure 2, steps 1-8).
+
+Test infrastructure: only the tests, the smoke check and the bench's CPU
+baseline use this module; the CUDA path shares no code with it.
+
+Each step is one call into the modules of this package, in the figure's
+order, and every intermediate is returned so that tests can compare the CUDA
+path with it step by step.
+"""
+from __future__ import annotations
+
+import time
+
+import numpy as np
+
+from . import condition, fct, leverage, rng, sampling, solve
+
+
+def form_x(A: np.ndarray, b: np.ndarray) -> np.ndarray:
+    """X = [A, −b] ∈ R^{n×(d+1)} in FP64 (Figure 2, step 1, k = 1)."""
+    A = np.asarray(A, dtype=np.float64)
+    return np.concatenate([A, -np.asarray(b, dtype=np.float64)[:, None]], axis=1)
+
+
+def fast_cauchy_regression(A, b, s: int, r1: int, r2: int, coreset: float,
+                           seed: int = 0, problem_id: int = 0, sign_flip: bool = True,
+                           solve_lp: bool = True, timings: dict | None = None) -> dict:
+    """All intermediates of Figure 2 for one problem (rows are numbered from 0)."""
+    t = {} if timings is None else timings
+    t0 = time.perf_counter()
+    X = form_x(A, b)                                                          # step 1
+    n, q = X.shape
+    pix, tsum = fct.fct1_embed(X, s, r1, seed, problem_id, 0, sign_flip)     # step 2, Π1X
+    t1 = time.perf_counter()
+    _, r_mat = condition.qr_positive(pix)                                     # step 2, QR
+    condition.check_rank(r_mat)
+    pi2 = rng.pi2_matrix(seed, problem_id, q, r2)                             # step 3
+    m_mat = condition.m_matrix(r_mat, pi2)                                    # R⁻¹Π2
+    t2 = time.perf_counter()
+    lam = leverage.lambda_estimates(X, m_mat)                                 # steps 4-5
+    t3 = time.perf_counter()
+    p_hat, tau, total = sampling.probabilities(lam, coreset)                  # step 6
+    u = rng.sample_uniforms(seed, problem_id, np.arange(n))
+    idx, wts = sampling.bernoulli_sample(p_hat, u)                            # step 7
+    t4 = time.perf_counter()
+    out = {"X": X, "PiX": pix, "T": tsum, "R": r_mat, "Pi2": pi2, "M": m_mat,
+           "lam": lam, "lam_total": total, "tau": tau, "p": p_hat, "u": u,
+           "idx": idx, "w": wts}
+    if solve_lp:                                                              # step 8
+        xs, fs = solve.lad_lp(X[idx, :-1], -X[idx, -1], wts)
+        out["x_hat"] = xs
+        out["coreset_objective"] = fs
+        out["objective"] = solve.objective(X[:, :-1], -X[:, -1], xs)
+    t5 = time.perf_counter()
+    t.update({"fct": t1 - t0, "condition": t2 - t1, "lambda": t3 - t2,
+              "sample": t4 - t3, "solve": t5 - t4})
+    return out

@@ -1,0 +1,37 @@
+"""Coreset sampling, FP64 oracle side (Figure 2, steps 6-7; ℓ1 sampling lemma, §2).
+
+Test infrastructure: only the tests, the smoke check and the bench's CPU
+baseline use this module; the CUDA path shares no code with it.
+
+p̂_i = min{1, m_s·λ_i / Σ_j λ_j}, evaluated in FP64 as τ = m_s / Σλ (one
+division) followed by p̂_i = min(1, τ·λ_i); D_ii = 1/p̂_i with probability p̂_i,
+else 0, decided by u_i < p̂_i with the 53-bit uniform of row i.  Kept indices
+are returned in ascending order.  Σλ is the correctly rounded FP64 sum.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+
+def lambda_total(lam: np.ndarray) -> float:
+    return math.fsum(np.asarray(lam, dtype=np.float64).tolist())
+
+
+def probabilities(lam: np.ndarray, coreset: float, total: float | None = None):
+    lam = np.asarray(lam, dtype=np.float64)
+    if total is None:
+        total = lambda_total(lam)
+    if not (total > 0.0) or not math.isfinite(total):
+        raise ValueError("Σλ must be positive and finite")
+    tau = float(coreset) / total
+    return np.minimum(1.0, tau * lam), tau, total
+
+
+def bernoulli_sample(p: np.ndarray, u: np.ndarray):
+    """Indices i with u_i < p_i (ascending) and their weights 1/p_i."""
+    p = np.asarray(p, dtype=np.float64)
+    keep = np.asarray(u, dtype=np.float64) < p
+    idx = np.flatnonzero(keep)
+    return idx, 1.0 / p[idx]

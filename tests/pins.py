@@ -1,0 +1,310 @@
+"""Checks that pin the FP64 oracle to facts outside itself.
+
+Each check raises AssertionError when the oracle disagrees with what the
+paper or the mathematics fixes: closed forms, invariants stated in the
+paper's proofs, brute force on tiny inputs, and exact distributional
+consequences of Cauchy 1-stability.  test_oracle_pins.py runs every check on
+the oracle as written; test_oracle_mutations.py plants plausible mistakes in
+the oracle and asserts that some check here catches each of them.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+from scipy import stats
+
+from oracle import condition, fct, leverage, pipeline, rng, sampling, solve
+
+
+# ----------------------------------------------------------------- Hadamard
+def check_hadamard_closed_form(max_log2: int = 10) -> None:
+    """Sylvester H_s has entries (−1)^{popcount(i AND j)} and H_s·H_s = s·I (§3.1)."""
+    for lg in range(0, max_log2 + 1):
+        s = 1 << lg
+        h = fct.sylvester_hadamard(s)
+        i = np.arange(s)
+        par = np.vectorize(lambda v: bin(v).count("1") & 1)(i[:, None] & i[None, :])
+        assert np.array_equal(h, np.where(par == 1, -1.0, 1.0)), f"H_{s} entries"
+        assert np.array_equal(h @ h, s * np.eye(s)), f"H_{s}^2 != s I"
+
+
+# ----------------------------------------------------------------- Cauchy
+def check_cauchy_quantiles(step: int = 1) -> None:
+    """c(k) is the standard Cauchy quantile at (k+½)·2^-24.
+
+    Tail form: P(C > |c|) = atan(1/|c|)/π must equal min(u, 1−u), and the
+    sign of c must be the sign of u − ½.  Also compared with tan(π(u−½)) away
+    from the poles (a different formula).
+    """
+    k = np.arange(0, 1 << 24, step, dtype=np.int64)
+    c = rng.cauchy_from_k(k)
+    u = (k.astype(np.float64) + 0.5) * 2.0 ** -24
+    tail = np.arctan2(1.0, np.abs(c)) / np.pi
+    assert np.allclose(tail, np.minimum(u, 1.0 - u), rtol=1e-13, atol=0), "Cauchy tail"
+    assert np.array_equal(np.sign(c), np.sign(u - 0.5)), "Cauchy sign"
+    mid = np.abs(u - 0.5) < 0.4
+    assert np.allclose(c[mid], np.tan(np.pi * (u[mid] - 0.5)), rtol=1e-12, atol=1e-15), "tan form"
+
+
+def check_draw_statistics(n: int = 1 << 18, r1: int = 97, seed: int = 12345) -> None:
+    """Uniform buckets, balanced signs, Cauchy scales and uniforms with the right laws."""
+    d = rng.fct_draws(seed, 3, np.arange(n), r1)
+    for key in ("hash_h", "hash_i"):
+        cnt = np.bincount(d[key], minlength=r1)
+        assert cnt.size == r1
+        p = stats.chisquare(cnt).pvalue
+        assert p > 1e-5, f"{key} not uniform (p={p})"
+    joint = np.bincount(d["hash_h"] % 8 * 8 + d["hash_i"] % 8, minlength=64).reshape(8, 8)
+    assert stats.chi2_contingency(joint).pvalue > 1e-5, "hash_h, hash_i dependent"
+    plus = int((d["sigma"] > 0).sum())
+    assert abs(plus - n / 2) < 5 * math.sqrt(n) / 2, "sign imbalance"
+    for key in ("cauchy_h", "cauchy_i"):
+        ks = stats.kstest(d[key], "cauchy")
+        assert ks.pvalue > 1e-5, f"{key} not Cauchy (p={ks.pvalue})"
+    sg = d["sigma"]
+    assert abs(np.mean(sg * np.sign(d["cauchy_i"]))) < 5 / math.sqrt(n), "σ tied to C_I sign"
+    u = rng.sample_uniforms(seed, 3, np.arange(n))
+    assert np.all((u >= 0) & (u < 1))
+    assert stats.kstest(u, "uniform").pvalue > 1e-5, "sampling uniforms"
+    assert abs(np.corrcoef(u[0::2], u[1::2])[0, 1]) < 5 / math.sqrt(n / 2), "even/odd rows correlated"
+    pi2 = rng.pi2_matrix(seed, 3, 257, 64)
+    assert stats.kstest(pi2.ravel(), "cauchy").pvalue > 1e-5, "Π2 entries"
+    a = rng.fct_draws(seed, 4, np.arange(n), r1)["cauchy_h"]
+    assert stats.kstest(a - 0.0, "cauchy").pvalue > 1e-5
+    assert not np.array_equal(a, d["cauchy_h"]), "problem id ignored"
+
+
+# ----------------------------------------------------------------- FCT1
+def check_fct_dense(cases=((1000, 64, 37), (2048, 256, 23), (4096, 64, 53), (300, 128, 11)),
+                    seed: int = 7) -> None:
+    """Block-wise Π1·X equals the explicit product 4·B·C·H̃·D of the four factors."""
+    g = np.random.default_rng(seed)
+    for n, s, r1 in cases:
+        for sign_flip in (True, False):
+            X = g.standard_normal((n, 5))
+            pix, tsum = fct.fct1_embed(X, s, r1, seed, 1, 0, sign_flip)
+            n_pad = fct.padded_rows(n, s)
+            xp = np.zeros((n_pad, 5))
+            xp[:n] = X
+            dense = fct.dense_pi1(n, s, r1, seed, 1, 0, sign_flip) @ xp
+            scale = np.abs(dense).max()
+            assert np.allclose(pix, dense, rtol=1e-12, atol=1e-12 * scale), f"Π1X n={n} s={s}"
+            assert np.all(tsum >= np.abs(pix) * (1 - 1e-12)), "T < |Π1X|"
+
+
+def _identity_draws(n_pad: int):
+    """C ≡ 1 and every virtual row in its own bucket: Hadamard row ι → 2ι, identity row ι → 2ι+1."""
+    rows = np.arange(n_pad)
+    return {"hash_h": 2 * rows, "hash_i": 2 * rows + 1,
+            "cauchy_h": np.ones(n_pad), "cauchy_i": np.ones(n_pad),
+            "sigma": np.where(rows % 3 == 0, -1.0, 1.0)}
+
+
+def check_fct_blocks(seed: int = 11) -> None:
+    """With C ≡ 1 and injective buckets Π1X exposes g = H̃·D·x, which must satisfy
+    ‖G_s z‖₂² = 2‖z‖₂² (proof of FCT1), the uncertainty lemma ‖G_s z‖₁ ≥ ½ s^{1/4}‖z‖₂,
+    and H_s z = the closed-form Walsh sum Σ_j (−1)^{popcount(i∧j)} z_j / √s."""
+    g = np.random.default_rng(seed)
+    for s in (1, 2, 16, 64, 256):
+        n = 3 * s + (s // 2 if s > 1 else 0)
+        n_pad = fct.padded_rows(n, s)
+        X = g.standard_normal((n, 3))
+        X[: s // 2 + 1, 1] = 0.0
+        X[0, 1] = 5.0                     # a spiky column: the adversarial case of the lemma
+        dr = _identity_draws(n_pad)
+        pix, tsum = fct.fct1_embed(X, s, 2 * n_pad, draws=dr)
+        gh = pix[0::2] / 4.0
+        gi = pix[1::2] / 4.0
+        xp = np.zeros((n_pad, 3))
+        xp[:n] = X
+        z = dr["sigma"][:, None] * xp
+        assert np.allclose(gi, z, rtol=0, atol=1e-13), "identity half"
+        idx = np.arange(s)
+        walsh = np.where(np.vectorize(lambda v: bin(v).count("1") & 1)(idx[:, None] & idx[None, :]) == 1, -1.0, 1.0)
+        for beta in range(n_pad // s):
+            zb = z[beta * s:(beta + 1) * s]
+            hb = gh[beta * s:(beta + 1) * s]
+            assert np.allclose(hb, walsh @ zb / math.sqrt(s), atol=1e-12), "H_s z"
+            for c in range(3):
+                gz = np.concatenate([hb[:, c], zb[:, c]])
+                n2 = np.sum(zb[:, c] ** 2)
+                assert math.isclose(np.sum(gz ** 2), 2 * n2, rel_tol=1e-12, abs_tol=1e-12), "energy"
+                assert np.sum(np.abs(gz)) >= 0.5 * s ** 0.25 * math.sqrt(n2) - 1e-12, "uncertainty"
+        assert np.allclose(tsum, np.abs(pix), atol=1e-13), "T with one term per bucket"
+
+
+def check_fct_mass(seed: int = 5) -> None:
+    """With C ≡ 1 and random buckets, Σ_rows Π1X = 4·Σ g and Σ_rows T = 4‖g‖₁ per column
+    (the hashed sums γ_j add up to ‖g‖₁, proof of FCT1)."""
+    g = np.random.default_rng(seed)
+    n, s, r1 = 700, 64, 19
+    X = g.standard_normal((n, 4))
+    n_pad = fct.padded_rows(n, s)
+    dr = rng.fct_draws(seed, 0, np.arange(n_pad), r1)
+    dr = dict(dr, cauchy_h=np.ones(n_pad), cauchy_i=np.ones(n_pad))
+    pix, tsum = fct.fct1_embed(X, s, r1, draws=dr)
+    dense_g = _explicit_g(X, s, dr["sigma"])
+    assert np.allclose(pix.sum(0), 4 * dense_g.sum(0), rtol=1e-12), "mass"
+    assert np.allclose(tsum.sum(0), 4 * np.abs(dense_g).sum(0), rtol=1e-12), "ℓ1 mass"
+
+
+def _explicit_g(X, s, sigma):
+    n = X.shape[0]
+    n_pad = fct.padded_rows(n, s)
+    xp = np.zeros((n_pad, X.shape[1]))
+    xp[:n] = X
+    z = sigma[:n_pad, None] * xp
+    idx = np.arange(s)
+    walsh = np.where(np.vectorize(lambda v: bin(v).count("1") & 1)(idx[:, None] & idx[None, :]) == 1, -1.0, 1.0)
+    gh = np.concatenate([walsh @ z[b * s:(b + 1) * s] / math.sqrt(s) for b in range(n_pad // s)])
+    return np.concatenate([gh, z])
+
+
+def check_fct_stability(seeds: int = 40) -> None:
+    """Conditional on B, (Π1X)_jc is a Cauchy scaled by 4·Σ_{v→j}|g_v| (1-stability, §2):
+    the standardized entries pooled over seeds pass a KS test against Cauchy(0,1)."""
+    g = np.random.default_rng(99)
+    n, s, r1 = 512, 64, 13
+    X = g.standard_normal((n, 3))
+    vals = []
+    for sd in range(seeds):
+        dr = rng.fct_draws(1000 + sd, 0, np.arange(n), r1)
+        pix, _ = fct.fct1_embed(X, s, r1, draws=dr)
+        ones = dict(dr, cauchy_h=np.ones(n), cauchy_i=np.ones(n))
+        _, t1 = fct.fct1_embed(X, s, r1, draws=ones)
+        vals.append((pix / t1).ravel())
+    v = np.concatenate(vals)
+    assert stats.kstest(v, "cauchy").pvalue > 1e-4, "Π1X entries not Cauchy-scaled"
+
+
+# ----------------------------------------------------------------- conditioning
+def check_qr(seed: int = 3) -> None:
+    """Q·R = Π1X, QᵀQ = I, R upper with positive diagonal, RᵀR = Gram (Cholesky route),
+    R·M = Π2, and Π1X·R⁻¹ has orthonormal columns (Figure 2, step 2)."""
+    g = np.random.default_rng(seed)
+    A = g.standard_normal((355, 17)) * (10.0 ** g.uniform(-2, 2, 17))[None, :]
+    qm, rm = condition.qr_positive(A)
+    assert np.allclose(qm @ rm, A, rtol=0, atol=1e-12 * np.abs(A).max()), "QR product"
+    assert np.allclose(qm.T @ qm, np.eye(17), atol=1e-13), "Q orthonormal"
+    assert np.allclose(rm, np.triu(rm)), "R upper"
+    assert np.all(np.diag(rm) > 0), "diag R > 0"
+    chol = np.linalg.cholesky(A.T @ A).T
+    assert np.allclose(rm, chol, rtol=1e-8, atol=1e-8 * np.abs(rm).max()), "R vs Cholesky"
+    pi2 = rng.pi2_matrix(1, 0, 17, 16)
+    mm = condition.m_matrix(rm, pi2)
+    assert np.allclose(rm @ mm, pi2, rtol=1e-11, atol=1e-11 * np.abs(pi2).max()), "R·M = Π2"
+    ri = condition.r_inverse(rm)
+    assert np.allclose((A @ ri).T @ (A @ ri), np.eye(17), atol=1e-10), "Π1X R⁻¹ orthonormal"
+    bad = A.copy()
+    bad[:, 3] = bad[:, 2]
+    try:
+        condition.check_rank(condition.qr_positive(bad)[1])
+    except condition.RankDeficient:
+        pass
+    else:
+        raise AssertionError("rank deficiency not detected")
+
+
+# ----------------------------------------------------------------- leverage
+def _half_cauchy_median_fraction(r2: int, k: int) -> float:
+    f = lambda x: 2.0 / math.pi * math.atan(x)   # noqa: E731  CDF of |Cauchy|
+    return float(stats.binom.sf(k - 1, r2, f(1.5)) - stats.binom.sf(k - 1, r2, f(0.5)))
+
+
+def check_lambda_distribution(r2: int = 16, seeds: int = 300, rows: int = 128) -> None:
+    """Λ_ij / ‖U_(i)‖₁ is standard Cauchy (proof of the fast ℓ1 regression theorem), and
+    the share of rows with ½‖U_(i)‖₁ ≤ λ_i ≤ 3/2‖U_(i)‖₁ matches the exact order-statistic
+    value for the lower median of r2 half-Cauchys (0.8328 for r2 = 16)."""
+    g = np.random.default_rng(17)
+    X = g.standard_normal((rows, 6)) * np.array([1, 10, 0.1, 3, 1, 1.0])[None, :]
+    _, rm = condition.qr_positive(g.standard_normal((40, 6)))
+    ri = condition.r_inverse(rm)
+    norms = leverage.exact_row_l1(X, ri)
+    assert np.allclose(norms, np.abs(X @ np.linalg.inv(rm)).sum(1), rtol=1e-12)
+    fr, std = [], []
+    for sd in range(seeds):
+        pi2 = rng.pi2_matrix(500 + sd, 0, 6, r2)
+        mm = condition.m_matrix(rm, pi2)
+        lam = leverage.lambda_estimates(X, mm)
+        i = sd % rows                      # one row per seed: its r2 entries are independent
+        std.append((X[i] @ mm) / norms[i])
+        ratio = lam / norms
+        fr.append(np.mean((ratio >= 0.5) & (ratio <= 1.5)))
+    fr = np.array(fr)
+    assert stats.kstest(np.concatenate(std), "cauchy").pvalue > 1e-4, "Λ/‖U‖₁ not Cauchy"
+    want = _half_cauchy_median_fraction(r2, (r2 - 1) // 2 + 1)
+    se = fr.std(ddof=1) / math.sqrt(seeds)
+    assert abs(fr.mean() - want) < 4 * se + 1e-3, f"median fraction {fr.mean()} vs {want}"
+
+
+# ----------------------------------------------------------------- sampling
+def check_sampling(seed: int = 21) -> None:
+    """p̂ = min(1, m_s λ/Σλ) sums to m_s when no row saturates; kept rows satisfy u < p̂ in
+    ascending order; S concentrates at Σp̂; the Horvitz–Thompson sum Σ_kept |r_i|/p̂_i is
+    unbiased for ‖r‖₁ (ℓ1 sampling lemma, E[D_ii] = 1)."""
+    g = np.random.default_rng(seed)
+    n = 50000
+    flat = g.uniform(1.0, 2.0, 4000)
+    pf, tf, _ = sampling.probabilities(flat, 500.0)
+    assert pf.max() < 1.0 and math.isclose(pf.sum(), 500.0, rel_tol=1e-12), "Σp̂ = m_s"
+    lam = np.abs(g.standard_cauchy(n)) + 0.01
+    lam[:3] = 1e6                                           # saturating rows
+    p, tau, total = sampling.probabilities(lam, 1000.0)
+    assert math.isclose(total, math.fsum(lam.tolist()), rel_tol=0)
+    assert np.all(p[:3] == 1.0) and p.max() <= 1.0 and p.sum() <= 1000.0 * (1 + 1e-12)
+    free = p < 1.0
+    assert np.allclose(p[free] / lam[free], tau, rtol=1e-15)
+    assert math.isclose(tau, 1000.0 / total, rel_tol=1e-15)
+    u = rng.sample_uniforms(seed, 0, np.arange(n))
+    idx, w = sampling.bernoulli_sample(p, u)
+    mask = np.zeros(n, bool)
+    mask[idx] = True
+    assert np.array_equal(mask, u < p) and np.all(np.diff(idx) > 0)
+    assert np.allclose(w, 1.0 / p[idx], rtol=0)
+    es, var = p.sum(), (p * (1 - p)).sum()
+    assert abs(idx.size - es) < 5 * math.sqrt(var) + 1
+    r = np.abs(g.standard_normal(n)) * lam
+    est = []
+    for sd in range(200):
+        u = rng.sample_uniforms(seed + 1 + sd, 0, np.arange(n))
+        k, ww = sampling.bernoulli_sample(p, u)
+        est.append(np.sum(ww * r[k]))
+    est = np.array(est)
+    assert abs(est.mean() - r.sum()) < 5 * est.std(ddof=1) / math.sqrt(est.size), "HT biased"
+
+
+# ----------------------------------------------------------------- solve
+def check_solver(seed: int = 8) -> None:
+    """LP optimum = brute-force vertex optimum on tiny instances; = weighted median for a
+    single all-ones column; = per-coordinate weighted median for canonical-vector rows
+    (the separable design of the large-scale experiment, §6.3)."""
+    g = np.random.default_rng(seed)
+    for m, d in ((7, 1), (9, 2), (12, 3), (11, 2)):
+        A = g.standard_normal((m, d))
+        b = g.standard_normal(m) * 3
+        w = g.uniform(0.2, 3.0, m)
+        _, f_lp = solve.lad_lp(A, b, w)
+        _, f_bf = solve.lad_bruteforce(A, b, w)
+        assert math.isclose(f_lp, f_bf, rel_tol=1e-12, abs_tol=1e-12), f"LP vs brute force {m}x{d}"
+    b = g.standard_cauchy(301)
+    w = g.uniform(0.5, 2.0, 301)
+    x, f = solve.lad_lp(np.ones((301, 1)), b, w)
+    med = solve.weighted_median(b, w)
+    assert math.isclose(f, solve.weighted_objective(np.ones((301, 1)), b, w, [med]), rel_tol=1e-12)
+    d = 5
+    rows = g.integers(0, d, 400)
+    A = np.eye(d)[rows]
+    b = g.standard_normal(400) + rows
+    w = g.uniform(0.5, 2.0, 400)
+    x, f = solve.lad_lp(A, b, w)
+    xm = np.array([solve.weighted_median(b[rows == j], w[rows == j]) for j in range(d)])
+    assert math.isclose(f, solve.weighted_objective(A, b, w, xm), rel_tol=1e-12), "canonical rows"
+    Xr = np.array([[1.0, 2.0], [3.0, -1.0]])
+    assert np.allclose(pipeline.form_x(Xr, np.array([5.0, 7.0])) @ np.array([0.5, -1.0, 1.0]),
+                       Xr @ np.array([0.5, -1.0]) - np.array([5.0, 7.0])), "X·[x;1] = Ax − b"
+
+
+ALL_CHECKS = [check_hadamard_closed_form, check_cauchy_quantiles, check_draw_statistics,
+              check_fct_dense, check_fct_blocks, check_fct_mass, check_fct_stability,
+              check_qr, check_lambda_distribution, check_sampling, check_solver]

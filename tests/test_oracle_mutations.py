@@ -1,0 +1,154 @@
+"""Plant plausible mistakes in the FP64 oracle and check that a pin catches each.
+
+Every mutation is applied to the oracle on the CPU with monkeypatch; the test
+passes only if the named pin check raises AssertionError on the mutated
+oracle.  This shows the pins in pins.py are not vacuous.
+"""
+import numpy as np
+import pytest
+
+import pins
+from oracle import condition, fct, leverage, pipeline, rng, sampling, solve
+
+ORIG_EMBED = fct.fct1_embed
+ORIG_HAD = fct.sylvester_hadamard
+ORIG_CAUCHY = rng.cauchy_from_k
+ORIG_QR = condition.qr_positive
+ORIG_M = condition.m_matrix
+ORIG_LAMBDA = leverage.lambda_estimates
+ORIG_PROB = sampling.probabilities
+ORIG_BERN = sampling.bernoulli_sample
+ORIG_LP = solve.lad_lp
+ORIG_FORMX = pipeline.form_x
+
+
+def _draws_of(X, s, r1, seed, problem_id, row_offset, draws):
+    if draws is not None:
+        return dict(draws)
+    n_pad = fct.padded_rows(X.shape[0], s)
+    return rng.fct_draws(seed, problem_id, row_offset + np.arange(n_pad), r1)
+
+
+def embed_no_identity(X, s, r1, seed=0, problem_id=0, row_offset=0, sign_flip=True, draws=None):
+    dr = _draws_of(X, s, r1, seed, problem_id, row_offset, draws)
+    dr["cauchy_i"] = np.zeros_like(dr["cauchy_i"])
+    return ORIG_EMBED(X, s, r1, seed, problem_id, row_offset, sign_flip, dr)
+
+
+def embed_no_hadamard(X, s, r1, seed=0, problem_id=0, row_offset=0, sign_flip=True, draws=None):
+    dr = _draws_of(X, s, r1, seed, problem_id, row_offset, draws)
+    dr["cauchy_h"] = np.zeros_like(dr["cauchy_h"])
+    return ORIG_EMBED(X, s, r1, seed, problem_id, row_offset, sign_flip, dr)
+
+
+def embed_factor2(*a, **k):
+    p, t = ORIG_EMBED(*a, **k)
+    return p / 2, t / 2
+
+
+def embed_swapped_halves(X, s, r1, seed=0, problem_id=0, row_offset=0, sign_flip=True, draws=None):
+    dr = _draws_of(X, s, r1, seed, problem_id, row_offset, draws)
+    dr["hash_h"], dr["hash_i"] = dr["hash_i"], dr["hash_h"]
+    return ORIG_EMBED(X, s, r1, seed, problem_id, row_offset, sign_flip, dr)
+
+
+def embed_sign_ignored(X, s, r1, seed=0, problem_id=0, row_offset=0, sign_flip=True, draws=None):
+    return ORIG_EMBED(X, s, r1, seed, problem_id, row_offset, False, draws)
+
+
+def embed_abs_terms_wrong(*a, **k):
+    p, t = ORIG_EMBED(*a, **k)
+    return p, np.abs(p)
+
+
+def had_unnormalized_sign(s):
+    h = np.ones((1, 1))
+    while h.shape[0] < s:
+        h = np.block([[h, h], [-h, h]])
+    return h
+
+
+def had_scaled(s):
+    return ORIG_HAD(s) * np.sqrt(s)
+
+
+def cauchy_neg(k):
+    return -ORIG_CAUCHY(k)
+
+
+def cauchy_offset(k):
+    k = np.asarray(k, dtype=np.int64)
+    u = k.astype(np.float64) * 2.0 ** -24
+    return np.tan(np.pi * (u - 0.5))
+
+
+def qr_no_signfix(pix):
+    return np.linalg.qr(np.asarray(pix, dtype=np.float64), mode="reduced")
+
+
+def qr_transposed(pix):
+    q, r = ORIG_QR(pix)
+    return q, r.T
+
+
+def m_times_r(r_mat, pi2):
+    return r_mat @ pi2
+
+
+def lambda_upper_median(X, M, chunk=1 << 20):
+    lam = np.abs(np.asarray(X, dtype=np.float64) @ M)
+    return np.sort(lam, axis=1)[:, M.shape[1] // 2]
+
+
+def lambda_no_rinv(X, M, chunk=1 << 20):
+    return ORIG_LAMBDA(X, M * np.linspace(0.2, 5.0, M.shape[0])[:, None])
+
+
+def prob_no_cap(lam, coreset, total=None):
+    p, tau, tot = ORIG_PROB(lam, coreset, total)
+    lam = np.asarray(lam, dtype=np.float64)
+    return tau * lam, tau, tot
+
+
+def bern_weights_p(p, u):
+    idx, w = ORIG_BERN(p, u)
+    return idx, 1.0 / w
+
+
+def lp_unweighted(A, b, w=None):
+    return ORIG_LP(A, b, None)
+
+
+def formx_plus_b(A, b):
+    return np.concatenate([np.asarray(A, float), np.asarray(b, float)[:, None]], axis=1)
+
+
+MUTATIONS = [
+    ("identity half dropped", fct, "fct1_embed", embed_no_identity, pins.check_fct_dense),
+    ("Hadamard half dropped", fct, "fct1_embed", embed_no_hadamard, pins.check_fct_dense),
+    ("factor 4 → 2", fct, "fct1_embed", embed_factor2, pins.check_fct_blocks),
+    ("halves swapped", fct, "fct1_embed", embed_swapped_halves, pins.check_fct_dense),
+    ("sign flip ignored", fct, "fct1_embed", embed_sign_ignored, pins.check_fct_dense),
+    ("Σ|terms| wrong", fct, "fct1_embed", embed_abs_terms_wrong, pins.check_fct_mass),
+    ("Hadamard recursion sign", fct, "sylvester_hadamard", had_unnormalized_sign, pins.check_hadamard_closed_form),
+    ("Hadamard not normalized", fct, "sylvester_hadamard", had_scaled, pins.check_fct_blocks),
+    ("Cauchy sign", rng, "cauchy_from_k", cauchy_neg, pins.check_cauchy_quantiles),
+    ("Cauchy cell edge", rng, "cauchy_from_k", cauchy_offset, pins.check_cauchy_quantiles),
+    ("R sign not fixed", condition, "qr_positive", qr_no_signfix, pins.check_qr),
+    ("R transposed", condition, "qr_positive", qr_transposed, pins.check_qr),
+    ("R·Π2 for R⁻¹·Π2", condition, "m_matrix", m_times_r, pins.check_qr),
+    ("upper median", leverage, "lambda_estimates", lambda_upper_median, pins.check_lambda_distribution),
+    ("R⁻¹ distorted", condition, "m_matrix", lambda r, p: ORIG_M(r, p) * np.linspace(0.2, 5, r.shape[0])[:, None],
+     pins.check_lambda_distribution),
+    ("p̂ not capped at 1", sampling, "probabilities", prob_no_cap, pins.check_sampling),
+    ("weight p̂ for 1/p̂", sampling, "bernoulli_sample", bern_weights_p, pins.check_sampling),
+    ("LP ignores weights", solve, "lad_lp", lp_unweighted, pins.check_solver),
+    ("X = [A, +b]", pipeline, "form_x", formx_plus_b, pins.check_solver),
+]
+
+
+@pytest.mark.parametrize("name,mod,attr,bad,check", MUTATIONS, ids=[m[0] for m in MUTATIONS])
+def test_pin_catches_mutation(monkeypatch, name, mod, attr, bad, check):
+    monkeypatch.setattr(mod, attr, bad)
+    with pytest.raises(AssertionError):
+        check()
