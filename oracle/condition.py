@@ -15,7 +15,7 @@ from __future__ import annotations
 import numpy as np
 from scipy.linalg import solve_triangular
 
-RANK_TOL = 1e-13
+RANK_TOL = 1e-5
 
 
 class RankDeficient(ValueError):
@@ -31,8 +31,12 @@ def qr_positive(pix: np.ndarray):
 
 
 def check_rank(r_mat: np.ndarray, tol: float = RANK_TOL) -> None:
+    """Full column rank (§2 assumes it) to the precision Π1·X is formed in: column k of
+    Π1X = QR has norm ‖R_{:k,k}‖₂, and it is dependent on the columns before it when
+    |R_kk| ≤ tol·‖R_{:k,k}‖₂ (1e-5: Π1·X is accumulated in FP32 on the GPU)."""
     dg = np.abs(np.diag(r_mat))
-    if dg.size == 0 or not np.all(np.isfinite(r_mat)) or dg.min() <= tol * dg.max():
+    coln = np.linalg.norm(np.triu(r_mat), axis=0)
+    if dg.size == 0 or not np.all(np.isfinite(r_mat)) or np.any(dg <= tol * coln):
         raise RankDeficient("Π1·X is numerically rank deficient")
 
 

@@ -54,8 +54,12 @@ def fct1_embed(X: np.ndarray, s: int, r1: int, seed: int = 0, problem_id: int = 
                row_offset: int = 0, sign_flip: bool = True, draws: dict | None = None):
     """Π1·X in FP64, block by block, and the per-entry sum of |terms|.
 
-    Returns (PiX, T): PiX ∈ R^{r1×q}; T[r, c] = Σ |4·c_v·g_{v,c}| over the
-    virtual rows v hashed to bucket r, the scale the FP32 tolerance refers to.
+    Returns (PiX, T): PiX ∈ R^{r1×q}, and T, the sum of |contributing terms| of
+    each entry: (Π1X)_rc = Σ_k (Π1)_rk·X_kc expands, through H̃, into the terms
+    4·c_v·(H̃)_vk·σ_k·X_kc over the virtual rows v hashed to r and the rows k of
+    v's block, so T_rc = Σ_{v→r} 4|c_v|·Σ_k |(H̃)_vk|·|X_kc|, i.e. 4|c_v|·|z_vc|
+    for an identity row and 4|c_v|·Σ_{k∈block}|z_kc|/√s for a Hadamard row.
+    This is the scale the FP32 tolerance refers to.
     `draws` may replace the generated draws (tests use this to set C ≡ 1).
     """
     X = np.asarray(X, dtype=np.float64)
@@ -72,6 +76,9 @@ def fct1_embed(X: np.ndarray, s: int, r1: int, seed: int = 0, problem_id: int = 
     g_i = z                                                   # I_s·z_β per block
     t_h = 4.0 * dr["cauchy_h"][:n_pad, None] * g_h            # 4·C on the Hadamard half
     t_i = 4.0 * dr["cauchy_i"][:n_pad, None] * g_i            # 4·C on the identity half
+    zabs = np.abs(z).reshape(nb, s, q).sum(axis=1) / np.sqrt(s)              # Σ_k |H_s,ιk|·|z_k| per block
+    a_h = 4.0 * np.abs(dr["cauchy_h"][:n_pad, None]) * np.repeat(zabs, s, axis=0)
+    a_i = np.abs(t_i)
     hh = dr["hash_h"][:n_pad]
     hi = dr["hash_i"][:n_pad]
     pix = np.zeros((r1, q))
@@ -79,8 +86,8 @@ def fct1_embed(X: np.ndarray, s: int, r1: int, seed: int = 0, problem_id: int = 
     for c in range(q):                                        # B: sum each virtual row into its bucket
         pix[:, c] = (np.bincount(hh, weights=t_h[:, c], minlength=r1)
                      + np.bincount(hi, weights=t_i[:, c], minlength=r1))
-        tsum[:, c] = (np.bincount(hh, weights=np.abs(t_h[:, c]), minlength=r1)
-                      + np.bincount(hi, weights=np.abs(t_i[:, c]), minlength=r1))
+        tsum[:, c] = (np.bincount(hh, weights=a_h[:, c], minlength=r1)
+                      + np.bincount(hi, weights=a_i[:, c], minlength=r1))
     return pix, tsum
 
 

@@ -30,7 +30,8 @@ conventions; the paper only fixes the distributions):
 A standard Cauchy variate from a 24-bit integer k is the inverse CDF at the
 cell midpoint u = (k + ½)·2^-24, written with the reflected argument so that it
 is accurate near the poles: with m = 2k + 1 − 2^24 (odd) and
-w = (2^24 − |m|)·2^-25 ∈ (0, ½], c = sign(m)·cos(πw)/sin(πw) = tan(π(u − ½)).
+w = (2^24 − |m|)·2^-25 ∈ (0, ½], c = sign(m)·cos(πw)/sin(πw) = tan(π(u − ½)),
+evaluated as sign(m)·sin(π|m|·2^-25)/sin(πw) (cos(πw) = sin(π(½ − w))).
 """
 from __future__ import annotations
 
@@ -87,12 +88,18 @@ def bucket(word, r1: int):
 
 
 def cauchy_from_k(k):
-    """Standard Cauchy from a 24-bit integer k (inverse CDF at (k+½)/2^24), FP64."""
+    """Standard Cauchy from a 24-bit integer k (inverse CDF at (k+½)/2^24), FP64.
+
+    With v = u − ½ and w = ½ − |v| (both exact), tan(πv) = sign(v)·cos(πw)/sin(πw)
+    and cos(πw) = sin(π|v|), so c = sign(v)·sin(π|v|)/sin(πw): both sines take
+    arguments in (0, π/2] and keep full relative accuracy at both ends.
+    """
     k = np.asarray(k, dtype=np.int64)
     m = 2 * k + 1 - (1 << 24)
     w = ((1 << 24) - np.abs(m)).astype(np.float64) * 2.0 ** -25
+    v = np.abs(m).astype(np.float64) * 2.0 ** -25
     sign = np.where(m > 0, 1.0, -1.0)
-    return sign * np.cos(np.pi * w) / np.sin(np.pi * w)
+    return sign * np.sin(np.pi * v) / np.sin(np.pi * w)
 
 
 def fct_draws(seed: int, problem_id: int, rows, r1: int) -> dict:

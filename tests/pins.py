@@ -45,6 +45,16 @@ def check_cauchy_quantiles(step: int = 1) -> None:
     assert np.array_equal(np.sign(c), np.sign(u - 0.5)), "Cauchy sign"
     mid = np.abs(u - 0.5) < 0.4
     assert np.allclose(c[mid], np.tan(np.pi * (u[mid] - 0.5)), rtol=1e-12, atol=1e-15), "tan form"
+    try:
+        import mpmath
+    except ImportError:
+        return
+    mpmath.mp.prec = 120
+    for kk in (0, 1, 2, 1000, (1 << 23) - 2, (1 << 23) - 1, 1 << 23, (1 << 23) + 1, (1 << 24) - 2, (1 << 24) - 1,
+               5_000_000, 12_345_678):
+        exact = mpmath.tan(mpmath.pi * (mpmath.mpf(kk) + mpmath.mpf(0.5) - mpmath.mpf(2) ** 23) / mpmath.mpf(2) ** 24)
+        got = float(rng.cauchy_from_k(np.array([kk]))[0])
+        assert abs(got - float(exact)) <= 4e-16 * abs(float(exact)), f"relative accuracy at k={kk}"
 
 
 def check_draw_statistics(n: int = 1 << 18, r1: int = 97, seed: int = 12345) -> None:
@@ -131,12 +141,15 @@ def check_fct_blocks(seed: int = 11) -> None:
                 n2 = np.sum(zb[:, c] ** 2)
                 assert math.isclose(np.sum(gz ** 2), 2 * n2, rel_tol=1e-12, abs_tol=1e-12), "energy"
                 assert np.sum(np.abs(gz)) >= 0.5 * s ** 0.25 * math.sqrt(n2) - 1e-12, "uncertainty"
-        assert np.allclose(tsum, np.abs(pix), atol=1e-13), "T with one term per bucket"
+        assert np.allclose(tsum[1::2], np.abs(pix[1::2]), atol=1e-13), "T of an identity row"
+        blocksum = np.repeat(np.abs(z).reshape(-1, s, 3).sum(axis=1), s, axis=0)
+        assert np.allclose(tsum[0::2], 4.0 * blocksum / math.sqrt(s), rtol=1e-13), "T of a Hadamard row"
 
 
 def check_fct_mass(seed: int = 5) -> None:
-    """With C ≡ 1 and random buckets, Σ_rows Π1X = 4·Σ g and Σ_rows T = 4‖g‖₁ per column
-    (the hashed sums γ_j add up to ‖g‖₁, proof of FCT1)."""
+    """With C ≡ 1 and random buckets, Σ_rows Π1X = 4·Σ g per column (the hashed sums add
+    up, proof of FCT1), and Σ_rows T = 4·(1 + √s)·‖z‖₁: every input entry enters one identity
+    row and the s Hadamard rows of its block with |H_s entry| = 1/√s."""
     g = np.random.default_rng(seed)
     n, s, r1 = 700, 64, 19
     X = g.standard_normal((n, 4))
@@ -146,7 +159,8 @@ def check_fct_mass(seed: int = 5) -> None:
     pix, tsum = fct.fct1_embed(X, s, r1, draws=dr)
     dense_g = _explicit_g(X, s, dr["sigma"])
     assert np.allclose(pix.sum(0), 4 * dense_g.sum(0), rtol=1e-12), "mass"
-    assert np.allclose(tsum.sum(0), 4 * np.abs(dense_g).sum(0), rtol=1e-12), "ℓ1 mass"
+    z1 = np.abs(dense_g[fct.padded_rows(n, s):]).sum(0)          # identity half = z
+    assert np.allclose(tsum.sum(0), 4 * (1 + math.sqrt(s)) * z1, rtol=1e-12), "ℓ1 mass"
 
 
 def _explicit_g(X, s, sigma):
@@ -162,8 +176,9 @@ def _explicit_g(X, s, sigma):
 
 
 def check_fct_stability(seeds: int = 40) -> None:
-    """Conditional on B, (Π1X)_jc is a Cauchy scaled by 4·Σ_{v→j}|g_v| (1-stability, §2):
-    the standardized entries pooled over seeds pass a KS test against Cauchy(0,1)."""
+    """Conditional on B, (Π1X)_jc is a Cauchy scaled by γ_jc = 4·Σ_{v→j}|g_vc| with g = H̃·D·x
+    (1-stability, §2; proof of FCT1): the standardized entries pooled over seeds pass a KS test
+    against Cauchy(0,1).  g comes from the closed-form Walsh matrix, not from the oracle."""
     g = np.random.default_rng(99)
     n, s, r1 = 512, 64, 13
     X = g.standard_normal((n, 3))
@@ -171,9 +186,10 @@ def check_fct_stability(seeds: int = 40) -> None:
     for sd in range(seeds):
         dr = rng.fct_draws(1000 + sd, 0, np.arange(n), r1)
         pix, _ = fct.fct1_embed(X, s, r1, draws=dr)
-        ones = dict(dr, cauchy_h=np.ones(n), cauchy_i=np.ones(n))
-        _, t1 = fct.fct1_embed(X, s, r1, draws=ones)
-        vals.append((pix / t1).ravel())
+        gfull = np.abs(_explicit_g(X, s, dr["sigma"]))          # [Hadamard half; identity half]
+        buckets = np.concatenate([dr["hash_h"], dr["hash_i"]])
+        gam = np.stack([4.0 * np.bincount(buckets, weights=gfull[:, c], minlength=r1) for c in range(3)], axis=1)
+        vals.append((pix / gam).ravel())
     v = np.concatenate(vals)
     assert stats.kstest(v, "cauchy").pvalue > 1e-4, "Π1X entries not Cauchy-scaled"
 
