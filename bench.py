@@ -1,0 +1,354 @@
+"""Rows/s through the FCT + ℓ1-sampling pass (Figure 2, steps 1-7) on GB300.
+
+One step = fct_embed (Π1·X), l1_condition (QR, M = R⁻¹Π2) and l1_sample (λ,
+Σλ, p̂, Bernoulli keep, compaction, coreset gather) over the n = 2^22, d = 16
+workload (columns scaled by 10^U(−2,2), Laplace noise with 5% Cauchy(0,100)
+outliers; s = 256, r1 = 355, r2 = 16, m_s = 20000), inputs resident in HBM.
+It prints one JSON line; see the design doc for the roofline figures it carries.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+Under torchrun each rank runs its own problem (problem_id = rank) on its own
+GPU: weak scaling with no collective on the data path.  `--impl reference`
+times the FP64 CPU oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "colscale_n4M_d16"
+METRIC = "Rows/s through FCT+ℓ1 sampling, % HBM peak; BF16/batched vs plain FP32"
+UNIT = "rows/s"
+L2_BYTES = 129 * 2 ** 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def measured_peaks() -> dict:
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return {"hbm_gbs": d["hbm_gbs"], "source": "measured"}
+    return {"hbm_gbs": 6800.0, "source": "fallback"}
+
+
+def algorithmic_bytes(n: int, d: int, elem: int, coreset_rows: int) -> dict:
+    """Bytes the method must move: X read in phase 1 and phase 2, λ written and read
+    back, and the coreset gather (index, weight, FP64 row) — D, C, B, Π2 are
+    counter-generated and never stored."""
+    q = d + 1
+    x_bytes = n * (d * elem + 4)
+    phase1 = x_bytes
+    phase2 = x_bytes + 4 * n
+    phase3 = 4 * n + n // 8 + coreset_rows * (16 + 8 * q + d * elem + 4)
+    return {"phase1": phase1, "phase2": phase2, "phase3": phase3, "step": phase1 + phase2 + phase3}
+
+
+# ----------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self) -> dict:
+        if self.proc is None or not self.path:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ----------------------------------------------------------------- CPU oracle baseline
+def cpu_oracle_rows_per_s(pr: dict, w, seconds: float) -> dict:
+    """The FP64 oracle as it stands, steps 1-7 (no LP), on a bounded prefix of the workload."""
+    import numpy as np
+
+    from oracle import pipeline
+
+    rows = 1 << 17
+    A = pr["A"][:rows]
+    b = pr["b"][:rows]
+    done, t_total, reps = 0, 0.0, 0
+    while t_total < seconds or reps == 0:
+        t0 = time.perf_counter()
+        pipeline.fast_cauchy_regression(A, b, w.s, w.r1, w.r2, w.coreset * rows / w.n, w.seed, w.problem_id,
+                                        solve_lp=False)
+        t_total += time.perf_counter() - t0
+        done += rows
+        reps += 1
+    threads = None
+    try:
+        from threadpoolctl import threadpool_info
+
+        threads = max((i.get("num_threads", 1) for i in threadpool_info()), default=1)
+    except Exception:
+        threads = None
+    cores = os.cpu_count()
+    return {"value": done / t_total, "unit": UNIT, "cores": threads or cores, "kind": "oracle",
+            "sample": f"first {rows} rows of {w.name} (n={w.n}), {reps} passes of Figure 2 steps 1-7 "
+                      f"in FP64 numpy, {t_total:.1f} s; m_s scaled to the sample",
+            "host_cores": cores}
+
+
+def run_reference(args) -> None:
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from synth import WORKLOADS, make_problem
+
+    w = WORKLOADS[args.workload]
+    pr = make_problem(w, n=1 << 17)
+    times = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        from oracle import pipeline
+
+        pipeline.fast_cauchy_regression(pr["A"], pr["b"], w.s, w.r1, w.r2, w.coreset * (1 << 17) / w.n,
+                                        w.seed, w.problem_id, solve_lp=False)
+        if i >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    rows = 1 << 17
+    val = rows * len(times) / sum(times)
+    cores = os.cpu_count()
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": w.name, "n": w.n, "d": w.d, "s": w.s, "r1": w.r1,
+                                             "r2": w.r2, "coreset": w.coreset, "sample_rows": rows},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"each step: the FP64 oracle (Figure 2 steps 1-7, numpy) on the "
+                                       f"first {rows} rows of {w.name}"},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------- GPU arm
+def run_gpu(args) -> None:
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_1207_4684_gb300 as L
+    from synth import WORKLOADS, make_problem
+
+    w = WORKLOADS[args.workload]
+    pr = make_problem(w)
+    n, d = pr["A"].shape
+    q = d + 1
+    bf16 = pr["A"].dtype == np.uint16
+    dt = L.BF16 if bf16 else L.F32
+    elem = 2 if bf16 else 4
+    if bf16:
+        A = torch.from_numpy(pr["A"].view(np.int16)).view(torch.bfloat16).to(dev)
+    else:
+        A = torch.from_numpy(pr["A"]).to(dev)
+    b = torch.from_numpy(pr["b"]).to(dev)
+    prm = L.make_params(w.s, w.r1, w.r2, w.coreset, seed=w.seed, problem_id=rank)
+    ws = L.workspace(prm, n, d, dt, device=dev)
+    cap = int(2 * w.coreset) + 64
+    idx = torch.empty(cap, dtype=torch.int64, device=dev)
+    wts = torch.empty(cap, dtype=torch.float64, device=dev)
+    core = torch.empty((cap, q), dtype=torch.float64, device=dev)
+    cnt = torch.zeros(1, dtype=torch.int64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        L.l1_coreset(A, b, prm, cap, idx, wts, core, cnt, ws, stream=stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    flags = L.l1s_status_read(ws)
+    kept = int(cnt.item())
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    # ---- timed region: K steps, CUDA events on the launching stream
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        barrier()
+        t_host0 = time.perf_counter()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step()
+        ev1.record(stream)
+        barrier()
+        t_host = time.perf_counter() - t_host0
+    gpu_ms = ev0.elapsed_time(ev1)
+    if world > 1:
+        t = torch.tensor([gpu_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        gpu_ms = float(t.item())
+    ms_per_step = gpu_ms / args.steps
+    value = world * n * args.steps / (gpu_ms / 1e3)
+
+    # ---- per-phase times (same work, split into the three entry points with events between)
+    R = torch.empty((q, q), dtype=torch.float64, device=dev)
+    M = torch.empty((q, w.r2), dtype=torch.float64, device=dev)
+    pix = torch.empty((w.r1, q), dtype=torch.float32, device=dev)
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    acc = [0.0, 0.0, 0.0]
+    for it in range(args.warmup + args.steps):
+        evs[0].record(stream)
+        L.fct_embed(A, b, prm, pix, ws, stream=stream)
+        evs[1].record(stream)
+        L.l1_condition(pix, prm, R, M, ws, stream=stream)
+        evs[2].record(stream)
+        L.l1_sample(A, b, M, prm, cap, idx, wts, core, cnt, None, ws, stream=stream)
+        evs[3].record(stream)
+        if it >= args.warmup:
+            torch.cuda.synchronize(dev)
+            for k in range(3):
+                acc[k] += evs[k].elapsed_time(evs[k + 1])
+    phase_ms = [a / args.steps for a in acc]
+
+    # ---- end to end through the public API with host buffers (copies inside the timed region)
+    ws_h = L.workspace(prm, n, d, dt, host_staging=True, device=dev)
+    A_h = torch.from_numpy(pr["A"].view(np.int16) if bf16 else pr["A"]).pin_memory()
+    b_h = torch.from_numpy(pr["b"]).pin_memory()
+    idx_h = torch.empty(cap, dtype=torch.int64).pin_memory()
+    w_h = torch.empty(cap, dtype=torch.float64).pin_memory()
+    cnt_h = torch.zeros(1, dtype=torch.int64)
+    e2e_steps = max(3, min(args.steps, 10))
+    for _ in range(2):
+        L.l1_coreset_host(A_h, b_h, prm, cap, idx_h, w_h, cnt_h, ws_h, stream=stream)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        rc = L.l1_coreset_host(A_h, b_h, prm, cap, idx_h, w_h, cnt_h, ws_h, stream=stream)
+    barrier()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    if world > 1:
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    del ws_h
+
+    # ---- roofline of the dominant kernel (phase-level events bracket it)
+    peaks = measured_peaks()
+    ab = algorithmic_bytes(n, d, elem, kept)
+    names = ["fct_embed", "l1_condition", "l1_sample"]
+    dom = max(range(3), key=lambda k: phase_ms[k])
+    dom_bytes = [ab["phase1"], 0, ab["phase2"] + ab["phase3"]][dom]
+    achieved = dom_bytes / (phase_ms[dom] / 1e3) / 1e9
+    step_gbs = ab["step"] / (ms_per_step / 1e3) / 1e9
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(prof):
+        with open(prof) as f:
+            tr = json.load(f)
+        traffic = tr.get(f"{names[dom]}:{w.name}")
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16" if bf16 else "f32", "data": "synthetic",
+        "config": {"workload": w.name, "n": n, "d": d, "q": q, "s": w.s, "r1": w.r1, "r2": w.r2,
+                   "coreset": w.coreset, "parallelism": f"replicas{world}",
+                   "l2": f"inputs {n * (d * elem + 4) / 2**20:.0f} MiB exceed the {L2_BYTES // 2**20} MiB L2; no flush"},
+        "roofline": {"kernel": names[dom], "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
+                     "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
+                     "peak_source": peaks["source"], "algorithmic_bytes": dom_bytes,
+                     "launch_ms": phase_ms[dom]},
+        "step_roofline": {"achieved": step_gbs, "frac": step_gbs / peaks["hbm_gbs"],
+                          "algorithmic_bytes": ab["step"]},
+        "phase_ms": dict(zip(names, phase_ms)),
+        "e2e": {"value": world * n / e2e_s, "unit": UNIT, "h2d_bytes_per_step": n * (d * elem + 4),
+                "d2h_bytes_per_step": 8 + cap * 16, "status": rc},
+        "gpu_launches": 7 * args.steps,
+        "clocks": clk.summary(),
+        "coreset_rows": kept, "status_flags": flags, "host_wall_s": t_host,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_oracle_rows_per_s(pr, w, args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

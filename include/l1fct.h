@@ -1,0 +1,216 @@
+/*
+ * l1fct — Fast Cauchy Transform ℓ1 regression on NVIDIA GB300 (sm_103a).
+ *
+ * C ABI of the library libl1fct.so.  The method is FastCauchyRegression
+ * (Clarkson, Drineas, Magdon-Ismail, Mahoney, Meng, Woodruff, "The Fast
+ * Cauchy Transform and Faster Robust Linear Regression", Figure 2) for the
+ * problem statement min_x ‖A·x − b‖₁ (§4.2, eq. (original_prob)).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - A is n × d, row-major with leading dimension lda ≥ d (elements), stored
+ *   FP32 or BF16 (l1s_dtype); b is n FP32 values.  X = [A, −b] (n × q,
+ *   q = d + 1) is never materialised; −b is applied on load.
+ * - Pointers named *_dev are device pointers; *_host are host pointers.  All
+ *   arrays are owned by the caller.  The library allocates no memory: every
+ *   call that needs scratch takes a caller-allocated device workspace
+ *   (`ws`, `ws_bytes`), sized by l1s_workspace_size and aligned to 256 bytes.
+ *   One workspace must not be used by two calls that overlap on the GPU.
+ * - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *   Unless stated otherwise a call only enqueues work on `stream` and returns.
+ * - Return value: L1S_OK when the arguments were valid and the work was
+ *   enqueued; otherwise an error code and nothing was enqueued.  Conditions
+ *   that only the GPU can see (rank deficiency, non-finite input, zero mass,
+ *   capacity overflow) are OR-ed into a status word inside the workspace and
+ *   read back with l1s_status_read.  l1s_last_error() returns the text of the
+ *   calling thread's last host-side error.
+ * - Random draws come from Philox4x32-10 (Salmon et al., SC'11) keyed by
+ *   params.seed, with counters built from the global row id, params.problem_id
+ *   and a stream number (0: signs/buckets/Cauchy scales of Π1, 1: Π2,
+ *   2: sampling uniforms).  Row ids are global: row r of A has id
+ *   params.global_row_offset + r, so shards of one problem reproduce the
+ *   unsharded draws.
+ * - Not thread-safe per workspace; distinct workspaces may be used from
+ *   distinct threads.  l1_lambda, l1_sample, l1_coreset, l1_coreset_host and
+ *   l1_regress load M into a per-device constant bank: calls of these on
+ *   different streams of one device must not overlap.
+ */
+#ifndef L1FCT_H
+#define L1FCT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define L1S_API __attribute__((visibility("default")))
+#else
+#define L1S_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  L1S_OK = 0,
+  L1S_ERR_INVALID_ARG = 1,   /* an argument violates the documented constraints */
+  L1S_ERR_WORKSPACE = 2,     /* workspace missing, misaligned or too small */
+  L1S_ERR_CUDA = 3,          /* a CUDA runtime call failed (see l1s_last_error) */
+  L1S_ERR_RANK_DEFICIENT = 4,/* status bit: |R_kk| <= 1e-5·‖(Π1X)_{:,k}‖₂ for some k, or R non-finite */
+  L1S_ERR_NONFINITE = 5,     /* status bit: NaN/Inf met in A, b or Π1X */
+  L1S_ERR_ZERO_MASS = 6,     /* status bit: Σλ is zero or not finite */
+  L1S_ERR_CAPACITY = 7,      /* status bit: coreset larger than the caller's capacity */
+  L1S_ERR_NOT_CONVERGED = 8  /* status bit: IRLS stopped at its iteration cap */
+} l1s_status;
+
+/* Bits of the device status word (bit = 1 << (code − 1)). */
+#define L1S_FLAG(code) (1u << ((code) - 1))
+
+typedef enum { L1S_F32 = 0, L1S_BF16 = 1 } l1s_dtype;
+
+typedef struct {
+  uint64_t seed;              /* key of every Philox draw */
+  uint32_t problem_id;        /* counter word 2: independent draws per problem */
+  int32_t s;                  /* Hadamard block size of FCT1, power of two, 1..4096 (§3.1) */
+  int32_t r1;                 /* rows of Π1·X, q ≤ r1 ≤ 65535 (§3.1, r1 = O(d log d)) */
+  int32_t r2;                 /* columns of Π2, 1..64 (Figure 2, step 3) */
+  double coreset_size;        /* m_s > 0: expected coreset size bound (Figure 2, step 6) */
+  int64_t global_row_offset;  /* global id of A's first row; a multiple of s */
+  int32_t sign_flip;          /* 1: Π1·D·X with random ±1 diagonal D; 0: Π1·X as in §3.1 */
+  int32_t reserved;           /* must be 0 */
+} l1s_params;
+
+/* Text of the calling thread's last host-side error ("" if none). */
+L1S_API const char* l1s_last_error(void);
+
+/* Library version string. */
+L1S_API const char* l1s_version(void);
+
+/* Bytes of device workspace that every entry point below needs for a problem
+ * of n rows and d columns with these params on the current device.  With
+ * host_staging = 1 the size also covers the device copies of A and b used by
+ * l1_coreset_host and l1_regress with host inputs. */
+L1S_API int l1s_workspace_size(const l1s_params* params, int64_t n, int32_t d, l1s_dtype dtype,
+                       int32_t host_staging, size_t* bytes);
+
+/* Clear the workspace status word (enqueued on stream). */
+L1S_API int l1s_status_reset(void* ws, size_t ws_bytes, void* stream);
+
+/* Synchronise `stream` and read the workspace status word: *flags is an OR of
+ * L1S_FLAG(code) bits (0 = no device-side error since the last reset). */
+L1S_API int l1s_status_read(const void* ws, size_t ws_bytes, void* stream, uint32_t* flags);
+
+/* Phase 1 — the FCT1 embedding (§3.1; Figure 2, steps 1-2):
+ *   PiX_dev = Π1·X = 4·B·C·H̃·D·[A, −b]          (r1 × q, FP32, row-major)
+ * H̃ is block diagonal with blocks [H_s; I_s] (H_s the Sylvester Hadamard
+ * matrix scaled by 1/√s), C a diagonal of standard Cauchys, B a hash of each
+ * of the 2n virtual rows into r1 buckets, D a ±1 diagonal (params.sign_flip).
+ * n need not be a multiple of s: X is padded with zero rows to the next
+ * multiple of s, and the padded rows' Hadamard virtual rows take the draws of
+ * their row ids.  The r1 × q sums are formed per thread block in shared
+ * memory and combined in a fixed order; float rounding still depends on the
+ * order of shared-memory additions, so repeated calls may differ in the last
+ * bits.  Requires n ≥ 1, 1 ≤ d ≤ 128, lda ≥ d. */
+L1S_API int fct_embed(const void* A_dev, int64_t lda, l1s_dtype dtype, const float* b_dev,
+              int64_t n, int32_t d, const l1s_params* params, float* PiX_dev,
+              void* ws, size_t ws_bytes, void* stream);
+
+/* Conditioning (Figure 2, steps 2-3; Figure 1): FP64 QR of Π1·X (r1 × q,
+ * FP32 row-major input) with positive diag(R), then M = R⁻¹·Π2 where Π2 is
+ * q × r2 of standard Cauchys.  Outputs (device, FP64, row-major, may be NULL):
+ * R_dev (q × q, upper triangular) and M_dev (q × r2).  Rank deficiency sets
+ * the RANK_DEFICIENT status bit: column k counts as dependent on the columns
+ * before it when |R_kk| ≤ 1e-5·‖(Π1X)_{:,k}‖₂, the resolution of an FP32 Π1X. */
+L1S_API int l1_condition(const float* PiX_dev, int32_t r1, int32_t q, const l1s_params* params,
+                 double* R_dev, double* M_dev, void* ws, size_t ws_bytes, void* stream);
+
+/* Phase 2 (Figure 2, steps 4-5): λ_i = lower median_j |(X·M)_ij| with M the
+ * q × r2 FP64 matrix (rounded to FP32 for the product; FP32 accumulation),
+ * (BF16 A is widened to FP32 exactly).  The lower median
+ * is the ((r2−1)/2)-th order statistic counting from 0.  Writes lambda_dev
+ * (n floats) and *lambda_sum_dev (FP64 sum of the written λ, fixed order). */
+L1S_API int l1_lambda(const void* A_dev, int64_t lda, l1s_dtype dtype, const float* b_dev,
+              int64_t n, int32_t d, const double* M_dev, const l1s_params* params,
+              float* lambda_dev, double* lambda_sum_dev, void* ws, size_t ws_bytes,
+              void* stream);
+
+/* Phases 2-3 (Figure 2, steps 4-7): λ as in l1_lambda, Σλ, τ = m_s/Σλ in FP64,
+ * p̂_i = min(1, τ·λ_i) in FP64, row i kept iff u_i < p̂_i with its 53-bit
+ * uniform u_i (exact FP64 comparison).  Kept rows are written in ascending
+ * order: idx_dev (row index into A, int64), w_dev (1/p̂_i, FP64) and
+ * coreset_dev (the row of X = [A_i, −b_i] in FP64, row-major, q per row), up to
+ * `capacity` rows; *count_dev receives the number kept (which may exceed
+ * capacity: the CAPACITY status bit is then set).  lambda_dev (n floats) and
+ * coreset_dev may be NULL. */
+L1S_API int l1_sample(const void* A_dev, int64_t lda, l1s_dtype dtype, const float* b_dev,
+              int64_t n, int32_t d, const double* M_dev, const l1s_params* params,
+              int64_t capacity, int64_t* idx_dev, double* w_dev, double* coreset_dev,
+              int64_t* count_dev, float* lambda_dev, void* ws, size_t ws_bytes, void* stream);
+
+/* The Bernoulli step alone (Figure 2, step 7) from caller-given probabilities
+ * p_dev (n FP64 values in [0,1]): row i kept iff u_i < p_i.  Writes up to
+ * capacity ascending indices and *count_dev. */
+L1S_API int l1_sample_from_p(const double* p_dev, int64_t n, const l1s_params* params,
+                     int64_t capacity, int64_t* idx_dev, int64_t* count_dev,
+                     void* ws, size_t ws_bytes, void* stream);
+
+/* The whole sampling pass (Figure 2, steps 1-7): fct_embed, l1_condition,
+ * l1_sample, enqueued back to back with intermediates in the workspace.
+ * Resets the status word first.  Outputs as in l1_sample. */
+L1S_API int l1_coreset(const void* A_dev, int64_t lda, l1s_dtype dtype, const float* b_dev,
+               int64_t n, int32_t d, const l1s_params* params, int64_t capacity,
+               int64_t* idx_dev, double* w_dev, double* coreset_dev, int64_t* count_dev,
+               void* ws, size_t ws_bytes, void* stream);
+
+/* l1_coreset from host memory: copies A (n rows of lda elements) and b from
+ * host buffers (pinned memory gives asynchronous copies) into the workspace
+ * (sized with host_staging = 1), runs the sampling pass, copies the kept
+ * indices and weights (up to capacity) and the count back to host memory and
+ * synchronises `stream`.  Returns the first device-side error code, if any. */
+L1S_API int l1_coreset_host(const void* A_host, int64_t lda, l1s_dtype dtype, const float* b_host,
+                    int64_t n, int32_t d, const l1s_params* params, int64_t capacity,
+                    int64_t* idx_host, double* w_host, int64_t* count_host,
+                    void* ws, size_t ws_bytes, void* stream);
+
+/* Weighted ℓ1 regression on a coreset (Figure 2, step 8): x̂ minimising
+ * Σ_k w_k·|X_k·[x; 1]| over rows X_k = [A_k, −b_k] (coreset_dev, FP64, q per
+ * row, count from *count_dev, at most capacity) by FP64 iteratively
+ * reweighted least squares, finished by an exact solve on the d rows with
+ * the smallest residuals when that lowers the objective.  Writes x_dev (d
+ * FP64) and *objective_dev (the weighted objective at x_dev). */
+L1S_API int l1_solve(const double* coreset_dev, const double* w_dev, const int64_t* count_dev,
+             int64_t capacity, int32_t d, int32_t max_iter, double* x_dev,
+             double* objective_dev, void* ws, size_t ws_bytes, void* stream);
+
+/* ‖A·x − b‖₁ in FP64 over all n rows (problem statement, §4.2). */
+L1S_API int l1_objective(const void* A_dev, int64_t lda, l1s_dtype dtype, const float* b_dev,
+                 int64_t n, int32_t d, const double* x_dev, double* objective_dev,
+                 void* ws, size_t ws_bytes, void* stream);
+
+/* FastCauchyRegression end to end (Figure 2, steps 1-8): l1_coreset with a
+ * coreset capacity of 2·m_s + 64 rows, l1_solve, l1_objective.  A and b are
+ * device pointers (inputs_on_host = 0) or host pointers (inputs_on_host = 1,
+ * workspace sized with host_staging = 1).  Synchronises `stream`; writes
+ * x_host (d FP64), *objective_host and *coreset_rows_host (may be NULL) and
+ * returns the first device-side error code, if any. */
+L1S_API int l1_regress(const void* A, int64_t lda, l1s_dtype dtype, const float* b,
+               int64_t n, int32_t d, const l1s_params* params, int32_t inputs_on_host,
+               double* x_host, double* objective_host, int64_t* coreset_rows_host,
+               void* ws, size_t ws_bytes, void* stream);
+
+/* Debug: the Philox draws of global rows [row_start, row_start + count) as the
+ * kernels use them (device outputs, any may be NULL): bucket_h/bucket_i in
+ * [0, r1), k_h/k_i the 24-bit integers of the Cauchy scales, cauchy_h/cauchy_i
+ * the FP32 Cauchy variates, sign (±1), u_bits the 53-bit sampling integers. */
+L1S_API int l1s_debug_variates(const l1s_params* params, int64_t row_start, int64_t count,
+                       int32_t* bucket_h, int32_t* bucket_i, int32_t* k_h, int32_t* k_i,
+                       float* cauchy_h, float* cauchy_i, int8_t* sign, uint64_t* u_bits,
+                       void* stream);
+
+/* Debug: Π2 (q × r2, FP64, row-major) as l1_condition draws it. */
+L1S_API int l1s_debug_pi2(const l1s_params* params, int32_t q, double* pi2_dev, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* L1FCT_H */

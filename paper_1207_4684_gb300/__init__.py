@@ -1,0 +1,33 @@
+"""GB300-native Fast Cauchy Transform ℓ1 regression (FastCauchyRegression, Figure 2).
+
+The compute path is libl1fct.so (CUDA for sm_103a, built in-tree by
+`paper_1207_4684_gb300.build`); `paper_1207_4684_gb300.l1fct` is its ctypes
+binding.  PyTorch provides device memory and streams only.
+"""
+from .l1fct import (  # noqa: F401
+    BF16,
+    EXPORTS,
+    F32,
+    L1SError,
+    Params,
+    fct_embed,
+    flag,
+    l1_coreset,
+    l1_coreset_host,
+    l1_condition,
+    l1_lambda,
+    l1_objective,
+    l1_regress,
+    l1_sample,
+    l1_sample_from_p,
+    l1_solve,
+    l1s_debug_pi2,
+    l1s_debug_variates,
+    l1s_status_read,
+    l1s_status_reset,
+    l1s_workspace_size,
+    load,
+    make_params,
+    version,
+    workspace,
+)

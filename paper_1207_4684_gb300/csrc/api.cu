@@ -1,0 +1,516 @@
+// C ABI of libl1fct: argument checks, workspace layout, and the order in which
+// the kernels of each entry point are enqueued.  See include/l1fct.h.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <mutex>
+
+#include "l1s_common.cuh"
+
+namespace l1s {
+
+// kernels (defined in the other translation units)
+const void* fct_kernel(int log2s, l1s_dtype dt);
+size_t fct_smem_bytes(int s, int r1, int width);
+int fct_threads();
+bool launch_fct(const Plan& pl, const void* A, int64_t lda, l1s_dtype dt, const float* b,
+                const l1s_params* p, float* pix, unsigned char* ws, cudaStream_t st);
+bool launch_condition(const Plan& pl, const float* pix, const l1s_params* p, double* R_user,
+                      double* M_user, unsigned char* ws, cudaStream_t st);
+bool launch_pi2(const l1s_params* p, int q, double* out, cudaStream_t st);
+int lambda_threads();
+bool launch_lambda(const Plan& pl, const void* A, int64_t lda, l1s_dtype dt, const float* b,
+                   const float* m32, const l1s_params* p, float* lam, double* user_sum,
+                   unsigned char* ws, cudaStream_t st);
+bool launch_m_to_f32(const double* m, int total, float* out, cudaStream_t st);
+int sample_threads();
+bool launch_sample(const Plan& pl, const float* lam, const double* p, const l1s_params* prm,
+                   const void* A, int64_t lda, l1s_dtype dt, const float* b, int64_t capacity,
+                   int64_t* idx, double* w, double* coreset, int64_t* count_out, unsigned char* ws,
+                   cudaStream_t st);
+bool launch_debug_variates(const l1s_params* p, int64_t row_start, int64_t count, int32_t* bh,
+                           int32_t* bi, int32_t* kh, int32_t* ki, float* ch, float* ci, int8_t* sg,
+                           uint64_t* ub, cudaStream_t st);
+int irls_entries(int q);
+size_t irls_state_bytes();
+bool launch_solve(const double* X, const double* w, const int64_t* count, int64_t capacity, int d,
+                  int max_iter, double* x_out, double* obj_out, int nblocks, double* partials,
+                  void* state, float* scratch, StatusBlock* status, cudaStream_t st);
+bool launch_objective(const void* A, int64_t lda, l1s_dtype dt, const float* b, int64_t n, int d,
+                      const double* x, double* out, int nblocks, double* partials, cudaStream_t st);
+
+static thread_local char g_err[512] = "";
+
+void set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+
+bool cuda_ok(cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return true;
+  set_error("%s: %s", what, cudaGetErrorString(e));
+  return false;
+}
+
+DeviceInfo device_info() {
+  static std::mutex mu;
+  static DeviceInfo cache[64];
+  static bool have[64] = {};
+  DeviceInfo di{-1, 0, 0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return di;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!have[dev]) {
+    cache[dev].device = dev;
+    cudaDeviceGetAttribute(&cache[dev].sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&cache[dev].max_smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    have[dev] = true;
+  }
+  return cache[dev];
+}
+
+static bool check_params(const l1s_params* p, int64_t n, int d) {
+  if (!p) return set_error("params is NULL"), false;
+  if (n < 1) return set_error("n must be >= 1 (got %lld)", (long long)n), false;
+  if (d < 1 || d > kMaxD) return set_error("d must be in [1, %d] (got %d)", kMaxD, d), false;
+  const int l2 = log2_exact(p->s);
+  if (p->s < 1 || l2 < 0 || l2 > kMaxLog2S)
+    return set_error("s must be a power of two in [1, 4096] (got %d)", p->s), false;
+  if (p->r1 < d + 1 || p->r1 > 65535)
+    return set_error("r1 must be in [q, 65535] with q = d+1 = %d (got %d)", d + 1, p->r1), false;
+  if (p->r2 < 1 || p->r2 > kMaxR2) return set_error("r2 must be in [1, %d] (got %d)", kMaxR2, p->r2), false;
+  if (!(p->coreset_size > 0.0) || !isfinite(p->coreset_size))
+    return set_error("coreset_size must be positive and finite"), false;
+  if (p->global_row_offset < 0 || p->global_row_offset % p->s != 0)
+    return set_error("global_row_offset must be a non-negative multiple of s"), false;
+  if (p->sign_flip != 0 && p->sign_flip != 1) return set_error("sign_flip must be 0 or 1"), false;
+  if (p->reserved != 0) return set_error("reserved must be 0"), false;
+  return true;
+}
+
+static int64_t coreset_capacity_of(const l1s_params* p) {
+  return static_cast<int64_t>(ceil(2.0 * p->coreset_size)) + 64;
+}
+
+bool make_plan(const l1s_params* p, int64_t n, int d, l1s_dtype dt, bool host_staging, Plan* pl) {
+  if (!check_params(p, n, d)) return false;
+  if (dt != L1S_F32 && dt != L1S_BF16) return set_error("dtype must be L1S_F32 or L1S_BF16"), false;
+  const DeviceInfo di = device_info();
+  if (di.device < 0 || di.sms <= 0) return set_error("no CUDA device"), false;
+  Plan& P = *pl;
+  memset(&P, 0, sizeof(P));
+  P.n = n;
+  P.d = d;
+  P.q = d + 1;
+  P.s = p->s;
+  P.log2s = log2_exact(p->s);
+  P.r1 = p->r1;
+  P.r2 = p->r2;
+  P.nblocks = (n + P.s - 1) / P.s;
+
+  // Phase 1: widest column slice whose shared-memory footprint allows two blocks
+  // per SM; otherwise the widest that fits at all.
+  P.fct_threads = fct_threads();
+  const size_t budget2 = std::min<size_t>(110 * 1024, di.max_smem_optin);
+  const size_t budget1 = di.max_smem_optin;
+  int slices = 1;
+  for (;; ++slices) {
+    const int w = (P.q + slices - 1) / slices;
+    if (fct_smem_bytes(P.s, P.r1, w) <= budget2 || w == 1) break;
+  }
+  int width = (P.q + slices - 1) / slices;
+  if (fct_smem_bytes(P.s, P.r1, width) > budget2) {
+    slices = 1;
+    for (;; ++slices) {
+      width = (P.q + slices - 1) / slices;
+      if (fct_smem_bytes(P.s, P.r1, width) <= budget1) break;
+      if (width == 1) return set_error("r1 and s too large for shared memory"), false;
+    }
+  }
+  P.fct_slices = (P.q + width - 1) / width;
+  P.fct_width = width;
+  P.fct_smem = fct_smem_bytes(P.s, P.r1, width);
+  const void* fn = fct_kernel(P.log2s, dt);
+  if (!cuda_ok(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    static_cast<int>(P.fct_smem)),
+               "cudaFuncSetAttribute(fct_embed)"))
+    return false;
+  int per_sm = 0;
+  if (!cuda_ok(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, P.fct_threads, P.fct_smem),
+               "occupancy(fct_embed)"))
+    return false;
+  per_sm = std::max(per_sm, 1);
+  const int64_t want = std::max<int64_t>(1, static_cast<int64_t>(di.sms) * per_sm / P.fct_slices);
+  P.fct_ctas = static_cast<int>(std::min<int64_t>(P.nblocks, want));
+
+  // Phase 2: a persistent-style grid of 8 blocks per SM.
+  P.lam_threads = lambda_threads();
+  P.lam_ctas = static_cast<int>(std::max<int64_t>(
+      1, std::min<int64_t>((n + P.lam_threads - 1) / P.lam_threads, static_cast<int64_t>(di.sms) * 8)));
+
+  // Phase 3: contiguous chunks (multiples of 64 rows), about 4 per SM.
+  P.smp_threads = sample_threads();
+  {
+    const int64_t target = static_cast<int64_t>(di.sms) * 4;
+    int64_t chunk = (n + target - 1) / target;
+    chunk = std::max<int64_t>(64, (chunk + 63) / 64 * 64);
+    P.smp_chunk = chunk;
+    P.smp_ctas = static_cast<int>((n + chunk - 1) / chunk);
+  }
+  P.irls_ctas = di.sms;
+
+  const int64_t cap = coreset_capacity_of(p);
+  const size_t esz = dt == L1S_BF16 ? 2 : 4;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t o = off;
+    off = align_up(off + bytes);
+    return o;
+  };
+  P.off_status = take(256);
+  // IRLS region first, so that l1_solve can use the same offsets with only (d, capacity).
+  P.off_irls = take(sizeof(double) * static_cast<size_t>(P.irls_ctas) * (irls_entries(P.q) + 1));
+  P.off_x = take(irls_state_bytes());
+  P.off_objp = take(sizeof(float) * static_cast<size_t>(cap));  // IRLS residual scratch
+  P.off_partials = take(sizeof(float) * static_cast<size_t>(P.fct_slices) * P.fct_ctas * P.r1 * P.fct_width);
+  P.off_pix = take(sizeof(float) * P.r1 * P.q);
+  P.off_qr = take(sizeof(double) * P.r1 * P.q);
+  P.off_r = take(sizeof(double) * P.q * P.q);
+  P.off_m64 = take(sizeof(double) * P.q * P.r2);
+  P.off_m32 = take(sizeof(float) * P.q * P.r2);
+  P.off_pi2 = take(sizeof(double) * P.q * P.r2);
+  P.off_lam = take(sizeof(float) * static_cast<size_t>(n));
+  P.off_lamsum = take(sizeof(double) * std::max(P.lam_ctas, P.irls_ctas));
+  P.off_mask = take(sizeof(uint64_t) * static_cast<size_t>((n + 63) / 64));
+  P.off_counts = take(sizeof(int64_t) * static_cast<size_t>(P.smp_ctas));
+  P.off_idx_tmp = take(static_cast<size_t>(cap) * (sizeof(int64_t) + sizeof(double) + sizeof(double) * P.q) +
+                       2 * sizeof(double) * (P.q + 1));
+  if (host_staging) {
+    P.off_stage_a = take(esz * static_cast<size_t>(n) * d);
+    P.off_stage_b = take(sizeof(float) * static_cast<size_t>(n));
+  }
+  P.total = off;
+  return true;
+}
+
+static bool check_ws(const Plan& pl, const void* ws, size_t ws_bytes) {
+  if (!ws) return set_error("workspace is NULL"), false;
+  if (reinterpret_cast<uintptr_t>(ws) % 256 != 0) return set_error("workspace must be 256-byte aligned"), false;
+  if (ws_bytes < pl.total)
+    return set_error("workspace too small: %zu bytes given, %zu needed", ws_bytes, pl.total), false;
+  return true;
+}
+
+static bool check_a(const void* A, int64_t lda, const float* b, int d) {
+  if (!A || !b) return set_error("A and b must not be NULL"), false;
+  if (lda < d) return set_error("lda must be >= d"), false;
+  return true;
+}
+
+}  // namespace l1s
+
+using namespace l1s;
+
+extern "C" {
+
+const char* l1s_last_error(void) { return g_err; }
+
+const char* l1s_version(void) { return "l1fct 0.1 (sm_103a)"; }
+
+int l1s_workspace_size(const l1s_params* params, int64_t n, int32_t d, l1s_dtype dtype,
+                       int32_t host_staging, size_t* bytes) {
+  if (!bytes) return set_error("bytes is NULL"), L1S_ERR_INVALID_ARG;
+  Plan pl;
+  if (!make_plan(params, n, d, dtype, host_staging != 0, &pl)) return L1S_ERR_INVALID_ARG;
+  *bytes = pl.total;
+  return L1S_OK;
+}
+
+int l1s_status_reset(void* ws, size_t ws_bytes, void* stream) {
+  if (!ws || ws_bytes < sizeof(StatusBlock)) return set_error("workspace too small"), L1S_ERR_WORKSPACE;
+  if (!cuda_ok(cudaMemsetAsync(ws, 0, sizeof(StatusBlock), static_cast<cudaStream_t>(stream)),
+               "status reset"))
+    return L1S_ERR_CUDA;
+  return L1S_OK;
+}
+
+int l1s_status_read(const void* ws, size_t ws_bytes, void* stream, uint32_t* flags) {
+  if (!ws || ws_bytes < sizeof(StatusBlock) || !flags) return set_error("bad arguments"), L1S_ERR_WORKSPACE;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (!cuda_ok(cudaStreamSynchronize(st), "stream synchronize")) return L1S_ERR_CUDA;
+  uint32_t v = 0;
+  if (!cuda_ok(cudaMemcpy(&v, ws, sizeof(v), cudaMemcpyDeviceToHost), "status read")) return L1S_ERR_CUDA;
+  *flags = v;
+  return L1S_OK;
+}
+
+int fct_embed(const void* A, int64_t lda, l1s_dtype dtype, const float* b, int64_t n, int32_t d,
+              const l1s_params* params, float* PiX, void* ws, size_t ws_bytes, void* stream) {
+  Plan pl;
+  if (!make_plan(params, n, d, dtype, false, &pl)) return L1S_ERR_INVALID_ARG;
+  if (!check_a(A, lda, b, d) || !PiX) return L1S_ERR_INVALID_ARG;
+  if (!check_ws(pl, ws, ws_bytes)) return L1S_ERR_WORKSPACE;
+  if (!launch_fct(pl, A, lda, dtype, b, params, PiX, static_cast<unsigned char*>(ws),
+                  static_cast<cudaStream_t>(stream)))
+    return L1S_ERR_CUDA;
+  return L1S_OK;
+}
+
+int l1_condition(const float* PiX, int32_t r1, int32_t q, const l1s_params* params, double* R,
+                 double* M, void* ws, size_t ws_bytes, void* stream) {
+  if (!params || !PiX) return set_error("params and PiX must not be NULL"), L1S_ERR_INVALID_ARG;
+  if (r1 != params->r1) return set_error("r1 must equal params->r1"), L1S_ERR_INVALID_ARG;
+  Plan pl;
+  if (!make_plan(params, std::max<int64_t>(1, r1), q - 1, L1S_F32, false, &pl)) return L1S_ERR_INVALID_ARG;
+  // Only the conditioning regions are used; they sit at fixed offsets for given (r1, q, r2).
+  if (!check_ws(pl, ws, ws_bytes)) return L1S_ERR_WORKSPACE;
+  if (!launch_condition(pl, PiX, params, R, M, static_cast<unsigned char*>(ws),
+                        static_cast<cudaStream_t>(stream)))
+    return L1S_ERR_CUDA;
+  return L1S_OK;
+}
+
+int l1_lambda(const void* A, int64_t lda, l1s_dtype dtype, const float* b, int64_t n, int32_t d,
+              const double* M, const l1s_params* params, float* lambda, double* lambda_sum, void* ws,
+              size_t ws_bytes, void* stream) {
+  Plan pl;
+  if (!make_plan(params, n, d, dtype, false, &pl)) return L1S_ERR_INVALID_ARG;
+  if (!check_a(A, lda, b, d) || !M || !lambda) return set_error("M and lambda must not be NULL"), L1S_ERR_INVALID_ARG;
+  if (!check_ws(pl, ws, ws_bytes)) return L1S_ERR_WORKSPACE;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  unsigned char* w = static_cast<unsigned char*>(ws);
+  float* m32 = reinterpret_cast<float*>(w + pl.off_m32);
+  if (!launch_m_to_f32(M, pl.q * pl.r2, m32, st)) return L1S_ERR_CUDA;
+  if (!launch_lambda(pl, A, lda, dtype, b, m32, params, lambda, lambda_sum, w, st)) return L1S_ERR_CUDA;
+  return L1S_OK;
+}
+
+static int sample_impl(const Plan& pl, const void* A, int64_t lda, l1s_dtype dtype, const float* b,
+                       const float* m32, const l1s_params* params, int64_t capacity, int64_t* idx,
+                       double* wts, double* coreset, int64_t* count, float* lambda, unsigned char* w,
+                       cudaStream_t st) {
+  float* lam = lambda ? lambda : reinterpret_cast<float*>(w + pl.off_lam);
+  if (!launch_lambda(pl, A, lda, dtype, b, m32, params, lam, nullptr, w, st)) return L1S_ERR_CUDA;
+  if (!launch_sample(pl, lam, nullptr, params, A, lda, dtype, b, capacity, idx, wts, coreset, count, w, st))
+    return L1S_ERR_CUDA;
+  return L1S_OK;
+}
+
+int l1_sample(const void* A, int64_t lda, l1s_dtype dtype, const float* b, int64_t n, int32_t d,
+              const double* M, const l1s_params* params, int64_t capacity, int64_t* idx, double* wts,
+              double* coreset, int64_t* count, float* lambda, void* ws, size_t ws_bytes, void* stream) {
+  Plan pl;
+  if (!make_plan(params, n, d, dtype, false, &pl)) return L1S_ERR_INVALID_ARG;
+  if (!check_a(A, lda, b, d) || !M) return set_error("M must not be NULL"), L1S_ERR_INVALID_ARG;
+  if (capacity < 0 || (capacity > 0 && (!idx || !wts)) || !count)
+    return set_error("idx, w (capacity > 0) and count must not be NULL"), L1S_ERR_INVALID_ARG;
+  if (!check_ws(pl, ws, ws_bytes)) return L1S_ERR_WORKSPACE;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  unsigned char* w = static_cast<unsigned char*>(ws);
+  float* m32 = reinterpret_cast<float*>(w + pl.off_m32);
+  if (!launch_m_to_f32(M, pl.q * pl.r2, m32, st)) return L1S_ERR_CUDA;
+  return sample_impl(pl, A, lda, dtype, b, m32, params, capacity, idx, wts, coreset, count, lambda, w, st);
+}
+
+int l1_sample_from_p(const double* p, int64_t n, const l1s_params* params, int64_t capacity, int64_t* idx,
+                     int64_t* count, void* ws, size_t ws_bytes, void* stream) {
+  Plan pl;
+  if (!make_plan(params, n, 1, L1S_F32, false, &pl)) return L1S_ERR_INVALID_ARG;
+  if (!p || !count || capacity < 0 || (capacity > 0 && !idx))
+    return set_error("p, count (and idx when capacity > 0) must not be NULL"), L1S_ERR_INVALID_ARG;
+  if (!check_ws(pl, ws, ws_bytes)) return L1S_ERR_WORKSPACE;
+  unsigned char* w = static_cast<unsigned char*>(ws);
+  if (!launch_sample(pl, nullptr, p, params, nullptr, 0, L1S_F32, nullptr, capacity, idx, nullptr, nullptr,
+                     count, w, static_cast<cudaStream_t>(stream)))
+    return L1S_ERR_CUDA;
+  return L1S_OK;
+}
+
+static int coreset_impl(const Plan& pl, const void* A, int64_t lda, l1s_dtype dtype, const float* b,
+                        const l1s_params* params, int64_t capacity, int64_t* idx, double* wts,
+                        double* coreset, int64_t* count, unsigned char* w, cudaStream_t st) {
+  if (!cuda_ok(cudaMemsetAsync(w + pl.off_status, 0, sizeof(StatusBlock), st), "status reset"))
+    return L1S_ERR_CUDA;
+  float* pix = reinterpret_cast<float*>(w + pl.off_pix);
+  if (!launch_fct(pl, A, lda, dtype, b, params, pix, w, st)) return L1S_ERR_CUDA;
+  if (!launch_condition(pl, pix, params, nullptr, nullptr, w, st)) return L1S_ERR_CUDA;
+  return sample_impl(pl, A, lda, dtype, b, reinterpret_cast<float*>(w + pl.off_m32), params, capacity, idx,
+                     wts, coreset, count, nullptr, w, st);
+}
+
+int l1_coreset(const void* A, int64_t lda, l1s_dtype dtype, const float* b, int64_t n, int32_t d,
+               const l1s_params* params, int64_t capacity, int64_t* idx, double* wts, double* coreset,
+               int64_t* count, void* ws, size_t ws_bytes, void* stream) {
+  Plan pl;
+  if (!make_plan(params, n, d, dtype, false, &pl)) return L1S_ERR_INVALID_ARG;
+  if (!check_a(A, lda, b, d)) return L1S_ERR_INVALID_ARG;
+  if (capacity < 0 || (capacity > 0 && (!idx || !wts)) || !count)
+    return set_error("idx, w (capacity > 0) and count must not be NULL"), L1S_ERR_INVALID_ARG;
+  if (!check_ws(pl, ws, ws_bytes)) return L1S_ERR_WORKSPACE;
+  return coreset_impl(pl, A, lda, dtype, b, params, capacity, idx, wts, coreset, count,
+                      static_cast<unsigned char*>(ws), static_cast<cudaStream_t>(stream));
+}
+
+static int first_error(uint32_t flags) {
+  for (int code = L1S_ERR_RANK_DEFICIENT; code <= L1S_ERR_CAPACITY; ++code)
+    if (flags & L1S_FLAG(code)) return code;
+  return L1S_OK;
+}
+
+static bool stage_inputs(const Plan& pl, const void* A_host, int64_t lda, l1s_dtype dtype, const float* b_host,
+                         unsigned char* w, cudaStream_t st) {
+  const size_t esz = dtype == L1S_BF16 ? 2 : 4;
+  return cuda_ok(cudaMemcpy2DAsync(w + pl.off_stage_a, esz * pl.d, A_host, esz * lda, esz * pl.d, pl.n,
+                                   cudaMemcpyHostToDevice, st),
+                 "copy A to device") &&
+         cuda_ok(cudaMemcpyAsync(w + pl.off_stage_b, b_host, sizeof(float) * pl.n, cudaMemcpyHostToDevice, st),
+                 "copy b to device");
+}
+
+int l1_coreset_host(const void* A_host, int64_t lda, l1s_dtype dtype, const float* b_host, int64_t n,
+                    int32_t d, const l1s_params* params, int64_t capacity, int64_t* idx_host, double* w_host,
+                    int64_t* count_host, void* ws, size_t ws_bytes, void* stream) {
+  Plan pl;
+  if (!make_plan(params, n, d, dtype, true, &pl)) return L1S_ERR_INVALID_ARG;
+  if (!check_a(A_host, lda, b_host, d) || !count_host || capacity < 0 ||
+      (capacity > 0 && (!idx_host || !w_host)))
+    return set_error("bad host buffers"), L1S_ERR_INVALID_ARG;
+  if (!check_ws(pl, ws, ws_bytes)) return L1S_ERR_WORKSPACE;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  unsigned char* w = static_cast<unsigned char*>(ws);
+  if (!stage_inputs(pl, A_host, lda, dtype, b_host, w, st)) return L1S_ERR_CUDA;
+  const int64_t cap_ws = coreset_capacity_of(params);
+  const int64_t cap = std::min(capacity, cap_ws);
+  int64_t* idx_dev = reinterpret_cast<int64_t*>(w + pl.off_idx_tmp);
+  double* w_dev = reinterpret_cast<double*>(idx_dev + cap_ws);
+  StatusBlock* sb = reinterpret_cast<StatusBlock*>(w + pl.off_status);
+  int rc = coreset_impl(pl, w + pl.off_stage_a, d, dtype, reinterpret_cast<const float*>(w + pl.off_stage_b),
+                        params, cap, idx_dev, w_dev, nullptr, &sb->count, w, st);
+  if (rc != L1S_OK) return rc;
+  int64_t cnt = 0;
+  if (!cuda_ok(cudaMemcpyAsync(&cnt, &sb->count, sizeof(int64_t), cudaMemcpyDeviceToHost, st), "copy count") ||
+      !cuda_ok(cudaMemcpyAsync(idx_host, idx_dev, sizeof(int64_t) * cap, cudaMemcpyDeviceToHost, st),
+               "copy idx") ||
+      !cuda_ok(cudaMemcpyAsync(w_host, w_dev, sizeof(double) * cap, cudaMemcpyDeviceToHost, st), "copy w"))
+    return L1S_ERR_CUDA;
+  uint32_t flags = 0;
+  if (l1s_status_read(ws, ws_bytes, stream, &flags) != L1S_OK) return L1S_ERR_CUDA;
+  *count_host = cnt;
+  if (cnt > capacity) flags |= L1S_FLAG(L1S_ERR_CAPACITY);
+  return first_error(flags);
+}
+
+int l1_solve(const double* coreset, const double* wts, const int64_t* count, int64_t capacity, int32_t d,
+             int32_t max_iter, double* x, double* objective, void* ws, size_t ws_bytes, void* stream) {
+  if (!coreset || !wts || !count || !x || !objective) return set_error("NULL argument"), L1S_ERR_INVALID_ARG;
+  if (d < 1 || d > kMaxD || capacity < 1 || max_iter < 0 || max_iter > 100000)
+    return set_error("bad d, capacity or max_iter"), L1S_ERR_INVALID_ARG;
+  const DeviceInfo di = device_info();
+  if (di.device < 0) return set_error("no CUDA device"), L1S_ERR_CUDA;
+  // Same leading layout as make_plan: status, IRLS partials, IRLS state, residual scratch.
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t o = off;
+    off = align_up(off + bytes);
+    return o;
+  };
+  const int q = d + 1;
+  const size_t o_status = take(256);
+  const size_t o_part = take(sizeof(double) * static_cast<size_t>(di.sms) * (irls_entries(q) + 1));
+  const size_t o_state = take(irls_state_bytes());
+  const size_t o_scr = take(sizeof(float) * static_cast<size_t>(capacity));
+  if (!ws || reinterpret_cast<uintptr_t>(ws) % 256 || ws_bytes < off)
+    return set_error("workspace too small for l1_solve: %zu needed", off), L1S_ERR_WORKSPACE;
+  unsigned char* w = static_cast<unsigned char*>(ws);
+  if (!launch_solve(coreset, wts, count, capacity, d, max_iter, x, objective, di.sms,
+                    reinterpret_cast<double*>(w + o_part), w + o_state, reinterpret_cast<float*>(w + o_scr),
+                    reinterpret_cast<StatusBlock*>(w + o_status), static_cast<cudaStream_t>(stream)))
+    return L1S_ERR_CUDA;
+  return L1S_OK;
+}
+
+int l1_objective(const void* A, int64_t lda, l1s_dtype dtype, const float* b, int64_t n, int32_t d,
+                 const double* x, double* objective, void* ws, size_t ws_bytes, void* stream) {
+  if (!check_a(A, lda, b, d) || !x || !objective || n < 1 || d < 1 || d > kMaxD)
+    return set_error("bad arguments"), L1S_ERR_INVALID_ARG;
+  const DeviceInfo di = device_info();
+  if (di.device < 0) return set_error("no CUDA device"), L1S_ERR_CUDA;
+  const int nb = di.sms * 4;
+  if (!ws || ws_bytes < 256 + sizeof(double) * nb) return set_error("workspace too small"), L1S_ERR_WORKSPACE;
+  double* partials = reinterpret_cast<double*>(static_cast<unsigned char*>(ws) + 256);
+  if (!launch_objective(A, lda, dtype, b, n, d, x, objective, nb, partials, static_cast<cudaStream_t>(stream)))
+    return L1S_ERR_CUDA;
+  return L1S_OK;
+}
+
+int l1_regress(const void* A, int64_t lda, l1s_dtype dtype, const float* b, int64_t n, int32_t d,
+               const l1s_params* params, int32_t inputs_on_host, double* x_host, double* objective_host,
+               int64_t* coreset_rows_host, void* ws, size_t ws_bytes, void* stream) {
+  Plan pl;
+  if (!make_plan(params, n, d, dtype, inputs_on_host != 0, &pl)) return L1S_ERR_INVALID_ARG;
+  if (!check_a(A, lda, b, d) || !x_host || !objective_host) return set_error("NULL argument"), L1S_ERR_INVALID_ARG;
+  if (!check_ws(pl, ws, ws_bytes)) return L1S_ERR_WORKSPACE;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  unsigned char* w = static_cast<unsigned char*>(ws);
+  const void* Ad = A;
+  const float* bd = b;
+  int64_t ld = lda;
+  if (inputs_on_host) {
+    if (!stage_inputs(pl, A, lda, dtype, b, w, st)) return L1S_ERR_CUDA;
+    Ad = w + pl.off_stage_a;
+    bd = reinterpret_cast<const float*>(w + pl.off_stage_b);
+    ld = d;
+  }
+  const int64_t cap = coreset_capacity_of(params);
+  const int q = d + 1;
+  int64_t* idx = reinterpret_cast<int64_t*>(w + pl.off_idx_tmp);
+  double* wts = reinterpret_cast<double*>(idx + cap);
+  double* core = wts + cap;
+  double* xd = core + cap * q;
+  double* objd = xd + q + 1;
+  StatusBlock* sb = reinterpret_cast<StatusBlock*>(w + pl.off_status);
+  int rc = coreset_impl(pl, Ad, ld, dtype, bd, params, cap, idx, wts, core, &sb->count, w, st);
+  if (rc != L1S_OK) return rc;
+  rc = l1_solve(core, wts, &sb->count, cap, d, 100, xd, objd, ws, ws_bytes, stream);
+  if (rc != L1S_OK) return rc;
+  if (!launch_objective(Ad, ld, dtype, bd, n, d, xd, objd + 1, pl.lam_ctas,
+                        reinterpret_cast<double*>(w + pl.off_lamsum), st))
+    return L1S_ERR_CUDA;
+  double res[2];
+  int64_t cnt = 0;
+  if (!cuda_ok(cudaMemcpyAsync(x_host, xd, sizeof(double) * d, cudaMemcpyDeviceToHost, st), "copy x") ||
+      !cuda_ok(cudaMemcpyAsync(res, objd, sizeof(res), cudaMemcpyDeviceToHost, st), "copy objective") ||
+      !cuda_ok(cudaMemcpyAsync(&cnt, &sb->count, sizeof(cnt), cudaMemcpyDeviceToHost, st), "copy count"))
+    return L1S_ERR_CUDA;
+  uint32_t flags = 0;
+  if (l1s_status_read(ws, ws_bytes, stream, &flags) != L1S_OK) return L1S_ERR_CUDA;
+  *objective_host = res[1];
+  if (coreset_rows_host) *coreset_rows_host = cnt;
+  return first_error(flags);
+}
+
+int l1s_debug_variates(const l1s_params* params, int64_t row_start, int64_t count, int32_t* bucket_h,
+                       int32_t* bucket_i, int32_t* k_h, int32_t* k_i, float* cauchy_h, float* cauchy_i,
+                       int8_t* sign, uint64_t* u_bits, void* stream) {
+  if (!params || row_start < 0 || count < 0) return set_error("bad arguments"), L1S_ERR_INVALID_ARG;
+  if (params->r1 < 1 || params->r1 > 65535) return set_error("bad r1"), L1S_ERR_INVALID_ARG;
+  if (count == 0) return L1S_OK;
+  if (!launch_debug_variates(params, row_start, count, bucket_h, bucket_i, k_h, k_i, cauchy_h, cauchy_i, sign,
+                             u_bits, static_cast<cudaStream_t>(stream)))
+    return L1S_ERR_CUDA;
+  return L1S_OK;
+}
+
+int l1s_debug_pi2(const l1s_params* params, int32_t q, double* pi2, void* stream) {
+  if (!params || !pi2 || q < 1 || params->r2 < 1 || params->r2 > kMaxR2)
+    return set_error("bad arguments"), L1S_ERR_INVALID_ARG;
+  if (!launch_pi2(params, q, pi2, static_cast<cudaStream_t>(stream))) return L1S_ERR_CUDA;
+  return L1S_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,165 @@
+// Shared device helpers and host plumbing of libl1fct (CUDA side only).
+//
+// Random draws: Philox4x32-10 as published by Salmon, Moraes, Dror and Shaw
+// (SC'11), written here for the device.  Each 10-round call maps a 128-bit
+// counter and a 64-bit key to four 32-bit words; the method's random objects
+// (§3.1: the ±1 diagonal, the Cauchy diagonal C and the hash matrix B;
+// Figure 2: Π2 and the sampling uniforms) are read from those words as
+// described in include/l1fct.h.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/l1fct.h"
+
+namespace l1s {
+
+// ----------------------------------------------------------------- limits
+constexpr int kMaxLog2S = 12;       // s ≤ 4096
+constexpr int kMaxD = 128;          // d ≤ 128 (q ≤ 129)
+constexpr int kMaxR2 = 64;
+constexpr int kMaxConstM = 129 * 64;
+
+// Draw streams (counter word 3).
+constexpr uint32_t kStreamFct = 0;
+constexpr uint32_t kStreamPi2 = 1;
+constexpr uint32_t kStreamSample = 2;
+
+// Status word layout inside the workspace (first 256 bytes).
+struct StatusBlock {
+  uint32_t flags;        // OR of L1S_FLAG(code)
+  uint32_t pad0;
+  int64_t count;         // coreset rows kept (before capacity clipping)
+  double lambda_total;   // Σλ
+  double tau;            // m_s / Σλ
+  float tau32;           // τ rounded to FP32 (fast pre-test in phase 3)
+  uint32_t irls_done;    // IRLS convergence flag
+  double irls_prev_obj;  // IRLS objective of the previous iterate
+  double irls_obj;       // IRLS objective of the current iterate
+  double irls_eta;       // IRLS smoothing floor
+  int32_t irls_iters;
+  int32_t pad1;
+};
+
+__device__ __forceinline__ void raise_flag(uint32_t* flags, int code) {
+  atomicOr(flags, L1S_FLAG(code));
+}
+
+// ----------------------------------------------------------------- Philox4x32-10
+struct Key2 {
+  uint32_t k0, k1;
+};
+
+__host__ __device__ __forceinline__ Key2 make_key(uint64_t seed) {
+  return Key2{static_cast<uint32_t>(seed), static_cast<uint32_t>(seed >> 32)};
+}
+
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, Key2 k) {
+  constexpr uint32_t kMulA = 0xD2511F53u;  // multiplies counter word 0
+  constexpr uint32_t kMulB = 0xCD9E8D57u;  // multiplies counter word 2
+  constexpr uint32_t kWeylA = 0x9E3779B9u;
+  constexpr uint32_t kWeylB = 0xBB67AE85u;
+  uint32_t k0 = k.k0, k1 = k.k1;
+#pragma unroll
+  for (int round = 0; round < 10; ++round) {
+    const uint32_t hiA = __umulhi(kMulA, c.x);
+    const uint32_t loA = kMulA * c.x;
+    const uint32_t hiB = __umulhi(kMulB, c.z);
+    const uint32_t loB = kMulB * c.z;
+    c = make_uint4(hiB ^ c.y ^ k0, loB, hiA ^ c.w ^ k1, loA);
+    k0 += kWeylA;
+    k1 += kWeylB;
+  }
+  return c;
+}
+
+__device__ __forceinline__ uint4 draw_row(Key2 key, uint64_t row, uint32_t problem, uint32_t stream) {
+  return philox4x32_10(make_uint4(static_cast<uint32_t>(row), static_cast<uint32_t>(row >> 32),
+                                  problem, stream), key);
+}
+
+// Bucket in [0, r) from a 32-bit word: high half of word·r.
+__device__ __forceinline__ int bucket_of(uint32_t word, uint32_t r) {
+  return static_cast<int>(__umulhi(word, r));
+}
+
+// Standard Cauchy from the 24-bit integer k: tan(π(u − ½)) at u = (k + ½)/2^24,
+// evaluated through the reflection w = ½ − |u − ½| = j·2^-25 (j odd, exact in
+// FP32) as ±cos(πw)/sin(πw), which keeps full relative accuracy near the poles.
+__device__ __forceinline__ float cauchy_f32(uint32_t k) {
+  const int m = 2 * static_cast<int>(k) + 1 - (1 << 24);
+  const int j = (1 << 24) - abs(m);
+  const float w = static_cast<float>(j) * 0x1p-25f;
+  float sn, cs;
+  sincospif(w, &sn, &cs);
+  const float r = cs / sn;
+  return m > 0 ? r : -r;
+}
+
+__device__ __forceinline__ double cauchy_f64(uint32_t k) {
+  const int m = 2 * static_cast<int>(k) + 1 - (1 << 24);
+  const int j = (1 << 24) - abs(m);
+  const double w = static_cast<double>(j) * 0x1p-25;
+  double sn, cs;
+  sincospi(w, &sn, &cs);
+  const double r = cs / sn;
+  return m > 0 ? r : -r;
+}
+
+// 53-bit sampling integer of row `row` from its stream-2 words (a, b).
+__device__ __forceinline__ uint64_t u53_of(uint32_t wa, uint32_t wb) {
+  return (static_cast<uint64_t>(wa >> 5) << 26) | static_cast<uint64_t>(wb >> 6);
+}
+
+// ----------------------------------------------------------------- element loads
+template <typename T>
+__device__ __forceinline__ float load_elem(const T* p);
+template <>
+__device__ __forceinline__ float load_elem<float>(const float* p) { return __ldg(p); }
+template <>
+__device__ __forceinline__ float load_elem<uint16_t>(const uint16_t* p) {
+  return __uint_as_float(static_cast<uint32_t>(__ldg(p)) << 16);
+}
+
+// ----------------------------------------------------------------- host side
+struct DeviceInfo {
+  int device;
+  int sms;
+  int max_smem_optin;
+};
+DeviceInfo device_info();
+
+void set_error(const char* fmt, ...);
+bool cuda_ok(cudaError_t e, const char* what);
+
+inline size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }
+
+inline int log2_exact(int64_t v) {
+  int l = 0;
+  while ((int64_t(1) << l) < v) ++l;
+  return (int64_t(1) << l) == v ? l : -1;
+}
+
+// Launch geometry and workspace regions, a pure function of (params, n, d, dtype, device).
+struct Plan {
+  int64_t n;
+  int d, q, s, log2s, r1, r2;
+  int64_t nblocks;          // ⌈n / s⌉
+  int fct_threads;
+  int fct_slices, fct_width;  // column slices of Π1X handled per thread block
+  int fct_ctas;             // thread blocks per slice
+  size_t fct_smem;
+  int lam_ctas, lam_threads;
+  int smp_ctas, smp_threads;
+  int64_t smp_chunk;        // rows per sampling block (multiple of 64)
+  int irls_ctas;
+  // workspace offsets (bytes)
+  size_t off_status, off_partials, off_pix, off_qr, off_r, off_m64, off_m32, off_pi2,
+      off_lam, off_lamsum, off_mask, off_counts, off_idx_tmp, off_irls, off_x, off_objp,
+      off_stage_a, off_stage_b, total;
+};
+
+bool make_plan(const l1s_params* p, int64_t n, int d, l1s_dtype dt, bool host_staging, Plan* plan);
+
+}  // namespace l1s

@@ -1,0 +1,317 @@
+// Phase 2 (Figure 2, steps 4-5): λ_i = median_j |Λ_ij|, Λ = X·M, M = R⁻¹·Π2.
+//
+// One thread per row: the q values of X_(i) are loaded (vectorised when A's
+// rows allow it), the q × r2 product accumulates in FP32 registers with M read
+// from the constant bank (every lane of a warp reads the same M entry, so the
+// operand comes straight from the constant cache into the FMA), |·| is taken,
+// and the lower median — the ((r2−1)/2)-th order statistic from 0 — is picked
+// by a Batcher odd–even merge network whose unused comparators the compiler
+// drops.  λ is written once (4 B/row) and each block adds its λ's into an FP64
+// partial of Σλ through compensated FP32 pairs, so Σλ does not depend on the
+// launch order.  X crosses HBM once.
+#include <float.h>
+
+#include <utility>
+
+#include "l1s_common.cuh"
+
+namespace l1s {
+
+__constant__ float c_M[kMaxConstM];
+
+constexpr int kLamThreads = 256;
+
+__host__ __device__ constexpr int next_pow2(int v) { return v <= 1 ? 1 : 2 * next_pow2((v + 1) / 2); }
+
+// Batcher's odd–even merge sort network on P = 2^k inputs, as a compile-time list
+// of comparators (lo[c], hi[c]) applied in order.
+template <int P>
+struct OddEvenMergeNet {
+  static constexpr int kMax = 1024;  // ≥ the 543 comparators of P = 64
+  int lo[kMax];
+  int hi[kMax];
+  int count;
+  constexpr OddEvenMergeNet() : lo(), hi(), count(0) {
+    for (int p = 1; p < P; p <<= 1)
+      for (int k = p; k >= 1; k >>= 1)
+        for (int j = k % p; j + k < P; j += 2 * k)
+          for (int i = 0; i < k && i + j + k < P; ++i)
+            if ((i + j) / (2 * p) == (i + j + k) / (2 * p)) {
+              lo[count] = i + j;
+              hi[count] = i + j + k;
+              ++count;
+            }
+  }
+};
+
+template <int P>
+struct NetOf {
+  static constexpr OddEvenMergeNet<P> value{};
+};
+
+template <int P, int I>
+__device__ __forceinline__ void compare_exchange(float (&a)[P]) {
+  constexpr int l = NetOf<P>::value.lo[I];
+  constexpr int h = NetOf<P>::value.hi[I];
+  const float x = a[l], y = a[h];
+  a[l] = fminf(x, y);
+  a[h] = fmaxf(x, y);
+}
+
+template <int P, int... I>
+__device__ __forceinline__ void apply_net(float (&a)[P], std::integer_sequence<int, I...>) {
+  (compare_exchange<P, I>(a), ...);
+}
+
+// Sorts a[0..P) ascending (P a power of two); the compiler drops every comparator
+// that does not feed the entries the caller reads.
+template <int P>
+__device__ __forceinline__ void sort_net(float (&a)[P]) {
+  apply_net<P>(a, std::make_integer_sequence<int, NetOf<P>::value.count>{});
+}
+
+template <int N>
+__device__ __forceinline__ float lower_median(const float (&v)[N]) {
+  constexpr int P = next_pow2(N);
+  float a[P];
+#pragma unroll
+  for (int i = 0; i < P; ++i) a[i] = i < N ? v[i] : INFINITY;
+  sort_net<P>(a);
+  return a[(N - 1) / 2];
+}
+
+// s + c ← s + c + v with the rounding error of s + v carried in c (Knuth's TwoSum).
+__device__ __forceinline__ void two_sum_add(float& s, float& c, float v) {
+  const float t = s + v;
+  const float bp = t - s;
+  const float e = (s - (t - bp)) + (v - bp);
+  s = t;
+  c += e;
+}
+
+// Block total of per-thread (s, c) pairs, in a fixed order; returns on thread 0.
+__device__ double block_pair_total(float s, float c) {
+  __shared__ double wsum[32];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const float s2 = __shfl_xor_sync(0xffffffffu, s, off);
+    const float c2 = __shfl_xor_sync(0xffffffffu, c, off);
+    const float t = s + s2;
+    const float bp = t - s;
+    const float e = (s - (t - bp)) + (s2 - bp);
+    s = t;
+    c = (c + c2) + e;
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) wsum[warp] = static_cast<double>(s) + static_cast<double>(c);
+  __syncthreads();
+  double tot = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < (blockDim.x >> 5); ++w) tot += wsum[w];
+  return tot;
+}
+
+template <int D, typename TA, bool VEC>
+__device__ __forceinline__ void load_row(const TA* __restrict__ p, float (&x)[D + 1]) {
+  if constexpr (VEC && sizeof(TA) == 4) {
+    static_assert(D % 4 == 0, "vector path needs d % 4 == 0");
+#pragma unroll
+    for (int k = 0; k < D; k += 4) {
+      const float4 v = __ldg(reinterpret_cast<const float4*>(p + k));
+      x[k] = v.x;
+      x[k + 1] = v.y;
+      x[k + 2] = v.z;
+      x[k + 3] = v.w;
+    }
+  } else if constexpr (VEC && sizeof(TA) == 2) {
+    static_assert(D % 8 == 0, "vector path needs d % 8 == 0");
+#pragma unroll
+    for (int k = 0; k < D; k += 8) {
+      const uint4 v = __ldg(reinterpret_cast<const uint4*>(p + k));
+      const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        x[k + 2 * t] = __uint_as_float(w[t] << 16);
+        x[k + 2 * t + 1] = __uint_as_float(w[t] & 0xffff0000u);
+      }
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < D; ++k) x[k] = load_elem<TA>(p + k);
+  }
+}
+
+// Specialised for q = D + 1 and r2 = R2 known at compile time.
+template <int D, int R2, typename TA, bool VEC>
+__global__ void __launch_bounds__(kLamThreads) lambda_kernel(const TA* __restrict__ A, int64_t lda,
+                                                             const float* __restrict__ b, int64_t n,
+                                                             float* __restrict__ lam,
+                                                             double* __restrict__ block_sums) {
+  constexpr int Q = D + 1;
+  float s = 0.f, c = 0.f;
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  for (int64_t row = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; row < n; row += stride) {
+    float x[Q];
+    load_row<D, TA, VEC>(A + row * lda, x);
+    x[D] = -__ldg(b + row);
+    float acc[R2];
+#pragma unroll
+    for (int j = 0; j < R2; ++j) acc[j] = x[0] * c_M[j];
+#pragma unroll
+    for (int k = 1; k < Q; ++k) {
+#pragma unroll
+      for (int j = 0; j < R2; ++j) acc[j] = fmaf(x[k], c_M[k * R2 + j], acc[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < R2; ++j) acc[j] = fabsf(acc[j]);
+    const float med = lower_median<R2>(acc);
+    lam[row] = med;
+    two_sum_add(s, c, med);
+  }
+  const double tot = block_pair_total(s, c);
+  if (threadIdx.x == 0) block_sums[blockIdx.x] = tot;
+}
+
+// Any q ≤ 129 and r2 ≤ R2P (columns beyond r2 are ignored by the median).
+template <int R2P, typename TA>
+__global__ void __launch_bounds__(kLamThreads) lambda_kernel_generic(const TA* __restrict__ A, int64_t lda,
+                                                                     const float* __restrict__ b, int64_t n,
+                                                                     int d, int r2, float* __restrict__ lam,
+                                                                     double* __restrict__ block_sums) {
+  float s = 0.f, c = 0.f;
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  for (int64_t row = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; row < n; row += stride) {
+    float acc[R2P];
+#pragma unroll
+    for (int j = 0; j < R2P; ++j) acc[j] = 0.f;
+    const TA* p = A + row * lda;
+    for (int k = 0; k <= d; ++k) {
+      const float xk = k < d ? load_elem<TA>(p + k) : -__ldg(b + row);
+#pragma unroll
+      for (int j = 0; j < R2P; ++j)
+        if (j < r2) acc[j] = (k == 0) ? xk * c_M[j] : fmaf(xk, c_M[k * r2 + j], acc[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < R2P; ++j) acc[j] = j < r2 ? fabsf(acc[j]) : INFINITY;
+    float med;
+    {
+      // lower median of the first r2 entries: the padded +inf entries sort last, so the
+      // ((r2−1)/2)-th order statistic of all R2P values is the wanted one.
+      constexpr int P = R2P;
+      float a[P];
+#pragma unroll
+      for (int i = 0; i < P; ++i) a[i] = acc[i];
+      sort_net<P>(a);
+      const int mid = (r2 - 1) / 2;
+      med = a[0];
+#pragma unroll
+      for (int i = 0; i < P; ++i)
+        if (i == mid) med = a[i];
+    }
+    lam[row] = med;
+    two_sum_add(s, c, med);
+  }
+  const double tot = block_pair_total(s, c);
+  if (threadIdx.x == 0) block_sums[blockIdx.x] = tot;
+}
+
+// Σλ over the block partials in a fixed order; τ = m_s / Σλ.
+__global__ void lambda_finalize_kernel(const double* __restrict__ block_sums, int nblocks, double coreset,
+                                       StatusBlock* status, double* user_sum) {
+  __shared__ double part[256];
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < nblocks; i += blockDim.x) acc += block_sums[i];
+  part[threadIdx.x] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tot = 0.0;
+    for (int i = 0; i < static_cast<int>(blockDim.x); ++i) tot += part[i];
+    status->lambda_total = tot;
+    if (user_sum) *user_sum = tot;
+    if (!(tot > 0.0) || !isfinite(tot)) {
+      raise_flag(&status->flags, L1S_ERR_ZERO_MASS);
+      status->tau = 0.0;
+      status->tau32 = 0.f;
+    } else {
+      const double tau = coreset / tot;
+      status->tau = tau;
+      status->tau32 = tau > static_cast<double>(FLT_MAX) ? FLT_MAX : static_cast<float>(tau);
+    }
+  }
+}
+
+__global__ void m_to_f32_kernel(const double* __restrict__ m, int total, float* __restrict__ out) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < total) out[e] = static_cast<float>(m[e]);
+}
+
+// ----------------------------------------------------------------- dispatch
+template <int DD, int RR, typename TA>
+static void launch_lambda_case(dim3 grid, dim3 block, cudaStream_t st, bool aligned, const TA* A, int64_t lda,
+                               const float* b, int64_t n, float* lam, double* sums) {
+  if constexpr ((DD * sizeof(TA)) % 16 == 0) {
+    if (aligned) {
+      lambda_kernel<DD, RR, TA, true><<<grid, block, 0, st>>>(A, lda, b, n, lam, sums);
+      return;
+    }
+  }
+  lambda_kernel<DD, RR, TA, false><<<grid, block, 0, st>>>(A, lda, b, n, lam, sums);
+}
+
+template <typename TA>
+static bool launch_lambda_t(const Plan& pl, const TA* A, int64_t lda, const float* b, float* lam,
+                            double* sums, cudaStream_t st) {
+  const dim3 grid(pl.lam_ctas), block(pl.lam_threads);
+  const size_t esz = sizeof(TA);
+  const bool aligned = (reinterpret_cast<uintptr_t>(A) % 16 == 0) && ((lda * esz) % 16 == 0);
+  const int d = pl.d, r2 = pl.r2;
+#define L1S_LAMBDA_CASE(DD, RR)                                                        \
+  if (d == DD && r2 == RR) {                                                           \
+    launch_lambda_case<DD, RR, TA>(grid, block, st, aligned, A, lda, b, pl.n, lam, sums); \
+    return cuda_ok(cudaGetLastError(), "launch lambda");                               \
+  }
+  L1S_LAMBDA_CASE(4, 16)
+  L1S_LAMBDA_CASE(8, 16)
+  L1S_LAMBDA_CASE(16, 16)
+  L1S_LAMBDA_CASE(32, 16)
+  L1S_LAMBDA_CASE(64, 16)
+  L1S_LAMBDA_CASE(8, 32)
+  L1S_LAMBDA_CASE(16, 32)
+  L1S_LAMBDA_CASE(32, 32)
+  L1S_LAMBDA_CASE(64, 32)
+#undef L1S_LAMBDA_CASE
+  if (r2 <= 16)
+    lambda_kernel_generic<16, TA><<<grid, block, 0, st>>>(A, lda, b, pl.n, d, r2, lam, sums);
+  else if (r2 <= 32)
+    lambda_kernel_generic<32, TA><<<grid, block, 0, st>>>(A, lda, b, pl.n, d, r2, lam, sums);
+  else
+    lambda_kernel_generic<64, TA><<<grid, block, 0, st>>>(A, lda, b, pl.n, d, r2, lam, sums);
+  return cuda_ok(cudaGetLastError(), "launch lambda (generic)");
+}
+
+int lambda_threads() { return kLamThreads; }
+
+// M (FP32, q × r2 in the workspace) → constant bank, then λ and Σλ.
+bool launch_lambda(const Plan& pl, const void* A, int64_t lda, l1s_dtype dt, const float* b,
+                   const float* m32, const l1s_params* p, float* lam, double* user_sum,
+                   unsigned char* ws, cudaStream_t st) {
+  if (!cuda_ok(cudaMemcpyToSymbolAsync(c_M, m32, sizeof(float) * pl.q * pl.r2, 0,
+                                       cudaMemcpyDeviceToDevice, st),
+               "copy M to constant memory"))
+    return false;
+  double* sums = reinterpret_cast<double*>(ws + pl.off_lamsum);
+  bool ok = dt == L1S_BF16
+                ? launch_lambda_t<uint16_t>(pl, static_cast<const uint16_t*>(A), lda, b, lam, sums, st)
+                : launch_lambda_t<float>(pl, static_cast<const float*>(A), lda, b, lam, sums, st);
+  if (!ok) return false;
+  lambda_finalize_kernel<<<1, 256, 0, st>>>(sums, pl.lam_ctas, p->coreset_size,
+                                           reinterpret_cast<StatusBlock*>(ws + pl.off_status), user_sum);
+  return cuda_ok(cudaGetLastError(), "launch lambda_finalize");
+}
+
+bool launch_m_to_f32(const double* m, int total, float* out, cudaStream_t st) {
+  m_to_f32_kernel<<<(total + 255) / 256, 256, 0, st>>>(m, total, out);
+  return cuda_ok(cudaGetLastError(), "launch m_to_f32");
+}
+
+}  // namespace l1s

@@ -1,0 +1,249 @@
+// Phase 3 (Figure 2, steps 6-7; ℓ1 sampling lemma, §2):
+//   p̂_i = min(1, τ·λ_i) with τ = m_s/Σλ (FP64),  D_ii = 1/p̂_i if u_i < p̂_i else 0.
+//
+// mark:    each block owns a contiguous chunk of rows (a multiple of 64).  For
+//          row i the 53-bit uniform comes from Philox stream 2 (one call serves
+//          two rows).  The comparison u_i < p̂_i is decided exactly in FP64, but
+//          FP64 arithmetic is slow on this part, so an FP32 pre-test settles
+//          almost every row: p̂ is known to ~2^-22 relative from τ32·λ and u to
+//          2^-24 from its top 24 bits, and only rows inside that margin are
+//          re-decided in FP64.  Decisions become a 64-bit mask per 64 rows; the
+//          block's kept count is written out.
+// compact: each block adds the counts of the blocks before it (fixed order),
+//          scans its mask words, and writes kept rows in ascending order:
+//          index, weight 1/p̂_i, and the FP64 row [A_i, −b_i] of the coreset.
+#include "l1s_common.cuh"
+
+namespace l1s {
+
+constexpr int kSmpThreads = 256;
+
+__device__ __forceinline__ uint64_t spread_bits(uint32_t x) {
+  uint64_t v = x;
+  v = (v | (v << 16)) & 0x0000FFFF0000FFFFull;
+  v = (v | (v << 8)) & 0x00FF00FF00FF00FFull;
+  v = (v | (v << 4)) & 0x0F0F0F0F0F0F0F0Full;
+  v = (v | (v << 2)) & 0x3333333333333333ull;
+  v = (v | (v << 1)) & 0x5555555555555555ull;
+  return v;
+}
+
+// p̂ = min(1, τ·λ) in FP64 (the exact definition both sides evaluate).
+__device__ __forceinline__ double p_hat(double tau, float lam) { return fmin(1.0, tau * static_cast<double>(lam)); }
+
+// Keep decision for one row: exact result of (U·2^-53 < min(1, τ·λ)).
+__device__ __forceinline__ bool keep_row(float lam, float tau32, double tau, uint32_t wa, uint32_t wb) {
+  const float p32 = lam > 0.f ? fminf(1.f, tau32 * lam) : 0.f;
+  const float u_lo = static_cast<float>(wa >> 8) * 0x1p-24f;   // u ∈ [u_lo, u_lo + 2^-24)
+  const float u_hi = u_lo + 0x1p-24f;
+  if (u_hi < p32 * (1.f - 0x1p-20f)) return true;
+  if (u_lo > p32 * (1.f + 0x1p-20f)) return false;
+  const double u = static_cast<double>(u53_of(wa, wb)) * 0x1p-53;
+  return u < p_hat(tau, lam);
+}
+
+struct MarkArgs {
+  const float* lam;      // λ (mode 0) — or nullptr
+  const double* p;       // caller's p̂ (mode 1) — or nullptr
+  int64_t n;
+  int64_t chunk;         // rows per block, multiple of 64
+  Key2 key;
+  uint32_t problem;
+  int64_t row_offset;
+  const StatusBlock* status;
+  uint64_t* mask;        // ⌈n/64⌉ words
+  int64_t* counts;       // per block
+};
+
+__global__ void __launch_bounds__(kSmpThreads) sample_mark_kernel(const MarkArgs a) {
+  __shared__ int64_t wcount[kSmpThreads / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int64_t start = static_cast<int64_t>(blockIdx.x) * a.chunk;
+  const int64_t stop = min(a.n, start + a.chunk);
+  const double tau = a.p ? 0.0 : a.status->tau;
+  const float tau32 = a.p ? 0.f : a.status->tau32;
+  const bool odd_offset = (a.row_offset & 1) != 0;
+  int64_t kept = 0;
+  for (int64_t base = start + 64 * warp; base < stop; base += 64 * nwarps) {
+    const int64_t r0 = base + 2 * lane;      // this lane's two rows: r0, r0 + 1
+    const uint64_t g0 = static_cast<uint64_t>(a.row_offset + r0);
+    uint32_t w0a, w0b, w1a, w1b;
+    if (!odd_offset) {
+      const uint4 o = draw_row(a.key, g0 >> 1, a.problem, kStreamSample);
+      w0a = o.x; w0b = o.y; w1a = o.z; w1b = o.w;
+    } else {
+      const uint4 o0 = draw_row(a.key, g0 >> 1, a.problem, kStreamSample);
+      const uint4 o1 = draw_row(a.key, (g0 + 1) >> 1, a.problem, kStreamSample);
+      w0a = o0.z; w0b = o0.w; w1a = o1.x; w1b = o1.y;
+    }
+    bool k0 = false, k1 = false;
+    if (a.p) {
+      if (r0 < stop) k0 = static_cast<double>(u53_of(w0a, w0b)) * 0x1p-53 < a.p[r0];
+      if (r0 + 1 < stop) k1 = static_cast<double>(u53_of(w1a, w1b)) * 0x1p-53 < a.p[r0 + 1];
+    } else {
+      if (r0 < stop) k0 = keep_row(a.lam[r0], tau32, tau, w0a, w0b);
+      if (r0 + 1 < stop) k1 = keep_row(a.lam[r0 + 1], tau32, tau, w1a, w1b);
+    }
+    const uint32_t be = __ballot_sync(0xffffffffu, k0);
+    const uint32_t bo = __ballot_sync(0xffffffffu, k1);
+    const uint64_t m = spread_bits(be) | (spread_bits(bo) << 1);
+    if (lane == 0) a.mask[base >> 6] = m;
+    kept += __popcll(m);
+  }
+  if (lane == 0) wcount[warp] = kept;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int64_t t = 0;
+    for (int w = 0; w < nwarps; ++w) t += wcount[w];
+    a.counts[blockIdx.x] = t;
+  }
+}
+
+template <typename TA>
+struct CompactArgs {
+  const uint64_t* mask;
+  const int64_t* counts;
+  int nblocks;
+  int64_t n, chunk, capacity;
+  const float* lam;           // for weights (may be null when w is null)
+  const StatusBlock* status;
+  const TA* A;
+  int64_t lda;
+  const float* b;
+  int d;
+  int64_t* idx;
+  double* w;                  // may be null
+  double* coreset;            // may be null
+  int64_t* count_out;         // may be null
+  StatusBlock* status_rw;
+};
+
+template <typename TA>
+__global__ void __launch_bounds__(kSmpThreads) sample_compact_kernel(const CompactArgs<TA> a) {
+  __shared__ int64_t sh[kSmpThreads];
+  __shared__ int64_t s_base;
+  const int tid = threadIdx.x;
+  // Offset of this block: Σ counts of the blocks before it.
+  int64_t pre = 0;
+  for (int i = tid; i < static_cast<int>(blockIdx.x); i += blockDim.x) pre += a.counts[i];
+  sh[tid] = pre;
+  __syncthreads();
+  if (tid == 0) {
+    int64_t t = 0;
+    for (int i = 0; i < static_cast<int>(blockDim.x); ++i) t += sh[i];
+    s_base = t;
+    if (blockIdx.x == gridDim.x - 1) {
+      const int64_t total = t + a.counts[blockIdx.x];
+      if (a.count_out) *a.count_out = total;
+      a.status_rw->count = total;
+      if (total > a.capacity) raise_flag(&a.status_rw->flags, L1S_ERR_CAPACITY);
+    }
+  }
+  __syncthreads();
+  int64_t base = s_base;
+  const int64_t start = static_cast<int64_t>(blockIdx.x) * a.chunk;
+  const int64_t stop = min(a.n, start + a.chunk);
+  const int64_t w0 = start >> 6, w1 = (stop + 63) >> 6;
+  const double tau = a.status->tau;
+  const int q = a.d + 1;
+  for (int64_t tile = w0; tile < w1; tile += blockDim.x) {
+    const int64_t wi = tile + tid;
+    const uint64_t m = wi < w1 ? a.mask[wi] : 0ull;
+    const int64_t c = __popcll(m);
+    // inclusive scan of c over the block (Hillis–Steele in shared memory)
+    sh[tid] = c;
+    __syncthreads();
+    for (int off = 1; off < static_cast<int>(blockDim.x); off <<= 1) {
+      const int64_t v = tid >= off ? sh[tid - off] : 0;
+      __syncthreads();
+      sh[tid] += v;
+      __syncthreads();
+    }
+    int64_t pos = base + sh[tid] - c;
+    const int64_t tile_total = sh[blockDim.x - 1];
+    uint64_t bits = m;
+    while (bits) {
+      const int bit = __ffsll(static_cast<long long>(bits)) - 1;
+      bits &= bits - 1;
+      const int64_t row = (wi << 6) + bit;
+      if (pos < a.capacity) {
+        a.idx[pos] = row;
+        if (a.w) a.w[pos] = 1.0 / p_hat(tau, a.lam[row]);
+        if (a.coreset) {
+          double* out = a.coreset + pos * q;
+          const TA* src = a.A + row * a.lda;
+          for (int k = 0; k < a.d; ++k) out[k] = static_cast<double>(load_elem<TA>(src + k));
+          out[a.d] = -static_cast<double>(a.b[row]);
+        }
+      }
+      ++pos;
+    }
+    base += tile_total;
+    __syncthreads();
+  }
+}
+
+int sample_threads() { return kSmpThreads; }
+
+bool launch_sample(const Plan& pl, const float* lam, const double* p, const l1s_params* prm,
+                   const void* A, int64_t lda, l1s_dtype dt, const float* b, int64_t capacity,
+                   int64_t* idx, double* w, double* coreset, int64_t* count_out, unsigned char* ws,
+                   cudaStream_t st) {
+  MarkArgs m;
+  m.lam = lam;
+  m.p = p;
+  m.n = pl.n;
+  m.chunk = pl.smp_chunk;
+  m.key = make_key(prm->seed);
+  m.problem = prm->problem_id;
+  m.row_offset = prm->global_row_offset;
+  m.status = reinterpret_cast<const StatusBlock*>(ws + pl.off_status);
+  m.mask = reinterpret_cast<uint64_t*>(ws + pl.off_mask);
+  m.counts = reinterpret_cast<int64_t*>(ws + pl.off_counts);
+  sample_mark_kernel<<<pl.smp_ctas, pl.smp_threads, 0, st>>>(m);
+  if (!cuda_ok(cudaGetLastError(), "launch sample_mark")) return false;
+  StatusBlock* sb = reinterpret_cast<StatusBlock*>(ws + pl.off_status);
+  if (dt == L1S_BF16) {
+    CompactArgs<uint16_t> c{m.mask, m.counts, pl.smp_ctas, pl.n, pl.smp_chunk, capacity, lam, sb,
+                            static_cast<const uint16_t*>(A), lda, b, pl.d, idx, w, coreset, count_out, sb};
+    sample_compact_kernel<uint16_t><<<pl.smp_ctas, pl.smp_threads, 0, st>>>(c);
+  } else {
+    CompactArgs<float> c{m.mask, m.counts, pl.smp_ctas, pl.n, pl.smp_chunk, capacity, lam, sb,
+                         static_cast<const float*>(A), lda, b, pl.d, idx, w, coreset, count_out, sb};
+    sample_compact_kernel<float><<<pl.smp_ctas, pl.smp_threads, 0, st>>>(c);
+  }
+  return cuda_ok(cudaGetLastError(), "launch sample_compact");
+}
+
+// ----------------------------------------------------------------- debug draws
+__global__ void debug_variates_kernel(Key2 key, uint32_t problem, uint32_t r1, int64_t row_start,
+                                      int64_t count, int32_t* bh, int32_t* bi, int32_t* kh, int32_t* ki,
+                                      float* ch, float* ci, int8_t* sg, uint64_t* ub) {
+  const int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t >= count) return;
+  const uint64_t g = static_cast<uint64_t>(row_start + t);
+  const uint4 o = draw_row(key, g, problem, kStreamFct);
+  if (bh) bh[t] = bucket_of(o.x, r1);
+  if (bi) bi[t] = bucket_of(o.z, r1);
+  if (kh) kh[t] = static_cast<int32_t>(o.y >> 8);
+  if (ki) ki[t] = static_cast<int32_t>(o.w >> 8);
+  if (ch) ch[t] = cauchy_f32(o.y >> 8);
+  if (ci) ci[t] = cauchy_f32(o.w >> 8);
+  if (sg) sg[t] = (o.w & 1u) ? -1 : 1;
+  if (ub) {
+    const uint4 s = draw_row(key, g >> 1, problem, kStreamSample);
+    ub[t] = (g & 1) ? u53_of(s.z, s.w) : u53_of(s.x, s.y);
+  }
+}
+
+bool launch_debug_variates(const l1s_params* p, int64_t row_start, int64_t count, int32_t* bh,
+                           int32_t* bi, int32_t* kh, int32_t* ki, float* ch, float* ci, int8_t* sg,
+                           uint64_t* ub, cudaStream_t st) {
+  const int64_t blocks = (count + 255) / 256;
+  debug_variates_kernel<<<static_cast<unsigned>(blocks), 256, 0, st>>>(
+      make_key(p->seed), p->problem_id, static_cast<uint32_t>(p->r1), row_start, count, bh, bi, kh, ki,
+      ch, ci, sg, ub);
+  return cuda_ok(cudaGetLastError(), "launch debug_variates");
+}
+
+}  // namespace l1s

@@ -1,0 +1,455 @@
+// Step 8 of Figure 2: x̂ = argmin_x ‖D·(A·x − b)‖₁ on the coreset, in FP64, and
+// the objective ‖A·x − b‖₁ over all rows (problem statement, §4.2).
+//
+// The paper solves the small problem by linear programming; here it is solved
+// by iteratively reweighted least squares: with residuals r_k = X_k·[x; 1] of
+// the coreset rows X_k = [A_k, −b_k] and sampling weights w_k,
+//   x ← argmin Σ_k ω_k r_k²,  ω_k = w_k / max(|r_k|, η),  η = 10⁻⁶·Σ w|r| / Σ w,
+// starting from ω = w.  The iterate with the smallest objective is kept; the
+// loop stops early once the objective changes by less than 10⁻¹² relative.
+// An ℓ1 optimum is attained where d residuals vanish, so the result is then
+// polished: the d rows with the smallest |r_k| are solved exactly and the
+// vertex replaces the iterate when its objective is not larger.
+//
+// Kernels: irls_accum (many blocks: objective and the weighted normal
+// equations, per-block partials), irls_step (one block: fixed-order sum,
+// Cholesky solve, bookkeeping), irls_residuals (many blocks), irls_polish (one
+// block), objective (many blocks + fixed-order finish).  A device flag turns
+// the remaining iterations into no-ops after convergence, so the whole solve is
+// enqueued without host synchronisation.
+#include "l1s_common.cuh"
+
+namespace l1s {
+
+constexpr int kIrlsThreads = 256;
+constexpr int kIrlsTile = 64;
+constexpr int kIrlsSlots = 33;  // ⌈(129·130/2)/256⌉ entries per thread at most
+
+// State kept in the workspace between kernels.
+struct IrlsState {
+  double x[kMaxD + 1];      // current iterate, x[d] = 1
+  double best_x[kMaxD + 1];
+  double best_f;
+  double w_total;
+};
+
+struct IrlsArgs {
+  const double* X;        // coreset rows, q per row
+  const double* w;
+  const int64_t* count;
+  int64_t capacity;
+  int d, q;
+  double* partials;       // [blocks][entries + 2]
+  IrlsState* state;
+  StatusBlock* status;
+  float* scratch;         // |r| per row (polish)
+  double* x_out;
+  double* obj_out;
+  int max_iter;
+};
+
+__device__ __forceinline__ int64_t coreset_rows(const IrlsArgs& a) {
+  const int64_t c = *a.count;
+  return c < a.capacity ? c : a.capacity;
+}
+
+__device__ __forceinline__ int pair_count(int q) { return q * (q + 1) / 2 - 1; }
+
+// Entry e → (j, l), 0 ≤ j ≤ l < q, (j, l) ≠ (d, d), row-major over the upper triangle.
+__device__ __forceinline__ void pair_of(int e, int q, int& j, int& l) {
+  int row = 0, left = e;
+  while (left >= q - row) {
+    left -= q - row;
+    ++row;
+  }
+  j = row;
+  l = row + left;
+}
+
+__global__ void __launch_bounds__(kIrlsThreads) irls_accum_kernel(const IrlsArgs a) {
+  if (a.status->irls_done) return;
+  extern __shared__ __align__(16) double sm[];
+  const int q = a.q;
+  double* tile = sm;                      // kIrlsTile × q
+  double* om = tile + kIrlsTile * q;      // kIrlsTile
+  double* xs = om + kIrlsTile;            // q
+  __shared__ double red_f[kIrlsThreads], red_w[kIrlsThreads];
+  const int tid = threadIdx.x;
+  const int64_t S = coreset_rows(a);
+  const int64_t chunk = (S + gridDim.x - 1) / gridDim.x;
+  const int64_t start = blockIdx.x * chunk;
+  const int64_t stop = min(S, start + chunk);
+  for (int k = tid; k < q; k += blockDim.x) xs[k] = a.state->x[k];
+  const bool first = a.status->irls_iters == 0;
+  const double eta = a.status->irls_eta;
+  const int np = pair_count(q);
+  int pj[kIrlsSlots], pl[kIrlsSlots];
+  double acc[kIrlsSlots];
+#pragma unroll
+  for (int s = 0; s < kIrlsSlots; ++s) {
+    acc[s] = 0.0;
+    const int e = tid + s * blockDim.x;
+    if (e < np) pair_of(e, q, pj[s], pl[s]);
+    else pj[s] = pl[s] = 0;
+  }
+  double f_acc = 0.0, w_acc = 0.0;
+  __syncthreads();
+  for (int64_t t0 = start; t0 < stop; t0 += kIrlsTile) {
+    const int rows = static_cast<int>(min(static_cast<int64_t>(kIrlsTile), stop - t0));
+    for (int i = tid; i < rows * q; i += blockDim.x) tile[i] = a.X[t0 * q + i];
+    __syncthreads();
+    if (tid < rows) {
+      double r = 0.0;
+      for (int k = 0; k < q; ++k) r = fma(tile[tid * q + k], xs[k], r);
+      const double ar = fabs(r);
+      const double wk = a.w[t0 + tid];
+      f_acc += wk * ar;
+      w_acc += wk;
+      om[tid] = first ? wk : wk / fmax(ar, eta);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int s = 0; s < kIrlsSlots; ++s) {
+      if (tid + s * static_cast<int>(blockDim.x) < np) {
+        const int j = pj[s], l = pl[s];
+        double v = 0.0;
+        for (int t = 0; t < rows; ++t) v = fma(om[t] * tile[t * q + j], tile[t * q + l], v);
+        acc[s] += v;
+      }
+    }
+    __syncthreads();
+  }
+  const int ne = np + 2;
+  double* out = a.partials + static_cast<size_t>(blockIdx.x) * ne;
+#pragma unroll
+  for (int s = 0; s < kIrlsSlots; ++s) {
+    const int e = tid + s * blockDim.x;
+    if (e < np) out[e] = acc[s];
+  }
+  red_f[tid] = f_acc;
+  red_w[tid] = w_acc;
+  __syncthreads();
+  if (tid == 0) {
+    double f = 0.0, w = 0.0;
+    for (int i = 0; i < static_cast<int>(blockDim.x); ++i) {
+      f += red_f[i];
+      w += red_w[i];
+    }
+    out[np] = f;
+    out[np + 1] = w;
+  }
+}
+
+// One block: totals, bookkeeping, Cholesky solve of the weighted normal equations.
+__global__ void __launch_bounds__(kIrlsThreads) irls_step_kernel(const IrlsArgs a, int nblocks, int final_pass) {
+  StatusBlock* st = a.status;
+  if (st->irls_done && !final_pass) return;
+  extern __shared__ __align__(16) double sm[];
+  const int q = a.q, d = a.d, tid = threadIdx.x;
+  const int np = pair_count(q), ne = np + 2;
+  double* tot = sm;                 // ne
+  double* G = tot + ne;             // d × d (lower Cholesky factor in place)
+  double* y = G + d * d;            // d
+  __shared__ int s_fail;
+  for (int e = tid; e < ne; e += blockDim.x) {
+    double v = 0.0;
+    for (int b = 0; b < nblocks; ++b) v += a.partials[static_cast<size_t>(b) * ne + e];
+    tot[e] = v;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    const double f = tot[np];
+    IrlsState* S = a.state;
+    if (st->irls_iters == 0) {
+      S->w_total = tot[np + 1];
+      S->best_f = INFINITY;
+    }
+    if (f < S->best_f) {
+      S->best_f = f;
+      for (int k = 0; k < q; ++k) S->best_x[k] = S->x[k];
+    }
+    if (st->irls_iters > 0 && fabs(st->irls_obj - f) <= 1e-12 * f) st->irls_done = 1;
+    st->irls_prev_obj = st->irls_obj;
+    st->irls_obj = f;
+    st->irls_eta = 1e-6 * f / fmax(S->w_total, 1e-300);
+    s_fail = 0;
+  }
+  __syncthreads();
+  if (final_pass || st->irls_done) return;
+  // Scatter the upper-triangle entries into a full symmetric G and the right-hand side.
+  for (int e = tid; e < np; e += blockDim.x) {
+    int j, l;
+    pair_of(e, q, j, l);
+    if (l < d) {
+      G[j * d + l] = tot[e];
+      G[l * d + j] = tot[e];
+    } else {
+      y[j] = -tot[e];  // Σ ω a_j b = −Σ ω X_j X_d
+    }
+  }
+  __syncthreads();
+  for (int k = 0; k < d; ++k) {
+    if (tid == 0) {
+      const double piv = G[k * d + k];
+      if (!(piv > 0.0) || !isfinite(piv)) s_fail = 1;
+      G[k * d + k] = sqrt(fmax(piv, 1e-300));
+    }
+    __syncthreads();
+    const double gkk = G[k * d + k];
+    for (int i = k + 1 + tid; i < d; i += blockDim.x) G[i * d + k] /= gkk;
+    __syncthreads();
+    for (int e = tid; e < (d - k - 1) * (d - k - 1); e += blockDim.x) {
+      const int i = k + 1 + e / (d - k - 1), j = k + 1 + e % (d - k - 1);
+      if (j <= i) G[i * d + j] -= G[i * d + k] * G[j * d + k];
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    if (s_fail) {
+      st->irls_done = 1;
+    } else {
+      for (int i = 0; i < d; ++i) {  // L·z = y
+        double v = y[i];
+        for (int j = 0; j < i; ++j) v -= G[i * d + j] * y[j];
+        y[i] = v / G[i * d + i];
+      }
+      for (int i = d - 1; i >= 0; --i) {  // Lᵀ·x = z
+        double v = y[i];
+        for (int j = i + 1; j < d; ++j) v -= G[j * d + i] * y[j];
+        y[i] = v / G[i * d + i];
+      }
+      bool ok = true;
+      for (int i = 0; i < d; ++i) ok &= isfinite(y[i]);
+      if (ok) {
+        for (int i = 0; i < d; ++i) a.state->x[i] = y[i];
+        a.state->x[d] = 1.0;
+      } else {
+        st->irls_done = 1;
+      }
+    }
+    st->irls_iters += 1;
+  }
+}
+
+__global__ void irls_init_kernel(const IrlsArgs a) {
+  const int tid = threadIdx.x;
+  for (int k = tid; k < a.q; k += blockDim.x) a.state->x[k] = k == a.d ? 1.0 : 0.0;
+  if (tid == 0) {
+    a.status->irls_done = 0;
+    a.status->irls_iters = 0;
+    a.status->irls_obj = 0.0;
+    a.status->irls_prev_obj = 0.0;
+    a.status->irls_eta = 0.0;
+  }
+}
+
+__global__ void irls_residuals_kernel(const IrlsArgs a) {
+  const int64_t S = coreset_rows(a);
+  for (int64_t k = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; k < S;
+       k += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    double r = 0.0;
+    for (int j = 0; j < a.q; ++j) r = fma(a.X[k * a.q + j], a.state->best_x[j], r);
+    a.scratch[k] = static_cast<float>(fabs(r));
+  }
+}
+
+// One block: pick the d rows with the smallest |r|, solve them exactly, keep the better point.
+__global__ void __launch_bounds__(kIrlsThreads) irls_polish_kernel(const IrlsArgs a) {
+  extern __shared__ __align__(16) double sm[];
+  const int q = a.q, d = a.d, tid = threadIdx.x;
+  double* Mx = sm;               // d × (d + 1) augmented system
+  double* xp = Mx + d * (d + 1); // q
+  __shared__ float rv[kIrlsThreads];
+  __shared__ int64_t ri[kIrlsThreads];
+  __shared__ double red[kIrlsThreads];
+  __shared__ int s_ok;
+  const int64_t S = coreset_rows(a);
+  IrlsState* st = a.state;
+  if (tid == 0) s_ok = S >= d ? 1 : 0;
+  __syncthreads();
+  for (int k = 0; k < d && s_ok; ++k) {
+    float best = INFINITY;
+    int64_t bi = -1;
+    for (int64_t i = tid; i < S; i += blockDim.x) {
+      const float v = a.scratch[i];
+      if (v < best) {
+        best = v;
+        bi = i;
+      }
+    }
+    rv[tid] = best;
+    ri[tid] = bi;
+    __syncthreads();
+    if (tid == 0) {
+      float b = INFINITY;
+      int64_t idx = -1;
+      for (int t = 0; t < static_cast<int>(blockDim.x); ++t)
+        if (ri[t] >= 0 && (rv[t] < b || (rv[t] == b && ri[t] < idx))) {
+          b = rv[t];
+          idx = ri[t];
+        }
+      if (idx < 0) {
+        s_ok = 0;
+      } else {
+        a.scratch[idx] = INFINITY;
+        for (int j = 0; j < d; ++j) Mx[k * (d + 1) + j] = a.X[idx * q + j];
+        Mx[k * (d + 1) + d] = -a.X[idx * q + d];  // b
+      }
+    }
+    __syncthreads();
+  }
+  if (tid == 0 && s_ok) {
+    // Gaussian elimination with partial pivoting.
+    for (int c = 0; c < d && s_ok; ++c) {
+      int piv = c;
+      for (int r = c + 1; r < d; ++r)
+        if (fabs(Mx[r * (d + 1) + c]) > fabs(Mx[piv * (d + 1) + c])) piv = r;
+      if (!(fabs(Mx[piv * (d + 1) + c]) > 0.0)) {
+        s_ok = 0;
+        break;
+      }
+      if (piv != c)
+        for (int j = 0; j <= d; ++j) {
+          const double t = Mx[c * (d + 1) + j];
+          Mx[c * (d + 1) + j] = Mx[piv * (d + 1) + j];
+          Mx[piv * (d + 1) + j] = t;
+        }
+      for (int r = c + 1; r < d; ++r) {
+        const double f = Mx[r * (d + 1) + c] / Mx[c * (d + 1) + c];
+        for (int j = c; j <= d; ++j) Mx[r * (d + 1) + j] -= f * Mx[c * (d + 1) + j];
+      }
+    }
+    if (s_ok) {
+      for (int r = d - 1; r >= 0; --r) {
+        double v = Mx[r * (d + 1) + d];
+        for (int j = r + 1; j < d; ++j) v -= Mx[r * (d + 1) + j] * xp[j];
+        xp[r] = v / Mx[r * (d + 1) + r];
+      }
+      xp[d] = 1.0;
+      for (int j = 0; j < d; ++j) s_ok &= isfinite(xp[j]) ? 1 : 0;
+    }
+  }
+  __syncthreads();
+  double fp = INFINITY;
+  if (s_ok) {
+    double acc = 0.0;
+    for (int64_t k = tid; k < S; k += blockDim.x) {
+      double r = 0.0;
+      for (int j = 0; j < q; ++j) r = fma(a.X[k * q + j], xp[j], r);
+      acc += a.w[k] * fabs(r);
+    }
+    red[tid] = acc;
+    __syncthreads();
+    if (tid == 0) {
+      fp = 0.0;
+      for (int t = 0; t < static_cast<int>(blockDim.x); ++t) fp += red[t];
+    }
+  }
+  if (tid == 0) {
+    const bool use = s_ok && fp <= st->best_f;
+    for (int j = 0; j < d; ++j) a.x_out[j] = use ? xp[j] : st->best_x[j];
+    if (a.obj_out) *a.obj_out = use ? fp : st->best_f;
+    if (!a.status->irls_done) raise_flag(&a.status->flags, L1S_ERR_NOT_CONVERGED);
+  }
+}
+
+int irls_entries(int q) { return q * (q + 1) / 2 + 1; }
+size_t irls_state_bytes() { return sizeof(IrlsState); }
+
+bool launch_solve(const double* X, const double* w, const int64_t* count, int64_t capacity, int d,
+                  int max_iter, double* x_out, double* obj_out, int nblocks, double* partials,
+                  void* state, float* scratch, StatusBlock* status, cudaStream_t st) {
+  IrlsArgs a;
+  a.X = X;
+  a.w = w;
+  a.count = count;
+  a.capacity = capacity;
+  a.d = d;
+  a.q = d + 1;
+  a.partials = partials;
+  a.state = static_cast<IrlsState*>(state);
+  a.status = status;
+  a.scratch = scratch;
+  a.x_out = x_out;
+  a.obj_out = obj_out;
+  a.max_iter = max_iter;
+  const int q = d + 1;
+  const size_t acc_smem = sizeof(double) * (kIrlsTile * q + kIrlsTile + q);
+  const size_t step_smem = sizeof(double) * (irls_entries(q) + d * d + d);
+  const size_t pol_smem = sizeof(double) * (d * (d + 1) + q);
+  if (!cuda_ok(cudaFuncSetAttribute(irls_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    static_cast<int>(step_smem)),
+               "irls_step smem") ||
+      !cuda_ok(cudaFuncSetAttribute(irls_accum_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    static_cast<int>(acc_smem)),
+               "irls_accum smem") ||
+      !cuda_ok(cudaFuncSetAttribute(irls_polish_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    static_cast<int>(pol_smem)),
+               "irls_polish smem"))
+    return false;
+  irls_init_kernel<<<1, 256, 0, st>>>(a);
+  for (int it = 0; it < max_iter; ++it) {
+    irls_accum_kernel<<<nblocks, kIrlsThreads, acc_smem, st>>>(a);
+    irls_step_kernel<<<1, kIrlsThreads, step_smem, st>>>(a, nblocks, 0);
+  }
+  // Objective of the last iterate, then the vertex polish.
+  irls_accum_kernel<<<nblocks, kIrlsThreads, acc_smem, st>>>(a);
+  irls_step_kernel<<<1, kIrlsThreads, step_smem, st>>>(a, nblocks, 1);
+  irls_residuals_kernel<<<nblocks, 256, 0, st>>>(a);
+  irls_polish_kernel<<<1, kIrlsThreads, pol_smem, st>>>(a);
+  return cuda_ok(cudaGetLastError(), "launch l1_solve kernels");
+}
+
+// ----------------------------------------------------------------- objective
+template <typename TA>
+__global__ void __launch_bounds__(256) objective_kernel(const TA* __restrict__ A, int64_t lda,
+                                                        const float* __restrict__ b, int64_t n, int d,
+                                                        const double* __restrict__ x,
+                                                        double* __restrict__ partials) {
+  __shared__ double xs[kMaxD];
+  __shared__ double red[256];
+  for (int k = threadIdx.x; k < d; k += blockDim.x) xs[k] = x[k];
+  __syncthreads();
+  double acc = 0.0;
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const TA* p = A + i * lda;
+    double r = -static_cast<double>(b[i]);
+    for (int k = 0; k < d; ++k) r = fma(static_cast<double>(load_elem<TA>(p + k)), xs[k], r);
+    acc += fabs(r);
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int k = 0; k < static_cast<int>(blockDim.x); ++k) t += red[k];
+    partials[blockIdx.x] = t;
+  }
+}
+
+__global__ void sum_partials_kernel(const double* __restrict__ partials, int count, double* out) {
+  __shared__ double red[256];
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < count; i += blockDim.x) acc += partials[i];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int k = 0; k < static_cast<int>(blockDim.x); ++k) t += red[k];
+    *out = t;
+  }
+}
+
+bool launch_objective(const void* A, int64_t lda, l1s_dtype dt, const float* b, int64_t n, int d,
+                      const double* x, double* out, int nblocks, double* partials, cudaStream_t st) {
+  if (dt == L1S_BF16)
+    objective_kernel<uint16_t><<<nblocks, 256, 0, st>>>(static_cast<const uint16_t*>(A), lda, b, n, d, x,
+                                                       partials);
+  else
+    objective_kernel<float><<<nblocks, 256, 0, st>>>(static_cast<const float*>(A), lda, b, n, d, x,
+                                                    partials);
+  sum_partials_kernel<<<1, 256, 0, st>>>(partials, nblocks, out);
+  return cuda_ok(cudaGetLastError(), "launch objective");
+}
+
+}  // namespace l1s

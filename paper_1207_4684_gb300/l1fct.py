@@ -1,0 +1,244 @@
+"""Python binding of libl1fct.so (ctypes): argument marshalling only.
+
+Every function here has the name of the C entry point it wraps (see
+include/l1fct.h), takes torch tensors for device arrays, passes their data
+pointers, sizes and the current CUDA stream, and raises L1SError when the
+library reports an error.  No step of the method runs in Python; if the
+shared library is missing the import fails instead of falling back to
+anything else.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libl1fct.so")
+
+L1S_OK = 0
+ERRORS = {1: "INVALID_ARG", 2: "WORKSPACE", 3: "CUDA", 4: "RANK_DEFICIENT", 5: "NONFINITE",
+          6: "ZERO_MASS", 7: "CAPACITY", 8: "NOT_CONVERGED"}
+F32, BF16 = 0, 1
+
+
+def flag(code: int) -> int:
+    return 1 << (code - 1)
+
+
+class L1SError(RuntimeError):
+    def __init__(self, code: int, where: str, text: str):
+        self.code = code
+        super().__init__(f"{where}: {ERRORS.get(code, code)}: {text}")
+
+
+class Params(C.Structure):
+    _fields_ = [("seed", C.c_uint64), ("problem_id", C.c_uint32), ("s", C.c_int32),
+                ("r1", C.c_int32), ("r2", C.c_int32), ("coreset_size", C.c_double),
+                ("global_row_offset", C.c_int64), ("sign_flip", C.c_int32), ("reserved", C.c_int32)]
+
+
+def make_params(s: int, r1: int, r2: int, coreset: float, seed: int = 0, problem_id: int = 0,
+                global_row_offset: int = 0, sign_flip: bool = True) -> Params:
+    return Params(seed, problem_id, s, r1, r2, float(coreset), global_row_offset, int(bool(sign_flip)), 0)
+
+
+_lib = None
+_P = C.c_void_p
+_I64 = C.c_int64
+_I32 = C.c_int32
+_SZ = C.c_size_t
+_PP = C.POINTER(Params)
+
+_SIGS = {
+    "l1s_last_error": (C.c_char_p, []),
+    "l1s_version": (C.c_char_p, []),
+    "l1s_workspace_size": (C.c_int, [_PP, _I64, _I32, C.c_int, _I32, C.POINTER(_SZ)]),
+    "l1s_status_reset": (C.c_int, [_P, _SZ, _P]),
+    "l1s_status_read": (C.c_int, [_P, _SZ, _P, C.POINTER(C.c_uint32)]),
+    "fct_embed": (C.c_int, [_P, _I64, C.c_int, _P, _I64, _I32, _PP, _P, _P, _SZ, _P]),
+    "l1_condition": (C.c_int, [_P, _I32, _I32, _PP, _P, _P, _P, _SZ, _P]),
+    "l1_lambda": (C.c_int, [_P, _I64, C.c_int, _P, _I64, _I32, _P, _PP, _P, _P, _P, _SZ, _P]),
+    "l1_sample": (C.c_int, [_P, _I64, C.c_int, _P, _I64, _I32, _P, _PP, _I64, _P, _P, _P, _P, _P, _P,
+                            _SZ, _P]),
+    "l1_sample_from_p": (C.c_int, [_P, _I64, _PP, _I64, _P, _P, _P, _SZ, _P]),
+    "l1_coreset": (C.c_int, [_P, _I64, C.c_int, _P, _I64, _I32, _PP, _I64, _P, _P, _P, _P, _P, _SZ, _P]),
+    "l1_coreset_host": (C.c_int, [_P, _I64, C.c_int, _P, _I64, _I32, _PP, _I64, _P, _P, _P, _P, _SZ, _P]),
+    "l1_solve": (C.c_int, [_P, _P, _P, _I64, _I32, _I32, _P, _P, _P, _SZ, _P]),
+    "l1_objective": (C.c_int, [_P, _I64, C.c_int, _P, _I64, _I32, _P, _P, _P, _SZ, _P]),
+    "l1_regress": (C.c_int, [_P, _I64, C.c_int, _P, _I64, _I32, _PP, _I32, _P, _P, _P, _P, _SZ, _P]),
+    "l1s_debug_variates": (C.c_int, [_PP, _I64, _I64, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "l1s_debug_pi2": (C.c_int, [_PP, _I32, _P, _P]),
+}
+EXPORTS = tuple(_SIGS)
+
+
+def load() -> C.CDLL:
+    """Load libl1fct.so (built by paper_1207_4684_gb300.build); raise if it is missing."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libl1fct.so is not built ({LIB_PATH}); run paper_1207_4684_gb300.build.build()")
+        lib = C.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def _check(rc: int, where: str) -> None:
+    if rc != L1S_OK:
+        raise L1SError(rc, where, load().l1s_last_error().decode())
+
+
+def _ptr(t, contiguous: bool = True) -> int | None:
+    """Data pointer of a tensor (None → NULL); arrays other than A must be contiguous."""
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    if contiguous and not t.is_contiguous():
+        raise ValueError("array arguments must be contiguous (row-major)")
+    return t.data_ptr()
+
+
+def _stream(stream=None) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream
+
+
+def _dtype_code(A: torch.Tensor) -> int:
+    if A.dtype == torch.float32:
+        return F32
+    if A.dtype in (torch.bfloat16, torch.uint16, torch.int16):
+        return BF16
+    raise TypeError(f"A must be float32 or bfloat16, not {A.dtype}")
+
+
+def _matrix(A: torch.Tensor):
+    if A.dim() != 2 or A.stride(1) != 1:
+        raise ValueError("A must be a 2-D row-major tensor (unit column stride)")
+    return A.shape[0], A.shape[1], A.stride(0), _dtype_code(A)
+
+
+def version() -> str:
+    return load().l1s_version().decode()
+
+
+def l1s_workspace_size(params: Params, n: int, d: int, dtype: int = F32, host_staging: bool = False) -> int:
+    out = _SZ(0)
+    _check(load().l1s_workspace_size(C.byref(params), n, d, dtype, int(host_staging), C.byref(out)),
+           "l1s_workspace_size")
+    return out.value
+
+
+def workspace(params: Params, n: int, d: int, dtype: int = F32, host_staging: bool = False,
+              device=None) -> torch.Tensor:
+    """A device byte tensor of the size l1s_workspace_size asks for (torch's allocator is 256-B aligned)."""
+    nbytes = l1s_workspace_size(params, n, d, dtype, host_staging)
+    return torch.empty(nbytes, dtype=torch.uint8, device=device or "cuda")
+
+
+def l1s_status_reset(ws: torch.Tensor, stream=None) -> None:
+    _check(load().l1s_status_reset(_ptr(ws), ws.numel(), _stream(stream)), "l1s_status_reset")
+
+
+def l1s_status_read(ws: torch.Tensor, stream=None) -> int:
+    v = C.c_uint32(0)
+    _check(load().l1s_status_read(_ptr(ws), ws.numel(), _stream(stream), C.byref(v)), "l1s_status_read")
+    return v.value
+
+
+def fct_embed(A, b, params: Params, PiX, ws, stream=None) -> None:
+    n, d, lda, dt = _matrix(A)
+    _check(load().fct_embed(_ptr(A, False), lda, dt, _ptr(b), n, d, C.byref(params), _ptr(PiX), _ptr(ws),
+                            ws.numel(), _stream(stream)), "fct_embed")
+
+
+def l1_condition(PiX, params: Params, R, M, ws, stream=None) -> None:
+    r1, q = PiX.shape
+    _check(load().l1_condition(_ptr(PiX), r1, q, C.byref(params), _ptr(R), _ptr(M), _ptr(ws), ws.numel(),
+                               _stream(stream)), "l1_condition")
+
+
+def l1_lambda(A, b, M, params: Params, lam, lam_sum, ws, stream=None) -> None:
+    n, d, lda, dt = _matrix(A)
+    _check(load().l1_lambda(_ptr(A, False), lda, dt, _ptr(b), n, d, _ptr(M), C.byref(params), _ptr(lam),
+                            _ptr(lam_sum), _ptr(ws), ws.numel(), _stream(stream)), "l1_lambda")
+
+
+def l1_sample(A, b, M, params: Params, capacity: int, idx, w, coreset, count, lam, ws, stream=None) -> None:
+    n, d, lda, dt = _matrix(A)
+    _check(load().l1_sample(_ptr(A, False), lda, dt, _ptr(b), n, d, _ptr(M), C.byref(params), capacity, _ptr(idx),
+                            _ptr(w), _ptr(coreset), _ptr(count), _ptr(lam), _ptr(ws), ws.numel(),
+                            _stream(stream)), "l1_sample")
+
+
+def l1_sample_from_p(p, params: Params, capacity: int, idx, count, ws, stream=None) -> None:
+    _check(load().l1_sample_from_p(_ptr(p), p.numel(), C.byref(params), capacity, _ptr(idx), _ptr(count),
+                                   _ptr(ws), ws.numel(), _stream(stream)), "l1_sample_from_p")
+
+
+def l1_coreset(A, b, params: Params, capacity: int, idx, w, coreset, count, ws, stream=None) -> None:
+    n, d, lda, dt = _matrix(A)
+    _check(load().l1_coreset(_ptr(A, False), lda, dt, _ptr(b), n, d, C.byref(params), capacity, _ptr(idx), _ptr(w),
+                             _ptr(coreset), _ptr(count), _ptr(ws), ws.numel(), _stream(stream)), "l1_coreset")
+
+
+def l1_coreset_host(A, b, params: Params, capacity: int, idx, w, count, ws, stream=None) -> int:
+    """A, b, idx, w, count are CPU tensors (pin them for asynchronous copies); returns the status code."""
+    n, d, lda, dt = _matrix(A)
+    return load().l1_coreset_host(_ptr(A, False), lda, dt, _ptr(b), n, d, C.byref(params), capacity, _ptr(idx),
+                                  _ptr(w), _ptr(count), _ptr(ws), ws.numel(), _stream(stream))
+
+
+def l1_solve(coreset, w, count, capacity: int, d: int, max_iter: int, x, objective, ws, stream=None) -> None:
+    _check(load().l1_solve(_ptr(coreset), _ptr(w), _ptr(count), capacity, d, max_iter, _ptr(x), _ptr(objective),
+                           _ptr(ws), ws.numel(), _stream(stream)), "l1_solve")
+
+
+def l1_objective(A, b, x, objective, ws, stream=None) -> None:
+    n, d, lda, dt = _matrix(A)
+    _check(load().l1_objective(_ptr(A, False), lda, dt, _ptr(b), n, d, _ptr(x), _ptr(objective), _ptr(ws), ws.numel(),
+                               _stream(stream)), "l1_objective")
+
+
+def l1_regress(A, b, params: Params, ws, inputs_on_host: bool = False, stream=None):
+    """Returns (x̂ as a float64 CPU tensor, objective, coreset rows, status code)."""
+    n, d, lda, dt = _matrix(A)
+    x = torch.empty(d, dtype=torch.float64)
+    obj = C.c_double(0.0)
+    rows = C.c_int64(0)
+    rc = load().l1_regress(_ptr(A, False), lda, dt, _ptr(b), n, d, C.byref(params), int(inputs_on_host), _ptr(x),
+                           C.addressof(obj), C.addressof(rows), _ptr(ws), ws.numel(), _stream(stream))
+    if rc in (1, 2, 3):
+        _check(rc, "l1_regress")
+    return x, obj.value, rows.value, rc
+
+
+def l1s_debug_variates(params: Params, row_start: int, count: int, device="cuda", stream=None) -> dict:
+    out = {
+        "bucket_h": torch.empty(count, dtype=torch.int32, device=device),
+        "bucket_i": torch.empty(count, dtype=torch.int32, device=device),
+        "k_h": torch.empty(count, dtype=torch.int32, device=device),
+        "k_i": torch.empty(count, dtype=torch.int32, device=device),
+        "cauchy_h": torch.empty(count, dtype=torch.float32, device=device),
+        "cauchy_i": torch.empty(count, dtype=torch.float32, device=device),
+        "sign": torch.empty(count, dtype=torch.int8, device=device),
+        "u_bits": torch.empty(count, dtype=torch.int64, device=device),
+    }
+    o = out
+    _check(load().l1s_debug_variates(C.byref(params), row_start, count, _ptr(o["bucket_h"]), _ptr(o["bucket_i"]),
+                                     _ptr(o["k_h"]), _ptr(o["k_i"]), _ptr(o["cauchy_h"]), _ptr(o["cauchy_i"]),
+                                     _ptr(o["sign"]), _ptr(o["u_bits"]), _stream(stream)), "l1s_debug_variates")
+    return out
+
+
+def l1s_debug_pi2(params: Params, q: int, device="cuda", stream=None) -> torch.Tensor:
+    out = torch.empty((q, params.r2), dtype=torch.float64, device=device)
+    _check(load().l1s_debug_pi2(C.byref(params), q, _ptr(out), _stream(stream)), "l1s_debug_pi2")
+    return out
