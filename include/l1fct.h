@@ -60,7 +60,8 @@ typedef enum {
   L1S_ERR_NONFINITE = 5,     /* status bit: NaN/Inf met in A, b or Π1X */
   L1S_ERR_ZERO_MASS = 6,     /* status bit: Σλ is zero or not finite */
   L1S_ERR_CAPACITY = 7,      /* status bit: coreset larger than the caller's capacity */
-  L1S_ERR_NOT_CONVERGED = 8  /* status bit: IRLS stopped at its iteration cap */
+  L1S_ERR_NOT_CONVERGED = 8, /* status bit: IRLS stopped at its iteration cap */
+  L1S_ERR_TIMEOUT = 9        /* status bit: a bounded wait inside a kernel gave up */
 } l1s_status;
 
 /* Bits of the device status word (bit = 1 << (code − 1)). */

@@ -13,9 +13,9 @@
 namespace l1s {
 
 // kernels (defined in the other translation units)
-const void* fct_kernel(int log2s, l1s_dtype dt);
-size_t fct_smem_bytes(int s, int r1, int width);
-int fct_threads();
+const void* fct_kernel(int log2s, l1s_dtype dt, bool staged);
+size_t fct_smem_bytes(int s, int d, l1s_dtype dt, int r1, int width, bool staged);
+int fct_threads_for(int log2s, int width);
 bool launch_fct(const Plan& pl, const void* A, int64_t lda, l1s_dtype dt, const float* b,
                 const l1s_params* p, float* pix, unsigned char* ws, cudaStream_t st);
 bool launch_condition(const Plan& pl, const float* pix, const l1s_params* p, double* R_user,
@@ -113,29 +113,33 @@ bool make_plan(const l1s_params* p, int64_t n, int d, l1s_dtype dt, bool host_st
   P.r2 = p->r2;
   P.nblocks = (n + P.s - 1) / P.s;
 
-  // Phase 1: widest column slice whose shared-memory footprint allows two blocks
-  // per SM; otherwise the widest that fits at all.
-  P.fct_threads = fct_threads();
+  // Phase 1.  Preferred: all q columns in one thread block with X tiles staged by TMA.
+  // Otherwise direct loads and the widest column slice whose shared-memory footprint
+  // allows two blocks per SM (or, failing that, one).
   const size_t budget2 = std::min<size_t>(110 * 1024, di.max_smem_optin);
   const size_t budget1 = di.max_smem_optin;
-  int slices = 1;
-  for (;; ++slices) {
-    const int w = (P.q + slices - 1) / slices;
-    if (fct_smem_bytes(P.s, P.r1, w) <= budget2 || w == 1) break;
-  }
-  int width = (P.q + slices - 1) / slices;
-  if (fct_smem_bytes(P.s, P.r1, width) > budget2) {
-    slices = 1;
+  int width = P.q;
+  bool staged = fct_smem_bytes(P.s, P.d, dt, P.r1, P.q, true) <= budget1;
+  if (!staged) {
+    int slices = 1;
     for (;; ++slices) {
       width = (P.q + slices - 1) / slices;
-      if (fct_smem_bytes(P.s, P.r1, width) <= budget1) break;
-      if (width == 1) return set_error("r1 and s too large for shared memory"), false;
+      if (fct_smem_bytes(P.s, P.d, dt, P.r1, width, false) <= budget2 || width == 1) break;
+    }
+    if (fct_smem_bytes(P.s, P.d, dt, P.r1, width, false) > budget2) {
+      for (slices = 1;; ++slices) {
+        width = (P.q + slices - 1) / slices;
+        if (fct_smem_bytes(P.s, P.d, dt, P.r1, width, false) <= budget1) break;
+        if (width == 1) return set_error("r1 and s too large for shared memory"), false;
+      }
     }
   }
+  P.fct_staged = staged ? 1 : 0;
   P.fct_slices = (P.q + width - 1) / width;
   P.fct_width = width;
-  P.fct_smem = fct_smem_bytes(P.s, P.r1, width);
-  const void* fn = fct_kernel(P.log2s, dt);
+  P.fct_smem = fct_smem_bytes(P.s, P.d, dt, P.r1, width, staged);
+  P.fct_threads = fct_threads_for(P.log2s, width);
+  const void* fn = fct_kernel(P.log2s, dt, staged);
   if (!cuda_ok(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     static_cast<int>(P.fct_smem)),
                "cudaFuncSetAttribute(fct_embed)"))
@@ -359,6 +363,7 @@ int l1_coreset(const void* A, int64_t lda, l1s_dtype dtype, const float* b, int6
 static int first_error(uint32_t flags) {
   for (int code = L1S_ERR_RANK_DEFICIENT; code <= L1S_ERR_CAPACITY; ++code)
     if (flags & L1S_FLAG(code)) return code;
+  if (flags & L1S_FLAG(L1S_ERR_TIMEOUT)) return L1S_ERR_TIMEOUT;
   return L1S_OK;
 }
 

@@ -5,12 +5,14 @@
 // argument uses (proof of the fast ℓ1 regression theorem: R⁻¹Π2 before X·(R⁻¹Π2)).
 //
 // A single thread block runs Householder reflections on a column-major FP64
-// copy of Π1·X held in the workspace (a few hundred KB at most, L2-resident).
+// copy of Π1·X, held in shared memory when it fits (r1·q·8 bytes ≤ 160 KB) and
+// in the workspace (L2-resident) otherwise.
 #include "l1s_common.cuh"
 
 namespace l1s {
 
 constexpr int kCondThreads = 512;
+constexpr size_t kCondSmemMax = 160 * 1024;
 
 // Column k of Π1·X counts as dependent on columns 0..k−1 when |R_kk| ≤ kRankTol·‖(Π1X)_{:,k}‖₂:
 // Π1·X carries FP32 rounding of about 1e-7 of its terms, so a smaller residual cannot be told apart
@@ -52,7 +54,8 @@ struct CondArgs {
   int r1, q, r2;
   Key2 key;
   uint32_t problem;
-  double* work;       // r1 × q column-major FP64
+  double* work;       // r1 × q column-major FP64 (workspace copy, used when it does not fit in shared memory)
+  int in_smem;
   double* R;          // q × q row-major (workspace)
   double* M64;        // q × r2 row-major (workspace)
   float* M32;         // q × r2 row-major (workspace)
@@ -63,13 +66,14 @@ struct CondArgs {
 };
 
 __global__ void __launch_bounds__(kCondThreads) condition_kernel(const CondArgs a) {
+  extern __shared__ __align__(16) double cond_smem[];
   __shared__ double scratch[33];
   __shared__ double s_vtv;
   __shared__ int s_rank_bad;
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int lane = tid & 31, warp = tid >> 5, nwarps = nthr >> 5;
   const int r1 = a.r1, q = a.q;
-  double* W = a.work;
+  double* W = a.in_smem ? cond_smem : a.work;
 
   for (int i = tid; i < r1 * q; i += nthr) {
     const int r = i / q, c = i - r * q;
@@ -171,7 +175,14 @@ bool launch_condition(const Plan& pl, const float* pix, const l1s_params* p, dou
   a.R_user = R_user;
   a.M_user = M_user;
   a.flags = reinterpret_cast<uint32_t*>(ws + pl.off_status);
-  condition_kernel<<<1, kCondThreads, 0, st>>>(a);
+  const size_t bytes = sizeof(double) * static_cast<size_t>(pl.r1) * pl.q;
+  a.in_smem = bytes <= kCondSmemMax ? 1 : 0;
+  const size_t smem = a.in_smem ? bytes : 0;
+  if (!cuda_ok(cudaFuncSetAttribute(condition_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    static_cast<int>(smem)),
+               "condition smem"))
+    return false;
+  condition_kernel<<<1, kCondThreads, smem, st>>>(a);
   return cuda_ok(cudaGetLastError(), "launch condition");
 }
 

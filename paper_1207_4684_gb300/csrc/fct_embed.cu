@@ -1,23 +1,28 @@
 // Phase 1: the FCT1 embedding Π1·X = 4·B·C·H̃·D·X (§3.1, FCT1 construction;
 // Figure 2, steps 1-2), X = [A, −b].
 //
-// One thread block owns a slice of columns of X and walks over s-row blocks
-// β (grid-stride).  Per block:
+// Persistent thread blocks walk over s-row blocks β of X (grid stride); each
+// thread block owns a slice of w columns of Π1X.  Per block β:
 //   1. one Philox call per row gives the row's sign σ, the buckets of its two
-//      virtual rows and their Cauchy scales (kept in shared memory);
-//   2. the s × w tile of X is read with coalesced loads, the sign is applied
-//      on load, and the identity half of G_s = [H_s; I_s] is scattered at once:
-//      P[h_I(i), c] += 4·c_I(i)·σ_i·x_ic;
-//   3. the Sylvester–Hadamard transform of each column runs in shared memory
-//      as two passes of radix-2^k butterflies held in registers (k = ⌈log2 s / 2⌉),
-//      and the second pass scatters the Hadamard half straight from registers:
-//      P[h_H(i), c] += 4·c_H(i)/√s·(H_s z)_ic.
+//      virtual rows and their Cauchy scales (shared memory);
+//   2. the s rows of A and b arrive in a shared-memory stage by TMA bulk copies
+//      (cp.async.bulk, completion on an mbarrier) issued two blocks ahead, so
+//      HBM traffic overlaps the arithmetic; a ragged last block, a padded lda
+//      or an unaligned base are read with ordinary loads instead;
+//   3. pass 1 reads the raw tile, applies σ, scatters the identity half of
+//      G_s = [H_s; I_s] (P[h_I(i), c] += 4·c_I(i)·σ_i·x_ic), runs the first
+//      ⌊log2 s / 2⌋ radix-2 butterfly stages in registers and stores the tile;
+//   4. pass 2 runs the remaining stages and scatters the Hadamard half
+//      (P[h_H(i), c] += 4·c_H(i)/√s·(H_s z)_ic) straight from registers.
 // P, the block's r1 × w partial of Π1X, lives in shared memory (B's hashed sum
-// as a shared-memory reduction, no global atomics).  A second kernel adds the
+// is a shared-memory reduction, no global atomics).  A second kernel adds the
 // per-block partials in a fixed order.
 #include "l1s_common.cuh"
 
 namespace l1s {
+
+constexpr int kFctStages = 2;
+constexpr int kFctMaxThreads = 512;
 
 struct FctArgs {
   const void* A;
@@ -26,23 +31,104 @@ struct FctArgs {
   int64_t n;
   int d, q, r1, width;
   int64_t nblocks;
+  int64_t full_blocks;    // blocks with s valid rows
+  int tma;                // 1: full blocks arrive by bulk copy
+  uint32_t stage_a_bytes; // bytes of A in a stage (s·d·elem, multiple of 16 when tma)
+  uint32_t stage_bytes;   // A part rounded up to 16 + s·4 for b
   Key2 key;
   uint32_t problem;
   int64_t row_offset;
   int sign_flip;
   float inv_sqrt_s;
-  float* partials;  // [slices][gridDim.x][r1][width]
+  float* partials;        // [slices][gridDim.x][r1][width]
   uint32_t* flags;
 };
 
-constexpr int kFctThreads = 256;
+struct RowMeta {          // draws of one input row
+  int hI;
+  float wI;               // 4·c_I
+  int hH;
+  float wH;               // 4·c_H/√s
+};
 
-// One radix-2^K pass over index bits [LO, LO+K) of every column of the tile.
-// tile is s × W (row-major, row stride W).  LAST: scatter instead of store.
-template <int LOG2S, int K, int LO, bool LAST>
-__device__ __forceinline__ void fwht_pass(float* __restrict__ tile, float* __restrict__ part,
-                                          const int* __restrict__ hH, const float* __restrict__ wH,
-                                          int W, int wcols) {
+template <typename TA>
+__device__ __forceinline__ float widen(TA v) {
+  if constexpr (sizeof(TA) == 4) return v;
+  else return __uint_as_float(static_cast<uint32_t>(v) << 16);
+}
+
+// x_{row0+row, col} of X = [A, −b]: from the shared-memory stage (STAGED) or from global memory.
+template <typename TA, bool STAGED>
+__device__ __forceinline__ float x_value(const FctArgs& a, const unsigned char* stage, int64_t row0, int row,
+                                         int col) {
+  if constexpr (STAGED) {
+    if (col < a.d) return widen<TA>(reinterpret_cast<const TA*>(stage)[row * a.d + col]);
+    return -reinterpret_cast<const float*>(stage + ((a.stage_a_bytes + 15) & ~15u))[row];
+  } else {
+    const int64_t r = row0 + row;
+    if (r >= a.n) return 0.f;
+    if (col < a.d) return widen<TA>(__ldg(static_cast<const TA*>(a.A) + r * a.lda + col));
+    return -__ldg(a.b + r);
+  }
+}
+
+// Pass 1: bits [0, K) of the row index.  Reads the raw stage, signs, scatters the identity half.
+template <int LOG2S, int K, bool LAST, typename TA, bool STAGED>
+__device__ __forceinline__ void fwht_first(const FctArgs& a, const unsigned char* __restrict__ stage, int64_t row0,
+                                           int c0, float* __restrict__ tile, float* __restrict__ part,
+                                           const RowMeta* __restrict__ meta, const float* __restrict__ sg,
+                                           int W, int wcols) {
+  constexpr int G = 1 << K;
+  const int ngroups = ((1 << LOG2S) >> K) * W;
+  const int step = blockDim.x;
+  int rest = threadIdx.x / W;
+  int c = threadIdx.x - rest * W;
+  const int drest = step / W, dc = step - drest * W;
+  for (int g = threadIdx.x; g < ngroups; g += step) {
+    const int base = rest << K;
+    const bool live = c < wcols;
+    float v[G];
+#pragma unroll
+    for (int j = 0; j < G; ++j) v[j] = live ? x_value<TA, STAGED>(a, stage, row0, base + j, c0 + c) : 0.f;
+#pragma unroll
+    for (int j = 0; j < G; ++j) {
+      const int row = base + j;
+      v[j] *= sg[row];
+      if (live) atomicAdd(&part[meta[row].hI * W + c], meta[row].wI * v[j]);
+    }
+#pragma unroll
+    for (int t = 0; t < K; ++t) {
+#pragma unroll
+      for (int j = 0; j < G; ++j) {
+        if ((j & (1 << t)) == 0) {
+          const float lo = v[j], hi = v[j | (1 << t)];
+          v[j] = lo + hi;
+          v[j | (1 << t)] = lo - hi;
+        }
+      }
+    }
+    if constexpr (LAST) {
+      if (live) {
+#pragma unroll
+        for (int j = 0; j < G; ++j) atomicAdd(&part[meta[base + j].hH * W + c], meta[base + j].wH * v[j]);
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < G; ++j) tile[(base + j) * W + c] = v[j];
+    }
+    c += dc;
+    rest += drest;
+    if (c >= W) {
+      c -= W;
+      ++rest;
+    }
+  }
+}
+
+// Pass 2: bits [LO, LO+K) of the row index from the tile, then the Hadamard-half scatter.
+template <int LOG2S, int K, int LO>
+__device__ __forceinline__ void fwht_second(const float* __restrict__ tile, float* __restrict__ part,
+                                            const RowMeta* __restrict__ meta, int W, int wcols) {
   constexpr int G = 1 << K;
   const int ngroups = ((1 << LOG2S) >> K) * W;
   const int step = blockDim.x;
@@ -65,16 +151,11 @@ __device__ __forceinline__ void fwht_pass(float* __restrict__ tile, float* __res
         }
       }
     }
-    if constexpr (!LAST) {
+    if (c < wcols) {
 #pragma unroll
-      for (int j = 0; j < G; ++j) tile[(base + (j << LO)) * W + c] = v[j];
-    } else {
-      if (c < wcols) {
-#pragma unroll
-        for (int j = 0; j < G; ++j) {
-          const int row = base + (j << LO);
-          atomicAdd(&part[hH[row] * W + c], wH[row] * v[j]);
-        }
+      for (int j = 0; j < G; ++j) {
+        const RowMeta m = meta[base + (j << LO)];
+        atomicAdd(&part[m.hH * W + c], m.wH * v[j]);
       }
     }
     c += dc;
@@ -86,77 +167,129 @@ __device__ __forceinline__ void fwht_pass(float* __restrict__ tile, float* __res
   }
 }
 
-template <int LOG2S, typename TA>
-__global__ void __launch_bounds__(kFctThreads) fct_embed_kernel(const FctArgs a) {
+template <typename TA>
+__device__ __forceinline__ void load_stage_plain(const FctArgs& a, int64_t row0, int S, unsigned char* stage) {
+  TA* ra = reinterpret_cast<TA*>(stage);
+  float* rb = reinterpret_cast<float*>(stage + ((a.stage_a_bytes + 15) & ~15u));
+  const TA* A = static_cast<const TA*>(a.A);
+  const int d = a.d;
+  for (int e = threadIdx.x; e < S * d; e += blockDim.x) {
+    const int i = e / d, c = e - i * d;
+    const int64_t row = row0 + i;
+    TA v = TA(0);
+    if (row < a.n) v = A[row * a.lda + c];
+    ra[e] = v;
+  }
+  for (int i = threadIdx.x; i < S; i += blockDim.x) {
+    const int64_t row = row0 + i;
+    rb[i] = row < a.n ? a.b[row] : 0.f;
+  }
+}
+
+template <typename TA>
+__device__ __forceinline__ void issue_stage_tma(const FctArgs& a, int64_t blk, int S, unsigned char* stage,
+                                                uint64_t* bar) {
+  const unsigned char* srcA = static_cast<const unsigned char*>(a.A) + static_cast<size_t>(blk) * a.stage_a_bytes;
+  const float* srcB = a.b + static_cast<size_t>(blk) * S;
+  fence_proxy_async_smem();
+  mbar_arrive_expect_tx(bar, a.stage_a_bytes + static_cast<uint32_t>(S) * 4u);
+  bulk_copy_g2s(stage, srcA, a.stage_a_bytes, bar);
+  bulk_copy_g2s(stage + ((a.stage_a_bytes + 15) & ~15u), srcB, static_cast<uint32_t>(S) * 4u, bar);
+}
+
+template <int LOG2S, typename TA, bool STAGED>
+__global__ void __launch_bounds__(kFctMaxThreads) fct_embed_kernel(const FctArgs a) {
   constexpr int S = 1 << LOG2S;
-  constexpr int K1 = LOG2S / 2;          // first pass: bits [0, K1)
-  constexpr int K2 = LOG2S - K1;         // second pass: bits [K1, LOG2S)
+  constexpr int K1 = LOG2S / 2;          // pass 1: bits [0, K1)
+  constexpr int K2 = LOG2S - K1;         // pass 2: bits [K1, LOG2S)
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ uint64_t bars[kFctStages];
+  __shared__ int s_timeout;
   const int W = a.width;
   const int c0 = blockIdx.y * W;
   const int wcols = min(W, a.q - c0);
-  float* part = reinterpret_cast<float*>(smem_raw);
+  // layout: stages (STAGED only) | part | tile | meta | sg
+  unsigned char* stages = smem_raw;
+  float* part = reinterpret_cast<float*>(stages + (STAGED ? static_cast<size_t>(kFctStages) * a.stage_bytes : 0));
   float* tile = part + a.r1 * W;
-  int* hH = reinterpret_cast<int*>(tile + S * W);
-  int* hI = hH + S;
-  float* wH = reinterpret_cast<float*>(hI + S);
-  float* wI = wH + S;
-  float* sg = wI + S;
-  const TA* A = static_cast<const TA*>(a.A);
+  RowMeta* meta = reinterpret_cast<RowMeta*>(tile + S * W);
+  float* sg = reinterpret_cast<float*>(meta + S);
 
   for (int i = threadIdx.x; i < a.r1 * W; i += blockDim.x) part[i] = 0.f;
-  bool finite = true;
-  const int step = blockDim.x;
-  const int di = step / W, dcol = step - di * W;
-
-  for (int64_t blk = blockIdx.x; blk < a.nblocks; blk += gridDim.x) {
+  if (threadIdx.x == 0) {
+    s_timeout = 0;
+    for (int k = 0; k < kFctStages; ++k) mbar_init(&bars[k], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  const bool tma = STAGED;
+  if (threadIdx.x == 0 && tma) {
+    for (int k = 0; k < kFctStages; ++k) {
+      const int64_t blk = blockIdx.x + static_cast<int64_t>(k) * gridDim.x;
+      if (blk < a.full_blocks) issue_stage_tma<TA>(a, blk, S, stages + static_cast<size_t>(k) * a.stage_bytes, &bars[k]);
+    }
+  }
+  int64_t it = 0;
+  for (int64_t blk = blockIdx.x; blk < a.nblocks; blk += gridDim.x, ++it) {
     const int64_t row0 = blk * S;
-    __syncthreads();  // the previous block is done with tile and draws
-    for (int i = threadIdx.x; i < S; i += step) {
+    const int st = static_cast<int>(it % kFctStages);
+    unsigned char* stage = stages + static_cast<size_t>(st) * a.stage_bytes;
+    for (int i = threadIdx.x; i < S; i += blockDim.x) {
       const uint64_t grow = static_cast<uint64_t>(a.row_offset + row0 + i);
       const uint4 o = draw_row(a.key, grow, a.problem, kStreamFct);
-      hH[i] = bucket_of(o.x, a.r1);
-      hI[i] = bucket_of(o.z, a.r1);
-      wH[i] = 4.f * cauchy_f32(o.y >> 8) * a.inv_sqrt_s;
-      wI[i] = 4.f * cauchy_f32(o.w >> 8);
+      RowMeta m;
+      m.hH = bucket_of(o.x, a.r1);
+      m.hI = bucket_of(o.z, a.r1);
+      m.wH = 4.f * cauchy_f32(o.y >> 8) * a.inv_sqrt_s;
+      m.wI = 4.f * cauchy_f32(o.w >> 8);
+      meta[i] = m;
       sg[i] = (a.sign_flip && (o.w & 1u)) ? -1.f : 1.f;
     }
-    __syncthreads();
-    {
-      int i = threadIdx.x / W;
-      int c = threadIdx.x - i * W;
-      for (int e = threadIdx.x; e < S * W; e += step) {
-        const int64_t row = row0 + i;
-        const int col = c0 + c;
-        float x = 0.f;
-        if (row < a.n && c < wcols) {
-          x = (col < a.d) ? load_elem<TA>(A + row * a.lda + col) : -__ldg(a.b + row);
-          finite &= isfinite(x);
-        }
-        const float z = sg[i] * x;
-        tile[e] = z;
-        if (c < wcols) atomicAdd(&part[hI[i] * W + c], wI[i] * z);
-        c += dcol;
-        i += di;
-        if (c >= W) {
-          c -= W;
-          ++i;
-        }
+    if constexpr (STAGED) {
+      if (blk < a.full_blocks) {
+        const bool ok = mbar_wait_bounded(&bars[st], static_cast<uint32_t>((it / kFctStages) & 1), kWaitCycles);
+        if (!ok) s_timeout = 1;
+      } else {
+        load_stage_plain<TA>(a, row0, S, stage);
       }
     }
     __syncthreads();
+    if (s_timeout) break;
     if constexpr (LOG2S <= 1) {
-      fwht_pass<LOG2S, LOG2S, 0, true>(tile, part, hH, wH, W, wcols);
-    } else {
-      fwht_pass<LOG2S, K1, 0, false>(tile, part, hH, wH, W, wcols);
+      fwht_first<LOG2S, LOG2S, true, TA, STAGED>(a, stage, row0, c0, tile, part, meta, sg, W, wcols);
       __syncthreads();
-      fwht_pass<LOG2S, K2, K1, true>(tile, part, hH, wH, W, wcols);
+      if (threadIdx.x == 0 && tma) {
+        const int64_t nxt = blk + static_cast<int64_t>(kFctStages) * gridDim.x;
+        if (nxt < a.full_blocks) issue_stage_tma<TA>(a, nxt, S, stage, &bars[st]);
+      }
+    } else {
+      fwht_first<LOG2S, K1, false, TA, STAGED>(a, stage, row0, c0, tile, part, meta, sg, W, wcols);
+      __syncthreads();
+      if (threadIdx.x == 0 && tma) {
+        const int64_t nxt = blk + static_cast<int64_t>(kFctStages) * gridDim.x;
+        if (nxt < a.full_blocks) issue_stage_tma<TA>(a, nxt, S, stage, &bars[st]);
+      }
+      fwht_second<LOG2S, K2, K1>(tile, part, meta, W, wcols);
     }
+    __syncthreads();
   }
-  __syncthreads();
+  if (s_timeout) {
+    // Drain the copies still in flight (bounded) before the block's shared memory is released.
+    if (threadIdx.x == 0) {
+      raise_flag(a.flags, L1S_ERR_TIMEOUT);
+      for (int64_t k = 0; k < kFctStages; ++k) {
+        const int64_t j = it + k;
+        const int64_t blk = blockIdx.x + j * gridDim.x;
+        if (tma && blk < a.full_blocks)
+          mbar_wait_bounded(&bars[j % kFctStages], static_cast<uint32_t>((j / kFctStages) & 1), kWaitCycles);
+      }
+    }
+    __syncthreads();
+    return;
+  }
+  // Non-finite input shows up as a non-finite partial (checked in the reduction).
   float* out = a.partials + (static_cast<size_t>(blockIdx.y) * gridDim.x + blockIdx.x) * a.r1 * W;
   for (int i = threadIdx.x; i < a.r1 * W; i += blockDim.x) out[i] = part[i];
-  if (!finite) raise_flag(a.flags, L1S_ERR_NONFINITE);
 }
 
 // Fixed-order sum of the per-block partials: PiX[r][c0+c] = Σ_blocks partial[r][c].
@@ -201,36 +334,58 @@ __global__ void __launch_bounds__(1024) fct_reduce_kernel(const float* __restric
 }
 
 // ----------------------------------------------------------------- dispatch
-template <typename TA>
+template <typename TA, bool STAGED>
 static const void* fct_kernel_for(int log2s) {
   switch (log2s) {
-    case 0: return reinterpret_cast<const void*>(&fct_embed_kernel<0, TA>);
-    case 1: return reinterpret_cast<const void*>(&fct_embed_kernel<1, TA>);
-    case 2: return reinterpret_cast<const void*>(&fct_embed_kernel<2, TA>);
-    case 3: return reinterpret_cast<const void*>(&fct_embed_kernel<3, TA>);
-    case 4: return reinterpret_cast<const void*>(&fct_embed_kernel<4, TA>);
-    case 5: return reinterpret_cast<const void*>(&fct_embed_kernel<5, TA>);
-    case 6: return reinterpret_cast<const void*>(&fct_embed_kernel<6, TA>);
-    case 7: return reinterpret_cast<const void*>(&fct_embed_kernel<7, TA>);
-    case 8: return reinterpret_cast<const void*>(&fct_embed_kernel<8, TA>);
-    case 9: return reinterpret_cast<const void*>(&fct_embed_kernel<9, TA>);
-    case 10: return reinterpret_cast<const void*>(&fct_embed_kernel<10, TA>);
-    case 11: return reinterpret_cast<const void*>(&fct_embed_kernel<11, TA>);
-    case 12: return reinterpret_cast<const void*>(&fct_embed_kernel<12, TA>);
+    case 0: return reinterpret_cast<const void*>(&fct_embed_kernel<0, TA, STAGED>);
+    case 1: return reinterpret_cast<const void*>(&fct_embed_kernel<1, TA, STAGED>);
+    case 2: return reinterpret_cast<const void*>(&fct_embed_kernel<2, TA, STAGED>);
+    case 3: return reinterpret_cast<const void*>(&fct_embed_kernel<3, TA, STAGED>);
+    case 4: return reinterpret_cast<const void*>(&fct_embed_kernel<4, TA, STAGED>);
+    case 5: return reinterpret_cast<const void*>(&fct_embed_kernel<5, TA, STAGED>);
+    case 6: return reinterpret_cast<const void*>(&fct_embed_kernel<6, TA, STAGED>);
+    case 7: return reinterpret_cast<const void*>(&fct_embed_kernel<7, TA, STAGED>);
+    case 8: return reinterpret_cast<const void*>(&fct_embed_kernel<8, TA, STAGED>);
+    case 9: return reinterpret_cast<const void*>(&fct_embed_kernel<9, TA, STAGED>);
+    case 10: return reinterpret_cast<const void*>(&fct_embed_kernel<10, TA, STAGED>);
+    case 11: return reinterpret_cast<const void*>(&fct_embed_kernel<11, TA, STAGED>);
+    case 12: return reinterpret_cast<const void*>(&fct_embed_kernel<12, TA, STAGED>);
     default: return nullptr;
   }
 }
 
-const void* fct_kernel(int log2s, l1s_dtype dt) {
-  return dt == L1S_BF16 ? fct_kernel_for<uint16_t>(log2s) : fct_kernel_for<float>(log2s);
+const void* fct_kernel(int log2s, l1s_dtype dt, bool staged) {
+  if (dt == L1S_BF16) return staged ? fct_kernel_for<uint16_t, true>(log2s) : fct_kernel_for<uint16_t, false>(log2s);
+  return staged ? fct_kernel_for<float, true>(log2s) : fct_kernel_for<float, false>(log2s);
 }
 
-size_t fct_smem_bytes(int s, int r1, int width) {
-  return static_cast<size_t>(r1) * width * 4 + static_cast<size_t>(s) * width * 4 +
-         static_cast<size_t>(s) * 20;
+uint32_t fct_stage_bytes(int s, int d, l1s_dtype dt) {
+  const uint32_t esz = dt == L1S_BF16 ? 2u : 4u;
+  const uint32_t a_bytes = static_cast<uint32_t>(s) * d * esz;
+  return ((a_bytes + 15u) & ~15u) + static_cast<uint32_t>(s) * 4u;
 }
 
-int fct_threads() { return kFctThreads; }
+size_t fct_smem_bytes(int s, int d, l1s_dtype dt, int r1, int width, bool staged) {
+  return (staged ? static_cast<size_t>(kFctStages) * fct_stage_bytes(s, d, dt) : 0) +
+         static_cast<size_t>(r1) * width * 4 + static_cast<size_t>(s) * width * 4 +
+         static_cast<size_t>(s) * (sizeof(RowMeta) + 4);
+}
+
+// TMA staging needs A's rows back to back (lda = d), 16-byte aligned bases and stage parts.
+bool fct_can_stage(int s, int d, l1s_dtype dt, int64_t lda, const void* A, const float* b) {
+  const uint32_t esz = dt == L1S_BF16 ? 2u : 4u;
+  return lda == d && (reinterpret_cast<uintptr_t>(A) % 16 == 0) && (reinterpret_cast<uintptr_t>(b) % 16 == 0) &&
+         ((static_cast<uint64_t>(s) * d * esz) % 16 == 0) && ((s * 4) % 16 == 0);
+}
+
+// Threads: enough for one butterfly group per (column, row group) of the larger pass.
+int fct_threads_for(int log2s, int width) {
+  const int k = log2s / 2;
+  const int groups = std::max(((1 << log2s) >> k) * width, ((1 << log2s) >> (log2s - k)) * width);
+  int t = (groups + 31) / 32 * 32;
+  t = t < 256 ? 256 : t;
+  return t > kFctMaxThreads ? kFctMaxThreads : t;
+}
 
 bool launch_fct(const Plan& pl, const void* A, int64_t lda, l1s_dtype dt, const float* b,
                 const l1s_params* p, float* pix, unsigned char* ws, cudaStream_t st) {
@@ -244,6 +399,12 @@ bool launch_fct(const Plan& pl, const void* A, int64_t lda, l1s_dtype dt, const 
   a.r1 = pl.r1;
   a.width = pl.fct_width;
   a.nblocks = pl.nblocks;
+  a.full_blocks = pl.n / pl.s;
+  const uint32_t esz = dt == L1S_BF16 ? 2u : 4u;
+  a.stage_a_bytes = static_cast<uint32_t>(pl.s) * pl.d * esz;
+  a.stage_bytes = fct_stage_bytes(pl.s, pl.d, dt);
+  const bool staged = pl.fct_staged && fct_can_stage(pl.s, pl.d, dt, lda, A, b);
+  a.tma = staged ? 1 : 0;
   a.key = make_key(p->seed);
   a.problem = p->problem_id;
   a.row_offset = p->global_row_offset;
@@ -251,20 +412,20 @@ bool launch_fct(const Plan& pl, const void* A, int64_t lda, l1s_dtype dt, const 
   a.inv_sqrt_s = static_cast<float>(1.0 / sqrt(static_cast<double>(pl.s)));
   a.partials = reinterpret_cast<float*>(ws + pl.off_partials);
   a.flags = reinterpret_cast<uint32_t*>(ws + pl.off_status);
-  const void* fn = fct_kernel(pl.log2s, dt);
-  if (!cuda_ok(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    static_cast<int>(pl.fct_smem)),
+  // A layout that cannot be staged falls back to direct loads with the same grid; the
+  // direct variant needs less shared memory than the staged one it was planned for.
+  const void* fn = fct_kernel(pl.log2s, dt, staged);
+  const size_t smem = fct_smem_bytes(pl.s, pl.d, dt, pl.r1, pl.fct_width, staged);
+  if (!cuda_ok(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)),
                "cudaFuncSetAttribute(fct_embed)"))
     return false;
   void* args[] = {&a};
   dim3 grid(pl.fct_ctas, pl.fct_slices);
-  if (!cuda_ok(cudaLaunchKernel(fn, grid, dim3(pl.fct_threads), args, pl.fct_smem, st),
-               "launch fct_embed"))
+  if (!cuda_ok(cudaLaunchKernel(fn, grid, dim3(pl.fct_threads), args, smem, st), "launch fct_embed"))
     return false;
   const int per = pl.r1 * pl.fct_width;
   dim3 rgrid((per + 31) / 32, pl.fct_slices);
-  fct_reduce_kernel<<<rgrid, 1024, 0, st>>>(a.partials, pl.fct_ctas, pl.r1, pl.fct_width, pl.q, pix,
-                                            a.flags);
+  fct_reduce_kernel<<<rgrid, 1024, 0, st>>>(a.partials, pl.fct_ctas, pl.r1, pl.fct_width, pl.q, pix, a.flags);
   return cuda_ok(cudaGetLastError(), "launch fct_reduce");
 }
 

@@ -215,17 +215,20 @@ __global__ void __launch_bounds__(kLamThreads) lambda_kernel_generic(const TA* _
   if (threadIdx.x == 0) block_sums[blockIdx.x] = tot;
 }
 
-// Σλ over the block partials in a fixed order; τ = m_s / Σλ.
-__global__ void lambda_finalize_kernel(const double* __restrict__ block_sums, int nblocks, double coreset,
-                                       StatusBlock* status, double* user_sum) {
-  __shared__ double part[256];
+// Σλ over the block partials in a fixed order (strided per-thread sums, then a
+// fixed shuffle tree and the warp sums in order); τ = m_s / Σλ.
+__global__ void __launch_bounds__(256) lambda_finalize_kernel(const double* __restrict__ block_sums, int nblocks,
+                                                              double coreset, StatusBlock* status, double* user_sum) {
+  __shared__ double wsum[8];
   double acc = 0.0;
   for (int i = threadIdx.x; i < nblocks; i += blockDim.x) acc += block_sums[i];
-  part[threadIdx.x] = acc;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+  if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = acc;
   __syncthreads();
   if (threadIdx.x == 0) {
     double tot = 0.0;
-    for (int i = 0; i < static_cast<int>(blockDim.x); ++i) tot += part[i];
+    for (int w = 0; w < (blockDim.x >> 5); ++w) tot += wsum[w];
     status->lambda_total = tot;
     if (user_sum) *user_sum = tot;
     if (!(tot > 0.0) || !isfinite(tot)) {

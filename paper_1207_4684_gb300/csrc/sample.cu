@@ -53,7 +53,10 @@ struct MarkArgs {
   const StatusBlock* status;
   uint64_t* mask;        // ⌈n/64⌉ words
   int64_t* counts;       // per block
+  int lam_pairs;         // 1: λ is 8-byte aligned, read two rows per load
 };
+
+constexpr int kMarkUnroll = 4;
 
 __global__ void __launch_bounds__(kSmpThreads) sample_mark_kernel(const MarkArgs a) {
   __shared__ int64_t wcount[kSmpThreads / 32];
@@ -63,32 +66,59 @@ __global__ void __launch_bounds__(kSmpThreads) sample_mark_kernel(const MarkArgs
   const double tau = a.p ? 0.0 : a.status->tau;
   const float tau32 = a.p ? 0.f : a.status->tau32;
   const bool odd_offset = (a.row_offset & 1) != 0;
+  const int64_t stride = 64 * static_cast<int64_t>(nwarps);
   int64_t kept = 0;
-  for (int64_t base = start + 64 * warp; base < stop; base += 64 * nwarps) {
-    const int64_t r0 = base + 2 * lane;      // this lane's two rows: r0, r0 + 1
-    const uint64_t g0 = static_cast<uint64_t>(a.row_offset + r0);
-    uint32_t w0a, w0b, w1a, w1b;
-    if (!odd_offset) {
-      const uint4 o = draw_row(a.key, g0 >> 1, a.problem, kStreamSample);
-      w0a = o.x; w0b = o.y; w1a = o.z; w1b = o.w;
-    } else {
-      const uint4 o0 = draw_row(a.key, g0 >> 1, a.problem, kStreamSample);
-      const uint4 o1 = draw_row(a.key, (g0 + 1) >> 1, a.problem, kStreamSample);
-      w0a = o0.z; w0b = o0.w; w1a = o1.x; w1b = o1.y;
+  // Each warp covers 64 consecutive rows per step (two per lane); kMarkUnroll steps are
+  // loaded before any is decided so that several loads are in flight per warp.
+  for (int64_t base0 = start + 64 * warp; base0 < stop; base0 += stride * kMarkUnroll) {
+    float l0[kMarkUnroll], l1[kMarkUnroll];
+    double p0[kMarkUnroll], p1[kMarkUnroll];
+#pragma unroll
+    for (int u = 0; u < kMarkUnroll; ++u) {
+      const int64_t r0 = base0 + u * stride + 2 * lane;
+      l0[u] = l1[u] = 0.f;
+      p0[u] = p1[u] = 0.0;
+      if (a.p) {
+        if (r0 < stop) p0[u] = a.p[r0];
+        if (r0 + 1 < stop) p1[u] = a.p[r0 + 1];
+      } else if (a.lam_pairs && r0 + 1 < stop) {
+        const float2 v = *reinterpret_cast<const float2*>(a.lam + r0);
+        l0[u] = v.x;
+        l1[u] = v.y;
+      } else {
+        if (r0 < stop) l0[u] = a.lam[r0];
+        if (r0 + 1 < stop) l1[u] = a.lam[r0 + 1];
+      }
     }
-    bool k0 = false, k1 = false;
-    if (a.p) {
-      if (r0 < stop) k0 = static_cast<double>(u53_of(w0a, w0b)) * 0x1p-53 < a.p[r0];
-      if (r0 + 1 < stop) k1 = static_cast<double>(u53_of(w1a, w1b)) * 0x1p-53 < a.p[r0 + 1];
-    } else {
-      if (r0 < stop) k0 = keep_row(a.lam[r0], tau32, tau, w0a, w0b);
-      if (r0 + 1 < stop) k1 = keep_row(a.lam[r0 + 1], tau32, tau, w1a, w1b);
+#pragma unroll
+    for (int u = 0; u < kMarkUnroll; ++u) {
+      const int64_t base = base0 + u * stride;
+      if (base >= stop) break;                 // uniform across the warp
+      const int64_t r0 = base + 2 * lane;      // this lane's two rows: r0, r0 + 1
+      const uint64_t g0 = static_cast<uint64_t>(a.row_offset + r0);
+      uint32_t w0a, w0b, w1a, w1b;
+      if (!odd_offset) {
+        const uint4 o = draw_row(a.key, g0 >> 1, a.problem, kStreamSample);
+        w0a = o.x; w0b = o.y; w1a = o.z; w1b = o.w;
+      } else {
+        const uint4 o0 = draw_row(a.key, g0 >> 1, a.problem, kStreamSample);
+        const uint4 o1 = draw_row(a.key, (g0 + 1) >> 1, a.problem, kStreamSample);
+        w0a = o0.z; w0b = o0.w; w1a = o1.x; w1b = o1.y;
+      }
+      bool k0 = false, k1 = false;
+      if (a.p) {
+        if (r0 < stop) k0 = static_cast<double>(u53_of(w0a, w0b)) * 0x1p-53 < p0[u];
+        if (r0 + 1 < stop) k1 = static_cast<double>(u53_of(w1a, w1b)) * 0x1p-53 < p1[u];
+      } else {
+        if (r0 < stop) k0 = keep_row(l0[u], tau32, tau, w0a, w0b);
+        if (r0 + 1 < stop) k1 = keep_row(l1[u], tau32, tau, w1a, w1b);
+      }
+      const uint32_t be = __ballot_sync(0xffffffffu, k0);
+      const uint32_t bo = __ballot_sync(0xffffffffu, k1);
+      const uint64_t m = spread_bits(be) | (spread_bits(bo) << 1);
+      if (lane == 0) a.mask[base >> 6] = m;
+      kept += __popcll(m);
     }
-    const uint32_t be = __ballot_sync(0xffffffffu, k0);
-    const uint32_t bo = __ballot_sync(0xffffffffu, k1);
-    const uint64_t m = spread_bits(be) | (spread_bits(bo) << 1);
-    if (lane == 0) a.mask[base >> 6] = m;
-    kept += __popcll(m);
   }
   if (lane == 0) wcount[warp] = kept;
   __syncthreads();
@@ -200,6 +230,7 @@ bool launch_sample(const Plan& pl, const float* lam, const double* p, const l1s_
   m.status = reinterpret_cast<const StatusBlock*>(ws + pl.off_status);
   m.mask = reinterpret_cast<uint64_t*>(ws + pl.off_mask);
   m.counts = reinterpret_cast<int64_t*>(ws + pl.off_counts);
+  m.lam_pairs = (reinterpret_cast<uintptr_t>(lam) % 8 == 0) ? 1 : 0;
   sample_mark_kernel<<<pl.smp_ctas, pl.smp_threads, 0, st>>>(m);
   if (!cuda_ok(cudaGetLastError(), "launch sample_mark")) return false;
   StatusBlock* sb = reinterpret_cast<StatusBlock*>(ws + pl.off_status);

@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_HERE, "lib", "libl1fct.so")
 
 L1S_OK = 0
 ERRORS = {1: "INVALID_ARG", 2: "WORKSPACE", 3: "CUDA", 4: "RANK_DEFICIENT", 5: "NONFINITE",
-          6: "ZERO_MASS", 7: "CAPACITY", 8: "NOT_CONVERGED"}
+          6: "ZERO_MASS", 7: "CAPACITY", 8: "NOT_CONVERGED", 9: "TIMEOUT"}
 F32, BF16 = 0, 1
 
 
