@@ -135,6 +135,23 @@ L1S_API int l1_lambda(const void* A_dev, int64_t lda, l1s_dtype dtype, const flo
               float* lambda_dev, double* lambda_sum_dev, void* ws, size_t ws_bytes,
               void* stream);
 
+/* l1_lambda without a workspace, for callers that cannot allocate device
+ * memory (the paper has no counterpart: this is a property of the library).
+ * cudaMalloc may synchronise the whole device, which a latency-bound loop cannot
+ * afford once it runs, and some host programs give all device memory to their own
+ * pool at start-up and let plug-in code allocate none.  Arguments and results are
+ * those of l1_lambda minus ws/ws_bytes.  Scratch (M in FP32, the per-block Σλ
+ * partials, a status block) lives in one library-owned 40 KiB device array per GPU,
+ * held until the process exits; 4·q·r2 bytes plus 8 bytes per partial (8 per SM)
+ * must fit in it (d ≤ 64 with r2 ≤ 64 does), else L1S_ERR_INVALID_ARG.  The first
+ * call on a device looks up that array's address (cudaGetSymbolAddress); make it
+ * before any stream capture.  Every call shares the array and clears what must
+ * start at zero; calls that overlap on the GPU race on it.  Allocates nothing: no
+ * cudaMalloc, cudaFree or allocating library call. */
+L1S_API int l1_lambda_noalloc(const void* A_dev, int64_t lda, l1s_dtype dtype, const float* b_dev,
+                              int64_t n, int32_t d, const double* M_dev, const l1s_params* params,
+                              float* lambda_dev, double* lambda_sum_dev, void* stream);
+
 /* Phases 2-3 (Figure 2, steps 4-7): λ as in l1_lambda, Σλ, τ = m_s/Σλ in FP64,
  * p̂_i = min(1, τ·λ_i) in FP64, row i kept iff u_i < p̂_i with its 53-bit
  * uniform u_i (exact FP64 comparison).  Kept rows are written in ascending

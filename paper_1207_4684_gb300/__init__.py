@@ -16,6 +16,7 @@ from .l1fct import (  # noqa: F401
     l1_coreset_host,
     l1_condition,
     l1_lambda,
+    l1_lambda_noalloc,
     l1_objective,
     l1_regress,
     l1_sample,

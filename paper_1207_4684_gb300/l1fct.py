@@ -70,6 +70,7 @@ _SIGS = {
     "l1_regress": (C.c_int, [_P, _I64, C.c_int, _P, _I64, _I32, _PP, _I32, _P, _P, _P, _P, _SZ, _P]),
     "l1s_debug_variates": (C.c_int, [_PP, _I64, _I64, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "l1s_debug_pi2": (C.c_int, [_PP, _I32, _P, _P]),
+    "l1_lambda_noalloc": (C.c_int, [_P, _I64, C.c_int, _P, _I64, _I32, _P, _PP, _P, _P, _P]),
 }
 EXPORTS = tuple(_SIGS)
 
@@ -242,3 +243,11 @@ def l1s_debug_pi2(params: Params, q: int, device="cuda", stream=None) -> torch.T
     out = torch.empty((q, params.r2), dtype=torch.float64, device=device)
     _check(load().l1s_debug_pi2(C.byref(params), q, _ptr(out), _stream(stream)), "l1s_debug_pi2")
     return out
+
+
+def l1_lambda_noalloc(A, b, M, params: Params, lam, lam_sum, stream=None) -> None:
+    """l1_lambda without a workspace: the library's own per-device scratch array serves
+    callers that cannot allocate device memory (see include/l1fct.h)."""
+    n, d, lda, dt = _matrix(A)
+    _check(load().l1_lambda_noalloc(_ptr(A, False), lda, dt, _ptr(b), n, d, _ptr(M), C.byref(params), _ptr(lam),
+                                    _ptr(lam_sum), _stream(stream)), "l1_lambda_noalloc")
