@@ -30,6 +30,27 @@ def lambda_estimates(X: np.ndarray, M: np.ndarray, chunk: int = 1 << 20) -> np.n
     return out
 
 
+def bf16_round(values: np.ndarray) -> np.ndarray:
+    """Round to FP32 (nearest even), then to bfloat16 (nearest even, 8 significant bits), in FP64.
+
+    This is the mixed-precision form of M: the tensor-core product uses M's first d rows
+    rounded this way, the b column's row stays FP32.
+    """
+    f = np.ascontiguousarray(np.asarray(values, dtype=np.float64).astype(np.float32))
+    u = f.view(np.uint32).astype(np.uint64)
+    r = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
+    return r.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def mixed_precision_m(M: np.ndarray) -> np.ndarray:
+    """M as the mixed-precision λ uses it: rows 0..d−1 in BF16, row d (the b column) in FP32."""
+    M = np.asarray(M, dtype=np.float64)
+    out = np.empty_like(M)
+    out[:-1] = bf16_round(M[:-1])
+    out[-1] = M[-1].astype(np.float32).astype(np.float64)
+    return out
+
+
 def lambda_term_scale(X: np.ndarray, M: np.ndarray, chunk: int = 1 << 20) -> np.ndarray:
     """Per row, max_j Σ_k |X_ik|·|M_kj|: the magnitude that bounds the rounding of Λ_i·."""
     X = np.asarray(X)

@@ -16,11 +16,16 @@ namespace l1s {
 const void* fct_kernel(int log2s, l1s_dtype dt, bool staged);
 size_t fct_smem_bytes(int s, int d, l1s_dtype dt, int r1, int width, bool staged);
 int fct_threads_for(int log2s, int width);
+bool fct_t16_applies(int log2s, int d);
+const void* fct_t16_kernel(int log2s, l1s_dtype dt);
+int fct_t16_threads();
+size_t fct_t16_smem_bytes(int s, int d, l1s_dtype dt, int r1);
 bool launch_fct(const Plan& pl, const void* A, int64_t lda, l1s_dtype dt, const float* b,
                 const l1s_params* p, float* pix, unsigned char* ws, cudaStream_t st);
 bool launch_condition(const Plan& pl, const float* pix, const l1s_params* p, double* R_user,
                       double* M_user, unsigned char* ws, cudaStream_t st);
 bool launch_pi2(const l1s_params* p, int q, double* out, cudaStream_t st);
+size_t cond2_scratch_bytes(int r1, int q, int sms);
 int lambda_threads();
 bool launch_lambda(const Plan& pl, const void* A, int64_t lda, l1s_dtype dt, const float* b,
                    const float* m32, const l1s_params* p, float* lam, double* user_sum,
@@ -134,12 +139,17 @@ bool make_plan(const l1s_params* p, int64_t n, int d, l1s_dtype dt, bool host_st
       }
     }
   }
+  P.fct_t16 = fct_t16_applies(P.log2s, P.d) && fct_t16_smem_bytes(P.s, P.d, dt, P.r1) <= budget1;
+  if (P.fct_t16) {
+    width = P.q;
+    staged = true;
+  }
   P.fct_staged = staged ? 1 : 0;
   P.fct_slices = (P.q + width - 1) / width;
   P.fct_width = width;
-  P.fct_smem = fct_smem_bytes(P.s, P.d, dt, P.r1, width, staged);
-  P.fct_threads = fct_threads_for(P.log2s, width);
-  const void* fn = fct_kernel(P.log2s, dt, staged);
+  P.fct_smem = P.fct_t16 ? fct_t16_smem_bytes(P.s, P.d, dt, P.r1) : fct_smem_bytes(P.s, P.d, dt, P.r1, width, staged);
+  P.fct_threads = P.fct_t16 ? fct_t16_threads() : fct_threads_for(P.log2s, width);
+  const void* fn = P.fct_t16 ? fct_t16_kernel(P.log2s, dt) : fct_kernel(P.log2s, dt, staged);
   if (!cuda_ok(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     static_cast<int>(P.fct_smem)),
                "cudaFuncSetAttribute(fct_embed)"))
@@ -183,7 +193,7 @@ bool make_plan(const l1s_params* p, int64_t n, int d, l1s_dtype dt, bool host_st
   P.off_objp = take(sizeof(float) * static_cast<size_t>(cap));  // IRLS residual scratch
   P.off_partials = take(sizeof(float) * static_cast<size_t>(P.fct_slices) * P.fct_ctas * P.r1 * P.fct_width);
   P.off_pix = take(sizeof(float) * P.r1 * P.q);
-  P.off_qr = take(sizeof(double) * P.r1 * P.q);
+  P.off_qr = take(std::max(sizeof(double) * P.r1 * P.q, cond2_scratch_bytes(P.r1, P.q, di.sms)));
   P.off_r = take(sizeof(double) * P.q * P.q);
   P.off_m64 = take(sizeof(double) * P.q * P.r2);
   P.off_m32 = take(sizeof(float) * P.q * P.r2);

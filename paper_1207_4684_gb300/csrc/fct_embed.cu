@@ -292,6 +292,287 @@ __global__ void __launch_bounds__(kFctMaxThreads) fct_embed_kernel(const FctArgs
   for (int i = threadIdx.x; i < a.r1 * W; i += blockDim.x) out[i] = part[i];
 }
 
+// ----------------------------------------------------------------- d ≤ 16, 32 ≤ s ≤ 512
+// A dedicated kernel for narrow X, where the generic kernel is bound by shared-memory
+// bank conflicts and per-element draw loads.  It is warp-specialised and software
+// pipelined over the s-row blocks of a thread block:
+//  * 4 producer warps compute the draws of block i into one of two draw buffers while
+//    the consumers work on block i−1, and one producer thread issues the TMA copy of
+//    block i into one of two stages;
+//  * 8 A warps: a half-warp owns one 16-column tile of one row group, and the two
+//    half-warps of a warp always hold rows of opposite parity, so each shared-memory
+//    access of a warp covers both bank halves once.  Pass 1 runs the butterflies over
+//    row bits 1-4 (and scatters the identity half), pass 2 over bit 0 and bits 5 and up
+//    (the stages of H_s commute).  In pass 2 the odd half-warp reads its rows in the
+//    order j ^ 1, which negates its outputs at odd positions (H_s applied to a permuted
+//    vector); the sign is undone in the scatter.  P is kept as two copies, one per
+//    half-warp, at bank offsets 0 and 16, so a warp's hashed scatter never conflicts;
+//    the copies are added when the partial is written out;
+//  * 1 b warp: 32 rows per register slot; stages over row bits ≥ 5 in registers, over
+//    bits 0-4 by shuffles; its own scatter array.
+// Hand-offs use mbarriers (bounded waits; a timeout raises the TIMEOUT status bit and
+// every role stops).  Draws of a row are packed as {32·h_I, 4·c_I·σ, sign mask, h_I}
+// and {32·h_H, 4·c_H/√s}.
+constexpr int kWsA = 8, kWsB = 1, kWsP = 4;
+constexpr int kT16Threads = 32 * (kWsA + kWsB + kWsP);   // 416
+
+struct __align__(16) T16Meta {
+  int offI;           // 32·h_I: first word of row h_I of P
+  float wIs;          // 4·c_I·σ (the identity term of row i is wIs·x_i)
+  uint32_t smask;     // 0x80000000 when σ = −1 (z = x with its sign bit flipped)
+  int hI;             // h_I (the b column's own array)
+};
+struct __align__(8) T16MetaH {
+  int offH;           // 32·h_H
+  float wH;           // 4·c_H/√s
+};
+
+template <int LOG2S, typename TA>
+__global__ void __launch_bounds__(kT16Threads) fct_embed_t16_kernel(const FctArgs a) {
+  constexpr int S = 1 << LOG2S;
+  constexpr int K2 = LOG2S - 4;          // pass 2: row bit 0 and bits [5, LOG2S)
+  constexpr int G2 = 1 << K2;
+  constexpr int KB = S / 32;             // b column: values per lane
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  // mbarriers: stage_full (TMA or producer), stage_free (A + b warps done with pass 1),
+  // meta_full (producers), meta_free (A + b warps done with the block)
+  __shared__ uint64_t stage_full[2], stage_free[2], meta_full[2], meta_free[2];
+  __shared__ volatile int s_abort;
+  const int r1 = a.r1;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int d = a.d;
+  unsigned char* stages = smem_raw;
+  float* P = reinterpret_cast<float*>(stages + 2 * static_cast<size_t>(a.stage_bytes));        // [r1][32]
+  float* Pb = P + r1 * 32;                                                                         // [r1]
+  float* tile = Pb + ((r1 + 3) & ~3);                                                              // [S][16]
+  T16Meta* mI = reinterpret_cast<T16Meta*>(tile + S * 16);                                         // [2][S]
+  T16MetaH* mH = reinterpret_cast<T16MetaH*>(mI + 2 * S);                                          // [2][S]
+
+  for (int i = tid; i < r1 * 33; i += blockDim.x) P[i] = 0.f;   // P and Pb
+  if (tid == 0) {
+    s_abort = 0;
+    for (int k = 0; k < 2; ++k) {
+      mbar_init(&stage_full[k], 1);
+      mbar_init(&stage_free[k], kWsA + kWsB);
+      mbar_init(&meta_full[k], 1);
+      mbar_init(&meta_free[k], kWsA + kWsB);
+    }
+    fence_mbar_init();
+  }
+  __syncthreads();
+  const bool tma = a.tma != 0;
+  const uint32_t b_off = (a.stage_a_bytes + 15) & ~15u;
+
+  if (warp >= kWsA + kWsB) {
+    // ---------------- producers: draws of block i and its stage
+    const int pt = tid - 32 * (kWsA + kWsB);       // 0..127
+    int64_t i = 0;
+    for (int64_t blk = blockIdx.x; blk < a.nblocks; blk += gridDim.x, ++i) {
+      const int buf = static_cast<int>(i & 1);
+      const uint32_t use = static_cast<uint32_t>((i >> 1) & 1);
+      unsigned char* stage = stages + static_cast<size_t>(buf) * a.stage_bytes;
+      const int64_t row0 = blk * S;
+      const bool by_tma = tma && blk < a.full_blocks;
+      // the stage and the draw buffer are free once block i−2 is done with them
+      if (pt == 0) {
+        const bool ok = mbar_wait_bounded(&stage_free[buf], use ^ 1u, kWaitCycles) &&
+                        mbar_wait_bounded(&meta_free[buf], use ^ 1u, kWaitCycles);
+        if (!ok) s_abort = 1;
+        else if (by_tma) issue_stage_tma<TA>(a, blk, S, stage, &stage_full[buf]);
+      }
+      named_barrier(1, 32 * kWsP);
+      if (s_abort) break;                           // uniform: read after the barrier
+      if (!by_tma) {
+        // plain loads into the stage (ragged last block or unaligned input)
+        TA* ra = reinterpret_cast<TA*>(stage);
+        float* rb = reinterpret_cast<float*>(stage + b_off);
+        const TA* A = static_cast<const TA*>(a.A);
+        for (int e = pt; e < S * d; e += 32 * kWsP) {
+          const int r = e / d, c = e - r * d;
+          ra[e] = (row0 + r < a.n) ? A[(row0 + r) * a.lda + c] : TA(0);
+        }
+        for (int r = pt; r < S; r += 32 * kWsP) rb[r] = (row0 + r < a.n) ? a.b[row0 + r] : 0.f;
+      }
+      T16Meta* mi = mI + buf * S;
+      T16MetaH* mh = mH + buf * S;
+      for (int r = pt; r < S; r += 32 * kWsP) {
+        const uint64_t grow = static_cast<uint64_t>(a.row_offset + row0 + r);
+        const uint4 o = draw_row(a.key, grow, a.problem, kStreamFct);
+        const bool neg = a.sign_flip && (o.w & 1u);
+        T16Meta m;
+        m.hI = bucket_of(o.z, r1);
+        m.offI = 32 * m.hI;
+        const float wI = 4.f * cauchy_f32(o.w >> 8);
+        m.wIs = neg ? -wI : wI;
+        m.smask = neg ? 0x80000000u : 0u;
+        mi[r] = m;
+        T16MetaH h;
+        h.offH = 32 * bucket_of(o.x, r1);
+        h.wH = 4.f * cauchy_f32(o.y >> 8) * a.inv_sqrt_s;
+        mh[r] = h;
+      }
+      named_barrier(1, 32 * kWsP);                  // all draws (and a plain stage) written
+      if (pt == 0) {
+        if (!by_tma) mbar_arrive(&stage_full[buf]);
+        mbar_arrive(&meta_full[buf]);
+      }
+    }
+  } else {
+    // ---------------- consumers: 8 A warps and the b warp
+    const bool is_b = warp == kWsA;
+    int64_t i = 0;
+    for (int64_t blk = blockIdx.x; blk < a.nblocks; blk += gridDim.x, ++i) {
+      const int buf = static_cast<int>(i & 1);
+      const uint32_t use = static_cast<uint32_t>((i >> 1) & 1);
+      bool ok = true;
+      if (lane == 0)
+        ok = mbar_wait_bounded(&meta_full[buf], use, kWaitCycles) && mbar_wait_bounded(&stage_full[buf], use, kWaitCycles);
+      ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+      // all consumer warps take the same decision, so none is left waiting at a barrier
+      if (named_barrier_any(3, 32 * (kWsA + kWsB), !ok || s_abort)) {
+        s_abort = 1;
+        break;
+      }
+      const unsigned char* stage = stages + static_cast<size_t>(buf) * a.stage_bytes;
+      const TA* rawA = reinterpret_cast<const TA*>(stage);
+      const float* rawB = reinterpret_cast<const float*>(stage + b_off);
+      const T16Meta* mi = mI + buf * S;
+      const T16MetaH* mh = mH + buf * S;
+      if (!is_b) {
+        // ---- pass 1 on A: row bits 1-4 in registers, identity scatter on the way in
+        for (int task = tid; task < S; task += 32 * kWsA) {
+          const int c = task & 15;
+          const int g = task >> 4;
+          const int hb = g & 1;
+          const int base = (g & 1) | ((g >> 1) << 5);
+          const bool live = c < d;
+          float* Pl = P + hb * 16 + c;
+          float v[16];
+#pragma unroll
+          for (int j = 0; j < 16; ++j) v[j] = live ? widen<TA>(rawA[(base | (j << 1)) * d + c]) : 0.f;
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int4 m = *reinterpret_cast<const int4*>(&mi[base | (j << 1)]);
+            const float x = v[j];
+            v[j] = __uint_as_float(__float_as_uint(x) ^ static_cast<uint32_t>(m.z));
+            if (live) atomicAdd(Pl + m.x, __int_as_float(m.y) * x);
+          }
+#pragma unroll
+          for (int t = 0; t < 4; ++t) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              if ((j & (1 << t)) == 0) {
+                const float lo = v[j], hi = v[j | (1 << t)];
+                v[j] = lo + hi;
+                v[j | (1 << t)] = lo - hi;
+              }
+            }
+          }
+#pragma unroll
+          for (int j = 0; j < 16; ++j) tile[(base | (j << 1)) * 16 + c] = v[j];
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&stage_free[buf]);
+        named_barrier(2, 32 * kWsA);                   // tile complete
+        // ---- pass 2 on A: row bit 0 and bits [5, LOG2S), then the Hadamard scatter
+        {
+          const int c = tid & 15;
+          const int g2 = tid >> 4;
+          const int hb = g2 & 1;
+          float v[G2];
+#pragma unroll
+          for (int j = 0; j < G2; ++j) {
+            const int jj = j ^ hb;
+            v[j] = tile[((g2 << 1) | (jj & 1) | ((jj >> 1) << 5)) * 16 + c];
+          }
+#pragma unroll
+          for (int t = 0; t < K2; ++t) {
+#pragma unroll
+            for (int j = 0; j < G2; ++j) {
+              if ((j & (1 << t)) == 0) {
+                const float lo = v[j], hi = v[j | (1 << t)];
+                v[j] = lo + hi;
+                v[j | (1 << t)] = lo - hi;
+              }
+            }
+          }
+          if (c < d) {
+            float* Pl = P + hb * 16 + c;
+            const float odd_sign = hb ? -1.f : 1.f;
+#pragma unroll
+            for (int k = 0; k < G2; ++k) {
+              const int2 h = *reinterpret_cast<const int2*>(&mh[(g2 << 1) | (k & 1) | ((k >> 1) << 5)]);
+              const float val = (k & 1) ? odd_sign * v[k] : v[k];
+              atomicAdd(Pl + h.x, __int_as_float(h.y) * val);
+            }
+          }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&meta_free[buf]);
+        named_barrier(2, 32 * kWsA);                   // tile free for the next block
+      } else {
+        // ---- the b column: one warp, all stages, both scatters
+        float v[KB];
+#pragma unroll
+        for (int k = 0; k < KB; ++k) {
+          const int row = lane + 32 * k;
+          const int4 m = *reinterpret_cast<const int4*>(&mi[row]);
+          const float x = -rawB[row];
+          v[k] = __uint_as_float(__float_as_uint(x) ^ static_cast<uint32_t>(m.z));
+          atomicAdd(&Pb[m.w], __int_as_float(m.y) * x);
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&stage_free[buf]);
+#pragma unroll
+        for (int t = 0; (1 << t) < KB; ++t) {
+#pragma unroll
+          for (int k = 0; k < KB; ++k) {
+            if ((k & (1 << t)) == 0) {
+              const float lo = v[k], hi = v[k | (1 << t)];
+              v[k] = lo + hi;
+              v[k | (1 << t)] = lo - hi;
+            }
+          }
+        }
+#pragma unroll
+        for (int t = 0; t < 5; ++t) {
+          const bool upper = (lane >> t) & 1;
+#pragma unroll
+          for (int k = 0; k < KB; ++k) {
+            const float o = __shfl_xor_sync(0xffffffffu, v[k], 1 << t);
+            v[k] = upper ? (o - v[k]) : (v[k] + o);
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < KB; ++k) {
+          const int2 h = *reinterpret_cast<const int2*>(&mh[lane + 32 * k]);
+          atomicAdd(&Pb[h.x >> 5], __int_as_float(h.y) * v[k]);
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&meta_free[buf]);
+      }
+    }
+  }
+  __syncthreads();
+  if (s_abort) {
+    // Let copies still in flight land (a bounded pause) before shared memory is released.
+    if (tid == 0) {
+      raise_flag(a.flags, L1S_ERR_TIMEOUT);
+      const long long t0 = clock64();
+      while (clock64() - t0 < 20000000LL) {
+      }
+    }
+    __syncthreads();
+    return;
+  }
+  const int q = d + 1;
+  float* out = a.partials + static_cast<size_t>(blockIdx.x) * r1 * q;
+  for (int i = tid; i < r1 * q; i += blockDim.x) {
+    const int h = i / q, c = i - h * q;
+    out[i] = c < d ? P[h * 32 + c] + P[h * 32 + 16 + c] : Pb[h];
+  }
+}
+
 // Fixed-order sum of the per-block partials: PiX[r][c0+c] = Σ_blocks partial[r][c].
 // Block = 32 warps; warp w adds partials w, w+32, …; warp 0 then adds the 32
 // warp sums in order, so the result does not depend on scheduling.
@@ -359,6 +640,27 @@ const void* fct_kernel(int log2s, l1s_dtype dt, bool staged) {
   return staged ? fct_kernel_for<float, true>(log2s) : fct_kernel_for<float, false>(log2s);
 }
 
+template <typename TA>
+static const void* t16_kernel_for(int log2s) {
+  switch (log2s) {
+    case 5: return reinterpret_cast<const void*>(&fct_embed_t16_kernel<5, TA>);
+    case 6: return reinterpret_cast<const void*>(&fct_embed_t16_kernel<6, TA>);
+    case 7: return reinterpret_cast<const void*>(&fct_embed_t16_kernel<7, TA>);
+    case 8: return reinterpret_cast<const void*>(&fct_embed_t16_kernel<8, TA>);
+    case 9: return reinterpret_cast<const void*>(&fct_embed_t16_kernel<9, TA>);
+    default: return nullptr;
+  }
+}
+
+// The narrow-X kernel applies for d ≤ 16 and 32 ≤ s ≤ 512.
+bool fct_t16_applies(int log2s, int d) { return d <= 16 && log2s >= 5 && log2s <= 9; }
+
+const void* fct_t16_kernel(int log2s, l1s_dtype dt) {
+  return dt == L1S_BF16 ? t16_kernel_for<uint16_t>(log2s) : t16_kernel_for<float>(log2s);
+}
+
+int fct_t16_threads() { return kT16Threads; }
+
 uint32_t fct_stage_bytes(int s, int d, l1s_dtype dt) {
   const uint32_t esz = dt == L1S_BF16 ? 2u : 4u;
   const uint32_t a_bytes = static_cast<uint32_t>(s) * d * esz;
@@ -369,6 +671,12 @@ size_t fct_smem_bytes(int s, int d, l1s_dtype dt, int r1, int width, bool staged
   return (staged ? static_cast<size_t>(kFctStages) * fct_stage_bytes(s, d, dt) : 0) +
          static_cast<size_t>(r1) * width * 4 + static_cast<size_t>(s) * width * 4 +
          static_cast<size_t>(s) * (sizeof(RowMeta) + 4);
+}
+
+size_t fct_t16_smem_bytes(int s, int d, l1s_dtype dt, int r1) {
+  return 2 * static_cast<size_t>(fct_stage_bytes(s, d, dt)) + static_cast<size_t>(r1) * 32 * 4 +
+         static_cast<size_t>((r1 + 3) & ~3) * 4 + static_cast<size_t>(s) * 16 * 4 +
+         2 * static_cast<size_t>(s) * (sizeof(T16Meta) + sizeof(T16MetaH));
 }
 
 // TMA staging needs A's rows back to back (lda = d), 16-byte aligned bases and stage parts.
@@ -414,8 +722,11 @@ bool launch_fct(const Plan& pl, const void* A, int64_t lda, l1s_dtype dt, const 
   a.flags = reinterpret_cast<uint32_t*>(ws + pl.off_status);
   // A layout that cannot be staged falls back to direct loads with the same grid; the
   // direct variant needs less shared memory than the staged one it was planned for.
-  const void* fn = fct_kernel(pl.log2s, dt, staged);
-  const size_t smem = fct_smem_bytes(pl.s, pl.d, dt, pl.r1, pl.fct_width, staged);
+  // The narrow-X kernel stages every block (by TMA when it can, else with plain loads).
+  const bool t16 = pl.fct_t16 != 0;
+  if (t16) a.tma = fct_can_stage(pl.s, pl.d, dt, lda, A, b) ? 1 : 0;
+  const void* fn = t16 ? fct_t16_kernel(pl.log2s, dt) : fct_kernel(pl.log2s, dt, staged);
+  const size_t smem = t16 ? fct_t16_smem_bytes(pl.s, pl.d, dt, pl.r1) : fct_smem_bytes(pl.s, pl.d, dt, pl.r1, pl.fct_width, staged);
   if (!cuda_ok(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)),
                "cudaFuncSetAttribute(fct_embed)"))
     return false;

@@ -39,7 +39,7 @@ struct StatusBlock {
   double irls_obj;       // IRLS objective of the current iterate
   double irls_eta;       // IRLS smoothing floor
   int32_t irls_iters;
-  int32_t pad1;
+  uint32_t cond_ticket;  // blocks of the conditioning pass that have finished
 };
 
 __device__ __forceinline__ void raise_flag(uint32_t* flags, int code) {
@@ -87,13 +87,15 @@ __device__ __forceinline__ int bucket_of(uint32_t word, uint32_t r) {
 // Standard Cauchy from the 24-bit integer k: tan(π(u − ½)) at u = (k + ½)/2^24,
 // evaluated through the reflection w = ½ − |u − ½| = j·2^-25 (j odd, exact in
 // FP32) as ±cos(πw)/sin(πw), which keeps full relative accuracy near the poles.
+// The quotient uses the fast division (≤ 2 ulp for denominators in [2^-126, 2^126];
+// sin(πw) ≥ sin(π·2^-25) here), so the variate is within a few ulp of cot(πw).
 __device__ __forceinline__ float cauchy_f32(uint32_t k) {
   const int m = 2 * static_cast<int>(k) + 1 - (1 << 24);
   const int j = (1 << 24) - abs(m);
   const float w = static_cast<float>(j) * 0x1p-25f;
   float sn, cs;
   sincospif(w, &sn, &cs);
-  const float r = cs / sn;
+  const float r = __fdividef(cs, sn);
   return m > 0 ? r : -r;
 }
 
@@ -168,6 +170,26 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
 
 constexpr long long kWaitCycles = 4000000000LL;  // about two seconds at 2 GHz
 
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Named barrier `id` over `count` threads (a multiple of 32).
+__device__ __forceinline__ void named_barrier(int id, int count) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+
+// Named barrier that also ORs a predicate over the participating threads.
+__device__ __forceinline__ bool named_barrier_any(int id, int count, bool pred) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\tbar.red.or.pred q, %2, %3, p;\n\tselp.u32 %0, 1, 0, q;\n\t}"
+      : "=r"(r)
+      : "r"(pred ? 1u : 0u), "r"(id), "r"(count)
+      : "memory");
+  return r != 0;
+}
+
 // ----------------------------------------------------------------- element loads
 template <typename T>
 __device__ __forceinline__ float load_elem(const T* p);
@@ -205,6 +227,7 @@ struct Plan {
   int fct_threads;
   int fct_slices, fct_width;  // column slices of Π1X handled per thread block
   int fct_staged;           // 1: tiles of X arrive in shared memory by TMA bulk copies
+  int fct_t16;              // 1: the narrow-X kernel (d ≤ 16) runs phase 1
   int fct_ctas;             // thread blocks per slice
   size_t fct_smem;
   int lam_ctas, lam_threads;

@@ -11,6 +11,7 @@
 // launch order.  X crosses HBM once.
 #include <float.h>
 
+#include <algorithm>
 #include <utility>
 
 #include "l1s_common.cuh"
@@ -141,7 +142,23 @@ __device__ __forceinline__ void load_row(const TA* __restrict__ p, float (&x)[D 
   }
 }
 
-// Specialised for q = D + 1 and r2 = R2 known at compile time.
+template <int Q, int R2>
+__device__ __forceinline__ float lambda_of_row(const float (&x)[Q]) {
+  float acc[R2];
+#pragma unroll
+  for (int j = 0; j < R2; ++j) acc[j] = x[0] * c_M[j];
+#pragma unroll
+  for (int k = 1; k < Q; ++k) {
+#pragma unroll
+    for (int j = 0; j < R2; ++j) acc[j] = fmaf(x[k], c_M[k * R2 + j], acc[j]);
+  }
+#pragma unroll
+  for (int j = 0; j < R2; ++j) acc[j] = fabsf(acc[j]);
+  return lower_median<R2>(acc);
+}
+
+// Specialised for q = D + 1 and r2 = R2 known at compile time.  The loads of a thread's
+// next row are issued before the current row is computed (software pipelining).
 template <int D, int R2, typename TA, bool VEC>
 __global__ void __launch_bounds__(kLamThreads) lambda_kernel(const TA* __restrict__ A, int64_t lda,
                                                              const float* __restrict__ b, int64_t n,
@@ -150,21 +167,22 @@ __global__ void __launch_bounds__(kLamThreads) lambda_kernel(const TA* __restric
   constexpr int Q = D + 1;
   float s = 0.f, c = 0.f;
   const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
-  for (int64_t row = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; row < n; row += stride) {
+  int64_t row = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  float nx[Q];
+  if (row < n) {
+    load_row<D, TA, VEC>(A + row * lda, nx);
+    nx[D] = -__ldg(b + row);
+  }
+  for (; row < n; row += stride) {
     float x[Q];
-    load_row<D, TA, VEC>(A + row * lda, x);
-    x[D] = -__ldg(b + row);
-    float acc[R2];
 #pragma unroll
-    for (int j = 0; j < R2; ++j) acc[j] = x[0] * c_M[j];
-#pragma unroll
-    for (int k = 1; k < Q; ++k) {
-#pragma unroll
-      for (int j = 0; j < R2; ++j) acc[j] = fmaf(x[k], c_M[k * R2 + j], acc[j]);
+    for (int k = 0; k < Q; ++k) x[k] = nx[k];
+    const int64_t nrow = row + stride;
+    if (nrow < n) {
+      load_row<D, TA, VEC>(A + nrow * lda, nx);
+      nx[D] = -__ldg(b + nrow);
     }
-#pragma unroll
-    for (int j = 0; j < R2; ++j) acc[j] = fabsf(acc[j]);
-    const float med = lower_median<R2>(acc);
+    const float med = lambda_of_row<Q, R2>(x);
     lam[row] = med;
     two_sum_add(s, c, med);
   }
@@ -294,7 +312,12 @@ static bool launch_lambda_t(const Plan& pl, const TA* A, int64_t lda, const floa
 
 int lambda_threads() { return kLamThreads; }
 
-// M (FP32, q × r2 in the workspace) → constant bank, then λ and Σλ.
+bool lambda_tc_applies(int d, int r2, int64_t lda, const void* A, l1s_dtype dt);
+bool launch_lambda_tc(int64_t n, const void* A, const float* b, const float* m32, uint16_t* mt_bf16, float* lam,
+                      double* block_sums, int blocks, uint32_t* flags, cudaStream_t st);
+
+// M (FP32, q × r2 in the workspace) → constant bank, then λ and Σλ.  BF16 A with d = r2 = 32
+// runs on the tensor cores (M_A rounded to BF16; its transpose goes to the Π2 region, 2 KB).
 bool launch_lambda(const Plan& pl, const void* A, int64_t lda, l1s_dtype dt, const float* b,
                    const float* m32, const l1s_params* p, float* lam, double* user_sum,
                    unsigned char* ws, cudaStream_t st) {
@@ -303,11 +326,19 @@ bool launch_lambda(const Plan& pl, const void* A, int64_t lda, l1s_dtype dt, con
                "copy M to constant memory"))
     return false;
   double* sums = reinterpret_cast<double*>(ws + pl.off_lamsum);
-  bool ok = dt == L1S_BF16
-                ? launch_lambda_t<uint16_t>(pl, static_cast<const uint16_t*>(A), lda, b, lam, sums, st)
-                : launch_lambda_t<float>(pl, static_cast<const float*>(A), lda, b, lam, sums, st);
+  int blocks = pl.lam_ctas;
+  bool ok;
+  if (lambda_tc_applies(pl.d, pl.r2, lda, A, dt)) {
+    blocks = std::min(pl.lam_ctas, device_info().sms);
+    ok = launch_lambda_tc(pl.n, A, b, m32, reinterpret_cast<uint16_t*>(ws + pl.off_pi2), lam, sums, blocks,
+                          reinterpret_cast<uint32_t*>(ws + pl.off_status), st);
+  } else {
+    ok = dt == L1S_BF16
+             ? launch_lambda_t<uint16_t>(pl, static_cast<const uint16_t*>(A), lda, b, lam, sums, st)
+             : launch_lambda_t<float>(pl, static_cast<const float*>(A), lda, b, lam, sums, st);
+  }
   if (!ok) return false;
-  lambda_finalize_kernel<<<1, 256, 0, st>>>(sums, pl.lam_ctas, p->coreset_size,
+  lambda_finalize_kernel<<<1, 256, 0, st>>>(sums, blocks, p->coreset_size,
                                            reinterpret_cast<StatusBlock*>(ws + pl.off_status), user_sum);
   return cuda_ok(cudaGetLastError(), "launch lambda_finalize");
 }

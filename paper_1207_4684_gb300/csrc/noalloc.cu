@@ -60,10 +60,11 @@ extern "C" int l1_lambda_noalloc(const void* A, int64_t lda, l1s_dtype dtype, co
   Plan pl;
   if (!make_plan(params, n, d, dtype, false, &pl)) return L1S_ERR_INVALID_ARG;
   if (!A || !b || !M || !lambda || lda < d) return set_error("A, b, M, lambda must be given and lda >= d"), L1S_ERR_INVALID_ARG;
-  // Scratch layout: status block | Σλ block partials | M in FP32.
+  // Scratch layout: status block | Σλ block partials | M in FP32 | M_Aᵀ in BF16 (tensor-core form).
   const size_t off_sums = 256;
   const size_t off_m32 = align_up(off_sums + sizeof(double) * static_cast<size_t>(pl.lam_ctas));
-  const size_t need = off_m32 + sizeof(float) * static_cast<size_t>(pl.q) * pl.r2;
+  const size_t off_mt = align_up(off_m32 + sizeof(float) * static_cast<size_t>(pl.q) * pl.r2);
+  const size_t need = off_mt + 2048;
   if (need > kScratchBytes)
     return set_error("l1_lambda_noalloc: q·r2 = %d and %d partial sums need %zu bytes, more than its %zu-byte scratch",
                      pl.q * pl.r2, pl.lam_ctas, need, kScratchBytes),
@@ -75,6 +76,7 @@ extern "C" int l1_lambda_noalloc(const void* A, int64_t lda, l1s_dtype dtype, co
   local.off_status = 0;
   local.off_lamsum = off_sums;
   local.off_m32 = off_m32;
+  local.off_pi2 = off_mt;
   float* m32 = reinterpret_cast<float*>(scratch + off_m32);
   if (!cuda_ok(cudaMemsetAsync(scratch, 0, sizeof(StatusBlock), st), "clear no-alloc status")) return L1S_ERR_CUDA;
   if (!launch_m_to_f32(M, pl.q * pl.r2, m32, st)) return L1S_ERR_CUDA;

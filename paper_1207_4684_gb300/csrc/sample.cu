@@ -90,28 +90,33 @@ __global__ void __launch_bounds__(kSmpThreads) sample_mark_kernel(const MarkArgs
         if (r0 + 1 < stop) l1[u] = a.lam[r0 + 1];
       }
     }
+    // The kMarkUnroll Philox calls are independent: compute them together (ILP), then decide.
+    uint32_t w0a[kMarkUnroll], w0b[kMarkUnroll], w1a[kMarkUnroll], w1b[kMarkUnroll];
+#pragma unroll
+    for (int u = 0; u < kMarkUnroll; ++u) {
+      const int64_t r0 = base0 + u * stride + 2 * lane;
+      const uint64_t g0 = static_cast<uint64_t>(a.row_offset + r0);
+      if (!odd_offset) {
+        const uint4 o = draw_row(a.key, g0 >> 1, a.problem, kStreamSample);
+        w0a[u] = o.x; w0b[u] = o.y; w1a[u] = o.z; w1b[u] = o.w;
+      } else {
+        const uint4 o0 = draw_row(a.key, g0 >> 1, a.problem, kStreamSample);
+        const uint4 o1 = draw_row(a.key, (g0 + 1) >> 1, a.problem, kStreamSample);
+        w0a[u] = o0.z; w0b[u] = o0.w; w1a[u] = o1.x; w1b[u] = o1.y;
+      }
+    }
 #pragma unroll
     for (int u = 0; u < kMarkUnroll; ++u) {
       const int64_t base = base0 + u * stride;
       if (base >= stop) break;                 // uniform across the warp
       const int64_t r0 = base + 2 * lane;      // this lane's two rows: r0, r0 + 1
-      const uint64_t g0 = static_cast<uint64_t>(a.row_offset + r0);
-      uint32_t w0a, w0b, w1a, w1b;
-      if (!odd_offset) {
-        const uint4 o = draw_row(a.key, g0 >> 1, a.problem, kStreamSample);
-        w0a = o.x; w0b = o.y; w1a = o.z; w1b = o.w;
-      } else {
-        const uint4 o0 = draw_row(a.key, g0 >> 1, a.problem, kStreamSample);
-        const uint4 o1 = draw_row(a.key, (g0 + 1) >> 1, a.problem, kStreamSample);
-        w0a = o0.z; w0b = o0.w; w1a = o1.x; w1b = o1.y;
-      }
       bool k0 = false, k1 = false;
       if (a.p) {
-        if (r0 < stop) k0 = static_cast<double>(u53_of(w0a, w0b)) * 0x1p-53 < p0[u];
-        if (r0 + 1 < stop) k1 = static_cast<double>(u53_of(w1a, w1b)) * 0x1p-53 < p1[u];
+        if (r0 < stop) k0 = static_cast<double>(u53_of(w0a[u], w0b[u])) * 0x1p-53 < p0[u];
+        if (r0 + 1 < stop) k1 = static_cast<double>(u53_of(w1a[u], w1b[u])) * 0x1p-53 < p1[u];
       } else {
-        if (r0 < stop) k0 = keep_row(l0[u], tau32, tau, w0a, w0b);
-        if (r0 + 1 < stop) k1 = keep_row(l1[u], tau32, tau, w1a, w1b);
+        if (r0 < stop) k0 = keep_row(l0[u], tau32, tau, w0a[u], w0b[u]);
+        if (r0 + 1 < stop) k1 = keep_row(l1[u], tau32, tau, w1a[u], w1b[u]);
       }
       const uint32_t be = __ballot_sync(0xffffffffu, k0);
       const uint32_t bo = __ballot_sync(0xffffffffu, k1);

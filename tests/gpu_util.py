@@ -82,6 +82,22 @@ def lambda_tol(X: np.ndarray, M: np.ndarray) -> np.ndarray:
     return (q + 2) * 2.0 ** -24 * leverage.lambda_term_scale(X, M)
 
 
+def tensor_core_form(dtype: str, d: int, r2: int, lda) -> bool:
+    """Shapes whose λ runs on the tensor cores (BF16 A, d = r2 = 32, rows back to back)."""
+    return dtype == "bf16" and d == 32 and r2 == 32 and (lda is None or lda == d)
+
+
+def lambda_tol_tc(X: np.ndarray, Mm: np.ndarray) -> np.ndarray:
+    """Rounding bound of a tensor-core Λ row against the FP64 value with the same BF16 M_A:
+    the BF16 products are exact in FP32; the K = d accumulation and the FP32 b term add at
+    most (d + 2) roundings; a factor 2 covers an accumulator that truncates instead of
+    rounding to nearest."""
+    from oracle import leverage
+
+    q = X.shape[1]
+    return 2 * (q + 2) * 2.0 ** -24 * leverage.lambda_term_scale(X, Mm)
+
+
 def ambiguous(u: np.ndarray, p: np.ndarray, rel: float) -> np.ndarray:
     return np.abs(u - p) <= rel * np.maximum(p, 1e-300)
 

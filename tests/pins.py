@@ -324,3 +324,32 @@ def check_solver(seed: int = 8) -> None:
 ALL_CHECKS = [check_hadamard_closed_form, check_cauchy_quantiles, check_draw_statistics,
               check_fct_dense, check_fct_blocks, check_fct_mass, check_fct_stability,
               check_qr, check_lambda_distribution, check_sampling, check_solver]
+
+
+def _all_checks():
+    return ALL_CHECKS + [check_bf16_round]
+
+
+# ----------------------------------------------------------------- BF16 rounding of M
+def check_bf16_round() -> None:
+    """Values with at most 8 significant bits are unchanged; midpoints go to the even
+    neighbour; the relative error is at most 2^-8 (half an ulp of an 8-bit significand at the
+    bottom of a binade) plus the FP32 step."""
+    from oracle import leverage
+
+    exact = np.array([1.0, -3.5, 0.0078125, 2.0 ** -30 * 255 / 128, 1.9921875, -100.0])
+    assert np.array_equal(leverage.bf16_round(exact), exact)
+    ulp = 2.0 ** -7
+    assert leverage.bf16_round(np.array([1.0 + ulp / 2]))[0] == 1.0            # tie → even (1.0)
+    assert leverage.bf16_round(np.array([1.0 + 3 * ulp / 2]))[0] == 1.0 + 2 * ulp  # tie → even
+    assert leverage.bf16_round(np.array([1.0 + ulp / 2 + 1e-6]))[0] == 1.0 + ulp   # past the midpoint
+    # the FP32 step comes first: a nudge below FP32 resolution is lost and the tie goes to even
+    assert leverage.bf16_round(np.array([1.0 + ulp / 2 + 1e-9]))[0] == 1.0
+    g = np.random.default_rng(3)
+    x = g.standard_normal(100000) * 10.0 ** g.uniform(-5, 5, 100000)
+    r = leverage.bf16_round(x)
+    assert np.all(np.abs(r - x) <= (2.0 ** -8 + 2.0 ** -23) * np.abs(x))   # BF16 half-ulp + the FP32 step
+    assert np.quantile(np.abs(r - x) / np.abs(x), 0.99) > 2.0 ** -9      # and it is attained
+    M = g.standard_normal((5, 3))
+    mm = leverage.mixed_precision_m(M)
+    assert np.array_equal(mm[-1], M[-1].astype(np.float32)) and np.array_equal(mm[:-1], leverage.bf16_round(M[:-1]))

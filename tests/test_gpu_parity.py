@@ -13,7 +13,8 @@ import pytest
 import torch
 
 import paper_1207_4684_gb300 as L
-from gpu_util import DEV, ambiguous, check_pix, fsum, gpu_pix, host_x, lambda_tol, problem, to_device
+from gpu_util import (DEV, ambiguous, check_pix, fsum, gpu_pix, host_x, lambda_tol, lambda_tol_tc, problem,
+                      tensor_core_form, to_device)
 from oracle import condition, fct, leverage, rng, sampling, solve
 from synth import r1_for
 
@@ -107,9 +108,11 @@ def test_fct_nonfinite_flag():
 
 
 # ----------------------------------------------------------------- conditioning
-@pytest.mark.parametrize("n,d,s,r2", [(65536, 8, 64, 16), (30000, 32, 256, 32), (5000, 64, 64, 32), (4000, 1, 16, 5)])
-def test_condition_parity(n, d, s, r2):
-    pr = problem(n, d, seed=d)
+@pytest.mark.parametrize("n,d,s,r2,design", [(65536, 8, 64, 16, "gauss"), (30000, 32, 256, 32, "gauss"),
+                                             (5000, 64, 64, 32, "gauss"), (4000, 1, 16, 5, "gauss"),
+                                             (65536, 16, 256, 16, "gauss_colscale")])
+def test_condition_parity(n, d, s, r2, design):
+    pr = problem(n, d, seed=d, design=design)
     A, b = to_device(pr)
     r1 = max(r1_for(max(d, 2)), d + 1)
     prm = L.make_params(s, r1, r2, 100.0, seed=4)
@@ -147,6 +150,8 @@ def test_condition_rank_deficient_flag():
 # ----------------------------------------------------------------- phase 2
 @pytest.mark.parametrize("n,d,r2,dtype,lda", [(100000, 16, 16, "f32", None), (70001, 8, 16, "f32", None),
                                               (50000, 32, 32, "bf16", None), (40000, 64, 32, "f32", None),
+                                              (128, 32, 32, "bf16", None), (200001, 32, 32, "bf16", None),
+                                              (1000, 32, 32, "bf16", 40),
                                               (30000, 5, 16, "f32", 9), (20000, 7, 9, "f32", None),
                                               (12345, 12, 32, "bf16", None), (1000, 3, 64, "f32", None),
                                               (257, 4, 1, "f32", None)])
@@ -163,8 +168,13 @@ def test_lambda_parity(n, d, r2, dtype, lda):
     tot = torch.zeros(1, dtype=torch.float64, device=DEV)
     L.l1_lambda(A, b, torch.from_numpy(np.ascontiguousarray(M)).to(DEV), prm, lam, tot, ws)
     got = lam.cpu().double().numpy()
-    ref = leverage.lambda_estimates(X, M)
-    tol = lambda_tol(X, M)
+    if tensor_core_form(dtype, d, r2, lda):
+        Mm = leverage.mixed_precision_m(M)          # the mixed-precision form: M_A in BF16
+        ref = leverage.lambda_estimates(X, Mm)
+        tol = lambda_tol_tc(X, Mm)
+    else:
+        ref = leverage.lambda_estimates(X, M)
+        tol = lambda_tol(X, M)
     assert np.all(np.abs(got - ref) <= tol), f"worst {(np.abs(got - ref) / tol).max():.3f} of the bound"
     assert math.isclose(tot.item(), fsum(got), rel_tol=1e-12)
 

@@ -15,7 +15,7 @@ import pytest
 import torch
 
 import paper_1207_4684_gb300 as L
-from gpu_util import DEV, fsum, host_x, lambda_tol, problem, to_device
+from gpu_util import DEV, fsum, host_x, lambda_tol, lambda_tol_tc, problem, tensor_core_form, to_device
 from oracle import condition, leverage, rng
 
 pytestmark = pytest.mark.gpu
@@ -51,11 +51,16 @@ def test_lambda_noalloc_matches_workspace_entry_point():
         got = lam.cpu().double().numpy()
         want = lam_ws.cpu().double().numpy()
         X = host_x(pr)
-        assert np.all(np.abs(got - want) <= lambda_tol(X, M)), "λ differs from l1_lambda"
+        if tensor_core_form(dtype, d, r2, None):
+            Mref = leverage.mixed_precision_m(M)
+            tol = lambda_tol_tc(X, Mref)
+        else:
+            Mref, tol = M, lambda_tol(X, M)
+        assert np.all(np.abs(got - want) <= tol), "λ differs from l1_lambda"
         assert math.isclose(tot.item(), tot_ws.item(), rel_tol=1e-12)
         assert math.isclose(tot.item(), fsum(got), rel_tol=1e-12)
-        ref = leverage.lambda_estimates(X, M)
-        assert np.all(np.abs(got - ref) <= lambda_tol(X, M))
+        ref = leverage.lambda_estimates(X, Mref)
+        assert np.all(np.abs(got - ref) <= tol)
 
 
 def test_lambda_noalloc_rejects_sizes_beyond_its_scratch():
