@@ -42,6 +42,8 @@ def parse():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the BF16 and batched forms (measured after the main line's timed region)")
     return ap.parse_args()
 
 
@@ -183,6 +185,157 @@ def run_reference(args) -> None:
     print(json.dumps(line), flush=True)
 
 
+# ----------------------------------------------------------------- BF16 and batched forms
+def _time_ms(step, stream, warmup: int, steps: int) -> float:
+    """Mean device time of one step: CUDA events on `stream` around `steps` back-to-back steps."""
+    import torch
+
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        step()
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def _phase_ms(L, A, b, prm, cap, q, dev, stream, warmup, steps) -> dict:
+    import torch
+
+    R = torch.empty((q, q), dtype=torch.float64, device=dev)
+    M = torch.empty((q, prm.r2), dtype=torch.float64, device=dev)
+    pix = torch.empty((prm.r1, q), dtype=torch.float32, device=dev)
+    idx = torch.empty(cap, dtype=torch.int64, device=dev)
+    wts = torch.empty(cap, dtype=torch.float64, device=dev)
+    cnt = torch.zeros(1, dtype=torch.int64, device=dev)
+    n, d = A.shape
+    ws = L.workspace(prm, n, d, L.BF16 if A.dtype == torch.bfloat16 else L.F32, device=dev)
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    acc = [0.0, 0.0, 0.0]
+    for it in range(warmup + steps):
+        evs[0].record(stream)
+        L.fct_embed(A, b, prm, pix, ws, stream=stream)
+        evs[1].record(stream)
+        L.l1_condition(pix, prm, R, M, ws, stream=stream)
+        evs[2].record(stream)
+        L.l1_sample(A, b, M, prm, cap, idx, wts, None, cnt, None, ws, stream=stream)
+        evs[3].record(stream)
+        if it >= warmup:
+            torch.cuda.synchronize(dev)
+            for k in range(3):
+                acc[k] += evs[k].elapsed_time(evs[k + 1])
+    return dict(zip(["fct_embed", "l1_condition", "l1_sample"], [a / steps for a in acc]))
+
+
+def bf16_variant(L, dev, stream, args, peak: float) -> dict:
+    """The mixed-precision form (A streamed as BF16, λ on tcgen05 tensor cores) against the plain
+    FP32 path on the same values widened to FP32: rows/s of each, and the relative difference of
+    the final objectives ‖A·x̂ − b‖₁ after the coreset solve."""
+    import numpy as np
+    import torch
+
+    from synth import WORKLOADS, make_problem
+
+    w = WORKLOADS["t2rows_n16M_d32_bf16"]
+    pr = make_problem(w)
+    n, d = pr["A"].shape
+    q = d + 1
+    A16 = torch.from_numpy(pr["A"].view(np.int16)).view(torch.bfloat16).to(dev)
+    A32 = A16.float()
+    b = torch.from_numpy(pr["b"]).to(dev)
+    del pr
+    prm = L.make_params(w.s, w.r1, w.r2, w.coreset, seed=w.seed, problem_id=w.problem_id)
+    cap = int(2 * w.coreset) + 64
+    ws = L.workspace(prm, n, d, L.F32, device=dev)
+    assert ws.numel() >= L.l1s_workspace_size(prm, n, d, L.BF16)
+    idx = torch.empty(cap, dtype=torch.int64, device=dev)
+    wts = torch.empty(cap, dtype=torch.float64, device=dev)
+    cnt = torch.zeros(1, dtype=torch.int64, device=dev)
+    out = {"workload": w.name, "n": n, "d": d, "s": w.s, "r1": w.r1, "r2": w.r2, "coreset": w.coreset}
+    for tag, A, elem in (("bf16", A16, 2), ("f32", A32, 4)):
+        ms = _time_ms(lambda: L.l1_coreset(A, b, prm, cap, idx, wts, None, cnt, ws, stream=stream), stream,
+                      args.warmup, args.steps)
+        kept = int(cnt.item())
+        ab = algorithmic_bytes(n, d, elem, kept)["step"]
+        x, f, rows, rc = L.l1_regress(A, b, prm, ws, stream=stream)
+        out[tag] = {"value": n / (ms / 1e3), "ms_per_step": ms, "step_gbs": ab / (ms / 1e3) / 1e9,
+                    "step_frac": ab / (ms / 1e3) / 1e9 / peak, "algorithmic_bytes": ab, "coreset_rows": kept,
+                    "objective": f, "status": rc,
+                    "phase_ms": _phase_ms(L, A, b, prm, cap, q, dev, stream, 2, max(3, args.steps // 4))}
+    f16, f32 = out["bf16"]["objective"], out["f32"]["objective"]
+    out["objective_rel_err_vs_f32"] = abs(f16 - f32) / f32
+    out["speedup_vs_f32"] = out["bf16"]["value"] / out["f32"]["value"]
+    return out
+
+
+def batched_variant(L, dev, stream, args, peak: float) -> dict:
+    """256 independent regressions of uneven n and d in one l1_regress_batched call, schedules
+    picked by l1s_autotune per (d, s), the call captured into one CUDA graph and replayed."""
+    import torch
+
+    from synth import make_batched_problems
+
+    t0 = time.perf_counter()
+    prs = make_batched_problems(256)
+    gen_s = time.perf_counter() - t0
+    members = []
+    for pr in prs:
+        w = pr["w"]
+        A = torch.from_numpy(pr["A"]).to(dev)
+        b = torch.from_numpy(pr["b"]).to(dev)
+        prm = L.make_params(w.s, w.r1, w.r2, w.coreset, seed=w.seed, problem_id=w.problem_id)
+        cnt = torch.zeros(1, dtype=torch.int64, device=dev)
+        members.append(dict(w=w, A=A, b=b, prm=prm, cnt=cnt))
+    del prs
+    # Autotune one representative (the largest n) per (d, s).
+    tuned = {}
+    t0 = time.perf_counter()
+    for m in sorted(members, key=lambda m: -m["w"].n):
+        key = (m["w"].d, m["w"].s)
+        if key in tuned:
+            continue
+        ws1 = L.workspace(m["prm"], m["w"].n, m["w"].d, device=dev)
+        sched, ms = L.l1s_autotune(L.make_problem(m["A"], m["b"], m["prm"]), ws1, trials=3, stream=stream)
+        tuned[key] = {"schedule": sched, "ms": ms, "n": m["w"].n}
+        del ws1
+    tune_s = time.perf_counter() - t0
+    probs = [L.make_problem(m["A"], m["b"], m["prm"], count=m["cnt"]) for m in members]
+    ws = L.batched_workspace(probs, device=dev)
+    flags = torch.zeros(len(probs), dtype=torch.int32, device=dev)
+    side = torch.cuda.Stream(dev)   # graphs are not captured on the legacy default stream
+    side.wait_stream(stream)
+
+    def eager():
+        L.l1_regress_batched(probs, ws, flags, stream=side)
+
+    with torch.cuda.stream(side):
+        c0 = L.l1s_kernel_launches()
+        eager()
+        launches = L.l1s_kernel_launches() - c0
+        eager_ms = _time_ms(eager, side, args.warmup, args.steps)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=side):
+            eager()
+        graph_ms = _time_ms(g.replay, side, args.warmup, args.steps)
+    torch.cuda.synchronize()
+    fl = flags.cpu().numpy()
+    rows = sum(m["w"].n for m in members)
+    ab = sum(algorithmic_bytes(m["w"].n, m["w"].d, 4, int(m["cnt"].item()))["step"] for m in members)
+    ds = sorted({m["w"].d for m in members})
+    return {"workload": "batched_256_n2^12..2^20_d4..64", "problems": len(members), "rows": rows,
+            "value": rows / (graph_ms / 1e3), "ms_per_step": graph_ms, "graph": True,
+            "eager": {"value": rows / (eager_ms / 1e3), "ms_per_step": eager_ms},
+            "step_gbs": ab / (graph_ms / 1e3) / 1e9, "step_frac": ab / (graph_ms / 1e3) / 1e9 / peak,
+            "algorithmic_bytes": ab, "gpu_launches_per_step": launches,
+            "status_nonzero": int((fl != 0).sum()),
+            "d_values": ds, "s_by_d": {str(m["w"].d): m["w"].s for m in members},
+            "autotuned": {f"d{k[0]}_s{k[1]}": v for k, v in sorted(tuned.items())},
+            "host_s": {"generate": gen_s, "autotune": tune_s}}
+
+
 # ----------------------------------------------------------------- GPU arm
 def run_gpu(args) -> None:
     import numpy as np
@@ -243,10 +396,12 @@ def run_gpu(args) -> None:
     with ClockSampler(local) as clk:
         barrier()
         t_host0 = time.perf_counter()
+        launches0 = L.l1s_kernel_launches()
         ev0.record(stream)
         for _ in range(args.steps):
             step()
         ev1.record(stream)
+        launches = L.l1s_kernel_launches() - launches0
         barrier()
         t_host = time.perf_counter() - t_host0
     gpu_ms = ev0.elapsed_time(ev1)
@@ -330,10 +485,18 @@ def run_gpu(args) -> None:
         "phase_ms": dict(zip(names, phase_ms)),
         "e2e": {"value": world * n / e2e_s, "unit": UNIT, "h2d_bytes_per_step": n * (d * elem + 4),
                 "d2h_bytes_per_step": 8 + cap * 16, "status": rc},
-        "gpu_launches": 7 * args.steps,
+        "gpu_launches": launches,
         "clocks": clk.summary(),
         "coreset_rows": kept, "status_flags": flags, "host_wall_s": t_host,
     }
+    if rank == 0 and not args.no_variants and world == 1:
+        del ws, A, b
+        torch.cuda.empty_cache()
+        line["variants"] = {"bf16": bf16_variant(L, dev, stream, args, peaks["hbm_gbs"])}
+        torch.cuda.empty_cache()
+        line["variants"]["batched"] = batched_variant(L, dev, stream, args, peaks["hbm_gbs"])
+        line["variants"]["f32_plain"] = {"workload": w.name, "value": value, "ms_per_step": ms_per_step,
+                                         "step_frac": step_gbs / peaks["hbm_gbs"]}
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_oracle_rows_per_s(pr, w, args.cpu_seconds)
     if rank == 0:

@@ -33,7 +33,8 @@
  * - Not thread-safe per workspace; distinct workspaces may be used from
  *   distinct threads.  l1_lambda, l1_sample, l1_coreset, l1_coreset_host and
  *   l1_regress load M into a per-device constant bank: calls of these on
- *   different streams of one device must not overlap.
+ *   different streams of one device must not overlap (l1_regress_batched
+ *   keeps M in shared memory and has no such limit).
  */
 #ifndef L1FCT_H
 #define L1FCT_H
@@ -86,6 +87,11 @@ L1S_API const char* l1s_last_error(void);
 
 /* Library version string. */
 L1S_API const char* l1s_version(void);
+
+/* Number of kernels this process has launched through the library so far.  A
+ * CUDA graph counts its kernels once, when they are captured; its replays
+ * re-run them without counting. */
+L1S_API uint64_t l1s_kernel_launches(void);
 
 /* Bytes of device workspace that every entry point below needs for a problem
  * of n rows and d columns with these params on the current device.  With
@@ -197,9 +203,12 @@ L1S_API int l1_coreset_host(const void* A_host, int64_t lda, l1s_dtype dtype, co
 /* Weighted ℓ1 regression on a coreset (Figure 2, step 8): x̂ minimising
  * Σ_k w_k·|X_k·[x; 1]| over rows X_k = [A_k, −b_k] (coreset_dev, FP64, q per
  * row, count from *count_dev, at most capacity) by FP64 iteratively
- * reweighted least squares, finished by an exact solve on the d rows with
- * the smallest residuals when that lowers the objective.  Writes x_dev (d
- * FP64) and *objective_dev (the weighted objective at x_dev). */
+ * reweighted least squares, finished by simplex pivots of the LAD linear
+ * program from the vertex of the d rows with the smallest residuals, up to a
+ * vertex whose optimality the dual multipliers certify.  Writes x_dev (d
+ * FP64) and *objective_dev (the weighted objective at x_dev).  The status bit
+ * L1S_ERR_NOT_CONVERGED is raised when neither the iteration converged nor the
+ * vertex was certified optimal. */
 L1S_API int l1_solve(const double* coreset_dev, const double* w_dev, const int64_t* count_dev,
              int64_t capacity, int32_t d, int32_t max_iter, double* x_dev,
              double* objective_dev, void* ws, size_t ws_bytes, void* stream);
@@ -231,6 +240,72 @@ L1S_API int l1s_debug_variates(const l1s_params* params, int64_t row_start, int6
 
 /* Debug: Π2 (q × r2, FP64, row-major) as l1_condition draws it. */
 L1S_API int l1s_debug_pi2(const l1s_params* params, int32_t q, double* pi2_dev, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Launch schedules and the autotuner
+ *
+ * A schedule fixes how the kernels of one (d, dtype, s) tile the work; it never
+ * changes what they compute (s itself is a parameter of Π1, §3.1, and is not
+ * tuned here).  Zero fields mean "the default rule".
+ * ------------------------------------------------------------------------- */
+typedef struct {
+  int32_t fct_variant;       /* phase 1 kernel: 0 default, 1 warp-specialised narrow-X kernel
+                                (d ≤ 16, 32 ≤ s ≤ 512), 2 all columns with TMA-staged tiles,
+                                3 direct loads over column slices.  A variant that does not
+                                apply to the shape falls back to the default. */
+  int32_t fct_ctas_per_sm;   /* phase 1 resident blocks per SM (capped by occupancy); 0 = most */
+  int32_t lam_ctas_per_sm;   /* λ pass blocks per SM, 1..32; 0 = 8 */
+  int32_t smp_chunks_per_sm; /* sampling row chunks per SM, 1..16; 0 = 4 */
+} l1s_schedule;
+
+/* Install `sch` for every later call on this process with this d, dtype and s
+ * (NULL removes the entry).  Workspace sizes do not depend on the schedule. */
+L1S_API int l1s_schedule_set(int32_t d, l1s_dtype dtype, int32_t s, const l1s_schedule* sch);
+
+/* The schedule installed for (d, dtype, s); all zeros when none is. */
+L1S_API int l1s_schedule_get(int32_t d, l1s_dtype dtype, int32_t s, l1s_schedule* sch);
+
+/* One problem of a batch (device pointers).  idx/w/coreset/count, x and
+ * objective may be NULL: the coreset then stays in the workspace, and the
+ * solve (Figure 2, step 8) runs only when x is non-NULL. */
+typedef struct {
+  const void* A_dev;         /* n × d, leading dimension lda, FP32 or BF16 */
+  const float* b_dev;        /* n */
+  int64_t lda;
+  int64_t n;
+  int32_t d;
+  l1s_dtype dtype;
+  l1s_params params;
+  int64_t capacity;          /* rows of idx_dev / w_dev / coreset_dev */
+  int64_t* idx_dev;          /* kept row ids, ascending */
+  double* w_dev;             /* weights 1/p̂ */
+  double* coreset_dev;       /* capacity × q FP64 rows w·X_i (may be NULL) */
+  int64_t* count_dev;        /* number of kept rows */
+  double* x_dev;             /* d: the coreset solution x̂ (NULL: no solve) */
+  double* objective_dev;     /* 1: ‖A·x̂ − b‖₁ over all n rows (needs x_dev) */
+} l1s_problem;
+
+/* Time the schedules that apply to `prob`'s shape (l1_coreset on its data,
+ * median of `trials` runs per candidate, CUDA events on `stream`), install
+ * the fastest with l1s_schedule_set, and return it in *best (and its time in
+ * *best_ms when non-NULL).  The workspace is sized by l1s_workspace_size for
+ * the problem.  Synchronises `stream`; not for use inside stream capture. */
+L1S_API int l1s_autotune(const l1s_problem* prob, int32_t trials, l1s_schedule* best, double* best_ms,
+                         void* ws, size_t ws_bytes, void* stream);
+
+/* Device workspace for l1_regress_batched over these problems. */
+L1S_API int l1s_batched_workspace_size(const l1s_problem* probs, int32_t count, size_t* bytes);
+
+/* Many independent regressions (Figure 2 per problem, each with its own n, d,
+ * dtype and params) in one call.  The problems are spread over a pool of
+ * library-owned streams (longest first, each onto the least loaded stream)
+ * that fork from `stream` and join back into it, so the whole batch can be
+ * captured into one CUDA graph and replayed.  λ reads M from shared memory
+ * here, so concurrent problems do not share the constant bank.  flags_dev
+ * (count uint32, may be NULL) receives each problem's status word.  Enqueues
+ * only; `stream` sees every problem finished. */
+L1S_API int l1_regress_batched(const l1s_problem* probs, int32_t count, uint32_t* flags_dev, void* ws,
+                               size_t ws_bytes, void* stream);
 
 #ifdef __cplusplus
 }

@@ -10,6 +10,9 @@ from .l1fct import (  # noqa: F401
     F32,
     L1SError,
     Params,
+    Problem,
+    Schedule,
+    batched_workspace,
     fct_embed,
     flag,
     l1_coreset,
@@ -19,16 +22,23 @@ from .l1fct import (  # noqa: F401
     l1_lambda_noalloc,
     l1_objective,
     l1_regress,
+    l1_regress_batched,
     l1_sample,
     l1_sample_from_p,
     l1_solve,
     l1s_debug_pi2,
+    l1s_autotune,
+    l1s_batched_workspace_size,
     l1s_debug_variates,
+    l1s_kernel_launches,
+    l1s_schedule_get,
+    l1s_schedule_set,
     l1s_status_read,
     l1s_status_reset,
     l1s_workspace_size,
     load,
     make_params,
+    make_problem,
     version,
     workspace,
 )

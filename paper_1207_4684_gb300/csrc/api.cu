@@ -6,6 +6,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <mutex>
 
 #include "l1s_common.cuh"
@@ -41,6 +42,7 @@ bool launch_debug_variates(const l1s_params* p, int64_t row_start, int64_t count
                            uint64_t* ub, cudaStream_t st);
 int irls_entries(int q);
 size_t irls_state_bytes();
+size_t solve_scratch_bytes(int64_t capacity);
 bool launch_solve(const double* X, const double* w, const int64_t* count, int64_t capacity, int d,
                   int max_iter, double* x_out, double* obj_out, int nblocks, double* partials,
                   void* state, float* scratch, StatusBlock* status, cudaStream_t st);
@@ -48,6 +50,9 @@ bool launch_objective(const void* A, int64_t lda, l1s_dtype dt, const float* b, 
                       const double* x, double* out, int nblocks, double* partials, cudaStream_t st);
 
 static thread_local char g_err[512] = "";
+static std::atomic<uint64_t> g_launches{0};
+
+void count_launch(int k) { g_launches.fetch_add(static_cast<uint64_t>(k), std::memory_order_relaxed); }
 
 void set_error(const char* fmt, ...) {
   va_list ap;
@@ -98,11 +103,122 @@ static bool check_params(const l1s_params* p, int64_t n, int d) {
   return true;
 }
 
-static int64_t coreset_capacity_of(const l1s_params* p) {
+
+int64_t coreset_capacity_of(const l1s_params* p) {
   return static_cast<int64_t>(ceil(2.0 * p->coreset_size)) + 64;
 }
 
-bool make_plan(const l1s_params* p, int64_t n, int d, l1s_dtype dt, bool host_staging, Plan* pl) {
+bool check_ws(const Plan& pl, const void* ws, size_t ws_bytes) {
+  if (!ws) return set_error("workspace is NULL"), false;
+  if (reinterpret_cast<uintptr_t>(ws) % 256 != 0) return set_error("workspace must be 256-byte aligned"), false;
+  if (ws_bytes < pl.total)
+    return set_error("workspace too small: %zu bytes given, %zu needed", ws_bytes, pl.total), false;
+  return true;
+}
+
+bool check_a(const void* A, int64_t lda, const float* b, int d) {
+  if (!A || !b) return set_error("A and b must not be NULL"), false;
+  if (lda < d) return set_error("lda must be >= d"), false;
+  return true;
+}
+
+int first_error(uint32_t flags) {
+  for (int code = L1S_ERR_RANK_DEFICIENT; code <= L1S_ERR_CAPACITY; ++code)
+    if (flags & L1S_FLAG(code)) return code;
+  if (flags & L1S_FLAG(L1S_ERR_TIMEOUT)) return L1S_ERR_TIMEOUT;
+  return L1S_OK;
+}
+
+int sample_impl(const Plan& pl, const void* A, int64_t lda, l1s_dtype dtype, const float* b,
+                       const float* m32, const l1s_params* params, int64_t capacity, int64_t* idx,
+                       double* wts, double* coreset, int64_t* count, float* lambda, unsigned char* w,
+                       cudaStream_t st) {
+  float* lam = lambda ? lambda : reinterpret_cast<float*>(w + pl.off_lam);
+  if (!launch_lambda(pl, A, lda, dtype, b, m32, params, lam, nullptr, w, st)) return L1S_ERR_CUDA;
+  if (!launch_sample(pl, lam, nullptr, params, A, lda, dtype, b, capacity, idx, wts, coreset, count, w, st))
+    return L1S_ERR_CUDA;
+  return L1S_OK;
+}
+
+int coreset_impl(const Plan& pl, const void* A, int64_t lda, l1s_dtype dtype, const float* b,
+                        const l1s_params* params, int64_t capacity, int64_t* idx, double* wts,
+                        double* coreset, int64_t* count, unsigned char* w, cudaStream_t st) {
+  if (!cuda_ok(cudaMemsetAsync(w + pl.off_status, 0, sizeof(StatusBlock), st), "status reset"))
+    return L1S_ERR_CUDA;
+  float* pix = reinterpret_cast<float*>(w + pl.off_pix);
+  if (!launch_fct(pl, A, lda, dtype, b, params, pix, w, st)) return L1S_ERR_CUDA;
+  if (!launch_condition(pl, pix, params, nullptr, nullptr, w, st)) return L1S_ERR_CUDA;
+  return sample_impl(pl, A, lda, dtype, b, reinterpret_cast<float*>(w + pl.off_m32), params, capacity, idx,
+                     wts, coreset, count, nullptr, w, st);
+}
+
+// Geometry of one phase-1 kernel variant for a shape: which kernel, its column slicing,
+// shared memory, threads, and the resident blocks per SM that occupancy allows.
+struct FctGeometry {
+  bool ok;
+  bool t16, staged;
+  int slices, width, threads, per_sm;
+  size_t smem;
+};
+
+static FctGeometry fct_geometry(int variant, const Plan& P, l1s_dtype dt, const DeviceInfo& di) {
+  FctGeometry g{};
+  const size_t budget2 = std::min<size_t>(110 * 1024, di.max_smem_optin);
+  const size_t budget1 = di.max_smem_optin;
+  int width = P.q;
+  bool staged = false;
+  if (variant == 1) {
+    if (!fct_t16_applies(P.log2s, P.d) || fct_t16_smem_bytes(P.s, P.d, dt, P.r1) > budget1) return g;
+    g.t16 = true;
+    staged = true;
+  } else if (variant == 2) {
+    if (fct_smem_bytes(P.s, P.d, dt, P.r1, P.q, true) > budget1) return g;
+    staged = true;
+  } else {
+    // Direct loads: the widest column slice whose shared-memory footprint allows two
+    // blocks per SM, or failing that one.
+    int slices = 1;
+    for (;; ++slices) {
+      width = (P.q + slices - 1) / slices;
+      if (fct_smem_bytes(P.s, P.d, dt, P.r1, width, false) <= budget2 || width == 1) break;
+    }
+    if (fct_smem_bytes(P.s, P.d, dt, P.r1, width, false) > budget2) {
+      for (slices = 1;; ++slices) {
+        width = (P.q + slices - 1) / slices;
+        if (fct_smem_bytes(P.s, P.d, dt, P.r1, width, false) <= budget1) break;
+        if (width == 1) return g;
+      }
+    }
+  }
+  g.staged = staged;
+  g.slices = (P.q + width - 1) / width;
+  g.width = width;
+  g.smem = g.t16 ? fct_t16_smem_bytes(P.s, P.d, dt, P.r1) : fct_smem_bytes(P.s, P.d, dt, P.r1, width, staged);
+  g.threads = g.t16 ? fct_t16_threads() : fct_threads_for(P.log2s, width);
+  const void* fn = g.t16 ? fct_t16_kernel(P.log2s, dt) : fct_kernel(P.log2s, dt, staged);
+  if (!cuda_ok(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(g.smem)),
+               "cudaFuncSetAttribute(fct_embed)"))
+    return g;
+  int per_sm = 0;
+  if (!cuda_ok(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, g.threads, g.smem),
+               "occupancy(fct_embed)"))
+    return g;
+  g.per_sm = std::max(per_sm, 1);
+  g.ok = true;
+  return g;
+}
+
+static int64_t fct_ctas_of(const FctGeometry& g, const Plan& P, const DeviceInfo& di, int per_sm) {
+  const int64_t want = std::max<int64_t>(1, static_cast<int64_t>(di.sms) * per_sm / g.slices);
+  return std::min<int64_t>(P.nblocks, want);
+}
+
+// Bounds of the schedule fields (the workspace is sized for the largest).
+constexpr int kMaxLamPerSm = 32;
+constexpr int kMaxSmpPerSm = 16;
+
+bool make_plan(const l1s_params* p, int64_t n, int d, l1s_dtype dt, bool host_staging, Plan* pl,
+               const l1s_schedule* override_sch) {
   if (!check_params(p, n, d)) return false;
   if (dt != L1S_F32 && dt != L1S_BF16) return set_error("dtype must be L1S_F32 or L1S_BF16"), false;
   const DeviceInfo di = device_info();
@@ -117,65 +233,56 @@ bool make_plan(const l1s_params* p, int64_t n, int d, l1s_dtype dt, bool host_st
   P.r1 = p->r1;
   P.r2 = p->r2;
   P.nblocks = (n + P.s - 1) / P.s;
+  l1s_schedule sch{};
+  if (override_sch)
+    sch = *override_sch;
+  else
+    schedule_lookup(d, dt, P.log2s, &sch);
 
-  // Phase 1.  Preferred: all q columns in one thread block with X tiles staged by TMA.
-  // Otherwise direct loads and the widest column slice whose shared-memory footprint
-  // allows two blocks per SM (or, failing that, one).
-  const size_t budget2 = std::min<size_t>(110 * 1024, di.max_smem_optin);
-  const size_t budget1 = di.max_smem_optin;
-  int width = P.q;
-  bool staged = fct_smem_bytes(P.s, P.d, dt, P.r1, P.q, true) <= budget1;
-  if (!staged) {
-    int slices = 1;
-    for (;; ++slices) {
-      width = (P.q + slices - 1) / slices;
-      if (fct_smem_bytes(P.s, P.d, dt, P.r1, width, false) <= budget2 || width == 1) break;
-    }
-    if (fct_smem_bytes(P.s, P.d, dt, P.r1, width, false) > budget2) {
-      for (slices = 1;; ++slices) {
-        width = (P.q + slices - 1) / slices;
-        if (fct_smem_bytes(P.s, P.d, dt, P.r1, width, false) <= budget1) break;
-        if (width == 1) return set_error("r1 and s too large for shared memory"), false;
-      }
-    }
-  }
-  P.fct_t16 = fct_t16_applies(P.log2s, P.d) && fct_t16_smem_bytes(P.s, P.d, dt, P.r1) <= budget1;
-  if (P.fct_t16) {
-    width = P.q;
-    staged = true;
-  }
-  P.fct_staged = staged ? 1 : 0;
-  P.fct_slices = (P.q + width - 1) / width;
-  P.fct_width = width;
-  P.fct_smem = P.fct_t16 ? fct_t16_smem_bytes(P.s, P.d, dt, P.r1) : fct_smem_bytes(P.s, P.d, dt, P.r1, width, staged);
-  P.fct_threads = P.fct_t16 ? fct_t16_threads() : fct_threads_for(P.log2s, width);
-  const void* fn = P.fct_t16 ? fct_t16_kernel(P.log2s, dt) : fct_kernel(P.log2s, dt, staged);
-  if (!cuda_ok(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    static_cast<int>(P.fct_smem)),
-               "cudaFuncSetAttribute(fct_embed)"))
-    return false;
-  int per_sm = 0;
-  if (!cuda_ok(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, P.fct_threads, P.fct_smem),
-               "occupancy(fct_embed)"))
-    return false;
-  per_sm = std::max(per_sm, 1);
-  const int64_t want = std::max<int64_t>(1, static_cast<int64_t>(di.sms) * per_sm / P.fct_slices);
-  P.fct_ctas = static_cast<int>(std::min<int64_t>(P.nblocks, want));
+  // Phase 1.  Default: the warp-specialised narrow-X kernel where it applies, else all
+  // q columns in one block with TMA-staged X tiles, else direct loads over column slices.
+  FctGeometry geo[4];
+  for (int v = 1; v <= 3; ++v) geo[v] = fct_geometry(v, P, dt, di);
+  if (!geo[3].ok) return set_error("r1 and s too large for shared memory"), false;
+  int variant = geo[1].ok ? 1 : (geo[2].ok ? 2 : 3);
+  if (sch.fct_variant >= 1 && sch.fct_variant <= 3 && geo[sch.fct_variant].ok) variant = sch.fct_variant;
+  const FctGeometry& g = geo[variant];
+  P.fct_t16 = g.t16 ? 1 : 0;
+  P.fct_staged = g.staged ? 1 : 0;
+  P.fct_slices = g.slices;
+  P.fct_width = g.width;
+  P.fct_smem = g.smem;
+  P.fct_threads = g.threads;
+  const int per_sm = sch.fct_ctas_per_sm > 0 ? std::min(sch.fct_ctas_per_sm, g.per_sm) : g.per_sm;
+  P.fct_ctas = static_cast<int>(fct_ctas_of(g, P, di, per_sm));
+  // Partial sums sized for the largest variant at full occupancy.
+  size_t partial_floats = 0;
+  for (int v = 1; v <= 3; ++v)
+    if (geo[v].ok)
+      partial_floats = std::max<size_t>(
+          partial_floats, static_cast<size_t>(geo[v].slices) * fct_ctas_of(geo[v], P, di, geo[v].per_sm) *
+                              P.r1 * geo[v].width);
 
-  // Phase 2: a persistent-style grid of 8 blocks per SM.
+  // Phase 2: a persistent-style grid, 8 blocks per SM by default.
   P.lam_threads = lambda_threads();
-  P.lam_ctas = static_cast<int>(std::max<int64_t>(
-      1, std::min<int64_t>((n + P.lam_threads - 1) / P.lam_threads, static_cast<int64_t>(di.sms) * 8)));
+  const int lam_per_sm = sch.lam_ctas_per_sm > 0 ? std::min(sch.lam_ctas_per_sm, kMaxLamPerSm) : 8;
+  const int64_t lam_rows_ctas = (n + P.lam_threads - 1) / P.lam_threads;
+  P.lam_ctas = static_cast<int>(
+      std::max<int64_t>(1, std::min<int64_t>(lam_rows_ctas, static_cast<int64_t>(di.sms) * lam_per_sm)));
+  const int lam_ctas_max = static_cast<int>(
+      std::max<int64_t>(1, std::min<int64_t>(lam_rows_ctas, static_cast<int64_t>(di.sms) * kMaxLamPerSm)));
 
-  // Phase 3: contiguous chunks (multiples of 64 rows), about 4 per SM.
+  // Phase 3: contiguous chunks (multiples of 64 rows), 4 per SM by default.
   P.smp_threads = sample_threads();
-  {
-    const int64_t target = static_cast<int64_t>(di.sms) * 4;
+  auto chunk_for = [&](int per) {
+    const int64_t target = static_cast<int64_t>(di.sms) * per;
     int64_t chunk = (n + target - 1) / target;
-    chunk = std::max<int64_t>(64, (chunk + 63) / 64 * 64);
-    P.smp_chunk = chunk;
-    P.smp_ctas = static_cast<int>((n + chunk - 1) / chunk);
-  }
+    return std::max<int64_t>(64, (chunk + 63) / 64 * 64);
+  };
+  const int smp_per_sm = sch.smp_chunks_per_sm > 0 ? std::min(sch.smp_chunks_per_sm, kMaxSmpPerSm) : 4;
+  P.smp_chunk = chunk_for(smp_per_sm);
+  P.smp_ctas = static_cast<int>((n + P.smp_chunk - 1) / P.smp_chunk);
+  const int64_t smp_ctas_max = (n + chunk_for(kMaxSmpPerSm) - 1) / chunk_for(kMaxSmpPerSm);
   P.irls_ctas = di.sms;
 
   const int64_t cap = coreset_capacity_of(p);
@@ -190,8 +297,8 @@ bool make_plan(const l1s_params* p, int64_t n, int d, l1s_dtype dt, bool host_st
   // IRLS region first, so that l1_solve can use the same offsets with only (d, capacity).
   P.off_irls = take(sizeof(double) * static_cast<size_t>(P.irls_ctas) * (irls_entries(P.q) + 1));
   P.off_x = take(irls_state_bytes());
-  P.off_objp = take(sizeof(float) * static_cast<size_t>(cap));  // IRLS residual scratch
-  P.off_partials = take(sizeof(float) * static_cast<size_t>(P.fct_slices) * P.fct_ctas * P.r1 * P.fct_width);
+  P.off_objp = take(solve_scratch_bytes(cap));  // residuals and breakpoints of the solve
+  P.off_partials = take(sizeof(float) * partial_floats);
   P.off_pix = take(sizeof(float) * P.r1 * P.q);
   P.off_qr = take(std::max(sizeof(double) * P.r1 * P.q, cond2_scratch_bytes(P.r1, P.q, di.sms)));
   P.off_r = take(sizeof(double) * P.q * P.q);
@@ -199,9 +306,9 @@ bool make_plan(const l1s_params* p, int64_t n, int d, l1s_dtype dt, bool host_st
   P.off_m32 = take(sizeof(float) * P.q * P.r2);
   P.off_pi2 = take(sizeof(double) * P.q * P.r2);
   P.off_lam = take(sizeof(float) * static_cast<size_t>(n));
-  P.off_lamsum = take(sizeof(double) * std::max(P.lam_ctas, P.irls_ctas));
+  P.off_lamsum = take(sizeof(double) * std::max(lam_ctas_max, P.irls_ctas));
   P.off_mask = take(sizeof(uint64_t) * static_cast<size_t>((n + 63) / 64));
-  P.off_counts = take(sizeof(int64_t) * static_cast<size_t>(P.smp_ctas));
+  P.off_counts = take(sizeof(int64_t) * static_cast<size_t>(smp_ctas_max));
   P.off_idx_tmp = take(static_cast<size_t>(cap) * (sizeof(int64_t) + sizeof(double) + sizeof(double) * P.q) +
                        2 * sizeof(double) * (P.q + 1));
   if (host_staging) {
@@ -212,19 +319,7 @@ bool make_plan(const l1s_params* p, int64_t n, int d, l1s_dtype dt, bool host_st
   return true;
 }
 
-static bool check_ws(const Plan& pl, const void* ws, size_t ws_bytes) {
-  if (!ws) return set_error("workspace is NULL"), false;
-  if (reinterpret_cast<uintptr_t>(ws) % 256 != 0) return set_error("workspace must be 256-byte aligned"), false;
-  if (ws_bytes < pl.total)
-    return set_error("workspace too small: %zu bytes given, %zu needed", ws_bytes, pl.total), false;
-  return true;
-}
 
-static bool check_a(const void* A, int64_t lda, const float* b, int d) {
-  if (!A || !b) return set_error("A and b must not be NULL"), false;
-  if (lda < d) return set_error("lda must be >= d"), false;
-  return true;
-}
 
 }  // namespace l1s
 
@@ -235,6 +330,8 @@ extern "C" {
 const char* l1s_last_error(void) { return g_err; }
 
 const char* l1s_version(void) { return "l1fct 0.1 (sm_103a)"; }
+
+uint64_t l1s_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
 
 int l1s_workspace_size(const l1s_params* params, int64_t n, int32_t d, l1s_dtype dtype,
                        int32_t host_staging, size_t* bytes) {
@@ -304,16 +401,6 @@ int l1_lambda(const void* A, int64_t lda, l1s_dtype dtype, const float* b, int64
   return L1S_OK;
 }
 
-static int sample_impl(const Plan& pl, const void* A, int64_t lda, l1s_dtype dtype, const float* b,
-                       const float* m32, const l1s_params* params, int64_t capacity, int64_t* idx,
-                       double* wts, double* coreset, int64_t* count, float* lambda, unsigned char* w,
-                       cudaStream_t st) {
-  float* lam = lambda ? lambda : reinterpret_cast<float*>(w + pl.off_lam);
-  if (!launch_lambda(pl, A, lda, dtype, b, m32, params, lam, nullptr, w, st)) return L1S_ERR_CUDA;
-  if (!launch_sample(pl, lam, nullptr, params, A, lda, dtype, b, capacity, idx, wts, coreset, count, w, st))
-    return L1S_ERR_CUDA;
-  return L1S_OK;
-}
 
 int l1_sample(const void* A, int64_t lda, l1s_dtype dtype, const float* b, int64_t n, int32_t d,
               const double* M, const l1s_params* params, int64_t capacity, int64_t* idx, double* wts,
@@ -345,17 +432,6 @@ int l1_sample_from_p(const double* p, int64_t n, const l1s_params* params, int64
   return L1S_OK;
 }
 
-static int coreset_impl(const Plan& pl, const void* A, int64_t lda, l1s_dtype dtype, const float* b,
-                        const l1s_params* params, int64_t capacity, int64_t* idx, double* wts,
-                        double* coreset, int64_t* count, unsigned char* w, cudaStream_t st) {
-  if (!cuda_ok(cudaMemsetAsync(w + pl.off_status, 0, sizeof(StatusBlock), st), "status reset"))
-    return L1S_ERR_CUDA;
-  float* pix = reinterpret_cast<float*>(w + pl.off_pix);
-  if (!launch_fct(pl, A, lda, dtype, b, params, pix, w, st)) return L1S_ERR_CUDA;
-  if (!launch_condition(pl, pix, params, nullptr, nullptr, w, st)) return L1S_ERR_CUDA;
-  return sample_impl(pl, A, lda, dtype, b, reinterpret_cast<float*>(w + pl.off_m32), params, capacity, idx,
-                     wts, coreset, count, nullptr, w, st);
-}
 
 int l1_coreset(const void* A, int64_t lda, l1s_dtype dtype, const float* b, int64_t n, int32_t d,
                const l1s_params* params, int64_t capacity, int64_t* idx, double* wts, double* coreset,
@@ -370,12 +446,6 @@ int l1_coreset(const void* A, int64_t lda, l1s_dtype dtype, const float* b, int6
                       static_cast<unsigned char*>(ws), static_cast<cudaStream_t>(stream));
 }
 
-static int first_error(uint32_t flags) {
-  for (int code = L1S_ERR_RANK_DEFICIENT; code <= L1S_ERR_CAPACITY; ++code)
-    if (flags & L1S_FLAG(code)) return code;
-  if (flags & L1S_FLAG(L1S_ERR_TIMEOUT)) return L1S_ERR_TIMEOUT;
-  return L1S_OK;
-}
 
 static bool stage_inputs(const Plan& pl, const void* A_host, int64_t lda, l1s_dtype dtype, const float* b_host,
                          unsigned char* w, cudaStream_t st) {
@@ -438,7 +508,7 @@ int l1_solve(const double* coreset, const double* wts, const int64_t* count, int
   const size_t o_status = take(256);
   const size_t o_part = take(sizeof(double) * static_cast<size_t>(di.sms) * (irls_entries(q) + 1));
   const size_t o_state = take(irls_state_bytes());
-  const size_t o_scr = take(sizeof(float) * static_cast<size_t>(capacity));
+  const size_t o_scr = take(solve_scratch_bytes(capacity));
   if (!ws || reinterpret_cast<uintptr_t>(ws) % 256 || ws_bytes < off)
     return set_error("workspace too small for l1_solve: %zu needed", off), L1S_ERR_WORKSPACE;
   unsigned char* w = static_cast<unsigned char*>(ws);

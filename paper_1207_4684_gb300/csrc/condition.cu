@@ -416,6 +416,7 @@ bool launch_condition(const Plan& pl, const float* pix, const l1s_params* p, dou
   if (!cuda_ok(cudaMemsetAsync(a.ticket, 0, sizeof(unsigned int), st), "reset conditioning ticket")) return false;
   cond2_kernel<0><<<grid, kGramThreads, smem, st>>>(a);
   cond2_kernel<1><<<grid, kGramThreads, smem, st>>>(a);
+  count_launch(2);
   return cuda_ok(cudaGetLastError(), "launch condition");
 }
 
@@ -445,12 +446,14 @@ bool launch_condition_householder(const Plan& pl, const float* pix, const l1s_pa
                "condition smem"))
     return false;
   condition_kernel<<<1, kCondThreads, smem, st>>>(a);
+  count_launch(1);
   return cuda_ok(cudaGetLastError(), "launch condition");
 }
 
 bool launch_pi2(const l1s_params* p, int q, double* out, cudaStream_t st) {
   const int total = q * p->r2;
   pi2_kernel<<<(total + 127) / 128, 128, 0, st>>>(make_key(p->seed), p->problem_id, total, out);
+  count_launch(1);
   return cuda_ok(cudaGetLastError(), "launch pi2");
 }
 

@@ -737,6 +737,7 @@ bool launch_fct(const Plan& pl, const void* A, int64_t lda, l1s_dtype dt, const 
   const int per = pl.r1 * pl.fct_width;
   dim3 rgrid((per + 31) / 32, pl.fct_slices);
   fct_reduce_kernel<<<rgrid, 1024, 0, st>>>(a.partials, pl.fct_ctas, pl.r1, pl.fct_width, pl.q, pix, a.flags);
+  count_launch(2);
   return cuda_ok(cudaGetLastError(), "launch fct_reduce");
 }
 

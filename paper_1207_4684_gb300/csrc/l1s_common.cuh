@@ -231,6 +231,7 @@ struct Plan {
   int fct_ctas;             // thread blocks per slice
   size_t fct_smem;
   int lam_ctas, lam_threads;
+  int lam_m_in_smem;        // 1: the λ kernel reads M from shared memory instead of the constant bank
   int smp_ctas, smp_threads;
   int64_t smp_chunk;        // rows per sampling block (multiple of 64)
   int irls_ctas;
@@ -240,6 +241,11 @@ struct Plan {
       off_stage_a, off_stage_b, total;
 };
 
-bool make_plan(const l1s_params* p, int64_t n, int d, l1s_dtype dt, bool host_staging, Plan* plan);
+bool make_plan(const l1s_params* p, int64_t n, int d, l1s_dtype dt, bool host_staging, Plan* plan,
+               const l1s_schedule* override_sch = nullptr);
+// Adds k to the process-wide count of kernels the library has launched.
+void count_launch(int k);
+// The schedule installed for (d, dt, log2 s); false (and *out zeroed) when none is.
+bool schedule_lookup(int d, l1s_dtype dt, int log2s, l1s_schedule* out);
 
 }  // namespace l1s

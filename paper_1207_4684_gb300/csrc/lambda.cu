@@ -142,15 +142,17 @@ __device__ __forceinline__ void load_row(const TA* __restrict__ p, float (&x)[D 
   }
 }
 
-template <int Q, int R2>
-__device__ __forceinline__ float lambda_of_row(const float (&x)[Q]) {
+// M is read from the constant bank (single-problem calls) or from a shared-memory copy
+// (calls that may run concurrently with other problems' λ passes).
+template <int Q, int R2, bool SMEM_M>
+__device__ __forceinline__ float lambda_of_row(const float (&x)[Q], const float* __restrict__ sM) {
   float acc[R2];
 #pragma unroll
-  for (int j = 0; j < R2; ++j) acc[j] = x[0] * c_M[j];
+  for (int j = 0; j < R2; ++j) acc[j] = x[0] * (SMEM_M ? sM[j] : c_M[j]);
 #pragma unroll
   for (int k = 1; k < Q; ++k) {
 #pragma unroll
-    for (int j = 0; j < R2; ++j) acc[j] = fmaf(x[k], c_M[k * R2 + j], acc[j]);
+    for (int j = 0; j < R2; ++j) acc[j] = fmaf(x[k], SMEM_M ? sM[k * R2 + j] : c_M[k * R2 + j], acc[j]);
   }
 #pragma unroll
   for (int j = 0; j < R2; ++j) acc[j] = fabsf(acc[j]);
@@ -159,12 +161,18 @@ __device__ __forceinline__ float lambda_of_row(const float (&x)[Q]) {
 
 // Specialised for q = D + 1 and r2 = R2 known at compile time.  The loads of a thread's
 // next row are issued before the current row is computed (software pipelining).
-template <int D, int R2, typename TA, bool VEC>
+template <int D, int R2, typename TA, bool VEC, bool SMEM_M>
 __global__ void __launch_bounds__(kLamThreads) lambda_kernel(const TA* __restrict__ A, int64_t lda,
                                                              const float* __restrict__ b, int64_t n,
                                                              float* __restrict__ lam,
-                                                             double* __restrict__ block_sums) {
+                                                             double* __restrict__ block_sums,
+                                                             const float* __restrict__ mg) {
   constexpr int Q = D + 1;
+  __shared__ float sM[SMEM_M ? Q * R2 : 1];
+  if constexpr (SMEM_M) {
+    for (int e = threadIdx.x; e < Q * R2; e += blockDim.x) sM[e] = mg[e];
+    __syncthreads();
+  }
   float s = 0.f, c = 0.f;
   const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
   int64_t row = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -182,7 +190,7 @@ __global__ void __launch_bounds__(kLamThreads) lambda_kernel(const TA* __restric
       load_row<D, TA, VEC>(A + nrow * lda, nx);
       nx[D] = -__ldg(b + nrow);
     }
-    const float med = lambda_of_row<Q, R2>(x);
+    const float med = lambda_of_row<Q, R2, SMEM_M>(x, sM);
     lam[row] = med;
     two_sum_add(s, c, med);
   }
@@ -191,11 +199,17 @@ __global__ void __launch_bounds__(kLamThreads) lambda_kernel(const TA* __restric
 }
 
 // Any q ≤ 129 and r2 ≤ R2P (columns beyond r2 are ignored by the median).
-template <int R2P, typename TA>
+template <int R2P, typename TA, bool SMEM_M>
 __global__ void __launch_bounds__(kLamThreads) lambda_kernel_generic(const TA* __restrict__ A, int64_t lda,
                                                                      const float* __restrict__ b, int64_t n,
                                                                      int d, int r2, float* __restrict__ lam,
-                                                                     double* __restrict__ block_sums) {
+                                                                     double* __restrict__ block_sums,
+                                                                     const float* __restrict__ mg) {
+  extern __shared__ float sMg[];
+  if constexpr (SMEM_M) {
+    for (int e = threadIdx.x; e < (d + 1) * r2; e += blockDim.x) sMg[e] = mg[e];
+    __syncthreads();
+  }
   float s = 0.f, c = 0.f;
   const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
   for (int64_t row = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; row < n; row += stride) {
@@ -207,7 +221,10 @@ __global__ void __launch_bounds__(kLamThreads) lambda_kernel_generic(const TA* _
       const float xk = k < d ? load_elem<TA>(p + k) : -__ldg(b + row);
 #pragma unroll
       for (int j = 0; j < R2P; ++j)
-        if (j < r2) acc[j] = (k == 0) ? xk * c_M[j] : fmaf(xk, c_M[k * r2 + j], acc[j]);
+        if (j < r2) {
+          const float m = SMEM_M ? sMg[k * r2 + j] : c_M[k * r2 + j];
+          acc[j] = (k == 0) ? xk * m : fmaf(xk, m, acc[j]);
+        }
     }
 #pragma unroll
     for (int j = 0; j < R2P; ++j) acc[j] = j < r2 ? fabsf(acc[j]) : INFINITY;
@@ -267,29 +284,30 @@ __global__ void m_to_f32_kernel(const double* __restrict__ m, int total, float* 
 }
 
 // ----------------------------------------------------------------- dispatch
-template <int DD, int RR, typename TA>
+template <int DD, int RR, typename TA, bool SM>
 static void launch_lambda_case(dim3 grid, dim3 block, cudaStream_t st, bool aligned, const TA* A, int64_t lda,
-                               const float* b, int64_t n, float* lam, double* sums) {
+                               const float* b, int64_t n, float* lam, double* sums, const float* mg) {
   if constexpr ((DD * sizeof(TA)) % 16 == 0) {
     if (aligned) {
-      lambda_kernel<DD, RR, TA, true><<<grid, block, 0, st>>>(A, lda, b, n, lam, sums);
+      lambda_kernel<DD, RR, TA, true, SM><<<grid, block, 0, st>>>(A, lda, b, n, lam, sums, mg);
       return;
     }
   }
-  lambda_kernel<DD, RR, TA, false><<<grid, block, 0, st>>>(A, lda, b, n, lam, sums);
+  lambda_kernel<DD, RR, TA, false, SM><<<grid, block, 0, st>>>(A, lda, b, n, lam, sums, mg);
 }
 
-template <typename TA>
+template <typename TA, bool SM>
 static bool launch_lambda_t(const Plan& pl, const TA* A, int64_t lda, const float* b, float* lam,
-                            double* sums, cudaStream_t st) {
+                            double* sums, const float* mg, cudaStream_t st) {
   const dim3 grid(pl.lam_ctas), block(pl.lam_threads);
   const size_t esz = sizeof(TA);
   const bool aligned = (reinterpret_cast<uintptr_t>(A) % 16 == 0) && ((lda * esz) % 16 == 0);
   const int d = pl.d, r2 = pl.r2;
-#define L1S_LAMBDA_CASE(DD, RR)                                                        \
-  if (d == DD && r2 == RR) {                                                           \
-    launch_lambda_case<DD, RR, TA>(grid, block, st, aligned, A, lda, b, pl.n, lam, sums); \
-    return cuda_ok(cudaGetLastError(), "launch lambda");                               \
+#define L1S_LAMBDA_CASE(DD, RR)                                                               \
+  if (d == DD && r2 == RR) {                                                                  \
+    launch_lambda_case<DD, RR, TA, SM>(grid, block, st, aligned, A, lda, b, pl.n, lam, sums, mg); \
+    count_launch(1);                                                                          \
+    return cuda_ok(cudaGetLastError(), "launch lambda");                                      \
   }
   L1S_LAMBDA_CASE(4, 16)
   L1S_LAMBDA_CASE(8, 16)
@@ -301,12 +319,14 @@ static bool launch_lambda_t(const Plan& pl, const TA* A, int64_t lda, const floa
   L1S_LAMBDA_CASE(32, 32)
   L1S_LAMBDA_CASE(64, 32)
 #undef L1S_LAMBDA_CASE
+  const size_t gsm = SM ? sizeof(float) * (d + 1) * r2 : 0;
   if (r2 <= 16)
-    lambda_kernel_generic<16, TA><<<grid, block, 0, st>>>(A, lda, b, pl.n, d, r2, lam, sums);
+    lambda_kernel_generic<16, TA, SM><<<grid, block, gsm, st>>>(A, lda, b, pl.n, d, r2, lam, sums, mg);
   else if (r2 <= 32)
-    lambda_kernel_generic<32, TA><<<grid, block, 0, st>>>(A, lda, b, pl.n, d, r2, lam, sums);
+    lambda_kernel_generic<32, TA, SM><<<grid, block, gsm, st>>>(A, lda, b, pl.n, d, r2, lam, sums, mg);
   else
-    lambda_kernel_generic<64, TA><<<grid, block, 0, st>>>(A, lda, b, pl.n, d, r2, lam, sums);
+    lambda_kernel_generic<64, TA, SM><<<grid, block, gsm, st>>>(A, lda, b, pl.n, d, r2, lam, sums, mg);
+  count_launch(1);
   return cuda_ok(cudaGetLastError(), "launch lambda (generic)");
 }
 
@@ -321,9 +341,10 @@ bool launch_lambda_tc(int64_t n, const void* A, const float* b, const float* m32
 bool launch_lambda(const Plan& pl, const void* A, int64_t lda, l1s_dtype dt, const float* b,
                    const float* m32, const l1s_params* p, float* lam, double* user_sum,
                    unsigned char* ws, cudaStream_t st) {
-  if (!cuda_ok(cudaMemcpyToSymbolAsync(c_M, m32, sizeof(float) * pl.q * pl.r2, 0,
-                                       cudaMemcpyDeviceToDevice, st),
-               "copy M to constant memory"))
+  const bool smem_m = pl.lam_m_in_smem != 0;
+  if (!smem_m && !cuda_ok(cudaMemcpyToSymbolAsync(c_M, m32, sizeof(float) * pl.q * pl.r2, 0,
+                                                  cudaMemcpyDeviceToDevice, st),
+                          "copy M to constant memory"))
     return false;
   double* sums = reinterpret_cast<double*>(ws + pl.off_lamsum);
   int blocks = pl.lam_ctas;
@@ -333,18 +354,25 @@ bool launch_lambda(const Plan& pl, const void* A, int64_t lda, l1s_dtype dt, con
     ok = launch_lambda_tc(pl.n, A, b, m32, reinterpret_cast<uint16_t*>(ws + pl.off_pi2), lam, sums, blocks,
                           reinterpret_cast<uint32_t*>(ws + pl.off_status), st);
   } else {
-    ok = dt == L1S_BF16
-             ? launch_lambda_t<uint16_t>(pl, static_cast<const uint16_t*>(A), lda, b, lam, sums, st)
-             : launch_lambda_t<float>(pl, static_cast<const float*>(A), lda, b, lam, sums, st);
+    if (smem_m)
+      ok = dt == L1S_BF16
+               ? launch_lambda_t<uint16_t, true>(pl, static_cast<const uint16_t*>(A), lda, b, lam, sums, m32, st)
+               : launch_lambda_t<float, true>(pl, static_cast<const float*>(A), lda, b, lam, sums, m32, st);
+    else
+      ok = dt == L1S_BF16
+               ? launch_lambda_t<uint16_t, false>(pl, static_cast<const uint16_t*>(A), lda, b, lam, sums, m32, st)
+               : launch_lambda_t<float, false>(pl, static_cast<const float*>(A), lda, b, lam, sums, m32, st);
   }
   if (!ok) return false;
   lambda_finalize_kernel<<<1, 256, 0, st>>>(sums, blocks, p->coreset_size,
                                            reinterpret_cast<StatusBlock*>(ws + pl.off_status), user_sum);
+  count_launch(1);
   return cuda_ok(cudaGetLastError(), "launch lambda_finalize");
 }
 
 bool launch_m_to_f32(const double* m, int total, float* out, cudaStream_t st) {
   m_to_f32_kernel<<<(total + 255) / 256, 256, 0, st>>>(m, total, out);
+  count_launch(1);
   return cuda_ok(cudaGetLastError(), "launch m_to_f32");
 }
 

@@ -343,6 +343,7 @@ size_t lambda_tc_smem_bytes() { return 1024 + kTcStages * kTcTileBytes + kTcBByt
 bool launch_lambda_tc(int64_t n, const void* A, const float* b, const float* m32, uint16_t* mt_bf16, float* lam,
                       double* block_sums, int blocks, uint32_t* flags, cudaStream_t st) {
   m_bf16_kernel<<<(kTcK * kTcN + 255) / 256, 256, 0, st>>>(m32, kTcK, kTcN, mt_bf16);
+  count_launch(1);
   if (!cuda_ok(cudaGetLastError(), "launch m_bf16")) return false;
   CUtensorMap mapA, mapB;
   if (!encode_bf16_2d(&mapA, A, static_cast<uint64_t>(n), kTcK, kTcK * 2, kTcTile)) return false;
@@ -361,6 +362,7 @@ bool launch_lambda_tc(int64_t n, const void* A, const float* b, const float* m32
                "lambda_tc smem"))
     return false;
   lambda_tc_kernel<<<blocks, kTcThreads, smem, st>>>(mapA, mapB, args);
+  count_launch(1);
   return cuda_ok(cudaGetLastError(), "launch lambda_tc");
 }
 

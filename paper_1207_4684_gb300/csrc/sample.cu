@@ -237,6 +237,7 @@ bool launch_sample(const Plan& pl, const float* lam, const double* p, const l1s_
   m.counts = reinterpret_cast<int64_t*>(ws + pl.off_counts);
   m.lam_pairs = (reinterpret_cast<uintptr_t>(lam) % 8 == 0) ? 1 : 0;
   sample_mark_kernel<<<pl.smp_ctas, pl.smp_threads, 0, st>>>(m);
+  count_launch(1);
   if (!cuda_ok(cudaGetLastError(), "launch sample_mark")) return false;
   StatusBlock* sb = reinterpret_cast<StatusBlock*>(ws + pl.off_status);
   if (dt == L1S_BF16) {
@@ -248,6 +249,7 @@ bool launch_sample(const Plan& pl, const float* lam, const double* p, const l1s_
                          static_cast<const float*>(A), lda, b, pl.d, idx, w, coreset, count_out, sb};
     sample_compact_kernel<float><<<pl.smp_ctas, pl.smp_threads, 0, st>>>(c);
   }
+  count_launch(1);
   return cuda_ok(cudaGetLastError(), "launch sample_compact");
 }
 
@@ -279,6 +281,7 @@ bool launch_debug_variates(const l1s_params* p, int64_t row_start, int64_t count
   debug_variates_kernel<<<static_cast<unsigned>(blocks), 256, 0, st>>>(
       make_key(p->seed), p->problem_id, static_cast<uint32_t>(p->r1), row_start, count, bh, bi, kh, ki,
       ch, ci, sg, ub);
+  count_launch(1);
   return cuda_ok(cudaGetLastError(), "launch debug_variates");
 }
 

@@ -7,14 +7,15 @@
 //   x ← argmin Σ_k ω_k r_k²,  ω_k = w_k / max(|r_k|, η),  η = 10⁻⁶·Σ w|r| / Σ w,
 // starting from ω = w.  The iterate with the smallest objective is kept; the
 // loop stops early once the objective changes by less than 10⁻¹² relative.
-// An ℓ1 optimum is attained where d residuals vanish, so the result is then
-// polished: the d rows with the smallest |r_k| are solved exactly and the
-// vertex replaces the iterate when its objective is not larger.
+// An ℓ1 optimum is attained at a vertex where d residuals vanish, so the result
+// is then finished by simplex pivots of the LAD linear program, starting from the
+// d rows with the smallest |r_k|, until the dual multipliers certify the vertex
+// optimal; the vertex replaces the iterate when its objective is not larger.
 //
 // Kernels: irls_accum (many blocks: objective and the weighted normal
 // equations, per-block partials), irls_step (one block: fixed-order sum,
 // Cholesky solve, bookkeeping), irls_residuals (many blocks), irls_polish (one
-// block), objective (many blocks + fixed-order finish).  A device flag turns
+// block: the vertex finish), objective (many blocks + fixed-order finish).  A device flag turns
 // the remaining iterations into no-ops after convergence, so the whole solve is
 // enqueued without host synchronisation.
 #include "l1s_common.cuh"
@@ -253,20 +254,133 @@ __global__ void irls_residuals_kernel(const IrlsArgs a) {
   }
 }
 
-// One block: pick the d rows with the smallest |r|, solve them exactly, keep the better point.
+// ----------------------------------------------------------------- vertex finish
+// Block-parallel dense LU (partial pivoting) of the d × d matrix B of the active
+// rows, and the two triangular solves a simplex pivot needs (B·v = rhs and
+// Bᵀ·v = rhs).  Row i of P·B is row perm[i] of B.
+__device__ bool block_lu(double* LU, int* perm, int d, int* s_ok) {
+  const int tid = threadIdx.x;
+  for (int c = 0; c < d; ++c) {
+    if (tid == 0) {
+      int piv = c;
+      for (int r = c + 1; r < d; ++r)
+        if (fabs(LU[r * d + c]) > fabs(LU[piv * d + c])) piv = r;
+      if (!(fabs(LU[piv * d + c]) > 0.0)) {
+        *s_ok = 0;
+      } else if (piv != c) {
+        for (int j = 0; j < d; ++j) {
+          const double t = LU[c * d + j];
+          LU[c * d + j] = LU[piv * d + j];
+          LU[piv * d + j] = t;
+        }
+        const int t = perm[c];
+        perm[c] = perm[piv];
+        perm[piv] = t;
+      }
+    }
+    __syncthreads();
+    if (!*s_ok) return false;
+    for (int r = c + 1 + tid; r < d; r += blockDim.x) LU[r * d + c] /= LU[c * d + c];
+    __syncthreads();
+    const int w = d - c - 1;
+    for (int e = tid; e < w * w; e += blockDim.x) {
+      const int r = c + 1 + e / w, j = c + 1 + e % w;
+      LU[r * d + j] = fma(-LU[r * d + c], LU[c * d + j], LU[r * d + j]);
+    }
+    __syncthreads();
+  }
+  return true;
+}
+
+// v ← B⁻¹·v (transposed = false) or B⁻ᵀ·v (transposed = true); tmp holds d doubles.
+__device__ void block_lu_solve(const double* LU, const int* perm, int d, double* v, double* tmp,
+                               bool transposed) {
+  const int tid = threadIdx.x;
+  if (!transposed) {
+    for (int i = tid; i < d; i += blockDim.x) tmp[i] = v[perm[i]];
+    __syncthreads();
+    for (int r = 0; r < d; ++r) {          // L (unit lower)
+      for (int k = r + 1 + tid; k < d; k += blockDim.x) tmp[k] = fma(-LU[k * d + r], tmp[r], tmp[k]);
+      __syncthreads();
+    }
+    for (int r = d - 1; r >= 0; --r) {     // U
+      if (tid == 0) tmp[r] /= LU[r * d + r];
+      __syncthreads();
+      for (int k = tid; k < r; k += blockDim.x) tmp[k] = fma(-LU[k * d + r], tmp[r], tmp[k]);
+      __syncthreads();
+    }
+    for (int i = tid; i < d; i += blockDim.x) v[i] = tmp[i];
+  } else {
+    for (int i = tid; i < d; i += blockDim.x) tmp[i] = v[i];
+    __syncthreads();
+    for (int r = 0; r < d; ++r) {          // Uᵀ (lower, diagonal of U)
+      if (tid == 0) tmp[r] /= LU[r * d + r];
+      __syncthreads();
+      for (int k = r + 1 + tid; k < d; k += blockDim.x) tmp[k] = fma(-LU[r * d + k], tmp[r], tmp[k]);
+      __syncthreads();
+    }
+    for (int r = d - 1; r >= 0; --r) {     // Lᵀ (unit upper)
+      for (int k = tid; k < r; k += blockDim.x) tmp[k] = fma(-LU[r * d + k], tmp[r], tmp[k]);
+      __syncthreads();
+    }
+    for (int i = tid; i < d; i += blockDim.x) v[perm[i]] = tmp[i];
+  }
+  __syncthreads();
+}
+
+// Fixed-order block sum of one value per thread (thread 0's result is broadcast).
+__device__ double block_sum(double v, double* red) {
+  red[threadIdx.x] = v;
+  __syncthreads();
+  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+    if (static_cast<int>(threadIdx.x) < h) red[threadIdx.x] += red[threadIdx.x + h];
+    __syncthreads();
+  }
+  const double t = red[0];
+  __syncthreads();
+  return t;
+}
+
+constexpr int kMaxPivots = 64;
+
+// One block.  Start from the d coreset rows with the smallest |r| at the best IRLS
+// iterate, and walk vertex to vertex (simplex pivots of the LAD linear program):
+// at a vertex with active rows Z (r_Z = 0) and B = A_Z, the objective along the edge
+// that frees active row j is, to first order, sgn·y_j + w_{Z_j} with y = B⁻ᵀ·c and
+// c = Σ_{i∉Z} w_i sign(r_i)·A_i.  The vertex is optimal when |y_j| ≤ w_{Z_j} for
+// every j (the multipliers −y certify it); otherwise step along the steepest such
+// edge to the minimiser of the piecewise-linear objective on it (a weighted median
+// of the breakpoints −r_i/g_i, found by bisection on their bit patterns), where the
+// row with that breakpoint enters Z.  The better of this vertex and the IRLS iterate
+// is returned.
 __global__ void __launch_bounds__(kIrlsThreads) irls_polish_kernel(const IrlsArgs a) {
   extern __shared__ __align__(16) double sm[];
-  const int q = a.q, d = a.d, tid = threadIdx.x;
-  double* Mx = sm;               // d × (d + 1) augmented system
-  double* xp = Mx + d * (d + 1); // q
+  const int q = a.q, d = a.d, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nwarps = blockDim.x >> 5;
+  double* LU = sm;                 // d × d
+  double* xs = LU + d * d;         // q: current vertex
+  double* xb = xs + q;             // q: best vertex
+  double* cv = xb + q;             // d: c, then y
+  double* dv = cv + d;             // d: edge direction
+  double* tmp = dv + d;            // d
+  int64_t* Z = reinterpret_cast<int64_t*>(tmp + d);  // d active rows
+  int* perm = reinterpret_cast<int*>(Z + d);         // d
   __shared__ float rv[kIrlsThreads];
   __shared__ int64_t ri[kIrlsThreads];
   __shared__ double red[kIrlsThreads];
-  __shared__ int s_ok;
+  __shared__ int s_ok, s_more, s_j, s_certified;
+  __shared__ double s_sgn, s_h, s_fb;
   const int64_t S = coreset_rows(a);
+  double* rs = reinterpret_cast<double*>(a.scratch);   // S doubles: r, then breakpoints
+  double* vs = rs + a.capacity;                        // S doubles: breakpoint weights
   IrlsState* st = a.state;
-  if (tid == 0) s_ok = S >= d ? 1 : 0;
+  if (tid == 0) {
+    s_ok = S >= d ? 1 : 0;
+    s_certified = 0;
+    s_fb = INFINITY;
+  }
   __syncthreads();
+  // The d rows with the smallest |r| at the IRLS iterate (the float |r| sit in scratch).
   for (int k = 0; k < d && s_ok; ++k) {
     float best = INFINITY;
     int64_t bi = -1;
@@ -292,66 +406,140 @@ __global__ void __launch_bounds__(kIrlsThreads) irls_polish_kernel(const IrlsArg
         s_ok = 0;
       } else {
         a.scratch[idx] = INFINITY;
-        for (int j = 0; j < d; ++j) Mx[k * (d + 1) + j] = a.X[idx * q + j];
-        Mx[k * (d + 1) + d] = -a.X[idx * q + d];  // b
+        Z[k] = idx;
       }
     }
     __syncthreads();
-  }
-  if (tid == 0 && s_ok) {
-    // Gaussian elimination with partial pivoting.
-    for (int c = 0; c < d && s_ok; ++c) {
-      int piv = c;
-      for (int r = c + 1; r < d; ++r)
-        if (fabs(Mx[r * (d + 1) + c]) > fabs(Mx[piv * (d + 1) + c])) piv = r;
-      if (!(fabs(Mx[piv * (d + 1) + c]) > 0.0)) {
-        s_ok = 0;
-        break;
-      }
-      if (piv != c)
-        for (int j = 0; j <= d; ++j) {
-          const double t = Mx[c * (d + 1) + j];
-          Mx[c * (d + 1) + j] = Mx[piv * (d + 1) + j];
-          Mx[piv * (d + 1) + j] = t;
-        }
-      for (int r = c + 1; r < d; ++r) {
-        const double f = Mx[r * (d + 1) + c] / Mx[c * (d + 1) + c];
-        for (int j = c; j <= d; ++j) Mx[r * (d + 1) + j] -= f * Mx[c * (d + 1) + j];
-      }
-    }
-    if (s_ok) {
-      for (int r = d - 1; r >= 0; --r) {
-        double v = Mx[r * (d + 1) + d];
-        for (int j = r + 1; j < d; ++j) v -= Mx[r * (d + 1) + j] * xp[j];
-        xp[r] = v / Mx[r * (d + 1) + r];
-      }
-      xp[d] = 1.0;
-      for (int j = 0; j < d; ++j) s_ok &= isfinite(xp[j]) ? 1 : 0;
-    }
   }
   __syncthreads();
-  double fp = INFINITY;
-  if (s_ok) {
-    double acc = 0.0;
-    for (int64_t k = tid; k < S; k += blockDim.x) {
-      double r = 0.0;
-      for (int j = 0; j < q; ++j) r = fma(a.X[k * q + j], xp[j], r);
-      acc += a.w[k] * fabs(r);
+
+  for (int piv = 0; piv < kMaxPivots && s_ok; ++piv) {
+    // Vertex of the active rows: B·x = b_Z with B = A_Z (first d columns of X_Z), b = −X_{:,d}.
+    for (int e = tid; e < d * d; e += blockDim.x) LU[e] = a.X[Z[e / d] * q + e % d];
+    for (int i = tid; i < d; i += blockDim.x) {
+      perm[i] = i;
+      xs[i] = -a.X[Z[i] * q + d];
     }
-    red[tid] = acc;
+    __syncthreads();
+    if (!block_lu(LU, perm, d, &s_ok)) break;
+    block_lu_solve(LU, perm, d, xs, tmp, false);
+    if (tid == 0) {
+      xs[d] = 1.0;
+      for (int j = 0; j < d; ++j) s_ok &= isfinite(xs[j]) ? 1 : 0;
+    }
+    __syncthreads();
+    if (!s_ok) break;
+    // Residuals and objective; active rows are exactly on the vertex.
+    double facc = 0.0;
+    for (int64_t i = tid; i < S; i += blockDim.x) {
+      double r = 0.0;
+      for (int k = 0; k < q; ++k) r = fma(a.X[i * q + k], xs[k], r);
+      rs[i] = r;
+      facc += a.w[i] * fabs(r);
+    }
+    const double f = block_sum(facc, red);
+    for (int i = tid; i < d; i += blockDim.x) rs[Z[i]] = 0.0;
+    if (!(f < s_fb)) break;   // no further decrease (rounding): keep the best vertex
+    for (int k = tid; k < q; k += blockDim.x) xb[k] = xs[k];
+    __syncthreads();
+    if (tid == 0) s_fb = f;
+    // c_k = Σ_{i∉Z} w_i·sign(r_i)·A_ik, one warp per column, lanes over rows.
+    for (int k = warp; k < d; k += nwarps) {
+      double acc = 0.0;
+      for (int64_t i = lane; i < S; i += 32) {
+        const double r = rs[i];
+        const double sg = r > 0.0 ? 1.0 : (r < 0.0 ? -1.0 : 0.0);
+        acc = fma(a.w[i] * sg, a.X[i * q + k], acc);
+      }
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if (lane == 0) cv[k] = acc;
+    }
+    __syncthreads();
+    block_lu_solve(LU, perm, d, cv, tmp, true);   // y = B⁻ᵀ·c
+    if (tid == 0) {
+      int jb = -1;
+      double worst = 0.0;
+      for (int j = 0; j < d; ++j) {
+        const double wz = a.w[Z[j]];
+        const double slope = wz - fabs(cv[j]);
+        if (slope < -1e-12 * (wz + fabs(cv[j])) && slope < worst) {
+          worst = slope;
+          jb = j;
+        }
+      }
+      s_more = jb >= 0 ? 1 : 0;
+      if (jb < 0) s_certified = 1;
+      s_j = jb;
+      s_sgn = jb >= 0 ? (cv[jb] > 0.0 ? -1.0 : 1.0) : 0.0;
+      s_h = -0.5 * worst;
+    }
+    __syncthreads();
+    if (!s_more) break;
+    // Edge direction: B·dv = sgn·e_j.
+    for (int i = tid; i < d; i += blockDim.x) dv[i] = i == s_j ? s_sgn : 0.0;
+    __syncthreads();
+    block_lu_solve(LU, perm, d, dv, tmp, false);
+    // Breakpoints t_i = −r_i/g_i > 0 with weights w_i·|g_i| (others: +inf, weight 0).
+    for (int64_t i = tid; i < S; i += blockDim.x) {
+      double g = 0.0;
+      for (int k = 0; k < d; ++k) g = fma(a.X[i * q + k], dv[k], g);
+      double t = g != 0.0 ? -rs[i] / g : 0.0;
+      const bool live = t > 0.0 && isfinite(t);
+      rs[i] = live ? t : INFINITY;
+      vs[i] = live ? a.w[i] * fabs(g) : 0.0;
+    }
+    __syncthreads();
+    // Smallest breakpoint T with Σ_{t_i ≤ T} w_i|g_i| ≥ h: bisection on the bit patterns
+    // of positive doubles (their order is the order of the values).
+    long long lo = 0, hi = 0x7FF0000000000000LL;
+    {
+      double wtot = 0.0;
+      for (int64_t i = tid; i < S; i += blockDim.x) wtot += vs[i];
+      if (!(block_sum(wtot, red) >= s_h)) break;   // no finite minimiser on this edge
+    }
+    while (lo < hi) {
+      const long long mid = lo + (hi - lo) / 2;
+      const double T = __longlong_as_double(mid);
+      double acc = 0.0;
+      for (int64_t i = tid; i < S; i += blockDim.x)
+        if (rs[i] <= T) acc += vs[i];
+      if (block_sum(acc, red) >= s_h)
+        hi = mid;
+      else
+        lo = mid + 1;
+    }
+    const double T = __longlong_as_double(lo);
+    int64_t enter = S;
+    for (int64_t i = tid; i < S; i += blockDim.x)
+      if (rs[i] == T) {
+        enter = i;
+        break;
+      }
+    ri[tid] = enter;
     __syncthreads();
     if (tid == 0) {
-      fp = 0.0;
-      for (int t = 0; t < static_cast<int>(blockDim.x); ++t) fp += red[t];
+      int64_t k = S;
+      for (int t = 0; t < static_cast<int>(blockDim.x); ++t) k = ri[t] < k ? ri[t] : k;
+      if (k >= S) s_ok = 0;
+      else Z[s_j] = k;
     }
+    __syncthreads();
   }
+  __syncthreads();
   if (tid == 0) {
-    const bool use = s_ok && fp <= st->best_f;
-    for (int j = 0; j < d; ++j) a.x_out[j] = use ? xp[j] : st->best_x[j];
-    if (a.obj_out) *a.obj_out = use ? fp : st->best_f;
-    if (!a.status->irls_done) raise_flag(&a.status->flags, L1S_ERR_NOT_CONVERGED);
+    const bool use = isfinite(s_fb) && s_fb <= st->best_f;
+    for (int j = 0; j < d; ++j) a.x_out[j] = use ? xb[j] : st->best_x[j];
+    if (a.obj_out) *a.obj_out = use ? s_fb : st->best_f;
+    if (!a.status->irls_done && !(use && s_certified)) raise_flag(&a.status->flags, L1S_ERR_NOT_CONVERGED);
   }
 }
+
+size_t polish_smem_bytes(int d) {
+  const int q = d + 1;
+  return sizeof(double) * (static_cast<size_t>(d) * d + 2 * q + 3 * d) + sizeof(int64_t) * d + sizeof(int) * d;
+}
+
+size_t solve_scratch_bytes(int64_t capacity) { return 2 * sizeof(double) * static_cast<size_t>(capacity); }
 
 int irls_entries(int q) { return q * (q + 1) / 2 + 1; }
 size_t irls_state_bytes() { return sizeof(IrlsState); }
@@ -376,7 +564,7 @@ bool launch_solve(const double* X, const double* w, const int64_t* count, int64_
   const int q = d + 1;
   const size_t acc_smem = sizeof(double) * (kIrlsTile * q + kIrlsTile + q);
   const size_t step_smem = sizeof(double) * (irls_entries(q) + d * d + d);
-  const size_t pol_smem = sizeof(double) * (d * (d + 1) + q);
+  const size_t pol_smem = polish_smem_bytes(d);
   if (!cuda_ok(cudaFuncSetAttribute(irls_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     static_cast<int>(step_smem)),
                "irls_step smem") ||
@@ -397,6 +585,7 @@ bool launch_solve(const double* X, const double* w, const int64_t* count, int64_
   irls_step_kernel<<<1, kIrlsThreads, step_smem, st>>>(a, nblocks, 1);
   irls_residuals_kernel<<<nblocks, 256, 0, st>>>(a);
   irls_polish_kernel<<<1, kIrlsThreads, pol_smem, st>>>(a);
+  count_launch(2 * max_iter + 5);
   return cuda_ok(cudaGetLastError(), "launch l1_solve kernels");
 }
 
@@ -449,6 +638,7 @@ bool launch_objective(const void* A, int64_t lda, l1s_dtype dt, const float* b, 
     objective_kernel<float><<<nblocks, 256, 0, st>>>(static_cast<const float*>(A), lda, b, n, d, x,
                                                     partials);
   sum_partials_kernel<<<1, 256, 0, st>>>(partials, nblocks, out);
+  count_launch(2);
   return cuda_ok(cudaGetLastError(), "launch objective");
 }
 

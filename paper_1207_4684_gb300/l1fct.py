@@ -44,6 +44,21 @@ def make_params(s: int, r1: int, r2: int, coreset: float, seed: int = 0, problem
     return Params(seed, problem_id, s, r1, r2, float(coreset), global_row_offset, int(bool(sign_flip)), 0)
 
 
+class Schedule(C.Structure):
+    _fields_ = [("fct_variant", C.c_int32), ("fct_ctas_per_sm", C.c_int32), ("lam_ctas_per_sm", C.c_int32),
+                ("smp_chunks_per_sm", C.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class Problem(C.Structure):
+    _fields_ = [("A_dev", C.c_void_p), ("b_dev", C.c_void_p), ("lda", C.c_int64), ("n", C.c_int64),
+                ("d", C.c_int32), ("dtype", C.c_int32), ("params", Params), ("capacity", C.c_int64),
+                ("idx_dev", C.c_void_p), ("w_dev", C.c_void_p), ("coreset_dev", C.c_void_p),
+                ("count_dev", C.c_void_p), ("x_dev", C.c_void_p), ("objective_dev", C.c_void_p)]
+
+
 _lib = None
 _P = C.c_void_p
 _I64 = C.c_int64
@@ -54,6 +69,7 @@ _PP = C.POINTER(Params)
 _SIGS = {
     "l1s_last_error": (C.c_char_p, []),
     "l1s_version": (C.c_char_p, []),
+    "l1s_kernel_launches": (C.c_uint64, []),
     "l1s_workspace_size": (C.c_int, [_PP, _I64, _I32, C.c_int, _I32, C.POINTER(_SZ)]),
     "l1s_status_reset": (C.c_int, [_P, _SZ, _P]),
     "l1s_status_read": (C.c_int, [_P, _SZ, _P, C.POINTER(C.c_uint32)]),
@@ -71,6 +87,12 @@ _SIGS = {
     "l1s_debug_variates": (C.c_int, [_PP, _I64, _I64, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "l1s_debug_pi2": (C.c_int, [_PP, _I32, _P, _P]),
     "l1_lambda_noalloc": (C.c_int, [_P, _I64, C.c_int, _P, _I64, _I32, _P, _PP, _P, _P, _P]),
+    "l1s_schedule_set": (C.c_int, [_I32, C.c_int, _I32, C.POINTER(Schedule)]),
+    "l1s_schedule_get": (C.c_int, [_I32, C.c_int, _I32, C.POINTER(Schedule)]),
+    "l1s_autotune": (C.c_int, [C.POINTER(Problem), _I32, C.POINTER(Schedule), C.POINTER(C.c_double), _P, _SZ,
+                               _P]),
+    "l1s_batched_workspace_size": (C.c_int, [C.POINTER(Problem), _I32, C.POINTER(_SZ)]),
+    "l1_regress_batched": (C.c_int, [C.POINTER(Problem), _I32, _P, _P, _SZ, _P]),
 }
 EXPORTS = tuple(_SIGS)
 
@@ -128,6 +150,10 @@ def _matrix(A: torch.Tensor):
 
 def version() -> str:
     return load().l1s_version().decode()
+
+
+def l1s_kernel_launches() -> int:
+    return int(load().l1s_kernel_launches())
 
 
 def l1s_workspace_size(params: Params, n: int, d: int, dtype: int = F32, host_staging: bool = False) -> int:
@@ -251,3 +277,54 @@ def l1_lambda_noalloc(A, b, M, params: Params, lam, lam_sum, stream=None) -> Non
     n, d, lda, dt = _matrix(A)
     _check(load().l1_lambda_noalloc(_ptr(A, False), lda, dt, _ptr(b), n, d, _ptr(M), C.byref(params), _ptr(lam),
                                     _ptr(lam_sum), _stream(stream)), "l1_lambda_noalloc")
+
+
+def make_problem(A, b, params: Params, capacity: int = 0, idx=None, w=None, coreset=None, count=None, x=None,
+                 objective=None) -> Problem:
+    """One member of a batch; the caller keeps every tensor alive while the batch runs."""
+    n, d, lda, dt = _matrix(A)
+    return Problem(_ptr(A, False), _ptr(b), lda, n, d, dt, params, capacity, _ptr(idx), _ptr(w), _ptr(coreset),
+                   _ptr(count), _ptr(x), _ptr(objective))
+
+
+def _problem_array(problems):
+    arr = (Problem * len(problems))(*problems)
+    return arr
+
+
+def l1s_batched_workspace_size(problems) -> int:
+    out = _SZ(0)
+    _check(load().l1s_batched_workspace_size(_problem_array(problems), len(problems), C.byref(out)),
+           "l1s_batched_workspace_size")
+    return out.value
+
+
+def batched_workspace(problems, device=None) -> torch.Tensor:
+    return torch.empty(l1s_batched_workspace_size(problems), dtype=torch.uint8, device=device or "cuda")
+
+
+def l1_regress_batched(problems, ws, flags=None, stream=None) -> None:
+    _check(load().l1_regress_batched(_problem_array(problems), len(problems), _ptr(flags), _ptr(ws), ws.numel(),
+                                     _stream(stream)), "l1_regress_batched")
+
+
+def l1s_schedule_set(d: int, dtype: int, s: int, schedule: Schedule | dict | None) -> None:
+    if isinstance(schedule, dict):
+        schedule = Schedule(**schedule)
+    _check(load().l1s_schedule_set(d, dtype, s, C.byref(schedule) if schedule is not None else None),
+           "l1s_schedule_set")
+
+
+def l1s_schedule_get(d: int, dtype: int, s: int) -> dict:
+    out = Schedule()
+    _check(load().l1s_schedule_get(d, dtype, s, C.byref(out)), "l1s_schedule_get")
+    return out.as_dict()
+
+
+def l1s_autotune(problem: Problem, ws, trials: int = 5, stream=None):
+    """Returns (the installed schedule as a dict, its median coreset-pass time in ms)."""
+    best = Schedule()
+    ms = C.c_double(0.0)
+    _check(load().l1s_autotune(C.byref(problem), trials, C.byref(best), C.byref(ms), _ptr(ws), ws.numel(),
+                               _stream(stream)), "l1s_autotune")
+    return best.as_dict(), ms.value

@@ -159,6 +159,11 @@ def make_problem(w: Workload | str, n: int | None = None, seed: int | None = Non
     return {"A": A, "b": b, "x_star": x_star, "w": w}
 
 
+def batched_block_size(d: int) -> int:
+    """Hadamard block size of a batch member: the power of two at or above r1, within [64, 1024]."""
+    return min(1024, max(64, 1 << int(math.ceil(math.log2(r1_for(d))))))
+
+
 def make_batched_problems(count: int = 256, seed: int = 0,
                           log2n_range=(12.0, 20.0), dims=(4, 8, 16, 32, 64),
                           r2: int = 16, coreset: float = 2000.0) -> list[dict]:
@@ -166,14 +171,15 @@ def make_batched_problems(count: int = 256, seed: int = 0,
 
     n is log-uniform on [2^12, 2^20], d uniform over {4, 8, 16, 32, 64}; the
     design is Gaussian and the noise Laplace with 5% Cauchy(0,100) outliers.
-    Each problem gets its own data seed and problem id.
+    Each problem gets its own data seed and problem id; s follows
+    batched_block_size(d).
     """
     rng = np.random.Generator(np.random.PCG64(seed))
     out = []
     for p in range(count):
         n = int(round(2.0 ** rng.uniform(*log2n_range)))
         d = int(rng.choice(dims))
-        s = 1 << max(1, int(math.ceil(math.log2(max(r1_for(d), 2)))))
+        s = batched_block_size(d)
         w = Workload(f"batched_{p}", n, d, s, r2, coreset, "f32", "gauss",
                      "laplace_outliers", seed=seed * 100003 + p + 1, problem_id=p)
         out.append(make_problem(w))

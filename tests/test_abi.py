@@ -44,24 +44,37 @@ def test_every_declared_symbol_is_exported(lib):
         assert hasattr(lib, name)
 
 
-def test_params_struct_layout(tmp_path):
-    """The ctypes Params mirrors l1s_params byte for byte (checked with the C compiler)."""
+@pytest.mark.parametrize("cname,pyname", [("l1s_params", "Params"), ("l1s_schedule", "Schedule"),
+                                          ("l1s_problem", "Problem")])
+def test_struct_layout(tmp_path, cname, pyname):
+    """Each ctypes structure mirrors its C struct byte for byte (checked with the C compiler)."""
     import ctypes
 
-    from paper_1207_4684_gb300.l1fct import Params
+    from paper_1207_4684_gb300 import l1fct
 
+    cls = getattr(l1fct, pyname)
+    fields = [f for f, _ in cls._fields_]
+    fmt = " ".join(["%zu"] * (len(fields) + 1))
+    offs = ", ".join(f"offsetof({cname},{f})" for f in fields)
     src = tmp_path / "layout.c"
     src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "l1fct.h"\nint main(void){'
-                   'printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(l1s_params),'
-                   'offsetof(l1s_params,seed), offsetof(l1s_params,problem_id), offsetof(l1s_params,s),'
-                   'offsetof(l1s_params,r1), offsetof(l1s_params,r2), offsetof(l1s_params,coreset_size),'
-                   'offsetof(l1s_params,global_row_offset), offsetof(l1s_params,sign_flip),'
-                   'offsetof(l1s_params,reserved)); return 0;}\n')
+                   f'printf("{fmt}\\n", sizeof({cname}), {offs}); return 0;}}\n')
     exe = tmp_path / "layout"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
     got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True).stdout.split()]
-    want = [ctypes.sizeof(Params)] + [getattr(Params, f).offset for f, _ in Params._fields_]
+    want = [ctypes.sizeof(cls)] + [getattr(cls, f).offset for f in fields]
     assert got == want
+
+
+def test_schedule_table_argument_checks(lib):
+    import paper_1207_4684_gb300 as L
+
+    with pytest.raises(L.L1SError) as e:
+        L.l1s_schedule_set(16, L.F32, 48, {"fct_variant": 1})
+    assert e.value.code == 1
+    with pytest.raises(L.L1SError) as e:
+        L.l1s_schedule_set(16, L.F32, 256, {"fct_variant": 7})
+    assert e.value.code == 1 and "out of range" in str(e.value)
 
 
 def test_version_and_argument_errors_without_gpu(lib):
