@@ -17,10 +17,14 @@ namespace l1s {
 const void* fct_kernel(int log2s, l1s_dtype dt, bool staged);
 size_t fct_smem_bytes(int s, int d, l1s_dtype dt, int r1, int width, bool staged);
 int fct_threads_for(int log2s, int width);
-bool fct_t16_applies(int log2s, int d);
-const void* fct_t16_kernel(int log2s, l1s_dtype dt);
-int fct_t16_threads();
-size_t fct_t16_smem_bytes(int s, int d, l1s_dtype dt, int r1);
+int fct_ws_width(int log2s, int d);
+const void* fct_ws_kernel(int log2s, l1s_dtype dt, int w);
+int fct_ws_threads(int w);
+size_t fct_ws_smem_bytes(int s, int d, l1s_dtype dt, int r1, int w);
+int fct_sorted_width(int log2s, int d);
+const void* fct_sorted_kernel(int log2s, l1s_dtype dt, int w);
+int fct_sorted_threads(int w);
+size_t fct_sorted_smem_bytes(int s, int d, l1s_dtype dt, int r1, int w);
 bool launch_fct(const Plan& pl, const void* A, int64_t lda, l1s_dtype dt, const float* b,
                 const l1s_params* p, float* pix, unsigned char* ws, cudaStream_t st);
 bool launch_condition(const Plan& pl, const float* pix, const l1s_params* p, double* R_user,
@@ -156,7 +160,9 @@ int coreset_impl(const Plan& pl, const void* A, int64_t lda, l1s_dtype dtype, co
 // shared memory, threads, and the resident blocks per SM that occupancy allows.
 struct FctGeometry {
   bool ok;
-  bool t16, staged;
+  bool staged;
+  int ws;                 // column width of the narrow-X kernel, 0 otherwise
+  int sorted;             // column width of the bucket-sorted kernel, 0 otherwise
   int slices, width, threads, per_sm;
   size_t smem;
 };
@@ -167,9 +173,15 @@ static FctGeometry fct_geometry(int variant, const Plan& P, l1s_dtype dt, const 
   const size_t budget1 = di.max_smem_optin;
   int width = P.q;
   bool staged = false;
-  if (variant == 1) {
-    if (!fct_t16_applies(P.log2s, P.d) || fct_t16_smem_bytes(P.s, P.d, dt, P.r1) > budget1) return g;
-    g.t16 = true;
+  if (variant == 4) {
+    const int w = fct_sorted_width(P.log2s, P.d);
+    if (!w || fct_sorted_smem_bytes(P.s, P.d, dt, P.r1, w) > budget1) return g;
+    g.sorted = w;
+    staged = true;
+  } else if (variant == 1) {
+    const int w = fct_ws_width(P.log2s, P.d);
+    if (!w || fct_ws_smem_bytes(P.s, P.d, dt, P.r1, w) > budget1) return g;
+    g.ws = w;
     staged = true;
   } else if (variant == 2) {
     if (fct_smem_bytes(P.s, P.d, dt, P.r1, P.q, true) > budget1) return g;
@@ -193,9 +205,11 @@ static FctGeometry fct_geometry(int variant, const Plan& P, l1s_dtype dt, const 
   g.staged = staged;
   g.slices = (P.q + width - 1) / width;
   g.width = width;
-  g.smem = g.t16 ? fct_t16_smem_bytes(P.s, P.d, dt, P.r1) : fct_smem_bytes(P.s, P.d, dt, P.r1, width, staged);
-  g.threads = g.t16 ? fct_t16_threads() : fct_threads_for(P.log2s, width);
-  const void* fn = g.t16 ? fct_t16_kernel(P.log2s, dt) : fct_kernel(P.log2s, dt, staged);
+  g.smem = g.sorted ? fct_sorted_smem_bytes(P.s, P.d, dt, P.r1, g.sorted)
+                    : (g.ws ? fct_ws_smem_bytes(P.s, P.d, dt, P.r1, g.ws) : fct_smem_bytes(P.s, P.d, dt, P.r1, width, staged));
+  g.threads = g.sorted ? fct_sorted_threads(g.sorted) : (g.ws ? fct_ws_threads(g.ws) : fct_threads_for(P.log2s, width));
+  const void* fn = g.sorted ? fct_sorted_kernel(P.log2s, dt, g.sorted)
+                            : (g.ws ? fct_ws_kernel(P.log2s, dt, g.ws) : fct_kernel(P.log2s, dt, staged));
   if (!cuda_ok(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(g.smem)),
                "cudaFuncSetAttribute(fct_embed)"))
     return g;
@@ -239,15 +253,18 @@ bool make_plan(const l1s_params* p, int64_t n, int d, l1s_dtype dt, bool host_st
   else
     schedule_lookup(d, dt, P.log2s, &sch);
 
-  // Phase 1.  Default: the warp-specialised narrow-X kernel where it applies, else all
-  // q columns in one block with TMA-staged X tiles, else direct loads over column slices.
-  FctGeometry geo[4];
-  for (int v = 1; v <= 3; ++v) geo[v] = fct_geometry(v, P, dt, di);
+  // Phase 1.  Default: the warp-specialised narrow-X kernel where it applies, else all q
+  // columns in one block with TMA-staged X tiles, else direct loads over column slices.
+  // The bucket-sorted kernel is a schedule choice (slower than the narrow-X kernel on the
+  // shapes measured so far).
+  FctGeometry geo[5];
+  for (int v = 1; v <= 4; ++v) geo[v] = fct_geometry(v, P, dt, di);
   if (!geo[3].ok) return set_error("r1 and s too large for shared memory"), false;
   int variant = geo[1].ok ? 1 : (geo[2].ok ? 2 : 3);
-  if (sch.fct_variant >= 1 && sch.fct_variant <= 3 && geo[sch.fct_variant].ok) variant = sch.fct_variant;
+  if (sch.fct_variant >= 1 && sch.fct_variant <= 4 && geo[sch.fct_variant].ok) variant = sch.fct_variant;
   const FctGeometry& g = geo[variant];
-  P.fct_t16 = g.t16 ? 1 : 0;
+  P.fct_ws = g.ws;
+  P.fct_sorted = g.sorted;
   P.fct_staged = g.staged ? 1 : 0;
   P.fct_slices = g.slices;
   P.fct_width = g.width;
@@ -257,7 +274,7 @@ bool make_plan(const l1s_params* p, int64_t n, int d, l1s_dtype dt, bool host_st
   P.fct_ctas = static_cast<int>(fct_ctas_of(g, P, di, per_sm));
   // Partial sums sized for the largest variant at full occupancy.
   size_t partial_floats = 0;
-  for (int v = 1; v <= 3; ++v)
+  for (int v = 1; v <= 4; ++v)
     if (geo[v].ok)
       partial_floats = std::max<size_t>(
           partial_floats, static_cast<size_t>(geo[v].slices) * fct_ctas_of(geo[v], P, di, geo[v].per_sm) *

@@ -292,10 +292,12 @@ __global__ void __launch_bounds__(kFctMaxThreads) fct_embed_kernel(const FctArgs
   for (int i = threadIdx.x; i < a.r1 * W; i += blockDim.x) out[i] = part[i];
 }
 
-// ----------------------------------------------------------------- d ≤ 16, 32 ≤ s ≤ 512
+// ----------------------------------------------------------------- d ≤ 32, 32 ≤ s ≤ 512
 // A dedicated kernel for narrow X, where the generic kernel is bound by shared-memory
 // bank conflicts and per-element draw loads.  It is warp-specialised and software
-// pipelined over the s-row blocks of a thread block:
+// pipelined over the s-row blocks of a thread block.  W = 16 (d ≤ 16) is described
+// below; W = 32 (16 < d ≤ 32) has 16 A warps whose lanes are the 32 columns of one row
+// (pass 1 over row bits 0-3, pass 2 over bits 4 and up) and a single copy of P.
 //  * 4 producer warps compute the draws of block i into one of two draw buffers while
 //    the consumers work on block i−1, and one producer thread issues the TMA copy of
 //    block i into one of two stages;
@@ -313,8 +315,12 @@ __global__ void __launch_bounds__(kFctMaxThreads) fct_embed_kernel(const FctArgs
 // Hand-offs use mbarriers (bounded waits; a timeout raises the TIMEOUT status bit and
 // every role stops).  Draws of a row are packed as {32·h_I, 4·c_I·σ, sign mask, h_I}
 // and {32·h_H, 4·c_H/√s}.
-constexpr int kWsA = 8, kWsB = 1, kWsP = 4;
-constexpr int kT16Threads = 32 * (kWsA + kWsB + kWsP);   // 416
+constexpr int kWsB = 1, kWsP = 4;
+template <int W>
+struct WsCfg {
+  static constexpr int kA = W / 2;                              // A warps
+  static constexpr int kThreads = 32 * (kA + kWsB + kWsP);      // 416 or 672
+};
 
 struct __align__(16) T16Meta {
   int offI;           // 32·h_I: first word of row h_I of P
@@ -327,8 +333,9 @@ struct __align__(8) T16MetaH {
   float wH;           // 4·c_H/√s
 };
 
-template <int LOG2S, typename TA>
-__global__ void __launch_bounds__(kT16Threads) fct_embed_t16_kernel(const FctArgs a) {
+template <int LOG2S, typename TA, int W>
+__global__ void __launch_bounds__(WsCfg<W>::kThreads) fct_embed_ws_kernel(const FctArgs a) {
+  constexpr int kWsA = WsCfg<W>::kA;
   constexpr int S = 1 << LOG2S;
   constexpr int K2 = LOG2S - 4;          // pass 2: row bit 0 and bits [5, LOG2S)
   constexpr int G2 = 1 << K2;
@@ -345,7 +352,7 @@ __global__ void __launch_bounds__(kT16Threads) fct_embed_t16_kernel(const FctArg
   float* P = reinterpret_cast<float*>(stages + 2 * static_cast<size_t>(a.stage_bytes));        // [r1][32]
   float* Pb = P + r1 * 32;                                                                         // [r1]
   float* tile = Pb + ((r1 + 3) & ~3);                                                              // [S][16]
-  T16Meta* mI = reinterpret_cast<T16Meta*>(tile + S * 16);                                         // [2][S]
+  T16Meta* mI = reinterpret_cast<T16Meta*>(tile + S * W);                                          // [2][S]
   T16MetaH* mH = reinterpret_cast<T16MetaH*>(mI + 2 * S);                                          // [2][S]
 
   for (int i = tid; i < r1 * 33; i += blockDim.x) P[i] = 0.f;   // P and Pb
@@ -380,8 +387,8 @@ __global__ void __launch_bounds__(kT16Threads) fct_embed_t16_kernel(const FctArg
         if (!ok) s_abort = 1;
         else if (by_tma) issue_stage_tma<TA>(a, blk, S, stage, &stage_full[buf]);
       }
-      named_barrier(1, 32 * kWsP);
-      if (s_abort) break;                           // uniform: read after the barrier
+      // one decision for all producers (a consumer may set s_abort at any moment)
+      if (named_barrier_any(1, 32 * kWsP, s_abort != 0)) break;
       if (!by_tma) {
         // plain loads into the stage (ragged last block or unaligned input)
         TA* ra = reinterpret_cast<TA*>(stage);
@@ -439,7 +446,36 @@ __global__ void __launch_bounds__(kT16Threads) fct_embed_t16_kernel(const FctArg
       const T16Meta* mi = mI + buf * S;
       const T16MetaH* mh = mH + buf * S;
       if (!is_b) {
-        // ---- pass 1 on A: row bits 1-4 in registers, identity scatter on the way in
+        // ---- pass 1 on A: 4 row bits in registers, identity scatter on the way in
+        if constexpr (W == 32) {
+          for (int task = tid; task < 2 * S; task += 32 * kWsA) {
+            const int c = task & 31, g = task >> 5;
+            const int base = g << 4;                            // row bits 0-3 vary
+            const bool live = c < d;
+            float* Pl = P + c;
+            float v[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) v[j] = live ? widen<TA>(rawA[(base | j) * d + c]) : 0.f;
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              const int4 m = *reinterpret_cast<const int4*>(&mi[base | j]);
+              const float x = v[j];
+              v[j] = __uint_as_float(__float_as_uint(x) ^ static_cast<uint32_t>(m.z));
+              if (live) atomicAdd(Pl + m.x, __int_as_float(m.y) * x);
+            }
+#pragma unroll
+            for (int t = 0; t < 4; ++t)
+#pragma unroll
+              for (int j = 0; j < 16; ++j)
+                if ((j & (1 << t)) == 0) {
+                  const float lo = v[j], hi = v[j | (1 << t)];
+                  v[j] = lo + hi;
+                  v[j | (1 << t)] = lo - hi;
+                }
+#pragma unroll
+            for (int j = 0; j < 16; ++j) tile[(base | j) * 32 + c] = v[j];
+          }
+        } else
         for (int task = tid; task < S; task += 32 * kWsA) {
           const int c = task & 15;
           const int g = task >> 4;
@@ -474,8 +510,32 @@ __global__ void __launch_bounds__(kT16Threads) fct_embed_t16_kernel(const FctArg
         __syncwarp();
         if (lane == 0) mbar_arrive(&stage_free[buf]);
         named_barrier(2, 32 * kWsA);                   // tile complete
-        // ---- pass 2 on A: row bit 0 and bits [5, LOG2S), then the Hadamard scatter
-        {
+        // ---- pass 2 on A: the remaining row bits, then the Hadamard scatter
+        if constexpr (W == 32) {
+          constexpr int K2 = LOG2S - 4;
+          constexpr int G2 = 1 << K2;
+          const int c = tid & 31, g2 = tid >> 5;               // g2 = row bits 0-3
+          float v[G2];
+#pragma unroll
+          for (int j = 0; j < G2; ++j) v[j] = tile[(g2 | (j << 4)) * 32 + c];
+#pragma unroll
+          for (int t = 0; t < K2; ++t)
+#pragma unroll
+            for (int j = 0; j < G2; ++j)
+              if ((j & (1 << t)) == 0) {
+                const float lo = v[j], hi = v[j | (1 << t)];
+                v[j] = lo + hi;
+                v[j | (1 << t)] = lo - hi;
+              }
+          if (c < d) {
+            float* Pl = P + c;
+#pragma unroll
+            for (int k = 0; k < G2; ++k) {
+              const int2 h = *reinterpret_cast<const int2*>(&mh[g2 | (k << 4)]);
+              atomicAdd(Pl + h.x, __int_as_float(h.y) * v[k]);
+            }
+          }
+        } else {
           const int c = tid & 15;
           const int g2 = tid >> 4;
           const int hb = g2 & 1;
@@ -569,7 +629,407 @@ __global__ void __launch_bounds__(kT16Threads) fct_embed_t16_kernel(const FctArg
   float* out = a.partials + static_cast<size_t>(blockIdx.x) * r1 * q;
   for (int i = tid; i < r1 * q; i += blockDim.x) {
     const int h = i / q, c = i - h * q;
-    out[i] = c < d ? P[h * 32 + c] + P[h * 32 + 16 + c] : Pb[h];
+    out[i] = c < d ? (W == 16 ? P[h * 32 + c] + P[h * 32 + 16 + c] : P[h * 32 + c]) : Pb[h];
+  }
+}
+
+// ----------------------------------------------------------------- bucket-sorted scatter
+// d ≤ 32, 32 ≤ s ≤ 512.  Shared-memory float atomics run at a small fraction of the
+// rate of plain loads and stores, so this kernel avoids them on A: the producers sort
+// the 2s virtual rows of a block by bucket (a counting sort: one integer atomic per
+// virtual row gives its rank, a scan gives the bucket offsets), and each consumer warp
+// owns a contiguous range of buckets — split at bucket boundaries, so no two warps,
+// and no two half-warps, ever touch the same row of P.  A warp walks its sorted
+// entries, sums the scaled rows of one bucket in registers (lane = column) and adds
+// the sum to P once per bucket with a plain read-modify-write.  Roles:
+//  * 4 producer warps: the TMA copy (or plain loads) of block i into one of two stages,
+//    the row draws, the sign mask (one ballot per 32 rows), the sort;
+//  * W/2 A warps (8 for W = 16 columns per entry, 16 for W = 32): pass 1 (σ and the
+//    butterflies over 4 row bits, in registers) and pass 2 (the remaining bits), both
+//    through the tile, then the sorted scatter; the identity half reads the raw stage,
+//    with σ folded into its weight;
+//  * 1 b warp: the b column as in the narrow-X kernel (its own atomics on a 1-column P).
+// W = 16: the two half-warps of a warp hold rows of opposite parity in both passes, as
+// in the narrow-X kernel (its second pass reads in the order j ^ 1 and undoes the sign
+// on the way back to the tile); in the scatter each half-warp takes one half of the
+// warp's bucket range.
+constexpr int kSrtP = 4;
+
+template <int W>
+struct SrtCfg {
+  static constexpr int kA = W / 2;
+  static constexpr int kThreads = 32 * (kA + 1 + kSrtP);
+};
+
+struct __align__(16) SrtBMeta {   // draws of one row for the b warp
+  int hI;
+  float wI;                       // 4·c_I·σ
+  int hH;
+  float wH;                       // 4·c_H/√s
+};
+
+__host__ __device__ constexpr int srt_cnt_len(int r1) { return (r1 + 4) & ~3; }   // r1 + 1 offsets, padded
+
+template <int LOG2S, typename TA, int W>
+__global__ void __launch_bounds__(SrtCfg<W>::kThreads) fct_embed_sorted_kernel(const FctArgs a) {
+  constexpr int S = 1 << LOG2S;
+  constexpr int NA = SrtCfg<W>::kA;
+  constexpr int E = 2 * S;                 // entries (virtual rows) per block
+  constexpr int KB = S / 32;               // b column: values per lane
+  constexpr int SW = S / 32;               // sign-mask words per block
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ uint64_t stage_full[2], stage_free[2], meta_full[2], meta_free[2];
+  __shared__ volatile int s_abort;
+  __shared__ int s_wsum[kSrtP];
+  const int r1 = a.r1, d = a.d;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int rc = srt_cnt_len(r1);
+  unsigned char* stages = smem_raw;
+  float* P = reinterpret_cast<float*>(stages + 2 * static_cast<size_t>(a.stage_bytes));   // [r1][W]
+  float* Pb = P + r1 * W;                                                                    // [r1]
+  float* tile = Pb + ((r1 + 3) & ~3);                                                        // [S][W]
+  uint2* ent = reinterpret_cast<uint2*>(tile + S * W);                                       // [2][E]
+  int* cnt = reinterpret_cast<int*>(ent + 2 * E);                                            // [2][rc]
+  SrtBMeta* bm = reinterpret_cast<SrtBMeta*>(cnt + 2 * rc);                                  // [2][S]
+  uint32_t* smask = reinterpret_cast<uint32_t*>(bm + 2 * S);                                 // [2][SW]
+
+  for (int i = tid; i < r1 * W + ((r1 + 3) & ~3); i += blockDim.x) P[i] = 0.f;   // P and Pb
+  if (tid == 0) {
+    s_abort = 0;
+    for (int k = 0; k < 2; ++k) {
+      mbar_init(&stage_full[k], 1);
+      mbar_init(&stage_free[k], NA + 1);
+      mbar_init(&meta_full[k], 1);
+      mbar_init(&meta_free[k], NA + 1);
+    }
+    fence_mbar_init();
+  }
+  __syncthreads();
+  const bool tma = a.tma != 0;
+  const uint32_t b_off = (a.stage_a_bytes + 15) & ~15u;
+
+  if (warp > NA) {
+    // ---------------- producers
+    const int pt = tid - 32 * (NA + 1);            // 0..127
+    constexpr int RP = (S + 32 * kSrtP - 1) / (32 * kSrtP);
+    int64_t i = 0;
+    for (int64_t blk = blockIdx.x; blk < a.nblocks; blk += gridDim.x, ++i) {
+      const int buf = static_cast<int>(i & 1);
+      const uint32_t use = static_cast<uint32_t>((i >> 1) & 1);
+      unsigned char* stage = stages + static_cast<size_t>(buf) * a.stage_bytes;
+      const int64_t row0 = blk * S;
+      const bool by_tma = tma && blk < a.full_blocks;
+      if (pt == 0) {
+        const bool ok = mbar_wait_bounded(&stage_free[buf], use ^ 1u, kWaitCycles) &&
+                        mbar_wait_bounded(&meta_free[buf], use ^ 1u, kWaitCycles);
+        if (!ok) s_abort = 1;
+        else if (by_tma) issue_stage_tma<TA>(a, blk, S, stage, &stage_full[buf]);
+      }
+      // one decision for all producers (a consumer may set s_abort at any moment)
+      if (named_barrier_any(1, 32 * kSrtP, s_abort != 0)) break;
+      if (!by_tma) {
+        TA* ra = reinterpret_cast<TA*>(stage);
+        float* rb = reinterpret_cast<float*>(stage + b_off);
+        const TA* A = static_cast<const TA*>(a.A);
+        for (int e = pt; e < S * d; e += 32 * kSrtP) {
+          const int r = e / d, c = e - r * d;
+          ra[e] = (row0 + r < a.n) ? A[(row0 + r) * a.lda + c] : TA(0);
+        }
+        for (int r = pt; r < S; r += 32 * kSrtP) rb[r] = (row0 + r < a.n) ? a.b[row0 + r] : 0.f;
+      }
+      int* cb = cnt + buf * rc;
+      for (int h = pt; h < rc; h += 32 * kSrtP) cb[h] = 0;
+      named_barrier(1, 32 * kSrtP);
+      int hH[RP], hI[RP], rkH[RP], rkI[RP];
+      float wH[RP], wI[RP];
+#pragma unroll
+      for (int k = 0; k < RP; ++k) {
+        const int r = pt + 32 * kSrtP * k;
+        bool neg = false;
+        if (r < S) {
+          const uint64_t grow = static_cast<uint64_t>(a.row_offset + row0 + r);
+          const uint4 o = draw_row(a.key, grow, a.problem, kStreamFct);
+          neg = a.sign_flip && (o.w & 1u);
+          hI[k] = bucket_of(o.z, r1);
+          const float ci = 4.f * cauchy_f32(o.w >> 8);
+          wI[k] = neg ? -ci : ci;
+          hH[k] = bucket_of(o.x, r1);
+          wH[k] = 4.f * cauchy_f32(o.y >> 8) * a.inv_sqrt_s;
+          rkH[k] = atomicAdd(&cb[hH[k]], 1);
+          rkI[k] = atomicAdd(&cb[hI[k]], 1);
+          bm[buf * S + r] = SrtBMeta{hI[k], wI[k], hH[k], wH[k]};
+        }
+        // rows r of a warp are 32 consecutive rows, all below S or all at or above it
+        const unsigned m = __ballot_sync(0xffffffffu, neg);
+        if (r < S && lane == 0) smask[buf * SW + (r >> 5)] = m;
+      }
+      named_barrier(1, 32 * kSrtP);
+      // Exclusive scan of the counts over buckets 0..r1 (cb[r1] stays 0, so its offset is E).
+      {
+        const int per = (r1 + 1 + 32 * kSrtP - 1) / (32 * kSrtP);
+        const int h0 = pt * per;
+        int loc = 0;
+        for (int j = 0; j < per; ++j)
+          if (h0 + j <= r1) loc += cb[h0 + j];
+        int incl = loc;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int t = __shfl_up_sync(0xffffffffu, incl, o);
+          if (lane >= o) incl += t;
+        }
+        if (lane == 31) s_wsum[pt >> 5] = incl;
+        named_barrier(1, 32 * kSrtP);
+        int run = incl - loc;
+        for (int w = 0; w < (pt >> 5); ++w) run += s_wsum[w];
+        for (int j = 0; j < per; ++j) {
+          const int h = h0 + j;
+          if (h <= r1) {
+            const int c = cb[h];
+            cb[h] = run;
+            run += c;
+          }
+        }
+      }
+      named_barrier(1, 32 * kSrtP);
+      uint2* eb = ent + buf * E;
+#pragma unroll
+      for (int k = 0; k < RP; ++k) {
+        const int r = pt + 32 * kSrtP * k;
+        if (r < S) {
+          eb[cb[hH[k]] + rkH[k]] = make_uint2((static_cast<uint32_t>(hH[k]) << 16) | 0x8000u | r,
+                                              __float_as_uint(wH[k]));
+          eb[cb[hI[k]] + rkI[k]] = make_uint2((static_cast<uint32_t>(hI[k]) << 16) | r, __float_as_uint(wI[k]));
+        }
+      }
+      named_barrier(1, 32 * kSrtP);                  // entries, offsets, masks and a plain stage written
+      if (pt == 0) {
+        if (!by_tma) mbar_arrive(&stage_full[buf]);
+        mbar_arrive(&meta_full[buf]);
+      }
+    }
+  } else {
+    // ---------------- consumers: NA A warps and the b warp
+    const bool is_b = warp == NA;
+    int64_t i = 0;
+    for (int64_t blk = blockIdx.x; blk < a.nblocks; blk += gridDim.x, ++i) {
+      const int buf = static_cast<int>(i & 1);
+      const uint32_t use = static_cast<uint32_t>((i >> 1) & 1);
+      bool ok = true;
+      if (lane == 0)
+        ok = mbar_wait_bounded(&meta_full[buf], use, kWaitCycles) && mbar_wait_bounded(&stage_full[buf], use, kWaitCycles);
+      ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+      if (named_barrier_any(3, 32 * (NA + 1), !ok || s_abort)) {
+        s_abort = 1;
+        break;
+      }
+      const unsigned char* stage = stages + static_cast<size_t>(buf) * a.stage_bytes;
+      const TA* rawA = reinterpret_cast<const TA*>(stage);
+      const float* rawB = reinterpret_cast<const float*>(stage + b_off);
+      const uint32_t* sm = smask + buf * SW;
+      if (!is_b) {
+        // ---- pass 1: σ, butterflies over 4 row bits
+        if constexpr (W == 16) {
+          for (int task = tid; task < S; task += 32 * NA) {
+            const int c = task & 15, g = task >> 4;
+            const int base = (g & 1) | ((g >> 1) << 5);       // row bits 1-4 vary in registers
+            const bool live = c < d;
+            const uint32_t mw = sm[base >> 5];
+            float v[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              const int row = base | (j << 1);
+              const float x = live ? widen<TA>(rawA[row * d + c]) : 0.f;
+              v[j] = __uint_as_float(__float_as_uint(x) ^ (((mw >> (row & 31)) & 1u) << 31));
+            }
+#pragma unroll
+            for (int t = 0; t < 4; ++t)
+#pragma unroll
+              for (int j = 0; j < 16; ++j)
+                if ((j & (1 << t)) == 0) {
+                  const float lo = v[j], hi = v[j | (1 << t)];
+                  v[j] = lo + hi;
+                  v[j | (1 << t)] = lo - hi;
+                }
+#pragma unroll
+            for (int j = 0; j < 16; ++j) tile[(base | (j << 1)) * 16 + c] = v[j];
+          }
+        } else {
+          for (int task = tid; task < 2 * S; task += 32 * NA) {
+            const int c = task & 31, g = task >> 5;
+            const int base = g << 4;                            // row bits 0-3 vary in registers
+            const bool live = c < d;
+            const uint32_t mw = sm[base >> 5];
+            float v[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              const int row = base | j;
+              const float x = live ? widen<TA>(rawA[row * d + c]) : 0.f;
+              v[j] = __uint_as_float(__float_as_uint(x) ^ (((mw >> (row & 31)) & 1u) << 31));
+            }
+#pragma unroll
+            for (int t = 0; t < 4; ++t)
+#pragma unroll
+              for (int j = 0; j < 16; ++j)
+                if ((j & (1 << t)) == 0) {
+                  const float lo = v[j], hi = v[j | (1 << t)];
+                  v[j] = lo + hi;
+                  v[j | (1 << t)] = lo - hi;
+                }
+#pragma unroll
+            for (int j = 0; j < 16; ++j) tile[(base | j) * 32 + c] = v[j];
+          }
+        }
+        named_barrier(2, 32 * NA);                    // tile holds pass 1
+        // ---- pass 2: the remaining row bits
+        {
+          constexpr int K2 = LOG2S - 4;
+          constexpr int G2 = 1 << K2;
+          float v[G2];
+          if constexpr (W == 16) {
+            const int c = tid & 15, g2 = tid >> 4, hb = g2 & 1;   // g2 = row bits 1-4
+            auto row2 = [&](int k) { return (g2 << 1) | (k & 1) | ((k >> 1) << 5); };
+#pragma unroll
+            for (int j = 0; j < G2; ++j) v[j] = tile[row2(j ^ hb) * 16 + c];
+#pragma unroll
+            for (int t = 0; t < K2; ++t)
+#pragma unroll
+              for (int j = 0; j < G2; ++j)
+                if ((j & (1 << t)) == 0) {
+                  const float lo = v[j], hi = v[j | (1 << t)];
+                  v[j] = lo + hi;
+                  v[j | (1 << t)] = lo - hi;
+                }
+            // The odd half-warp transformed its rows in the order j ^ 1, which negates its
+            // outputs at odd positions; it writes output k = j ^ 1 at step j with the sign undone.
+#pragma unroll
+            for (int j = 0; j < G2; ++j) {
+              const float val = hb ? ((j & 1) ? v[j ^ 1] : -v[j ^ 1]) : v[j];
+              tile[row2(j ^ hb) * 16 + c] = val;
+            }
+          } else {
+            const int c = tid & 31, g2 = tid >> 5;               // g2 = row bits 0-3
+#pragma unroll
+            for (int j = 0; j < G2; ++j) v[j] = tile[(g2 | (j << 4)) * 32 + c];
+#pragma unroll
+            for (int t = 0; t < K2; ++t)
+#pragma unroll
+              for (int j = 0; j < G2; ++j)
+                if ((j & (1 << t)) == 0) {
+                  const float lo = v[j], hi = v[j | (1 << t)];
+                  v[j] = lo + hi;
+                  v[j | (1 << t)] = lo - hi;
+                }
+#pragma unroll
+            for (int j = 0; j < G2; ++j) tile[(g2 | (j << 4)) * 32 + c] = v[j];
+          }
+        }
+        named_barrier(2, 32 * NA);                    // tile holds H_s·z
+        // ---- sorted scatter over this warp's bucket range
+        {
+          const uint2* eb = ent + buf * E;
+          const int* off = cnt + buf * rc;
+          auto snap = [&](int e) { return e >= E ? E : off[eb[e].x >> 16]; };
+          const int start = warp == 0 ? 0 : snap((warp * E) / NA);
+          const int end = warp == NA - 1 ? E : snap(((warp + 1) * E) / NA);
+          int lo = start, hi = end;
+          if constexpr (W == 16) {
+            const int mid = (start + end) >> 1;
+            int M = end;
+            if (mid < end) {
+              const int h = eb[mid].x >> 16;
+              M = off[h];
+              if (M <= start) M = off[h + 1];
+            }
+            if (lane >> 4) lo = M;
+            else hi = M;
+          }
+          const int c = lane & (W - 1);
+          const bool live = c < d;
+          const int cnt_mine = hi - lo;
+          const int steps = W == 16 ? max(cnt_mine, __shfl_xor_sync(0xffffffffu, cnt_mine, 16)) : cnt_mine;
+          float acc = 0.f;
+          int cur = -1;
+          for (int t = 0; t < steps; ++t) {
+            if (t < cnt_mine) {
+              const uint2 en = eb[lo + t];
+              const int h = static_cast<int>(en.x >> 16);
+              const int row = static_cast<int>(en.x & 0x7FFFu);
+              float val = 0.f;
+              if (live) val = (en.x & 0x8000u) ? tile[row * W + c] : widen<TA>(rawA[row * d + c]);
+              if (h != cur) {
+                if (cur >= 0 && live) P[cur * W + c] += acc;
+                acc = 0.f;
+                cur = h;
+              }
+              acc = fmaf(__uint_as_float(en.y), val, acc);
+            }
+          }
+          if (cur >= 0 && live) P[cur * W + c] += acc;
+        }
+        __syncwarp();
+        if (lane == 0) {
+          mbar_arrive(&stage_free[buf]);
+          mbar_arrive(&meta_free[buf]);
+        }
+        named_barrier(2, 32 * NA);                    // tile free for the next block
+      } else {
+        // ---- the b column: one warp, all stages, both scatters (atomics on Pb)
+        const SrtBMeta* mb = bm + buf * S;
+        float v[KB];
+#pragma unroll
+        for (int k = 0; k < KB; ++k) {
+          const int row = lane + 32 * k;
+          const float x = -rawB[row];
+          const SrtBMeta m = mb[row];
+          atomicAdd(&Pb[m.hI], m.wI * x);
+          v[k] = __uint_as_float(__float_as_uint(x) ^ (((sm[k] >> lane) & 1u) << 31));
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&stage_free[buf]);
+#pragma unroll
+        for (int t = 0; (1 << t) < KB; ++t)
+#pragma unroll
+          for (int k = 0; k < KB; ++k)
+            if ((k & (1 << t)) == 0) {
+              const float lo = v[k], hi = v[k | (1 << t)];
+              v[k] = lo + hi;
+              v[k | (1 << t)] = lo - hi;
+            }
+#pragma unroll
+        for (int t = 0; t < 5; ++t) {
+          const bool upper = (lane >> t) & 1;
+#pragma unroll
+          for (int k = 0; k < KB; ++k) {
+            const float o = __shfl_xor_sync(0xffffffffu, v[k], 1 << t);
+            v[k] = upper ? (o - v[k]) : (v[k] + o);
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < KB; ++k) {
+          const SrtBMeta m = mb[lane + 32 * k];
+          atomicAdd(&Pb[m.hH], m.wH * v[k]);
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&meta_free[buf]);
+      }
+    }
+  }
+  __syncthreads();
+  if (s_abort) {
+    if (tid == 0) {
+      raise_flag(a.flags, L1S_ERR_TIMEOUT);
+      const long long t0 = clock64();
+      while (clock64() - t0 < 20000000LL) {
+      }
+    }
+    __syncthreads();
+    return;
+  }
+  const int q = d + 1;
+  float* out = a.partials + static_cast<size_t>(blockIdx.x) * r1 * q;
+  for (int i = tid; i < r1 * q; i += blockDim.x) {
+    const int h = i / q, c = i - h * q;
+    out[i] = c < d ? P[h * W + c] : Pb[h];
   }
 }
 
@@ -640,26 +1100,31 @@ const void* fct_kernel(int log2s, l1s_dtype dt, bool staged) {
   return staged ? fct_kernel_for<float, true>(log2s) : fct_kernel_for<float, false>(log2s);
 }
 
-template <typename TA>
-static const void* t16_kernel_for(int log2s) {
+template <typename TA, int W>
+static const void* ws_kernel_for(int log2s) {
   switch (log2s) {
-    case 5: return reinterpret_cast<const void*>(&fct_embed_t16_kernel<5, TA>);
-    case 6: return reinterpret_cast<const void*>(&fct_embed_t16_kernel<6, TA>);
-    case 7: return reinterpret_cast<const void*>(&fct_embed_t16_kernel<7, TA>);
-    case 8: return reinterpret_cast<const void*>(&fct_embed_t16_kernel<8, TA>);
-    case 9: return reinterpret_cast<const void*>(&fct_embed_t16_kernel<9, TA>);
+    case 5: return reinterpret_cast<const void*>(&fct_embed_ws_kernel<5, TA, W>);
+    case 6: return reinterpret_cast<const void*>(&fct_embed_ws_kernel<6, TA, W>);
+    case 7: return reinterpret_cast<const void*>(&fct_embed_ws_kernel<7, TA, W>);
+    case 8: return reinterpret_cast<const void*>(&fct_embed_ws_kernel<8, TA, W>);
+    case 9: return reinterpret_cast<const void*>(&fct_embed_ws_kernel<9, TA, W>);
     default: return nullptr;
   }
 }
 
-// The narrow-X kernel applies for d ≤ 16 and 32 ≤ s ≤ 512.
-bool fct_t16_applies(int log2s, int d) { return d <= 16 && log2s >= 5 && log2s <= 9; }
-
-const void* fct_t16_kernel(int log2s, l1s_dtype dt) {
-  return dt == L1S_BF16 ? t16_kernel_for<uint16_t>(log2s) : t16_kernel_for<float>(log2s);
+// Column width of the narrow-X kernel for d (16 or 32; 32 ≤ s ≤ 512), 0 when it does not apply.
+int fct_ws_width(int log2s, int d) {
+  if (log2s < 5 || log2s > 9) return 0;
+  return d <= 16 ? 16 : (d <= 32 ? 32 : 0);
 }
 
-int fct_t16_threads() { return kT16Threads; }
+const void* fct_ws_kernel(int log2s, l1s_dtype dt, int w) {
+  if (w == 16) return dt == L1S_BF16 ? ws_kernel_for<uint16_t, 16>(log2s) : ws_kernel_for<float, 16>(log2s);
+  if (w == 32) return dt == L1S_BF16 ? ws_kernel_for<uint16_t, 32>(log2s) : ws_kernel_for<float, 32>(log2s);
+  return nullptr;
+}
+
+int fct_ws_threads(int w) { return w == 16 ? WsCfg<16>::kThreads : WsCfg<32>::kThreads; }
 
 uint32_t fct_stage_bytes(int s, int d, l1s_dtype dt) {
   const uint32_t esz = dt == L1S_BF16 ? 2u : 4u;
@@ -667,15 +1132,49 @@ uint32_t fct_stage_bytes(int s, int d, l1s_dtype dt) {
   return ((a_bytes + 15u) & ~15u) + static_cast<uint32_t>(s) * 4u;
 }
 
+template <typename TA, int W>
+static const void* sorted_kernel_for(int log2s) {
+  switch (log2s) {
+    case 5: return reinterpret_cast<const void*>(&fct_embed_sorted_kernel<5, TA, W>);
+    case 6: return reinterpret_cast<const void*>(&fct_embed_sorted_kernel<6, TA, W>);
+    case 7: return reinterpret_cast<const void*>(&fct_embed_sorted_kernel<7, TA, W>);
+    case 8: return reinterpret_cast<const void*>(&fct_embed_sorted_kernel<8, TA, W>);
+    case 9: return reinterpret_cast<const void*>(&fct_embed_sorted_kernel<9, TA, W>);
+    default: return nullptr;
+  }
+}
+
+// Column width of the bucket-sorted kernel for d (16 or 32), 0 when it does not apply.
+int fct_sorted_width(int log2s, int d) {
+  if (log2s < 5 || log2s > 9) return 0;
+  return d <= 16 ? 16 : (d <= 32 ? 32 : 0);
+}
+
+const void* fct_sorted_kernel(int log2s, l1s_dtype dt, int w) {
+  if (w == 16) return dt == L1S_BF16 ? sorted_kernel_for<uint16_t, 16>(log2s) : sorted_kernel_for<float, 16>(log2s);
+  if (w == 32) return dt == L1S_BF16 ? sorted_kernel_for<uint16_t, 32>(log2s) : sorted_kernel_for<float, 32>(log2s);
+  return nullptr;
+}
+
+int fct_sorted_threads(int w) { return w == 16 ? SrtCfg<16>::kThreads : SrtCfg<32>::kThreads; }
+
+size_t fct_sorted_smem_bytes(int s, int d, l1s_dtype dt, int r1, int w) {
+  return 2 * static_cast<size_t>(fct_stage_bytes(s, d, dt)) + static_cast<size_t>(r1) * w * 4 +
+         static_cast<size_t>((r1 + 3) & ~3) * 4 + static_cast<size_t>(s) * w * 4 +
+         2 * static_cast<size_t>(2 * s) * sizeof(uint2) + 2 * static_cast<size_t>(srt_cnt_len(r1)) * 4 +
+         2 * static_cast<size_t>(s) * sizeof(SrtBMeta) + 2 * static_cast<size_t>(s / 32) * 4;
+}
+
+
 size_t fct_smem_bytes(int s, int d, l1s_dtype dt, int r1, int width, bool staged) {
   return (staged ? static_cast<size_t>(kFctStages) * fct_stage_bytes(s, d, dt) : 0) +
          static_cast<size_t>(r1) * width * 4 + static_cast<size_t>(s) * width * 4 +
          static_cast<size_t>(s) * (sizeof(RowMeta) + 4);
 }
 
-size_t fct_t16_smem_bytes(int s, int d, l1s_dtype dt, int r1) {
+size_t fct_ws_smem_bytes(int s, int d, l1s_dtype dt, int r1, int w) {
   return 2 * static_cast<size_t>(fct_stage_bytes(s, d, dt)) + static_cast<size_t>(r1) * 32 * 4 +
-         static_cast<size_t>((r1 + 3) & ~3) * 4 + static_cast<size_t>(s) * 16 * 4 +
+         static_cast<size_t>((r1 + 3) & ~3) * 4 + static_cast<size_t>(s) * w * 4 +
          2 * static_cast<size_t>(s) * (sizeof(T16Meta) + sizeof(T16MetaH));
 }
 
@@ -723,10 +1222,15 @@ bool launch_fct(const Plan& pl, const void* A, int64_t lda, l1s_dtype dt, const 
   // A layout that cannot be staged falls back to direct loads with the same grid; the
   // direct variant needs less shared memory than the staged one it was planned for.
   // The narrow-X kernel stages every block (by TMA when it can, else with plain loads).
-  const bool t16 = pl.fct_t16 != 0;
-  if (t16) a.tma = fct_can_stage(pl.s, pl.d, dt, lda, A, b) ? 1 : 0;
-  const void* fn = t16 ? fct_t16_kernel(pl.log2s, dt) : fct_kernel(pl.log2s, dt, staged);
-  const size_t smem = t16 ? fct_t16_smem_bytes(pl.s, pl.d, dt, pl.r1) : fct_smem_bytes(pl.s, pl.d, dt, pl.r1, pl.fct_width, staged);
+  // So does the bucket-sorted kernel.
+  const int wsw = pl.fct_ws;
+  const int srt = pl.fct_sorted;
+  if (wsw || srt) a.tma = fct_can_stage(pl.s, pl.d, dt, lda, A, b) ? 1 : 0;
+  const void* fn = srt ? fct_sorted_kernel(pl.log2s, dt, srt)
+                       : (wsw ? fct_ws_kernel(pl.log2s, dt, wsw) : fct_kernel(pl.log2s, dt, staged));
+  const size_t smem = srt ? fct_sorted_smem_bytes(pl.s, pl.d, dt, pl.r1, srt)
+                          : (wsw ? fct_ws_smem_bytes(pl.s, pl.d, dt, pl.r1, wsw)
+                                 : fct_smem_bytes(pl.s, pl.d, dt, pl.r1, pl.fct_width, staged));
   if (!cuda_ok(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)),
                "cudaFuncSetAttribute(fct_embed)"))
     return false;

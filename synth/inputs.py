@@ -30,6 +30,13 @@ def r1_for(d: int) -> int:
     return int(math.ceil(8.0 * d * math.log(d)))
 
 
+def block_size_for(d: int) -> int:
+    """FCT1 block size where a workload does not fix it: ⌈2·d·ln d⌉ (the experiments'
+    choice, §6.1) rounded up to a power of two, as FCT1 needs.  The same rule gives the
+    fixed values s = 64 at d = 8 and s = 1024 at d = 64."""
+    return 1 << int(math.ceil(math.log2(2.0 * d * math.log(d))))
+
+
 @dataclass(frozen=True)
 class Workload:
     name: str
@@ -65,7 +72,7 @@ WORKLOADS = {
     "colscale_n4M_d16": Workload("colscale_n4M_d16", 1 << 22, 16, 256, 16, 20000.0,
                                  "f32", "gauss_colscale", "laplace_outliers"),
     # n=2^24, d=32, rows scaled by |Student-t(2)| magnitudes, A stored BF16.
-    "t2rows_n16M_d32_bf16": Workload("t2rows_n16M_d32_bf16", 1 << 24, 32, 1024, 32,
+    "t2rows_n16M_d32_bf16": Workload("t2rows_n16M_d32_bf16", 1 << 24, 32, 256, 32,
                                      100000.0, "bf16", "gauss_t2rows",
                                      "laplace_outliers"),
     # n=2^26, d=64, 0.1% of rows scaled by 1e3, Cauchy(0,1) noise.
@@ -160,8 +167,8 @@ def make_problem(w: Workload | str, n: int | None = None, seed: int | None = Non
 
 
 def batched_block_size(d: int) -> int:
-    """Hadamard block size of a batch member: the power of two at or above r1, within [64, 1024]."""
-    return min(1024, max(64, 1 << int(math.ceil(math.log2(r1_for(d))))))
+    """Hadamard block size of a batch member (block_size_for)."""
+    return block_size_for(d)
 
 
 def make_batched_problems(count: int = 256, seed: int = 0,

@@ -167,7 +167,7 @@ def test_batched_argument_errors():
     assert e.value.code == 2
 
 
-@pytest.mark.parametrize("variant", [1, 2, 3])
+@pytest.mark.parametrize("variant", [1, 2, 3, 4])
 def test_every_phase1_variant_matches_the_oracle(variant):
     """Each schedule's phase-1 kernel (narrow-X warp-specialised, TMA-staged, direct) meets
     the Π1X bar on one shape where all three apply."""
