@@ -26,21 +26,21 @@ const void* fct_sorted_kernel(int log2s, l1s_dtype dt, int w);
 int fct_sorted_threads(int w);
 size_t fct_sorted_smem_bytes(int s, int d, l1s_dtype dt, int r1, int w);
 bool launch_fct(const Plan& pl, const void* A, int64_t lda, l1s_dtype dt, const float* b,
-                const l1s_params* p, float* pix, unsigned char* ws, cudaStream_t st);
+                const l1s_params* p, float* pix, unsigned char* ws, cudaStream_t st, double* pi2_out = nullptr);
 bool launch_condition(const Plan& pl, const float* pix, const l1s_params* p, double* R_user,
-                      double* M_user, unsigned char* ws, cudaStream_t st);
+                      double* M_user, unsigned char* ws, cudaStream_t st, bool pi2_ready = false);
 bool launch_pi2(const l1s_params* p, int q, double* out, cudaStream_t st);
 size_t cond2_scratch_bytes(int r1, int q, int sms);
 int lambda_threads();
 bool launch_lambda(const Plan& pl, const void* A, int64_t lda, l1s_dtype dt, const float* b,
                    const float* m32, const l1s_params* p, float* lam, double* user_sum,
-                   unsigned char* ws, cudaStream_t st);
+                   unsigned char* ws, cudaStream_t st, int* nsums_out = nullptr);
 bool launch_m_to_f32(const double* m, int total, float* out, cudaStream_t st);
 int sample_threads();
 bool launch_sample(const Plan& pl, const float* lam, const double* p, const l1s_params* prm,
                    const void* A, int64_t lda, l1s_dtype dt, const float* b, int64_t capacity,
                    int64_t* idx, double* w, double* coreset, int64_t* count_out, unsigned char* ws,
-                   cudaStream_t st);
+                   cudaStream_t st, int lam_nsums = 0);
 bool launch_debug_variates(const l1s_params* p, int64_t row_start, int64_t count, int32_t* bh,
                            int32_t* bi, int32_t* kh, int32_t* ki, float* ch, float* ci, int8_t* sg,
                            uint64_t* ub, cudaStream_t st);
@@ -138,8 +138,10 @@ int sample_impl(const Plan& pl, const void* A, int64_t lda, l1s_dtype dtype, con
                        double* wts, double* coreset, int64_t* count, float* lambda, unsigned char* w,
                        cudaStream_t st) {
   float* lam = lambda ? lambda : reinterpret_cast<float*>(w + pl.off_lam);
-  if (!launch_lambda(pl, A, lda, dtype, b, m32, params, lam, nullptr, w, st)) return L1S_ERR_CUDA;
-  if (!launch_sample(pl, lam, nullptr, params, A, lda, dtype, b, capacity, idx, wts, coreset, count, w, st))
+  int nsums = 0;   // Σλ and τ are formed at the start of the sampling kernel
+  if (!launch_lambda(pl, A, lda, dtype, b, m32, params, lam, nullptr, w, st, &nsums)) return L1S_ERR_CUDA;
+  if (!launch_sample(pl, lam, nullptr, params, A, lda, dtype, b, capacity, idx, wts, coreset, count, w, st,
+                     nsums))
     return L1S_ERR_CUDA;
   return L1S_OK;
 }
@@ -150,8 +152,10 @@ int coreset_impl(const Plan& pl, const void* A, int64_t lda, l1s_dtype dtype, co
   if (!cuda_ok(cudaMemsetAsync(w + pl.off_status, 0, sizeof(StatusBlock), st), "status reset"))
     return L1S_ERR_CUDA;
   float* pix = reinterpret_cast<float*>(w + pl.off_pix);
-  if (!launch_fct(pl, A, lda, dtype, b, params, pix, w, st)) return L1S_ERR_CUDA;
-  if (!launch_condition(pl, pix, params, nullptr, nullptr, w, st)) return L1S_ERR_CUDA;
+  // Π2 is drawn by the phase-1 reduction, off the conditioning's serial path.
+  if (!launch_fct(pl, A, lda, dtype, b, params, pix, w, st, reinterpret_cast<double*>(w + pl.off_pi2)))
+    return L1S_ERR_CUDA;
+  if (!launch_condition(pl, pix, params, nullptr, nullptr, w, st, true)) return L1S_ERR_CUDA;
   return sample_impl(pl, A, lda, dtype, b, reinterpret_cast<float*>(w + pl.off_m32), params, capacity, idx,
                      wts, coreset, count, nullptr, w, st);
 }

@@ -4,9 +4,11 @@
 // phase 2 multiplies X by one skinny matrix, the order the paper's running-time
 // argument uses (proof of the fast ℓ1 regression theorem: R⁻¹Π2 before X·(R⁻¹Π2)).
 //
-// A single thread block runs Householder reflections on a column-major FP64
-// copy of Π1·X, held in shared memory when it fits (r1·q·8 bytes ≤ 160 KB) and
-// in the workspace (L2-resident) otherwise.
+// The QR is CholeskyQR2 (below) in two launches over many thread blocks.  When
+// its blocks do not fit in shared memory (q near 129), a single thread block runs
+// Householder reflections on a column-major FP64 copy of Π1·X instead, held in
+// shared memory when it fits (r1·q·8 bytes ≤ 160 KB) and in the workspace
+// (L2-resident) otherwise.
 #include <stddef.h>
 
 #include <algorithm>
@@ -46,12 +48,6 @@ __device__ double block_sum_f64(double v, double* scratch) {
   return scratch[32];
 }
 
-// Π2 entry e (row-major q × r2): word e mod 4 of Philox call ⌊e/4⌋ on stream 1.
-__device__ __forceinline__ double pi2_entry(Key2 key, uint32_t problem, int e) {
-  const uint4 o = philox4x32_10(make_uint4(static_cast<uint32_t>(e >> 2), 0u, problem, kStreamPi2), key);
-  const uint32_t w = (e & 3) == 0 ? o.x : (e & 3) == 1 ? o.y : (e & 3) == 2 ? o.z : o.w;
-  return cauchy_f64(w >> 8);
-}
 
 struct CondArgs {
   const float* pix;   // r1 × q row-major FP32
@@ -164,15 +160,17 @@ __global__ void __launch_bounds__(kCondThreads) condition_kernel(const CondArgs 
 // number is below about 1e7 — far past what an FP32-accumulated Π1X resolves (the
 // rank test flags columns dependent to 1e-5).  The Gram products spread over thread
 // blocks; the last block to finish (an atomic ticket, no waiting) sums the partials in
-// a fixed order and factors the q×q matrix in one warp.  Two launches: pass 0 (Gram of
-// Π1X → R1), pass 1 (rows of Π1X·R1⁻¹ by forward substitution, their Gram → R2, then
-// R = R2·R1 and M = R⁻¹Π2).
+// a fixed order and factors the q×q matrix.  Two launches: pass 0 (Gram of Π1X → R1),
+// pass 1 (rows of Π1X·R1⁻¹ by forward substitution, their Gram → R2, then R = R2·R1
+// and M = R⁻¹Π2).  Π2 is drawn by the phase-1 reduction when the whole pass runs.
 //
-// FP64 arithmetic on this part has long latencies (a dependent FMA takes ~64 cycles,
-// a division ~430, a square root ~670), so the serial parts avoid divisions and
-// square roots: 1/√x comes from an FP32 estimate refined by two Newton steps in FP64,
-// and every division by a diagonal entry is a multiplication by its stored reciprocal;
-// sums keep four independent partial accumulators (combined in a fixed order).
+// FP64 arithmetic on this part is slow (a dependent FMA takes ~64 cycles, a division
+// ~430, a square root ~670, and a full-warp FP64 instruction holds its sub-partition
+// for ~80 cycles), so the serial parts avoid divisions and square roots — reciprocals
+// and reciprocal square roots come from FP32 estimates refined by Newton steps in
+// FP64, and every division by a diagonal entry is a multiplication by its stored
+// reciprocal — and run right-looking (each step finishes one row or column and updates
+// the rest in parallel), so the dependent chain per step is a few operations long.
 constexpr int kGramThreads = 256;
 
 struct Cond2Args {
@@ -193,40 +191,85 @@ struct Cond2Args {
   double* R_user;
   double* M_user;
   uint32_t* flags;
+  int pi2_ready;         // 1: Π2 is already in pi2 (drawn by the phase-1 reduction)
 };
 
-// 1/√x for x > 0: FP32 estimate, then two Newton steps y ← y·(3 − x·y²)/2 in FP64.
-__device__ __forceinline__ double rsqrt_f64(double x) {
-  double y = static_cast<double>(rsqrtf(static_cast<float>(x)));
-  y = y * fma(-0.5 * x * y, y, 1.5);
-  y = y * fma(-0.5 * x * y, y, 1.5);
+// On this part every FP64 warp instruction occupies its SM sub-partition for tens of
+// cycles, so the serial steps below keep their FP64 chains short and spread the
+// independent work over four warps (one per sub-partition, named barrier 1).
+constexpr int kCholThreads = 128;
+
+// 1/x and 1/√x for x > 0 in FP64: an FP32 estimate of the mantissa part (the exponent is
+// split off first, so any normal FP64 x works), then Newton steps in FP64 — for 1/x
+// y ← y + y·(1 − x·y), for 1/√x y ← y·(3/2 − (x/2)·y²).  Each step doubles the number of
+// correct bits: one leaves a relative error near 1e-13, two reach FP64 rounding.
+__device__ __forceinline__ double rcp_f64(double x, int steps) {
+  int e;
+  const double m = frexp(x, &e);                         // x = m·2^e, m ∈ [1/2, 1)
+  double y = ldexp(static_cast<double>(__frcp_rn(static_cast<float>(m))), -e);
+  for (int i = 0; i < steps; ++i) y = fma(y, fma(-x, y, 1.0), y);
   return y;
 }
 
-// Cholesky of the symmetric q×q matrix G (row-major, upper triangle used) by one warp:
-// on return the upper triangle of G holds R with RᵀR = G and dinv[k] = 1/R_kk.
-// Returns false when a pivot is not positive.
-__device__ bool warp_cholesky(double* G, double* dinv, int q) {
-  const int lane = threadIdx.x & 31;
-  bool ok = true;
-  for (int k = 0; k < q; ++k) {
-    const double a = G[k * q + k];
-    if (!(a > 0.0) || !isfinite(a)) ok = false;
-    const double inv = rsqrt_f64(fmax(a, 1e-300));
-    __syncwarp();
-    for (int j = k + lane; j < q; j += 32) G[k * q + j] = (j == k) ? a * inv : G[k * q + j] * inv;
-    if (lane == 0) dinv[k] = inv;
-    __syncwarp();
-    // trailing update of rows i > k, columns j ≥ i (upper triangle)
-    for (int e = lane; e < (q - k - 1) * (q - k - 1); e += 32) {
-      const int i = k + 1 + e / (q - k - 1), j = k + 1 + e % (q - k - 1);
-      if (j >= i) G[i * q + j] = fma(-G[k * q + i], G[k * q + j], G[i * q + j]);
-    }
-    __syncwarp();
+__device__ __forceinline__ double rsqrt_f64(double x, int steps) {
+  int e;
+  double m = frexp(x, &e);
+  if (e & 1) {                                           // make the exponent even
+    m *= 2.0;
+    e -= 1;
   }
-  for (int e = lane; e < q * q; e += 32)
-    if (e % q < e / q) G[e] = 0.0;
-  __syncwarp();
+  double y = ldexp(static_cast<double>(rsqrtf(static_cast<float>(m))), -e / 2);
+  const double h = 0.5 * x;
+  for (int i = 0; i < steps; ++i) y = y * fma(-h, y * y, 1.5);
+  return y;
+}
+
+// Cholesky of the symmetric q×q matrix G (row-major, upper triangle, shared memory) by
+// threads 0..127, in the square-root-free form G = LᵀDL first: step k subtracts
+// G_ki·G_kj/d_k from the trailing block (warps 1-3) while thread 0 forms the next
+// pivot — the same FMA the update would apply to G_{k+1,k+1} — and its reciprocal,
+// so the serial chain per step is one reciprocal.  Then R_kj = G_kj/√d_k for all
+// entries at once, and dinv[k] = 1/R_kk.  s_r holds q doubles.  Returns false when a
+// pivot is not positive.
+// chain_steps Newton steps refine the pivots' reciprocals on the serial chain (0 leaves
+// them FP32-accurate, which only perturbs G by about 1e-7 relative: enough for a
+// preconditioner); the final 1/√d_k always take two.
+__device__ bool block_cholesky(double* G, double* R, double* dinv, double* s_r, int q, int chain_steps) {
+  const int t = threadIdx.x;
+  const int steps = chain_steps;
+  bool ok = true;
+  if (t == 0) {
+    const double a = G[0];
+    s_r[0] = rcp_f64(fmax(a, 1e-300), steps);
+    if (!(a > 0.0) || !isfinite(a)) ok = false;
+  }
+  named_barrier(1, kCholThreads);
+  for (int k = 0; k + 1 < q; ++k) {
+    const double r = s_r[k];
+    if (t == 0) {
+      const double g = G[k * q + k + 1];
+      const double an = fma(-(g * r), g, G[(k + 1) * q + k + 1]);
+      G[(k + 1) * q + k + 1] = an;   // the one trailing entry warps 1-3 leave to thread 0
+      s_r[k + 1] = rcp_f64(fmax(an, 1e-300), steps);
+      if (!(an > 0.0) || !isfinite(an)) ok = false;
+    } else if (t >= 32) {
+      const int w = q - k - 1;
+      for (int e = t - 32; e < w * w; e += kCholThreads - 32) {
+        const int i = k + 1 + e / w, j = k + 1 + e % w;
+        if (j >= i && (j != k + 1 || i != k + 1))
+          G[i * q + j] = fma(-(G[k * q + i] * r), G[k * q + j], G[i * q + j]);
+      }
+    }
+    named_barrier(1, kCholThreads);
+  }
+  // R_kj = G_kj/√d_k (d_k = G_kk after its step), zero below the diagonal
+  for (int k = t; k < q; k += kCholThreads) dinv[k] = rsqrt_f64(fmax(G[k * q + k], 1e-300), 2);
+  named_barrier(1, kCholThreads);
+  for (int e = t; e < q * q; e += kCholThreads) {
+    const int i = e / q, j = e - i * q;
+    R[e] = j < i ? 0.0 : G[e] * dinv[i];
+  }
+  named_barrier(1, kCholThreads);
   return ok;
 }
 
@@ -254,39 +297,100 @@ __device__ __forceinline__ void pair_index(int e, int q, int& j, int& l) {
   l = row + left;
 }
 
+// Shared memory of a cond2 block (doubles): rows | R1 | dinv | dn | Rc | inv | R | Π2 | M.
+struct Cond2Smem {
+  int rows, r1q, dinv, dn, Rc, inv, R, P, M, total;
+  __host__ __device__ Cond2Smem(int rpb, int q, int r2) {
+    rows = 0;
+    r1q = rows + (rpb > q ? rpb : q) * q;
+    dinv = r1q + q * q;
+    dn = dinv + q;
+    Rc = dn + q;
+    inv = Rc + q * q;
+    R = inv + 2 * q;
+    P = R + q * q;
+    M = P + q * r2;
+    total = M + q * r2;
+  }
+};
+
 template <int PASS>
 __global__ void __launch_bounds__(kGramThreads) cond2_kernel(const Cond2Args a) {
   extern __shared__ __align__(16) double sm2[];
   __shared__ int s_last;
-  const int q = a.q, tid = threadIdx.x;
+  __shared__ int s_ok;
+  const int q = a.q, tid = threadIdx.x, lane = tid & 31;
   const int ne = q * (q + 1) / 2;
   const int r_lo = blockIdx.x * a.rows_per_block;
   const int r_hi = min(a.r1, r_lo + a.rows_per_block);
   const int nrows = r_hi - r_lo;
-  double* rows = sm2;                         // max(rows_per_block, q) × q: this block's rows, later the Gram
-  double* R1s = rows + max(a.rows_per_block, q) * q;   // q × q (pass 1: R1), then q reciprocals
-  double* dinv = R1s + q * q;
-  if (PASS == 1) {
+  const Cond2Smem L(a.rows_per_block, q, a.r2);
+  double* rows = sm2 + L.rows;                // this block's rows, later the Gram
+  double* R1s = sm2 + L.r1q;                  // pass 1: R1
+  double* dinv = sm2 + L.dinv;                // pass 1: 1/(R1)_kk
+  double* dn = sm2 + L.dn;                    // reciprocals of this pass's factor
+  if (PASS == 0) {
+    // Π2, unless the phase-1 reduction drew it, spread over all blocks.
+    if (!a.pi2_ready)
+      for (int e = blockIdx.x * blockDim.x + tid; e < q * a.r2; e += gridDim.x * blockDim.x)
+        a.pi2[e] = pi2_entry(a.key, a.problem, e);
+  } else {
     for (int e = tid; e < q * q; e += blockDim.x) R1s[e] = a.R1[e];
     for (int e = tid; e < q; e += blockDim.x) dinv[e] = a.R1dinv[e];
-    __syncthreads();
   }
-  if (PASS == 0) {
-    for (int e = tid; e < nrows * q; e += blockDim.x)
-      rows[e] = static_cast<double>(a.pix[static_cast<size_t>(r_lo) * q + e]);
-  } else {
-    // y·R1 = x by forward substitution, one row per thread
-    for (int i = tid; i < nrows; i += blockDim.x) {
-      const float* x = a.pix + static_cast<size_t>(r_lo + i) * q;
-      double* y = rows + i * q;
-      for (int c = 0; c < q; ++c) {
-        double v = static_cast<double>(x[c]);
-        for (int k = 0; k < c; ++k) v = fma(-y[k], R1s[k * q + c], v);
-        y[c] = v * dinv[c];
+  for (int e = tid; e < nrows * q; e += blockDim.x)
+    rows[e] = static_cast<double>(a.pix[static_cast<size_t>(r_lo) * q + e]);
+  __syncthreads();
+  if (PASS == 1) {
+    // y·R1 = x by forward substitution, right-looking: lane c of a warp holds the running
+    // value of column c of up to three rows; at step k the lane holding column k
+    // finishes y_k (a shuffle broadcasts it) and every later column subtracts y_k·R1_kc.
+    // The three rows of a warp are independent chains that overlap.  (Columns beyond 32:
+    // one row per thread.)
+    if (q <= 32) {
+      const int lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+      for (int i0 = warp; i0 < nrows; i0 += 3 * nw) {
+        double acc[3];
+        bool live[3];
+#pragma unroll
+        for (int u = 0; u < 3; ++u) {
+          const int i = i0 + u * nw;
+          live[u] = i < nrows;
+          acc[u] = (live[u] && lane < q) ? rows[i * q + lane] : 0.0;
+        }
+        for (int k = 0; k < q; ++k) {
+          const double rk = lane < q ? R1s[k * q + lane] : 0.0;
+          const double dk = dinv[k];
+#pragma unroll
+          for (int u = 0; u < 3; ++u) {
+            const double yk = __shfl_sync(0xffffffffu, acc[u], k) * dk;
+            if (lane == k) acc[u] = yk;
+            else if (lane > k) acc[u] = fma(-yk, rk, acc[u]);
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 3; ++u)
+          if (live[u] && lane < q) rows[(i0 + u * nw) * q + lane] = acc[u];
+      }
+    } else {
+      for (int i = tid; i < nrows; i += blockDim.x) {
+        double* y = rows + i * q;
+        for (int c = 0; c < q; ++c) {
+          double s0 = y[c], s1 = 0.0, s2 = 0.0, s3 = 0.0;
+          int k = 0;
+          for (; k + 3 < c; k += 4) {
+            s0 = fma(-y[k], R1s[k * q + c], s0);
+            s1 = fma(-y[k + 1], R1s[(k + 1) * q + c], s1);
+            s2 = fma(-y[k + 2], R1s[(k + 2) * q + c], s2);
+            s3 = fma(-y[k + 3], R1s[(k + 3) * q + c], s3);
+          }
+          for (; k < c; ++k) s0 = fma(-y[k], R1s[k * q + c], s0);
+          y[c] = ((s0 + s1) + (s2 + s3)) * dinv[c];
+        }
       }
     }
+    __syncthreads();
   }
-  __syncthreads();
   for (int e = tid; e < ne; e += blockDim.x) {
     int j, l;
     pair_index(e, q, j, l);
@@ -315,54 +419,79 @@ __global__ void __launch_bounds__(kGramThreads) cond2_kernel(const Cond2Args a) 
     pair_index(e, q, j, l);
     Gs[j * q + l] = v;
     Gs[l * q + j] = v;
+    if (PASS == 0 && j == l) a.colnorm[j] = sqrt(v);
   }
+  double* Ps = sm2 + L.P;
+  double* Rc = sm2 + L.Rc;                    // this pass's Cholesky factor
   if (PASS == 1)
-    for (int e = tid; e < q * a.r2; e += blockDim.x) a.pi2[e] = pi2_entry(a.key, a.problem, e);
+    for (int e = tid; e < q * a.r2; e += blockDim.x) Ps[e] = a.pi2[e];
   __syncthreads();
-  if (tid >= 32) return;
-  if (PASS == 0)
-    for (int k = tid; k < q; k += 32) a.colnorm[k] = sqrt(Gs[k * q + k]);
-  double* dn = dinv + q;                      // reciprocals of this pass's factor
-  const bool ok = warp_cholesky(Gs, dn, q);
-  if (tid == 0 && !ok) raise_flag(a.flags, L1S_ERR_RANK_DEFICIENT);
+  if (tid < kCholThreads) {
+    // FP32-accurate pivot reciprocals suffice for R1, which only preconditions pass 1
+    const bool ok = block_cholesky(Gs, Rc, dn, sm2 + L.inv, q, PASS == 0 ? 0 : 2);
+    if (tid == 0) s_ok = ok ? 1 : 0;
+  }
+  __syncthreads();
   if (PASS == 0) {
-    for (int e = tid; e < q * q; e += 32) a.R1[e] = Gs[e];
-    for (int e = tid; e < q; e += 32) a.R1dinv[e] = dn[e];
+    if (tid == 0 && !s_ok) raise_flag(a.flags, L1S_ERR_RANK_DEFICIENT);
+    for (int e = tid; e < q * q; e += blockDim.x) a.R1[e] = Rc[e];
+    for (int e = tid; e < q; e += blockDim.x) a.R1dinv[e] = dn[e];
   } else {
-    // R = R2·R1 (both upper triangular) and the reciprocals of its diagonal
-    for (int e = tid; e < q * q; e += 32) {
+    double* Rs = sm2 + L.R;
+    double* Ms = sm2 + L.M;
+    // R = R2·R1 (both upper triangular), all threads
+    for (int e = tid; e < q * q; e += blockDim.x) {
       const int i = e / q, j = e - i * q;
-      double v = 0.0;
-      for (int k = i; k <= j; ++k) v = fma(Gs[i * q + k], R1s[k * q + j], v);
-      a.R[e] = j < i ? 0.0 : v;
+      double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+      int k = i;
+      for (; k + 3 <= j; k += 4) {
+        s0 = fma(Rc[i * q + k], R1s[k * q + j], s0);
+        s1 = fma(Rc[i * q + k + 1], R1s[(k + 1) * q + j], s1);
+        s2 = fma(Rc[i * q + k + 2], R1s[(k + 2) * q + j], s2);
+        s3 = fma(Rc[i * q + k + 3], R1s[(k + 3) * q + j], s3);
+      }
+      for (; k <= j; ++k) s0 = fma(Rc[i * q + k], R1s[k * q + j], s0);
+      Rs[e] = j < i ? 0.0 : (s0 + s1) + (s2 + s3);
     }
-    __syncwarp();
-    for (int k = tid; k < q; k += 32) dn[k] = dn[k] * dinv[k];   // 1/(R2_kk·R1_kk)
-    __syncwarp();
-    if (tid == 0) {
-      bool bad = !ok;
-      for (int k = 0; k < q; ++k) {
-        const double rkk = a.R[k * q + k];
+    for (int k = tid; k < q; k += blockDim.x) dn[k] = dn[k] * dinv[k];   // 1/(R2_kk·R1_kk)
+    __syncthreads();
+    if (tid < 32) {
+      // rank test over the columns, one lane per column
+      bool bad = false;
+      for (int k = tid; k < q; k += 32) {
+        const double rkk = Rs[k * q + k];
         if (!(rkk > kRankTol * a.colnorm[k]) || !isfinite(rkk)) bad = true;
       }
-      if (bad) raise_flag(a.flags, L1S_ERR_RANK_DEFICIENT);
-    }
-    // M = R⁻¹·Π2 by back substitution with the stored reciprocals, one column per lane
-    for (int c = tid; c < a.r2; c += 32) {
-      for (int k = q - 1; k >= 0; --k) {
-        double acc = a.pi2[k * a.r2 + c];
-        for (int j = k + 1; j < q; ++j) acc = fma(-a.R[k * q + j], a.M64[j * a.r2 + c], acc);
-        a.M64[k * a.r2 + c] = acc * dn[k];
+      if (__any_sync(0xffffffffu, bad) || !s_ok) {
+        if (tid == 0) raise_flag(a.flags, L1S_ERR_RANK_DEFICIENT);
       }
     }
-    __syncwarp();
-    for (int e = tid; e < q * a.r2; e += 32) {
-      const double m = a.M64[e];
+    // M = R⁻¹·Π2 by back substitution, right-looking, threads 0..127: M starts as Π2; at
+    // step k row k is finished (times 1/R_kk) and every row above subtracts R_jk·M_k·.
+    if (tid < kCholThreads) {
+      for (int e = tid; e < q * a.r2; e += kCholThreads) Ms[e] = Ps[e];
+      named_barrier(1, kCholThreads);
+      for (int k = q - 1; k >= 0; --k) {
+        for (int c = tid; c < a.r2; c += kCholThreads) Ms[k * a.r2 + c] *= dn[k];
+        named_barrier(1, kCholThreads);
+        for (int e = tid; e < k * a.r2; e += kCholThreads) {
+          const int j = e / a.r2, c = e - j * a.r2;
+          Ms[e] = fma(-Rs[j * q + k], Ms[k * a.r2 + c], Ms[e]);
+        }
+        named_barrier(1, kCholThreads);
+      }
+    }
+    __syncthreads();
+    for (int e = tid; e < q * a.r2; e += blockDim.x) {
+      const double m = Ms[e];
+      a.M64[e] = m;
       a.M32[e] = static_cast<float>(m);
       if (a.M_user) a.M_user[e] = m;
     }
-    if (a.R_user)
-      for (int e = tid; e < q * q; e += 32) a.R_user[e] = a.R[e];
+    for (int e = tid; e < q * q; e += blockDim.x) {
+      a.R[e] = Rs[e];
+      if (a.R_user) a.R_user[e] = Rs[e];
+    }
   }
   if (tid == 0) *a.ticket = 0u;   // ready for the next launch
 }
@@ -382,8 +511,16 @@ size_t cond2_scratch_bytes(int r1, int q, int sms) {
   return sizeof(double) * (static_cast<size_t>(blocks) * (q * (q + 1) / 2) + q * q + 2 * q) + 256;
 }
 
+bool launch_condition_householder(const Plan& pl, const float* pix, const l1s_params* p, double* R_user,
+                                  double* M_user, unsigned char* ws, cudaStream_t st);
+
 bool launch_condition(const Plan& pl, const float* pix, const l1s_params* p, double* R_user,
-                      double* M_user, unsigned char* ws, cudaStream_t st) {
+                      double* M_user, unsigned char* ws, cudaStream_t st, bool pi2_ready) {
+  // Wide X (q near 129) does not fit the CholeskyQR2 blocks in shared memory: one block
+  // of Householder reflections on a workspace copy handles it instead.
+  if (sizeof(double) * static_cast<size_t>(Cond2Smem(cond2_rows_per_block(pl.r1, pl.q), pl.q, pl.r2).total) >
+      static_cast<size_t>(device_info().max_smem_optin))
+    return launch_condition_householder(pl, pix, p, R_user, M_user, ws, st);
   Cond2Args a;
   a.pix = pix;
   a.r1 = pl.r1;
@@ -407,7 +544,8 @@ bool launch_condition(const Plan& pl, const float* pix, const l1s_params* p, dou
   a.R_user = R_user;
   a.M_user = M_user;
   a.flags = reinterpret_cast<uint32_t*>(ws + pl.off_status);
-  const size_t smem = sizeof(double) * (static_cast<size_t>(std::max(a.rows_per_block, pl.q)) * pl.q + 2 * pl.q * pl.q + 2 * pl.q);
+  a.pi2_ready = pi2_ready ? 1 : 0;
+  const size_t smem = sizeof(double) * static_cast<size_t>(Cond2Smem(a.rows_per_block, pl.q, pl.r2).total);
   if (!cuda_ok(cudaFuncSetAttribute(cond2_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)),
                "cond2 smem") ||
       !cuda_ok(cudaFuncSetAttribute(cond2_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)),
@@ -420,7 +558,7 @@ bool launch_condition(const Plan& pl, const float* pix, const l1s_params* p, dou
   return cuda_ok(cudaGetLastError(), "launch condition");
 }
 
-// The one-block Householder variant (kept for reference checks of the Cholesky route).
+// The one-block Householder variant (wide X).
 bool launch_condition_householder(const Plan& pl, const float* pix, const l1s_params* p, double* R_user,
                                   double* M_user, unsigned char* ws, cudaStream_t st) {
   CondArgs a;

@@ -1036,9 +1036,15 @@ __global__ void __launch_bounds__(SrtCfg<W>::kThreads) fct_embed_sorted_kernel(c
 // Fixed-order sum of the per-block partials: PiX[r][c0+c] = Σ_blocks partial[r][c].
 // Block = 32 warps; warp w adds partials w, w+32, …; warp 0 then adds the 32
 // warp sums in order, so the result does not depend on scheduling.
+// It also draws Π2 (q × r2 FP64, when pi2 is non-null), which depends on no data, so
+// that the FP64 Cauchy transforms stay off the conditioning's serial path.
 __global__ void __launch_bounds__(1024) fct_reduce_kernel(const float* __restrict__ partials, int ctas,
                                                           int r1, int W, int q, float* __restrict__ pix,
-                                                          uint32_t* flags) {
+                                                          uint32_t* flags, Key2 key, uint32_t problem,
+                                                          int npi2, double* __restrict__ pi2) {
+  if (pi2 && blockIdx.y == 0)
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < npi2; e += gridDim.x * blockDim.x)
+      pi2[e] = pi2_entry(key, problem, e);
   __shared__ float red[32][33];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int per = r1 * W;
@@ -1195,7 +1201,7 @@ int fct_threads_for(int log2s, int width) {
 }
 
 bool launch_fct(const Plan& pl, const void* A, int64_t lda, l1s_dtype dt, const float* b,
-                const l1s_params* p, float* pix, unsigned char* ws, cudaStream_t st) {
+                const l1s_params* p, float* pix, unsigned char* ws, cudaStream_t st, double* pi2_out) {
   FctArgs a;
   a.A = A;
   a.lda = lda;
@@ -1240,7 +1246,8 @@ bool launch_fct(const Plan& pl, const void* A, int64_t lda, l1s_dtype dt, const 
     return false;
   const int per = pl.r1 * pl.fct_width;
   dim3 rgrid((per + 31) / 32, pl.fct_slices);
-  fct_reduce_kernel<<<rgrid, 1024, 0, st>>>(a.partials, pl.fct_ctas, pl.r1, pl.fct_width, pl.q, pix, a.flags);
+  fct_reduce_kernel<<<rgrid, 1024, 0, st>>>(a.partials, pl.fct_ctas, pl.r1, pl.fct_width, pl.q, pix, a.flags, a.key,
+                                            a.problem, pl.q * pl.r2, pi2_out);
   count_launch(2);
   return cuda_ok(cudaGetLastError(), "launch fct_reduce");
 }

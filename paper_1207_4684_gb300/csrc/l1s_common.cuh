@@ -9,6 +9,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <float.h>
 #include <stdint.h>
 
 #include "../../include/l1fct.h"
@@ -244,6 +245,41 @@ struct Plan {
 
 bool make_plan(const l1s_params* p, int64_t n, int d, l1s_dtype dt, bool host_staging, Plan* plan,
                const l1s_schedule* override_sch = nullptr);
+// Π2 entry e (row-major q × r2): word e mod 4 of Philox call ⌊e/4⌋ on stream 1.
+__device__ __forceinline__ double pi2_entry(Key2 key, uint32_t problem, int e) {
+  const uint4 o = philox4x32_10(make_uint4(static_cast<uint32_t>(e >> 2), 0u, problem, kStreamPi2), key);
+  const uint32_t w = (e & 3) == 0 ? o.x : (e & 3) == 1 ? o.y : (e & 3) == 2 ? o.z : o.w;
+  return cauchy_f64(w >> 8);
+}
+
+// Σ of the λ block partials in a fixed order, for a block of 256 threads: strided
+// per-thread sums, a fixed shuffle tree, then the eight warp sums in order (every
+// thread returns the total).  The finalize kernel and the sampling kernel both use it,
+// so they obtain the same bits.
+__device__ __forceinline__ double lambda_total_256(const double* __restrict__ sums, int n, double* wsum8) {
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < n; i += 256) acc += sums[i];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+  if ((threadIdx.x & 31) == 0) wsum8[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  double tot = 0.0;
+  for (int w = 0; w < 8; ++w) tot += wsum8[w];
+  return tot;
+}
+
+// τ = m_s / Σλ (FP64, one division) and its FP32 copy; false when Σλ is zero or not finite.
+__device__ __forceinline__ bool tau_of(double tot, double coreset, double* tau, float* tau32) {
+  if (!(tot > 0.0) || !isfinite(tot)) {
+    *tau = 0.0;
+    *tau32 = 0.f;
+    return false;
+  }
+  *tau = coreset / tot;
+  *tau32 = *tau > static_cast<double>(FLT_MAX) ? FLT_MAX : static_cast<float>(*tau);
+  return true;
+}
+
 // Adds k to the process-wide count of kernels the library has launched.
 void count_launch(int k);
 // The schedule installed for (d, dt, log2 s); false (and *out zeroed) when none is.

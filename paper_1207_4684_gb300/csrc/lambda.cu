@@ -255,26 +255,15 @@ __global__ void __launch_bounds__(kLamThreads) lambda_kernel_generic(const TA* _
 __global__ void __launch_bounds__(256) lambda_finalize_kernel(const double* __restrict__ block_sums, int nblocks,
                                                               double coreset, StatusBlock* status, double* user_sum) {
   __shared__ double wsum[8];
-  double acc = 0.0;
-  for (int i = threadIdx.x; i < nblocks; i += blockDim.x) acc += block_sums[i];
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
-  if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = acc;
-  __syncthreads();
+  const double tot = lambda_total_256(block_sums, nblocks, wsum);
   if (threadIdx.x == 0) {
-    double tot = 0.0;
-    for (int w = 0; w < (blockDim.x >> 5); ++w) tot += wsum[w];
     status->lambda_total = tot;
     if (user_sum) *user_sum = tot;
-    if (!(tot > 0.0) || !isfinite(tot)) {
-      raise_flag(&status->flags, L1S_ERR_ZERO_MASS);
-      status->tau = 0.0;
-      status->tau32 = 0.f;
-    } else {
-      const double tau = coreset / tot;
-      status->tau = tau;
-      status->tau32 = tau > static_cast<double>(FLT_MAX) ? FLT_MAX : static_cast<float>(tau);
-    }
+    double tau;
+    float tau32;
+    if (!tau_of(tot, coreset, &tau, &tau32)) raise_flag(&status->flags, L1S_ERR_ZERO_MASS);
+    status->tau = tau;
+    status->tau32 = tau32;
   }
 }
 
@@ -338,9 +327,11 @@ bool launch_lambda_tc(int64_t n, const void* A, const float* b, const float* m32
 
 // M (FP32, q × r2 in the workspace) → constant bank, then λ and Σλ.  BF16 A with d = r2 = 32
 // runs on the tensor cores (M_A rounded to BF16; its transpose goes to the Π2 region, 2 KB).
+// With nsums_out non-NULL the Σλ/τ step is left to the sampling kernel: the number of
+// block partials is returned there instead of launching the finalize kernel.
 bool launch_lambda(const Plan& pl, const void* A, int64_t lda, l1s_dtype dt, const float* b,
                    const float* m32, const l1s_params* p, float* lam, double* user_sum,
-                   unsigned char* ws, cudaStream_t st) {
+                   unsigned char* ws, cudaStream_t st, int* nsums_out) {
   const bool smem_m = pl.lam_m_in_smem != 0;
   if (!smem_m && !cuda_ok(cudaMemcpyToSymbolAsync(c_M, m32, sizeof(float) * pl.q * pl.r2, 0,
                                                   cudaMemcpyDeviceToDevice, st),
@@ -364,6 +355,10 @@ bool launch_lambda(const Plan& pl, const void* A, int64_t lda, l1s_dtype dt, con
                : launch_lambda_t<float, false>(pl, static_cast<const float*>(A), lda, b, lam, sums, m32, st);
   }
   if (!ok) return false;
+  if (nsums_out) {
+    *nsums_out = blocks;
+    return true;
+  }
   lambda_finalize_kernel<<<1, 256, 0, st>>>(sums, blocks, p->coreset_size,
                                            reinterpret_cast<StatusBlock*>(ws + pl.off_status), user_sum);
   count_launch(1);

@@ -25,7 +25,7 @@ namespace l1s {
 
 bool launch_lambda(const Plan& pl, const void* A, int64_t lda, l1s_dtype dt, const float* b,
                    const float* m32, const l1s_params* p, float* lam, double* user_sum,
-                   unsigned char* ws, cudaStream_t st);
+                   unsigned char* ws, cudaStream_t st, int* nsums_out = nullptr);
 bool launch_m_to_f32(const double* m, int total, float* out, cudaStream_t st);
 
 constexpr size_t kScratchBytes = 40 * 1024;  // holds q·r2 up to 65·64 with 1216 partial sums

@@ -17,6 +17,7 @@
 namespace l1s {
 
 constexpr int kSmpThreads = 256;
+static_assert(kSmpThreads == 256, "lambda_total_256 assumes blocks of 256 threads");
 
 __device__ __forceinline__ uint64_t spread_bits(uint32_t x) {
   uint64_t v = x;
@@ -54,17 +55,37 @@ struct MarkArgs {
   uint64_t* mask;        // ⌈n/64⌉ words
   int64_t* counts;       // per block
   int lam_pairs;         // 1: λ is 8-byte aligned, read two rows per load
+  const double* lam_sums;  // λ block partials when this kernel forms Σλ and τ itself (else null)
+  int nsums;
+  double coreset;        // m_s
+  StatusBlock* status_rw;
 };
 
 constexpr int kMarkUnroll = 4;
 
 __global__ void __launch_bounds__(kSmpThreads) sample_mark_kernel(const MarkArgs a) {
   __shared__ int64_t wcount[kSmpThreads / 32];
+  __shared__ double wsum[8];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const int64_t start = static_cast<int64_t>(blockIdx.x) * a.chunk;
   const int64_t stop = min(a.n, start + a.chunk);
-  const double tau = a.p ? 0.0 : a.status->tau;
-  const float tau32 = a.p ? 0.f : a.status->tau32;
+  double tau = 0.0;
+  float tau32 = 0.f;
+  if (a.lam_sums) {
+    // Σλ over the λ block partials (the same fixed order as the finalize kernel) and
+    // τ = m_s/Σλ, formed by every block; block 0 records them in the status block.
+    const double tot = lambda_total_256(a.lam_sums, a.nsums, wsum);
+    const bool ok = tau_of(tot, a.coreset, &tau, &tau32);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      a.status_rw->lambda_total = tot;
+      a.status_rw->tau = tau;
+      a.status_rw->tau32 = tau32;
+      if (!ok) raise_flag(&a.status_rw->flags, L1S_ERR_ZERO_MASS);
+    }
+  } else if (!a.p) {
+    tau = a.status->tau;
+    tau32 = a.status->tau32;
+  }
   const bool odd_offset = (a.row_offset & 1) != 0;
   const int64_t stride = 64 * static_cast<int64_t>(nwarps);
   int64_t kept = 0;
@@ -155,17 +176,21 @@ struct CompactArgs {
 
 template <typename TA>
 __global__ void __launch_bounds__(kSmpThreads) sample_compact_kernel(const CompactArgs<TA> a) {
-  __shared__ int64_t sh[kSmpThreads];
+  constexpr int kWarps = kSmpThreads / 32;
+  __shared__ int64_t s_warp[kWarps];
   __shared__ int64_t s_base;
-  const int tid = threadIdx.x;
-  // Offset of this block: Σ counts of the blocks before it.
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  // Offset of this block: Σ counts of the blocks before it (per-thread sums, then warp
+  // shuffles and the warp totals in a fixed order).
   int64_t pre = 0;
   for (int i = tid; i < static_cast<int>(blockIdx.x); i += blockDim.x) pre += a.counts[i];
-  sh[tid] = pre;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) pre += __shfl_xor_sync(0xffffffffu, pre, o);
+  if (lane == 0) s_warp[warp] = pre;
   __syncthreads();
   if (tid == 0) {
     int64_t t = 0;
-    for (int i = 0; i < static_cast<int>(blockDim.x); ++i) t += sh[i];
+    for (int w = 0; w < kWarps; ++w) t += s_warp[w];
     s_base = t;
     if (blockIdx.x == gridDim.x - 1) {
       const int64_t total = t + a.counts[blockIdx.x];
@@ -185,17 +210,24 @@ __global__ void __launch_bounds__(kSmpThreads) sample_compact_kernel(const Compa
     const int64_t wi = tile + tid;
     const uint64_t m = wi < w1 ? a.mask[wi] : 0ull;
     const int64_t c = __popcll(m);
-    // inclusive scan of c over the block (Hillis–Steele in shared memory)
-    sh[tid] = c;
-    __syncthreads();
-    for (int off = 1; off < static_cast<int>(blockDim.x); off <<= 1) {
-      const int64_t v = tid >= off ? sh[tid - off] : 0;
-      __syncthreads();
-      sh[tid] += v;
-      __syncthreads();
+    // inclusive scan of c over the block: within warps by shuffles, then over warp totals
+    int64_t incl = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int64_t t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
     }
-    int64_t pos = base + sh[tid] - c;
-    const int64_t tile_total = sh[blockDim.x - 1];
+    __syncthreads();                                  // s_warp free from the previous tile
+    if (lane == 31) s_warp[warp] = incl;
+    __syncthreads();
+    int64_t woff = 0, tile_total = 0;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) {
+      const int64_t v = s_warp[w];
+      woff += w < warp ? v : 0;
+      tile_total += v;
+    }
+    int64_t pos = base + woff + incl - c;
     uint64_t bits = m;
     while (bits) {
       const int bit = __ffsll(static_cast<long long>(bits)) - 1;
@@ -214,7 +246,6 @@ __global__ void __launch_bounds__(kSmpThreads) sample_compact_kernel(const Compa
       ++pos;
     }
     base += tile_total;
-    __syncthreads();
   }
 }
 
@@ -223,7 +254,7 @@ int sample_threads() { return kSmpThreads; }
 bool launch_sample(const Plan& pl, const float* lam, const double* p, const l1s_params* prm,
                    const void* A, int64_t lda, l1s_dtype dt, const float* b, int64_t capacity,
                    int64_t* idx, double* w, double* coreset, int64_t* count_out, unsigned char* ws,
-                   cudaStream_t st) {
+                   cudaStream_t st, int lam_nsums) {
   MarkArgs m;
   m.lam = lam;
   m.p = p;
@@ -236,6 +267,10 @@ bool launch_sample(const Plan& pl, const float* lam, const double* p, const l1s_
   m.mask = reinterpret_cast<uint64_t*>(ws + pl.off_mask);
   m.counts = reinterpret_cast<int64_t*>(ws + pl.off_counts);
   m.lam_pairs = (reinterpret_cast<uintptr_t>(lam) % 8 == 0) ? 1 : 0;
+  m.lam_sums = lam_nsums > 0 ? reinterpret_cast<const double*>(ws + pl.off_lamsum) : nullptr;
+  m.nsums = lam_nsums;
+  m.coreset = prm->coreset_size;
+  m.status_rw = reinterpret_cast<StatusBlock*>(ws + pl.off_status);
   sample_mark_kernel<<<pl.smp_ctas, pl.smp_threads, 0, st>>>(m);
   count_launch(1);
   if (!cuda_ok(cudaGetLastError(), "launch sample_mark")) return false;
