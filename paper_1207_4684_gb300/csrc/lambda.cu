@@ -341,7 +341,7 @@ bool launch_lambda(const Plan& pl, const void* A, int64_t lda, l1s_dtype dt, con
   int blocks = pl.lam_ctas;
   bool ok;
   if (lambda_tc_applies(pl.d, pl.r2, lda, A, dt)) {
-    blocks = std::min(pl.lam_ctas, device_info().sms);
+    blocks = std::min(pl.lam_ctas, 3 * device_info().sms);   // three resident per SM (64 TMEM columns each)
     ok = launch_lambda_tc(pl.n, A, b, m32, reinterpret_cast<uint16_t*>(ws + pl.off_pi2), lam, sums, blocks,
                           reinterpret_cast<uint32_t*>(ws + pl.off_status), st);
   } else {

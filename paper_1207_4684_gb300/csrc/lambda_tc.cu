@@ -5,7 +5,8 @@
 // tensor memory, M = 128 rows, N = r2 = 32, K = d = 32 in two K = 16 steps); the b
 // column, |·| and the median stay in FP32 registers.
 //
-// Roles of the six warps of a persistent thread block (one per SM):
+// Roles of the six warps of a persistent thread block (three per SM, so that twelve
+// epilogue warps share each SM):
 //   warp 0  TMA producer: 128-row tiles of A (2-D tensor map, 64-byte swizzle) into a
 //           ring of shared-memory stages, and the BF16 M_Aᵀ tile once;
 //   warp 1  allocates 64 TMEM columns (two accumulators) and, from one thread, issues
@@ -135,7 +136,7 @@ struct TcArgs {
   const float* mb;    // M's last row (the b column), FP32, r2 values
 };
 
-__global__ void __launch_bounds__(kTcThreads, 1) lambda_tc_kernel(const __grid_constant__ CUtensorMap mapA,
+__global__ void __launch_bounds__(kTcThreads, 3) lambda_tc_kernel(const __grid_constant__ CUtensorMap mapA,
                                                                   const __grid_constant__ CUtensorMap mapB,
                                                                   const TcArgs a) {
   extern __shared__ __align__(1024) unsigned char tc_smem[];
