@@ -18,7 +18,8 @@ const void* fct_kernel(int log2s, l1s_dtype dt, bool staged);
 size_t fct_smem_bytes(int s, int d, l1s_dtype dt, int r1, int width, bool staged);
 int fct_threads_for(int log2s, int width);
 int fct_ws_width(int log2s, int d);
-const void* fct_ws_kernel(int log2s, l1s_dtype dt, int w);
+int fct_ws_tile_log2(int log2s);
+const void* fct_ws_kernel(int log2t, int log2s, l1s_dtype dt, int w);
 int fct_ws_threads(int w);
 size_t fct_ws_smem_bytes(int s, int d, l1s_dtype dt, int r1, int w);
 int fct_sorted_width(int log2s, int d);
@@ -166,6 +167,7 @@ struct FctGeometry {
   bool ok;
   bool staged;
   int ws;                 // column width of the narrow-X kernel, 0 otherwise
+  int tile_log2;          // its tile
   int sorted;             // column width of the bucket-sorted kernel, 0 otherwise
   int slices, width, threads, per_sm;
   size_t smem;
@@ -184,8 +186,9 @@ static FctGeometry fct_geometry(int variant, const Plan& P, l1s_dtype dt, const 
     staged = true;
   } else if (variant == 1) {
     const int w = fct_ws_width(P.log2s, P.d);
-    if (!w || fct_ws_smem_bytes(P.s, P.d, dt, P.r1, w) > budget1) return g;
+    if (!w || fct_ws_smem_bytes(1 << fct_ws_tile_log2(P.log2s), P.d, dt, P.r1, w) > budget1) return g;
     g.ws = w;
+    g.tile_log2 = fct_ws_tile_log2(P.log2s);
     staged = true;
   } else if (variant == 2) {
     if (fct_smem_bytes(P.s, P.d, dt, P.r1, P.q, true) > budget1) return g;
@@ -210,10 +213,11 @@ static FctGeometry fct_geometry(int variant, const Plan& P, l1s_dtype dt, const 
   g.slices = (P.q + width - 1) / width;
   g.width = width;
   g.smem = g.sorted ? fct_sorted_smem_bytes(P.s, P.d, dt, P.r1, g.sorted)
-                    : (g.ws ? fct_ws_smem_bytes(P.s, P.d, dt, P.r1, g.ws) : fct_smem_bytes(P.s, P.d, dt, P.r1, width, staged));
+                    : (g.ws ? fct_ws_smem_bytes(1 << g.tile_log2, P.d, dt, P.r1, g.ws)
+                            : fct_smem_bytes(P.s, P.d, dt, P.r1, width, staged));
   g.threads = g.sorted ? fct_sorted_threads(g.sorted) : (g.ws ? fct_ws_threads(g.ws) : fct_threads_for(P.log2s, width));
   const void* fn = g.sorted ? fct_sorted_kernel(P.log2s, dt, g.sorted)
-                            : (g.ws ? fct_ws_kernel(P.log2s, dt, g.ws) : fct_kernel(P.log2s, dt, staged));
+                            : (g.ws ? fct_ws_kernel(g.tile_log2, P.log2s, dt, g.ws) : fct_kernel(P.log2s, dt, staged));
   if (!cuda_ok(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(g.smem)),
                "cudaFuncSetAttribute(fct_embed)"))
     return g;
@@ -228,7 +232,8 @@ static FctGeometry fct_geometry(int variant, const Plan& P, l1s_dtype dt, const 
 
 static int64_t fct_ctas_of(const FctGeometry& g, const Plan& P, const DeviceInfo& di, int per_sm) {
   const int64_t want = std::max<int64_t>(1, static_cast<int64_t>(di.sms) * per_sm / g.slices);
-  return std::min<int64_t>(P.nblocks, want);
+  const int64_t tiles = g.ws ? (P.n + (int64_t{1} << g.tile_log2) - 1) >> g.tile_log2 : P.nblocks;
+  return std::min<int64_t>(tiles, want);
 }
 
 // Bounds of the schedule fields (the workspace is sized for the largest).
@@ -268,6 +273,7 @@ bool make_plan(const l1s_params* p, int64_t n, int d, l1s_dtype dt, bool host_st
   if (sch.fct_variant >= 1 && sch.fct_variant <= 4 && geo[sch.fct_variant].ok) variant = sch.fct_variant;
   const FctGeometry& g = geo[variant];
   P.fct_ws = g.ws;
+  P.fct_tile_log2 = g.tile_log2;
   P.fct_sorted = g.sorted;
   P.fct_staged = g.staged ? 1 : 0;
   P.fct_slices = g.slices;

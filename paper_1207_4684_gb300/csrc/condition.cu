@@ -172,6 +172,9 @@ __global__ void __launch_bounds__(kCondThreads) condition_kernel(const CondArgs 
 // reciprocal — and run right-looking (each step finishes one row or column and updates
 // the rest in parallel), so the dependent chain per step is a few operations long.
 constexpr int kGramThreads = 256;
+// Blocks per first-level group of the partial sums: one group (a single level) for
+// q ≤ 32, groups of 8 for wider X, whose partials are long.
+__host__ __device__ __forceinline__ int cond2_group_size(int q, int blocks) { return q > 32 ? 8 : blocks; }
 
 struct Cond2Args {
   const float* pix;      // r1 × q row-major FP32
@@ -179,8 +182,8 @@ struct Cond2Args {
   int rows_per_block;
   Key2 key;
   uint32_t problem;
-  double* partials;      // [gridDim.x][q(q+1)/2]
-  unsigned int* ticket;
+  double* partials;      // [gridDim.x][q(q+1)/2], then the group sums
+  unsigned int* ticket;  // group tickets [groups], then the final ticket (zero before each pass)
   double* R1;            // q × q (pass 0 → pass 1)
   double* R1dinv;        // q: 1 / (R1)_kk
   double* colnorm;       // q: ‖(Π1X)_:k‖₂
@@ -196,8 +199,7 @@ struct Cond2Args {
 
 // On this part every FP64 warp instruction occupies its SM sub-partition for tens of
 // cycles, so the serial steps below keep their FP64 chains short and spread the
-// independent work over four warps (one per sub-partition, named barrier 1).
-constexpr int kCholThreads = 128;
+// independent work over all warps of the block.
 
 // 1/x and 1/√x for x > 0 in FP64: an FP32 estimate of the mantissa part (the exponent is
 // split off first, so any normal FP64 x works), then Newton steps in FP64 — for 1/x
@@ -225,17 +227,24 @@ __device__ __forceinline__ double rsqrt_f64(double x, int steps) {
 }
 
 // Cholesky of the symmetric q×q matrix G (row-major, upper triangle, shared memory) by
-// threads 0..127, in the square-root-free form G = LᵀDL first: step k subtracts
-// G_ki·G_kj/d_k from the trailing block (warps 1-3) while thread 0 forms the next
-// pivot — the same FMA the update would apply to G_{k+1,k+1} — and its reciprocal,
-// so the serial chain per step is one reciprocal.  Then R_kj = G_kj/√d_k for all
+// all threads of the block, in the square-root-free form G = LᵀDL first: step k
+// subtracts G_ki·G_kj/d_k from the trailing triangle (warps 1 and up, a row per warp)
+// while thread 0 forms the next pivot — the same FMA the update would apply to
+// G_{k+1,k+1} — and its reciprocal, so the serial chain per step is one reciprocal.  Then R_kj = G_kj/√d_k for all
 // entries at once, and dinv[k] = 1/R_kk.  s_r holds q doubles.  Returns false when a
 // pivot is not positive.
 // chain_steps Newton steps refine the pivots' reciprocals on the serial chain (0 leaves
 // them FP32-accurate, which only perturbs G by about 1e-7 relative: enough for a
 // preconditioner); the final 1/√d_k always take two.
-__device__ bool block_cholesky(double* G, double* R, double* dinv, double* s_r, int q, int chain_steps) {
-  const int t = threadIdx.x;
+// Threads [0, nt) take part (nt a multiple of 32: 128 for q ≤ 32, where four warps are
+// enough and a named barrier is cheaper, else the whole block).
+__device__ __forceinline__ void sync_first(int nt) {
+  if (nt == static_cast<int>(blockDim.x)) __syncthreads();
+  else named_barrier(1, nt);
+}
+
+__device__ bool block_cholesky(double* G, double* R, double* dinv, double* s_r, int q, int chain_steps, int nt) {
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5, nw = nt >> 5;
   const int steps = chain_steps;
   bool ok = true;
   if (t == 0) {
@@ -243,34 +252,60 @@ __device__ bool block_cholesky(double* G, double* R, double* dinv, double* s_r, 
     s_r[0] = rcp_f64(fmax(a, 1e-300), steps);
     if (!(a > 0.0) || !isfinite(a)) ok = false;
   }
-  named_barrier(1, kCholThreads);
+  sync_first(nt);
   for (int k = 0; k + 1 < q; ++k) {
     const double r = s_r[k];
     if (t == 0) {
       const double g = G[k * q + k + 1];
       const double an = fma(-(g * r), g, G[(k + 1) * q + k + 1]);
-      G[(k + 1) * q + k + 1] = an;   // the one trailing entry warps 1-3 leave to thread 0
+      G[(k + 1) * q + k + 1] = an;   // the one trailing entry the other warps leave to thread 0
       s_r[k + 1] = rcp_f64(fmax(an, 1e-300), steps);
       if (!(an > 0.0) || !isfinite(an)) ok = false;
-    } else if (t >= 32) {
+    } else if (warp > 0) {
       const int w = q - k - 1;
-      for (int e = t - 32; e < w * w; e += kCholThreads - 32) {
-        const int i = k + 1 + e / w, j = k + 1 + e % w;
-        if (j >= i && (j != k + 1 || i != k + 1))
-          G[i * q + j] = fma(-(G[k * q + i] * r), G[k * q + j], G[i * q + j]);
+      if (q <= 32) {
+        // small trailing block: its w×w entries spread flat over warps 1 and up
+        for (int e = t - 32; e < w * w; e += nt - 32) {
+          const int i = k + 1 + e / w, j = k + 1 + e % w;
+          if (j >= i && (j != k + 1 || i != k + 1))
+            G[i * q + j] = fma(-(G[k * q + i] * r), G[k * q + j], G[i * q + j]);
+        }
+      } else {
+        // rows i = k+1.. of the trailing upper triangle, one row per warp, lanes over j ≥ i
+        for (int i = k + warp; i < q; i += nw - 1) {
+          const double gki = G[k * q + i] * r;
+          for (int j = i + lane; j < q; j += 32)
+            if (j != k + 1 || i != k + 1) G[i * q + j] = fma(-gki, G[k * q + j], G[i * q + j]);
+        }
       }
     }
-    named_barrier(1, kCholThreads);
+    sync_first(nt);
   }
   // R_kj = G_kj/√d_k (d_k = G_kk after its step), zero below the diagonal
-  for (int k = t; k < q; k += kCholThreads) dinv[k] = rsqrt_f64(fmax(G[k * q + k], 1e-300), 2);
-  named_barrier(1, kCholThreads);
-  for (int e = t; e < q * q; e += kCholThreads) {
+  for (int k = t; k < q; k += nt) dinv[k] = rsqrt_f64(fmax(G[k * q + k], 1e-300), 2);
+  sync_first(nt);
+  for (int e = t; e < q * q; e += nt) {
     const int i = e / q, j = e - i * q;
     R[e] = j < i ? 0.0 : G[e] * dinv[i];
   }
-  named_barrier(1, kCholThreads);
+  sync_first(nt);
   return ok;
+}
+
+// Right-looking back substitution in place, all threads of the block: on entry M holds
+// B (q × r2), on return R⁻¹·B for the upper-triangular R (row-major q × q) with dinv[k] =
+// 1/R_kk: step k finishes row k, then every row above subtracts R_jk·M_k·.
+__device__ void block_back_subst(const double* R, const double* dinv, double* M, int q, int r2, int nt) {
+  const int t = threadIdx.x;
+  for (int k = q - 1; k >= 0; --k) {
+    for (int c = t; c < r2; c += nt) M[k * r2 + c] *= dinv[k];
+    sync_first(nt);
+    for (int e = t; e < k * r2; e += nt) {
+      const int j = e / r2, c = e - j * r2;
+      M[e] = fma(-R[j * q + k], M[k * r2 + c], M[e]);
+    }
+    sync_first(nt);
+  }
 }
 
 // Σ_{i<count} a[i·stride] with four independent accumulators, combined in a fixed order.
@@ -345,8 +380,8 @@ __global__ void __launch_bounds__(kGramThreads) cond2_kernel(const Cond2Args a) 
     // y·R1 = x by forward substitution, right-looking: lane c of a warp holds the running
     // value of column c of up to three rows; at step k the lane holding column k
     // finishes y_k (a shuffle broadcasts it) and every later column subtracts y_k·R1_kc.
-    // The three rows of a warp are independent chains that overlap.  (Columns beyond 32:
-    // one row per thread.)
+    // The three rows of a warp are independent chains that overlap.  (q > 64: one row per
+    // thread.)
     if (q <= 32) {
       const int lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
       for (int i0 = warp; i0 < nrows; i0 += 3 * nw) {
@@ -371,6 +406,43 @@ __global__ void __launch_bounds__(kGramThreads) cond2_kernel(const Cond2Args a) 
 #pragma unroll
         for (int u = 0; u < 3; ++u)
           if (live[u] && lane < q) rows[(i0 + u * nw) * q + lane] = acc[u];
+      }
+    } else if (q <= 64) {
+      // lane c holds columns c and c + 32
+      const int lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+      const int c1 = lane + 32;
+      for (int i0 = warp; i0 < nrows; i0 += 3 * nw) {
+        double acc[3], acc1[3];
+        bool live[3];
+#pragma unroll
+        for (int u = 0; u < 3; ++u) {
+          const int i = i0 + u * nw;
+          live[u] = i < nrows;
+          acc[u] = (live[u] && lane < q) ? rows[i * q + lane] : 0.0;
+          acc1[u] = (live[u] && c1 < q) ? rows[i * q + c1] : 0.0;
+        }
+        for (int k = 0; k < q; ++k) {
+          const double rk = lane < q ? R1s[k * q + lane] : 0.0;
+          const double rk1 = c1 < q ? R1s[k * q + c1] : 0.0;
+          const double dk = dinv[k];
+          const bool hi = k >= 32;
+#pragma unroll
+          for (int u = 0; u < 3; ++u) {
+            const double src = hi ? acc1[u] : acc[u];
+            const double yk = __shfl_sync(0xffffffffu, src, k & 31) * dk;
+            if (!hi) {
+              if (lane == k) acc[u] = yk;
+              else if (lane > k) acc[u] = fma(-yk, rk, acc[u]);
+            }
+            if (c1 == k) acc1[u] = yk;
+            else if (c1 > k) acc1[u] = fma(-yk, rk1, acc1[u]);
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 3; ++u) {
+          if (live[u] && lane < q) rows[(i0 + u * nw) * q + lane] = acc[u];
+          if (live[u] && c1 < q) rows[(i0 + u * nw) * q + c1] = acc1[u];
+        }
       }
     } else {
       for (int i = tid; i < nrows; i += blockDim.x) {
@@ -405,16 +477,36 @@ __global__ void __launch_bounds__(kGramThreads) cond2_kernel(const Cond2Args a) 
     for (; i < nrows; ++i) s0 = fma(rows[i * q + j], rows[i * q + l], s0);
     a.partials[static_cast<size_t>(blockIdx.x) * ne + e] = (s0 + s1) + (s2 + s3);
   }
+  // Two-level fixed-order sum of the partials: the last block of each group of
+  // kCondGroup blocks adds its group's partials; the last group to finish adds the
+  // group sums (both in block order, so the result does not depend on scheduling).
+  const int gsz = cond2_group_size(q, gridDim.x);
+  const int groups = (gridDim.x + gsz - 1) / gsz;
+  const int g = blockIdx.x / gsz;
+  const int g_lo = g * gsz, g_n = min(gsz, static_cast<int>(gridDim.x) - g_lo);
+  double* gsum = a.partials + static_cast<size_t>(gridDim.x) * ne;   // [groups][ne]
   __threadfence();
   __syncthreads();
-  if (tid == 0) s_last = (atomicAdd(a.ticket, 1u) == gridDim.x - 1) ? 1 : 0;
+  if (tid == 0) s_last = (atomicAdd(a.ticket + g, 1u) == static_cast<unsigned>(g_n - 1)) ? 1 : 0;
   __syncthreads();
   if (!s_last) return;
   __threadfence();
-  // ---- last block: fixed-order sum of the partials, then the q×q work
+  if (groups > 1) {
+    for (int e = tid; e < ne; e += blockDim.x)
+      gsum[static_cast<size_t>(g) * ne + e] = sum4(a.partials + static_cast<size_t>(g_lo) * ne + e, g_n, ne);
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) s_last = (atomicAdd(a.ticket + groups, 1u) == static_cast<unsigned>(groups - 1)) ? 1 : 0;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+  }
+  // ---- last group: the group sums (or, with one group, the partials), then the q×q work
   double* Gs = rows;
+  const double* src = groups > 1 ? gsum : a.partials;
+  const int nsrc = groups > 1 ? groups : static_cast<int>(gridDim.x);
   for (int e = tid; e < ne; e += blockDim.x) {
-    const double v = sum4(a.partials + e, gridDim.x, ne);
+    const double v = sum4(src + e, nsrc, ne);
     int j, l;
     pair_index(e, q, j, l);
     Gs[j * q + l] = v;
@@ -426,9 +518,10 @@ __global__ void __launch_bounds__(kGramThreads) cond2_kernel(const Cond2Args a) 
   if (PASS == 1)
     for (int e = tid; e < q * a.r2; e += blockDim.x) Ps[e] = a.pi2[e];
   __syncthreads();
-  if (tid < kCholThreads) {
+  const int nt = q > 32 ? static_cast<int>(blockDim.x) : 128;
+  if (tid < nt) {
     // FP32-accurate pivot reciprocals suffice for R1, which only preconditions pass 1
-    const bool ok = block_cholesky(Gs, Rc, dn, sm2 + L.inv, q, PASS == 0 ? 0 : 2);
+    const bool ok = block_cholesky(Gs, Rc, dn, sm2 + L.inv, q, PASS == 0 ? 0 : 2, nt);
     if (tid == 0) s_ok = ok ? 1 : 0;
   }
   __syncthreads();
@@ -439,46 +532,44 @@ __global__ void __launch_bounds__(kGramThreads) cond2_kernel(const Cond2Args a) 
   } else {
     double* Rs = sm2 + L.R;
     double* Ms = sm2 + L.M;
-    // R = R2·R1 (both upper triangular), all threads
-    for (int e = tid; e < q * q; e += blockDim.x) {
-      const int i = e / q, j = e - i * q;
-      double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-      int k = i;
-      for (; k + 3 <= j; k += 4) {
-        s0 = fma(Rc[i * q + k], R1s[k * q + j], s0);
-        s1 = fma(Rc[i * q + k + 1], R1s[(k + 1) * q + j], s1);
-        s2 = fma(Rc[i * q + k + 2], R1s[(k + 2) * q + j], s2);
-        s3 = fma(Rc[i * q + k + 3], R1s[(k + 3) * q + j], s3);
-      }
-      for (; k <= j; ++k) s0 = fma(Rc[i * q + k], R1s[k * q + j], s0);
-      Rs[e] = j < i ? 0.0 : (s0 + s1) + (s2 + s3);
-    }
-    for (int k = tid; k < q; k += blockDim.x) dn[k] = dn[k] * dinv[k];   // 1/(R2_kk·R1_kk)
-    __syncthreads();
     if (tid < 32) {
-      // rank test over the columns, one lane per column
+      // rank test over the columns, one lane per column: R_kk = (R2)_kk·(R1)_kk
       bool bad = false;
       for (int k = tid; k < q; k += 32) {
-        const double rkk = Rs[k * q + k];
+        const double rkk = Rc[k * q + k] * R1s[k * q + k];
         if (!(rkk > kRankTol * a.colnorm[k]) || !isfinite(rkk)) bad = true;
       }
       if (__any_sync(0xffffffffu, bad) || !s_ok) {
         if (tid == 0) raise_flag(a.flags, L1S_ERR_RANK_DEFICIENT);
       }
     }
-    // M = R⁻¹·Π2 by back substitution, right-looking, threads 0..127: M starts as Π2; at
-    // step k row k is finished (times 1/R_kk) and every row above subtracts R_jk·M_k·.
-    if (tid < kCholThreads) {
-      for (int e = tid; e < q * a.r2; e += kCholThreads) Ms[e] = Ps[e];
-      named_barrier(1, kCholThreads);
-      for (int k = q - 1; k >= 0; --k) {
-        for (int c = tid; c < a.r2; c += kCholThreads) Ms[k * a.r2 + c] *= dn[k];
-        named_barrier(1, kCholThreads);
-        for (int e = tid; e < k * a.r2; e += kCholThreads) {
-          const int j = e / a.r2, c = e - j * a.r2;
-          Ms[e] = fma(-Rs[j * q + k], Ms[k * a.r2 + c], Ms[e]);
+    // M = R⁻¹·Π2.  q ≤ 32: R = R2·R1 first, then one right-looking back substitution;
+    // wider X: R1⁻¹·(R2⁻¹·Π2) by two, which avoids the q³ product.
+    const bool small = q <= 32;
+    if (small) {
+      for (int e = tid; e < q * q; e += blockDim.x) {
+        const int i = e / q, j = e - i * q;
+        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+        int k = i;
+        for (; k + 3 <= j; k += 4) {
+          s0 = fma(Rc[i * q + k], R1s[k * q + j], s0);
+          s1 = fma(Rc[i * q + k + 1], R1s[(k + 1) * q + j], s1);
+          s2 = fma(Rc[i * q + k + 2], R1s[(k + 2) * q + j], s2);
+          s3 = fma(Rc[i * q + k + 3], R1s[(k + 3) * q + j], s3);
         }
-        named_barrier(1, kCholThreads);
+        for (; k <= j; ++k) s0 = fma(Rc[i * q + k], R1s[k * q + j], s0);
+        Rs[e] = j < i ? 0.0 : (s0 + s1) + (s2 + s3);
+      }
+      for (int k = tid; k < q; k += blockDim.x) dn[k] = dn[k] * dinv[k];   // 1/(R2_kk·R1_kk)
+    }
+    for (int e = tid; e < q * a.r2; e += blockDim.x) Ms[e] = Ps[e];
+    __syncthreads();
+    if (tid < nt) {
+      if (small) {
+        block_back_subst(Rs, dn, Ms, q, a.r2, nt);
+      } else {
+        block_back_subst(Rc, dn, Ms, q, a.r2, nt);
+        block_back_subst(R1s, dinv, Ms, q, a.r2, nt);
       }
     }
     __syncthreads();
@@ -488,12 +579,32 @@ __global__ void __launch_bounds__(kGramThreads) cond2_kernel(const Cond2Args a) 
       a.M32[e] = static_cast<float>(m);
       if (a.M_user) a.M_user[e] = m;
     }
-    for (int e = tid; e < q * q; e += blockDim.x) {
-      a.R[e] = Rs[e];
-      if (a.R_user) a.R_user[e] = Rs[e];
+    if (a.R_user && small) {
+      for (int e = tid; e < q * q; e += blockDim.x) {
+        a.R[e] = Rs[e];
+        a.R_user[e] = Rs[e];
+      }
+    } else if (a.R_user) {
+      // R = R2·R1 (both upper triangular), only when the caller asks for it
+      for (int e = tid; e < q * q; e += blockDim.x) {
+        const int i = e / q, j = e - i * q;
+        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+        int k = i;
+        for (; k + 3 <= j; k += 4) {
+          s0 = fma(Rc[i * q + k], R1s[k * q + j], s0);
+          s1 = fma(Rc[i * q + k + 1], R1s[(k + 1) * q + j], s1);
+          s2 = fma(Rc[i * q + k + 2], R1s[(k + 2) * q + j], s2);
+          s3 = fma(Rc[i * q + k + 3], R1s[(k + 3) * q + j], s3);
+        }
+        for (; k <= j; ++k) s0 = fma(Rc[i * q + k], R1s[k * q + j], s0);
+        const double v = j < i ? 0.0 : (s0 + s1) + (s2 + s3);
+        Rs[e] = v;
+        a.R[e] = v;
+        a.R_user[e] = v;
+      }
     }
   }
-  if (tid == 0) *a.ticket = 0u;   // ready for the next launch
+  for (int k = tid; k <= groups; k += blockDim.x) a.ticket[k] = 0u;   // ready for the next pass
 }
 
 __global__ void pi2_kernel(Key2 key, uint32_t problem, int total, double* out) {
@@ -501,14 +612,20 @@ __global__ void pi2_kernel(Key2 key, uint32_t problem, int total, double* out) {
   if (e < total) out[e] = pi2_entry(key, problem, e);
 }
 
-// Rows of Π1X per block of the Gram pass: at least q, and at most 32 blocks.
-static int cond2_rows_per_block(int r1, int q) { return std::max(q, (r1 + 31) / 32); }
+// Rows of Π1X per block of the Gram passes: for q ≤ 32 at least q and at most 32
+// blocks; wider X (whose Gram costs r1·q²/2 FP64 FMAs) spreads over about 128 blocks.
+static int cond2_rows_per_block(int r1, int q) {
+  if (q > 32) return std::max(4, (r1 + 127) / 128);
+  return std::max(q, (r1 + 31) / 32);
+}
 
 size_t cond2_scratch_bytes(int r1, int q, int sms) {
   (void)sms;
   const int rpb = cond2_rows_per_block(r1, q);
   const int blocks = (r1 + rpb - 1) / rpb;
-  return sizeof(double) * (static_cast<size_t>(blocks) * (q * (q + 1) / 2) + q * q + 2 * q) + 256;
+  const int groups = (blocks + cond2_group_size(q, blocks) - 1) / cond2_group_size(q, blocks);
+  return sizeof(double) * (static_cast<size_t>(blocks + groups) * (q * (q + 1) / 2) + q * q + 2 * q) +
+         sizeof(unsigned int) * (groups + 1) + 256;
 }
 
 bool launch_condition_householder(const Plan& pl, const float* pix, const l1s_params* p, double* R_user,
@@ -532,11 +649,12 @@ bool launch_condition(const Plan& pl, const float* pix, const l1s_params* p, dou
   a.problem = p->problem_id;
   double* scratch = reinterpret_cast<double*>(ws + pl.off_qr);
   const int ne = pl.q * (pl.q + 1) / 2;
+  const int groups = (grid + cond2_group_size(pl.q, grid) - 1) / cond2_group_size(pl.q, grid);
   a.partials = scratch;
-  a.R1 = scratch + static_cast<size_t>(grid) * ne;
+  a.R1 = scratch + static_cast<size_t>(grid + groups) * ne;
   a.R1dinv = a.R1 + pl.q * pl.q;
   a.colnorm = a.R1dinv + pl.q;
-  a.ticket = reinterpret_cast<unsigned int*>(ws + pl.off_status + offsetof(StatusBlock, cond_ticket));
+  a.ticket = reinterpret_cast<unsigned int*>(a.colnorm + pl.q);
   a.R = reinterpret_cast<double*>(ws + pl.off_r);
   a.M64 = reinterpret_cast<double*>(ws + pl.off_m64);
   a.M32 = reinterpret_cast<float*>(ws + pl.off_m32);
@@ -551,7 +669,8 @@ bool launch_condition(const Plan& pl, const float* pix, const l1s_params* p, dou
       !cuda_ok(cudaFuncSetAttribute(cond2_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)),
                "cond2 smem"))
     return false;
-  if (!cuda_ok(cudaMemsetAsync(a.ticket, 0, sizeof(unsigned int), st), "reset conditioning ticket")) return false;
+  if (!cuda_ok(cudaMemsetAsync(a.ticket, 0, sizeof(unsigned int) * (groups + 1), st), "reset conditioning tickets"))
+    return false;
   cond2_kernel<0><<<grid, kGramThreads, smem, st>>>(a);
   cond2_kernel<1><<<grid, kGramThreads, smem, st>>>(a);
   count_launch(2);

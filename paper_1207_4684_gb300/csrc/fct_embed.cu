@@ -39,6 +39,7 @@ struct FctArgs {
   uint32_t problem;
   int64_t row_offset;
   int sign_flip;
+  int log2s;              // log2 s (the narrow-X kernel's tile may hold several H_s blocks)
   float inv_sqrt_s;
   float* partials;        // [slices][gridDim.x][r1][width]
   uint32_t* flags;
@@ -333,10 +334,13 @@ struct __align__(8) T16MetaH {
   float wH;           // 4·c_H/√s
 };
 
-template <int LOG2S, typename TA, int W>
+// LOG2S here is the tile: 2^LOG2S rows per pipeline step, which may hold several
+// H_s blocks (s = 2^a.log2s ≤ tile): butterfly stages over row bits ≥ log2 s are skipped.
+template <int LOG2S, typename TA, int W, bool EXACT>
 __global__ void __launch_bounds__(WsCfg<W>::kThreads) fct_embed_ws_kernel(const FctArgs a) {
   constexpr int kWsA = WsCfg<W>::kA;
   constexpr int S = 1 << LOG2S;
+  const int lg = EXACT ? LOG2S : a.log2s;   // H_s acts on row bits [0, lg); EXACT: s is the tile
   constexpr int K2 = LOG2S - 4;          // pass 2: row bit 0 and bits [5, LOG2S)
   constexpr int G2 = 1 << K2;
   constexpr int KB = S / 32;             // b column: values per lane
@@ -465,13 +469,14 @@ __global__ void __launch_bounds__(WsCfg<W>::kThreads) fct_embed_ws_kernel(const 
             }
 #pragma unroll
             for (int t = 0; t < 4; ++t)
+              if (t < lg)                                       // row bit t
 #pragma unroll
-              for (int j = 0; j < 16; ++j)
-                if ((j & (1 << t)) == 0) {
-                  const float lo = v[j], hi = v[j | (1 << t)];
-                  v[j] = lo + hi;
-                  v[j | (1 << t)] = lo - hi;
-                }
+                for (int j = 0; j < 16; ++j)
+                  if ((j & (1 << t)) == 0) {
+                    const float lo = v[j], hi = v[j | (1 << t)];
+                    v[j] = lo + hi;
+                    v[j | (1 << t)] = lo - hi;
+                  }
 #pragma unroll
             for (int j = 0; j < 16; ++j) tile[(base | j) * 32 + c] = v[j];
           }
@@ -495,12 +500,14 @@ __global__ void __launch_bounds__(WsCfg<W>::kThreads) fct_embed_ws_kernel(const 
           }
 #pragma unroll
           for (int t = 0; t < 4; ++t) {
+            if (t + 1 < lg) {                                   // row bit t + 1
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
-              if ((j & (1 << t)) == 0) {
-                const float lo = v[j], hi = v[j | (1 << t)];
-                v[j] = lo + hi;
-                v[j | (1 << t)] = lo - hi;
+              for (int j = 0; j < 16; ++j) {
+                if ((j & (1 << t)) == 0) {
+                  const float lo = v[j], hi = v[j | (1 << t)];
+                  v[j] = lo + hi;
+                  v[j | (1 << t)] = lo - hi;
+                }
               }
             }
           }
@@ -520,13 +527,14 @@ __global__ void __launch_bounds__(WsCfg<W>::kThreads) fct_embed_ws_kernel(const 
           for (int j = 0; j < G2; ++j) v[j] = tile[(g2 | (j << 4)) * 32 + c];
 #pragma unroll
           for (int t = 0; t < K2; ++t)
+            if (4 + t < lg)                                     // row bit 4 + t
 #pragma unroll
-            for (int j = 0; j < G2; ++j)
-              if ((j & (1 << t)) == 0) {
-                const float lo = v[j], hi = v[j | (1 << t)];
-                v[j] = lo + hi;
-                v[j | (1 << t)] = lo - hi;
-              }
+              for (int j = 0; j < G2; ++j)
+                if ((j & (1 << t)) == 0) {
+                  const float lo = v[j], hi = v[j | (1 << t)];
+                  v[j] = lo + hi;
+                  v[j | (1 << t)] = lo - hi;
+                }
           if (c < d) {
             float* Pl = P + c;
 #pragma unroll
@@ -547,12 +555,14 @@ __global__ void __launch_bounds__(WsCfg<W>::kThreads) fct_embed_ws_kernel(const 
           }
 #pragma unroll
           for (int t = 0; t < K2; ++t) {
+            if (t == 0 || 4 + t < lg) {                         // row bit 0, then bits 5 and up
 #pragma unroll
-            for (int j = 0; j < G2; ++j) {
-              if ((j & (1 << t)) == 0) {
-                const float lo = v[j], hi = v[j | (1 << t)];
-                v[j] = lo + hi;
-                v[j | (1 << t)] = lo - hi;
+              for (int j = 0; j < G2; ++j) {
+                if ((j & (1 << t)) == 0) {
+                  const float lo = v[j], hi = v[j | (1 << t)];
+                  v[j] = lo + hi;
+                  v[j | (1 << t)] = lo - hi;
+                }
               }
             }
           }
@@ -585,22 +595,26 @@ __global__ void __launch_bounds__(WsCfg<W>::kThreads) fct_embed_ws_kernel(const 
         if (lane == 0) mbar_arrive(&stage_free[buf]);
 #pragma unroll
         for (int t = 0; (1 << t) < KB; ++t) {
+          if (5 + t < lg) {                                     // row bit 5 + t
 #pragma unroll
-          for (int k = 0; k < KB; ++k) {
-            if ((k & (1 << t)) == 0) {
-              const float lo = v[k], hi = v[k | (1 << t)];
-              v[k] = lo + hi;
-              v[k | (1 << t)] = lo - hi;
+            for (int k = 0; k < KB; ++k) {
+              if ((k & (1 << t)) == 0) {
+                const float lo = v[k], hi = v[k | (1 << t)];
+                v[k] = lo + hi;
+                v[k | (1 << t)] = lo - hi;
+              }
             }
           }
         }
 #pragma unroll
         for (int t = 0; t < 5; ++t) {
-          const bool upper = (lane >> t) & 1;
+          if (t < lg) {                                         // row bit t (uniform over the warp)
+            const bool upper = (lane >> t) & 1;
 #pragma unroll
-          for (int k = 0; k < KB; ++k) {
-            const float o = __shfl_xor_sync(0xffffffffu, v[k], 1 << t);
-            v[k] = upper ? (o - v[k]) : (v[k] + o);
+            for (int k = 0; k < KB; ++k) {
+              const float o = __shfl_xor_sync(0xffffffffu, v[k], 1 << t);
+              v[k] = upper ? (o - v[k]) : (v[k] + o);
+            }
           }
         }
 #pragma unroll
@@ -1107,26 +1121,32 @@ const void* fct_kernel(int log2s, l1s_dtype dt, bool staged) {
 }
 
 template <typename TA, int W>
-static const void* ws_kernel_for(int log2s) {
-  switch (log2s) {
-    case 5: return reinterpret_cast<const void*>(&fct_embed_ws_kernel<5, TA, W>);
-    case 6: return reinterpret_cast<const void*>(&fct_embed_ws_kernel<6, TA, W>);
-    case 7: return reinterpret_cast<const void*>(&fct_embed_ws_kernel<7, TA, W>);
-    case 8: return reinterpret_cast<const void*>(&fct_embed_ws_kernel<8, TA, W>);
-    case 9: return reinterpret_cast<const void*>(&fct_embed_ws_kernel<9, TA, W>);
+static const void* ws_kernel_for(int log2t, bool exact) {
+  switch (log2t) {
+    case 8: return exact ? reinterpret_cast<const void*>(&fct_embed_ws_kernel<8, TA, W, true>)
+                         : reinterpret_cast<const void*>(&fct_embed_ws_kernel<8, TA, W, false>);
+    case 9: return exact ? reinterpret_cast<const void*>(&fct_embed_ws_kernel<9, TA, W, true>)
+                         : reinterpret_cast<const void*>(&fct_embed_ws_kernel<9, TA, W, false>);
     default: return nullptr;
   }
 }
 
-// Column width of the narrow-X kernel for d (16 or 32; 32 ≤ s ≤ 512), 0 when it does not apply.
+// Column width of the narrow-X kernel for d (16 or 32; 2 ≤ s ≤ 512), 0 when it does not apply.
 int fct_ws_width(int log2s, int d) {
-  if (log2s < 5 || log2s > 9) return 0;
+  if (log2s < 1 || log2s > 9) return 0;
   return d <= 16 ? 16 : (d <= 32 ? 32 : 0);
 }
 
-const void* fct_ws_kernel(int log2s, l1s_dtype dt, int w) {
-  if (w == 16) return dt == L1S_BF16 ? ws_kernel_for<uint16_t, 16>(log2s) : ws_kernel_for<float, 16>(log2s);
-  if (w == 32) return dt == L1S_BF16 ? ws_kernel_for<uint16_t, 32>(log2s) : ws_kernel_for<float, 32>(log2s);
+// Its tile: at least 256 rows, so that blocks of small s share the per-tile pipeline costs.
+int fct_ws_tile_log2(int log2s) { return log2s < 8 ? 8 : log2s; }
+
+// The kernel for a tile of 2^log2t rows and blocks of 2^log2s rows (log2s ≤ log2t).
+const void* fct_ws_kernel(int log2t, int log2s, l1s_dtype dt, int w) {
+  const bool exact = log2s == log2t;
+  if (w == 16)
+    return dt == L1S_BF16 ? ws_kernel_for<uint16_t, 16>(log2t, exact) : ws_kernel_for<float, 16>(log2t, exact);
+  if (w == 32)
+    return dt == L1S_BF16 ? ws_kernel_for<uint16_t, 32>(log2t, exact) : ws_kernel_for<float, 32>(log2t, exact);
   return nullptr;
 }
 
@@ -1211,11 +1231,14 @@ bool launch_fct(const Plan& pl, const void* A, int64_t lda, l1s_dtype dt, const 
   a.q = pl.q;
   a.r1 = pl.r1;
   a.width = pl.fct_width;
-  a.nblocks = pl.nblocks;
-  a.full_blocks = pl.n / pl.s;
+  // The narrow-X kernel steps over tiles of 2^fct_tile_log2 ≥ s rows, the others over s-row blocks.
+  const int tile = pl.fct_ws ? (1 << pl.fct_tile_log2) : pl.s;
+  a.nblocks = (pl.n + tile - 1) / tile;
+  a.full_blocks = pl.n / tile;
+  a.log2s = pl.log2s;
   const uint32_t esz = dt == L1S_BF16 ? 2u : 4u;
-  a.stage_a_bytes = static_cast<uint32_t>(pl.s) * pl.d * esz;
-  a.stage_bytes = fct_stage_bytes(pl.s, pl.d, dt);
+  a.stage_a_bytes = static_cast<uint32_t>(tile) * pl.d * esz;
+  a.stage_bytes = fct_stage_bytes(tile, pl.d, dt);
   const bool staged = pl.fct_staged && fct_can_stage(pl.s, pl.d, dt, lda, A, b);
   a.tma = staged ? 1 : 0;
   a.key = make_key(p->seed);
@@ -1231,11 +1254,11 @@ bool launch_fct(const Plan& pl, const void* A, int64_t lda, l1s_dtype dt, const 
   // So does the bucket-sorted kernel.
   const int wsw = pl.fct_ws;
   const int srt = pl.fct_sorted;
-  if (wsw || srt) a.tma = fct_can_stage(pl.s, pl.d, dt, lda, A, b) ? 1 : 0;
+  if (wsw || srt) a.tma = fct_can_stage(tile, pl.d, dt, lda, A, b) ? 1 : 0;
   const void* fn = srt ? fct_sorted_kernel(pl.log2s, dt, srt)
-                       : (wsw ? fct_ws_kernel(pl.log2s, dt, wsw) : fct_kernel(pl.log2s, dt, staged));
+                       : (wsw ? fct_ws_kernel(pl.fct_tile_log2, pl.log2s, dt, wsw) : fct_kernel(pl.log2s, dt, staged));
   const size_t smem = srt ? fct_sorted_smem_bytes(pl.s, pl.d, dt, pl.r1, srt)
-                          : (wsw ? fct_ws_smem_bytes(pl.s, pl.d, dt, pl.r1, wsw)
+                          : (wsw ? fct_ws_smem_bytes(tile, pl.d, dt, pl.r1, wsw)
                                  : fct_smem_bytes(pl.s, pl.d, dt, pl.r1, pl.fct_width, staged));
   if (!cuda_ok(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)),
                "cudaFuncSetAttribute(fct_embed)"))
