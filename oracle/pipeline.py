@@ -24,8 +24,12 @@ def form_x(A: np.ndarray, b: np.ndarray) -> np.ndarray:
 
 def fast_cauchy_regression(A, b, s: int, r1: int, r2: int, coreset: float,
                            seed: int = 0, problem_id: int = 0, sign_flip: bool = True,
-                           solve_lp: bool = True, timings: dict | None = None) -> dict:
-    """All intermediates of Figure 2 for one problem (rows are numbered from 0)."""
+                           solve_lp: bool = True, timings: dict | None = None,
+                           variant: int = 0, sample_scale: float = 0.0) -> dict:
+    """All intermediates of Figure 2 for one problem (rows are numbered from 0).
+
+    variant 1 is OptimizedFastCauchyRegression (Figure "mainOpt"): Π2 Gaussian and
+    p̂ = min{1, sample_scale·λ̂} without the Σλ normalisation."""
     t = {} if timings is None else timings
     t0 = time.perf_counter()
     X = form_x(A, b)                                                          # step 1
@@ -34,12 +38,16 @@ def fast_cauchy_regression(A, b, s: int, r1: int, r2: int, coreset: float,
     t1 = time.perf_counter()
     _, r_mat = condition.qr_positive(pix)                                     # step 2, QR
     condition.check_rank(r_mat)
-    pi2 = rng.pi2_matrix(seed, problem_id, q, r2)                             # step 3
+    pi2 = (rng.pi2_gaussian_matrix(seed, problem_id, q, r2) if variant == 1
+           else rng.pi2_matrix(seed, problem_id, q, r2))                      # step 3
     m_mat = condition.m_matrix(r_mat, pi2)                                    # R⁻¹Π2
     t2 = time.perf_counter()
     lam = leverage.lambda_estimates(X, m_mat)                                 # steps 4-5
     t3 = time.perf_counter()
-    p_hat, tau, total = sampling.probabilities(lam, coreset)                  # step 6
+    if variant == 1:
+        p_hat, tau, total = sampling.probabilities_scaled(lam, sample_scale), sample_scale, None
+    else:
+        p_hat, tau, total = sampling.probabilities(lam, coreset)              # step 6
     u = rng.sample_uniforms(seed, problem_id, np.arange(n))
     idx, wts = sampling.bernoulli_sample(p_hat, u)                            # step 7
     t4 = time.perf_counter()

@@ -23,6 +23,11 @@ conventions; the paper only fixes the distributions):
 * stream 1, call t with counter (t, 0, problem, 1): the entries 4t … 4t+3 of
   Π2 (row-major, q × r2) from the four words, each through k = word >> 8
   (Figure 2, step 3).
+* stream 1 for the Gaussian Π2 of OptimizedFastCauchyRegression (Figure
+  "mainOpt", step 4): call t gives the entries 2t and 2t+1 by the Box–Muller
+  transform (Box and Muller, 1958) of two 53-bit uniforms in (0, 1),
+  u1 from (o0, o1) and u2 from (o2, o3), each ((o_a >> 5)·2^26 + (o_b >> 6) + ½)·2^-53:
+  ρ = √(−2 ln u1), entry 2t = ρ·cos(2π u2), entry 2t+1 = ρ·sin(2π u2).
 * stream 2, call t with counter (t_lo, t_hi, problem, 2) for t = ⌊i/2⌋: the
   sampling uniform of row i is u = ((o_a >> 5)·2^26 + (o_b >> 6))·2^-53 with
   (a, b) = (0, 1) for even i and (2, 3) for odd i (Figure 2, step 7).
@@ -133,6 +138,27 @@ def pi2_matrix(seed: int, problem_id: int, q: int, r2: int) -> np.ndarray:
     words = philox4x32_10(t, np.uint64(0), np.uint64(problem_id), np.uint64(STREAM_PI2), k0, k1)
     w = np.stack(words, axis=1).reshape(-1)[:n_entries]
     return cauchy_from_k((w >> np.uint64(8)).astype(np.int64)).reshape(q, r2)
+
+
+def pi2_gaussian_matrix(seed: int, problem_id: int, q: int, r2: int) -> np.ndarray:
+    """Π2 ∈ R^{q×r2} of independent standard Gaussians (Figure "mainOpt", step 4), stream 1."""
+    k0, k1 = _key(seed)
+    n_entries = q * r2
+    calls = (n_entries + 1) // 2
+    t = np.arange(calls, dtype=np.uint64)
+    o0, o1, o2, o3 = philox4x32_10(t, np.uint64(0), np.uint64(problem_id), np.uint64(STREAM_PI2), k0, k1)
+
+    def open_uniform(wa, wb):
+        bits = ((wa >> np.uint64(5)) << np.uint64(26)) | (wb >> np.uint64(6))
+        return (bits.astype(np.float64) + 0.5) * 2.0 ** -53
+
+    u1 = open_uniform(o0, o1)
+    u2 = open_uniform(o2, o3)
+    rho = np.sqrt(-2.0 * np.log(u1))
+    z = np.empty(2 * calls)
+    z[0::2] = rho * np.cos(2.0 * np.pi * u2)
+    z[1::2] = rho * np.sin(2.0 * np.pi * u2)
+    return z[:n_entries].reshape(q, r2)
 
 
 def sample_uniform_bits(seed: int, problem_id: int, rows) -> np.ndarray:

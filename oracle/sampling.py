@@ -29,6 +29,13 @@ def probabilities(lam: np.ndarray, coreset: float, total: float | None = None):
     return np.minimum(1.0, tau * lam), tau, total
 
 
+def probabilities_scaled(lam: np.ndarray, scale: float):
+    """p̂_i = min{1, s·λ̂_i} with the sampling size s given (Figure "mainOpt", step 7):
+    OptimizedFastCauchyRegression does not normalise by Σλ."""
+    lam = np.asarray(lam, dtype=np.float64)
+    return np.minimum(1.0, float(scale) * lam)
+
+
 def bernoulli_sample(p: np.ndarray, u: np.ndarray):
     """Indices i with u_i < p_i (ascending) and their weights 1/p_i."""
     p = np.asarray(p, dtype=np.float64)

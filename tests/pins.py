@@ -326,10 +326,6 @@ ALL_CHECKS = [check_hadamard_closed_form, check_cauchy_quantiles, check_draw_sta
               check_qr, check_lambda_distribution, check_sampling, check_solver]
 
 
-def _all_checks():
-    return ALL_CHECKS + [check_bf16_round]
-
-
 # ----------------------------------------------------------------- BF16 rounding of M
 def check_bf16_round() -> None:
     """Values with at most 8 significant bits are unchanged; midpoints go to the even
@@ -353,3 +349,64 @@ def check_bf16_round() -> None:
     M = g.standard_normal((5, 3))
     mm = leverage.mixed_precision_m(M)
     assert np.array_equal(mm[-1], M[-1].astype(np.float32)) and np.array_equal(mm[:-1], leverage.bf16_round(M[:-1]))
+
+
+# ----------------------------------------------------------------- OptimizedFastCauchyRegression
+def check_gaussian_pi2(q: int = 64, r2: int = 800) -> None:
+    """The Gaussian Π2 (Figure "mainOpt", step 4) is standard normal (KS), the two entries of
+    each Box–Muller pair are uncorrelated and their squared sum is χ²₂ (exponential, mean 2) —
+    which a pair built from one uniform twice, or a wrong ρ, fails — and different problems
+    draw independent matrices."""
+    z = rng.pi2_gaussian_matrix(99, 3, q, r2).ravel()
+    assert stats.kstest(z, "norm").pvalue > 1e-4, "Π2 entries not N(0,1)"
+    a, b = z[0::2], z[1::2]
+    assert abs(np.corrcoef(a, b)[0, 1]) < 4 / math.sqrt(a.size), "pair correlated"
+    assert stats.kstest(a * a + b * b, "expon", args=(0, 2)).pvalue > 1e-4, "pair radius not χ²₂"
+    other = rng.pi2_gaussian_matrix(99, 4, q, r2).ravel()
+    assert abs(np.corrcoef(z, other)[0, 1]) < 4 / math.sqrt(z.size), "problems not independent"
+
+
+def _half_normal_median_cdf(x: float, r2: int) -> float:
+    """P(lower median of r2 independent |N(0,1)| ≤ x): at least (r2−1)//2 + 1 of them ≤ x."""
+    p = math.erf(x / math.sqrt(2.0))
+    return float(stats.binom.sf((r2 - 1) // 2, r2, p))
+
+
+def check_gaussian_lambda_distribution(r2: int = 8, seeds: int = 400, rows: int = 64) -> None:
+    """With a Gaussian Π2, Λ_ij = (X·R⁻¹·Π2)_ij is N(0, ‖U_(i)‖₂²) (the intuition given for
+    OptimizedFastCauchyRegression), so λ̂_i/‖U_(i)‖₂ follows the lower-median order statistic of
+    r2 half-normals: KS against its exact CDF."""
+    g = np.random.default_rng(23)
+    X = g.standard_normal((rows, 5)) * np.array([1, 7, 0.2, 2, 1.0])[None, :]
+    _, rm = condition.qr_positive(g.standard_normal((30, 5)))
+    l2 = np.linalg.norm(X @ np.linalg.inv(rm), axis=1)
+    ratios = []
+    for sd in range(seeds):
+        mm = condition.m_matrix(rm, rng.pi2_gaussian_matrix(700 + sd, 0, 5, r2))
+        lam = leverage.lambda_estimates(X, mm)
+        ratios.append(lam[sd % rows] / l2[sd % rows])
+    cdf = np.vectorize(lambda x: _half_normal_median_cdf(x, r2))
+    assert stats.kstest(np.array(ratios), cdf).pvalue > 1e-4, "λ̂/‖U‖₂ not the half-normal median"
+
+
+def check_scaled_probabilities(seed: int = 31) -> None:
+    """p̂ = min{1, s·λ̂} without normalisation: linear below saturation, 1 above, and the
+    Horvitz–Thompson sum over the Bernoulli sample is unbiased for Σ|r_i|."""
+    g = np.random.default_rng(seed)
+    lam = np.abs(g.standard_normal(20000)) + 1e-3
+    p = sampling.probabilities_scaled(lam, 0.4)
+    below = 0.4 * lam < 1.0
+    assert np.array_equal(p[below], 0.4 * lam[below]) and np.all(p[~below] == 1.0)
+    r = np.abs(g.standard_normal(20000))
+    est = []
+    for t in range(200):
+        u = g.uniform(size=lam.size)
+        idx, w = sampling.bernoulli_sample(p, u)
+        est.append(math.fsum((r[idx] * w).tolist()))
+    est = np.array(est)
+    assert abs(est.mean() - r.sum()) < 4 * est.std(ddof=1) / math.sqrt(len(est)), "HT biased"
+
+
+def _all_checks():
+    return ALL_CHECKS + [check_bf16_round, check_gaussian_pi2, check_gaussian_lambda_distribution,
+                         check_scaled_probabilities]

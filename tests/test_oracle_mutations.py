@@ -20,6 +20,8 @@ ORIG_PROB = sampling.probabilities
 ORIG_BERN = sampling.bernoulli_sample
 ORIG_LP = solve.lad_lp
 ORIG_FORMX = pipeline.form_x
+ORIG_GAUSS = rng.pi2_gaussian_matrix
+ORIG_SCALED = sampling.probabilities_scaled
 
 
 def _draws_of(X, s, r1, seed, problem_id, row_offset, draws):
@@ -123,6 +125,20 @@ def formx_plus_b(A, b):
     return np.concatenate([np.asarray(A, float), np.asarray(b, float)[:, None]], axis=1)
 
 
+def gauss_var2(seed, problem_id, q, r2):
+    return ORIG_GAUSS(seed, problem_id, q, r2) * np.sqrt(2.0)
+
+
+def gauss_pair_copy(seed, problem_id, q, r2):
+    z = ORIG_GAUSS(seed, problem_id, q, r2).ravel().copy()
+    z[1::2] = z[0::2][: z[1::2].size]
+    return z.reshape(q, r2)
+
+
+def scaled_no_cap(lam, scale):
+    return float(scale) * np.asarray(lam, dtype=np.float64)
+
+
 MUTATIONS = [
     ("identity half dropped", fct, "fct1_embed", embed_no_identity, pins.check_fct_dense),
     ("Hadamard half dropped", fct, "fct1_embed", embed_no_hadamard, pins.check_fct_dense),
@@ -144,6 +160,12 @@ MUTATIONS = [
     ("weight p̂ for 1/p̂", sampling, "bernoulli_sample", bern_weights_p, pins.check_sampling),
     ("LP ignores weights", solve, "lad_lp", lp_unweighted, pins.check_solver),
     ("X = [A, +b]", pipeline, "form_x", formx_plus_b, pins.check_solver),
+    ("Gaussian Π2 variance 2", rng, "pi2_gaussian_matrix", gauss_var2, pins.check_gaussian_pi2),
+    ("Box–Muller pair copied", rng, "pi2_gaussian_matrix", gauss_pair_copy, pins.check_gaussian_pi2),
+    ("upper median (Gaussian)", leverage, "lambda_estimates", lambda_upper_median,
+     pins.check_gaussian_lambda_distribution),
+    ("Gaussian Π2 variance 2 in λ̂", rng, "pi2_gaussian_matrix", gauss_var2, pins.check_gaussian_lambda_distribution),
+    ("scaled p̂ not capped", sampling, "probabilities_scaled", scaled_no_cap, pins.check_scaled_probabilities),
 ]
 
 
