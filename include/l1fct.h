@@ -79,7 +79,12 @@ typedef struct {
   double coreset_size;        /* m_s > 0: expected coreset size bound (Figure 2, step 6) */
   int64_t global_row_offset;  /* global id of A's first row; a multiple of s */
   int32_t sign_flip;          /* 1: Π1·D·X with random ±1 diagonal D; 0: Π1·X as in §3.1 */
-  int32_t reserved;           /* must be 0 */
+  int32_t variant;            /* 0: FastCauchyRegression (Figure 2): Π2 Cauchy, p̂ = min(1, m_s·λ/Σλ).
+                                 1: OptimizedFastCauchyRegression (Figure "mainOpt"): Π2 Gaussian
+                                 (Box–Muller on stream 1), p̂ = min(1, sample_scale·λ̂), no Σλ;
+                                 coreset_size then only bounds the expected coreset size
+                                 (it sizes the workspace's coreset buffers). */
+  double sample_scale;        /* variant 1: the sampling size s of p̂ = min{1, s·λ̂}; variant 0: 0 */
 } l1s_params;
 
 /* Text of the calling thread's last host-side error ("" if none). */

@@ -104,7 +104,10 @@ static bool check_params(const l1s_params* p, int64_t n, int d) {
   if (p->global_row_offset < 0 || p->global_row_offset % p->s != 0)
     return set_error("global_row_offset must be a non-negative multiple of s"), false;
   if (p->sign_flip != 0 && p->sign_flip != 1) return set_error("sign_flip must be 0 or 1"), false;
-  if (p->reserved != 0) return set_error("reserved must be 0"), false;
+  if (p->variant != 0 && p->variant != 1) return set_error("variant must be 0 or 1"), false;
+  if (p->variant == 0 && p->sample_scale != 0.0) return set_error("sample_scale must be 0 for variant 0"), false;
+  if (p->variant == 1 && (!(p->sample_scale > 0.0) || !isfinite(p->sample_scale)))
+    return set_error("variant 1 needs a positive, finite sample_scale"), false;
   return true;
 }
 
@@ -139,10 +142,12 @@ int sample_impl(const Plan& pl, const void* A, int64_t lda, l1s_dtype dtype, con
                        double* wts, double* coreset, int64_t* count, float* lambda, unsigned char* w,
                        cudaStream_t st) {
   float* lam = lambda ? lambda : reinterpret_cast<float*>(w + pl.off_lam);
-  int nsums = 0;   // Σλ and τ are formed at the start of the sampling kernel
+  // Σλ and τ are formed at the start of the sampling kernel; OptimizedFastCauchyRegression
+  // (variant 1) needs no Σλ at all.
+  int nsums = 0;
   if (!launch_lambda(pl, A, lda, dtype, b, m32, params, lam, nullptr, w, st, &nsums)) return L1S_ERR_CUDA;
   if (!launch_sample(pl, lam, nullptr, params, A, lda, dtype, b, capacity, idx, wts, coreset, count, w, st,
-                     nsums))
+                     params->variant == 1 ? 0 : nsums))
     return L1S_ERR_CUDA;
   return L1S_OK;
 }

@@ -63,6 +63,7 @@ struct CondArgs {
   double* R_user;     // optional copies
   double* M_user;
   uint32_t* flags;
+  int pi2_gauss;      // 1: Gaussian Π2 (OptimizedFastCauchyRegression)
 };
 
 __global__ void __launch_bounds__(kCondThreads) condition_kernel(const CondArgs a) {
@@ -79,7 +80,7 @@ __global__ void __launch_bounds__(kCondThreads) condition_kernel(const CondArgs 
     const int r = i / q, c = i - r * q;
     W[static_cast<size_t>(c) * r1 + r] = static_cast<double>(a.pix[i]);
   }
-  for (int e = tid; e < q * a.r2; e += nthr) a.pi2[e] = pi2_entry(a.key, a.problem, e);
+  for (int e = tid; e < q * a.r2; e += nthr) a.pi2[e] = pi2_value(a.key, a.problem, e, a.pi2_gauss);
   if (tid == 0) s_rank_bad = 0;
   __syncthreads();
 
@@ -195,6 +196,7 @@ struct Cond2Args {
   double* M_user;
   uint32_t* flags;
   int pi2_ready;         // 1: Π2 is already in pi2 (drawn by the phase-1 reduction)
+  int pi2_gauss;         // 1: Gaussian Π2 (OptimizedFastCauchyRegression)
 };
 
 // On this part every FP64 warp instruction occupies its SM sub-partition for tens of
@@ -368,7 +370,7 @@ __global__ void __launch_bounds__(kGramThreads) cond2_kernel(const Cond2Args a) 
     // Π2, unless the phase-1 reduction drew it, spread over all blocks.
     if (!a.pi2_ready)
       for (int e = blockIdx.x * blockDim.x + tid; e < q * a.r2; e += gridDim.x * blockDim.x)
-        a.pi2[e] = pi2_entry(a.key, a.problem, e);
+        a.pi2[e] = pi2_value(a.key, a.problem, e, a.pi2_gauss);
   } else {
     for (int e = tid; e < q * q; e += blockDim.x) R1s[e] = a.R1[e];
     for (int e = tid; e < q; e += blockDim.x) dinv[e] = a.R1dinv[e];
@@ -607,9 +609,9 @@ __global__ void __launch_bounds__(kGramThreads) cond2_kernel(const Cond2Args a) 
   for (int k = tid; k <= groups; k += blockDim.x) a.ticket[k] = 0u;   // ready for the next pass
 }
 
-__global__ void pi2_kernel(Key2 key, uint32_t problem, int total, double* out) {
+__global__ void pi2_kernel(Key2 key, uint32_t problem, int total, int gaussian, double* out) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e < total) out[e] = pi2_entry(key, problem, e);
+  if (e < total) out[e] = pi2_value(key, problem, e, gaussian);
 }
 
 // Rows of Π1X per block of the Gram passes: for q ≤ 32 at least q and at most 32
@@ -661,8 +663,10 @@ bool launch_condition(const Plan& pl, const float* pix, const l1s_params* p, dou
   a.pi2 = reinterpret_cast<double*>(ws + pl.off_pi2);
   a.R_user = R_user;
   a.M_user = M_user;
+  a.pi2_gauss = p->variant == 1 ? 1 : 0;
   a.flags = reinterpret_cast<uint32_t*>(ws + pl.off_status);
   a.pi2_ready = pi2_ready ? 1 : 0;
+  a.pi2_gauss = p->variant == 1 ? 1 : 0;
   const size_t smem = sizeof(double) * static_cast<size_t>(Cond2Smem(a.rows_per_block, pl.q, pl.r2).total);
   if (!cuda_ok(cudaFuncSetAttribute(cond2_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)),
                "cond2 smem") ||
@@ -709,7 +713,7 @@ bool launch_condition_householder(const Plan& pl, const float* pix, const l1s_pa
 
 bool launch_pi2(const l1s_params* p, int q, double* out, cudaStream_t st) {
   const int total = q * p->r2;
-  pi2_kernel<<<(total + 127) / 128, 128, 0, st>>>(make_key(p->seed), p->problem_id, total, out);
+  pi2_kernel<<<(total + 127) / 128, 128, 0, st>>>(make_key(p->seed), p->problem_id, total, p->variant, out);
   count_launch(1);
   return cuda_ok(cudaGetLastError(), "launch pi2");
 }

@@ -1055,10 +1055,10 @@ __global__ void __launch_bounds__(SrtCfg<W>::kThreads) fct_embed_sorted_kernel(c
 __global__ void __launch_bounds__(1024) fct_reduce_kernel(const float* __restrict__ partials, int ctas,
                                                           int r1, int W, int q, float* __restrict__ pix,
                                                           uint32_t* flags, Key2 key, uint32_t problem,
-                                                          int npi2, double* __restrict__ pi2) {
+                                                          int npi2, int pi2_gauss, double* __restrict__ pi2) {
   if (pi2 && blockIdx.y == 0)
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < npi2; e += gridDim.x * blockDim.x)
-      pi2[e] = pi2_entry(key, problem, e);
+      pi2[e] = pi2_value(key, problem, e, pi2_gauss);
   __shared__ float red[32][33];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int per = r1 * W;
@@ -1270,7 +1270,7 @@ bool launch_fct(const Plan& pl, const void* A, int64_t lda, l1s_dtype dt, const 
   const int per = pl.r1 * pl.fct_width;
   dim3 rgrid((per + 31) / 32, pl.fct_slices);
   fct_reduce_kernel<<<rgrid, 1024, 0, st>>>(a.partials, pl.fct_ctas, pl.r1, pl.fct_width, pl.q, pix, a.flags, a.key,
-                                            a.problem, pl.q * pl.r2, pi2_out);
+                                            a.problem, pl.q * pl.r2, p->variant == 1 ? 1 : 0, pi2_out);
   count_launch(2);
   return cuda_ok(cudaGetLastError(), "launch fct_reduce");
 }

@@ -253,6 +253,23 @@ __device__ __forceinline__ double pi2_entry(Key2 key, uint32_t problem, int e) {
   return cauchy_f64(w >> 8);
 }
 
+// Gaussian Π2 entry e (OptimizedFastCauchyRegression): Box–Muller on Philox call ⌊e/2⌋ of
+// stream 1 with two open 53-bit uniforms, u1 from words (0, 1) and u2 from (2, 3);
+// entry 2t is √(−2 ln u1)·cos(2π u2), entry 2t+1 the sine.
+__device__ __forceinline__ double pi2_entry_gaussian(Key2 key, uint32_t problem, int e) {
+  const uint4 o = philox4x32_10(make_uint4(static_cast<uint32_t>(e >> 1), 0u, problem, kStreamPi2), key);
+  const double u1 = (static_cast<double>(u53_of(o.x, o.y)) + 0.5) * 0x1p-53;
+  const double u2 = (static_cast<double>(u53_of(o.z, o.w)) + 0.5) * 0x1p-53;
+  const double rho = sqrt(-2.0 * log(u1));
+  double sn, cs;
+  sincospi(2.0 * u2, &sn, &cs);
+  return rho * ((e & 1) ? sn : cs);
+}
+
+__device__ __forceinline__ double pi2_value(Key2 key, uint32_t problem, int e, int gaussian) {
+  return gaussian ? pi2_entry_gaussian(key, problem, e) : pi2_entry(key, problem, e);
+}
+
 // Σ of the λ block partials in a fixed order, for a block of 256 threads: strided
 // per-thread sums, a fixed shuffle tree, then the eight warp sums in order (every
 // thread returns the total).  The finalize kernel and the sampling kernel both use it,

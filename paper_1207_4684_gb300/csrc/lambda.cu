@@ -298,6 +298,10 @@ static bool launch_lambda_t(const Plan& pl, const TA* A, int64_t lda, const floa
     count_launch(1);                                                                          \
     return cuda_ok(cudaGetLastError(), "launch lambda");                                      \
   }
+  L1S_LAMBDA_CASE(4, 8)
+  L1S_LAMBDA_CASE(8, 8)
+  L1S_LAMBDA_CASE(16, 8)
+  L1S_LAMBDA_CASE(32, 8)
   L1S_LAMBDA_CASE(4, 16)
   L1S_LAMBDA_CASE(8, 16)
   L1S_LAMBDA_CASE(16, 16)

@@ -58,6 +58,7 @@ struct MarkArgs {
   const double* lam_sums;  // λ block partials when this kernel forms Σλ and τ itself (else null)
   int nsums;
   double coreset;        // m_s
+  double tau_fixed;      // > 0: p̂ = min(1, tau_fixed·λ) without Σλ (OptimizedFastCauchyRegression)
   StatusBlock* status_rw;
 };
 
@@ -71,7 +72,14 @@ __global__ void __launch_bounds__(kSmpThreads) sample_mark_kernel(const MarkArgs
   const int64_t stop = min(a.n, start + a.chunk);
   double tau = 0.0;
   float tau32 = 0.f;
-  if (a.lam_sums) {
+  if (a.tau_fixed > 0.0) {
+    tau = a.tau_fixed;
+    tau32 = tau > static_cast<double>(FLT_MAX) ? FLT_MAX : static_cast<float>(tau);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      a.status_rw->tau = tau;
+      a.status_rw->tau32 = tau32;
+    }
+  } else if (a.lam_sums) {
     // Σλ over the λ block partials (the same fixed order as the finalize kernel) and
     // τ = m_s/Σλ, formed by every block; block 0 records them in the status block.
     const double tot = lambda_total_256(a.lam_sums, a.nsums, wsum);
@@ -270,6 +278,7 @@ bool launch_sample(const Plan& pl, const float* lam, const double* p, const l1s_
   m.lam_sums = lam_nsums > 0 ? reinterpret_cast<const double*>(ws + pl.off_lamsum) : nullptr;
   m.nsums = lam_nsums;
   m.coreset = prm->coreset_size;
+  m.tau_fixed = (lam && prm->variant == 1) ? prm->sample_scale : 0.0;
   m.status_rw = reinterpret_cast<StatusBlock*>(ws + pl.off_status);
   sample_mark_kernel<<<pl.smp_ctas, pl.smp_threads, 0, st>>>(m);
   count_launch(1);
