@@ -19,9 +19,9 @@ size_t fct_smem_bytes(int s, int d, l1s_dtype dt, int r1, int width, bool staged
 int fct_threads_for(int log2s, int width);
 int fct_ws_width(int log2s, int d);
 int fct_ws_tile_log2(int log2s);
-const void* fct_ws_kernel(int log2t, int log2s, l1s_dtype dt, int w);
+const void* fct_ws_kernel(int log2t, int log2s, l1s_dtype dt, int w, bool lean);
 int fct_ws_threads(int w);
-size_t fct_ws_smem_bytes(int s, int d, l1s_dtype dt, int r1, int w);
+size_t fct_ws_smem_bytes(int s, int d, l1s_dtype dt, int r1, int w, bool lean);
 int fct_sorted_width(int log2s, int d);
 const void* fct_sorted_kernel(int log2s, l1s_dtype dt, int w);
 int fct_sorted_threads(int w);
@@ -173,6 +173,7 @@ struct FctGeometry {
   bool staged;
   int ws;                 // column width of the narrow-X kernel, 0 otherwise
   int tile_log2;          // its tile
+  bool lean;              // its one-stage, one-copy form
   int sorted;             // column width of the bucket-sorted kernel, 0 otherwise
   int slices, width, threads, per_sm;
   size_t smem;
@@ -189,10 +190,14 @@ static FctGeometry fct_geometry(int variant, const Plan& P, l1s_dtype dt, const 
     if (!w || fct_sorted_smem_bytes(P.s, P.d, dt, P.r1, w) > budget1) return g;
     g.sorted = w;
     staged = true;
-  } else if (variant == 1) {
+  } else if (variant == 1 || variant == 5) {
     const int w = fct_ws_width(P.log2s, P.d);
-    if (!w || fct_ws_smem_bytes(1 << fct_ws_tile_log2(P.log2s), P.d, dt, P.r1, w) > budget1) return g;
+    const bool lean = variant == 5;
+    if (!w || (lean && w != 16) ||
+        fct_ws_smem_bytes(1 << fct_ws_tile_log2(P.log2s), P.d, dt, P.r1, w, lean) > budget1)
+      return g;
     g.ws = w;
+    g.lean = lean;
     g.tile_log2 = fct_ws_tile_log2(P.log2s);
     staged = true;
   } else if (variant == 2) {
@@ -218,11 +223,12 @@ static FctGeometry fct_geometry(int variant, const Plan& P, l1s_dtype dt, const 
   g.slices = (P.q + width - 1) / width;
   g.width = width;
   g.smem = g.sorted ? fct_sorted_smem_bytes(P.s, P.d, dt, P.r1, g.sorted)
-                    : (g.ws ? fct_ws_smem_bytes(1 << g.tile_log2, P.d, dt, P.r1, g.ws)
+                    : (g.ws ? fct_ws_smem_bytes(1 << g.tile_log2, P.d, dt, P.r1, g.ws, g.lean)
                             : fct_smem_bytes(P.s, P.d, dt, P.r1, width, staged));
   g.threads = g.sorted ? fct_sorted_threads(g.sorted) : (g.ws ? fct_ws_threads(g.ws) : fct_threads_for(P.log2s, width));
   const void* fn = g.sorted ? fct_sorted_kernel(P.log2s, dt, g.sorted)
-                            : (g.ws ? fct_ws_kernel(g.tile_log2, P.log2s, dt, g.ws) : fct_kernel(P.log2s, dt, staged));
+                            : (g.ws ? fct_ws_kernel(g.tile_log2, P.log2s, dt, g.ws, g.lean)
+                                    : fct_kernel(P.log2s, dt, staged));
   if (!cuda_ok(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(g.smem)),
                "cudaFuncSetAttribute(fct_embed)"))
     return g;
@@ -271,14 +277,15 @@ bool make_plan(const l1s_params* p, int64_t n, int d, l1s_dtype dt, bool host_st
   // columns in one block with TMA-staged X tiles, else direct loads over column slices.
   // The bucket-sorted kernel is a schedule choice (slower than the narrow-X kernel on the
   // shapes measured so far).
-  FctGeometry geo[5];
-  for (int v = 1; v <= 4; ++v) geo[v] = fct_geometry(v, P, dt, di);
+  FctGeometry geo[6];
+  for (int v = 1; v <= 5; ++v) geo[v] = fct_geometry(v, P, dt, di);
   if (!geo[3].ok) return set_error("r1 and s too large for shared memory"), false;
   int variant = geo[1].ok ? 1 : (geo[2].ok ? 2 : 3);
-  if (sch.fct_variant >= 1 && sch.fct_variant <= 4 && geo[sch.fct_variant].ok) variant = sch.fct_variant;
+  if (sch.fct_variant >= 1 && sch.fct_variant <= 5 && geo[sch.fct_variant].ok) variant = sch.fct_variant;
   const FctGeometry& g = geo[variant];
   P.fct_ws = g.ws;
   P.fct_tile_log2 = g.tile_log2;
+  P.fct_lean = g.lean ? 1 : 0;
   P.fct_sorted = g.sorted;
   P.fct_staged = g.staged ? 1 : 0;
   P.fct_slices = g.slices;
@@ -289,7 +296,7 @@ bool make_plan(const l1s_params* p, int64_t n, int d, l1s_dtype dt, bool host_st
   P.fct_ctas = static_cast<int>(fct_ctas_of(g, P, di, per_sm));
   // Partial sums sized for the largest variant at full occupancy.
   size_t partial_floats = 0;
-  for (int v = 1; v <= 4; ++v)
+  for (int v = 1; v <= 5; ++v)
     if (geo[v].ok)
       partial_floats = std::max<size_t>(
           partial_floats, static_cast<size_t>(geo[v].slices) * fct_ctas_of(geo[v], P, di, geo[v].per_sm) *

@@ -336,9 +336,14 @@ struct __align__(8) T16MetaH {
 
 // LOG2S here is the tile: 2^LOG2S rows per pipeline step, which may hold several
 // H_s blocks (s = 2^a.log2s ≤ tile): butterfly stages over row bits ≥ log2 s are skipped.
-template <int LOG2S, typename TA, int W, bool EXACT>
-__global__ void __launch_bounds__(WsCfg<W>::kThreads) fct_embed_ws_kernel(const FctArgs a) {
+// LEAN (W = 16 only): one stage buffer (the next tile's copy overlaps pass 2, which no
+// longer reads the stage) and one copy of P with rows padded to 17 words instead of two
+// copies, so that three thread blocks fit an SM.
+template <int LOG2S, typename TA, int W, bool EXACT, bool LEAN>
+__global__ void __launch_bounds__(WsCfg<W>::kThreads, LEAN ? 3 : (W == 16 ? 2 : 1)) fct_embed_ws_kernel(const FctArgs a) {
   constexpr int kWsA = WsCfg<W>::kA;
+  constexpr int PST = LEAN ? 17 : 32;         // words per bucket row of P
+  constexpr int NSTAGE = LEAN ? 1 : 2;
   constexpr int S = 1 << LOG2S;
   const int lg = EXACT ? LOG2S : a.log2s;   // H_s acts on row bits [0, lg); EXACT: s is the tile
   constexpr int K2 = LOG2S - 4;          // pass 2: row bit 0 and bits [5, LOG2S)
@@ -353,13 +358,13 @@ __global__ void __launch_bounds__(WsCfg<W>::kThreads) fct_embed_ws_kernel(const 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int d = a.d;
   unsigned char* stages = smem_raw;
-  float* P = reinterpret_cast<float*>(stages + 2 * static_cast<size_t>(a.stage_bytes));        // [r1][32]
-  float* Pb = P + r1 * 32;                                                                         // [r1]
+  float* P = reinterpret_cast<float*>(stages + NSTAGE * static_cast<size_t>(a.stage_bytes));   // [r1][PST]
+  float* Pb = P + ((r1 * PST + 3) & ~3);                                                           // [r1]
   float* tile = Pb + ((r1 + 3) & ~3);                                                              // [S][16]
   T16Meta* mI = reinterpret_cast<T16Meta*>(tile + S * W);                                          // [2][S]
   T16MetaH* mH = reinterpret_cast<T16MetaH*>(mI + 2 * S);                                          // [2][S]
 
-  for (int i = tid; i < r1 * 33; i += blockDim.x) P[i] = 0.f;   // P and Pb
+  for (int i = tid; i < ((r1 * PST + 3) & ~3) + r1; i += blockDim.x) P[i] = 0.f;   // P and Pb
   if (tid == 0) {
     s_abort = 0;
     for (int k = 0; k < 2; ++k) {
@@ -381,15 +386,18 @@ __global__ void __launch_bounds__(WsCfg<W>::kThreads) fct_embed_ws_kernel(const 
     for (int64_t blk = blockIdx.x; blk < a.nblocks; blk += gridDim.x, ++i) {
       const int buf = static_cast<int>(i & 1);
       const uint32_t use = static_cast<uint32_t>((i >> 1) & 1);
-      unsigned char* stage = stages + static_cast<size_t>(buf) * a.stage_bytes;
+      const int sbuf = LEAN ? 0 : buf;                         // stage buffer and its phase parity
+      const uint32_t suse = LEAN ? static_cast<uint32_t>(i & 1) : use;
+      unsigned char* stage = stages + static_cast<size_t>(sbuf) * a.stage_bytes;
       const int64_t row0 = blk * S;
       const bool by_tma = tma && blk < a.full_blocks;
-      // the stage and the draw buffer are free once block i−2 is done with them
+      // the stage is free once its previous tile finished pass 1, the draw buffer once
+      // block i−2 is done with it
       if (pt == 0) {
-        const bool ok = mbar_wait_bounded(&stage_free[buf], use ^ 1u, kWaitCycles) &&
+        const bool ok = mbar_wait_bounded(&stage_free[sbuf], suse ^ 1u, kWaitCycles) &&
                         mbar_wait_bounded(&meta_free[buf], use ^ 1u, kWaitCycles);
         if (!ok) s_abort = 1;
-        else if (by_tma) issue_stage_tma<TA>(a, blk, S, stage, &stage_full[buf]);
+        else if (by_tma) issue_stage_tma<TA>(a, blk, S, stage, &stage_full[sbuf]);
       }
       // one decision for all producers (a consumer may set s_abort at any moment)
       if (named_barrier_any(1, 32 * kWsP, s_abort != 0)) break;
@@ -412,19 +420,19 @@ __global__ void __launch_bounds__(WsCfg<W>::kThreads) fct_embed_ws_kernel(const 
         const bool neg = a.sign_flip && (o.w & 1u);
         T16Meta m;
         m.hI = bucket_of(o.z, r1);
-        m.offI = 32 * m.hI;
+        m.offI = PST * m.hI;
         const float wI = 4.f * cauchy_f32(o.w >> 8);
         m.wIs = neg ? -wI : wI;
         m.smask = neg ? 0x80000000u : 0u;
         mi[r] = m;
         T16MetaH h;
-        h.offH = 32 * bucket_of(o.x, r1);
+        h.offH = PST * bucket_of(o.x, r1);
         h.wH = 4.f * cauchy_f32(o.y >> 8) * a.inv_sqrt_s;
         mh[r] = h;
       }
       named_barrier(1, 32 * kWsP);                  // all draws (and a plain stage) written
       if (pt == 0) {
-        if (!by_tma) mbar_arrive(&stage_full[buf]);
+        if (!by_tma) mbar_arrive(&stage_full[sbuf]);
         mbar_arrive(&meta_full[buf]);
       }
     }
@@ -435,16 +443,19 @@ __global__ void __launch_bounds__(WsCfg<W>::kThreads) fct_embed_ws_kernel(const 
     for (int64_t blk = blockIdx.x; blk < a.nblocks; blk += gridDim.x, ++i) {
       const int buf = static_cast<int>(i & 1);
       const uint32_t use = static_cast<uint32_t>((i >> 1) & 1);
+      const int sbuf = LEAN ? 0 : buf;
+      const uint32_t suse = LEAN ? static_cast<uint32_t>(i & 1) : use;
       bool ok = true;
       if (lane == 0)
-        ok = mbar_wait_bounded(&meta_full[buf], use, kWaitCycles) && mbar_wait_bounded(&stage_full[buf], use, kWaitCycles);
+        ok = mbar_wait_bounded(&meta_full[buf], use, kWaitCycles) &&
+             mbar_wait_bounded(&stage_full[sbuf], suse, kWaitCycles);
       ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
       // all consumer warps take the same decision, so none is left waiting at a barrier
       if (named_barrier_any(3, 32 * (kWsA + kWsB), !ok || s_abort)) {
         s_abort = 1;
         break;
       }
-      const unsigned char* stage = stages + static_cast<size_t>(buf) * a.stage_bytes;
+      const unsigned char* stage = stages + static_cast<size_t>(sbuf) * a.stage_bytes;
       const TA* rawA = reinterpret_cast<const TA*>(stage);
       const float* rawB = reinterpret_cast<const float*>(stage + b_off);
       const T16Meta* mi = mI + buf * S;
@@ -487,7 +498,7 @@ __global__ void __launch_bounds__(WsCfg<W>::kThreads) fct_embed_ws_kernel(const 
           const int hb = g & 1;
           const int base = (g & 1) | ((g >> 1) << 5);
           const bool live = c < d;
-          float* Pl = P + hb * 16 + c;
+          float* Pl = P + (LEAN ? 0 : hb * 16) + c;
           float v[16];
 #pragma unroll
           for (int j = 0; j < 16; ++j) v[j] = live ? widen<TA>(rawA[(base | (j << 1)) * d + c]) : 0.f;
@@ -515,7 +526,7 @@ __global__ void __launch_bounds__(WsCfg<W>::kThreads) fct_embed_ws_kernel(const 
           for (int j = 0; j < 16; ++j) tile[(base | (j << 1)) * 16 + c] = v[j];
         }
         __syncwarp();
-        if (lane == 0) mbar_arrive(&stage_free[buf]);
+        if (lane == 0) mbar_arrive(&stage_free[sbuf]);
         named_barrier(2, 32 * kWsA);                   // tile complete
         // ---- pass 2 on A: the remaining row bits, then the Hadamard scatter
         if constexpr (W == 32) {
@@ -567,7 +578,7 @@ __global__ void __launch_bounds__(WsCfg<W>::kThreads) fct_embed_ws_kernel(const 
             }
           }
           if (c < d) {
-            float* Pl = P + hb * 16 + c;
+            float* Pl = P + (LEAN ? 0 : hb * 16) + c;
             const float odd_sign = hb ? -1.f : 1.f;
 #pragma unroll
             for (int k = 0; k < G2; ++k) {
@@ -592,7 +603,7 @@ __global__ void __launch_bounds__(WsCfg<W>::kThreads) fct_embed_ws_kernel(const 
           atomicAdd(&Pb[m.w], __int_as_float(m.y) * x);
         }
         __syncwarp();
-        if (lane == 0) mbar_arrive(&stage_free[buf]);
+        if (lane == 0) mbar_arrive(&stage_free[sbuf]);
 #pragma unroll
         for (int t = 0; (1 << t) < KB; ++t) {
           if (5 + t < lg) {                                     // row bit 5 + t
@@ -620,7 +631,7 @@ __global__ void __launch_bounds__(WsCfg<W>::kThreads) fct_embed_ws_kernel(const 
 #pragma unroll
         for (int k = 0; k < KB; ++k) {
           const int2 h = *reinterpret_cast<const int2*>(&mh[lane + 32 * k]);
-          atomicAdd(&Pb[h.x >> 5], __int_as_float(h.y) * v[k]);
+          atomicAdd(&Pb[h.x / PST], __int_as_float(h.y) * v[k]);
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&meta_free[buf]);
@@ -643,7 +654,8 @@ __global__ void __launch_bounds__(WsCfg<W>::kThreads) fct_embed_ws_kernel(const 
   float* out = a.partials + static_cast<size_t>(blockIdx.x) * r1 * q;
   for (int i = tid; i < r1 * q; i += blockDim.x) {
     const int h = i / q, c = i - h * q;
-    out[i] = c < d ? (W == 16 ? P[h * 32 + c] + P[h * 32 + 16 + c] : P[h * 32 + c]) : Pb[h];
+    out[i] = c < d ? (LEAN ? P[h * PST + c] : (W == 16 ? P[h * 32 + c] + P[h * 32 + 16 + c] : P[h * 32 + c]))
+                   : Pb[h];
   }
 }
 
@@ -1120,13 +1132,13 @@ const void* fct_kernel(int log2s, l1s_dtype dt, bool staged) {
   return staged ? fct_kernel_for<float, true>(log2s) : fct_kernel_for<float, false>(log2s);
 }
 
-template <typename TA, int W>
+template <typename TA, int W, bool LEAN>
 static const void* ws_kernel_for(int log2t, bool exact) {
   switch (log2t) {
-    case 8: return exact ? reinterpret_cast<const void*>(&fct_embed_ws_kernel<8, TA, W, true>)
-                         : reinterpret_cast<const void*>(&fct_embed_ws_kernel<8, TA, W, false>);
-    case 9: return exact ? reinterpret_cast<const void*>(&fct_embed_ws_kernel<9, TA, W, true>)
-                         : reinterpret_cast<const void*>(&fct_embed_ws_kernel<9, TA, W, false>);
+    case 8: return exact ? reinterpret_cast<const void*>(&fct_embed_ws_kernel<8, TA, W, true, LEAN>)
+                         : reinterpret_cast<const void*>(&fct_embed_ws_kernel<8, TA, W, false, LEAN>);
+    case 9: return exact ? reinterpret_cast<const void*>(&fct_embed_ws_kernel<9, TA, W, true, LEAN>)
+                         : reinterpret_cast<const void*>(&fct_embed_ws_kernel<9, TA, W, false, LEAN>);
     default: return nullptr;
   }
 }
@@ -1140,13 +1152,19 @@ int fct_ws_width(int log2s, int d) {
 // Its tile: at least 256 rows, so that blocks of small s share the per-tile pipeline costs.
 int fct_ws_tile_log2(int log2s) { return log2s < 8 ? 8 : log2s; }
 
-// The kernel for a tile of 2^log2t rows and blocks of 2^log2s rows (log2s ≤ log2t).
-const void* fct_ws_kernel(int log2t, int log2s, l1s_dtype dt, int w) {
+// The kernel for a tile of 2^log2t rows and blocks of 2^log2s rows (log2s ≤ log2t); lean
+// (W = 16 only) selects the one-stage, one-copy form.
+const void* fct_ws_kernel(int log2t, int log2s, l1s_dtype dt, int w, bool lean) {
   const bool exact = log2s == log2t;
+  if (w == 16 && lean)
+    return dt == L1S_BF16 ? ws_kernel_for<uint16_t, 16, true>(log2t, exact)
+                          : ws_kernel_for<float, 16, true>(log2t, exact);
   if (w == 16)
-    return dt == L1S_BF16 ? ws_kernel_for<uint16_t, 16>(log2t, exact) : ws_kernel_for<float, 16>(log2t, exact);
+    return dt == L1S_BF16 ? ws_kernel_for<uint16_t, 16, false>(log2t, exact)
+                          : ws_kernel_for<float, 16, false>(log2t, exact);
   if (w == 32)
-    return dt == L1S_BF16 ? ws_kernel_for<uint16_t, 32>(log2t, exact) : ws_kernel_for<float, 32>(log2t, exact);
+    return dt == L1S_BF16 ? ws_kernel_for<uint16_t, 32, false>(log2t, exact)
+                          : ws_kernel_for<float, 32, false>(log2t, exact);
   return nullptr;
 }
 
@@ -1198,8 +1216,10 @@ size_t fct_smem_bytes(int s, int d, l1s_dtype dt, int r1, int width, bool staged
          static_cast<size_t>(s) * (sizeof(RowMeta) + 4);
 }
 
-size_t fct_ws_smem_bytes(int s, int d, l1s_dtype dt, int r1, int w) {
-  return 2 * static_cast<size_t>(fct_stage_bytes(s, d, dt)) + static_cast<size_t>(r1) * 32 * 4 +
+size_t fct_ws_smem_bytes(int s, int d, l1s_dtype dt, int r1, int w, bool lean) {
+  const int pst = lean ? 17 : 32;
+  return (lean ? 1 : 2) * static_cast<size_t>(fct_stage_bytes(s, d, dt)) +
+         static_cast<size_t>((r1 * pst + 3) & ~3) * 4 +
          static_cast<size_t>((r1 + 3) & ~3) * 4 + static_cast<size_t>(s) * w * 4 +
          2 * static_cast<size_t>(s) * (sizeof(T16Meta) + sizeof(T16MetaH));
 }
@@ -1256,9 +1276,10 @@ bool launch_fct(const Plan& pl, const void* A, int64_t lda, l1s_dtype dt, const 
   const int srt = pl.fct_sorted;
   if (wsw || srt) a.tma = fct_can_stage(tile, pl.d, dt, lda, A, b) ? 1 : 0;
   const void* fn = srt ? fct_sorted_kernel(pl.log2s, dt, srt)
-                       : (wsw ? fct_ws_kernel(pl.fct_tile_log2, pl.log2s, dt, wsw) : fct_kernel(pl.log2s, dt, staged));
+                       : (wsw ? fct_ws_kernel(pl.fct_tile_log2, pl.log2s, dt, wsw, pl.fct_lean != 0)
+                              : fct_kernel(pl.log2s, dt, staged));
   const size_t smem = srt ? fct_sorted_smem_bytes(pl.s, pl.d, dt, pl.r1, srt)
-                          : (wsw ? fct_ws_smem_bytes(tile, pl.d, dt, pl.r1, wsw)
+                          : (wsw ? fct_ws_smem_bytes(tile, pl.d, dt, pl.r1, wsw, pl.fct_lean != 0)
                                  : fct_smem_bytes(pl.s, pl.d, dt, pl.r1, pl.fct_width, staged));
   if (!cuda_ok(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)),
                "cudaFuncSetAttribute(fct_embed)"))

@@ -230,6 +230,7 @@ struct Plan {
   int fct_staged;           // 1: tiles of X arrive in shared memory by TMA bulk copies
   int fct_ws;               // 16 or 32: the narrow-X kernel with that column width runs phase 1
   int fct_tile_log2;        // its tile (rows per pipeline step, 2^fct_tile_log2 ≥ s)
+  int fct_lean;             // 1: its one-stage, one-copy form (W = 16)
   int fct_sorted;           // 16 or 32: the bucket-sorted kernel with that column width runs phase 1
   int fct_ctas;             // thread blocks per slice
   size_t fct_smem;
