@@ -28,6 +28,9 @@ int fct_sorted_threads(int w);
 size_t fct_sorted_smem_bytes(int s, int d, l1s_dtype dt, int r1, int w);
 bool launch_fct(const Plan& pl, const void* A, int64_t lda, l1s_dtype dt, const float* b,
                 const l1s_params* p, float* pix, unsigned char* ws, cudaStream_t st, double* pi2_out = nullptr);
+bool launch_fct_streamed(const Plan& pl, const void* A_host, int64_t lda_host, l1s_dtype dt, const float* b_host,
+                         void* A_dev, float* b_dev, const l1s_params* p, float* pix, unsigned char* ws,
+                         cudaStream_t st, cudaStream_t cp, const cudaEvent_t* evs, double* pi2_out);
 bool launch_condition(const Plan& pl, const float* pix, const l1s_params* p, double* R_user,
                       double* M_user, unsigned char* ws, cudaStream_t st, bool pi2_ready = false);
 bool launch_pi2(const l1s_params* p, int q, double* out, cudaStream_t st);
@@ -250,6 +253,7 @@ static int64_t fct_ctas_of(const FctGeometry& g, const Plan& P, const DeviceInfo
 // Bounds of the schedule fields (the workspace is sized for the largest).
 constexpr int kMaxLamPerSm = 32;
 constexpr int kMaxSmpPerSm = 16;
+constexpr int kMaxChunks = 8;
 
 bool make_plan(const l1s_params* p, int64_t n, int d, l1s_dtype dt, bool host_staging, Plan* pl,
                const l1s_schedule* override_sch) {
@@ -294,6 +298,14 @@ bool make_plan(const l1s_params* p, int64_t n, int d, l1s_dtype dt, bool host_st
   P.fct_threads = g.threads;
   const int per_sm = sch.fct_ctas_per_sm > 0 ? std::min(sch.fct_ctas_per_sm, g.per_sm) : g.per_sm;
   P.fct_ctas = static_cast<int>(fct_ctas_of(g, P, di, per_sm));
+  // Inputs in host memory arrive in up to kMaxChunks row chunks of at least two waves of
+  // tiles each, so that phase 1 on one chunk overlaps the copy of the next.
+  P.fct_chunks = 1;
+  if (host_staging) {
+    const int64_t tiles = g.ws ? (n + (int64_t{1} << g.tile_log2) - 1) >> g.tile_log2 : P.nblocks;
+    P.fct_chunks = static_cast<int>(
+        std::max<int64_t>(1, std::min<int64_t>(kMaxChunks, tiles / (2 * static_cast<int64_t>(P.fct_ctas)))));
+  }
   // Partial sums sized for the largest variant at full occupancy.
   size_t partial_floats = 0;
   for (int v = 1; v <= 5; ++v)
@@ -486,14 +498,59 @@ int l1_coreset(const void* A, int64_t lda, l1s_dtype dtype, const float* b, int6
 }
 
 
-static bool stage_inputs(const Plan& pl, const void* A_host, int64_t lda, l1s_dtype dtype, const float* b_host,
-                         unsigned char* w, cudaStream_t st) {
-  const size_t esz = dtype == L1S_BF16 ? 2 : 4;
-  return cuda_ok(cudaMemcpy2DAsync(w + pl.off_stage_a, esz * pl.d, A_host, esz * lda, esz * pl.d, pl.n,
-                                   cudaMemcpyHostToDevice, st),
-                 "copy A to device") &&
-         cuda_ok(cudaMemcpyAsync(w + pl.off_stage_b, b_host, sizeof(float) * pl.n, cudaMemcpyHostToDevice, st),
-                 "copy b to device");
+// Copy stream and events (per device) for inputs that arrive from host memory.  A call
+// holds the pool's mutex while it enqueues.
+struct CopyPool {
+  bool ready = false;
+  cudaStream_t cp;
+  cudaEvent_t start;
+  cudaEvent_t chunk[kMaxChunks];
+  std::mutex mu;
+};
+static CopyPool g_copy_pools[64];
+static std::mutex g_copy_pools_mu;
+
+static CopyPool* copy_pool() {
+  int dev = 0;
+  if (!cuda_ok(cudaGetDevice(&dev), "cudaGetDevice") || dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lock(g_copy_pools_mu);
+  CopyPool& P = g_copy_pools[dev];
+  if (!P.ready) {
+    if (!cuda_ok(cudaStreamCreateWithFlags(&P.cp, cudaStreamNonBlocking), "create copy stream") ||
+        !cuda_ok(cudaEventCreateWithFlags(&P.start, cudaEventDisableTiming), "create copy event"))
+      return nullptr;
+    for (int k = 0; k < kMaxChunks; ++k)
+      if (!cuda_ok(cudaEventCreateWithFlags(&P.chunk[k], cudaEventDisableTiming), "create copy event"))
+        return nullptr;
+    P.ready = true;
+  }
+  return &P;
+}
+
+// The coreset of inputs in host memory: the rows are copied into the workspace's staging
+// region chunk by chunk, overlapping phase 1, and phases 2 and 3 read the staged rows.
+static int coreset_impl_host(const Plan& pl, const void* A_host, int64_t lda, l1s_dtype dtype,
+                             const float* b_host, const l1s_params* params, int64_t capacity, int64_t* idx,
+                             double* wts, double* coreset, int64_t* count, unsigned char* w, cudaStream_t st) {
+  CopyPool* cpool = copy_pool();
+  if (!cpool) return L1S_ERR_CUDA;
+  void* A_dev = w + pl.off_stage_a;
+  float* b_dev = reinterpret_cast<float*>(w + pl.off_stage_b);
+  {
+    std::lock_guard<std::mutex> lock(cpool->mu);
+    if (!cuda_ok(cudaMemsetAsync(w + pl.off_status, 0, sizeof(StatusBlock), st), "status reset") ||
+        !cuda_ok(cudaEventRecord(cpool->start, st), "record copy start") ||
+        !cuda_ok(cudaStreamWaitEvent(cpool->cp, cpool->start, 0), "copy stream wait"))
+      return L1S_ERR_CUDA;
+    if (!launch_fct_streamed(pl, A_host, lda, dtype, b_host, A_dev, b_dev, params,
+                             reinterpret_cast<float*>(w + pl.off_pix), w, st, cpool->cp, cpool->chunk,
+                             reinterpret_cast<double*>(w + pl.off_pi2)))
+      return L1S_ERR_CUDA;
+  }
+  if (!launch_condition(pl, reinterpret_cast<float*>(w + pl.off_pix), params, nullptr, nullptr, w, st, true))
+    return L1S_ERR_CUDA;
+  return sample_impl(pl, A_dev, pl.d, dtype, b_dev, reinterpret_cast<float*>(w + pl.off_m32), params, capacity,
+                     idx, wts, coreset, count, nullptr, w, st);
 }
 
 int l1_coreset_host(const void* A_host, int64_t lda, l1s_dtype dtype, const float* b_host, int64_t n,
@@ -507,14 +564,13 @@ int l1_coreset_host(const void* A_host, int64_t lda, l1s_dtype dtype, const floa
   if (!check_ws(pl, ws, ws_bytes)) return L1S_ERR_WORKSPACE;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   unsigned char* w = static_cast<unsigned char*>(ws);
-  if (!stage_inputs(pl, A_host, lda, dtype, b_host, w, st)) return L1S_ERR_CUDA;
   const int64_t cap_ws = coreset_capacity_of(params);
   const int64_t cap = std::min(capacity, cap_ws);
   int64_t* idx_dev = reinterpret_cast<int64_t*>(w + pl.off_idx_tmp);
   double* w_dev = reinterpret_cast<double*>(idx_dev + cap_ws);
   StatusBlock* sb = reinterpret_cast<StatusBlock*>(w + pl.off_status);
-  int rc = coreset_impl(pl, w + pl.off_stage_a, d, dtype, reinterpret_cast<const float*>(w + pl.off_stage_b),
-                        params, cap, idx_dev, w_dev, nullptr, &sb->count, w, st);
+  int rc = coreset_impl_host(pl, A_host, lda, dtype, b_host, params, cap, idx_dev, w_dev, nullptr, &sb->count, w,
+                             st);
   if (rc != L1S_OK) return rc;
   int64_t cnt = 0;
   if (!cuda_ok(cudaMemcpyAsync(&cnt, &sb->count, sizeof(int64_t), cudaMemcpyDeviceToHost, st), "copy count") ||
@@ -585,7 +641,6 @@ int l1_regress(const void* A, int64_t lda, l1s_dtype dtype, const float* b, int6
   const float* bd = b;
   int64_t ld = lda;
   if (inputs_on_host) {
-    if (!stage_inputs(pl, A, lda, dtype, b, w, st)) return L1S_ERR_CUDA;
     Ad = w + pl.off_stage_a;
     bd = reinterpret_cast<const float*>(w + pl.off_stage_b);
     ld = d;
@@ -598,7 +653,8 @@ int l1_regress(const void* A, int64_t lda, l1s_dtype dtype, const float* b, int6
   double* xd = core + cap * q;
   double* objd = xd + q + 1;
   StatusBlock* sb = reinterpret_cast<StatusBlock*>(w + pl.off_status);
-  int rc = coreset_impl(pl, Ad, ld, dtype, bd, params, cap, idx, wts, core, &sb->count, w, st);
+  int rc = inputs_on_host ? coreset_impl_host(pl, A, lda, dtype, b, params, cap, idx, wts, core, &sb->count, w, st)
+                          : coreset_impl(pl, Ad, ld, dtype, bd, params, cap, idx, wts, core, &sb->count, w, st);
   if (rc != L1S_OK) return rc;
   rc = l1_solve(core, wts, &sb->count, cap, d, 100, xd, objd, ws, ws_bytes, stream);
   if (rc != L1S_OK) return rc;

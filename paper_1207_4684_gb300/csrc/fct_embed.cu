@@ -42,6 +42,7 @@ struct FctArgs {
   int log2s;              // log2 s (the narrow-X kernel's tile may hold several H_s blocks)
   float inv_sqrt_s;
   float* partials;        // [slices][gridDim.x][r1][width]
+  int accumulate;         // 1: add to the partials of an earlier launch over other rows
   uint32_t* flags;
 };
 
@@ -290,7 +291,7 @@ __global__ void __launch_bounds__(kFctMaxThreads) fct_embed_kernel(const FctArgs
   }
   // Non-finite input shows up as a non-finite partial (checked in the reduction).
   float* out = a.partials + (static_cast<size_t>(blockIdx.y) * gridDim.x + blockIdx.x) * a.r1 * W;
-  for (int i = threadIdx.x; i < a.r1 * W; i += blockDim.x) out[i] = part[i];
+  for (int i = threadIdx.x; i < a.r1 * W; i += blockDim.x) out[i] = (a.accumulate ? out[i] : 0.f) + part[i];
 }
 
 // ----------------------------------------------------------------- d ≤ 32, 32 ≤ s ≤ 512
@@ -654,8 +655,9 @@ __global__ void __launch_bounds__(WsCfg<W>::kThreads, LEAN ? 3 : (W == 16 ? 2 : 
   float* out = a.partials + static_cast<size_t>(blockIdx.x) * r1 * q;
   for (int i = tid; i < r1 * q; i += blockDim.x) {
     const int h = i / q, c = i - h * q;
-    out[i] = c < d ? (LEAN ? P[h * PST + c] : (W == 16 ? P[h * 32 + c] + P[h * 32 + 16 + c] : P[h * 32 + c]))
-                   : Pb[h];
+    const float v = c < d ? (LEAN ? P[h * PST + c] : (W == 16 ? P[h * 32 + c] + P[h * 32 + 16 + c] : P[h * 32 + c]))
+                          : Pb[h];
+    out[i] = (a.accumulate ? out[i] : 0.f) + v;
   }
 }
 
@@ -1055,7 +1057,7 @@ __global__ void __launch_bounds__(SrtCfg<W>::kThreads) fct_embed_sorted_kernel(c
   float* out = a.partials + static_cast<size_t>(blockIdx.x) * r1 * q;
   for (int i = tid; i < r1 * q; i += blockDim.x) {
     const int h = i / q, c = i - h * q;
-    out[i] = c < d ? P[h * W + c] : Pb[h];
+    out[i] = (a.accumulate ? out[i] : 0.f) + (c < d ? P[h * W + c] : Pb[h]);
   }
 }
 
@@ -1240,21 +1242,24 @@ int fct_threads_for(int log2s, int width) {
   return t > kFctMaxThreads ? kFctMaxThreads : t;
 }
 
-bool launch_fct(const Plan& pl, const void* A, int64_t lda, l1s_dtype dt, const float* b,
-                const l1s_params* p, float* pix, unsigned char* ws, cudaStream_t st, double* pi2_out) {
+// One phase-1 launch over rows [0, n) of A and b (device) whose global ids start at
+// row_offset, writing the per-block partials at `partials`.
+static bool launch_fct_part(const Plan& pl, const void* A, int64_t lda, l1s_dtype dt, const float* b, int64_t n,
+                            int64_t row_offset, const l1s_params* p, bool accumulate, unsigned char* ws,
+                            cudaStream_t st) {
   FctArgs a;
   a.A = A;
   a.lda = lda;
   a.b = b;
-  a.n = pl.n;
+  a.n = n;
   a.d = pl.d;
   a.q = pl.q;
   a.r1 = pl.r1;
   a.width = pl.fct_width;
   // The narrow-X kernel steps over tiles of 2^fct_tile_log2 ≥ s rows, the others over s-row blocks.
   const int tile = pl.fct_ws ? (1 << pl.fct_tile_log2) : pl.s;
-  a.nblocks = (pl.n + tile - 1) / tile;
-  a.full_blocks = pl.n / tile;
+  a.nblocks = (n + tile - 1) / tile;
+  a.full_blocks = n / tile;
   a.log2s = pl.log2s;
   const uint32_t esz = dt == L1S_BF16 ? 2u : 4u;
   a.stage_a_bytes = static_cast<uint32_t>(tile) * pl.d * esz;
@@ -1263,10 +1268,11 @@ bool launch_fct(const Plan& pl, const void* A, int64_t lda, l1s_dtype dt, const 
   a.tma = staged ? 1 : 0;
   a.key = make_key(p->seed);
   a.problem = p->problem_id;
-  a.row_offset = p->global_row_offset;
+  a.row_offset = row_offset;
   a.sign_flip = p->sign_flip;
   a.inv_sqrt_s = static_cast<float>(1.0 / sqrt(static_cast<double>(pl.s)));
   a.partials = reinterpret_cast<float*>(ws + pl.off_partials);
+  a.accumulate = accumulate ? 1 : 0;
   a.flags = reinterpret_cast<uint32_t*>(ws + pl.off_status);
   // A layout that cannot be staged falls back to direct loads with the same grid; the
   // direct variant needs less shared memory than the staged one it was planned for.
@@ -1286,14 +1292,61 @@ bool launch_fct(const Plan& pl, const void* A, int64_t lda, l1s_dtype dt, const 
     return false;
   void* args[] = {&a};
   dim3 grid(pl.fct_ctas, pl.fct_slices);
-  if (!cuda_ok(cudaLaunchKernel(fn, grid, dim3(pl.fct_threads), args, smem, st), "launch fct_embed"))
-    return false;
+  if (!cuda_ok(cudaLaunchKernel(fn, grid, dim3(pl.fct_threads), args, smem, st), "launch fct_embed")) return false;
+  count_launch(1);
+  return true;
+}
+
+static bool launch_fct_reduce(const Plan& pl, const l1s_params* p, float* pix, unsigned char* ws, cudaStream_t st,
+                              double* pi2_out) {
   const int per = pl.r1 * pl.fct_width;
   dim3 rgrid((per + 31) / 32, pl.fct_slices);
-  fct_reduce_kernel<<<rgrid, 1024, 0, st>>>(a.partials, pl.fct_ctas, pl.r1, pl.fct_width, pl.q, pix, a.flags, a.key,
-                                            a.problem, pl.q * pl.r2, p->variant == 1 ? 1 : 0, pi2_out);
-  count_launch(2);
+  fct_reduce_kernel<<<rgrid, 1024, 0, st>>>(reinterpret_cast<float*>(ws + pl.off_partials), pl.fct_ctas, pl.r1,
+                                            pl.fct_width, pl.q, pix, reinterpret_cast<uint32_t*>(ws + pl.off_status),
+                                            make_key(p->seed), p->problem_id, pl.q * pl.r2,
+                                            p->variant == 1 ? 1 : 0, pi2_out);
+  count_launch(1);
   return cuda_ok(cudaGetLastError(), "launch fct_reduce");
+}
+
+bool launch_fct(const Plan& pl, const void* A, int64_t lda, l1s_dtype dt, const float* b,
+                const l1s_params* p, float* pix, unsigned char* ws, cudaStream_t st, double* pi2_out) {
+  if (!launch_fct_part(pl, A, lda, dt, b, pl.n, p->global_row_offset, p, false, ws, st)) return false;
+  return launch_fct_reduce(pl, p, pix, ws, st, pi2_out);
+}
+
+// Phase 1 on inputs that are still in host memory: the rows arrive in pl.fct_chunks
+// chunks (multiples of the kernel's tile) by copies on `cp`, and the phase-1 launch of
+// chunk k on `st` waits only for its own copy (event evs[k]), so the transfer of chunk
+// k+1 overlaps the transform of chunk k.  Launches after the first add their block
+// partials to the earlier ones (the launches are ordered on `st`), and one reduction
+// forms Π1X.  A_dev and b_dev receive the rows (lda = d) for the later phases.  The
+// caller has made `cp` wait for earlier work on `st` that reads A_dev or b_dev.
+bool launch_fct_streamed(const Plan& pl, const void* A_host, int64_t lda_host, l1s_dtype dt, const float* b_host,
+                         void* A_dev, float* b_dev, const l1s_params* p, float* pix, unsigned char* ws,
+                         cudaStream_t st, cudaStream_t cp, const cudaEvent_t* evs, double* pi2_out) {
+  const int K = std::max(pl.fct_chunks, 1);
+  const int64_t tile = pl.fct_ws ? (int64_t{1} << pl.fct_tile_log2) : pl.s;
+  const int64_t per_chunk = ((pl.n + K - 1) / K + tile - 1) / tile * tile;
+  const size_t esz = dt == L1S_BF16 ? 2 : 4;
+  for (int k = 0; k < K; ++k) {
+    const int64_t r0 = k * per_chunk;
+    if (r0 >= pl.n) break;
+    const int64_t rows = std::min(per_chunk, pl.n - r0);
+    unsigned char* a_dst = static_cast<unsigned char*>(A_dev) + static_cast<size_t>(r0) * pl.d * esz;
+    const unsigned char* a_src = static_cast<const unsigned char*>(A_host) + static_cast<size_t>(r0) * lda_host * esz;
+    if (!cuda_ok(cudaMemcpy2DAsync(a_dst, esz * pl.d, a_src, esz * lda_host, esz * pl.d, rows,
+                                   cudaMemcpyHostToDevice, cp),
+                 "copy A chunk") ||
+        !cuda_ok(cudaMemcpyAsync(b_dev + r0, b_host + r0, sizeof(float) * rows, cudaMemcpyHostToDevice, cp),
+                 "copy b chunk") ||
+        !cuda_ok(cudaEventRecord(evs[k], cp), "record chunk event") ||
+        !cuda_ok(cudaStreamWaitEvent(st, evs[k], 0), "wait for chunk"))
+      return false;
+    if (!launch_fct_part(pl, a_dst, pl.d, dt, b_dev + r0, rows, p->global_row_offset + r0, p, k > 0, ws, st))
+      return false;
+  }
+  return launch_fct_reduce(pl, p, pix, ws, st, pi2_out);
 }
 
 }  // namespace l1s

@@ -233,6 +233,7 @@ struct Plan {
   int fct_lean;             // 1: its one-stage, one-copy form (W = 16)
   int fct_sorted;           // 16 or 32: the bucket-sorted kernel with that column width runs phase 1
   int fct_ctas;             // thread blocks per slice
+  int fct_chunks;           // inputs in host memory: row chunks whose copies overlap phase 1
   size_t fct_smem;
   int lam_ctas, lam_threads;
   int lam_m_in_smem;        // 1: the λ kernel reads M from shared memory instead of the constant bank

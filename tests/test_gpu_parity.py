@@ -351,3 +351,35 @@ def test_regress_end_to_end_host_inputs():
     f_star = solve.objective(X[:, :-1], -X[:, -1], pr["x_star"])
     assert f <= 1.01 * f_star
     assert 0 < rows < 2 * wl.coreset + 64
+
+
+def test_coreset_host_inputs_chunked():
+    """Inputs in host memory at a size where the rows arrive in several chunks whose
+    copies overlap phase 1: the kept set against the oracle's decisions (steps 1-7)."""
+    n, d, r2, m = (1 << 21) + 12345, 8, 16, 3000.0
+    pr = problem(n, d, seed=31)
+    X = host_x(pr)
+    s, r1, seed = 64, r1_for(d), 5
+    prm = L.make_params(s, r1, r2, m, seed=seed)
+    ws = L.workspace(prm, n, d, host_staging=True)
+    A = torch.from_numpy(pr["A"]).pin_memory()
+    b = torch.from_numpy(pr["b"]).pin_memory()
+    cap = int(2 * m) + 64
+    idx = torch.empty(cap, dtype=torch.int64).pin_memory()
+    w = torch.empty(cap, dtype=torch.float64).pin_memory()
+    cnt = torch.zeros(1, dtype=torch.int64)
+    rc = L.l1_coreset_host(A, b, prm, cap, idx, w, cnt, ws)
+    assert rc == 0, rc
+    k = int(cnt.item())
+    pix, _ = fct.fct1_embed(X, s, r1, seed, 0, 0, True)
+    _, rm = condition.qr_positive(pix)
+    M = condition.m_matrix(rm, rng.pi2_matrix(seed, 0, d + 1, r2))
+    lam = leverage.lambda_estimates(X, M)
+    p, _, _ = sampling.probabilities(lam, m)
+    u = rng.sample_uniforms(seed, 0, np.arange(n))
+    amb = ambiguous(u, p, 1e-4)
+    kg = np.zeros(n, bool)
+    kg[idx[:k].numpy()] = True
+    assert np.array_equal(kg[~amb], (u < p)[~amb]), int((kg != (u < p)).sum())
+    got = idx[:k].numpy()
+    assert np.allclose(w[:k].numpy(), 1.0 / p[got], rtol=1e-3)
