@@ -368,14 +368,92 @@ def optimized_variant(L, dev, stream, args, A, b, w, peak: float, plain_ms: floa
                   args.warmup, args.steps)
     kept = int(cnt.item())
     flags = L.l1s_status_read(ws, stream=stream)
-    ab = algorithmic_bytes(n, d, 4, kept)["step"]
+    # λ̂ and the keep decision share one pass: no λ write and read back (8 bytes per row)
+    ab = algorithmic_bytes(n, d, 4, kept)["step"] - 8 * n
     return {"workload": w.name, "variant": "OptimizedFastCauchyRegression (Gaussian Pi2, r2 = 8, no Sum(lambda))",
             "r2": r2, "sample_scale": scale, "value": n / (ms / 1e3), "ms_per_step": ms,
             "step_frac": ab / (ms / 1e3) / 1e9 / peak, "coreset_rows": kept, "status": flags,
             "speedup_vs_f32_plain": plain_ms / ms}
 
 
+def multi_variant(L, dev, stream, args, A, b, w, peak: float) -> dict:
+    """Multiple regression (§4.2.1) on the same design: X = [A | B] with k = 4 right-hand
+    sides (b and three more columns A·w_j + Laplace noise with 5% 100·Cauchy outliers),
+    one coreset for all of them (steps 1-7 on q = d + k columns)."""
+    import numpy as np
+    import torch
+
+    n, d = A.shape
+    k = 4
+    g = np.random.default_rng(w.seed + 77)
+    extra = torch.empty((n, k - 1), dtype=torch.float32)
+    Ah = A.cpu().numpy()
+    for j in range(k - 1):
+        e = g.laplace(size=n)
+        out = g.random(n) < 0.05
+        e[out] = 100.0 * g.standard_cauchy(int(out.sum()))
+        extra[:, j] = torch.from_numpy((Ah.astype(np.float64) @ g.standard_normal(d) + e).astype(np.float32))
+    X = torch.cat([A, b[:, None], extra.to(dev)], dim=1).contiguous()
+    del Ah, extra
+    from synth import r1_for
+
+    prm = L.make_params(w.s, r1_for(d + k), w.r2, w.coreset, seed=w.seed, problem_id=w.problem_id)
+    ws = L.multi_workspace(prm, n, d, k, device=dev)
+    cap = int(2 * w.coreset) + 64
+    idx = torch.empty(cap, dtype=torch.int64, device=dev)
+    wts = torch.empty(cap, dtype=torch.float64, device=dev)
+    cnt = torch.zeros(1, dtype=torch.int64, device=dev)
+    ms = _time_ms(lambda: L.l1_coreset_multi(X, k, prm, cap, idx, wts, None, cnt, ws, stream=stream), stream,
+                  args.warmup, args.steps)
+    kept = int(cnt.item())
+    flags = L.l1s_status_read(ws, stream=stream)
+    # the passes read d + k − 1 columns of X and B_k gathered once (read + write 4 bytes per row)
+    ab = algorithmic_bytes(n, d + k - 1, 4, kept)["step"] + 8 * n
+    return {"workload": f"{w.name} with k = {k} right-hand sides", "k": k, "q": d + k, "r1": prm.r1,
+            "value": n / (ms / 1e3),
+            "ms_per_step": ms, "step_frac": ab / (ms / 1e3) / 1e9 / peak, "coreset_rows": kept,
+            "status": flags}
+
+
 # ----------------------------------------------------------------- GPU arm
+def _parse_cpulist(txt: str) -> set:
+    cpus = set()
+    for part in txt.strip().split(","):
+        if not part:
+            continue
+        lo, _, hi = part.partition("-")
+        cpus.update(range(int(lo), int(hi or lo) + 1))
+    return cpus
+
+
+def bind_near_gpu(dev) -> str:
+    """Run this process on the CPUs local to the GPU (sysfs local_cpulist of its PCI
+    device), so that pinned host buffers are allocated in the memory next to it and the
+    host→device copies of the end-to-end number do not cross the CPU-to-CPU link."""
+    import torch
+
+    try:
+        uuid = str(torch.cuda.get_device_properties(dev).uuid).lower().replace("gpu-", "")
+        out = subprocess.run(["nvidia-smi", "--query-gpu=uuid,pci.bus_id", "--format=csv,noheader"],
+                             capture_output=True, text=True, timeout=30).stdout
+        bus = None
+        for line in out.splitlines():
+            u, _, b = (x.strip() for x in line.partition(","))
+            if u.lower().replace("gpu-", "") == uuid:
+                bus = b.lower()
+        if bus is None:
+            return "unbound: GPU not found in nvidia-smi"
+        dom, rest = bus.split(":", 1)
+        path = f"/sys/bus/pci/devices/{dom[-4:]}:{rest}/local_cpulist"
+        cpus = _parse_cpulist(open(path).read()) & os.sched_getaffinity(0)
+        if not cpus:
+            return "unbound: no local CPUs available"
+        os.sched_setaffinity(0, cpus)
+        return f"{len(cpus)} CPUs local to the GPU"
+    except Exception as e:  # noqa: BLE001 - diagnostics only
+        return f"unbound: {type(e).__name__}"
+
+
 def run_gpu(args) -> None:
     import numpy as np
     import torch
@@ -388,6 +466,7 @@ def run_gpu(args) -> None:
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    host_binding = bind_near_gpu(dev)
 
     import __graft_entry__
 
@@ -523,14 +602,17 @@ def run_gpu(args) -> None:
                           "algorithmic_bytes": ab["step"]},
         "phase_ms": dict(zip(names, phase_ms)),
         "e2e": {"value": world * n / e2e_s, "unit": UNIT, "h2d_bytes_per_step": n * (d * elem + 4),
-                "d2h_bytes_per_step": 8 + cap * 16, "status": rc},
+                "d2h_bytes_per_step": 8 + cap * 16, "status": rc, "host": host_binding},
         "gpu_launches": launches,
         "clocks": clk.summary(),
         "coreset_rows": kept, "status_flags": flags, "host_wall_s": t_host,
     }
     if rank == 0 and not args.no_variants and world == 1:
         line_opt = optimized_variant(L, dev, stream, args, A, b, w, peaks["hbm_gbs"], ms_per_step)
-        del ws, A, b
+        del ws
+        torch.cuda.empty_cache()
+        line_multi = multi_variant(L, dev, stream, args, A, b, w, peaks["hbm_gbs"])
+        del A, b
         torch.cuda.empty_cache()
         line["variants"] = {"bf16": bf16_variant(L, dev, stream, args, peaks["hbm_gbs"])}
         torch.cuda.empty_cache()
@@ -538,6 +620,7 @@ def run_gpu(args) -> None:
         line["variants"]["f32_plain"] = {"workload": w.name, "value": value, "ms_per_step": ms_per_step,
                                          "step_frac": step_gbs / peaks["hbm_gbs"]}
         line["variants"]["optimized"] = line_opt
+        line["variants"]["multi"] = line_multi
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_oracle_rows_per_s(pr, w, args.cpu_seconds)
     if rank == 0:

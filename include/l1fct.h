@@ -234,6 +234,36 @@ L1S_API int l1_regress(const void* A, int64_t lda, l1s_dtype dtype, const float*
                double* x_host, double* objective_host, int64_t* coreset_rows_host,
                void* ws, size_t ws_bytes, void* stream);
 
+/* Multiple ℓ1 regression (§4.2.1): min_W ‖A·W − B‖₁ with A ∈ R^{n×d} and B ∈ R^{n×k},
+ * FastCauchyRegression(A, B): the steps of Figure 2 on X = [A, −B] (q = d + k columns)
+ * give one coreset for all k right-hand sides.  X_dev holds [A | B] row by row (n rows
+ * of d + k values, leading dimension ldx ≥ d + k, FP32 or BF16 storage; device memory,
+ * caller-owned).  d ≥ 1, k ≥ 1, d + k − 1 ≤ 128; the other limits are those of
+ * l1s_workspace_size with d + k − 1 columns.  The workspace is sized by
+ * l1s_multi_workspace_size. */
+L1S_API int l1s_multi_workspace_size(const l1s_params* params, int64_t n, int32_t d, int32_t k,
+                                     l1s_dtype dtype, size_t* bytes);
+
+/* Steps 1-7 on X = [A, −B]: writes the kept row indices (ascending), weights 1/p̂ and,
+ * when coreset_dev is not NULL, the kept rows of X (FP64, d + k values per row: A_i then
+ * −B_i) for up to `capacity` rows, and *count_dev (all kept rows; L1S_ERR_CAPACITY is
+ * raised in the status word when it exceeds capacity).  Asynchronous on `stream`. */
+L1S_API int l1_coreset_multi(const void* X_dev, int64_t ldx, l1s_dtype dtype, int64_t n, int32_t d,
+                             int32_t k, const l1s_params* params, int64_t capacity, int64_t* idx_dev,
+                             double* w_dev, double* coreset_dev, int64_t* count_dev,
+                             void* ws, size_t ws_bytes, void* stream);
+
+/* FastCauchyRegression(A, B) end to end: l1_coreset_multi with a capacity of
+ * 2·m_s + 64 rows, then for each right-hand side j the weighted ℓ1 problem
+ * min_w Σ_i w_i·|A_i·w − B_ij| on the coreset (as l1_solve, max_iter IRLS steps) and
+ * its objective ‖A·w_j − B_j‖₁ over all n rows.  Synchronises `stream`; writes W_host
+ * (d × k row-major FP64: column j solves right-hand side j), objectives_host (k FP64)
+ * and *coreset_rows_host (may be NULL); returns the first device-side error code. */
+L1S_API int l1_regress_multi(const void* X_dev, int64_t ldx, l1s_dtype dtype, int64_t n, int32_t d,
+                             int32_t k, const l1s_params* params, int32_t max_iter, double* W_host,
+                             double* objectives_host, int64_t* coreset_rows_host,
+                             void* ws, size_t ws_bytes, void* stream);
+
 /* Debug: the Philox draws of global rows [row_start, row_start + count) as the
  * kernels use them (device outputs, any may be NULL): bucket_h/bucket_i in
  * [0, r1), k_h/k_i the 24-bit integers of the Cauchy scales, cauchy_h/cauchy_i

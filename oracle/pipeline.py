@@ -22,17 +22,22 @@ def form_x(A: np.ndarray, b: np.ndarray) -> np.ndarray:
     return np.concatenate([A, -np.asarray(b, dtype=np.float64)[:, None]], axis=1)
 
 
-def fast_cauchy_regression(A, b, s: int, r1: int, r2: int, coreset: float,
-                           seed: int = 0, problem_id: int = 0, sign_flip: bool = True,
-                           solve_lp: bool = True, timings: dict | None = None,
-                           variant: int = 0, sample_scale: float = 0.0) -> dict:
-    """All intermediates of Figure 2 for one problem (rows are numbered from 0).
+def form_x_multi(A: np.ndarray, B: np.ndarray) -> np.ndarray:
+    """X = [A, −B] ∈ R^{n×(d+k)} in FP64 (§4.2.1, multiple ℓ1 regression: Z = [W; I_k])."""
+    A = np.asarray(A, dtype=np.float64)
+    B = np.asarray(B, dtype=np.float64)
+    if B.ndim == 1:
+        B = B[:, None]
+    return np.concatenate([A, -B], axis=1)
 
-    variant 1 is OptimizedFastCauchyRegression (Figure "mainOpt"): Π2 Gaussian and
-    p̂ = min{1, sample_scale·λ̂} without the Σλ normalisation."""
+
+def coreset_of_x(X: np.ndarray, s: int, r1: int, r2: int, coreset: float, seed: int = 0,
+                 problem_id: int = 0, sign_flip: bool = True, variant: int = 0,
+                 sample_scale: float = 0.0, timings: dict | None = None) -> dict:
+    """Figure 2 steps 2-7 on a given X (any number of columns q): Π1X, its QR, M = R⁻¹Π2,
+    λ, p̂ and the Bernoulli coreset, with every intermediate."""
     t = {} if timings is None else timings
     t0 = time.perf_counter()
-    X = form_x(A, b)                                                          # step 1
     n, q = X.shape
     pix, tsum = fct.fct1_embed(X, s, r1, seed, problem_id, 0, sign_flip)     # step 2, Π1X
     t1 = time.perf_counter()
@@ -51,15 +56,56 @@ def fast_cauchy_regression(A, b, s: int, r1: int, r2: int, coreset: float,
     u = rng.sample_uniforms(seed, problem_id, np.arange(n))
     idx, wts = sampling.bernoulli_sample(p_hat, u)                            # step 7
     t4 = time.perf_counter()
-    out = {"X": X, "PiX": pix, "T": tsum, "R": r_mat, "Pi2": pi2, "M": m_mat,
-           "lam": lam, "lam_total": total, "tau": tau, "p": p_hat, "u": u,
-           "idx": idx, "w": wts}
+    t.update({"fct": t1 - t0, "condition": t2 - t1, "lambda": t3 - t2, "sample": t4 - t3})
+    return {"X": X, "PiX": pix, "T": tsum, "R": r_mat, "Pi2": pi2, "M": m_mat,
+            "lam": lam, "lam_total": total, "tau": tau, "p": p_hat, "u": u,
+            "idx": idx, "w": wts}
+
+
+def fast_cauchy_regression(A, b, s: int, r1: int, r2: int, coreset: float,
+                           seed: int = 0, problem_id: int = 0, sign_flip: bool = True,
+                           solve_lp: bool = True, timings: dict | None = None,
+                           variant: int = 0, sample_scale: float = 0.0) -> dict:
+    """All intermediates of Figure 2 for one problem (rows are numbered from 0).
+
+    variant 1 is OptimizedFastCauchyRegression (Figure "mainOpt"): Π2 Gaussian and
+    p̂ = min{1, sample_scale·λ̂} without the Σλ normalisation."""
+    t = {} if timings is None else timings
+    X = form_x(A, b)                                                          # step 1
+    out = coreset_of_x(X, s, r1, r2, coreset, seed, problem_id, sign_flip, variant, sample_scale, t)
+    t4 = time.perf_counter()
     if solve_lp:                                                              # step 8
+        idx, wts = out["idx"], out["w"]
         xs, fs = solve.lad_lp(X[idx, :-1], -X[idx, -1], wts)
         out["x_hat"] = xs
         out["coreset_objective"] = fs
         out["objective"] = solve.objective(X[:, :-1], -X[:, -1], xs)
-    t5 = time.perf_counter()
-    t.update({"fct": t1 - t0, "condition": t2 - t1, "lambda": t3 - t2,
-              "sample": t4 - t3, "solve": t5 - t4})
+    t["solve"] = time.perf_counter() - t4
+    return out
+
+
+def fast_cauchy_multiple_regression(A, B, s: int, r1: int, r2: int, coreset: float,
+                                    seed: int = 0, problem_id: int = 0, sign_flip: bool = True,
+                                    solve_lp: bool = True, variant: int = 0,
+                                    sample_scale: float = 0.0) -> dict:
+    """FastCauchyRegression(A, B) of §4.2.1: the same steps on X = [A, −B] (q = d + k
+    columns), one coreset for all k right-hand sides, then k weighted ℓ1 problems
+    min_w Σ_i w_i |A_i·w − B_ij| on it.  W is d × k (column j solves right-hand side j)."""
+    A = np.asarray(A, dtype=np.float64)
+    d = A.shape[1]
+    X = form_x_multi(A, B)
+    k = X.shape[1] - d
+    out = coreset_of_x(X, s, r1, r2, coreset, seed, problem_id, sign_flip, variant, sample_scale)
+    if solve_lp:
+        idx, wts = out["idx"], out["w"]
+        W = np.zeros((d, k))
+        fc = np.zeros(k)
+        f = np.zeros(k)
+        for j in range(k):
+            bj = -X[:, d + j]
+            W[:, j], fc[j] = solve.lad_lp(X[idx, :d], bj[idx], wts)
+            f[j] = solve.objective(X[:, :d], bj, W[:, j])
+        out["W"] = W
+        out["coreset_objectives"] = fc
+        out["objectives"] = f
     return out

@@ -40,6 +40,12 @@ bool launch_lambda(const Plan& pl, const void* A, int64_t lda, l1s_dtype dt, con
                    const float* m32, const l1s_params* p, float* lam, double* user_sum,
                    unsigned char* ws, cudaStream_t st, int* nsums_out = nullptr);
 bool launch_m_to_f32(const double* m, int total, float* out, cudaStream_t st);
+bool lambda_mark_applies(const Plan& pl, l1s_dtype dt, const l1s_params* p);
+bool launch_lambda_mark(const Plan& pl, const void* A, int64_t lda, const float* b, const float* m32,
+                        const l1s_params* p, float* lam_out, unsigned char* ws, cudaStream_t st);
+bool launch_compact(const Plan& pl, const float* lam, const float* m32, const void* A, int64_t lda, l1s_dtype dt,
+                    const float* b, int64_t capacity, int64_t* idx, double* w, double* coreset, int64_t* count_out,
+                    unsigned char* ws, cudaStream_t st);
 int sample_threads();
 bool launch_sample(const Plan& pl, const float* lam, const double* p, const l1s_params* prm,
                    const void* A, int64_t lda, l1s_dtype dt, const float* b, int64_t capacity,
@@ -144,6 +150,17 @@ int sample_impl(const Plan& pl, const void* A, int64_t lda, l1s_dtype dtype, con
                        const float* m32, const l1s_params* params, int64_t capacity, int64_t* idx,
                        double* wts, double* coreset, int64_t* count, float* lambda, unsigned char* w,
                        cudaStream_t st) {
+  // OptimizedFastCauchyRegression needs no Σλ: λ̂ and the keep mask come from one pass,
+  // and the compaction recomputes λ̂ of the kept rows unless the caller wants every λ̂.
+  if (lambda_mark_applies(pl, dtype, params)) {
+    Plan pf = pl;
+    pf.smp_chunk = pl.lm_chunk;
+    pf.smp_ctas = pl.lm_ctas;
+    if (!launch_lambda_mark(pf, A, lda, b, m32, params, lambda, w, st) ||
+        !launch_compact(pf, lambda, m32, A, lda, dtype, b, capacity, idx, wts, coreset, count, w, st))
+      return L1S_ERR_CUDA;
+    return L1S_OK;
+  }
   float* lam = lambda ? lambda : reinterpret_cast<float*>(w + pl.off_lam);
   // Σλ and τ are formed at the start of the sampling kernel; OptimizedFastCauchyRegression
   // (variant 1) needs no Σλ at all.
@@ -333,7 +350,12 @@ bool make_plan(const l1s_params* p, int64_t n, int d, l1s_dtype dt, bool host_st
   const int smp_per_sm = sch.smp_chunks_per_sm > 0 ? std::min(sch.smp_chunks_per_sm, kMaxSmpPerSm) : 4;
   P.smp_chunk = chunk_for(smp_per_sm);
   P.smp_ctas = static_cast<int>((n + P.smp_chunk - 1) / P.smp_chunk);
-  const int64_t smp_ctas_max = (n + chunk_for(kMaxSmpPerSm) - 1) / chunk_for(kMaxSmpPerSm);
+  // The fused λ-and-mark pass (OptimizedFastCauchyRegression) is a λ pass: its chunks
+  // follow the λ residency.
+  P.lm_chunk = chunk_for(lam_per_sm);
+  P.lm_ctas = static_cast<int>((n + P.lm_chunk - 1) / P.lm_chunk);
+  const int max_per_sm = std::max(kMaxSmpPerSm, kMaxLamPerSm);
+  const int64_t smp_ctas_max = (n + chunk_for(max_per_sm) - 1) / chunk_for(max_per_sm);
   P.irls_ctas = di.sms;
 
   const int64_t cap = coreset_capacity_of(p);

@@ -1069,10 +1069,16 @@ __global__ void __launch_bounds__(SrtCfg<W>::kThreads) fct_embed_sorted_kernel(c
 __global__ void __launch_bounds__(1024) fct_reduce_kernel(const float* __restrict__ partials, int ctas,
                                                           int r1, int W, int q, float* __restrict__ pix,
                                                           uint32_t* flags, Key2 key, uint32_t problem,
-                                                          int npi2, int pi2_gauss, double* __restrict__ pi2) {
+                                                          int npi2, int r2, int pi2_gauss, int neg_lo, int neg_hi,
+                                                          double* __restrict__ pi2) {
+  // Π2 rows [neg_lo, neg_hi) are stored negated: they pair with columns of X that the
+  // passes read with the opposite sign (multiple regression), so that X·M is unchanged.
   if (pi2 && blockIdx.y == 0)
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < npi2; e += gridDim.x * blockDim.x)
-      pi2[e] = pi2_value(key, problem, e, pi2_gauss);
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < npi2; e += gridDim.x * blockDim.x) {
+      const double v = pi2_value(key, problem, e, pi2_gauss);
+      const int row = e / r2;
+      pi2[e] = (row >= neg_lo && row < neg_hi) ? -v : v;
+    }
   __shared__ float red[32][33];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int per = r1 * W;
@@ -1303,8 +1309,8 @@ static bool launch_fct_reduce(const Plan& pl, const l1s_params* p, float* pix, u
   dim3 rgrid((per + 31) / 32, pl.fct_slices);
   fct_reduce_kernel<<<rgrid, 1024, 0, st>>>(reinterpret_cast<float*>(ws + pl.off_partials), pl.fct_ctas, pl.r1,
                                             pl.fct_width, pl.q, pix, reinterpret_cast<uint32_t*>(ws + pl.off_status),
-                                            make_key(p->seed), p->problem_id, pl.q * pl.r2,
-                                            p->variant == 1 ? 1 : 0, pi2_out);
+                                            make_key(p->seed), p->problem_id, pl.q * pl.r2, pl.r2,
+                                            p->variant == 1 ? 1 : 0, pl.pi2_neg_lo, pl.pi2_neg_hi, pi2_out);
   count_launch(1);
   return cuda_ok(cudaGetLastError(), "launch fct_reduce");
 }

@@ -239,6 +239,9 @@ struct Plan {
   int lam_m_in_smem;        // 1: the λ kernel reads M from shared memory instead of the constant bank
   int smp_ctas, smp_threads;
   int64_t smp_chunk;        // rows per sampling block (multiple of 64)
+  int pi2_neg_lo, pi2_neg_hi;  // multiple regression: Π2 rows stored negated (columns read as +B)
+  int lm_ctas;              // the fused λ-and-mark pass: blocks and rows per block (λ residency)
+  int64_t lm_chunk;
   int irls_ctas;
   // workspace offsets (bytes)
   size_t off_status, off_partials, off_pix, off_qr, off_r, off_m64, off_m32, off_pi2,
@@ -298,6 +301,31 @@ __device__ __forceinline__ bool tau_of(double tot, double coreset, double* tau, 
   *tau = coreset / tot;
   *tau32 = *tau > static_cast<double>(FLT_MAX) ? FLT_MAX : static_cast<float>(*tau);
   return true;
+}
+
+// Keep mask bits: lane t's even row goes to bit 2t, its odd row to bit 2t+1.
+__device__ __forceinline__ uint64_t spread_bits(uint32_t x) {
+  uint64_t v = x;
+  v = (v | (v << 16)) & 0x0000FFFF0000FFFFull;
+  v = (v | (v << 8)) & 0x00FF00FF00FF00FFull;
+  v = (v | (v << 4)) & 0x0F0F0F0F0F0F0F0Full;
+  v = (v | (v << 2)) & 0x3333333333333333ull;
+  v = (v | (v << 1)) & 0x5555555555555555ull;
+  return v;
+}
+
+// p̂ = min(1, τ·λ) in FP64 (the exact definition both sides evaluate).
+__device__ __forceinline__ double p_hat(double tau, float lam) { return fmin(1.0, tau * static_cast<double>(lam)); }
+
+// Keep decision for one row: exact result of (U·2^-53 < min(1, τ·λ)).
+__device__ __forceinline__ bool keep_row(float lam, float tau32, double tau, uint32_t wa, uint32_t wb) {
+  const float p32 = lam > 0.f ? fminf(1.f, tau32 * lam) : 0.f;
+  const float u_lo = static_cast<float>(wa >> 8) * 0x1p-24f;   // u ∈ [u_lo, u_lo + 2^-24)
+  const float u_hi = u_lo + 0x1p-24f;
+  if (u_hi < p32 * (1.f - 0x1p-20f)) return true;
+  if (u_lo > p32 * (1.f + 0x1p-20f)) return false;
+  const double u = static_cast<double>(u53_of(wa, wb)) * 0x1p-53;
+  return u < p_hat(tau, lam);
 }
 
 // Adds k to the process-wide count of kernels the library has launched.

@@ -250,6 +250,110 @@ __global__ void __launch_bounds__(kLamThreads) lambda_kernel_generic(const TA* _
   if (threadIdx.x == 0) block_sums[blockIdx.x] = tot;
 }
 
+// OptimizedFastCauchyRegression (p̂_i = min{1, s·λ̂_i}, no Σλ): λ̂ and the Bernoulli keep
+// decision in one pass, so λ̂ never leaves registers (it is written only when the caller
+// asked for it).  Blocks own contiguous chunks of rows (multiples of 64) as in the
+// separate sampling pass, and produce the same keep mask and per-block counts for the
+// ordered compaction.  A warp handles 64 consecutive rows per step: lane l computes λ̂
+// of rows base+l and base+32+l (coalesced row loads, next step's rows in flight), then
+// the uniforms move by shuffles from the lane that drew them (one Philox call per row pair).
+struct LamMarkArgs {
+  const void* A;
+  int64_t lda;
+  const float* b;
+  int64_t n;
+  int64_t chunk;           // rows per block, multiple of 64
+  const float* mg;         // M (FP32, q × r2) in global memory (SMEM_M)
+  float* lam_out;          // optional λ̂ output
+  Key2 key;
+  uint32_t problem;
+  int64_t row_offset;
+  double tau;              // s of the figure (sample_scale)
+  uint64_t* mask;
+  int64_t* counts;
+  StatusBlock* status;
+};
+
+template <int D, typename TA, bool VEC>
+__device__ __forceinline__ void load_x(const LamMarkArgs& a, int64_t row, int64_t stop, float (&x)[D + 1]) {
+  if (row < stop) {
+    load_row<D, TA, VEC>(static_cast<const TA*>(a.A) + row * a.lda, x);
+    x[D] = -__ldg(a.b + row);
+  } else {
+#pragma unroll
+    for (int k = 0; k <= D; ++k) x[k] = 0.f;
+  }
+}
+
+template <int D, int R2, typename TA, bool VEC, bool SMEM_M>
+__global__ void __launch_bounds__(kLamThreads) lambda_mark_kernel(const LamMarkArgs a) {
+  constexpr int Q = D + 1;
+  __shared__ float sM[SMEM_M ? Q * R2 : 1];
+  __shared__ int64_t wcount[kLamThreads / 32];
+  if constexpr (SMEM_M) {
+    for (int e = threadIdx.x; e < Q * R2; e += blockDim.x) sM[e] = a.mg[e];
+    __syncthreads();
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int64_t start = static_cast<int64_t>(blockIdx.x) * a.chunk;
+  const int64_t stop = min(a.n, start + a.chunk);
+  const double tau = a.tau;
+  const float tau32 = tau > static_cast<double>(FLT_MAX) ? FLT_MAX : static_cast<float>(tau);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    a.status->tau = tau;
+    a.status->tau32 = tau32;
+  }
+  const int64_t stride = 64 * static_cast<int64_t>(nwarps);
+  int64_t kept = 0;
+  int64_t base = start + 64 * warp;
+  float nx[Q];
+  if (base < stop) load_x<D, TA, VEC>(a, base + lane, stop, nx);
+  for (; base < stop; base += stride) {           // uniform across the warp
+    // Row base + j (j < 64) takes its uniforms from Philox call ⌊(g + j)/2⌋, g the global
+    // id of row base, word pair (g + j) mod 2; lane l draws call ⌊g/2⌋ + l, and call
+    // ⌊g/2⌋ + 32 is needed too when g is odd.
+    const uint64_t g = static_cast<uint64_t>(a.row_offset + base);
+    const int off0 = static_cast<int>(g & 1);
+    const uint4 o = draw_row(a.key, (g >> 1) + lane, a.problem, kStreamSample);
+    uint4 o32 = make_uint4(0u, 0u, 0u, 0u);
+    if (off0) o32 = draw_row(a.key, (g >> 1) + 32, a.problem, kStreamSample);
+    uint32_t bal0 = 0, bal1 = 0;
+#pragma unroll 1
+    for (int t = 0; t < 2; ++t) {
+      float x[Q];
+#pragma unroll
+      for (int k = 0; k < Q; ++k) x[k] = nx[k];
+      const int64_t row = base + 32 * t + lane;
+      load_x<D, TA, VEC>(a, t == 0 ? row + 32 : base + stride + lane, stop, nx);   // next row in flight
+      const float lam = lambda_of_row<Q, R2, SMEM_M>(x, sM);
+      if (a.lam_out && row < stop) a.lam_out[row] = lam;
+      const int j = 32 * t + lane;
+      const int src = ((off0 + j) >> 1) & 31;
+      const bool hi = ((off0 + j) & 1) != 0;
+      const uint32_t sx = __shfl_sync(0xffffffffu, o.x, src), sy = __shfl_sync(0xffffffffu, o.y, src);
+      const uint32_t sz = __shfl_sync(0xffffffffu, o.z, src), sw = __shfl_sync(0xffffffffu, o.w, src);
+      uint32_t wa = hi ? sz : sx, wb = hi ? sw : sy;
+      if (off0 + j == 64) {
+        wa = o32.x;
+        wb = o32.y;
+      }
+      const uint32_t bt = __ballot_sync(0xffffffffu, row < stop && keep_row(lam, tau32, tau, wa, wb));
+      if (t == 0) bal0 = bt;
+      else bal1 = bt;
+    }
+    const uint64_t m = static_cast<uint64_t>(bal0) | (static_cast<uint64_t>(bal1) << 32);
+    if (lane == 0) a.mask[base >> 6] = m;
+    kept += __popcll(m);
+  }
+  if (lane == 0) wcount[warp] = kept;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int64_t t = 0;
+    for (int w = 0; w < nwarps; ++w) t += wcount[w];
+    a.counts[blockIdx.x] = t;
+  }
+}
+
 // Σλ over the block partials in a fixed order (strided per-thread sums, then a
 // fixed shuffle tree and the warp sums in order); τ = m_s / Σλ.
 __global__ void __launch_bounds__(256) lambda_finalize_kernel(const double* __restrict__ block_sums, int nblocks,
@@ -367,6 +471,67 @@ bool launch_lambda(const Plan& pl, const void* A, int64_t lda, l1s_dtype dt, con
                                            reinterpret_cast<StatusBlock*>(ws + pl.off_status), user_sum);
   count_launch(1);
   return cuda_ok(cudaGetLastError(), "launch lambda_finalize");
+}
+
+template <int DD, int RR, typename TA, bool SM>
+static void launch_lambda_mark_case(int grid, cudaStream_t st, bool aligned, const LamMarkArgs& a) {
+  if constexpr ((DD * sizeof(TA)) % 16 == 0) {
+    if (aligned) {
+      lambda_mark_kernel<DD, RR, TA, true, SM><<<grid, kLamThreads, 0, st>>>(a);
+      return;
+    }
+  }
+  lambda_mark_kernel<DD, RR, TA, false, SM><<<grid, kLamThreads, 0, st>>>(a);
+}
+
+bool lambda_mark_applies(const Plan& pl, l1s_dtype dt, const l1s_params* p) {
+  if (p->variant != 1 || dt != L1S_F32 || (pl.r2 != 8 && pl.r2 != 16)) return false;
+  return pl.d == 4 || pl.d == 8 || pl.d == 16 || pl.d == 32;
+}
+
+// λ̂ and the keep mask of OptimizedFastCauchyRegression in one launch over pl.smp_ctas
+// chunks of pl.smp_chunk rows (the compaction kernel then gathers the kept rows).
+bool launch_lambda_mark(const Plan& pl, const void* A, int64_t lda, const float* b, const float* m32,
+                        const l1s_params* p, float* lam_out, unsigned char* ws, cudaStream_t st) {
+  const bool smem_m = pl.lam_m_in_smem != 0;
+  if (!smem_m && !cuda_ok(cudaMemcpyToSymbolAsync(c_M, m32, sizeof(float) * pl.q * pl.r2, 0,
+                                                  cudaMemcpyDeviceToDevice, st),
+                          "copy M to constant memory"))
+    return false;
+  LamMarkArgs a;
+  a.A = A;
+  a.lda = lda;
+  a.b = b;
+  a.n = pl.n;
+  a.chunk = pl.smp_chunk;
+  a.mg = m32;
+  a.lam_out = lam_out;
+  a.key = make_key(p->seed);
+  a.problem = p->problem_id;
+  a.row_offset = p->global_row_offset;
+  a.tau = p->sample_scale;
+  a.mask = reinterpret_cast<uint64_t*>(ws + pl.off_mask);
+  a.counts = reinterpret_cast<int64_t*>(ws + pl.off_counts);
+  a.status = reinterpret_cast<StatusBlock*>(ws + pl.off_status);
+  const bool aligned = (reinterpret_cast<uintptr_t>(A) % 16 == 0) && ((lda * 4) % 16 == 0);
+  const int grid = pl.smp_ctas;
+#define L1S_LM_CASE(DD, RR)                                                                        \
+  if (pl.d == DD && pl.r2 == RR) {                                                                 \
+    if (smem_m) launch_lambda_mark_case<DD, RR, float, true>(grid, st, aligned, a);                \
+    else launch_lambda_mark_case<DD, RR, float, false>(grid, st, aligned, a);                      \
+    count_launch(1);                                                                               \
+    return cuda_ok(cudaGetLastError(), "launch lambda_mark");                                      \
+  }
+  L1S_LM_CASE(4, 8)
+  L1S_LM_CASE(8, 8)
+  L1S_LM_CASE(16, 8)
+  L1S_LM_CASE(32, 8)
+  L1S_LM_CASE(4, 16)
+  L1S_LM_CASE(8, 16)
+  L1S_LM_CASE(16, 16)
+  L1S_LM_CASE(32, 16)
+#undef L1S_LM_CASE
+  return set_error("lambda_mark: no kernel for d = %d, r2 = %d", pl.d, pl.r2), false;
 }
 
 bool launch_m_to_f32(const double* m, int total, float* out, cudaStream_t st) {

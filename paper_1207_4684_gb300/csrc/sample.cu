@@ -19,30 +19,6 @@ namespace l1s {
 constexpr int kSmpThreads = 256;
 static_assert(kSmpThreads == 256, "lambda_total_256 assumes blocks of 256 threads");
 
-__device__ __forceinline__ uint64_t spread_bits(uint32_t x) {
-  uint64_t v = x;
-  v = (v | (v << 16)) & 0x0000FFFF0000FFFFull;
-  v = (v | (v << 8)) & 0x00FF00FF00FF00FFull;
-  v = (v | (v << 4)) & 0x0F0F0F0F0F0F0F0Full;
-  v = (v | (v << 2)) & 0x3333333333333333ull;
-  v = (v | (v << 1)) & 0x5555555555555555ull;
-  return v;
-}
-
-// p̂ = min(1, τ·λ) in FP64 (the exact definition both sides evaluate).
-__device__ __forceinline__ double p_hat(double tau, float lam) { return fmin(1.0, tau * static_cast<double>(lam)); }
-
-// Keep decision for one row: exact result of (U·2^-53 < min(1, τ·λ)).
-__device__ __forceinline__ bool keep_row(float lam, float tau32, double tau, uint32_t wa, uint32_t wb) {
-  const float p32 = lam > 0.f ? fminf(1.f, tau32 * lam) : 0.f;
-  const float u_lo = static_cast<float>(wa >> 8) * 0x1p-24f;   // u ∈ [u_lo, u_lo + 2^-24)
-  const float u_hi = u_lo + 0x1p-24f;
-  if (u_hi < p32 * (1.f - 0x1p-20f)) return true;
-  if (u_lo > p32 * (1.f + 0x1p-20f)) return false;
-  const double u = static_cast<double>(u53_of(wa, wb)) * 0x1p-53;
-  return u < p_hat(tau, lam);
-}
-
 struct MarkArgs {
   const float* lam;      // λ (mode 0) — or nullptr
   const double* p;       // caller's p̂ (mode 1) — or nullptr
@@ -169,12 +145,15 @@ struct CompactArgs {
   const int64_t* counts;
   int nblocks;
   int64_t n, chunk, capacity;
-  const float* lam;           // for weights (may be null when w is null)
+  const float* lam;           // λ for the weights; null: recomputed from the kept row and M
+  const float* m32;           // M (FP32, q × r2) when lam is null
+  int r2;
   const StatusBlock* status;
   const TA* A;
   int64_t lda;
   const float* b;
   int d;
+  int neg_lo, neg_hi;         // coreset columns written negated (multiple regression: X = [A, −B])
   int64_t* idx;
   double* w;                  // may be null
   double* coreset;            // may be null
@@ -182,11 +161,53 @@ struct CompactArgs {
   StatusBlock* status_rw;
 };
 
-template <typename TA>
+// λ of one row with the operation order of the λ kernels (x_0·M_0j, then FMAs over k in
+// order, |·|, the ((r2−1)/2)-th order statistic), so the value is bit-identical to the one
+// the keep decision used.  R2C = r2 (8 or 16) at compile time, M in shared memory.
+template <typename TA, int R2C>
+__device__ __forceinline__ float lambda_recompute(const CompactArgs<TA>& a, const float* __restrict__ sM,
+                                                  int64_t row) {
+  float acc[R2C];
+  const TA* src = a.A + row * a.lda;
+  const int q = a.d + 1;
+  {
+    const float x0 = load_elem<TA>(src);
+#pragma unroll
+    for (int j = 0; j < R2C; ++j) acc[j] = x0 * sM[j];
+  }
+  for (int k = 1; k < q; ++k) {
+    const float xk = k < a.d ? load_elem<TA>(src + k) : -a.b[row];
+#pragma unroll
+    for (int j = 0; j < R2C; ++j) acc[j] = fmaf(xk, sM[k * R2C + j], acc[j]);
+  }
+#pragma unroll
+  for (int j = 0; j < R2C; ++j) acc[j] = fabsf(acc[j]);
+  constexpr int mid = (R2C - 1) / 2;
+  float med = acc[0];
+#pragma unroll
+  for (int i = 0; i < R2C; ++i) {
+    int lt = 0, le = 0;
+#pragma unroll
+    for (int j = 0; j < R2C; ++j) {
+      lt += acc[j] < acc[i];
+      le += acc[j] <= acc[i];
+    }
+    if (lt <= mid && mid < le) med = acc[i];
+  }
+  return med;
+}
+
+// Maximum q of the λ recomputation (the fused λ-and-mark pass serves d ≤ 32).
+constexpr int kRecomputeMaxQ = 33;
+
+template <typename TA, int R2C>
 __global__ void __launch_bounds__(kSmpThreads) sample_compact_kernel(const CompactArgs<TA> a) {
   constexpr int kWarps = kSmpThreads / 32;
   __shared__ int64_t s_warp[kWarps];
   __shared__ int64_t s_base;
+  __shared__ float sM[R2C > 0 ? kRecomputeMaxQ * R2C : 1];
+  if constexpr (R2C > 0)
+    for (int e = threadIdx.x; e < (a.d + 1) * R2C; e += blockDim.x) sM[e] = a.m32[e];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   // Offset of this block: Σ counts of the blocks before it (per-thread sums, then warp
   // shuffles and the warp totals in a fixed order).
@@ -243,11 +264,19 @@ __global__ void __launch_bounds__(kSmpThreads) sample_compact_kernel(const Compa
       const int64_t row = (wi << 6) + bit;
       if (pos < a.capacity) {
         a.idx[pos] = row;
-        if (a.w) a.w[pos] = 1.0 / p_hat(tau, a.lam[row]);
+        if (a.w) {
+          float lam;
+          if constexpr (R2C > 0) lam = lambda_recompute<TA, R2C>(a, sM, row);
+          else lam = a.lam[row];
+          a.w[pos] = 1.0 / p_hat(tau, lam);
+        }
         if (a.coreset) {
           double* out = a.coreset + pos * q;
           const TA* src = a.A + row * a.lda;
-          for (int k = 0; k < a.d; ++k) out[k] = static_cast<double>(load_elem<TA>(src + k));
+          for (int k = 0; k < a.d; ++k) {
+            const double v = static_cast<double>(load_elem<TA>(src + k));
+            out[k] = (k >= a.neg_lo && k < a.neg_hi) ? -v : v;
+          }
           out[a.d] = -static_cast<double>(a.b[row]);
         }
       }
@@ -258,6 +287,10 @@ __global__ void __launch_bounds__(kSmpThreads) sample_compact_kernel(const Compa
 }
 
 int sample_threads() { return kSmpThreads; }
+
+bool launch_compact(const Plan& pl, const float* lam, const float* m32, const void* A, int64_t lda, l1s_dtype dt,
+                    const float* b, int64_t capacity, int64_t* idx, double* w, double* coreset, int64_t* count_out,
+                    unsigned char* ws, cudaStream_t st);
 
 bool launch_sample(const Plan& pl, const float* lam, const double* p, const l1s_params* prm,
                    const void* A, int64_t lda, l1s_dtype dt, const float* b, int64_t capacity,
@@ -283,15 +316,34 @@ bool launch_sample(const Plan& pl, const float* lam, const double* p, const l1s_
   sample_mark_kernel<<<pl.smp_ctas, pl.smp_threads, 0, st>>>(m);
   count_launch(1);
   if (!cuda_ok(cudaGetLastError(), "launch sample_mark")) return false;
+  return launch_compact(pl, lam, nullptr, A, lda, dt, b, capacity, idx, w, coreset, count_out, ws, st);
+}
+
+// Ordered compaction of the keep mask (weights from λ, or from λ recomputed with M).
+bool launch_compact(const Plan& pl, const float* lam, const float* m32, const void* A, int64_t lda, l1s_dtype dt,
+                    const float* b, int64_t capacity, int64_t* idx, double* w, double* coreset, int64_t* count_out,
+                    unsigned char* ws, cudaStream_t st) {
+  const uint64_t* mask = reinterpret_cast<const uint64_t*>(ws + pl.off_mask);
+  const int64_t* counts = reinterpret_cast<const int64_t*>(ws + pl.off_counts);
   StatusBlock* sb = reinterpret_cast<StatusBlock*>(ws + pl.off_status);
+  // Weights without λ: λ recomputed from M (r2 ∈ {8, 16} and q ≤ kRecomputeMaxQ only).
+  const int r2c = (lam || !w) ? 0 : pl.r2;
+  if (r2c && (!m32 || (r2c != 8 && r2c != 16) || pl.q > kRecomputeMaxQ))
+    return set_error("compaction: no λ and no recomputation for r2 = %d, q = %d", pl.r2, pl.q), false;
   if (dt == L1S_BF16) {
-    CompactArgs<uint16_t> c{m.mask, m.counts, pl.smp_ctas, pl.n, pl.smp_chunk, capacity, lam, sb,
-                            static_cast<const uint16_t*>(A), lda, b, pl.d, idx, w, coreset, count_out, sb};
-    sample_compact_kernel<uint16_t><<<pl.smp_ctas, pl.smp_threads, 0, st>>>(c);
+    CompactArgs<uint16_t> c{mask, counts, pl.smp_ctas, pl.n, pl.smp_chunk, capacity, lam, m32, pl.r2, sb,
+                            static_cast<const uint16_t*>(A), lda, b, pl.d, pl.pi2_neg_lo, pl.pi2_neg_hi, idx, w,
+                            coreset, count_out, sb};
+    if (r2c == 8) sample_compact_kernel<uint16_t, 8><<<pl.smp_ctas, pl.smp_threads, 0, st>>>(c);
+    else if (r2c == 16) sample_compact_kernel<uint16_t, 16><<<pl.smp_ctas, pl.smp_threads, 0, st>>>(c);
+    else sample_compact_kernel<uint16_t, 0><<<pl.smp_ctas, pl.smp_threads, 0, st>>>(c);
   } else {
-    CompactArgs<float> c{m.mask, m.counts, pl.smp_ctas, pl.n, pl.smp_chunk, capacity, lam, sb,
-                         static_cast<const float*>(A), lda, b, pl.d, idx, w, coreset, count_out, sb};
-    sample_compact_kernel<float><<<pl.smp_ctas, pl.smp_threads, 0, st>>>(c);
+    CompactArgs<float> c{mask, counts, pl.smp_ctas, pl.n, pl.smp_chunk, capacity, lam, m32, pl.r2, sb,
+                         static_cast<const float*>(A), lda, b, pl.d, pl.pi2_neg_lo, pl.pi2_neg_hi, idx, w, coreset,
+                         count_out, sb};
+    if (r2c == 8) sample_compact_kernel<float, 8><<<pl.smp_ctas, pl.smp_threads, 0, st>>>(c);
+    else if (r2c == 16) sample_compact_kernel<float, 16><<<pl.smp_ctas, pl.smp_threads, 0, st>>>(c);
+    else sample_compact_kernel<float, 0><<<pl.smp_ctas, pl.smp_threads, 0, st>>>(c);
   }
   count_launch(1);
   return cuda_ok(cudaGetLastError(), "launch sample_compact");

@@ -98,6 +98,10 @@ _SIGS = {
                                _P]),
     "l1s_batched_workspace_size": (C.c_int, [C.POINTER(Problem), _I32, C.POINTER(_SZ)]),
     "l1_regress_batched": (C.c_int, [C.POINTER(Problem), _I32, _P, _P, _SZ, _P]),
+    "l1s_multi_workspace_size": (C.c_int, [_PP, _I64, _I32, _I32, C.c_int, C.POINTER(_SZ)]),
+    "l1_coreset_multi": (C.c_int, [_P, _I64, C.c_int, _I64, _I32, _I32, _PP, _I64, _P, _P, _P, _P, _P, _SZ,
+                                   _P]),
+    "l1_regress_multi": (C.c_int, [_P, _I64, C.c_int, _I64, _I32, _I32, _PP, _I32, _P, _P, _P, _P, _SZ, _P]),
 }
 EXPORTS = tuple(_SIGS)
 
@@ -250,6 +254,40 @@ def l1_regress(A, b, params: Params, ws, inputs_on_host: bool = False, stream=No
     if rc in (1, 2, 3):
         _check(rc, "l1_regress")
     return x, obj.value, rows.value, rc
+
+
+def l1s_multi_workspace_size(params: Params, n: int, d: int, k: int, dtype: int = F32) -> int:
+    out = C.c_size_t(0)
+    _check(load().l1s_multi_workspace_size(C.byref(params), n, d, k, dtype, C.byref(out)),
+           "l1s_multi_workspace_size")
+    return out.value
+
+
+def multi_workspace(params: Params, n: int, d: int, k: int, dtype: int = F32, device=None) -> torch.Tensor:
+    return torch.empty(l1s_multi_workspace_size(params, n, d, k, dtype), dtype=torch.uint8,
+                       device=device or "cuda")
+
+
+def l1_coreset_multi(X, k: int, params: Params, capacity: int, idx, w, coreset, count, ws, stream=None) -> None:
+    """X = [A | B] (n × (d + k) device matrix, rows contiguous); coreset rows are [A_i, −B_i]."""
+    n, q, ldx, dt = _matrix(X)
+    _check(load().l1_coreset_multi(_ptr(X, False), ldx, dt, n, q - k, k, C.byref(params), capacity, _ptr(idx),
+                                   _ptr(w), _ptr(coreset), _ptr(count), _ptr(ws), ws.numel(), _stream(stream)),
+           "l1_coreset_multi")
+
+
+def l1_regress_multi(X, k: int, params: Params, ws, max_iter: int = 100, stream=None):
+    """Returns (W as a d × k float64 CPU tensor, objectives (k,), coreset rows, status code)."""
+    n, q, ldx, dt = _matrix(X)
+    d = q - k
+    W = torch.empty((d, k), dtype=torch.float64)
+    obj = torch.empty(k, dtype=torch.float64)
+    rows = C.c_int64(0)
+    rc = load().l1_regress_multi(_ptr(X, False), ldx, dt, n, d, k, C.byref(params), max_iter, _ptr(W), _ptr(obj),
+                                 C.addressof(rows), _ptr(ws), ws.numel(), _stream(stream))
+    if rc in (1, 2, 3):
+        _check(rc, "l1_regress_multi")
+    return W, obj, rows.value, rc
 
 
 def l1s_debug_variates(params: Params, row_start: int, count: int, device="cuda", stream=None) -> dict:

@@ -409,4 +409,32 @@ def check_scaled_probabilities(seed: int = 31) -> None:
 
 def _all_checks():
     return ALL_CHECKS + [check_bf16_round, check_gaussian_pi2, check_gaussian_lambda_distribution,
-                         check_scaled_probabilities]
+                         check_scaled_probabilities, check_multiple_regression]
+
+
+# ----------------------------------------------------------------- multiple regression
+def check_multiple_regression(seed: int = 17) -> None:
+    """FastCauchyRegression(A, B) of §4.2.1.  (1) k = 1 reduces to the single right-hand
+    side pipeline (same draws, same coreset, same solution).  (2) B = A·W* + E with sparse gross
+    errors E is fitted exactly (ℓ1 regression's exact recovery): W = W* column by column
+    and objective j is ‖E_j‖₁.  (3) The objectives
+    add up to the entrywise ℓ1 norm of X·Z with X = [A, −B] and Z = [W; I_k]."""
+    g = np.random.default_rng(seed)
+    n, d, k = 3000, 4, 3
+    A = g.standard_normal((n, d))
+    Wstar = g.standard_normal((d, k))
+    B = A @ Wstar + g.laplace(size=(n, k))
+    one = pipeline.fast_cauchy_multiple_regression(A, B[:, :1], 64, 40, 16, 300.0, seed=2)
+    ref = pipeline.fast_cauchy_regression(A, B[:, 0], 64, 40, 16, 300.0, seed=2)
+    assert np.array_equal(one["idx"], ref["idx"]) and np.array_equal(one["w"], ref["w"])
+    assert np.allclose(one["W"][:, 0], ref["x_hat"], rtol=0, atol=1e-9)
+    assert abs(one["objectives"][0] - ref["objective"]) <= 1e-12 * ref["objective"]
+    # sparse gross errors (1% of rows) keep X full rank, and ℓ1 regression recovers W* exactly
+    E = np.where(g.random((n, k)) < 0.01, 50.0 * g.standard_normal((n, k)), 0.0)
+    exact = pipeline.fast_cauchy_multiple_regression(A, A @ Wstar + E, 64, 40, 16, 600.0, seed=3)
+    assert np.allclose(exact["W"], Wstar, rtol=0, atol=1e-8), np.abs(exact["W"] - Wstar).max()
+    assert np.allclose(exact["objectives"], np.abs(E).sum(axis=0), rtol=1e-10, atol=0)
+    res = pipeline.fast_cauchy_multiple_regression(A, B, 64, 40, 16, 300.0, seed=4)
+    Z = np.vstack([res["W"], np.eye(k)])
+    X = pipeline.form_x_multi(A, B)
+    assert abs(np.abs(X @ Z).sum() - res["objectives"].sum()) <= 1e-12 * res["objectives"].sum()

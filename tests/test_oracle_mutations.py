@@ -20,6 +20,7 @@ ORIG_PROB = sampling.probabilities
 ORIG_BERN = sampling.bernoulli_sample
 ORIG_LP = solve.lad_lp
 ORIG_FORMX = pipeline.form_x
+ORIG_FORM_X_MULTI = pipeline.form_x_multi
 ORIG_GAUSS = rng.pi2_gaussian_matrix
 ORIG_SCALED = sampling.probabilities_scaled
 
@@ -121,6 +122,10 @@ def lp_unweighted(A, b, w=None):
     return ORIG_LP(A, b, None)
 
 
+def formx_multi_plus_b(A, B):
+    return ORIG_FORM_X_MULTI(A, -np.asarray(B, dtype=np.float64))
+
+
 def formx_plus_b(A, b):
     return np.concatenate([np.asarray(A, float), np.asarray(b, float)[:, None]], axis=1)
 
@@ -166,6 +171,7 @@ MUTATIONS = [
      pins.check_gaussian_lambda_distribution),
     ("Gaussian Π2 variance 2 in λ̂", rng, "pi2_gaussian_matrix", gauss_var2, pins.check_gaussian_lambda_distribution),
     ("scaled p̂ not capped", sampling, "probabilities_scaled", scaled_no_cap, pins.check_scaled_probabilities),
+    ("X = [A, +B] (multiple)", pipeline, "form_x_multi", formx_multi_plus_b, pins.check_multiple_regression),
 ]
 
 
