@@ -43,7 +43,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-variants", action="store_true",
-                    help="skip the BF16 and batched forms (measured after the main line's timed region)")
+                    help="skip the other forms (measured after the main line's timed region)")
+    ap.add_argument("--variants", default="optimized,multi,bf16,batched",
+                    help="comma-separated forms to measure after the main line: optimized, multi, bf16, batched")
     return ap.parse_args()
 
 
@@ -608,19 +610,26 @@ def run_gpu(args) -> None:
         "coreset_rows": kept, "status_flags": flags, "host_wall_s": t_host,
     }
     if rank == 0 and not args.no_variants and world == 1:
-        line_opt = optimized_variant(L, dev, stream, args, A, b, w, peaks["hbm_gbs"], ms_per_step)
+        want = {v.strip() for v in args.variants.split(",") if v.strip()}
+        variants = {}
+        if w.dtype != "f32":                      # the optimized and multiple forms run on FP32 inputs
+            want -= {"optimized", "multi"}
+        if "optimized" in want:
+            variants["optimized"] = optimized_variant(L, dev, stream, args, A, b, w, peaks["hbm_gbs"], ms_per_step)
         del ws
         torch.cuda.empty_cache()
-        line_multi = multi_variant(L, dev, stream, args, A, b, w, peaks["hbm_gbs"])
+        if "multi" in want:
+            variants["multi"] = multi_variant(L, dev, stream, args, A, b, w, peaks["hbm_gbs"])
         del A, b
         torch.cuda.empty_cache()
-        line["variants"] = {"bf16": bf16_variant(L, dev, stream, args, peaks["hbm_gbs"])}
-        torch.cuda.empty_cache()
-        line["variants"]["batched"] = batched_variant(L, dev, stream, args, peaks["hbm_gbs"])
-        line["variants"]["f32_plain"] = {"workload": w.name, "value": value, "ms_per_step": ms_per_step,
-                                         "step_frac": step_gbs / peaks["hbm_gbs"]}
-        line["variants"]["optimized"] = line_opt
-        line["variants"]["multi"] = line_multi
+        if "bf16" in want:
+            variants["bf16"] = bf16_variant(L, dev, stream, args, peaks["hbm_gbs"])
+            torch.cuda.empty_cache()
+        if "batched" in want:
+            variants["batched"] = batched_variant(L, dev, stream, args, peaks["hbm_gbs"])
+        variants["f32_plain"] = {"workload": w.name, "value": value, "ms_per_step": ms_per_step,
+                                 "step_frac": step_gbs / peaks["hbm_gbs"]}
+        line["variants"] = variants
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_oracle_rows_per_s(pr, w, args.cpu_seconds)
     if rank == 0:
