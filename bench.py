@@ -560,6 +560,20 @@ def run_gpu(args) -> None:
     w_h = torch.empty(cap, dtype=torch.float64).pin_memory()
     cnt_h = torch.zeros(1, dtype=torch.int64)
     e2e_steps = max(3, min(args.steps, 10))
+    # the host link's own rate for the same bytes (a plain pinned copy), for reference
+    dst = torch.empty(A_h.numel() * A_h.element_size(), dtype=torch.uint8, device=dev)
+    src = A_h.view(-1).view(torch.uint8)
+    h2d = []
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            dst.copy_(src, non_blocking=True)
+            e1.record(stream)
+        e1.synchronize()
+        h2d.append(dst.numel() / (e0.elapsed_time(e1) / 1e3) / 1e9)
+    del dst
+    h2d_gbs = statistics.median(h2d)
     for _ in range(2):
         L.l1_coreset_host(A_h, b_h, prm, cap, idx_h, w_h, cnt_h, ws_h, stream=stream)
     barrier()
@@ -582,13 +596,25 @@ def run_gpu(args) -> None:
     dom_bytes = [ab["phase1"], 0, ab["phase2"] + ab["phase3"]][dom]
     achieved = dom_bytes / (phase_ms[dom] / 1e3) / 1e9
     step_gbs = ab["step"] / (ms_per_step / 1e3) / 1e9
-    traffic = None
+    traffic = instr = None
     prof = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(prof):
         with open(prof) as f:
             tr = json.load(f)
         traffic = tr.get(f"{names[dom]}:{w.name}")
+        instr = tr.get(f"{names[dom]}:{w.name}:warp_instructions")
 
+    clocks = clk.summary()
+    # The phase-1 kernel is bound by instruction issue and shared-memory atomics, not by
+    # HBM: its issue rate against 4 warp instructions per cycle per SM at the sampled clock
+    # (warp instructions per launch from the ncu capture in profiles/).
+    issue = None
+    if instr and clocks.get("sm_mhz"):
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        ach = instr / (phase_ms[dom] / 1e3)
+        pk = sms * 4 * clocks["sm_mhz"] * 1e6
+        issue = {"warp_instructions": instr, "achieved_per_s": ach, "peak_per_s": pk, "frac": ach / pk,
+                 "peak_basis": f"{sms} SMs x 4 warp instructions per cycle x sampled SM clock"}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -599,14 +625,15 @@ def run_gpu(args) -> None:
         "roofline": {"kernel": names[dom], "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
                      "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
                      "peak_source": peaks["source"], "algorithmic_bytes": dom_bytes,
-                     "launch_ms": phase_ms[dom]},
+                     "launch_ms": phase_ms[dom], "issue": issue},
         "step_roofline": {"achieved": step_gbs, "frac": step_gbs / peaks["hbm_gbs"],
                           "algorithmic_bytes": ab["step"]},
         "phase_ms": dict(zip(names, phase_ms)),
         "e2e": {"value": world * n / e2e_s, "unit": UNIT, "h2d_bytes_per_step": n * (d * elem + 4),
-                "d2h_bytes_per_step": 8 + cap * 16, "status": rc, "host": host_binding},
+                "d2h_bytes_per_step": 8 + cap * 16, "status": rc, "host": host_binding,
+                "h2d_copy_gbs": h2d_gbs},
         "gpu_launches": launches,
-        "clocks": clk.summary(),
+        "clocks": clocks,
         "coreset_rows": kept, "status_flags": flags, "host_wall_s": t_host,
     }
     if rank == 0 and not args.no_variants and world == 1:

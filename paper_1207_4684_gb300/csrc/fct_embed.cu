@@ -403,13 +403,30 @@ __global__ void __launch_bounds__(WsCfg<W>::kThreads, LEAN ? 3 : (W == 16 ? 2 : 
       // one decision for all producers (a consumer may set s_abort at any moment)
       if (named_barrier_any(1, 32 * kWsP, s_abort != 0)) break;
       if (!by_tma) {
-        // plain loads into the stage (ragged last block or unaligned input)
+        // plain loads into the stage (ragged last block, or rows that are not contiguous):
+        // producer warp w copies rows w, w + 4, …, its lanes the columns of a row
         TA* ra = reinterpret_cast<TA*>(stage);
         float* rb = reinterpret_cast<float*>(stage + b_off);
         const TA* A = static_cast<const TA*>(a.A);
-        for (int e = pt; e < S * d; e += 32 * kWsP) {
-          const int r = e / d, c = e - r * d;
-          ra[e] = (row0 + r < a.n) ? A[(row0 + r) * a.lda + c] : TA(0);
+        // (d ≤ 32; two rows per warp instruction when d ≤ 16), 16 loads in flight per
+        // lane before any is stored
+        const int pw = pt >> 5, pl = pt & 31;
+        const int cw = d <= 16 ? 16 : 32;                 // lanes per row
+        const int rpw = 32 / cw;                          // rows per warp instruction
+        const int c = pl & (cw - 1), rr = pl / cw;
+        constexpr int kBatch = 16;
+        for (int t0 = 0; (pw + kWsP * t0) * rpw < S; t0 += kBatch) {
+          TA v[kBatch];
+#pragma unroll
+          for (int u = 0; u < kBatch; ++u) {
+            const int r = (pw + kWsP * (t0 + u)) * rpw + rr;
+            v[u] = (r < S && c < d && row0 + r < a.n) ? A[(row0 + r) * a.lda + c] : TA(0);
+          }
+#pragma unroll
+          for (int u = 0; u < kBatch; ++u) {
+            const int r = (pw + kWsP * (t0 + u)) * rpw + rr;
+            if (r < S && c < d) ra[r * d + c] = v[u];
+          }
         }
         for (int r = pt; r < S; r += 32 * kWsP) rb[r] = (row0 + r < a.n) ? a.b[row0 + r] : 0.f;
       }

@@ -198,6 +198,49 @@ __global__ void __launch_bounds__(kLamThreads) lambda_kernel(const TA* __restric
   if (threadIdx.x == 0) block_sums[blockIdx.x] = tot;
 }
 
+// d < D columns on the D-column kernel: rows are read as D values with zeros beyond
+// column d, and M's rows are padded the same way (M's b row moves to row D), so the extra
+// products are exact zeros and λ equals the unpadded FMA chain bit for bit.
+template <int D, int R2, bool SMEM_M>
+__global__ void __launch_bounds__(kLamThreads) lambda_kernel_pad(const float* __restrict__ A, int64_t lda, int d,
+                                                                 const float* __restrict__ b, int64_t n,
+                                                                 float* __restrict__ lam,
+                                                                 double* __restrict__ block_sums,
+                                                                 const float* __restrict__ mg) {
+  constexpr int Q = D + 1;
+  __shared__ float sM[SMEM_M ? Q * R2 : 1];
+  if constexpr (SMEM_M) {
+    for (int e = threadIdx.x; e < Q * R2; e += blockDim.x) {
+      const int k = e / R2, j = e - k * R2;
+      sM[e] = k < d ? mg[k * R2 + j] : (k == D ? mg[d * R2 + j] : 0.f);
+    }
+    __syncthreads();
+  }
+  float s = 0.f, c = 0.f;
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  int64_t row = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  float nx[Q];
+  auto load = [&](int64_t r, float (&x)[Q]) {
+    const float* p = A + r * lda;
+#pragma unroll
+    for (int k = 0; k < D; ++k) x[k] = k < d ? __ldg(p + k) : 0.f;
+    x[D] = -__ldg(b + r);
+  };
+  if (row < n) load(row, nx);
+  for (; row < n; row += stride) {
+    float x[Q];
+#pragma unroll
+    for (int k = 0; k < Q; ++k) x[k] = nx[k];
+    const int64_t nrow = row + stride;
+    if (nrow < n) load(nrow, nx);
+    const float med = lambda_of_row<Q, R2, SMEM_M>(x, sM);
+    lam[row] = med;
+    two_sum_add(s, c, med);
+  }
+  const double tot = block_pair_total(s, c);
+  if (threadIdx.x == 0) block_sums[blockIdx.x] = tot;
+}
+
 // Any q ≤ 129 and r2 ≤ R2P (columns beyond r2 are ignored by the median).
 template <int R2P, typename TA, bool SMEM_M>
 __global__ void __launch_bounds__(kLamThreads) lambda_kernel_generic(const TA* __restrict__ A, int64_t lda,
@@ -389,6 +432,25 @@ static void launch_lambda_case(dim3 grid, dim3 block, cudaStream_t st, bool alig
   lambda_kernel<DD, RR, TA, false, SM><<<grid, block, 0, st>>>(A, lda, b, n, lam, sums, mg);
 }
 
+// The padded kernel's D for FP32 rows of d columns with no kernel of their own: the
+// smallest D ≥ d among the padded instantiations for this r2 (0: none, use the generic kernel).
+static bool lambda_has_case(int d, int r2) {
+  static const int cases[][2] = {{4, 8}, {8, 8}, {16, 8}, {32, 8}, {4, 16}, {8, 16}, {16, 16},
+                                 {32, 16}, {64, 16}, {8, 32}, {16, 32}, {32, 32}, {64, 32}};
+  for (const auto& c : cases)
+    if (c[0] == d && c[1] == r2) return true;
+  return false;
+}
+
+static int lambda_pad_target(int d, int r2) {
+  if (lambda_has_case(d, r2)) return 0;
+  static const int pads[][2] = {{8, 8}, {16, 8}, {32, 8}, {8, 16}, {16, 16}, {32, 16}, {64, 16},
+                                {16, 32}, {32, 32}, {64, 32}};
+  for (const auto& c : pads)
+    if (c[1] == r2 && c[0] >= d) return c[0];
+  return 0;
+}
+
 template <typename TA, bool SM>
 static bool launch_lambda_t(const Plan& pl, const TA* A, int64_t lda, const float* b, float* lam,
                             double* sums, const float* mg, cudaStream_t st) {
@@ -416,6 +478,27 @@ static bool launch_lambda_t(const Plan& pl, const TA* A, int64_t lda, const floa
   L1S_LAMBDA_CASE(32, 32)
   L1S_LAMBDA_CASE(64, 32)
 #undef L1S_LAMBDA_CASE
+  if constexpr (sizeof(TA) == 4) {
+    const int D = lambda_pad_target(d, r2);
+#define L1S_LAMBDA_PAD(DD, RR)                                                                         \
+  if (D == DD && r2 == RR) {                                                                           \
+    lambda_kernel_pad<DD, RR, SM><<<grid, block, 0, st>>>(reinterpret_cast<const float*>(A), lda, d, b, \
+                                                         pl.n, lam, sums, mg);                          \
+    count_launch(1);                                                                                   \
+    return cuda_ok(cudaGetLastError(), "launch lambda (padded)");                                      \
+  }
+    L1S_LAMBDA_PAD(8, 8)
+    L1S_LAMBDA_PAD(16, 8)
+    L1S_LAMBDA_PAD(32, 8)
+    L1S_LAMBDA_PAD(8, 16)
+    L1S_LAMBDA_PAD(16, 16)
+    L1S_LAMBDA_PAD(32, 16)
+    L1S_LAMBDA_PAD(64, 16)
+    L1S_LAMBDA_PAD(16, 32)
+    L1S_LAMBDA_PAD(32, 32)
+    L1S_LAMBDA_PAD(64, 32)
+#undef L1S_LAMBDA_PAD
+  }
   const size_t gsm = SM ? sizeof(float) * (d + 1) * r2 : 0;
   if (r2 <= 16)
     lambda_kernel_generic<16, TA, SM><<<grid, block, gsm, st>>>(A, lda, b, pl.n, d, r2, lam, sums, mg);
@@ -441,14 +524,32 @@ bool launch_lambda(const Plan& pl, const void* A, int64_t lda, l1s_dtype dt, con
                    const float* m32, const l1s_params* p, float* lam, double* user_sum,
                    unsigned char* ws, cudaStream_t st, int* nsums_out) {
   const bool smem_m = pl.lam_m_in_smem != 0;
-  if (!smem_m && !cuda_ok(cudaMemcpyToSymbolAsync(c_M, m32, sizeof(float) * pl.q * pl.r2, 0,
-                                                  cudaMemcpyDeviceToDevice, st),
-                          "copy M to constant memory"))
-    return false;
+  const bool tc = lambda_tc_applies(pl.d, pl.r2, lda, A, dt);
+  const int pad = (tc || dt != L1S_F32) ? 0 : lambda_pad_target(pl.d, pl.r2);
+  if (!smem_m) {
+    const size_t row = sizeof(float) * pl.r2;
+    if (!pad) {
+      if (!cuda_ok(cudaMemcpyToSymbolAsync(c_M, m32, row * pl.q, 0, cudaMemcpyDeviceToDevice, st),
+                   "copy M to constant memory"))
+        return false;
+    } else {
+      // rows 0..d−1, zero rows d..D−1, and M's b row as row D
+      void* cm = nullptr;
+      if (!cuda_ok(cudaGetSymbolAddress(&cm, c_M), "constant M address") ||
+          !cuda_ok(cudaMemcpyToSymbolAsync(c_M, m32, row * pl.d, 0, cudaMemcpyDeviceToDevice, st),
+                   "copy M to constant memory") ||
+          !cuda_ok(cudaMemsetAsync(static_cast<char*>(cm) + row * pl.d, 0, row * (pad - pl.d), st),
+                   "zero padded M rows") ||
+          !cuda_ok(cudaMemcpyToSymbolAsync(c_M, m32 + static_cast<size_t>(pl.d) * pl.r2, row, row * pad,
+                                           cudaMemcpyDeviceToDevice, st),
+                   "copy M's b row"))
+        return false;
+    }
+  }
   double* sums = reinterpret_cast<double*>(ws + pl.off_lamsum);
   int blocks = pl.lam_ctas;
   bool ok;
-  if (lambda_tc_applies(pl.d, pl.r2, lda, A, dt)) {
+  if (tc) {
     blocks = std::min(pl.lam_ctas, 3 * device_info().sms);   // three resident per SM (64 TMEM columns each)
     ok = launch_lambda_tc(pl.n, A, b, m32, reinterpret_cast<uint16_t*>(ws + pl.off_pi2), lam, sums, blocks,
                           reinterpret_cast<uint32_t*>(ws + pl.off_status), st);

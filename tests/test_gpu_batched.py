@@ -31,6 +31,7 @@ MEMBERS = [
     (16384, 32, 1024, 32, 1000.0, "bf16", None),
     (70000, 16, 512, 16, 2000.0, "f32", None),
     (1000, 8, 32, 16, 150.0, "bf16", None),
+    (6000, 12, 64, 16, 500.0, "f32", 14),
 ]
 
 

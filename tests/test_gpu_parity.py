@@ -154,7 +154,8 @@ def test_condition_rank_deficient_flag():
                                               (1000, 32, 32, "bf16", 40),
                                               (30000, 5, 16, "f32", 9), (20000, 7, 9, "f32", None),
                                               (12345, 12, 32, "bf16", None), (1000, 3, 64, "f32", None),
-                                              (257, 4, 1, "f32", None)])
+                                              (257, 4, 1, "f32", None), (50001, 19, 16, "f32", 20),
+                                              (20000, 12, 8, "f32", None), (30000, 40, 32, "f32", None)])
 def test_lambda_parity(n, d, r2, dtype, lda):
     pr = problem(n, d, seed=r2 + d, dtype=dtype, design="gauss")
     A, b = to_device(pr, lda)
