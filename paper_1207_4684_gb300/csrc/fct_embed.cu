@@ -43,6 +43,7 @@ struct FctArgs {
   float inv_sqrt_s;
   float* partials;        // [slices][gridDim.x][r1][width]
   int accumulate;         // 1: add to the partials of an earlier launch over other rows
+  int sd;                 // narrow-X kernel: row stride of a stage (d, or lda when padded rows are staged)
   uint32_t* flags;
 };
 
@@ -358,6 +359,7 @@ __global__ void __launch_bounds__(WsCfg<W>::kThreads, LEAN ? 3 : (W == 16 ? 2 : 
   const int r1 = a.r1;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int d = a.d;
+  const int sd = a.sd;                   // stage row stride
   unsigned char* stages = smem_raw;
   float* P = reinterpret_cast<float*>(stages + NSTAGE * static_cast<size_t>(a.stage_bytes));   // [r1][PST]
   float* Pb = P + ((r1 * PST + 3) & ~3);                                                           // [r1]
@@ -425,7 +427,7 @@ __global__ void __launch_bounds__(WsCfg<W>::kThreads, LEAN ? 3 : (W == 16 ? 2 : 
 #pragma unroll
           for (int u = 0; u < kBatch; ++u) {
             const int r = (pw + kWsP * (t0 + u)) * rpw + rr;
-            if (r < S && c < d) ra[r * d + c] = v[u];
+            if (r < S && c < d) ra[r * sd + c] = v[u];
           }
         }
         for (int r = pt; r < S; r += 32 * kWsP) rb[r] = (row0 + r < a.n) ? a.b[row0 + r] : 0.f;
@@ -488,7 +490,7 @@ __global__ void __launch_bounds__(WsCfg<W>::kThreads, LEAN ? 3 : (W == 16 ? 2 : 
             float* Pl = P + c;
             float v[16];
 #pragma unroll
-            for (int j = 0; j < 16; ++j) v[j] = live ? widen<TA>(rawA[(base | j) * d + c]) : 0.f;
+            for (int j = 0; j < 16; ++j) v[j] = live ? widen<TA>(rawA[(base | j) * sd + c]) : 0.f;
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
               const int4 m = *reinterpret_cast<const int4*>(&mi[base | j]);
@@ -519,7 +521,7 @@ __global__ void __launch_bounds__(WsCfg<W>::kThreads, LEAN ? 3 : (W == 16 ? 2 : 
           float* Pl = P + (LEAN ? 0 : hb * 16) + c;
           float v[16];
 #pragma unroll
-          for (int j = 0; j < 16; ++j) v[j] = live ? widen<TA>(rawA[(base | (j << 1)) * d + c]) : 0.f;
+          for (int j = 0; j < 16; ++j) v[j] = live ? widen<TA>(rawA[(base | (j << 1)) * sd + c]) : 0.f;
 #pragma unroll
           for (int j = 0; j < 16; ++j) {
             const int4 m = *reinterpret_cast<const int4*>(&mi[base | (j << 1)]);
@@ -1296,6 +1298,7 @@ static bool launch_fct_part(const Plan& pl, const void* A, int64_t lda, l1s_dtyp
   a.inv_sqrt_s = static_cast<float>(1.0 / sqrt(static_cast<double>(pl.s)));
   a.partials = reinterpret_cast<float*>(ws + pl.off_partials);
   a.accumulate = accumulate ? 1 : 0;
+  a.sd = pl.d;
   a.flags = reinterpret_cast<uint32_t*>(ws + pl.off_status);
   // A layout that cannot be staged falls back to direct loads with the same grid; the
   // direct variant needs less shared memory than the staged one it was planned for.
@@ -1303,12 +1306,32 @@ static bool launch_fct_part(const Plan& pl, const void* A, int64_t lda, l1s_dtyp
   // So does the bucket-sorted kernel.
   const int wsw = pl.fct_ws;
   const int srt = pl.fct_sorted;
-  if (wsw || srt) a.tma = fct_can_stage(tile, pl.d, dt, lda, A, b) ? 1 : 0;
+  if (srt) a.tma = fct_can_stage(tile, pl.d, dt, lda, A, b) ? 1 : 0;
+  if (wsw) {
+    // Rows with padding (lda > d) are staged whole by the same bulk copies (S consecutive
+    // rows are one contiguous range) when the wider stage keeps the planned residency.
+    if (lda != pl.d && lda <= 2 * pl.d && fct_can_stage(tile, static_cast<int>(lda), dt, lda, A, b)) {
+      const void* fw = fct_ws_kernel(pl.fct_tile_log2, pl.log2s, dt, wsw, pl.fct_lean != 0);
+      const size_t s0 = fct_ws_smem_bytes(tile, pl.d, dt, pl.r1, wsw, pl.fct_lean != 0);
+      const size_t s1 = fct_ws_smem_bytes(tile, static_cast<int>(lda), dt, pl.r1, wsw, pl.fct_lean != 0);
+      int o0 = 0, o1 = 0;
+      if (s1 <= device_info().max_smem_optin &&
+          cuda_ok(cudaFuncSetAttribute(fw, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(s1)),
+                  "cudaFuncSetAttribute(fct_embed)") &&
+          cuda_ok(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o0, fw, pl.fct_threads, s0), "occupancy") &&
+          cuda_ok(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o1, fw, pl.fct_threads, s1), "occupancy") &&
+          o1 >= o0 && o1 > 0)
+        a.sd = static_cast<int>(lda);
+    }
+    a.stage_a_bytes = static_cast<uint32_t>(tile) * a.sd * esz;
+    a.stage_bytes = fct_stage_bytes(tile, a.sd, dt);
+    a.tma = fct_can_stage(tile, a.sd, dt, a.sd == pl.d ? lda : a.sd, A, b) ? 1 : 0;
+  }
   const void* fn = srt ? fct_sorted_kernel(pl.log2s, dt, srt)
                        : (wsw ? fct_ws_kernel(pl.fct_tile_log2, pl.log2s, dt, wsw, pl.fct_lean != 0)
                               : fct_kernel(pl.log2s, dt, staged));
   const size_t smem = srt ? fct_sorted_smem_bytes(pl.s, pl.d, dt, pl.r1, srt)
-                          : (wsw ? fct_ws_smem_bytes(tile, pl.d, dt, pl.r1, wsw, pl.fct_lean != 0)
+                          : (wsw ? fct_ws_smem_bytes(tile, a.sd, dt, pl.r1, wsw, pl.fct_lean != 0)
                                  : fct_smem_bytes(pl.s, pl.d, dt, pl.r1, pl.fct_width, staged));
   if (!cuda_ok(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)),
                "cudaFuncSetAttribute(fct_embed)"))
