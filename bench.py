@@ -44,8 +44,9 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the other forms (measured after the main line's timed region)")
-    ap.add_argument("--variants", default="optimized,multi,bf16,batched",
-                    help="comma-separated forms to measure after the main line: optimized, multi, bf16, batched")
+    ap.add_argument("--variants", default="optimized,replacement,multi,bf16,batched",
+                    help="comma-separated forms to measure after the main line: optimized, replacement, multi, "
+                         "bf16, batched")
     return ap.parse_args()
 
 
@@ -378,6 +379,29 @@ def optimized_variant(L, dev, stream, args, A, b, w, peak: float, plain_ms: floa
             "speedup_vs_f32_plain": plain_ms / ms}
 
 
+def replacement_variant(L, dev, stream, args, A, b, w, peak: float, plain_ms: float) -> dict:
+    """Exactly m_s draws with replacement, p̂_i = λ_i/Σλ (the caption of Figure 2), on the
+    same data: steps 1-5, the running sum of λ and the m_s draws."""
+    import torch
+
+    n, d = A.shape
+    m = int(w.coreset)
+    prm = L.make_params(w.s, w.r1, w.r2, float(m), seed=w.seed, problem_id=w.problem_id, variant=2)
+    ws = L.workspace(prm, n, d, device=dev)
+    cap = 2 * m + 64
+    idx = torch.empty(cap, dtype=torch.int64, device=dev)
+    wts = torch.empty(cap, dtype=torch.float64, device=dev)
+    cnt = torch.zeros(1, dtype=torch.int64, device=dev)
+    ms = _time_ms(lambda: L.l1_coreset(A, b, prm, cap, idx, wts, None, cnt, ws, stream=stream), stream,
+                  args.warmup, args.steps)
+    flags = L.l1s_status_read(ws, stream=stream)
+    # X twice, λ written and read twice (sum, running sum), C written (8 bytes per row), the draws
+    ab = 2 * n * (d * 4 + 4) + 4 * n + 8 * n + 8 * n + m * (16 + 8 * (d + 1) + d * 4 + 4)
+    return {"workload": w.name, "variant": "FastCauchyRegression, m_s draws with replacement", "draws": m,
+            "value": n / (ms / 1e3), "ms_per_step": ms, "step_frac": ab / (ms / 1e3) / 1e9 / peak,
+            "status": flags, "speedup_vs_f32_plain": plain_ms / ms}
+
+
 def multi_variant(L, dev, stream, args, A, b, w, peak: float) -> dict:
     """Multiple regression (§4.2.1) on the same design: X = [A | B] with k = 4 right-hand
     sides (b and three more columns A·w_j + Laplace noise with 5% 100·Cauchy outliers),
@@ -639,11 +663,15 @@ def run_gpu(args) -> None:
     if rank == 0 and not args.no_variants and world == 1:
         want = {v.strip() for v in args.variants.split(",") if v.strip()}
         variants = {}
-        if w.dtype != "f32":                      # the optimized and multiple forms run on FP32 inputs
-            want -= {"optimized", "multi"}
+        if w.dtype != "f32":                      # these forms run on the FP32 inputs
+            want -= {"optimized", "replacement", "multi"}
         if "optimized" in want:
             variants["optimized"] = optimized_variant(L, dev, stream, args, A, b, w, peaks["hbm_gbs"], ms_per_step)
         del ws
+        torch.cuda.empty_cache()
+        if "replacement" in want:
+            variants["replacement"] = replacement_variant(L, dev, stream, args, A, b, w, peaks["hbm_gbs"],
+                                                          ms_per_step)
         torch.cuda.empty_cache()
         if "multi" in want:
             variants["multi"] = multi_variant(L, dev, stream, args, A, b, w, peaks["hbm_gbs"])

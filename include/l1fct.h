@@ -83,8 +83,12 @@ typedef struct {
                                  1: OptimizedFastCauchyRegression (Figure "mainOpt"): Π2 Gaussian
                                  (Box–Muller on stream 1), p̂ = min(1, sample_scale·λ̂), no Σλ;
                                  coreset_size then only bounds the expected coreset size
-                                 (it sizes the workspace's coreset buffers). */
-  double sample_scale;        /* variant 1: the sampling size s of p̂ = min{1, s·λ̂}; variant 0: 0 */
+                                 (it sizes the workspace's coreset buffers).
+                                 2: FastCauchyRegression drawing exactly coreset_size rows
+                                 (an integer) independently with replacement, p̂_i = λ_i/Σλ,
+                                 weight 1/(coreset_size·p̂_i) (caption of Figure 2); the
+                                 kept rows are listed in draw order, with repeats. */
+  double sample_scale;        /* variant 1: the sampling size s of p̂ = min{1, s·λ̂}; variants 0, 2: 0 */
 } l1s_params;
 
 /* Text of the calling thread's last host-side error ("" if none). */

@@ -49,12 +49,19 @@ def coreset_of_x(X: np.ndarray, s: int, r1: int, r2: int, coreset: float, seed: 
     t2 = time.perf_counter()
     lam = leverage.lambda_estimates(X, m_mat)                                 # steps 4-5
     t3 = time.perf_counter()
-    if variant == 1:
-        p_hat, tau, total = sampling.probabilities_scaled(lam, sample_scale), sample_scale, None
+    if variant == 2:                                      # exactly m_s draws with replacement
+        m = int(coreset)
+        u = rng.replacement_uniforms(seed, problem_id, np.arange(m))
+        idx, wts, cdf = sampling.sample_with_replacement(lam, m, u)
+        total = float(cdf[-1])
+        p_hat, tau = lam / total, 1.0 / total
     else:
-        p_hat, tau, total = sampling.probabilities(lam, coreset)              # step 6
-    u = rng.sample_uniforms(seed, problem_id, np.arange(n))
-    idx, wts = sampling.bernoulli_sample(p_hat, u)                            # step 7
+        if variant == 1:
+            p_hat, tau, total = sampling.probabilities_scaled(lam, sample_scale), sample_scale, None
+        else:
+            p_hat, tau, total = sampling.probabilities(lam, coreset)          # step 6
+        u = rng.sample_uniforms(seed, problem_id, np.arange(n))
+        idx, wts = sampling.bernoulli_sample(p_hat, u)                        # step 7
     t4 = time.perf_counter()
     t.update({"fct": t1 - t0, "condition": t2 - t1, "lambda": t3 - t2, "sample": t4 - t3})
     return {"X": X, "PiX": pix, "T": tsum, "R": r_mat, "Pi2": pi2, "M": m_mat,
@@ -69,7 +76,8 @@ def fast_cauchy_regression(A, b, s: int, r1: int, r2: int, coreset: float,
     """All intermediates of Figure 2 for one problem (rows are numbered from 0).
 
     variant 1 is OptimizedFastCauchyRegression (Figure "mainOpt"): Π2 Gaussian and
-    p̂ = min{1, sample_scale·λ̂} without the Σλ normalisation."""
+    p̂ = min{1, sample_scale·λ̂} without the Σλ normalisation; variant 2 draws exactly
+    m_s rows with replacement with p̂_i = λ_i/Σλ (the caption of Figure 2)."""
     t = {} if timings is None else timings
     X = form_x(A, b)                                                          # step 1
     out = coreset_of_x(X, s, r1, r2, coreset, seed, problem_id, sign_flip, variant, sample_scale, t)

@@ -51,6 +51,7 @@ PHILOX_W1 = np.uint64(0xBB67AE85)
 STREAM_FCT = 0
 STREAM_PI2 = 1
 STREAM_SAMPLE = 2
+STREAM_REPLACE = 3
 
 
 def philox4x32_10(c0, c1, c2, c3, k0, k1):
@@ -177,3 +178,17 @@ def sample_uniform_bits(seed: int, problem_id: int, rows) -> np.ndarray:
 def sample_uniforms(seed: int, problem_id: int, rows) -> np.ndarray:
     """Sampling uniforms u_i ∈ [0, 1) in FP64 (exact: 53-bit integers × 2^-53)."""
     return sample_uniform_bits(seed, problem_id, rows).astype(np.float64) * 2.0 ** -53
+
+
+def replacement_uniforms(seed: int, problem_id: int, draws) -> np.ndarray:
+    """Uniforms u_t ∈ [0, 1) of the with-replacement draws t (stream 3, one Philox call per
+    pair of draws (2k, 2k+1): words (0, 1) for the even draw, (2, 3) for the odd one)."""
+    k0, k1 = _key(seed)
+    draws = np.asarray(draws, dtype=np.int64)
+    lo, hi = _row_counter(draws >> 1)
+    o0, o1, o2, o3 = philox4x32_10(lo, hi, np.uint64(problem_id), np.uint64(STREAM_REPLACE), k0, k1)
+    odd = (draws & 1) == 1
+    wa = np.where(odd, o2, o0)
+    wb = np.where(odd, o3, o1)
+    bits = ((wa >> np.uint64(5)) << np.uint64(26)) | (wb >> np.uint64(6))
+    return bits.astype(np.float64) * 2.0 ** -53

@@ -42,3 +42,18 @@ def bernoulli_sample(p: np.ndarray, u: np.ndarray):
     keep = np.asarray(u, dtype=np.float64) < p
     idx = np.flatnonzero(keep)
     return idx, 1.0 / p[idx]
+
+
+def sample_with_replacement(lam: np.ndarray, m: int, u: np.ndarray):
+    """Exactly m rows drawn independently with replacement, p̂_i = λ_i/Σλ (the alternative
+    to step 6-7 that the caption of Figure 2 allows).  Draw t takes the row i with
+    C_{i−1} ≤ u_t·Σλ < C_i, C the running FP64 sum of λ (C_{−1} = 0, Σλ = C_{n−1}); its
+    weight is 1/(m·p̂_i) = Σλ/(m·λ_i).  Returns (rows in draw order, weights, C)."""
+    lam = np.asarray(lam, dtype=np.float64)
+    cdf = np.cumsum(lam)
+    total = float(cdf[-1])
+    if not (total > 0.0) or not math.isfinite(total):
+        raise ValueError("Σλ must be positive and finite")
+    target = np.asarray(u, dtype=np.float64)[:m] * total
+    idx = np.searchsorted(cdf, target, side="right")
+    return idx, total / (m * lam[idx]), cdf

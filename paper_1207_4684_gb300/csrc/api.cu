@@ -41,6 +41,9 @@ bool launch_lambda(const Plan& pl, const void* A, int64_t lda, l1s_dtype dt, con
                    unsigned char* ws, cudaStream_t st, int* nsums_out = nullptr);
 bool launch_m_to_f32(const double* m, int total, float* out, cudaStream_t st);
 bool lambda_mark_applies(const Plan& pl, l1s_dtype dt, const l1s_params* p);
+bool launch_replacement(const Plan& pl, const float* lam, const l1s_params* prm, const void* A, int64_t lda,
+                        l1s_dtype dt, const float* b, int64_t capacity, int64_t* idx, double* w, double* coreset,
+                        int64_t* count_out, unsigned char* ws, cudaStream_t st);
 bool launch_lambda_mark(const Plan& pl, const void* A, int64_t lda, const float* b, const float* m32,
                         const l1s_params* p, float* lam_out, unsigned char* ws, cudaStream_t st);
 bool launch_compact(const Plan& pl, const float* lam, const float* m32, const void* A, int64_t lda, l1s_dtype dt,
@@ -113,8 +116,10 @@ static bool check_params(const l1s_params* p, int64_t n, int d) {
   if (p->global_row_offset < 0 || p->global_row_offset % p->s != 0)
     return set_error("global_row_offset must be a non-negative multiple of s"), false;
   if (p->sign_flip != 0 && p->sign_flip != 1) return set_error("sign_flip must be 0 or 1"), false;
-  if (p->variant != 0 && p->variant != 1) return set_error("variant must be 0 or 1"), false;
-  if (p->variant == 0 && p->sample_scale != 0.0) return set_error("sample_scale must be 0 for variant 0"), false;
+  if (p->variant < 0 || p->variant > 2) return set_error("variant must be 0, 1 or 2"), false;
+  if (p->variant != 1 && p->sample_scale != 0.0) return set_error("sample_scale must be 0 for variants 0 and 2"), false;
+  if (p->variant == 2 && (p->coreset_size != floor(p->coreset_size) || p->coreset_size > 1e9))
+    return set_error("variant 2 draws coreset_size rows: it must be an integer in [1, 1e9]"), false;
   if (p->variant == 1 && (!(p->sample_scale > 0.0) || !isfinite(p->sample_scale)))
     return set_error("variant 1 needs a positive, finite sample_scale"), false;
   return true;
@@ -162,6 +167,13 @@ int sample_impl(const Plan& pl, const void* A, int64_t lda, l1s_dtype dtype, con
     return L1S_OK;
   }
   float* lam = lambda ? lambda : reinterpret_cast<float*>(w + pl.off_lam);
+  if (params->variant == 2) {
+    int nsums = 0;
+    if (!launch_lambda(pl, A, lda, dtype, b, m32, params, lam, nullptr, w, st, &nsums) ||
+        !launch_replacement(pl, lam, params, A, lda, dtype, b, capacity, idx, wts, coreset, count, w, st))
+      return L1S_ERR_CUDA;
+    return L1S_OK;
+  }
   // Σλ and τ are formed at the start of the sampling kernel; OptimizedFastCauchyRegression
   // (variant 1) needs no Σλ at all.
   int nsums = 0;
@@ -384,6 +396,7 @@ bool make_plan(const l1s_params* p, int64_t n, int d, l1s_dtype dt, bool host_st
   P.off_counts = take(sizeof(int64_t) * static_cast<size_t>(smp_ctas_max));
   P.off_idx_tmp = take(static_cast<size_t>(cap) * (sizeof(int64_t) + sizeof(double) + sizeof(double) * P.q) +
                        2 * sizeof(double) * (P.q + 1));
+  if (p->variant == 2) P.off_cdf = take(sizeof(double) * static_cast<size_t>(n));   // running sum of λ
   if (host_staging) {
     P.off_stage_a = take(esz * static_cast<size_t>(n) * d);
     P.off_stage_b = take(sizeof(float) * static_cast<size_t>(n));

@@ -26,6 +26,7 @@ constexpr int kMaxConstM = 129 * 64;
 constexpr uint32_t kStreamFct = 0;
 constexpr uint32_t kStreamPi2 = 1;
 constexpr uint32_t kStreamSample = 2;
+constexpr uint32_t kStreamReplace = 3;   // with-replacement draws (params.variant = 2)
 
 // Status word layout inside the workspace (first 256 bytes).
 struct StatusBlock {
@@ -246,7 +247,7 @@ struct Plan {
   // workspace offsets (bytes)
   size_t off_status, off_partials, off_pix, off_qr, off_r, off_m64, off_m32, off_pi2,
       off_lam, off_lamsum, off_mask, off_counts, off_idx_tmp, off_irls, off_x, off_objp,
-      off_stage_a, off_stage_b, total;
+      off_stage_a, off_stage_b, off_cdf, total;
 };
 
 bool make_plan(const l1s_params* p, int64_t n, int d, l1s_dtype dt, bool host_staging, Plan* plan,

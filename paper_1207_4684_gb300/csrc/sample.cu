@@ -12,6 +12,8 @@
 // compact: each block adds the counts of the blocks before it (fixed order),
 //          scans its mask words, and writes kept rows in ascending order:
 //          index, weight 1/p̂_i, and the FP64 row [A_i, −b_i] of the coreset.
+#include <algorithm>
+
 #include "l1s_common.cuh"
 
 namespace l1s {
@@ -347,6 +349,192 @@ bool launch_compact(const Plan& pl, const float* lam, const float* m32, const vo
   }
   count_launch(1);
   return cuda_ok(cudaGetLastError(), "launch sample_compact");
+}
+
+// ----------------------------------------------------------------- with replacement
+// params.variant = 2 (the alternative the caption of Figure 2 allows): exactly m draws
+// t = 0 … m−1, draw t takes the row i with C_{i−1} ≤ u_t·Σλ < C_i, C the running FP64 sum
+// of λ, and weight 1/(m·p̂_i) = Σλ/(m·λ_i).  C is formed over contiguous chunks of
+// pl.smp_chunk rows: one launch sums every chunk, a second adds each chunk's offset (the
+// sums of the chunks before it, in order) to its running sum and writes C; both run the
+// same per-chunk arithmetic (8 consecutive rows per thread, a warp-shuffle scan, the
+// warp totals in order).  C is non-decreasing up to FP64 rounding at thread boundaries.
+constexpr int kScanPer = 8;
+
+template <bool WRITE>
+__device__ double chunk_scan(const float* __restrict__ lam, int64_t start, int64_t stop, double offset,
+                             double* __restrict__ cdf, double* s_warp) {
+  constexpr int kWarps = kSmpThreads / 32;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  double carry = 0.0;                                   // the same in every thread
+  for (int64_t base = start; base < stop; base += static_cast<int64_t>(kSmpThreads) * kScanPer) {
+    const int64_t r0 = base + static_cast<int64_t>(tid) * kScanPer;
+    double loc[kScanPer];
+    double acc = 0.0;
+#pragma unroll
+    for (int k = 0; k < kScanPer; ++k) {
+      acc += (r0 + k < stop) ? static_cast<double>(lam[r0 + k]) : 0.0;
+      loc[k] = acc;
+    }
+    double incl = acc;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const double t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    double excl = __shfl_up_sync(0xffffffffu, incl, 1);
+    if (lane == 0) excl = 0.0;
+    __syncthreads();                                    // s_warp free from the previous tile
+    if (lane == 31) s_warp[warp] = incl;
+    __syncthreads();
+    double woff = 0.0, tile_total = 0.0;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) {
+      const double v = s_warp[w];
+      if (w < warp) woff += v;
+      tile_total += v;
+    }
+    if constexpr (WRITE) {
+      const double t0 = offset + (carry + (woff + excl));
+#pragma unroll
+      for (int k = 0; k < kScanPer; ++k)
+        if (r0 + k < stop) cdf[r0 + k] = t0 + loc[k];
+    }
+    carry += tile_total;
+  }
+  return carry;
+}
+
+__global__ void __launch_bounds__(kSmpThreads) cdf_total_kernel(const float* __restrict__ lam, int64_t n,
+                                                                int64_t chunk, double* __restrict__ totals) {
+  __shared__ double s_warp[kSmpThreads / 32];
+  const int64_t start = static_cast<int64_t>(blockIdx.x) * chunk;
+  const double t = chunk_scan<false>(lam, start, min(n, start + chunk), 0.0, nullptr, s_warp);
+  if (threadIdx.x == 0) totals[blockIdx.x] = t;
+}
+
+__global__ void __launch_bounds__(kSmpThreads) cdf_write_kernel(const float* __restrict__ lam, int64_t n,
+                                                                int64_t chunk, const double* __restrict__ totals,
+                                                                double* __restrict__ cdf) {
+  __shared__ double s_warp[kSmpThreads / 32];
+  __shared__ double s_off;
+  // This chunk's offset: every block runs the same exclusive scan of the chunk sums
+  // (a run of consecutive sums per thread, then a warp-shuffle scan and the warp totals
+  // in order) and keeps its own entry, so all blocks agree on every offset.
+  {
+    const int nb = static_cast<int>(gridDim.x);
+    const int per = (nb + kSmpThreads - 1) / kSmpThreads;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int k0 = tid * per;
+    double acc = 0.0;
+    for (int k = k0; k < min(nb, k0 + per); ++k) acc += totals[k];
+    double incl = acc;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const double t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    double excl = __shfl_up_sync(0xffffffffu, incl, 1);
+    if (lane == 0) excl = 0.0;
+    if (lane == 31) s_warp[warp] = incl;
+    __syncthreads();
+    double woff = 0.0;
+    for (int w = 0; w < warp; ++w) woff += s_warp[w];
+    const int kb = static_cast<int>(blockIdx.x);
+    if (kb >= k0 && kb < k0 + per) {
+      double off = woff + excl;
+      for (int k = k0; k < kb; ++k) off += totals[k];
+      s_off = off;
+    }
+    __syncthreads();
+  }
+  const int64_t start = static_cast<int64_t>(blockIdx.x) * chunk;
+  chunk_scan<true>(lam, start, min(n, start + chunk), s_off, cdf, s_warp);
+}
+
+template <typename TA>
+struct DrawArgs {
+  const float* lam;
+  const double* cdf;
+  int64_t n;
+  int64_t m;             // draws
+  Key2 key;
+  uint32_t problem;
+  const TA* A;
+  int64_t lda;
+  const float* b;
+  int d;
+  int64_t capacity;
+  int64_t* idx;
+  double* w;             // may be null
+  double* coreset;       // may be null
+  int64_t* count_out;    // may be null
+  StatusBlock* status;
+};
+
+template <typename TA>
+__global__ void __launch_bounds__(kSmpThreads) replacement_draw_kernel(const DrawArgs<TA> a) {
+  const double total = a.cdf[a.n - 1];
+  const bool ok = total > 0.0 && isfinite(total);
+  const int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t == 0) {
+    a.status->lambda_total = total;
+    a.status->count = a.m;
+    if (a.count_out) *a.count_out = a.m;
+    if (!ok) raise_flag(&a.status->flags, L1S_ERR_ZERO_MASS);
+    if (a.m > a.capacity) raise_flag(&a.status->flags, L1S_ERR_CAPACITY);
+  }
+  if (!ok || t >= a.m || t >= a.capacity) return;
+  const uint4 o = draw_row(a.key, static_cast<uint64_t>(t) >> 1, a.problem, kStreamReplace);
+  const bool odd = (t & 1) != 0;
+  const double u = static_cast<double>(u53_of(odd ? o.z : o.x, odd ? o.w : o.y)) * 0x1p-53;
+  const double target = u * total;
+  int64_t lo = 0, hi = a.n;                             // first i with C_i > target
+  while (lo < hi) {
+    const int64_t mid = lo + ((hi - lo) >> 1);
+    if (a.cdf[mid] > target) hi = mid;
+    else lo = mid + 1;
+  }
+  int64_t i = lo < a.n ? lo : a.n - 1;
+  // a row of zero mass can only be met through rounding of C: take the next row with mass
+  int64_t j = i;
+  while (j < a.n && !(a.lam[j] > 0.f)) ++j;
+  if (j < a.n) i = j;
+  a.idx[t] = i;
+  const float li = a.lam[i];
+  if (a.w) a.w[t] = li > 0.f ? total / (static_cast<double>(a.m) * static_cast<double>(li)) : 0.0;
+  if (a.coreset) {
+    double* out = a.coreset + t * (a.d + 1);
+    const TA* src = a.A + i * a.lda;
+    for (int k = 0; k < a.d; ++k) out[k] = static_cast<double>(load_elem<TA>(src + k));
+    out[a.d] = -static_cast<double>(a.b[i]);
+  }
+}
+
+bool launch_replacement(const Plan& pl, const float* lam, const l1s_params* prm, const void* A, int64_t lda,
+                        l1s_dtype dt, const float* b, int64_t capacity, int64_t* idx, double* w, double* coreset,
+                        int64_t* count_out, unsigned char* ws, cudaStream_t st) {
+  double* totals = reinterpret_cast<double*>(ws + pl.off_counts);
+  double* cdf = reinterpret_cast<double*>(ws + pl.off_cdf);
+  cdf_total_kernel<<<pl.smp_ctas, kSmpThreads, 0, st>>>(lam, pl.n, pl.smp_chunk, totals);
+  cdf_write_kernel<<<pl.smp_ctas, kSmpThreads, 0, st>>>(lam, pl.n, pl.smp_chunk, totals, cdf);
+  count_launch(2);
+  if (!cuda_ok(cudaGetLastError(), "launch cdf")) return false;
+  const int64_t m = static_cast<int64_t>(prm->coreset_size);
+  const int64_t draws = std::min(m, capacity);
+  const int blocks = static_cast<int>(std::max<int64_t>(1, (draws + kSmpThreads - 1) / kSmpThreads));
+  StatusBlock* sb = reinterpret_cast<StatusBlock*>(ws + pl.off_status);
+  if (dt == L1S_BF16) {
+    DrawArgs<uint16_t> a{lam, cdf, pl.n, m, make_key(prm->seed), prm->problem_id, static_cast<const uint16_t*>(A),
+                         lda, b, pl.d, capacity, idx, w, coreset, count_out, sb};
+    replacement_draw_kernel<uint16_t><<<blocks, kSmpThreads, 0, st>>>(a);
+  } else {
+    DrawArgs<float> a{lam, cdf, pl.n, m, make_key(prm->seed), prm->problem_id, static_cast<const float*>(A),
+                      lda, b, pl.d, capacity, idx, w, coreset, count_out, sb};
+    replacement_draw_kernel<float><<<blocks, kSmpThreads, 0, st>>>(a);
+  }
+  count_launch(1);
+  return cuda_ok(cudaGetLastError(), "launch replacement draws");
 }
 
 // ----------------------------------------------------------------- debug draws

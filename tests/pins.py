@@ -409,7 +409,7 @@ def check_scaled_probabilities(seed: int = 31) -> None:
 
 def _all_checks():
     return ALL_CHECKS + [check_bf16_round, check_gaussian_pi2, check_gaussian_lambda_distribution,
-                         check_scaled_probabilities, check_multiple_regression]
+                         check_scaled_probabilities, check_multiple_regression, check_with_replacement]
 
 
 # ----------------------------------------------------------------- multiple regression
@@ -438,3 +438,43 @@ def check_multiple_regression(seed: int = 17) -> None:
     Z = np.vstack([res["W"], np.eye(k)])
     X = pipeline.form_x_multi(A, B)
     assert abs(np.abs(X @ Z).sum() - res["objectives"].sum()) <= 1e-12 * res["objectives"].sum()
+
+
+# ----------------------------------------------------------------- sampling with replacement
+def check_with_replacement(seed: int = 23) -> None:
+    """Exactly m draws with p̂_i = λ_i/Σλ (caption of Figure 2).  (1) Each draw inverts the
+    running sum: brute force over rows on a small case, zero-λ rows never drawn.  (2) Every
+    weighted draw carries w_t·λ_{i_t} = Σλ/m, so the weights·λ add up to Σλ.  (3) Row
+    frequencies follow p̂ (χ²).  (4) Σ_t w_t·r_{i_t} is unbiased for Σ_i r_i."""
+    g = np.random.default_rng(seed)
+    lam = np.abs(g.standard_cauchy(40))
+    lam[[3, 17, 18]] = 0.0
+    u = rng.replacement_uniforms(5, 1, np.arange(500))
+    idx, w, cdf = sampling.sample_with_replacement(lam, 500, u)
+    total = math.fsum(lam.tolist())
+    for t in range(500):
+        acc, want = 0.0, None
+        for i in range(lam.size):
+            acc += lam[i]
+            if u[t] * cdf[-1] < acc:
+                want = i
+                break
+        assert idx[t] == want, (t, idx[t], want)
+    assert not np.isin(idx, [3, 17, 18]).any()
+    assert np.allclose(w * lam[idx], total / 500, rtol=1e-12)
+    lam2 = g.uniform(0.1, 1.0, 16)
+    m = 200000
+    u2 = rng.replacement_uniforms(9, 0, np.arange(m))
+    idx2, w2, _ = sampling.sample_with_replacement(lam2, m, u2)
+    f_obs = np.bincount(idx2, minlength=16)
+    f_exp = m * lam2 / lam2.sum()
+    chi2 = float(((f_obs - f_exp) ** 2 / f_exp).sum())
+    assert stats.chi2.sf(chi2, 15) > 1e-4, chi2
+    r = np.abs(g.standard_normal(16))
+    est = []
+    for rep in range(100):
+        uu = rng.replacement_uniforms(100 + rep, 0, np.arange(50))
+        ii, ww, _ = sampling.sample_with_replacement(lam2, 50, uu)
+        est.append(float((ww * r[ii]).sum()))
+    est = np.array(est)
+    assert abs(est.mean() - r.sum()) < 4 * est.std(ddof=1) / math.sqrt(len(est)), "estimator biased"

@@ -21,6 +21,7 @@ ORIG_BERN = sampling.bernoulli_sample
 ORIG_LP = solve.lad_lp
 ORIG_FORMX = pipeline.form_x
 ORIG_FORM_X_MULTI = pipeline.form_x_multi
+ORIG_REPLACE = sampling.sample_with_replacement
 ORIG_GAUSS = rng.pi2_gaussian_matrix
 ORIG_SCALED = sampling.probabilities_scaled
 
@@ -126,6 +127,18 @@ def formx_multi_plus_b(A, B):
     return ORIG_FORM_X_MULTI(A, -np.asarray(B, dtype=np.float64))
 
 
+def replace_weight_mp(lam, m, u):
+    idx, w, cdf = ORIG_REPLACE(lam, m, u)
+    return idx, 1.0 / w, cdf
+
+
+def replace_unscaled_target(lam, m, u):
+    lam = np.asarray(lam, dtype=np.float64)
+    cdf = np.cumsum(lam)
+    idx = np.minimum(np.searchsorted(cdf, np.asarray(u)[:m], side="right"), lam.size - 1)
+    return idx, cdf[-1] / (m * np.maximum(lam[idx], 1e-300)), cdf
+
+
 def formx_plus_b(A, b):
     return np.concatenate([np.asarray(A, float), np.asarray(b, float)[:, None]], axis=1)
 
@@ -172,6 +185,10 @@ MUTATIONS = [
     ("Gaussian Π2 variance 2 in λ̂", rng, "pi2_gaussian_matrix", gauss_var2, pins.check_gaussian_lambda_distribution),
     ("scaled p̂ not capped", sampling, "probabilities_scaled", scaled_no_cap, pins.check_scaled_probabilities),
     ("X = [A, +B] (multiple)", pipeline, "form_x_multi", formx_multi_plus_b, pins.check_multiple_regression),
+    ("with-replacement weight m·p̂", sampling, "sample_with_replacement", replace_weight_mp,
+     pins.check_with_replacement),
+    ("with-replacement target u, not u·Σλ", sampling, "sample_with_replacement", replace_unscaled_target,
+     pins.check_with_replacement),
 ]
 
 
