@@ -42,6 +42,8 @@ def parse():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-graph", action="store_true",
+                    help="time eager calls instead of replays of the step captured as a CUDA graph")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the other forms (measured after the main line's timed region)")
     ap.add_argument("--variants", default="optimized,replacement,multi,bf16,batched",
@@ -535,17 +537,42 @@ def run_gpu(args) -> None:
             dist.barrier()
         torch.cuda.synchronize(dev)
 
+    # One step captured as a CUDA graph on a side stream: the same launches, replayed
+    # without the host's per-call planning.  The eager calls are timed too.
+    gstream = torch.cuda.Stream(dev)
+    graph = None
+    per_step_launches = None
+    if not args.no_graph:
+        with torch.cuda.stream(gstream):
+            L.l1_coreset(A, b, prm, cap, idx, wts, core, cnt, ws, stream=gstream)
+        torch.cuda.synchronize(dev)
+        graph = torch.cuda.CUDAGraph()
+        c0 = L.l1s_kernel_launches()
+        with torch.cuda.graph(graph, stream=gstream):
+            L.l1_coreset(A, b, prm, cap, idx, wts, core, cnt, ws, stream=gstream)
+        per_step_launches = L.l1s_kernel_launches() - c0
+        for _ in range(args.warmup):
+            graph.replay()
+        torch.cuda.synchronize(dev)
+    eager_ms = _time_ms(step, stream, 0, args.steps)
+
     # ---- timed region: K steps, CUDA events on the launching stream
+    tstream = gstream if graph is not None else stream
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with ClockSampler(local) as clk:
+    with ClockSampler(local) as clk, torch.cuda.stream(tstream):
         barrier()
         t_host0 = time.perf_counter()
         launches0 = L.l1s_kernel_launches()
-        ev0.record(stream)
+        ev0.record(tstream)
         for _ in range(args.steps):
-            step()
-        ev1.record(stream)
+            if graph is not None:
+                graph.replay()
+            else:
+                step()
+        ev1.record(tstream)
         launches = L.l1s_kernel_launches() - launches0
+        if graph is not None:
+            launches = per_step_launches * args.steps      # graph nodes: counted at capture
         barrier()
         t_host = time.perf_counter() - t_host0
     gpu_ms = ev0.elapsed_time(ev1)
@@ -653,6 +680,8 @@ def run_gpu(args) -> None:
         "step_roofline": {"achieved": step_gbs, "frac": step_gbs / peaks["hbm_gbs"],
                           "algorithmic_bytes": ab["step"]},
         "phase_ms": dict(zip(names, phase_ms)),
+        "launch": {"mode": "cuda_graph" if graph is not None else "eager", "eager_ms_per_step": eager_ms,
+                   "launches_per_step": per_step_launches if graph is not None else launches // max(args.steps, 1)},
         "e2e": {"value": world * n / e2e_s, "unit": UNIT, "h2d_bytes_per_step": n * (d * elem + 4),
                 "d2h_bytes_per_step": 8 + cap * 16, "status": rc, "host": host_binding,
                 "h2d_copy_gbs": h2d_gbs},

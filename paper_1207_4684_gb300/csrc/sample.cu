@@ -357,14 +357,16 @@ bool launch_compact(const Plan& pl, const float* lam, const float* m32, const vo
 // of λ, and weight 1/(m·p̂_i) = Σλ/(m·λ_i).  C is formed over contiguous chunks of
 // pl.smp_chunk rows: one launch sums every chunk, a second adds each chunk's offset (the
 // sums of the chunks before it, in order) to its running sum and writes C; both run the
-// same per-chunk arithmetic (8 consecutive rows per thread, a warp-shuffle scan, the
-// warp totals in order).  C is non-decreasing up to FP64 rounding at thread boundaries.
-constexpr int kScanPer = 8;
+// same per-chunk arithmetic (16 consecutive rows per thread, a warp-shuffle scan, a scan
+// of the warp totals by one warp).  C is non-decreasing up to FP64 rounding at thread boundaries.
+constexpr int kScanPer = 16;
 
+// s_warp holds 2·(warps) + 1 doubles: the warp totals, their exclusive scan, the tile total.
 template <bool WRITE>
 __device__ double chunk_scan(const float* __restrict__ lam, int64_t start, int64_t stop, double offset,
                              double* __restrict__ cdf, double* s_warp) {
   constexpr int kWarps = kSmpThreads / 32;
+  static_assert(kWarps <= 32, "one warp scans the warp totals");
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   double carry = 0.0;                                   // the same in every thread
   for (int64_t base = start; base < stop; base += static_cast<int64_t>(kSmpThreads) * kScanPer) {
@@ -387,13 +389,19 @@ __device__ double chunk_scan(const float* __restrict__ lam, int64_t start, int64
     __syncthreads();                                    // s_warp free from the previous tile
     if (lane == 31) s_warp[warp] = incl;
     __syncthreads();
-    double woff = 0.0, tile_total = 0.0;
+    if (warp == 0) {                                    // exclusive scan of the warp totals
+      double v = lane < kWarps ? s_warp[lane] : 0.0;
 #pragma unroll
-    for (int w = 0; w < kWarps; ++w) {
-      const double v = s_warp[w];
-      if (w < warp) woff += v;
-      tile_total += v;
+      for (int o = 1; o < kWarps; o <<= 1) {
+        const double t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+      }
+      const double e = __shfl_up_sync(0xffffffffu, v, 1);
+      if (lane < kWarps) s_warp[kWarps + lane] = lane == 0 ? 0.0 : e;
+      if (lane == kWarps - 1) s_warp[2 * kWarps] = v;
     }
+    __syncthreads();
+    const double woff = s_warp[kWarps + warp], tile_total = s_warp[2 * kWarps];
     if constexpr (WRITE) {
       const double t0 = offset + (carry + (woff + excl));
 #pragma unroll
@@ -407,7 +415,7 @@ __device__ double chunk_scan(const float* __restrict__ lam, int64_t start, int64
 
 __global__ void __launch_bounds__(kSmpThreads) cdf_total_kernel(const float* __restrict__ lam, int64_t n,
                                                                 int64_t chunk, double* __restrict__ totals) {
-  __shared__ double s_warp[kSmpThreads / 32];
+  __shared__ double s_warp[2 * (kSmpThreads / 32) + 1];
   const int64_t start = static_cast<int64_t>(blockIdx.x) * chunk;
   const double t = chunk_scan<false>(lam, start, min(n, start + chunk), 0.0, nullptr, s_warp);
   if (threadIdx.x == 0) totals[blockIdx.x] = t;
@@ -416,7 +424,7 @@ __global__ void __launch_bounds__(kSmpThreads) cdf_total_kernel(const float* __r
 __global__ void __launch_bounds__(kSmpThreads) cdf_write_kernel(const float* __restrict__ lam, int64_t n,
                                                                 int64_t chunk, const double* __restrict__ totals,
                                                                 double* __restrict__ cdf) {
-  __shared__ double s_warp[kSmpThreads / 32];
+  __shared__ double s_warp[2 * (kSmpThreads / 32) + 1];
   __shared__ double s_off;
   // This chunk's offset: every block runs the same exclusive scan of the chunk sums
   // (a run of consecutive sums per thread, then a warp-shuffle scan and the warp totals
