@@ -191,6 +191,25 @@ def run_reference(args) -> None:
 
 
 # ----------------------------------------------------------------- BF16 and batched forms
+def _time_step_ms(step_on, stream, args) -> float:
+    """Mean device time of one step enqueued by step_on(stream): captured once as a CUDA
+    graph on a side stream and replayed (eager calls on `stream` with --no-graph)."""
+    import torch
+
+    if args.no_graph:
+        return _time_ms(lambda: step_on(stream), stream, args.warmup, args.steps)
+    gs = torch.cuda.Stream(stream.device)
+    with torch.cuda.stream(gs):
+        step_on(gs)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=gs):
+        step_on(gs)
+    with torch.cuda.stream(gs):
+        ms = _time_ms(g.replay, gs, args.warmup, args.steps)
+    return ms
+
+
 def _time_ms(step, stream, warmup: int, steps: int) -> float:
     """Mean device time of one step: CUDA events on `stream` around `steps` back-to-back steps."""
     import torch
@@ -261,8 +280,7 @@ def bf16_variant(L, dev, stream, args, peak: float) -> dict:
     cnt = torch.zeros(1, dtype=torch.int64, device=dev)
     out = {"workload": w.name, "n": n, "d": d, "s": w.s, "r1": w.r1, "r2": w.r2, "coreset": w.coreset}
     for tag, A, elem in (("bf16", A16, 2), ("f32", A32, 4)):
-        ms = _time_ms(lambda: L.l1_coreset(A, b, prm, cap, idx, wts, None, cnt, ws, stream=stream), stream,
-                      args.warmup, args.steps)
+        ms = _time_step_ms(lambda st: L.l1_coreset(A, b, prm, cap, idx, wts, None, cnt, ws, stream=st), stream, args)
         kept = int(cnt.item())
         ab = algorithmic_bytes(n, d, elem, kept)["step"]
         x, f, rows, rc = L.l1_regress(A, b, prm, ws, stream=stream)
@@ -369,8 +387,7 @@ def optimized_variant(L, dev, stream, args, A, b, w, peak: float, plain_ms: floa
     idx = torch.empty(cap, dtype=torch.int64, device=dev)
     wts = torch.empty(cap, dtype=torch.float64, device=dev)
     cnt = torch.zeros(1, dtype=torch.int64, device=dev)
-    ms = _time_ms(lambda: L.l1_coreset(A, b, prm, cap, idx, wts, None, cnt, ws, stream=stream), stream,
-                  args.warmup, args.steps)
+    ms = _time_step_ms(lambda st: L.l1_coreset(A, b, prm, cap, idx, wts, None, cnt, ws, stream=st), stream, args)
     kept = int(cnt.item())
     flags = L.l1s_status_read(ws, stream=stream)
     # λ̂ and the keep decision share one pass: no λ write and read back (8 bytes per row)
@@ -394,8 +411,7 @@ def replacement_variant(L, dev, stream, args, A, b, w, peak: float, plain_ms: fl
     idx = torch.empty(cap, dtype=torch.int64, device=dev)
     wts = torch.empty(cap, dtype=torch.float64, device=dev)
     cnt = torch.zeros(1, dtype=torch.int64, device=dev)
-    ms = _time_ms(lambda: L.l1_coreset(A, b, prm, cap, idx, wts, None, cnt, ws, stream=stream), stream,
-                  args.warmup, args.steps)
+    ms = _time_step_ms(lambda st: L.l1_coreset(A, b, prm, cap, idx, wts, None, cnt, ws, stream=st), stream, args)
     flags = L.l1s_status_read(ws, stream=stream)
     # X twice, λ written and read twice (sum, running sum), C written (8 bytes per row), the draws
     ab = 2 * n * (d * 4 + 4) + 4 * n + 8 * n + 8 * n + m * (16 + 8 * (d + 1) + d * 4 + 4)
@@ -431,8 +447,7 @@ def multi_variant(L, dev, stream, args, A, b, w, peak: float) -> dict:
     idx = torch.empty(cap, dtype=torch.int64, device=dev)
     wts = torch.empty(cap, dtype=torch.float64, device=dev)
     cnt = torch.zeros(1, dtype=torch.int64, device=dev)
-    ms = _time_ms(lambda: L.l1_coreset_multi(X, k, prm, cap, idx, wts, None, cnt, ws, stream=stream), stream,
-                  args.warmup, args.steps)
+    ms = _time_step_ms(lambda st: L.l1_coreset_multi(X, k, prm, cap, idx, wts, None, cnt, ws, stream=st), stream, args)
     kept = int(cnt.item())
     flags = L.l1s_status_read(ws, stream=stream)
     # the passes read d + k − 1 columns of X and B_k gathered once (read + write 4 bytes per row)

@@ -268,6 +268,12 @@ L1S_API int l1_regress_multi(const void* X_dev, int64_t ldx, l1s_dtype dtype, in
                              double* objectives_host, int64_t* coreset_rows_host,
                              void* ws, size_t ws_bytes, void* stream);
 
+/* Debug: one thread waits, at most max_cycles SM clock cycles (1000 … 4e9), on a
+ * barrier that nothing completes — the bounded wait of the pipelined kernels — and then
+ * raises L1S_ERR_TIMEOUT in the status word of `ws` and returns, leaving the context
+ * usable.  Lets a test exercise the timeout path without faulting or hanging the GPU. */
+L1S_API int l1s_debug_wait_timeout(void* ws, size_t ws_bytes, int64_t max_cycles, void* stream);
+
 /* Debug: the Philox draws of global rows [row_start, row_start + count) as the
  * kernels use them (device outputs, any may be NULL): bucket_h/bucket_i in
  * [0, r1), k_h/k_i the 24-bit integers of the Cauchy scales, cauchy_h/cauchy_i

@@ -41,6 +41,7 @@ bool launch_lambda(const Plan& pl, const void* A, int64_t lda, l1s_dtype dt, con
                    unsigned char* ws, cudaStream_t st, int* nsums_out = nullptr);
 bool launch_m_to_f32(const double* m, int total, float* out, cudaStream_t st);
 bool lambda_mark_applies(const Plan& pl, l1s_dtype dt, const l1s_params* p);
+bool launch_debug_wait(uint32_t* flags, long long max_cycles, cudaStream_t st);
 bool launch_replacement(const Plan& pl, const float* lam, const l1s_params* prm, const void* A, int64_t lda,
                         l1s_dtype dt, const float* b, int64_t capacity, int64_t* idx, double* w, double* coreset,
                         int64_t* count_out, unsigned char* ws, cudaStream_t st);
@@ -707,6 +708,14 @@ int l1_regress(const void* A, int64_t lda, l1s_dtype dtype, const float* b, int6
   *objective_host = res[1];
   if (coreset_rows_host) *coreset_rows_host = cnt;
   return first_error(flags);
+}
+
+int l1s_debug_wait_timeout(void* ws, size_t ws_bytes, int64_t max_cycles, void* stream) {
+  if (!ws || ws_bytes < sizeof(StatusBlock)) return set_error("workspace too small"), L1S_ERR_WORKSPACE;
+  if (max_cycles < 1000 || max_cycles > kWaitCycles) return set_error("max_cycles out of range"), L1S_ERR_INVALID_ARG;
+  if (!launch_debug_wait(&static_cast<StatusBlock*>(ws)->flags, max_cycles, static_cast<cudaStream_t>(stream)))
+    return L1S_ERR_CUDA;
+  return L1S_OK;
 }
 
 int l1s_debug_variates(const l1s_params* params, int64_t row_start, int64_t count, int32_t* bucket_h,

@@ -545,6 +545,26 @@ bool launch_replacement(const Plan& pl, const float* lam, const l1s_params* prm,
   return cuda_ok(cudaGetLastError(), "launch replacement draws");
 }
 
+// ----------------------------------------------------------------- bounded-wait check
+// One thread waits on an mbarrier that nothing arrives at, with the given cycle limit,
+// the same bounded wait the pipelined kernels use; when it gives up it raises the
+// TIMEOUT status bit and the kernel returns normally.
+__global__ void debug_wait_kernel(uint32_t* flags, long long max_cycles) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && !mbar_wait_bounded(&bar, 0u, max_cycles)) raise_flag(flags, L1S_ERR_TIMEOUT);
+}
+
+bool launch_debug_wait(uint32_t* flags, long long max_cycles, cudaStream_t st) {
+  debug_wait_kernel<<<1, 32, 0, st>>>(flags, max_cycles);
+  count_launch(1);
+  return cuda_ok(cudaGetLastError(), "launch debug_wait");
+}
+
 // ----------------------------------------------------------------- debug draws
 __global__ void debug_variates_kernel(Key2 key, uint32_t problem, uint32_t r1, int64_t row_start,
                                       int64_t count, int32_t* bh, int32_t* bi, int32_t* kh, int32_t* ki,

@@ -98,6 +98,7 @@ _SIGS = {
                                _P]),
     "l1s_batched_workspace_size": (C.c_int, [C.POINTER(Problem), _I32, C.POINTER(_SZ)]),
     "l1_regress_batched": (C.c_int, [C.POINTER(Problem), _I32, _P, _P, _SZ, _P]),
+    "l1s_debug_wait_timeout": (C.c_int, [_P, _SZ, _I64, _P]),
     "l1s_multi_workspace_size": (C.c_int, [_PP, _I64, _I32, _I32, C.c_int, C.POINTER(_SZ)]),
     "l1_coreset_multi": (C.c_int, [_P, _I64, C.c_int, _I64, _I32, _I32, _PP, _I64, _P, _P, _P, _P, _P, _SZ,
                                    _P]),
@@ -254,6 +255,11 @@ def l1_regress(A, b, params: Params, ws, inputs_on_host: bool = False, stream=No
     if rc in (1, 2, 3):
         _check(rc, "l1_regress")
     return x, obj.value, rows.value, rc
+
+
+def l1s_debug_wait_timeout(ws, max_cycles: int, stream=None) -> None:
+    _check(load().l1s_debug_wait_timeout(_ptr(ws), ws.numel(), int(max_cycles), _stream(stream)),
+           "l1s_debug_wait_timeout")
 
 
 def l1s_multi_workspace_size(params: Params, n: int, d: int, k: int, dtype: int = F32) -> int:

@@ -384,3 +384,24 @@ def test_coreset_host_inputs_chunked():
     assert np.array_equal(kg[~amb], (u < p)[~amb]), int((kg != (u < p)).sum())
     got = idx[:k].numpy()
     assert np.allclose(w[:k].numpy(), 1.0 / p[got], rtol=1e-3)
+
+
+def test_bounded_wait_raises_timeout_and_context_stays_usable():
+    """A bounded wait that nothing completes gives up, raises TIMEOUT and returns; the
+    next call on the same context runs normally (failure detection without a GPU fault)."""
+    prm = L.make_params(64, 40, 16, 300.0, seed=1)
+    n, d = 20000, 4
+    ws = L.workspace(prm, n, d)
+    L.l1s_status_reset(ws)
+    L.l1s_debug_wait_timeout(ws, 2_000_000)                     # about a millisecond
+    assert L.l1s_status_read(ws) == L.flag(9)
+    with pytest.raises(L.L1SError):
+        L.l1s_debug_wait_timeout(ws, 10)
+    pr = problem(n, d, seed=4)
+    A, b = to_device(pr)
+    cap = 2 * 300 + 64
+    idx = torch.empty(cap, dtype=torch.int64, device=DEV)
+    w = torch.empty(cap, dtype=torch.float64, device=DEV)
+    cnt = torch.zeros(1, dtype=torch.int64, device=DEV)
+    L.l1_coreset(A, b, prm, cap, idx, w, None, cnt, ws)
+    assert L.l1s_status_read(ws) == 0 and 0 < int(cnt.item()) <= cap
