@@ -295,11 +295,13 @@ L1S_API int l1s_debug_pi2(const l1s_params* params, int32_t q, double* pi2_dev, 
  * ------------------------------------------------------------------------- */
 typedef struct {
   int32_t fct_variant;       /* phase 1 kernel: 0 default, 1 warp-specialised narrow-X kernel
-                                (d ≤ 32, 32 ≤ s ≤ 512), 2 all columns with TMA-staged tiles,
-                                3 direct loads over column slices, 4 bucket-sorted scatter
-                                (d ≤ 32, 32 ≤ s ≤ 512), 5 the narrow-X kernel with one stage
-                                buffer and one copy of its partial (d ≤ 16).  A variant that
-                                does not apply to the shape falls back to the default. */
+                                (d ≤ 32, 2 ≤ s ≤ 512), 2 all columns with TMA-staged tiles,
+                                3 direct loads over column slices sized for two blocks per SM,
+                                4 bucket-sorted scatter (d ≤ 32, 32 ≤ s ≤ 512), 5 the narrow-X
+                                kernel with one stage buffer and one copy of its partial
+                                (d ≤ 16), 6 direct loads over the widest column slices that one
+                                block per SM allows.  A variant that does not apply to the
+                                shape falls back to the default. */
   int32_t fct_ctas_per_sm;   /* phase 1 resident blocks per SM (capped by occupancy); 0 = most */
   int32_t lam_ctas_per_sm;   /* λ pass blocks per SM, 1..32; 0 = 8 */
   int32_t smp_chunks_per_sm; /* sampling row chunks per SM, 1..16; 0 = 4 */

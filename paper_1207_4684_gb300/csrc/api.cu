@@ -238,13 +238,14 @@ static FctGeometry fct_geometry(int variant, const Plan& P, l1s_dtype dt, const 
     staged = true;
   } else {
     // Direct loads: the widest column slice whose shared-memory footprint allows two
-    // blocks per SM, or failing that one.
+    // blocks per SM, or failing that one (variant 6: the widest for one block per SM,
+    // fewer slices re-reading X and redrawing the row variates).
     int slices = 1;
     for (;; ++slices) {
       width = (P.q + slices - 1) / slices;
       if (fct_smem_bytes(P.s, P.d, dt, P.r1, width, false) <= budget2 || width == 1) break;
     }
-    if (fct_smem_bytes(P.s, P.d, dt, P.r1, width, false) > budget2) {
+    if (variant == 6 || fct_smem_bytes(P.s, P.d, dt, P.r1, width, false) > budget2) {
       for (slices = 1;; ++slices) {
         width = (P.q + slices - 1) / slices;
         if (fct_smem_bytes(P.s, P.d, dt, P.r1, width, false) <= budget1) break;
@@ -311,11 +312,11 @@ bool make_plan(const l1s_params* p, int64_t n, int d, l1s_dtype dt, bool host_st
   // columns in one block with TMA-staged X tiles, else direct loads over column slices.
   // The bucket-sorted kernel is a schedule choice (slower than the narrow-X kernel on the
   // shapes measured so far).
-  FctGeometry geo[6];
-  for (int v = 1; v <= 5; ++v) geo[v] = fct_geometry(v, P, dt, di);
+  FctGeometry geo[7];
+  for (int v = 1; v <= 6; ++v) geo[v] = fct_geometry(v, P, dt, di);
   if (!geo[3].ok) return set_error("r1 and s too large for shared memory"), false;
   int variant = geo[1].ok ? 1 : (geo[2].ok ? 2 : 3);
-  if (sch.fct_variant >= 1 && sch.fct_variant <= 5 && geo[sch.fct_variant].ok) variant = sch.fct_variant;
+  if (sch.fct_variant >= 1 && sch.fct_variant <= 6 && geo[sch.fct_variant].ok) variant = sch.fct_variant;
   const FctGeometry& g = geo[variant];
   P.fct_ws = g.ws;
   P.fct_tile_log2 = g.tile_log2;
@@ -338,7 +339,7 @@ bool make_plan(const l1s_params* p, int64_t n, int d, l1s_dtype dt, bool host_st
   }
   // Partial sums sized for the largest variant at full occupancy.
   size_t partial_floats = 0;
-  for (int v = 1; v <= 5; ++v)
+  for (int v = 1; v <= 6; ++v)
     if (geo[v].ok)
       partial_floats = std::max<size_t>(
           partial_floats, static_cast<size_t>(geo[v].slices) * fct_ctas_of(geo[v], P, di, geo[v].per_sm) *
