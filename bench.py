@@ -4,7 +4,12 @@ One step = fct_embed (Œ†1¬∑X), l1_condition (QR, M = R‚Åª¬πŒ†2) and l1_sample (Œ
 Œ£Œª, pÃÇ, Bernoulli keep, compaction, coreset gather) over the n = 2^22, d = 16
 workload (columns scaled by 10^U(‚àí2,2), Laplace noise with 5% Cauchy(0,100)
 outliers; s = 256, r1 = 355, r2 = 16, m_s = 20000), inputs resident in HBM.
-It prints one JSON line; see the design doc for the roofline figures it carries.
+It prints one JSON line: the step's rows/s (one step captured as a CUDA graph and
+replayed), the dominant kernel's algorithmic bytes per second against the measured
+HBM copy bandwidth and its issue rate, the end-to-end rate from pinned host memory,
+the other forms (OptimizedFastCauchyRegression, sampling with replacement, multiple
+regression, BF16 with tensor-core Œª, a batch of 256 problems) and the FP64 oracle's
+rate on the host cores.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
 
