@@ -450,6 +450,7 @@ int l1s_status_read(const void* ws, size_t ws_bytes, void* stream, uint32_t* fla
 
 int fct_embed(const void* A, int64_t lda, l1s_dtype dtype, const float* b, int64_t n, int32_t d,
               const l1s_params* params, float* PiX, void* ws, size_t ws_bytes, void* stream) {
+  TraceRange trace_("fct_embed");
   Plan pl;
   if (!make_plan(params, n, d, dtype, false, &pl)) return L1S_ERR_INVALID_ARG;
   if (!check_a(A, lda, b, d) || !PiX) return L1S_ERR_INVALID_ARG;
@@ -462,6 +463,7 @@ int fct_embed(const void* A, int64_t lda, l1s_dtype dtype, const float* b, int64
 
 int l1_condition(const float* PiX, int32_t r1, int32_t q, const l1s_params* params, double* R,
                  double* M, void* ws, size_t ws_bytes, void* stream) {
+  TraceRange trace_("l1_condition");
   if (!params || !PiX) return set_error("params and PiX must not be NULL"), L1S_ERR_INVALID_ARG;
   if (r1 != params->r1) return set_error("r1 must equal params->r1"), L1S_ERR_INVALID_ARG;
   Plan pl;
@@ -477,6 +479,7 @@ int l1_condition(const float* PiX, int32_t r1, int32_t q, const l1s_params* para
 int l1_lambda(const void* A, int64_t lda, l1s_dtype dtype, const float* b, int64_t n, int32_t d,
               const double* M, const l1s_params* params, float* lambda, double* lambda_sum, void* ws,
               size_t ws_bytes, void* stream) {
+  TraceRange trace_("l1_lambda");
   Plan pl;
   if (!make_plan(params, n, d, dtype, false, &pl)) return L1S_ERR_INVALID_ARG;
   if (!check_a(A, lda, b, d) || !M || !lambda) return set_error("M and lambda must not be NULL"), L1S_ERR_INVALID_ARG;
@@ -493,6 +496,7 @@ int l1_lambda(const void* A, int64_t lda, l1s_dtype dtype, const float* b, int64
 int l1_sample(const void* A, int64_t lda, l1s_dtype dtype, const float* b, int64_t n, int32_t d,
               const double* M, const l1s_params* params, int64_t capacity, int64_t* idx, double* wts,
               double* coreset, int64_t* count, float* lambda, void* ws, size_t ws_bytes, void* stream) {
+  TraceRange trace_("l1_sample");
   Plan pl;
   if (!make_plan(params, n, d, dtype, false, &pl)) return L1S_ERR_INVALID_ARG;
   if (!check_a(A, lda, b, d) || !M) return set_error("M must not be NULL"), L1S_ERR_INVALID_ARG;
@@ -524,6 +528,7 @@ int l1_sample_from_p(const double* p, int64_t n, const l1s_params* params, int64
 int l1_coreset(const void* A, int64_t lda, l1s_dtype dtype, const float* b, int64_t n, int32_t d,
                const l1s_params* params, int64_t capacity, int64_t* idx, double* wts, double* coreset,
                int64_t* count, void* ws, size_t ws_bytes, void* stream) {
+  TraceRange trace_("l1_coreset");
   Plan pl;
   if (!make_plan(params, n, d, dtype, false, &pl)) return L1S_ERR_INVALID_ARG;
   if (!check_a(A, lda, b, d)) return L1S_ERR_INVALID_ARG;
@@ -593,6 +598,7 @@ static int coreset_impl_host(const Plan& pl, const void* A_host, int64_t lda, l1
 int l1_coreset_host(const void* A_host, int64_t lda, l1s_dtype dtype, const float* b_host, int64_t n,
                     int32_t d, const l1s_params* params, int64_t capacity, int64_t* idx_host, double* w_host,
                     int64_t* count_host, void* ws, size_t ws_bytes, void* stream) {
+  TraceRange trace_("l1_coreset_host");
   Plan pl;
   if (!make_plan(params, n, d, dtype, true, &pl)) return L1S_ERR_INVALID_ARG;
   if (!check_a(A_host, lda, b_host, d) || !count_host || capacity < 0 ||
@@ -624,6 +630,7 @@ int l1_coreset_host(const void* A_host, int64_t lda, l1s_dtype dtype, const floa
 
 int l1_solve(const double* coreset, const double* wts, const int64_t* count, int64_t capacity, int32_t d,
              int32_t max_iter, double* x, double* objective, void* ws, size_t ws_bytes, void* stream) {
+  TraceRange trace_("l1_solve");
   if (!coreset || !wts || !count || !x || !objective) return set_error("NULL argument"), L1S_ERR_INVALID_ARG;
   if (d < 1 || d > kMaxD || capacity < 1 || max_iter < 0 || max_iter > 100000)
     return set_error("bad d, capacity or max_iter"), L1S_ERR_INVALID_ARG;
@@ -653,6 +660,7 @@ int l1_solve(const double* coreset, const double* wts, const int64_t* count, int
 
 int l1_objective(const void* A, int64_t lda, l1s_dtype dtype, const float* b, int64_t n, int32_t d,
                  const double* x, double* objective, void* ws, size_t ws_bytes, void* stream) {
+  TraceRange trace_("l1_objective");
   if (!check_a(A, lda, b, d) || !x || !objective || n < 1 || d < 1 || d > kMaxD)
     return set_error("bad arguments"), L1S_ERR_INVALID_ARG;
   const DeviceInfo di = device_info();
@@ -668,6 +676,7 @@ int l1_objective(const void* A, int64_t lda, l1s_dtype dtype, const float* b, in
 int l1_regress(const void* A, int64_t lda, l1s_dtype dtype, const float* b, int64_t n, int32_t d,
                const l1s_params* params, int32_t inputs_on_host, double* x_host, double* objective_host,
                int64_t* coreset_rows_host, void* ws, size_t ws_bytes, void* stream) {
+  TraceRange trace_("l1_regress");
   Plan pl;
   if (!make_plan(params, n, d, dtype, inputs_on_host != 0, &pl)) return L1S_ERR_INVALID_ARG;
   if (!check_a(A, lda, b, d) || !x_host || !objective_host) return set_error("NULL argument"), L1S_ERR_INVALID_ARG;

@@ -224,6 +224,7 @@ int l1s_batched_workspace_size(const l1s_problem* probs, int32_t count, size_t* 
 
 int l1_regress_batched(const l1s_problem* probs, int32_t count, uint32_t* flags_dev, void* ws, size_t ws_bytes,
                        void* stream) {
+  TraceRange trace_("l1_regress_batched");
   if (count < 0 || (count > 0 && !probs)) return set_error("bad arguments"), L1S_ERR_INVALID_ARG;
   if (count == 0) return L1S_OK;
   if (!ws || reinterpret_cast<uintptr_t>(ws) % 256 != 0)
@@ -276,6 +277,7 @@ int l1_regress_batched(const l1s_problem* probs, int32_t count, uint32_t* flags_
 
 int l1s_autotune(const l1s_problem* prob, int32_t trials, l1s_schedule* best, double* best_ms, void* ws,
                  size_t ws_bytes, void* stream) {
+  TraceRange trace_("l1s_autotune");
   if (!prob || !best || trials < 1 || trials > 1000) return set_error("bad arguments"), L1S_ERR_INVALID_ARG;
   if (!check_member(*prob, 0)) return L1S_ERR_INVALID_ARG;
   const l1s_problem& pr = *prob;

@@ -12,6 +12,8 @@
 #include <float.h>
 #include <stdint.h>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/l1fct.h"
 
 namespace l1s {
@@ -211,6 +213,14 @@ struct DeviceInfo {
 DeviceInfo device_info();
 
 void set_error(const char* fmt, ...);
+
+// A named range of an entry point on a profiler's timeline (NVTX; a no-op without a tool).
+struct TraceRange {
+  explicit TraceRange(const char* name) { nvtxRangePushA(name); }
+  ~TraceRange() { nvtxRangePop(); }
+  TraceRange(const TraceRange&) = delete;
+  TraceRange& operator=(const TraceRange&) = delete;
+};
 bool cuda_ok(cudaError_t e, const char* what);
 
 inline size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }

@@ -123,6 +123,7 @@ int l1s_multi_workspace_size(const l1s_params* params, int64_t n, int32_t d, int
 int l1_coreset_multi(const void* X, int64_t ldx, l1s_dtype dtype, int64_t n, int32_t d, int32_t k,
                      const l1s_params* params, int64_t capacity, int64_t* idx, double* wts, double* coreset,
                      int64_t* count, void* ws, size_t ws_bytes, void* stream) {
+  TraceRange trace_("l1_coreset_multi");
   MultiLayout M;
   if (!multi_layout(params, n, d, k, dtype, &M)) return L1S_ERR_INVALID_ARG;
   if (!check_x(X, ldx, d, k)) return L1S_ERR_INVALID_ARG;
@@ -137,6 +138,7 @@ int l1_coreset_multi(const void* X, int64_t ldx, l1s_dtype dtype, int64_t n, int
 int l1_regress_multi(const void* X, int64_t ldx, l1s_dtype dtype, int64_t n, int32_t d, int32_t k,
                      const l1s_params* params, int32_t max_iter, double* W_host, double* objectives_host,
                      int64_t* coreset_rows_host, void* ws, size_t ws_bytes, void* stream) {
+  TraceRange trace_("l1_regress_multi");
   MultiLayout M;
   if (!multi_layout(params, n, d, k, dtype, &M)) return L1S_ERR_INVALID_ARG;
   if (!check_x(X, ldx, d, k) || !W_host || !objectives_host) return set_error("NULL argument"), L1S_ERR_INVALID_ARG;
