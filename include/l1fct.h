@@ -352,9 +352,8 @@ L1S_API int l1s_batched_workspace_size(const l1s_problem* probs, int32_t count, 
  * captured into one CUDA graph and replayed.  λ reads M from shared memory
  * here, so concurrent problems do not share the constant bank.  flags_dev
  * (count uint32, may be NULL) receives each problem's status word.  Enqueues
- * only; `stream` sees every problem finished.  Members with params.variant = 2
- * (sampling with replacement) are rejected with L1S_ERR_INVALID_ARG: that form
- * runs one problem per call. */
+ * only; `stream` sees every problem finished.  The caller keeps every member's
+ * buffers alive until then. */
 L1S_API int l1_regress_batched(const l1s_problem* probs, int32_t count, uint32_t* flags_dev, void* ws,
                                size_t ws_bytes, void* stream);
 

@@ -135,8 +135,6 @@ static bool check_member(const l1s_problem& pr, int i) {
   if (pr.idx_dev && pr.capacity < 1) return set_error("problem %d: capacity must be >= 1", i), false;
   if (pr.coreset_dev && !pr.idx_dev) return set_error("problem %d: coreset_dev needs idx_dev and w_dev", i), false;
   if (pr.objective_dev && !pr.x_dev) return set_error("problem %d: objective_dev needs x_dev", i), false;
-  if (pr.params.variant == 2)
-    return set_error("problem %d: sampling with replacement (variant 2) runs one problem per call", i), false;
   return true;
 }
 

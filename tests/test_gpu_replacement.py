@@ -109,16 +109,36 @@ def test_replacement_argument_checks():
         L.l1s_workspace_size(L.make_params(64, 20, 16, 100.0, variant=2, sample_scale=1.0), 1000, 4)
 
 
-def test_replacement_is_rejected_in_batches():
-    """Sampling with replacement runs one problem per call: a batch member with variant 2
-    is an argument error, before anything is launched."""
-    pr = problem(3000, 4, seed=5)
-    A, b = to_device(pr)
-    prm = L.make_params(16, r1_for(4), 16, 100.0, seed=6, variant=2)
-    cap = 264
-    idx, w, _, cnt = buffers(cap, 5)
-    probs = [L.make_problem(A, b, prm, cap, idx, w, None, cnt)]
+def test_replacement_batch_members():
+    """Members of a batch drawing with replacement (M in shared memory, workspace slices):
+    each member's draws fall in the oracle's intervals of its own whole pass.  The
+    members' device inputs stay alive (in `data`) until the batch has run."""
+    members = [(30000, 8, 64, 16, 800), (12345, 16, 256, 16, 500), (5000, 4, 16, 16, 300)]
+    data, probs = [], []
+    for pid, (n, d, s, r2, m) in enumerate(members):
+        pr = problem(n, d, seed=300 + pid)
+        ref = pipeline.fast_cauchy_regression(pr["A"], pr["b"], s, r1_for(d), r2, float(m), seed=6,
+                                              problem_id=pid, solve_lp=False, variant=2)
+        A, b = to_device(pr)
+        prm = L.make_params(s, r1_for(d), r2, float(m), seed=6, problem_id=pid, variant=2)
+        cap = 2 * m + 64
+        idx, w, _, cnt = buffers(cap, d + 1)
+        data.append(dict(ref=ref, m=m, idx=idx, w=w, cnt=cnt, A=A, b=b))
+        probs.append(L.make_problem(A, b, prm, cap, idx, w, None, cnt))
     ws = L.batched_workspace(probs)
-    with pytest.raises(L.L1SError) as e:
-        L.l1_regress_batched(probs, ws)
-    assert e.value.code == 1 and "variant 2" in str(e.value)
+    flags = torch.zeros(len(probs), dtype=torch.int32, device=DEV)
+    L.l1_regress_batched(probs, ws, flags)
+    torch.cuda.synchronize()
+    assert int(flags.abs().sum().item()) == 0
+    for pid, e in enumerate(data):
+        m = e["m"]
+        assert int(e["cnt"].item()) == m
+        got = e["idx"][:m].cpu().numpy()
+        cdf = np.cumsum(e["ref"]["lam"])
+        total = cdf[-1]
+        tgt = rng.replacement_uniforms(6, pid, np.arange(m)) * total
+        lo = np.where(got > 0, cdf[np.maximum(got - 1, 0)], 0.0)
+        delta = 1e-5 * total
+        assert np.all((lo - delta <= tgt) & (tgt < cdf[got] + delta)), pid
+        assert (got == e["ref"]["idx"]).mean() >= 0.9, pid
+        assert np.allclose(e["w"][:m].cpu().numpy(), total / (m * e["ref"]["lam"][got]), rtol=1e-4), pid
