@@ -57,7 +57,7 @@ def build(verbose: bool = False, force: bool = False) -> str:
         newest = max(os.path.getmtime(p) for p in deps)
         if os.path.getmtime(LIB) >= newest:
             return LIB
-    with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
+    with cf.ThreadPoolExecutor(max_workers=max(1, min(len(srcs), os.cpu_count() or 1))) as ex:
         objs = list(ex.map(lambda s: _compile(s, verbose), srcs))
     tmp = LIB + ".tmp"
     cmd = [nvcc(), *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs]
