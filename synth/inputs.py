@@ -124,6 +124,51 @@ def _noise(rng: np.random.Generator, w: Workload, n: int) -> np.ndarray:
     return e
 
 
+# Workloads at least this tall are drawn chunk-parallel (see make_problem).
+PARALLEL_ROWS = 1 << 25
+
+
+def _chunk(rng, w: Workload, m: int, x_star: np.ndarray):
+    a = _design(rng, w, m)
+    if w.dtype == "bf16":
+        bits = f32_to_bf16_bits(a)
+        a_stored = bf16_bits_to_f32(bits)
+        stored = bits
+    elif w.dtype == "f32":
+        a_stored = a
+        stored = a
+    else:
+        raise ValueError(w.dtype)
+    e = _noise(rng, w, m)
+    b = a_stored.astype(np.float64) @ x_star + e
+    return stored, b.astype(np.float32)
+
+
+def _make_parallel(w: Workload, chunk: int) -> dict:
+    """Rows in chunks of `chunk`; chunk k is drawn from the k-th child of
+    SeedSequence(seed), x* from PCG64(seed), so the result does not depend on how many
+    threads draw the chunks."""
+    import concurrent.futures as cf
+    import os
+
+    x_star = np.random.Generator(np.random.PCG64(w.seed)).standard_normal(w.d)
+    nchunks = -(-w.n // chunk)
+    kids = np.random.SeedSequence(w.seed).spawn(nchunks)
+    A = np.empty((w.n, w.d), dtype=np.uint16 if w.dtype == "bf16" else np.float32)
+    b = np.empty(w.n, dtype=np.float32)
+
+    def fill(k):
+        lo = k * chunk
+        m = min(chunk, w.n - lo)
+        a_k, b_k = _chunk(np.random.Generator(np.random.PCG64(kids[k])), w, m, x_star)
+        A[lo:lo + m] = a_k
+        b[lo:lo + m] = b_k
+
+    with cf.ThreadPoolExecutor(max_workers=max(1, min(16, os.cpu_count() or 1))) as ex:
+        list(ex.map(fill, range(nchunks)))
+    return {"A": A, "b": b, "x_star": x_star, "w": w}
+
+
 def make_problem(w: Workload | str, n: int | None = None, seed: int | None = None,
                  chunk: int = 1 << 22) -> dict:
     """Generate (A, b) for a workload.
@@ -133,6 +178,10 @@ def make_problem(w: Workload | str, n: int | None = None, seed: int | None = Non
       b      (n,) float32, b = A·x* + noise computed in float64 from the stored A
       x_star (d,) float64 planted solution
       w      the Workload (with n overridden if given)
+
+    Workloads of PARALLEL_ROWS rows or more are drawn chunk by chunk from independent
+    child seeds on several threads (one sequential stream would take minutes at 2^26
+    rows); smaller ones from one sequential PCG64 stream.
     """
     if isinstance(w, str):
         w = WORKLOADS[w]
@@ -140,6 +189,8 @@ def make_problem(w: Workload | str, n: int | None = None, seed: int | None = Non
         w = w.with_n(n)
     if seed is not None:
         w = replace(w, seed=int(seed))
+    if w.n >= PARALLEL_ROWS:
+        return _make_parallel(w, chunk)
     rng = np.random.Generator(np.random.PCG64(w.seed))
     x_star = rng.standard_normal(w.d)
     n_total = w.n
@@ -147,19 +198,9 @@ def make_problem(w: Workload | str, n: int | None = None, seed: int | None = Non
     done = 0
     while done < n_total:
         m = min(chunk, n_total - done)
-        a = _design(rng, w, m)
-        if w.dtype == "bf16":
-            bits = f32_to_bf16_bits(a)
-            a_stored = bf16_bits_to_f32(bits)
-            a_parts.append(bits)
-        elif w.dtype == "f32":
-            a_stored = a
-            a_parts.append(a)
-        else:
-            raise ValueError(w.dtype)
-        e = _noise(rng, w, m)
-        b = a_stored.astype(np.float64) @ x_star + e
-        b_parts.append(b.astype(np.float32))
+        a_k, b_k = _chunk(rng, w, m, x_star)
+        a_parts.append(a_k)
+        b_parts.append(b_k)
         done += m
     A = a_parts[0] if len(a_parts) == 1 else np.concatenate(a_parts, axis=0)
     b = b_parts[0] if len(b_parts) == 1 else np.concatenate(b_parts)
