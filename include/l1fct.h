@@ -300,8 +300,10 @@ typedef struct {
                                 4 bucket-sorted scatter (d ≤ 32, 32 ≤ s ≤ 512), 5 the narrow-X
                                 kernel with one stage buffer and one copy of its partial
                                 (d ≤ 16), 6 direct loads over the widest column slices that one
-                                block per SM allows.  A variant that does not apply to the
-                                shape falls back to the default. */
+                                block per SM allows, 7 the column-sliced wide-X kernel (16
+                                columns of A per block, one block per SM, s ≤ 1024, the b column
+                                in a kernel of its own; the default for d > 32).  A variant that
+                                does not apply to the shape falls back to the default. */
   int32_t fct_ctas_per_sm;   /* phase 1 resident blocks per SM (capped by occupancy); 0 = most */
   int32_t lam_ctas_per_sm;   /* λ pass blocks per SM, 1..32; 0 = 8 */
   int32_t smp_chunks_per_sm; /* sampling row chunks per SM, 1..16; 0 = 4 */

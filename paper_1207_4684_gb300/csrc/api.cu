@@ -26,6 +26,12 @@ int fct_sorted_width(int log2s, int d);
 const void* fct_sorted_kernel(int log2s, l1s_dtype dt, int w);
 int fct_sorted_threads(int w);
 size_t fct_sorted_smem_bytes(int s, int d, l1s_dtype dt, int r1, int w);
+int fct_cols_slices(int log2s, int d, int r1, int max_smem);
+size_t fct_cols_smem_bytes(int r1);
+int fct_cols_threads();
+int fct_cols_tile();
+const void* fct_cols_kernel(l1s_dtype dt);
+size_t fct_cols_partial_floats(int slices, int ctas, int r1, int64_t n);
 bool launch_fct(const Plan& pl, const void* A, int64_t lda, l1s_dtype dt, const float* b,
                 const l1s_params* p, float* pix, unsigned char* ws, cudaStream_t st, double* pi2_out = nullptr);
 bool launch_fct_streamed(const Plan& pl, const void* A_host, int64_t lda_host, l1s_dtype dt, const float* b_host,
@@ -208,6 +214,7 @@ struct FctGeometry {
   int tile_log2;          // its tile
   bool lean;              // its one-stage, one-copy form
   int sorted;             // column width of the bucket-sorted kernel, 0 otherwise
+  int cols;               // slices of the column-sliced wide-X kernel, 0 otherwise
   int slices, width, threads, per_sm;
   size_t smem;
 };
@@ -218,6 +225,28 @@ static FctGeometry fct_geometry(int variant, const Plan& P, l1s_dtype dt, const 
   const size_t budget1 = di.max_smem_optin;
   int width = P.q;
   bool staged = false;
+  if (variant == 7) {
+    // The column-sliced wide-X kernel: 16 columns of A per block, one block per SM.
+    const int sl = P.d > 16 ? fct_cols_slices(P.log2s, P.d, P.r1, di.max_smem_optin) : 0;
+    if (!sl) return g;
+    g.cols = sl;
+    g.tile_log2 = 10;
+    g.slices = sl;
+    g.width = 16;
+    g.smem = fct_cols_smem_bytes(P.r1);
+    g.threads = fct_cols_threads();
+    const void* fn = fct_cols_kernel(dt);
+    if (!cuda_ok(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(g.smem)),
+                 "cudaFuncSetAttribute(fct_embed_cols)"))
+      return g;
+    int per_sm = 0;
+    if (!cuda_ok(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, g.threads, g.smem), "occupancy(fct_cols)") ||
+        per_sm < 1)
+      return g;
+    g.per_sm = per_sm;
+    g.ok = true;
+    return g;
+  }
   if (variant == 4) {
     const int w = fct_sorted_width(P.log2s, P.d);
     if (!w || fct_sorted_smem_bytes(P.s, P.d, dt, P.r1, w) > budget1) return g;
@@ -277,7 +306,7 @@ static FctGeometry fct_geometry(int variant, const Plan& P, l1s_dtype dt, const 
 
 static int64_t fct_ctas_of(const FctGeometry& g, const Plan& P, const DeviceInfo& di, int per_sm) {
   const int64_t want = std::max<int64_t>(1, static_cast<int64_t>(di.sms) * per_sm / g.slices);
-  const int64_t tiles = g.ws ? (P.n + (int64_t{1} << g.tile_log2) - 1) >> g.tile_log2 : P.nblocks;
+  const int64_t tiles = (g.ws || g.cols) ? (P.n + (int64_t{1} << g.tile_log2) - 1) >> g.tile_log2 : P.nblocks;
   return std::min<int64_t>(tiles, want);
 }
 
@@ -312,16 +341,18 @@ bool make_plan(const l1s_params* p, int64_t n, int d, l1s_dtype dt, bool host_st
   // columns in one block with TMA-staged X tiles, else direct loads over column slices.
   // The bucket-sorted kernel is a schedule choice (slower than the narrow-X kernel on the
   // shapes measured so far).
-  FctGeometry geo[7];
-  for (int v = 1; v <= 6; ++v) geo[v] = fct_geometry(v, P, dt, di);
+  FctGeometry geo[8];
+  for (int v = 1; v <= 7; ++v) geo[v] = fct_geometry(v, P, dt, di);
   if (!geo[3].ok) return set_error("r1 and s too large for shared memory"), false;
-  int variant = geo[1].ok ? 1 : (geo[2].ok ? 2 : 3);
-  if (sch.fct_variant >= 1 && sch.fct_variant <= 6 && geo[sch.fct_variant].ok) variant = sch.fct_variant;
+  // Wide X (d > 32): the column-sliced kernel where it fits.
+  int variant = geo[1].ok ? 1 : (geo[2].ok ? 2 : (P.d > 32 && geo[7].ok ? 7 : 3));
+  if (sch.fct_variant >= 1 && sch.fct_variant <= 7 && geo[sch.fct_variant].ok) variant = sch.fct_variant;
   const FctGeometry& g = geo[variant];
   P.fct_ws = g.ws;
   P.fct_tile_log2 = g.tile_log2;
   P.fct_lean = g.lean ? 1 : 0;
   P.fct_sorted = g.sorted;
+  P.fct_cols = g.cols;
   P.fct_staged = g.staged ? 1 : 0;
   P.fct_slices = g.slices;
   P.fct_width = g.width;
@@ -333,17 +364,20 @@ bool make_plan(const l1s_params* p, int64_t n, int d, l1s_dtype dt, bool host_st
   // tiles each, so that phase 1 on one chunk overlaps the copy of the next.
   P.fct_chunks = 1;
   if (host_staging) {
-    const int64_t tiles = g.ws ? (n + (int64_t{1} << g.tile_log2) - 1) >> g.tile_log2 : P.nblocks;
+    const int64_t tiles = (g.ws || g.cols) ? (n + (int64_t{1} << g.tile_log2) - 1) >> g.tile_log2 : P.nblocks;
     P.fct_chunks = static_cast<int>(
         std::max<int64_t>(1, std::min<int64_t>(kMaxChunks, tiles / (2 * static_cast<int64_t>(P.fct_ctas)))));
   }
   // Partial sums sized for the largest variant at full occupancy.
   size_t partial_floats = 0;
-  for (int v = 1; v <= 6; ++v)
+  for (int v = 1; v <= 7; ++v)
     if (geo[v].ok)
       partial_floats = std::max<size_t>(
-          partial_floats, static_cast<size_t>(geo[v].slices) * fct_ctas_of(geo[v], P, di, geo[v].per_sm) *
-                              P.r1 * geo[v].width);
+          partial_floats,
+          geo[v].cols ? fct_cols_partial_floats(geo[v].cols, static_cast<int>(fct_ctas_of(geo[v], P, di, geo[v].per_sm)),
+                                                P.r1, n)
+                      : static_cast<size_t>(geo[v].slices) * fct_ctas_of(geo[v], P, di, geo[v].per_sm) * P.r1 *
+                            geo[v].width);
 
   // Phase 2: a persistent-style grid, 8 blocks per SM by default.
   P.lam_threads = lambda_threads();

@@ -54,7 +54,7 @@ bool schedule_lookup(int d, l1s_dtype dt, int log2s, l1s_schedule* out) {
 }
 
 static bool valid_schedule(const l1s_schedule& s) {
-  return s.fct_variant >= 0 && s.fct_variant <= 6 && s.fct_ctas_per_sm >= 0 && s.fct_ctas_per_sm <= 64 &&
+  return s.fct_variant >= 0 && s.fct_variant <= 7 && s.fct_ctas_per_sm >= 0 && s.fct_ctas_per_sm <= 64 &&
          s.lam_ctas_per_sm >= 0 && s.lam_ctas_per_sm <= 32 && s.smp_chunks_per_sm >= 0 &&
          s.smp_chunks_per_sm <= 16;
 }
@@ -330,17 +330,18 @@ int l1s_autotune(const l1s_problem* prob, int32_t trials, l1s_schedule* best, do
     }
   };
   int v3_slices = 0;
-  for (int v = 1; v <= 6; ++v) {
+  for (int v = 1; v <= 7; ++v) {
     l1s_schedule c = cur;
     c.fct_variant = v;
     Plan probe;
     if (!make_plan(&pr.params, pr.n, pr.d, pr.dtype, false, &probe, &c)) continue;
-    const bool plain = !probe.fct_ws && !probe.fct_sorted;
+    const bool plain = !probe.fct_ws && !probe.fct_sorted && !probe.fct_cols;
     if (v == 3 && plain && !probe.fct_staged) v3_slices = probe.fct_slices;
     const bool applies = (v == 4 && probe.fct_sorted) || (v == 1 && probe.fct_ws && !probe.fct_lean) ||
                          (v == 5 && probe.fct_lean) ||
                          (v == 2 && plain && probe.fct_staged) || (v == 3 && plain && !probe.fct_staged) ||
-                         (v == 6 && plain && !probe.fct_staged && probe.fct_slices < v3_slices);
+                         (v == 6 && plain && !probe.fct_staged && probe.fct_slices < v3_slices) ||
+                         (v == 7 && probe.fct_cols);
     if (!applies) continue;
     for (int per = 1; per <= 4; ++per) {
       c.fct_ctas_per_sm = per;

@@ -1,0 +1,433 @@
+// Phase 1 for wide X: the FCT1 embedding Π1·X = 4·B·C·H̃·D·X (§3.1, FCT1 construction;
+// Figure 2, steps 1-2) when the r1 × q partial of Π1X does not fit one thread block's
+// shared memory (16 < d ≤ 128, s ≤ 1024, r1 ≤ 2300).
+//
+// The columns of A are cut into slices of 16; a thread block owns one slice and keeps
+// that slice's r1 × 16 FP32 partial of Π1X in shared memory (B's hashed sum is a
+// shared-memory reduction, no global atomics).  Blocks of one slice walk the tiles of
+// 1024 rows (each tile holds 1024/s blocks of H_s) in a grid stride; there is one block
+// per SM, and a slice's blocks read only its 16 columns of every row, so X crosses HBM
+// once.  Per tile, in a block of 16 warps:
+//   * the rows' values arrive straight in registers (coalesced loads issued one tile
+//     ahead, so the transfer of tile t+1 overlaps the arithmetic of tile t; no staging
+//     buffer, which leaves the shared memory to the partial);
+//   * pass 1: a half-warp holds one 16-column row group (rows g, g+32, …, g+992 of the
+//     tile; lanes are the columns); it scatters the identity half of G_s = [H_s; I_s]
+//     (P[h_I(i)][c] += 4·c_I(i)·σ_i·x_ic), applies σ, runs the butterflies over row bits
+//     5-9 in registers and stores the tile;
+//   * pass 2: a half-warp reads 32 consecutive rows of the tile (row bits 0-4 in
+//     registers), runs those butterflies and scatters the Hadamard half
+//     (P[h_H(i)][c] += 4·c_H(i)/√s·(H_s z)_ic);
+//   * the threads draw the next tile's signs, buckets and Cauchy scales (one Philox call
+//     per row, counter = global row id) while the atomics of the current passes drain.
+// Every slice redraws the row variates: the bound of this kernel is the shared-memory
+// FP32 atomic rate (two atomics per element), and the draws run on the ALUs beside it.
+// The tile and the draws are padded by 16 words / one entry after every 32 rows, so that
+// both passes read and write them without bank conflicts.
+//
+// The b column (−b, the last column of X) is transformed by a second, light kernel: one
+// warp per tile of 1024 rows, lane l holding rows l + 32k; it draws its own rows, runs the
+// butterflies over k in registers and over l by shuffles, and scatters both halves into
+// its block's r1-entry partial.
+#include <algorithm>
+
+#include "l1s_common.cuh"
+
+namespace l1s {
+
+constexpr int kColW = 16;                                   // columns of A per slice
+constexpr int kColT = 1024;                                 // rows per tile
+constexpr int kColAWarps = 16;
+constexpr int kColThreads = 32 * kColAWarps;
+constexpr int kBcolThreads = 256;                           // b-column kernel: 8 warps, one tile each
+constexpr int kColJ = 32;                                   // rows per thread in each pass
+constexpr int kColTileWords = kColT * kColW + (kColT / 32) * kColW;
+constexpr int kColMeta = kColT + kColT / 32;
+
+static_assert(kColT == 2 * kColAWarps * kColJ, "a pass covers the tile once");
+
+struct ColsArgs {
+  const void* A;
+  int64_t lda;
+  const float* b;
+  int64_t n;
+  int d, r1, nslices;
+  int log2s;
+  float inv_sqrt_s;
+  int64_t ntiles;
+  Key2 key;
+  uint32_t problem;
+  int64_t row_offset;
+  int sign_flip;
+  float* partials;      // [nslices][gridDim.x][r1][16]
+  float* partials_b;    // b-column kernel: [its blocks][r1]
+  int accumulate;       // 1: add to the partials of an earlier launch over other rows
+};
+
+__device__ __forceinline__ int col_tile_off(int row, int c) { return row * kColW + c + ((row >> 5) << 4); }
+__device__ __forceinline__ int col_meta(int row) { return row + (row >> 5); }
+
+template <typename TA>
+__device__ __forceinline__ uint32_t col_ld(const TA* p) {
+  if constexpr (sizeof(TA) == 4) return __float_as_uint(__ldcs(p));
+  else return static_cast<uint32_t>(__ldcs(reinterpret_cast<const unsigned short*>(p))) << 16;
+}
+
+// One pass-1/pass-2 step over tile t of this block's slice; x holds t's values (raw FP32
+// bits), xn receives tile t + stride's (loads issued here, consumed by the next step).
+template <typename TA>
+struct ColsBlock {
+  const ColsArgs& a;
+  float* P;
+  float* tile;
+  float2* mI;           // {4·c_I·σ, bits (h_I << 1) | [σ = −1]}
+  float2* mH;           // {4·c_H/√s, bits h_H}
+  int slice, c, hw;
+  bool live;
+
+  __device__ __forceinline__ void load(int64_t t, uint32_t (&x)[kColJ]) const {
+    if (t >= a.ntiles) return;
+    const int64_t r0 = t * kColT;
+    const TA* A = static_cast<const TA*>(a.A) + slice * kColW + c;
+#pragma unroll
+    for (int j = 0; j < kColJ; ++j) {
+      const int64_t row = r0 + hw + 32 * j;
+      x[j] = (live && row < a.n) ? col_ld<TA>(A + row * a.lda) : 0u;
+    }
+  }
+
+  // Draws of tile-row r of tile t: the identity and Hadamard entries of both halves.
+  __device__ __forceinline__ void draw(int64_t t, int r, float2& mi, float2& mh) const {
+    const uint64_t grow = static_cast<uint64_t>(a.row_offset + t * kColT + r);
+    const uint4 o = draw_row(a.key, grow, a.problem, kStreamFct);
+    const bool neg = a.sign_flip && (o.w & 1u);
+    const float wI = 4.f * cauchy_f32(o.w >> 8);
+    mi = make_float2(neg ? -wI : wI, __uint_as_float((static_cast<uint32_t>(bucket_of(o.z, a.r1)) << 1) | (neg ? 1u : 0u)));
+    mh = make_float2(4.f * cauchy_f32(o.y >> 8) * a.inv_sqrt_s, __uint_as_float(static_cast<uint32_t>(bucket_of(o.x, a.r1))));
+  }
+
+  __device__ __forceinline__ void step(int64_t t, uint32_t (&x)[kColJ], uint32_t (&xn)[kColJ]) const {
+    const int lg = a.log2s;
+    const int64_t tn = t + gridDim.x;
+    const int tid = threadIdx.x;
+    __syncthreads();                                     // draws of t visible; the tile is free
+    load(tn, xn);
+    float2 mi0 = make_float2(0.f, 0.f), mh0 = mi0, mi1 = mi0, mh1 = mi0;
+    {
+      // ---- pass 1: identity scatter, σ, butterflies over row bits 5-9, tile store
+      float* Pc = P + c;
+#pragma unroll
+      for (int j = 0; j < kColJ; ++j) {
+        const float2 m = mI[col_meta(hw + 32 * j)];
+        const uint32_t code = __float_as_uint(m.y);
+        const float xv = __uint_as_float(x[j]);
+        if (live) atomicAdd(Pc + (code >> 1) * kColW, m.x * xv);
+        x[j] = x[j] ^ (code << 31);                      // z = σ·x (raw bits)
+      }
+      float v[kColJ];
+#pragma unroll
+      for (int j = 0; j < kColJ; ++j) v[j] = __uint_as_float(x[j]);
+#pragma unroll
+      for (int b = 0; b < 5; ++b)
+        if (5 + b < lg)
+#pragma unroll
+          for (int j = 0; j < kColJ; ++j)
+            if ((j & (1 << b)) == 0) {
+              const float lo = v[j], hi = v[j | (1 << b)];
+              v[j] = lo + hi;
+              v[j | (1 << b)] = lo - hi;
+            }
+#pragma unroll
+      for (int j = 0; j < kColJ; ++j) tile[col_tile_off(hw + 32 * j, c)] = v[j];
+      if (tn < a.ntiles) draw(tn, tid, mi0, mh0);      // the next tile's draws, first row
+    }
+    __syncthreads();                                     // the tile holds pass 1; mI of t is free
+    if (tn < a.ntiles) mI[col_meta(tid)] = mi0;
+    {
+      // ---- pass 2: butterflies over row bits 0-4, Hadamard scatter
+      float v[kColJ];
+#pragma unroll
+      for (int i = 0; i < kColJ; ++i) v[i] = tile[col_tile_off(32 * hw + i, c)];
+#pragma unroll
+      for (int b = 0; b < 5; ++b)
+        if (b < lg)
+#pragma unroll
+          for (int i = 0; i < kColJ; ++i)
+            if ((i & (1 << b)) == 0) {
+              const float lo = v[i], hi = v[i | (1 << b)];
+              v[i] = lo + hi;
+              v[i | (1 << b)] = lo - hi;
+            }
+      if (live) {
+        float* Pc = P + c;
+#pragma unroll
+        for (int i = 0; i < kColJ; ++i) {
+          const float2 m = mH[col_meta(32 * hw + i)];
+          atomicAdd(Pc + __float_as_uint(m.y) * kColW, m.x * v[i]);
+        }
+      }
+      if (tn < a.ntiles) draw(tn, tid + kColT / 2, mi1, mh1);   // second row
+    }
+    __syncthreads();                                     // pass 2 done: mH of t and the tile are free
+    if (tn < a.ntiles) {
+      mH[col_meta(tid)] = mh0;
+      mI[col_meta(tid + kColT / 2)] = mi1;
+      mH[col_meta(tid + kColT / 2)] = mh1;
+    }
+  }
+};
+
+template <typename TA>
+__global__ void __launch_bounds__(kColThreads, 1) fct_embed_cols_kernel(const ColsArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int r1 = a.r1;
+  float* P = reinterpret_cast<float*>(smem_raw);                 // [r1][16]
+  float* tile = P + r1 * kColW;                                  // padded [1024][16]
+  float2* mI = reinterpret_cast<float2*>(tile + kColTileWords);  // padded [1024]
+  float2* mH = mI + kColMeta;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int slice = blockIdx.y;
+  const int wcols = min(kColW, a.d - slice * kColW);
+  ColsBlock<TA> blk{a, P, tile, mI, mH, slice, lane & 15, 2 * warp + (lane >> 4), (lane & 15) < wcols};
+  for (int i = tid; i < r1 * kColW; i += blockDim.x) P[i] = 0.f;
+  const int64_t t0 = blockIdx.x;
+  if (t0 < a.ntiles)
+    for (int r = tid; r < kColT; r += kColThreads) {
+      float2 mi, mh;
+      blk.draw(t0, r, mi, mh);
+      mI[col_meta(r)] = mi;
+      mH[col_meta(r)] = mh;
+    }
+  uint32_t xa[kColJ], xb[kColJ];
+  blk.load(t0, xa);
+#pragma unroll 1
+  for (int64_t t = t0; t < a.ntiles; t += 2 * static_cast<int64_t>(gridDim.x)) {
+    blk.step(t, xa, xb);
+    if (t + gridDim.x >= a.ntiles) break;
+    blk.step(t + gridDim.x, xb, xa);
+  }
+  __syncthreads();
+  // Non-finite input shows up as a non-finite partial (checked in the reduction).
+  const size_t cta = static_cast<size_t>(slice) * gridDim.x + blockIdx.x;
+  float* out = a.partials + cta * r1 * kColW;
+  for (int i = tid; i < r1 * kColW; i += blockDim.x) out[i] = (a.accumulate ? out[i] : 0.f) + P[i];
+}
+
+// The b column of X (−b): warp w of the grid transforms tiles w, w + warps, … of 1024 rows.
+// Lane l holds rows l + 32k (k < 32) and draws them itself; the Hadamard entries wait in
+// a per-warp shared-memory table until the transform is done.
+__global__ void __launch_bounds__(kBcolThreads) fct_embed_bcol_kernel(const ColsArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int r1 = a.r1;
+  float* Pb = reinterpret_cast<float*>(smem_raw);                           // [r1]
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  float2* mH = reinterpret_cast<float2*>(Pb + ((r1 + 3) & ~3)) + warp * kColT;   // [32 k][32 lanes]
+  for (int i = tid; i < r1; i += blockDim.x) Pb[i] = 0.f;
+  __syncthreads();
+  const int lg = a.log2s;
+  const int64_t nwarps = static_cast<int64_t>(gridDim.x) * (kBcolThreads / 32);
+  for (int64_t t = static_cast<int64_t>(blockIdx.x) * (kBcolThreads / 32) + warp; t < a.ntiles; t += nwarps) {
+    const int64_t r0 = t * kColT;
+    float v[kColJ];
+#pragma unroll
+    for (int k = 0; k < kColJ; ++k) {
+      const int64_t row = r0 + lane + 32 * k;
+      v[k] = row < a.n ? -__ldcs(a.b + row) : 0.f;
+    }
+#pragma unroll
+    for (int k = 0; k < kColJ; ++k) {
+      const uint4 o = draw_row(a.key, static_cast<uint64_t>(a.row_offset + r0 + lane + 32 * k), a.problem, kStreamFct);
+      const bool neg = a.sign_flip && (o.w & 1u);
+      const float wI = 4.f * cauchy_f32(o.w >> 8);
+      if (neg) v[k] = -v[k];                                                 // z = σ·x
+      atomicAdd(Pb + bucket_of(o.z, r1), wI * v[k]);                        // identity half
+      mH[k * 32 + lane] = make_float2(4.f * cauchy_f32(o.y >> 8) * a.inv_sqrt_s,
+                                      __uint_as_float(static_cast<uint32_t>(bucket_of(o.x, r1))));
+    }
+#pragma unroll
+    for (int b = 0; b < 5; ++b)
+      if (5 + b < lg)
+#pragma unroll
+        for (int k = 0; k < kColJ; ++k)
+          if ((k & (1 << b)) == 0) {
+            const float lo = v[k], hi = v[k | (1 << b)];
+            v[k] = lo + hi;
+            v[k | (1 << b)] = lo - hi;
+          }
+#pragma unroll
+    for (int b = 0; b < 5; ++b)
+      if (b < lg) {
+        const bool upper = (lane >> b) & 1;
+#pragma unroll
+        for (int k = 0; k < kColJ; ++k) {
+          const float o = __shfl_xor_sync(0xffffffffu, v[k], 1 << b);
+          v[k] = upper ? (o - v[k]) : (v[k] + o);
+        }
+      }
+#pragma unroll
+    for (int k = 0; k < kColJ; ++k) {
+      const float2 m = mH[k * 32 + lane];
+      atomicAdd(Pb + __float_as_uint(m.y), m.x * v[k]);                      // Hadamard half
+    }
+  }
+  __syncthreads();
+  float* out = a.partials_b + static_cast<size_t>(blockIdx.x) * r1;
+  for (int i = tid; i < r1; i += blockDim.x) out[i] = (a.accumulate ? out[i] : 0.f) + Pb[i];
+}
+
+// Fixed-order sum of the per-block partials: Π1X[r][16·k + c] = Σ_g partial[k][g][r][c]
+// (y-block k < slices) and Π1X[r][d] = Σ_g partial_b[g][r] over the b-column kernel's
+// blocks (y-block k = slices).
+// Warp w adds partials w, w + 32, …; warp 0 then adds the 32 warp sums in order.  Π2
+// (q × r2 FP64) is drawn here too, as in the other phase-1 reduction.
+__global__ void __launch_bounds__(1024) fct_reduce_cols_kernel(const float* __restrict__ partials,
+                                                               const float* __restrict__ partials_b, int ctas,
+                                                               int ctas_b, int slices, int r1, int d,
+                                                               float* __restrict__ pix,
+                                                               uint32_t* flags, Key2 key, uint32_t problem, int npi2,
+                                                               int r2, int pi2_gauss, int neg_lo, int neg_hi,
+                                                               double* __restrict__ pi2) {
+  if (pi2 && blockIdx.y == 0)
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < npi2; e += gridDim.x * blockDim.x) {
+      const double v = pi2_value(key, problem, e, pi2_gauss);
+      const int row = e / r2;
+      pi2[e] = (row >= neg_lo && row < neg_hi) ? -v : v;
+    }
+  __shared__ float red[32][33];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const bool bcol = static_cast<int>(blockIdx.y) == slices;
+  const int per = bcol ? r1 : r1 * kColW;
+  const int nparts = bcol ? ctas_b : ctas;
+  const float* base0 = bcol ? partials_b : partials + static_cast<size_t>(blockIdx.y) * ctas * per;
+  const int e = blockIdx.x * 32 + lane;
+  float acc = 0.f;
+  if (e < per) {
+    const float* base = base0 + e;
+    int c = warp;
+    for (; c + 96 < nparts; c += 128) {
+      const float v0 = base[static_cast<size_t>(c) * per];
+      const float v1 = base[static_cast<size_t>(c + 32) * per];
+      const float v2 = base[static_cast<size_t>(c + 64) * per];
+      const float v3 = base[static_cast<size_t>(c + 96) * per];
+      acc += v0;
+      acc += v1;
+      acc += v2;
+      acc += v3;
+    }
+    for (; c < nparts; c += 32) acc += base[static_cast<size_t>(c) * per];
+  }
+  red[warp][lane] = acc;
+  __syncthreads();
+  if (warp == 0 && e < per) {
+    float s = 0.f;
+#pragma unroll 8
+    for (int k = 0; k < 32; ++k) s += red[k][lane];
+    const int q = d + 1;
+    int r, col;
+    if (bcol) {
+      r = e;
+      col = d;
+    } else {
+      r = e / kColW;
+      col = blockIdx.y * kColW + (e - r * kColW);
+    }
+    if (col < q && (bcol || col < d)) {
+      pix[static_cast<size_t>(r) * q + col] = s;
+      if (!isfinite(s)) raise_flag(flags, L1S_ERR_NONFINITE);
+    }
+  }
+}
+
+// ----------------------------------------------------------------- host side
+size_t fct_cols_smem_bytes(int r1) {
+  return static_cast<size_t>(r1) * kColW * 4 + static_cast<size_t>(kColTileWords) * 4 +
+         2 * static_cast<size_t>(kColMeta) * sizeof(float2);
+}
+
+static size_t bcol_smem_bytes(int r1) {
+  return static_cast<size_t>((r1 + 3) & ~3) * 4 + static_cast<size_t>(kBcolThreads / 32) * kColT * sizeof(float2);
+}
+
+int fct_cols_slices(int log2s, int d, int r1, int max_smem) {
+  if (log2s > 10 || d <= 0) return 0;
+  if (fct_cols_smem_bytes(r1) > static_cast<size_t>(max_smem) || bcol_smem_bytes(r1) > static_cast<size_t>(max_smem))
+    return 0;
+  return (d + kColW - 1) / kColW;
+}
+
+int fct_cols_threads() { return kColThreads; }
+int fct_cols_tile() { return kColT; }
+
+const void* fct_cols_kernel(l1s_dtype dt) {
+  return dt == L1S_BF16 ? reinterpret_cast<const void*>(&fct_embed_cols_kernel<uint16_t>)
+                        : reinterpret_cast<const void*>(&fct_embed_cols_kernel<float>);
+}
+
+// Blocks of the b-column kernel: two per SM, no more than one warp per tile.
+static int bcol_ctas(int64_t n) {
+  const int64_t tiles = (n + kColT - 1) / kColT;
+  const int64_t want = 2 * static_cast<int64_t>(device_info().sms);
+  return static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(want, (tiles + 7) / 8)));
+}
+
+// Partial floats of a launch with `ctas` blocks per slice over n rows.
+size_t fct_cols_partial_floats(int slices, int ctas, int r1, int64_t n) {
+  return static_cast<size_t>(slices) * ctas * r1 * kColW + static_cast<size_t>(bcol_ctas(n)) * r1;
+}
+
+bool launch_fct_cols(const Plan& pl, const void* A, int64_t lda, l1s_dtype dt, const float* b, int64_t n,
+                     int64_t row_offset, const l1s_params* p, bool accumulate, unsigned char* ws, cudaStream_t st) {
+  ColsArgs a;
+  a.A = A;
+  a.lda = lda;
+  a.b = b;
+  a.n = n;
+  a.d = pl.d;
+  a.r1 = pl.r1;
+  a.nslices = pl.fct_cols;
+  a.log2s = pl.log2s;
+  a.inv_sqrt_s = static_cast<float>(1.0 / sqrt(static_cast<double>(pl.s)));
+  a.ntiles = (n + kColT - 1) / kColT;
+  a.key = make_key(p->seed);
+  a.problem = p->problem_id;
+  a.row_offset = row_offset;
+  a.sign_flip = p->sign_flip;
+  float* parts = reinterpret_cast<float*>(ws + pl.off_partials);
+  a.partials = parts;
+  a.partials_b = parts + static_cast<size_t>(pl.fct_cols) * pl.fct_ctas * pl.r1 * kColW;
+  a.accumulate = accumulate ? 1 : 0;
+  const void* fn = fct_cols_kernel(dt);
+  const size_t smem = fct_cols_smem_bytes(pl.r1);
+  if (!cuda_ok(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)),
+               "cudaFuncSetAttribute(fct_embed_cols)"))
+    return false;
+  void* args[] = {&a};
+  if (!cuda_ok(cudaLaunchKernel(fn, dim3(pl.fct_ctas, pl.fct_cols), dim3(kColThreads), args, smem, st),
+               "launch fct_embed_cols"))
+    return false;
+  // The b column: its blocks are a function of this launch's n (the reduction reads them).
+  const size_t bsmem = bcol_smem_bytes(pl.r1);
+  const void* fb = reinterpret_cast<const void*>(&fct_embed_bcol_kernel);
+  if (!cuda_ok(cudaFuncSetAttribute(fb, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(bsmem)),
+               "cudaFuncSetAttribute(fct_embed_bcol)") ||
+      !cuda_ok(cudaLaunchKernel(fb, dim3(bcol_ctas(pl.n)), dim3(kBcolThreads), args, bsmem, st),
+               "launch fct_embed_bcol"))
+    return false;
+  count_launch(2);
+  return true;
+}
+
+bool launch_fct_cols_reduce(const Plan& pl, const l1s_params* p, float* pix, unsigned char* ws, cudaStream_t st,
+                            double* pi2_out) {
+  const float* parts = reinterpret_cast<const float*>(ws + pl.off_partials);
+  const float* parts_b = parts + static_cast<size_t>(pl.fct_cols) * pl.fct_ctas * pl.r1 * kColW;
+  dim3 grid((pl.r1 * kColW + 31) / 32, pl.fct_cols + 1);
+  fct_reduce_cols_kernel<<<grid, 1024, 0, st>>>(parts, parts_b, pl.fct_ctas, bcol_ctas(pl.n), pl.fct_cols, pl.r1,
+                                                pl.d, pix, reinterpret_cast<uint32_t*>(ws + pl.off_status),
+                                                make_key(p->seed), p->problem_id, pl.q * pl.r2, pl.r2,
+                                                p->variant == 1 ? 1 : 0, pl.pi2_neg_lo, pl.pi2_neg_hi, pi2_out);
+  count_launch(1);
+  return cuda_ok(cudaGetLastError(), "launch fct_reduce_cols");
+}
+
+}  // namespace l1s

@@ -1267,11 +1267,18 @@ int fct_threads_for(int log2s, int width) {
   return t > kFctMaxThreads ? kFctMaxThreads : t;
 }
 
+bool launch_fct_cols(const Plan& pl, const void* A, int64_t lda, l1s_dtype dt, const float* b, int64_t n,
+                     int64_t row_offset, const l1s_params* p, bool accumulate, unsigned char* ws, cudaStream_t st);
+bool launch_fct_cols_reduce(const Plan& pl, const l1s_params* p, float* pix, unsigned char* ws, cudaStream_t st,
+                            double* pi2_out);
+int fct_cols_tile();
+
 // One phase-1 launch over rows [0, n) of A and b (device) whose global ids start at
 // row_offset, writing the per-block partials at `partials`.
 static bool launch_fct_part(const Plan& pl, const void* A, int64_t lda, l1s_dtype dt, const float* b, int64_t n,
                             int64_t row_offset, const l1s_params* p, bool accumulate, unsigned char* ws,
                             cudaStream_t st) {
+  if (pl.fct_cols) return launch_fct_cols(pl, A, lda, dt, b, n, row_offset, p, accumulate, ws, st);
   FctArgs a;
   a.A = A;
   a.lda = lda;
@@ -1345,6 +1352,7 @@ static bool launch_fct_part(const Plan& pl, const void* A, int64_t lda, l1s_dtyp
 
 static bool launch_fct_reduce(const Plan& pl, const l1s_params* p, float* pix, unsigned char* ws, cudaStream_t st,
                               double* pi2_out) {
+  if (pl.fct_cols) return launch_fct_cols_reduce(pl, p, pix, ws, st, pi2_out);
   const int per = pl.r1 * pl.fct_width;
   dim3 rgrid((per + 31) / 32, pl.fct_slices);
   fct_reduce_kernel<<<rgrid, 1024, 0, st>>>(reinterpret_cast<float*>(ws + pl.off_partials), pl.fct_ctas, pl.r1,
@@ -1372,7 +1380,7 @@ bool launch_fct_streamed(const Plan& pl, const void* A_host, int64_t lda_host, l
                          void* A_dev, float* b_dev, const l1s_params* p, float* pix, unsigned char* ws,
                          cudaStream_t st, cudaStream_t cp, const cudaEvent_t* evs, double* pi2_out) {
   const int K = std::max(pl.fct_chunks, 1);
-  const int64_t tile = pl.fct_ws ? (int64_t{1} << pl.fct_tile_log2) : pl.s;
+  const int64_t tile = pl.fct_cols ? fct_cols_tile() : (pl.fct_ws ? (int64_t{1} << pl.fct_tile_log2) : pl.s);
   const int64_t per_chunk = ((pl.n + K - 1) / K + tile - 1) / tile * tile;
   const size_t esz = dt == L1S_BF16 ? 2 : 4;
   for (int k = 0; k < K; ++k) {

@@ -243,6 +243,7 @@ struct Plan {
   int fct_tile_log2;        // its tile (rows per pipeline step, 2^fct_tile_log2 ≥ s)
   int fct_lean;             // 1: its one-stage, one-copy form (W = 16)
   int fct_sorted;           // 16 or 32: the bucket-sorted kernel with that column width runs phase 1
+  int fct_cols;             // > 0: the column-sliced wide-X kernel runs phase 1 over this many 16-column slices
   int fct_ctas;             // thread blocks per slice
   int fct_chunks;           // inputs in host memory: row chunks whose copies overlap phase 1
   size_t fct_smem;

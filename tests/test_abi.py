@@ -73,7 +73,7 @@ def test_schedule_table_argument_checks(lib):
         L.l1s_schedule_set(16, L.F32, 48, {"fct_variant": 1})
     assert e.value.code == 1
     with pytest.raises(L.L1SError) as e:
-        L.l1s_schedule_set(16, L.F32, 256, {"fct_variant": 7})
+        L.l1s_schedule_set(16, L.F32, 256, {"fct_variant": 8})
     assert e.value.code == 1 and "out of range" in str(e.value)
 
 

@@ -171,10 +171,12 @@ def test_batched_argument_errors():
 
 @pytest.mark.parametrize("variant,n,d,s", [(1, 70000, 8, 256), (2, 70000, 8, 256), (3, 70000, 8, 256),
                                            (4, 70000, 8, 256), (5, 70000, 8, 256), (6, 70000, 8, 256),
-                                           (3, 9000, 64, 1024), (6, 9000, 64, 1024)])
+                                           (3, 9000, 64, 1024), (6, 9000, 64, 1024), (7, 9000, 64, 1024),
+                                           (7, 40000, 40, 256), (7, 5000, 24, 32), (7, 70000, 64, 1024)])
 def test_every_phase1_variant_matches_the_oracle(variant, n, d, s):
     """Each schedule's phase-1 kernel (narrow-X warp-specialised and its lean form, TMA-staged,
-    bucket-sorted, direct over column slices for two or one blocks per SM) meets the Π1X bar."""
+    bucket-sorted, direct over column slices for two or one blocks per SM, the column-sliced
+    wide-X kernel with its b-column kernel) meets the Π1X bar."""
     pr = problem(n, d, seed=9)
     A, b = to_device(pr)
     prm = L.make_params(s, r1_for(d), 16, 1000.0, seed=3, problem_id=2)
