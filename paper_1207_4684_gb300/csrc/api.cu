@@ -30,7 +30,7 @@ int fct_cols_slices(int log2s, int d, int r1, int max_smem);
 size_t fct_cols_smem_bytes(int r1);
 int fct_cols_threads();
 int fct_cols_tile();
-const void* fct_cols_kernel(l1s_dtype dt);
+const void* fct_cols_kernel(l1s_dtype dt, bool full);
 size_t fct_cols_partial_floats(int slices, int ctas, int r1, int64_t n);
 bool launch_fct(const Plan& pl, const void* A, int64_t lda, l1s_dtype dt, const float* b,
                 const l1s_params* p, float* pix, unsigned char* ws, cudaStream_t st, double* pi2_out = nullptr);
@@ -235,7 +235,7 @@ static FctGeometry fct_geometry(int variant, const Plan& P, l1s_dtype dt, const 
     g.width = 16;
     g.smem = fct_cols_smem_bytes(P.r1);
     g.threads = fct_cols_threads();
-    const void* fn = fct_cols_kernel(dt);
+    const void* fn = fct_cols_kernel(dt, P.log2s == 10);
     if (!cuda_ok(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(g.smem)),
                  "cudaFuncSetAttribute(fct_embed_cols)"))
       return g;

@@ -1,6 +1,6 @@
 // Phase 1 for wide X: the FCT1 embedding Π1·X = 4·B·C·H̃·D·X (§3.1, FCT1 construction;
 // Figure 2, steps 1-2) when the r1 × q partial of Π1X does not fit one thread block's
-// shared memory (16 < d ≤ 128, s ≤ 1024, r1 ≤ 2300).
+// shared memory (16 < d ≤ 128, s ≤ 1024, r1 ≤ 2280).
 //
 // The columns of A are cut into slices of 16; a thread block owns one slice and keeps
 // that slice's r1 × 16 FP32 partial of Π1X in shared memory (B's hashed sum is a
@@ -23,12 +23,17 @@
 // Every slice redraws the row variates: the bound of this kernel is the shared-memory
 // FP32 atomic rate (two atomics per element), and the draws run on the ALUs beside it.
 // The tile and the draws are padded by 16 words / one entry after every 32 rows, so that
-// both passes read and write them without bank conflicts.
+// both passes read and write them without bank conflicts.  The draws hold the byte offset
+// of their row of the partial and σ as a sign mask, and the scatter is a shared-memory
+// reduction issued without a compiler memory barrier, so that a warp can keep loading the
+// draws of later rows while its earlier additions are in flight.
 //
 // The b column (−b, the last column of X) is transformed by a second, light kernel: one
 // warp per tile of 1024 rows, lane l holding rows l + 32k; it draws its own rows, runs the
 // butterflies over k in registers and over l by shuffles, and scatters both halves into
 // its block's r1-entry partial.
+#include <cuda.h>
+
 #include <algorithm>
 
 #include "l1s_common.cuh"
@@ -43,6 +48,13 @@ constexpr int kBcolThreads = 256;                           // b-column kernel: 
 constexpr int kColJ = 32;                                   // rows per thread in each pass
 constexpr int kColTileWords = kColT * kColW + (kColT / 32) * kColW;
 constexpr int kColMeta = kColT + kColT / 32;
+
+// P[off] += v in shared memory (off in bytes from the shared window), with no result and
+// no compiler memory barrier: nothing in the passes reads P, so later loads of other
+// arrays may be scheduled ahead of it (the block barriers order it before P is read).
+__device__ __forceinline__ void red_add_shared(uint32_t addr, float v) {
+  asm volatile("red.shared.add.f32 [%0], %1;" ::"r"(addr), "f"(v));
+}
 
 static_assert(kColT == 2 * kColAWarps * kColJ, "a pass covers the tile once");
 
@@ -62,81 +74,95 @@ struct ColsArgs {
   float* partials;      // [nslices][gridDim.x][r1][16]
   float* partials_b;    // b-column kernel: [its blocks][r1]
   int accumulate;       // 1: add to the partials of an earlier launch over other rows
+  uint32_t* flags;      // status word (TIMEOUT)
 };
 
 __device__ __forceinline__ int col_tile_off(int row, int c) { return row * kColW + c + ((row >> 5) << 4); }
 __device__ __forceinline__ int col_meta(int row) { return row + (row >> 5); }
 
+// Raw bits of one element (widened where it is used, so that a prefetch does not wait).
 template <typename TA>
 __device__ __forceinline__ uint32_t col_ld(const TA* p) {
   if constexpr (sizeof(TA) == 4) return __float_as_uint(__ldcs(p));
-  else return static_cast<uint32_t>(__ldcs(reinterpret_cast<const unsigned short*>(p))) << 16;
+  else return static_cast<uint32_t>(__ldcs(reinterpret_cast<const unsigned short*>(p)));
 }
 
-// One pass-1/pass-2 step over tile t of this block's slice; x holds t's values (raw FP32
-// bits), xn receives tile t + stride's (loads issued here, consumed by the next step).
 template <typename TA>
+__device__ __forceinline__ uint32_t col_widen(uint32_t raw) {
+  if constexpr (sizeof(TA) == 4) return raw;
+  else return raw << 16;
+}
+
+// One pass-1/pass-2 step over tile t of this block's slice; x holds t's values (raw bits),
+// xn receives tile t + stride's (loads issued here, consumed by the next step).  FULL: the
+// tile is one H_s block (s = 1024), every butterfly stage runs.
+template <typename TA, bool FULL>
 struct ColsBlock {
   const ColsArgs& a;
-  float* P;
+  uint32_t pc;          // shared address of P[0][c]
   float* tile;
-  float2* mI;           // {4·c_I·σ, bits (h_I << 1) | [σ = −1]}
-  float2* mH;           // {4·c_H/√s, bits h_H}
+  uint4* mI;            // {4·c_I·σ, byte offset of row h_I of P, σ sign mask, 0}
+  uint2* mH;            // {4·c_H/√s, byte offset of row h_H of P}
   int slice, c, hw;
   bool live;
 
   __device__ __forceinline__ void load(int64_t t, uint32_t (&x)[kColJ]) const {
     if (t >= a.ntiles) return;
-    const int64_t r0 = t * kColT;
-    const TA* A = static_cast<const TA*>(a.A) + slice * kColW + c;
+    const int64_t r0 = t * kColT + hw;
+    const TA* A = static_cast<const TA*>(a.A) + r0 * a.lda + slice * kColW + c;
+    const int64_t stride = 32 * a.lda;
+    if (live && t * kColT + kColT <= a.n) {
 #pragma unroll
-    for (int j = 0; j < kColJ; ++j) {
-      const int64_t row = r0 + hw + 32 * j;
-      x[j] = (live && row < a.n) ? col_ld<TA>(A + row * a.lda) : 0u;
+      for (int j = 0; j < kColJ; ++j) x[j] = col_ld<TA>(A + j * stride);
+    } else {
+#pragma unroll
+      for (int j = 0; j < kColJ; ++j) x[j] = (live && r0 + 32 * j < a.n) ? col_ld<TA>(A + j * stride) : 0u;
     }
   }
 
   // Draws of tile-row r of tile t: the identity and Hadamard entries of both halves.
-  __device__ __forceinline__ void draw(int64_t t, int r, float2& mi, float2& mh) const {
+  __device__ __forceinline__ void draw(int64_t t, int r, uint4& mi, uint2& mh) const {
     const uint64_t grow = static_cast<uint64_t>(a.row_offset + t * kColT + r);
     const uint4 o = draw_row(a.key, grow, a.problem, kStreamFct);
     const bool neg = a.sign_flip && (o.w & 1u);
     const float wI = 4.f * cauchy_f32(o.w >> 8);
-    mi = make_float2(neg ? -wI : wI, __uint_as_float((static_cast<uint32_t>(bucket_of(o.z, a.r1)) << 1) | (neg ? 1u : 0u)));
-    mh = make_float2(4.f * cauchy_f32(o.y >> 8) * a.inv_sqrt_s, __uint_as_float(static_cast<uint32_t>(bucket_of(o.x, a.r1))));
+    mi = make_uint4(__float_as_uint(neg ? -wI : wI), static_cast<uint32_t>(bucket_of(o.z, a.r1)) * (kColW * 4),
+                    neg ? 0x80000000u : 0u, 0u);
+    mh = make_uint2(__float_as_uint(4.f * cauchy_f32(o.y >> 8) * a.inv_sqrt_s),
+                    static_cast<uint32_t>(bucket_of(o.x, a.r1)) * (kColW * 4));
+  }
+
+  __device__ __forceinline__ void butterflies(float (&v)[kColJ], int lo_bit) const {
+#pragma unroll
+    for (int b = 0; b < 5; ++b)
+      if (FULL || lo_bit + b < a.log2s)
+#pragma unroll
+        for (int j = 0; j < kColJ; ++j)
+          if ((j & (1 << b)) == 0) {
+            const float lo = v[j], hi = v[j | (1 << b)];
+            v[j] = lo + hi;
+            v[j | (1 << b)] = lo - hi;
+          }
   }
 
   __device__ __forceinline__ void step(int64_t t, uint32_t (&x)[kColJ], uint32_t (&xn)[kColJ]) const {
-    const int lg = a.log2s;
     const int64_t tn = t + gridDim.x;
     const int tid = threadIdx.x;
     __syncthreads();                                     // draws of t visible; the tile is free
     load(tn, xn);
-    float2 mi0 = make_float2(0.f, 0.f), mh0 = mi0, mi1 = mi0, mh1 = mi0;
+    uint4 mi0 = make_uint4(0u, 0u, 0u, 0u), mi1 = mi0;
+    uint2 mh0 = make_uint2(0u, 0u), mh1 = mh0;
     {
       // ---- pass 1: identity scatter, σ, butterflies over row bits 5-9, tile store
-      float* Pc = P + c;
-#pragma unroll
-      for (int j = 0; j < kColJ; ++j) {
-        const float2 m = mI[col_meta(hw + 32 * j)];
-        const uint32_t code = __float_as_uint(m.y);
-        const float xv = __uint_as_float(x[j]);
-        if (live) atomicAdd(Pc + (code >> 1) * kColW, m.x * xv);
-        x[j] = x[j] ^ (code << 31);                      // z = σ·x (raw bits)
-      }
       float v[kColJ];
 #pragma unroll
-      for (int j = 0; j < kColJ; ++j) v[j] = __uint_as_float(x[j]);
-#pragma unroll
-      for (int b = 0; b < 5; ++b)
-        if (5 + b < lg)
-#pragma unroll
-          for (int j = 0; j < kColJ; ++j)
-            if ((j & (1 << b)) == 0) {
-              const float lo = v[j], hi = v[j | (1 << b)];
-              v[j] = lo + hi;
-              v[j | (1 << b)] = lo - hi;
-            }
+      for (int j = 0; j < kColJ; ++j) {
+        const uint4 m = mI[col_meta(hw + 32 * j)];
+        const uint32_t xb = col_widen<TA>(x[j]);
+        if (live) red_add_shared(pc + m.y, __uint_as_float(m.x) * __uint_as_float(xb));
+        v[j] = __uint_as_float(xb ^ m.z);                // z = σ·x
+      }
+      butterflies(v, 5);
 #pragma unroll
       for (int j = 0; j < kColJ; ++j) tile[col_tile_off(hw + 32 * j, c)] = v[j];
       if (tn < a.ntiles) draw(tn, tid, mi0, mh0);      // the next tile's draws, first row
@@ -148,22 +174,12 @@ struct ColsBlock {
       float v[kColJ];
 #pragma unroll
       for (int i = 0; i < kColJ; ++i) v[i] = tile[col_tile_off(32 * hw + i, c)];
-#pragma unroll
-      for (int b = 0; b < 5; ++b)
-        if (b < lg)
-#pragma unroll
-          for (int i = 0; i < kColJ; ++i)
-            if ((i & (1 << b)) == 0) {
-              const float lo = v[i], hi = v[i | (1 << b)];
-              v[i] = lo + hi;
-              v[i | (1 << b)] = lo - hi;
-            }
+      butterflies(v, 0);
       if (live) {
-        float* Pc = P + c;
 #pragma unroll
         for (int i = 0; i < kColJ; ++i) {
-          const float2 m = mH[col_meta(32 * hw + i)];
-          atomicAdd(Pc + __float_as_uint(m.y) * kColW, m.x * v[i]);
+          const uint2 m = mH[col_meta(32 * hw + i)];
+          red_add_shared(pc + m.y, __uint_as_float(m.x) * v[i]);
         }
       }
       if (tn < a.ntiles) draw(tn, tid + kColT / 2, mi1, mh1);   // second row
@@ -177,23 +193,25 @@ struct ColsBlock {
   }
 };
 
-template <typename TA>
+template <typename TA, bool FULL>
 __global__ void __launch_bounds__(kColThreads, 1) fct_embed_cols_kernel(const ColsArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int r1 = a.r1;
   float* P = reinterpret_cast<float*>(smem_raw);                 // [r1][16]
   float* tile = P + r1 * kColW;                                  // padded [1024][16]
-  float2* mI = reinterpret_cast<float2*>(tile + kColTileWords);  // padded [1024]
-  float2* mH = mI + kColMeta;
+  uint4* mI = reinterpret_cast<uint4*>(tile + kColTileWords);    // padded [1024]
+  uint2* mH = reinterpret_cast<uint2*>(mI + kColMeta);           // padded [1024]
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int slice = blockIdx.y;
   const int wcols = min(kColW, a.d - slice * kColW);
-  ColsBlock<TA> blk{a, P, tile, mI, mH, slice, lane & 15, 2 * warp + (lane >> 4), (lane & 15) < wcols};
+  const int c = lane & 15;
+  ColsBlock<TA, FULL> blk{a, smem_u32(P + c), tile, mI, mH, slice, c, 2 * warp + (lane >> 4), c < wcols};
   for (int i = tid; i < r1 * kColW; i += blockDim.x) P[i] = 0.f;
   const int64_t t0 = blockIdx.x;
   if (t0 < a.ntiles)
     for (int r = tid; r < kColT; r += kColThreads) {
-      float2 mi, mh;
+      uint4 mi;
+      uint2 mh;
       blk.draw(t0, r, mi, mh);
       mI[col_meta(r)] = mi;
       mH[col_meta(r)] = mh;
@@ -208,6 +226,184 @@ __global__ void __launch_bounds__(kColThreads, 1) fct_embed_cols_kernel(const Co
   }
   __syncthreads();
   // Non-finite input shows up as a non-finite partial (checked in the reduction).
+  const size_t cta = static_cast<size_t>(slice) * gridDim.x + blockIdx.x;
+  float* out = a.partials + cta * r1 * kColW;
+  for (int i = tid; i < r1 * kColW; i += blockDim.x) out[i] = (a.accumulate ? out[i] : 0.f) + P[i];
+}
+
+
+// ----------------------------------------------------------------- TMA-staged form
+// The same slices with twice the warps: shared-memory FP32 reductions are latency bound
+// per warp (about one in flight per warp), so their rate grows with the warps that issue
+// them; 32 warps of 64 registers hold 16 values each per pass.  The tile arrives by TMA
+// (2-D boxes of 16 columns × 256 rows; rows past n and columns past d read as zeros) in
+// the tile buffer itself, pass 1 transforms it in place, and the next tile's copy is
+// issued as soon as pass 2 has read the tile, so the transfer overlaps the scatter.
+//   pass 1: half h of warp w holds rows h + 2w + 64j (j < 16): butterflies over row bits
+//           6-9 in registers and bit 0 by a shuffle between the two half-warps;
+//   pass 2: rows (w & 1) + 2i + 32h + 64(w >> 1) (i < 16): bits 1-4 in registers and
+//           bit 5 by a shuffle.
+// BF16 tiles land in the upper half of the buffer and are widened to FP32 in pass 1.
+constexpr int kTmaThreads = 1024;
+constexpr int kTmaJ = 16;
+constexpr int kTmaBoxRows = 256;
+
+__device__ __forceinline__ void tma_load_box(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ int tma_hpad(int row) { return row + (row >> 5); }
+
+template <typename TA, bool FULL>
+__global__ void __launch_bounds__(kTmaThreads, 1)
+    fct_embed_cols_tma_kernel(const __grid_constant__ CUtensorMap mapA, const ColsArgs a) {
+  extern __shared__ unsigned char smem_raw[];
+  __shared__ uint64_t full_bar;
+  const int r1 = a.r1;
+  unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+  float* tile = reinterpret_cast<float*>(base);                   // [1024][16] FP32
+  float* P = tile + kColT * kColW;                                // [r1][16]
+  uint4* mI = reinterpret_cast<uint4*>(P + r1 * kColW);           // [1024]
+  uint2* mH = reinterpret_cast<uint2*>(mI + kColT);               // padded [1024]
+  unsigned char* stage = reinterpret_cast<unsigned char*>(tile) + (sizeof(TA) == 4 ? 0 : kColT * kColW * 2);
+  constexpr uint32_t kTileBytes = kColT * kColW * sizeof(TA);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, h = lane >> 4, c = lane & 15;
+  const int slice = blockIdx.y;
+  const bool live = c < min(kColW, a.d - slice * kColW);
+  const uint32_t pc = smem_u32(P + c);
+  const int lg = FULL ? 10 : a.log2s;
+  const int64_t G = gridDim.x;
+
+  auto draw = [&](int64_t t, int r, uint4& mi, uint2& mh) {
+    const uint64_t grow = static_cast<uint64_t>(a.row_offset + t * kColT + r);
+    const uint4 o = draw_row(a.key, grow, a.problem, kStreamFct);
+    const bool neg = a.sign_flip && (o.w & 1u);
+    const float wI = 4.f * cauchy_f32(o.w >> 8);
+    mi = make_uint4(__float_as_uint(neg ? -wI : wI), static_cast<uint32_t>(bucket_of(o.z, r1)) * (kColW * 4),
+                    neg ? 0x80000000u : 0u, 0u);
+    mh = make_uint2(__float_as_uint(4.f * cauchy_f32(o.y >> 8) * a.inv_sqrt_s),
+                    static_cast<uint32_t>(bucket_of(o.x, r1)) * (kColW * 4));
+  };
+  auto issue = [&](int64_t t) {
+    mbar_arrive_expect_tx(&full_bar, kTileBytes);
+#pragma unroll
+    for (int k = 0; k < kColT / kTmaBoxRows; ++k)
+      tma_load_box(stage + k * kTmaBoxRows * kColW * sizeof(TA), &mapA, slice * kColW,
+                   static_cast<int>(t * kColT + k * kTmaBoxRows), &full_bar);
+  };
+
+  for (int i = tid; i < r1 * kColW; i += blockDim.x) P[i] = 0.f;
+  if (tid == 0) {
+    mbar_init(&full_bar, 1);
+    fence_mbar_init();
+  }
+  const int64_t t0 = blockIdx.x;
+  uint2 mh_next = make_uint2(0u, 0u);
+  if (t0 < a.ntiles) {
+    uint4 mi;
+    draw(t0, tid, mi, mh_next);
+    mI[tid] = mi;
+  }
+  __syncthreads();
+  if (tid == 0 && t0 < a.ntiles) issue(t0);
+  uint32_t phase = 0;
+  bool aborted = false;
+#pragma unroll 1
+  for (int64_t t = t0; t < a.ntiles; t += G, phase ^= 1u) {
+    const bool ok = mbar_wait_bounded(&full_bar, phase, kWaitCycles);
+    if (__syncthreads_or(!ok)) {                         // the tile of t has landed; mI of t is visible
+      aborted = true;
+      break;
+    }
+    mH[tma_hpad(tid)] = mh_next;                         // pass 2 of the previous tile is done with mH
+    const int64_t tn = t + G;
+    uint4 mi_next = make_uint4(0u, 0u, 0u, 0u);
+    float v[kTmaJ];
+    // ---- pass 1: identity scatter, σ, butterflies over row bits 0 and 6-9, in place
+    {
+      const int rb = h + 2 * warp;
+#pragma unroll
+      for (int j = 0; j < kTmaJ; ++j) {
+        const int row = rb + 64 * j;
+        uint32_t xb;
+        if constexpr (sizeof(TA) == 4) xb = __float_as_uint(tile[row * kColW + c]);
+        else xb = static_cast<uint32_t>(reinterpret_cast<const uint16_t*>(stage)[row * kColW + c]) << 16;
+        const uint4 m = mI[row];
+        if (live) red_add_shared(pc + m.y, __uint_as_float(m.x) * __uint_as_float(xb));
+        v[j] = __uint_as_float(xb ^ m.z);                // z = σ·x
+      }
+      if constexpr (sizeof(TA) == 2) __syncthreads();    // every BF16 value read before FP32 rows are written
+      if (FULL || lg > 0) {
+#pragma unroll
+        for (int j = 0; j < kTmaJ; ++j) {
+          const float o = __shfl_xor_sync(0xffffffffu, v[j], 16);
+          v[j] = h ? (o - v[j]) : (v[j] + o);
+        }
+      }
+#pragma unroll
+      for (int b = 0; b < 4; ++b)
+        if (FULL || 6 + b < lg)
+#pragma unroll
+          for (int j = 0; j < kTmaJ; ++j)
+            if ((j & (1 << b)) == 0) {
+              const float lo = v[j], hi = v[j | (1 << b)];
+              v[j] = lo + hi;
+              v[j | (1 << b)] = lo - hi;
+            }
+#pragma unroll
+      for (int j = 0; j < kTmaJ; ++j) tile[(rb + 64 * j) * kColW + c] = v[j];
+      if (tn < a.ntiles) draw(tn, tid, mi_next, mh_next);
+    }
+    __syncthreads();                                     // the tile holds pass 1; mI of t is free
+    if (tn < a.ntiles) mI[tid] = mi_next;
+    // ---- pass 2: butterflies over row bits 1-5, Hadamard scatter
+    const int qb = (warp & 1) + 32 * h + 64 * (warp >> 1);
+#pragma unroll
+    for (int i = 0; i < kTmaJ; ++i) v[i] = tile[(qb + 2 * i) * kColW + c];
+    __syncthreads();                                     // the tile is free: the next copy may land
+    if (tid == 0 && tn < a.ntiles) {
+      fence_proxy_async_smem();
+      issue(tn);
+    }
+#pragma unroll
+    for (int b = 0; b < 4; ++b)
+      if (FULL || 1 + b < lg)
+#pragma unroll
+        for (int i = 0; i < kTmaJ; ++i)
+          if ((i & (1 << b)) == 0) {
+            const float lo = v[i], hi = v[i | (1 << b)];
+            v[i] = lo + hi;
+            v[i | (1 << b)] = lo - hi;
+          }
+    if (FULL || 5 < lg) {
+#pragma unroll
+      for (int i = 0; i < kTmaJ; ++i) {
+        const float o = __shfl_xor_sync(0xffffffffu, v[i], 16);
+        v[i] = h ? (o - v[i]) : (v[i] + o);
+      }
+    }
+    if (live) {
+#pragma unroll
+      for (int i = 0; i < kTmaJ; ++i) {
+        const uint2 m = mH[tma_hpad(qb + 2 * i)];
+        red_add_shared(pc + m.y, __uint_as_float(m.x) * v[i]);
+      }
+    }
+  }
+  __syncthreads();
+  if (aborted) {
+    // Let the copy in flight land (a bounded wait) before the shared memory is released.
+    if (tid == 0) {
+      raise_flag(a.flags, L1S_ERR_TIMEOUT);
+      mbar_wait_bounded(&full_bar, phase, 20000000LL);
+    }
+    __syncthreads();
+    return;
+  }
   const size_t cta = static_cast<size_t>(slice) * gridDim.x + blockIdx.x;
   float* out = a.partials + cta * r1 * kColW;
   for (int i = tid; i < r1 * kColW; i += blockDim.x) out[i] = (a.accumulate ? out[i] : 0.f) + P[i];
@@ -240,7 +436,7 @@ __global__ void __launch_bounds__(kBcolThreads) fct_embed_bcol_kernel(const Cols
       const bool neg = a.sign_flip && (o.w & 1u);
       const float wI = 4.f * cauchy_f32(o.w >> 8);
       if (neg) v[k] = -v[k];                                                 // z = σ·x
-      atomicAdd(Pb + bucket_of(o.z, r1), wI * v[k]);                        // identity half
+      red_add_shared(smem_u32(Pb + bucket_of(o.z, r1)), wI * v[k]);        // identity half
       mH[k * 32 + lane] = make_float2(4.f * cauchy_f32(o.y >> 8) * a.inv_sqrt_s,
                                       __uint_as_float(static_cast<uint32_t>(bucket_of(o.x, r1))));
     }
@@ -267,7 +463,7 @@ __global__ void __launch_bounds__(kBcolThreads) fct_embed_bcol_kernel(const Cols
 #pragma unroll
     for (int k = 0; k < kColJ; ++k) {
       const float2 m = mH[k * 32 + lane];
-      atomicAdd(Pb + __float_as_uint(m.y), m.x * v[k]);                      // Hadamard half
+      red_add_shared(smem_u32(Pb + __float_as_uint(m.y)), m.x * v[k]);     // Hadamard half
     }
   }
   __syncthreads();
@@ -341,16 +537,22 @@ __global__ void __launch_bounds__(1024) fct_reduce_cols_kernel(const float* __re
 // ----------------------------------------------------------------- host side
 size_t fct_cols_smem_bytes(int r1) {
   return static_cast<size_t>(r1) * kColW * 4 + static_cast<size_t>(kColTileWords) * 4 +
-         2 * static_cast<size_t>(kColMeta) * sizeof(float2);
+         static_cast<size_t>(kColMeta) * (sizeof(uint4) + sizeof(uint2));
 }
 
 static size_t bcol_smem_bytes(int r1) {
   return static_cast<size_t>((r1 + 3) & ~3) * 4 + static_cast<size_t>(kBcolThreads / 32) * kColT * sizeof(float2);
 }
 
+static size_t cols_tma_smem_bytes(int r1) {
+  return 128 + static_cast<size_t>(kColT) * kColW * 4 + static_cast<size_t>(r1) * kColW * 4 +
+         static_cast<size_t>(kColT) * sizeof(uint4) + static_cast<size_t>(kColMeta) * sizeof(uint2);
+}
+
 int fct_cols_slices(int log2s, int d, int r1, int max_smem) {
   if (log2s > 10 || d <= 0) return 0;
-  if (fct_cols_smem_bytes(r1) > static_cast<size_t>(max_smem) || bcol_smem_bytes(r1) > static_cast<size_t>(max_smem))
+  if (fct_cols_smem_bytes(r1) > static_cast<size_t>(max_smem) || bcol_smem_bytes(r1) > static_cast<size_t>(max_smem) ||
+      cols_tma_smem_bytes(r1) > static_cast<size_t>(max_smem))
     return 0;
   return (d + kColW - 1) / kColW;
 }
@@ -358,9 +560,15 @@ int fct_cols_slices(int log2s, int d, int r1, int max_smem) {
 int fct_cols_threads() { return kColThreads; }
 int fct_cols_tile() { return kColT; }
 
-const void* fct_cols_kernel(l1s_dtype dt) {
-  return dt == L1S_BF16 ? reinterpret_cast<const void*>(&fct_embed_cols_kernel<uint16_t>)
-                        : reinterpret_cast<const void*>(&fct_embed_cols_kernel<float>);
+bool encode_tiled_2d(CUtensorMap* map, CUtensorMapDataType dtype, const void* base, uint64_t rows, uint64_t cols,
+                     uint64_t row_bytes, uint32_t box_cols, uint32_t box_rows, CUtensorMapSwizzle swizzle);
+
+const void* fct_cols_kernel(l1s_dtype dt, bool full) {
+  if (full)
+    return dt == L1S_BF16 ? reinterpret_cast<const void*>(&fct_embed_cols_kernel<uint16_t, true>)
+                          : reinterpret_cast<const void*>(&fct_embed_cols_kernel<float, true>);
+  return dt == L1S_BF16 ? reinterpret_cast<const void*>(&fct_embed_cols_kernel<uint16_t, false>)
+                        : reinterpret_cast<const void*>(&fct_embed_cols_kernel<float, false>);
 }
 
 // Blocks of the b-column kernel: two per SM, no more than one warp per tile.
@@ -396,15 +604,38 @@ bool launch_fct_cols(const Plan& pl, const void* A, int64_t lda, l1s_dtype dt, c
   a.partials = parts;
   a.partials_b = parts + static_cast<size_t>(pl.fct_cols) * pl.fct_ctas * pl.r1 * kColW;
   a.accumulate = accumulate ? 1 : 0;
-  const void* fn = fct_cols_kernel(dt);
-  const size_t smem = fct_cols_smem_bytes(pl.r1);
-  if (!cuda_ok(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)),
-               "cudaFuncSetAttribute(fct_embed_cols)"))
-    return false;
+  a.flags = reinterpret_cast<uint32_t*>(ws + pl.off_status);
   void* args[] = {&a};
-  if (!cuda_ok(cudaLaunchKernel(fn, dim3(pl.fct_ctas, pl.fct_cols), dim3(kColThreads), args, smem, st),
-               "launch fct_embed_cols"))
-    return false;
+  // TMA staging needs a 16-byte aligned base and a row pitch that is a multiple of 16 bytes.
+  const size_t esz = dt == L1S_BF16 ? 2 : 4;
+  CUtensorMap mapA;
+  const bool tma = reinterpret_cast<uintptr_t>(A) % 16 == 0 && (static_cast<uint64_t>(lda) * esz) % 16 == 0 &&
+                   encode_tiled_2d(&mapA, dt == L1S_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                                   A, static_cast<uint64_t>(n), static_cast<uint64_t>(pl.d), static_cast<uint64_t>(lda) * esz,
+                                   kColW, kTmaBoxRows, CU_TENSOR_MAP_SWIZZLE_NONE);
+  if (tma) {
+    const bool full = pl.log2s == 10;
+    const void* fn = dt == L1S_BF16 ? (full ? reinterpret_cast<const void*>(&fct_embed_cols_tma_kernel<uint16_t, true>)
+                                            : reinterpret_cast<const void*>(&fct_embed_cols_tma_kernel<uint16_t, false>))
+                                    : (full ? reinterpret_cast<const void*>(&fct_embed_cols_tma_kernel<float, true>)
+                                            : reinterpret_cast<const void*>(&fct_embed_cols_tma_kernel<float, false>));
+    const size_t smem = cols_tma_smem_bytes(pl.r1);
+    void* targs[] = {&mapA, &a};
+    if (!cuda_ok(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)),
+                 "cudaFuncSetAttribute(fct_embed_cols_tma)") ||
+        !cuda_ok(cudaLaunchKernel(fn, dim3(pl.fct_ctas, pl.fct_cols), dim3(kTmaThreads), targs, smem, st),
+                 "launch fct_embed_cols_tma"))
+      return false;
+  } else {
+    set_error("");
+    const void* fn = fct_cols_kernel(dt, pl.log2s == 10);
+    const size_t smem = fct_cols_smem_bytes(pl.r1);
+    if (!cuda_ok(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)),
+                 "cudaFuncSetAttribute(fct_embed_cols)") ||
+        !cuda_ok(cudaLaunchKernel(fn, dim3(pl.fct_ctas, pl.fct_cols), dim3(kColThreads), args, smem, st),
+                 "launch fct_embed_cols"))
+      return false;
+  }
   // The b column: its blocks are a function of this launch's n (the reduction reads them).
   const size_t bsmem = bcol_smem_bytes(pl.r1);
   const void* fb = reinterpret_cast<const void*>(&fct_embed_bcol_kernel);

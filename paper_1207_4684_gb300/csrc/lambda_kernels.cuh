@@ -166,14 +166,17 @@ __device__ __forceinline__ float lambda_of_row(const float (&x)[Q], const float*
   return lower_median<R2>(acc);
 }
 
-// Specialised for q = D + 1 and r2 = R2 known at compile time.  The loads of a thread's
-// next row are issued before the current row is computed (software pipelining).
+// Specialised for q = D + 1 and r2 = R2 known at compile time.  Up to q = 33 the loads of a
+// thread's next row are issued before the current row is computed (software pipelining);
+// wider rows would double the registers a row takes, so those rows are loaded when needed
+// and two blocks per SM hide the latency instead.
+template <int D>
+constexpr bool lambda_prefetches() { return D + 1 <= 33; }
+
 template <int D, int R2, typename TA, bool VEC, bool SMEM_M>
-__global__ void __launch_bounds__(kLamThreads) lambda_kernel(const TA* __restrict__ A, int64_t lda,
-                                                             const float* __restrict__ b, int64_t n,
-                                                             float* __restrict__ lam,
-                                                             double* __restrict__ block_sums,
-                                                             const float* __restrict__ mg) {
+__global__ void __launch_bounds__(kLamThreads, lambda_prefetches<D>() ? 1 : 2)
+    lambda_kernel(const TA* __restrict__ A, int64_t lda, const float* __restrict__ b, int64_t n,
+                  float* __restrict__ lam, double* __restrict__ block_sums, const float* __restrict__ mg) {
   constexpr int Q = D + 1;
   __shared__ float sM[SMEM_M ? Q * R2 : 1];
   if constexpr (SMEM_M) {
@@ -183,6 +186,19 @@ __global__ void __launch_bounds__(kLamThreads) lambda_kernel(const TA* __restric
   float s = 0.f, c = 0.f;
   const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
   int64_t row = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if constexpr (!lambda_prefetches<D>()) {
+    for (; row < n; row += stride) {
+      float x[Q];
+      load_row<D, TA, VEC>(A + row * lda, x);
+      x[D] = -__ldg(b + row);
+      const float med = lambda_of_row<Q, R2, SMEM_M>(x, sM);
+      lam[row] = med;
+      two_sum_add(s, c, med);
+    }
+    const double tot = block_pair_total(s, c);
+    if (threadIdx.x == 0) block_sums[blockIdx.x] = tot;
+    return;
+  }
   float nx[Q];
   if (row < n) {
     load_row<D, TA, VEC>(A + row * lda, nx);

@@ -332,6 +332,22 @@ static bool encode_bf16_2d(CUtensorMap* map, const void* base, uint64_t rows, ui
   return true;
 }
 
+// A 2-D tiled tensor map over a row-major matrix (rows × cols elements, row pitch row_bytes),
+// box of box_cols × box_rows elements, rows and columns outside the matrix read as zeros.
+bool encode_tiled_2d(CUtensorMap* map, CUtensorMapDataType dtype, const void* base, uint64_t rows, uint64_t cols,
+                     uint64_t row_bytes, uint32_t box_cols, uint32_t box_rows, CUtensorMapSwizzle swizzle) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return set_error("cuTensorMapEncodeTiled is not available"), false;
+  const cuuint64_t dims[2] = {cols, rows};
+  const cuuint64_t strides[1] = {row_bytes};
+  const cuuint32_t box[2] = {box_cols, box_rows};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult r = fn(map, dtype, 2, const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        swizzle, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return set_error("cuTensorMapEncodeTiled failed (%d)", static_cast<int>(r)), false;
+  return true;
+}
+
 // The tensor-core λ applies to BF16 A with d = 32, r2 = 32, rows of 64 bytes back to back
 // (lda = 32) and a 16-byte aligned base.
 bool lambda_tc_applies(int d, int r2, int64_t lda, const void* A, l1s_dtype dt) {
