@@ -143,9 +143,10 @@ L1S_API int l1_condition(const float* PiX_dev, int32_t r1, int32_t q, const l1s_
 /* Phase 2 (Figure 2, steps 4-5): λ_i = lower median_j |(X·M)_ij| with M the
  * q × r2 FP64 matrix (rounded to FP32 for the product; FP32 accumulation;
  * BF16 A is widened to FP32 exactly).  Mixed-precision form: for BF16 A with
- * d = r2 = 32 and lda = d, A·M_A runs on the tensor cores with M_A (the first d
- * rows of M, rounded to FP32 then to BF16, nearest-even) and FP32 accumulation;
- * the b column's term −b_i·M_{d,j} is added in FP32.  The lower median
+ * 16 < d ≤ 64, r2 ∈ {16, 32}, a 16-byte aligned A and lda·2 a multiple of 16,
+ * A·M_A runs on the tensor cores with M_A (the first d rows of M, rounded to
+ * FP32 then to BF16, nearest-even) and FP32 accumulation; the b column's term
+ * −b_i·M_{d,j} is added in FP32.  The lower median
  * is the ((r2−1)/2)-th order statistic counting from 0.  Writes lambda_dev
  * (n floats) and *lambda_sum_dev (FP64 sum of the written λ, fixed order). */
 L1S_API int l1_lambda(const void* A_dev, int64_t lda, l1s_dtype dtype, const float* b_dev,
@@ -160,13 +161,18 @@ L1S_API int l1_lambda(const void* A_dev, int64_t lda, l1s_dtype dtype, const flo
  * pool at start-up and let plug-in code allocate none.  Arguments and results are
  * those of l1_lambda minus ws/ws_bytes.  Scratch (M in FP32, the per-block Σλ
  * partials, a status block) lives in one library-owned 40 KiB device array per GPU,
- * held until the process exits; 4·q·r2 bytes, 8 bytes per partial (8 per SM) and
- * 2 KiB for the BF16 copy of M must fit in it (d ≤ 64 with r2 ≤ 64 does), else
- * L1S_ERR_INVALID_ARG.  The first
+ * held until the process exits; 4·q·r2 bytes, 8 bytes per Σλ partial (one per block
+ * of the λ grid: 8 per SM by default, more when a schedule installed with
+ * l1s_schedule_set asks for more) and 4 KiB for the BF16 copy of M must fit in it,
+ * else L1S_ERR_INVALID_ARG.  Under the default grid every d ≤ 64 with r2 ≤ 64 fits;
+ * whether a shape fits therefore depends on the installed λ grid.  The first
  * call on a device looks up that array's address (cudaGetSymbolAddress); make it
  * before any stream capture.  Every call shares the array and clears what must
- * start at zero; calls that overlap on the GPU race on it.  Allocates nothing: no
- * cudaMalloc, cudaFree or allocating library call. */
+ * start at zero; calls that overlap on the GPU race on it.  The FP32 form also loads
+ * M into the per-device constant bank that l1_lambda, l1_sample, l1_coreset and
+ * l1_regress use, so a no-alloc call that overlaps any of those on the same device
+ * races with it too.  Allocates nothing: no cudaMalloc, cudaFree or allocating
+ * library call. */
 L1S_API int l1_lambda_noalloc(const void* A_dev, int64_t lda, l1s_dtype dtype, const float* b_dev,
                               int64_t n, int32_t d, const double* M_dev, const l1s_params* params,
                               float* lambda_dev, double* lambda_sum_dev, void* stream);

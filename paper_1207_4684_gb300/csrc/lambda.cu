@@ -57,8 +57,8 @@ int lambda_threads() { return kLamThreads; }
 
 
 bool lambda_tc_applies(int d, int r2, int64_t lda, const void* A, l1s_dtype dt);
-bool launch_lambda_tc(int64_t n, const void* A, const float* b, const float* m32, uint16_t* mt_bf16, float* lam,
-                      double* block_sums, int blocks, uint32_t* flags, cudaStream_t st);
+bool launch_lambda_tc(int64_t n, int d, int r2, const void* A, int64_t lda, const float* b, const float* m32,
+                      uint16_t* mt_bf16, float* lam, double* block_sums, int blocks, uint32_t* flags, cudaStream_t st);
 
 // M (FP32, q × r2 in the workspace) → constant bank, then λ and Σλ.  BF16 A with d = r2 = 32
 // runs on the tensor cores (M_A rounded to BF16; its transpose goes to the Π2 region, 2 KB).
@@ -74,8 +74,8 @@ bool launch_lambda(const Plan& pl, const void* A, int64_t lda, l1s_dtype dt, con
   bool ok;
   if (tc) {
     blocks = std::min(pl.lam_ctas, 3 * device_info().sms);   // three resident per SM (64 TMEM columns each)
-    ok = launch_lambda_tc(pl.n, A, b, m32, reinterpret_cast<uint16_t*>(ws + pl.off_pi2), lam, sums, blocks,
-                          reinterpret_cast<uint32_t*>(ws + pl.off_status), st);
+    ok = launch_lambda_tc(pl.n, pl.d, pl.r2, A, lda, b, m32, reinterpret_cast<uint16_t*>(ws + pl.off_pi2), lam, sums,
+                          blocks, reinterpret_cast<uint32_t*>(ws + pl.off_status), st);
   } else {
     if (dt == L1S_BF16)
       ok = smem_m ? launch_lambda_bf16_smem(pl, A, lda, b, lam, sums, m32, st)

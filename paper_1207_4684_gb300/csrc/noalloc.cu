@@ -64,7 +64,7 @@ extern "C" int l1_lambda_noalloc(const void* A, int64_t lda, l1s_dtype dtype, co
   const size_t off_sums = 256;
   const size_t off_m32 = align_up(off_sums + sizeof(double) * static_cast<size_t>(pl.lam_ctas));
   const size_t off_mt = align_up(off_m32 + sizeof(float) * static_cast<size_t>(pl.q) * pl.r2);
-  const size_t need = off_mt + 2048;
+  const size_t need = off_mt + 4096;                        // M_Aᵀ of the tensor-core form: r2 × 64 BF16 at most
   if (need > kScratchBytes)
     return set_error("l1_lambda_noalloc: q·r2 = %d and %d partial sums need %zu bytes, more than its %zu-byte scratch",
                      pl.q * pl.r2, pl.lam_ctas, need, kScratchBytes),

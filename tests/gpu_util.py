@@ -83,8 +83,10 @@ def lambda_tol(X: np.ndarray, M: np.ndarray) -> np.ndarray:
 
 
 def tensor_core_form(dtype: str, d: int, r2: int, lda) -> bool:
-    """Shapes whose λ runs on the tensor cores (BF16 A, d = r2 = 32, rows back to back)."""
-    return dtype == "bf16" and d == 32 and r2 == 32 and (lda is None or lda == d)
+    """Shapes whose λ runs on the tensor cores: BF16 A with 16 < d ≤ 64, r2 ∈ {16, 32} and a
+    row pitch that is a multiple of 16 bytes."""
+    pitch = d if lda is None else lda
+    return dtype == "bf16" and 16 < d <= 64 and r2 in (16, 32) and (pitch * 2) % 16 == 0
 
 
 def lambda_tol_tc(X: np.ndarray, Mm: np.ndarray) -> np.ndarray:

@@ -12,7 +12,7 @@ import pytest
 import torch
 
 import paper_1207_4684_gb300 as L
-from gpu_util import DEV, check_pix, gpu_pix, host_x, problem, to_device
+from gpu_util import DEV, check_pix, gpu_pix, host_x, problem, tensor_core_form, to_device
 from oracle import condition, fct, leverage, rng, sampling, solve
 from synth import r1_for
 
@@ -84,7 +84,7 @@ def build_batch(members, solve_x=True):
 
 def check_member(i, member, item, band=1e-3):
     n, d, s, r2, m, dt, lda = member
-    tc = dt == "bf16" and d == 32 and r2 == 32 and lda is None
+    tc = tensor_core_form(dt, d, r2, lda)
     X, p, u = oracle_decisions(item["pr"], n, d, s, r2, m, i, tc)
     o = item["out"]
     k = int(o["cnt"].item())

@@ -182,7 +182,11 @@ def test_condition_rank_deficient_flag():
                                               (30000, 5, 16, "f32", 9), (20000, 7, 9, "f32", None),
                                               (12345, 12, 32, "bf16", None), (1000, 3, 64, "f32", None),
                                               (257, 4, 1, "f32", None), (50001, 19, 16, "f32", 20),
-                                              (20000, 12, 8, "f32", None), (30000, 40, 32, "f32", None)])
+                                              (20000, 12, 8, "f32", None), (30000, 40, 32, "f32", None),
+                                              # tensor-core form for 16 < d <= 64, r2 in {16, 32}
+                                              (70001, 64, 32, "bf16", None), (30000, 48, 16, "bf16", None),
+                                              (20000, 24, 16, "bf16", None), (5000, 64, 16, "bf16", 72),
+                                              (129, 33, 32, "bf16", None)])
 def test_lambda_parity(n, d, r2, dtype, lda):
     pr = problem(n, d, seed=r2 + d, dtype=dtype, design="gauss")
     A, b = to_device(pr, lda)
@@ -243,7 +247,7 @@ def test_sample_capacity_flag():
 
 
 @pytest.mark.parametrize("n,d,r2,m,dtype", [(65536, 8, 16, 2000.0, "f32"), (200003, 16, 16, 20000.0, "f32"),
-                                            (50000, 32, 32, 5000.0, "bf16")])
+                                            (50000, 32, 32, 5000.0, "bf16"), (60000, 64, 32, 5000.0, "bf16")])
 def test_sample_parity(n, d, r2, m, dtype):
     """λ → Σλ → p̂ → Bernoulli → ascending indices, weights and coreset rows."""
     pr = problem(n, d, seed=3, dtype=dtype)
