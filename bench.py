@@ -1,15 +1,17 @@
 """Rows/s through the FCT + ℓ1-sampling pass (Figure 2, steps 1-7) on GB300.
 
 One step = fct_embed (Π1·X), l1_condition (QR, M = R⁻¹Π2) and l1_sample (λ,
-Σλ, p̂, Bernoulli keep, compaction, coreset gather) over the n = 2^22, d = 16
-workload (columns scaled by 10^U(−2,2), Laplace noise with 5% Cauchy(0,100)
-outliers; s = 256, r1 = 355, r2 = 16, m_s = 20000), inputs resident in HBM.
-It prints one JSON line: the step's rows/s (one step captured as a CUDA graph and
-replayed), the dominant kernel's algorithmic bytes per second against the measured
-HBM copy bandwidth and its issue rate, the end-to-end rate from pinned host memory,
-the other forms (OptimizedFastCauchyRegression, sampling with replacement, multiple
-regression, BF16 with tensor-core λ, a batch of 256 problems) and the FP64 oracle's
-rate on the host cores.
+Σλ, p̂, Bernoulli keep, compaction, coreset gather) over the n = 2^26, d = 64
+workload (FP32 A, 0.1% of rows scaled by 1e3, Cauchy(0,1) noise; s = 1024,
+r1 = 2130, r2 = 32, m_s = 100000), inputs resident in HBM.  It prints one JSON
+line: the step's rows/s (one step captured as a CUDA graph and replayed), the
+dominant kernel's algorithmic bytes per second against the measured HBM copy
+bandwidth and its issue rate, the end-to-end rate from pinned host memory, the
+BF16-streamed form of the same data (tensor-core λ) against the plain FP32 path
+with the relative difference of their objectives, the other forms (the n = 2^22,
+d = 16 workload plain and as OptimizedFastCauchyRegression, sampling with
+replacement and multiple regression; the n = 2^24, d = 32 BF16 workload; a batch
+of 256 problems) and the FP64 oracle's rate on the host cores.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
 
@@ -32,7 +34,7 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOAD = "colscale_n4M_d16"
+WORKLOAD = "spiky_n64M_d64"
 METRIC = "Rows/s through FCT+ℓ1 sampling, % HBM peak; BF16/batched vs plain FP32"
 UNIT = "rows/s"
 L2_BYTES = 129 * 2 ** 20
@@ -51,9 +53,10 @@ def parse():
                     help="time eager calls instead of replays of the step captured as a CUDA graph")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the other forms (measured after the main line's timed region)")
-    ap.add_argument("--variants", default="optimized,replacement,multi,bf16,batched",
-                    help="comma-separated forms to measure after the main line: optimized, replacement, multi, "
-                         "bf16, batched")
+    ap.add_argument("--variants", default="bf16,colscale,optimized,replacement,multi,t2rows_bf16,batched",
+                    help="comma-separated forms to measure after the main line: bf16 (the main data streamed as "
+                         "BF16), colscale (n = 2^22, d = 16, FP32), optimized, replacement, multi (on the n = 2^22 "
+                         "data), t2rows_bf16 (n = 2^24, d = 32, BF16), batched")
     return ap.parse_args()
 
 
@@ -257,6 +260,70 @@ def _phase_ms(L, A, b, prm, cap, q, dev, stream, warmup, steps) -> dict:
             for k in range(3):
                 acc[k] += evs[k].elapsed_time(evs[k + 1])
     return dict(zip(["fct_embed", "l1_condition", "l1_sample"], [a / steps for a in acc]))
+
+
+def bf16_same_data_variant(L, dev, stream, args, A32, b, w, peak: float, ws32, f32_ms: float) -> dict:
+    """The main workload streamed as BF16 (A rounded once, nearest even; λ on tcgen05 tensor
+    cores) against the plain FP32 path on the original FP32 data: rows/s of each and the
+    relative difference of the objectives ‖A·x̂ − b‖₁, both evaluated on the FP32 data."""
+    import torch
+
+    n, d = A32.shape
+    q = d + 1
+    A16 = A32.to(torch.bfloat16)
+    prm = L.make_params(w.s, w.r1, w.r2, w.coreset, seed=w.seed, problem_id=w.problem_id)
+    cap = int(2 * w.coreset) + 64
+    ws16 = L.workspace(prm, n, d, L.BF16, device=dev)
+    idx = torch.empty(cap, dtype=torch.int64, device=dev)
+    wts = torch.empty(cap, dtype=torch.float64, device=dev)
+    cnt = torch.zeros(1, dtype=torch.int64, device=dev)
+    ms = _time_step_ms(lambda st: L.l1_coreset(A16, b, prm, cap, idx, wts, None, cnt, ws16, stream=st), stream, args)
+    kept = int(cnt.item())
+    ab = algorithmic_bytes(n, d, 2, kept)["step"]
+    phase = _phase_ms(L, A16, b, prm, cap, q, dev, stream, 2, max(3, args.steps // 4))
+    x16, f16_own, rows16, rc16 = L.l1_regress(A16, b, prm, ws16, stream=stream)
+    x32, f32, rows32, rc32 = L.l1_regress(A32, b, prm, ws32, stream=stream)
+    out = torch.empty(1, dtype=torch.float64, device=dev)
+    L.l1_objective(A32, b, x16.to(dev), out, ws32, stream=stream)
+    f16_on32 = float(out.item())
+    del ws16, A16
+    return {"workload": f"{w.name} streamed as BF16", "value": n / (ms / 1e3), "ms_per_step": ms,
+            "step_gbs": ab / (ms / 1e3) / 1e9, "step_frac": ab / (ms / 1e3) / 1e9 / peak, "algorithmic_bytes": ab,
+            "coreset_rows": kept, "phase_ms": phase, "status": rc16,
+            "objective_bf16_on_f32_data": f16_on32, "objective_f32": f32, "objective_bf16_own_data": f16_own,
+            "objective_rel_err_vs_f32": abs(f16_on32 - f32) / f32, "f32_status": rc32,
+            "speedup_vs_f32": f32_ms / ms}
+
+
+def colscale_variant(L, dev, stream, args, peak: float) -> tuple:
+    """The n = 2^22, d = 16 FP32 workload (columns scaled by 10^U(−2,2)): the plain pass as CUDA-
+    graph replays, its phase split and the phase-1 kernel's share of HBM.  Returns the line and
+    the device inputs, which the forms measured on this data reuse."""
+    import torch
+
+    from synth import WORKLOADS, make_problem
+
+    w = WORKLOADS["colscale_n4M_d16"]
+    pr = make_problem(w)
+    n, d = pr["A"].shape
+    q = d + 1
+    A = torch.from_numpy(pr["A"]).to(dev)
+    b = torch.from_numpy(pr["b"]).to(dev)
+    prm = L.make_params(w.s, w.r1, w.r2, w.coreset, seed=w.seed, problem_id=w.problem_id)
+    ws = L.workspace(prm, n, d, device=dev)
+    cap = int(2 * w.coreset) + 64
+    idx = torch.empty(cap, dtype=torch.int64, device=dev)
+    wts = torch.empty(cap, dtype=torch.float64, device=dev)
+    cnt = torch.zeros(1, dtype=torch.int64, device=dev)
+    ms = _time_step_ms(lambda st: L.l1_coreset(A, b, prm, cap, idx, wts, None, cnt, ws, stream=st), stream, args)
+    kept = int(cnt.item())
+    ab = algorithmic_bytes(n, d, 4, kept)
+    phase = _phase_ms(L, A, b, prm, cap, q, dev, stream, 2, max(3, args.steps // 4))
+    del ws
+    return ({"workload": w.name, "n": n, "d": d, "s": w.s, "r1": w.r1, "r2": w.r2, "coreset": w.coreset,
+             "value": n / (ms / 1e3), "ms_per_step": ms, "step_frac": ab["step"] / (ms / 1e3) / 1e9 / peak,
+             "phase_ms": phase, "phase1_frac": ab["phase1"] / (phase["fct_embed"] / 1e3) / 1e9 / peak,
+             "coreset_rows": kept}, A, b, w)
 
 
 def bf16_variant(L, dev, stream, args, peak: float) -> dict:
@@ -657,7 +724,7 @@ def run_gpu(args) -> None:
         t = torch.tensor([e2e_s], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_s = float(t.item())
-    del ws_h
+    del ws_h, A_h, b_h
 
     # ---- roofline of the dominant kernel (phase-level events bracket it)
     peaks = measured_peaks()
@@ -712,27 +779,33 @@ def run_gpu(args) -> None:
     if rank == 0 and not args.no_variants and world == 1:
         want = {v.strip() for v in args.variants.split(",") if v.strip()}
         variants = {}
-        if w.dtype != "f32":                      # these forms run on the FP32 inputs
-            want -= {"optimized", "replacement", "multi"}
-        if "optimized" in want:
-            variants["optimized"] = optimized_variant(L, dev, stream, args, A, b, w, peaks["hbm_gbs"], ms_per_step)
-        del ws
+        if "bf16" in want and w.dtype == "f32":
+            variants["bf16"] = bf16_same_data_variant(L, dev, stream, args, A, b, w, peaks["hbm_gbs"], ws, ms_per_step)
+        del ws, A, b
         torch.cuda.empty_cache()
-        if "replacement" in want:
-            variants["replacement"] = replacement_variant(L, dev, stream, args, A, b, w, peaks["hbm_gbs"],
-                                                          ms_per_step)
-        torch.cuda.empty_cache()
-        if "multi" in want:
-            variants["multi"] = multi_variant(L, dev, stream, args, A, b, w, peaks["hbm_gbs"])
-        del A, b
-        torch.cuda.empty_cache()
-        if "bf16" in want:
-            variants["bf16"] = bf16_variant(L, dev, stream, args, peaks["hbm_gbs"])
+        if want & {"colscale", "optimized", "replacement", "multi"}:
+            line_c, A1, b1, w1 = colscale_variant(L, dev, stream, args, peaks["hbm_gbs"])
+            if "colscale" in want:
+                variants["colscale"] = line_c
+            if "optimized" in want:
+                variants["optimized"] = optimized_variant(L, dev, stream, args, A1, b1, w1, peaks["hbm_gbs"],
+                                                          line_c["ms_per_step"])
+            torch.cuda.empty_cache()
+            if "replacement" in want:
+                variants["replacement"] = replacement_variant(L, dev, stream, args, A1, b1, w1, peaks["hbm_gbs"],
+                                                              line_c["ms_per_step"])
+            torch.cuda.empty_cache()
+            if "multi" in want:
+                variants["multi"] = multi_variant(L, dev, stream, args, A1, b1, w1, peaks["hbm_gbs"])
+            del A1, b1
+            torch.cuda.empty_cache()
+        if "t2rows_bf16" in want:
+            variants["t2rows_bf16"] = bf16_variant(L, dev, stream, args, peaks["hbm_gbs"])
             torch.cuda.empty_cache()
         if "batched" in want:
             variants["batched"] = batched_variant(L, dev, stream, args, peaks["hbm_gbs"])
-        variants["f32_plain"] = {"workload": w.name, "value": value, "ms_per_step": ms_per_step,
-                                 "step_frac": step_gbs / peaks["hbm_gbs"]}
+        variants["main_f32"] = {"workload": w.name, "value": value, "ms_per_step": ms_per_step,
+                                "step_frac": step_gbs / peaks["hbm_gbs"]}
         line["variants"] = variants
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_oracle_rows_per_s(pr, w, args.cpu_seconds)
