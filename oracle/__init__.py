@@ -8,8 +8,9 @@ seeded input generators in `synth/` and through the published definition of
 the counter-based generator, which each side implements on its own.
 
 Modules, in the order of the method (Figure 2, FastCauchyRegression):
-  rng        Philox4x32-10 draws: signs, hash buckets, Cauchy scales, Π2, uniforms
+  rng        Philox4x32-10 draws: signs, hash buckets, Cauchy scales, Π2, uniforms, dense C
   fct        Π1·X = 4·B·C·H̃·D·X (§3.1), per block and as an explicit dense product
+  sct        Π1·X = (4/r1)·C·X, the slow Cauchy transform (§3, used to condition in §6.3)
   condition  QR of Π1·X with positive diag(R), M = R⁻¹·Π2 (steps 2-3)
   leverage   λ_i = lower median_j |(X·M)_ij| and exact ‖U_(i)‖₁ (steps 4-5)
   sampling   p̂_i = min(1, τ·λ_i), τ = m_s/Σλ, Bernoulli keep u_i < p̂_i (steps 6-7)

@@ -28,6 +28,10 @@ conventions; the paper only fixes the distributions):
   transform (Box and Muller, 1958) of two 53-bit uniforms in (0, 1),
   u1 from (o0, o1) and u2 from (o2, o3), each ((o_a >> 5)·2^26 + (o_b >> 6) + ½)·2^-53:
   ρ = √(−2 ln u1), entry 2t = ρ·cos(2π u2), entry 2t+1 = ρ·sin(2π u2).
+* stream 4 for the slow Cauchy transform (the dense r1 × n Cauchy matrix of the
+  theorem of Sohler and Woodruff quoted in §3, which §6.3 uses to condition):
+  entry (r, i) of C, for global row i and r = 4g + w, is word w of the call with
+  counter (i_lo, (i_hi mod 2^16) + g·2^16, problem, 4), through k = word >> 8.
 * stream 2, call t with counter (t_lo, t_hi, problem, 2) for t = ⌊i/2⌋: the
   sampling uniform of row i is u = ((o_a >> 5)·2^26 + (o_b >> 6))·2^-53 with
   (a, b) = (0, 1) for even i and (2, 3) for odd i (Figure 2, step 7).
@@ -52,6 +56,7 @@ STREAM_FCT = 0
 STREAM_PI2 = 1
 STREAM_SAMPLE = 2
 STREAM_REPLACE = 3
+STREAM_SCT = 4
 
 
 def philox4x32_10(c0, c1, c2, c3, k0, k1):
@@ -192,3 +197,19 @@ def replacement_uniforms(seed: int, problem_id: int, draws) -> np.ndarray:
     wb = np.where(odd, o3, o1)
     bits = ((wa >> np.uint64(5)) << np.uint64(26)) | (wb >> np.uint64(6))
     return bits.astype(np.float64) * 2.0 ** -53
+
+
+def sct_matrix(seed: int, problem_id: int, rows, r1: int) -> np.ndarray:
+    """The r1 × len(rows) block of the slow Cauchy transform's matrix C for global rows
+    `rows` (stream 4): column i holds C[:, i], entry r = 4g + w from word w of call g."""
+    k0, k1 = _key(seed)
+    rows = np.asarray(rows, dtype=np.int64)
+    lo, hi = _row_counter(rows)
+    groups = (r1 + 3) // 4
+    out = np.empty((4 * groups, rows.size))
+    for g in range(groups):
+        c1 = (hi & np.uint64(0xFFFF)) | (np.uint64(g) << np.uint64(16))
+        words = philox4x32_10(lo, c1, np.uint64(problem_id), np.uint64(STREAM_SCT), k0, k1)
+        for w in range(4):
+            out[4 * g + w] = cauchy_from_k((words[w] >> np.uint64(8)).astype(np.int64))
+    return out[:r1]

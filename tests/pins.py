@@ -14,7 +14,7 @@ import math
 import numpy as np
 from scipy import stats
 
-from oracle import condition, fct, leverage, pipeline, rng, sampling, solve
+from oracle import condition, fct, leverage, pipeline, rng, sampling, sct, solve
 
 
 # ----------------------------------------------------------------- Hadamard
@@ -409,7 +409,52 @@ def check_scaled_probabilities(seed: int = 31) -> None:
 
 def _all_checks():
     return ALL_CHECKS + [check_bf16_round, check_gaussian_pi2, check_gaussian_lambda_distribution,
-                         check_scaled_probabilities, check_multiple_regression, check_with_replacement]
+                         check_scaled_probabilities, check_multiple_regression, check_with_replacement,
+                         check_sct_draws, check_sct_stability, check_sct_embedding_bound]
+
+
+# ----------------------------------------------------------------- slow Cauchy transform
+def check_sct_draws(rows: int = 20000, r1: int = 13, seed: int = 77) -> None:
+    """Entries of the slow transform's C (stream 4) are standard Cauchy (KS), and entries drawn
+    from different words and from different calls of a row are independent (rank correlation
+    near zero, as it is for independent draws)."""
+    C = rng.sct_matrix(seed, 3, np.arange(rows) + 1000, r1)
+    assert C.shape == (r1, rows)
+    for r in range(r1):
+        assert stats.kstest(C[r], "cauchy").pvalue > 1e-4, f"row {r} of C not Cauchy"
+    for a, b in ((0, 1), (0, 4), (3, 7), (5, 12)):
+        rho = stats.spearmanr(C[a], C[b]).statistic
+        assert abs(rho) < 5.0 / math.sqrt(rows), f"rows {a} and {b} of C are dependent (rho {rho:.3f})"
+
+
+def check_sct_stability(seeds: int = 30) -> None:
+    """1-stability (§2): column c of C·X is a vector of independent Cauchys scaled by ‖X_{:,c}‖₁,
+    so (r1/4)·(Π1X)_{rc}/‖X_{:,c}‖₁ pooled over entries and seeds passes a KS test against
+    Cauchy(0,1); the norms come from X directly, not from the oracle."""
+    g = np.random.default_rng(5)
+    n, r1 = 1500, 37
+    X = g.standard_normal((n, 3)) * np.array([1.0, 10.0, 0.01])
+    vals = []
+    for sd in range(seeds):
+        pix, _ = sct.sct_embed(X, r1, seed=500 + sd, problem_id=1, block=512)
+        vals.append(((r1 / 4.0) * pix / np.abs(X).sum(axis=0)).ravel())
+    assert stats.kstest(np.concatenate(vals), "cauchy").pvalue > 1e-4, "slow transform not Cauchy-scaled"
+
+
+def check_sct_embedding_bound(seed: int = 9) -> None:
+    """The lower bound of the theorem of §3 on the slow transform: ‖y‖₁ ≤ (4/r1)‖C·y‖₁ for y in
+    the column space of X (r1 = ⌈8·d·ln d⌉ here), for every one of 50 random y.  The sum of r1
+    half-Cauchys exceeds r1/4 by a wide margin, so a missing factor or dropped rows fail it."""
+    g = np.random.default_rng(seed)
+    n, d = 3000, 6
+    X = g.standard_normal((n, d))
+    r1 = int(math.ceil(8 * d * math.log(d)))
+    pix, tsum = sct.sct_embed(X, r1, seed=seed, block=1024)
+    assert np.all(tsum >= np.abs(pix) * (1 - 1e-12)), "sum of |terms| below |entry|"
+    for _ in range(50):
+        x = g.standard_normal(d)
+        ratio = np.abs(pix @ x).sum() / np.abs(X @ x).sum()
+        assert ratio >= 1.0, f"(4/r1)·‖C·y‖₁ / ‖y‖₁ = {ratio:.3f} < 1"
 
 
 # ----------------------------------------------------------------- multiple regression

@@ -8,7 +8,7 @@ import numpy as np
 import pytest
 
 import pins
-from oracle import condition, fct, leverage, pipeline, rng, sampling, solve
+from oracle import condition, fct, leverage, pipeline, rng, sampling, sct, solve
 
 ORIG_EMBED = fct.fct1_embed
 ORIG_HAD = fct.sylvester_hadamard
@@ -24,6 +24,8 @@ ORIG_FORM_X_MULTI = pipeline.form_x_multi
 ORIG_REPLACE = sampling.sample_with_replacement
 ORIG_GAUSS = rng.pi2_gaussian_matrix
 ORIG_SCALED = sampling.probabilities_scaled
+ORIG_SCT = sct.sct_embed
+ORIG_SCT_MATRIX = rng.sct_matrix
 
 
 def _draws_of(X, s, r1, seed, problem_id, row_offset, draws):
@@ -157,8 +159,27 @@ def scaled_no_cap(lam, scale):
     return float(scale) * np.asarray(lam, dtype=np.float64)
 
 
+def sct_scale_one_over_r1(*a, **k):
+    p, t = ORIG_SCT(*a, **k)
+    return p / 4, t / 4
+
+
+def sct_group_ignored(seed, problem_id, rows, r1):
+    c = ORIG_SCT_MATRIX(seed, problem_id, rows, 4)
+    return np.tile(c, ((r1 + 3) // 4, 1))[:r1]
+
+
+def sct_last_block_dropped(X, r1, seed=0, problem_id=0, row_offset=0, block=1 << 14):
+    n = X.shape[0]
+    keep = max(1, n - n // 3)
+    return ORIG_SCT(X[:keep], r1, seed, problem_id, row_offset, block)
+
+
 MUTATIONS = [
     ("identity half dropped", fct, "fct1_embed", embed_no_identity, pins.check_fct_dense),
+    ("slow transform scaled by 1/r1", sct, "sct_embed", sct_scale_one_over_r1, pins.check_sct_stability),
+    ("slow transform: one call for all groups", rng, "sct_matrix", sct_group_ignored, pins.check_sct_draws),
+    ("slow transform: last rows dropped", sct, "sct_embed", sct_last_block_dropped, pins.check_sct_stability),
     ("Hadamard half dropped", fct, "fct1_embed", embed_no_hadamard, pins.check_fct_dense),
     ("factor 4 → 2", fct, "fct1_embed", embed_factor2, pins.check_fct_blocks),
     ("halves swapped", fct, "fct1_embed", embed_swapped_halves, pins.check_fct_dense),
