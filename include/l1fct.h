@@ -27,7 +27,7 @@
  * - Random draws come from Philox4x32-10 (Salmon et al., SC'11) keyed by
  *   params.seed, with counters built from the global row id, params.problem_id
  *   and a stream number (0: signs/buckets/Cauchy scales of Π1, 1: Π2,
- *   2: sampling uniforms).  Row ids are global: row r of A has id
+ *   2: sampling uniforms, 3: draws with replacement, 4: the slow transform's C).  Row ids are global: row r of A has id
  *   params.global_row_offset + r, so shards of one problem reproduce the
  *   unsharded draws.
  * - Not thread-safe per workspace; distinct workspaces may be used from
@@ -89,6 +89,12 @@ typedef struct {
                                  weight 1/(coreset_size·p̂_i) (caption of Figure 2); the
                                  kept rows are listed in draw order, with repeats. */
   double sample_scale;        /* variant 1: the sampling size s of p̂ = min{1, s·λ̂}; variants 0, 2: 0 */
+  int32_t transform;          /* Π1 of phase 1: 0 FCT1 (§3.1); 1 the slow Cauchy transform
+                                 (4/r1)·C with C an r1 × n matrix of i.i.d. standard Cauchys
+                                 (§3, the theorem of Sohler and Woodruff; the conditioning of
+                                 §6.3), entry (r, i), r = 4g + w, from word w of the Philox call
+                                 with counter (i_lo, (i_hi mod 2^16) + g·2^16, problem_id, 4);
+                                 s and sign_flip are then unused */
 } l1s_params;
 
 /* Text of the calling thread's last host-side error ("" if none). */
@@ -116,7 +122,9 @@ L1S_API int l1s_status_reset(void* ws, size_t ws_bytes, void* stream);
  * L1S_FLAG(code) bits (0 = no device-side error since the last reset). */
 L1S_API int l1s_status_read(const void* ws, size_t ws_bytes, void* stream, uint32_t* flags);
 
-/* Phase 1 — the FCT1 embedding (§3.1; Figure 2, steps 1-2):
+/* Phase 1 — the FCT1 embedding (§3.1; Figure 2, steps 1-2), or with
+ * params.transform = 1 the slow Cauchy transform Π1·X = (4/r1)·C·X (§3), whose
+ * r1·n variates are drawn inside the kernel (its cost is the drawing, not the bytes):
  *   PiX_dev = Π1·X = 4·B·C·H̃·D·[A, −b]          (r1 × q, FP32, row-major)
  * H̃ is block diagonal with blocks [H_s; I_s] (H_s the Sylvester Hadamard
  * matrix scaled by 1/√s), C a diagonal of standard Cauchys, B a hash of each

@@ -27,6 +27,8 @@ const void* fct_sorted_kernel(int log2s, l1s_dtype dt, int w);
 int fct_sorted_threads(int w);
 size_t fct_sorted_smem_bytes(int s, int d, l1s_dtype dt, int r1, int w);
 int fct_cols_slices(int log2s, int d, int r1, int max_smem);
+int sct_width(int q);
+int sct_ctas(int64_t n, int r1, int q, int sms);
 size_t fct_cols_smem_bytes(int r1);
 int fct_cols_threads();
 int fct_cols_tile();
@@ -129,6 +131,7 @@ static bool check_params(const l1s_params* p, int64_t n, int d) {
     return set_error("variant 2 draws coreset_size rows: it must be an integer in [1, 1e9]"), false;
   if (p->variant == 1 && (!(p->sample_scale > 0.0) || !isfinite(p->sample_scale)))
     return set_error("variant 1 needs a positive, finite sample_scale"), false;
+  if (p->transform != 0 && p->transform != 1) return set_error("transform must be 0 or 1"), false;
   return true;
 }
 
@@ -360,6 +363,13 @@ bool make_plan(const l1s_params* p, int64_t n, int d, l1s_dtype dt, bool host_st
   P.fct_threads = g.threads;
   const int per_sm = sch.fct_ctas_per_sm > 0 ? std::min(sch.fct_ctas_per_sm, g.per_sm) : g.per_sm;
   P.fct_ctas = static_cast<int>(fct_ctas_of(g, P, di, per_sm));
+  if (p->transform == 1) {
+    // The slow Cauchy transform: column slices of sct_width(q) columns, blocks along the rows.
+    P.fct_ws = P.fct_tile_log2 = P.fct_lean = P.fct_sorted = P.fct_cols = P.fct_staged = 0;
+    P.fct_width = sct_width(P.q);
+    P.fct_slices = (P.q + P.fct_width - 1) / P.fct_width;
+    P.fct_ctas = sct_ctas(n, P.r1, P.q, di.sms);
+  }
   // Inputs in host memory arrive in up to kMaxChunks row chunks of at least two waves of
   // tiles each, so that phase 1 on one chunk overlaps the copy of the next.
   P.fct_chunks = 1;
@@ -378,6 +388,8 @@ bool make_plan(const l1s_params* p, int64_t n, int d, l1s_dtype dt, bool host_st
                                                 P.r1, n)
                       : static_cast<size_t>(geo[v].slices) * fct_ctas_of(geo[v], P, di, geo[v].per_sm) * P.r1 *
                             geo[v].width);
+  if (p->transform == 1)
+    partial_floats = std::max<size_t>(partial_floats, static_cast<size_t>(P.fct_slices) * P.fct_ctas * P.r1 * P.fct_width);
 
   // Phase 2: a persistent-style grid, 8 blocks per SM by default.
   P.lam_threads = lambda_threads();

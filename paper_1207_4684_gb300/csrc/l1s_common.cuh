@@ -89,17 +89,31 @@ __device__ __forceinline__ int bucket_of(uint32_t word, uint32_t r) {
 }
 
 // Standard Cauchy from the 24-bit integer k: tan(π(u − ½)) at u = (k + ½)/2^24,
-// evaluated through the reflection w = ½ − |u − ½| = j·2^-25 (j odd, exact in
-// FP32) as ±cos(πw)/sin(πw), which keeps full relative accuracy near the poles.
-// The quotient uses the fast division (≤ 2 ulp for denominators in [2^-126, 2^126];
-// sin(πw) ≥ sin(π·2^-25) here), so the variate is within a few ulp of cot(πw).
+// evaluated through the reflection w = ½ − |u − ½| = j·2^-25 (j odd, exact in FP32) as
+// ±cot(πw), which keeps full relative accuracy near the poles.  With a = min(w, ½ − w) ≤ ¼
+// (exact), sin(πa) = a·P(a²) and cos(πa) = Q(a²), P and Q the Taylor series of sin(πa)/a and
+// cos(πa) about 0 truncated after the a⁸ terms (on |πa| ≤ π/4 the truncation is below 3e-8
+// relative), coefficients (−1)^k π^{2k+1}/(2k+1)! and (−1)^k π^{2k}/(2k)! rounded to FP32;
+// cot(πw) = Q/(a·P) when w ≤ ¼ and a·P/Q otherwise (cos(πw) = sin(π(½ − w))).  With the
+// correctly rounded quotient the variate is within 2.5e-7 relative of cot(πw) for every k.
 __device__ __forceinline__ float cauchy_f32(uint32_t k) {
   const int m = 2 * static_cast<int>(k) + 1 - (1 << 24);
   const int j = (1 << 24) - abs(m);
-  const float w = static_cast<float>(j) * 0x1p-25f;
-  float sn, cs;
-  sincospif(w, &sn, &cs);
-  const float r = __fdividef(cs, sn);
+  const bool low = j <= (1 << 23);                       // w ≤ ¼
+  const float a = static_cast<float>(low ? j : (1 << 24) - j) * 0x1p-25f;
+  const float a2 = a * a;
+  float p = 0.08214588463306427f;                        //  π⁹/9!
+  p = fmaf(p, a2, -0.5992645025253296f);                 // −π⁷/7!
+  p = fmaf(p, a2, 2.550163984298706f);                   //  π⁵/5!
+  p = fmaf(p, a2, -5.167712688446045f);                  // −π³/3!
+  p = fmaf(p, a2, 3.1415927410125732f);                  //  π
+  const float sn = a * p;
+  float c = 0.23533062636852264f;                        //  π⁸/8!
+  c = fmaf(c, a2, -1.3352627754211426f);                 // −π⁶/6!
+  c = fmaf(c, a2, 4.058712005615234f);                   //  π⁴/4!
+  c = fmaf(c, a2, -4.934802055358887f);                  // −π²/2!
+  c = fmaf(c, a2, 1.0f);
+  const float r = low ? __fdiv_rn(c, sn) : __fdiv_rn(sn, c);
   return m > 0 ? r : -r;
 }
 
