@@ -53,10 +53,11 @@ def parse():
                     help="time eager calls instead of replays of the step captured as a CUDA graph")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the other forms (measured after the main line's timed region)")
-    ap.add_argument("--variants", default="bf16,colscale,optimized,replacement,multi,t2rows_bf16,batched",
+    ap.add_argument("--variants", default="bf16,colscale,optimized,replacement,multi,sct,t2rows_bf16,batched",
                     help="comma-separated forms to measure after the main line: bf16 (the main data streamed as "
-                         "BF16), colscale (n = 2^22, d = 16, FP32), optimized, replacement, multi (on the n = 2^22 "
-                         "data), t2rows_bf16 (n = 2^24, d = 32, BF16), batched")
+                         "BF16), colscale (n = 2^22, d = 16, FP32), optimized, replacement, multi, sct (the slow "
+                         "Cauchy transform; these on the n = 2^22 data), t2rows_bf16 (n = 2^24, d = 32, BF16), "
+                         "batched")
     return ap.parse_args()
 
 
@@ -324,6 +325,32 @@ def colscale_variant(L, dev, stream, args, peak: float) -> tuple:
              "value": n / (ms / 1e3), "ms_per_step": ms, "step_frac": ab["step"] / (ms / 1e3) / 1e9 / peak,
              "phase_ms": phase, "phase1_frac": ab["phase1"] / (phase["fct_embed"] / 1e3) / 1e9 / peak,
              "coreset_rows": kept}, A, b, w)
+
+
+def sct_variant(L, dev, stream, args, A, b, w, plain_ms: float, fct1_ms: float) -> dict:
+    """The slow Cauchy transform as Π1 (§3; the conditioning of §6.3) on the same data:
+    steps 1-7 with Π1·X = (4/r1)·C·X.  Its cost is drawing r1·n Cauchy variates (one Philox
+    call per four), so its phase 1 is reported against the SM issue rate, not HBM."""
+    import torch
+
+    n, d = A.shape
+    q = d + 1
+    prm = L.make_params(1, w.r1, w.r2, w.coreset, seed=w.seed, problem_id=w.problem_id, transform=1)
+    ws = L.workspace(prm, n, d, device=dev)
+    cap = int(2 * w.coreset) + 64
+    idx = torch.empty(cap, dtype=torch.int64, device=dev)
+    wts = torch.empty(cap, dtype=torch.float64, device=dev)
+    cnt = torch.zeros(1, dtype=torch.int64, device=dev)
+    ms = _time_step_ms(lambda st: L.l1_coreset(A, b, prm, cap, idx, wts, None, cnt, ws, stream=st), stream, args)
+    kept = int(cnt.item())
+    phase = _phase_ms(L, A, b, prm, cap, q, dev, stream, 2, max(3, args.steps // 4))
+    del ws
+    variates = n * w.r1
+    return {"workload": w.name, "transform": "slow Cauchy transform (4/r1)*C", "value": n / (ms / 1e3),
+            "ms_per_step": ms, "phase_ms": phase, "coreset_rows": kept,
+            "variates_per_s": variates / (phase["fct_embed"] / 1e3),
+            "fma_per_s": variates * q / (phase["fct_embed"] / 1e3),
+            "phase1_vs_fct1": phase["fct_embed"] / fct1_ms, "speedup_vs_f32_plain": plain_ms / ms}
 
 
 def bf16_variant(L, dev, stream, args, peak: float) -> dict:
@@ -783,7 +810,7 @@ def run_gpu(args) -> None:
             variants["bf16"] = bf16_same_data_variant(L, dev, stream, args, A, b, w, peaks["hbm_gbs"], ws, ms_per_step)
         del ws, A, b
         torch.cuda.empty_cache()
-        if want & {"colscale", "optimized", "replacement", "multi"}:
+        if want & {"colscale", "optimized", "replacement", "multi", "sct"}:
             line_c, A1, b1, w1 = colscale_variant(L, dev, stream, args, peaks["hbm_gbs"])
             if "colscale" in want:
                 variants["colscale"] = line_c
@@ -797,6 +824,10 @@ def run_gpu(args) -> None:
             torch.cuda.empty_cache()
             if "multi" in want:
                 variants["multi"] = multi_variant(L, dev, stream, args, A1, b1, w1, peaks["hbm_gbs"])
+            torch.cuda.empty_cache()
+            if "sct" in want:
+                variants["sct"] = sct_variant(L, dev, stream, args, A1, b1, w1, line_c["ms_per_step"],
+                                              line_c["phase_ms"]["fct_embed"])
             del A1, b1
             torch.cuda.empty_cache()
         if "t2rows_bf16" in want:

@@ -185,6 +185,17 @@ L1S_API int l1_lambda_noalloc(const void* A_dev, int64_t lda, l1s_dtype dtype, c
                               int64_t n, int32_t d, const double* M_dev, const l1s_params* params,
                               float* lambda_dev, double* lambda_sum_dev, void* stream);
 
+/* The ℓ1 well-conditioned basis U = X·R⁻¹ of §4.1 (Figure 1) with R the q × q upper
+ * triangular factor from l1_condition (device, FP64, row-major), and its exact ℓ1 row
+ * norms ‖U_(i)‖₁, the ℓ1 leverage scores that λ estimates (Figure 2, step 5); FP64, one
+ * forward substitution per row (R⁻¹ is not formed).  Outputs (device, may be NULL):
+ * U_dev (n × q FP64, row-major), rownorm_dev (n FP64) and *total_dev = Σ_i ‖U_(i)‖₁ = ‖U‖₁
+ * (the α of an (α, β)-conditioned basis, §6.1), summed in a fixed order.  The workspace
+ * needs 256 + 8·1024 bytes (256-byte aligned).  Asynchronous on `stream`. */
+L1S_API int l1_basis(const void* A_dev, int64_t lda, l1s_dtype dtype, const float* b_dev, int64_t n,
+                     int32_t d, const double* R_dev, double* U_dev, double* rownorm_dev,
+                     double* total_dev, void* ws, size_t ws_bytes, void* stream);
+
 /* Phases 2-3 (Figure 2, steps 4-7): λ as in l1_lambda, Σλ, τ = m_s/Σλ in FP64,
  * p̂_i = min(1, τ·λ_i) in FP64, row i kept iff u_i < p̂_i with its 53-bit
  * uniform u_i (exact FP64 comparison).  Kept rows are written in ascending

@@ -15,6 +15,7 @@ Modules, in the order of the method (Figure 2, FastCauchyRegression):
   leverage   λ_i = lower median_j |(X·M)_ij| and exact ‖U_(i)‖₁ (steps 4-5)
   sampling   p̂_i = min(1, τ·λ_i), τ = m_s/Σλ, Bernoulli keep u_i < p̂_i (steps 6-7)
   solve      weighted LAD by LP, brute force and weighted median (step 8)
+  quality    κ̄₁(U), the conditioning metric of §6.1, from d exact ℓ1 regressions
   pipeline   the steps chained, with every intermediate returned
 
 Parity status: every function above is pinned by the CPU tests in

@@ -8,7 +8,11 @@
 // its blocks do not fit in shared memory (q near 129), a single thread block runs
 // Householder reflections on a column-major FP64 copy of Π1·X instead, held in
 // shared memory when it fits (r1·q·8 bytes ≤ 160 KB) and in the workspace
-// (L2-resident) otherwise.
+// (L2-resident) otherwise.  CholeskyQR2 squares the condition number in its Gram
+// matrices and breaks down when Π1·X is conditioned worse than about 1e7-1e8; a
+// breakdown (a Cholesky pivot that is not positive, or a non-finite R or M) is recorded
+// in the status block, and the Householder kernel, enqueued after the two passes, then
+// redoes the step (it returns at once otherwise), so the decision stays on the device.
 #include <stddef.h>
 
 #include <algorithm>
@@ -64,9 +68,11 @@ struct CondArgs {
   double* M_user;
   uint32_t* flags;
   int pi2_gauss;      // 1: Gaussian Π2 (OptimizedFastCauchyRegression)
+  const uint32_t* only_if;   // non-NULL: run only when *only_if != 0 (CholeskyQR2 broke down)
 };
 
 __global__ void __launch_bounds__(kCondThreads) condition_kernel(const CondArgs a) {
+  if (a.only_if && *a.only_if == 0u) return;
   extern __shared__ __align__(16) double cond_smem[];
   __shared__ double scratch[33];
   __shared__ double s_vtv;
@@ -195,6 +201,7 @@ struct Cond2Args {
   double* R_user;
   double* M_user;
   uint32_t* flags;
+  uint32_t* breakdown;   // set when a Cholesky factorisation fails or R, M are not finite
   int pi2_ready;         // 1: Π2 is already in pi2 (drawn by the phase-1 reduction)
   int pi2_gauss;         // 1: Gaussian Π2 (OptimizedFastCauchyRegression)
 };
@@ -528,22 +535,25 @@ __global__ void __launch_bounds__(kGramThreads) cond2_kernel(const Cond2Args a) 
   }
   __syncthreads();
   if (PASS == 0) {
-    if (tid == 0 && !s_ok) raise_flag(a.flags, L1S_ERR_RANK_DEFICIENT);
+    if (tid == 0) *a.breakdown = s_ok ? 0u : 1u;     // the Householder kernel redoes the step
     for (int e = tid; e < q * q; e += blockDim.x) a.R1[e] = Rc[e];
     for (int e = tid; e < q; e += blockDim.x) a.R1dinv[e] = dn[e];
   } else {
     double* Rs = sm2 + L.R;
     double* Ms = sm2 + L.M;
+    const bool broke0 = *a.breakdown != 0u || !s_ok;
     if (tid < 32) {
-      // rank test over the columns, one lane per column: R_kk = (R2)_kk·(R1)_kk
+      // rank test over the columns, one lane per column: R_kk = (R2)_kk·(R1)_kk (skipped after a
+      // breakdown: the Householder kernel runs its own)
       bool bad = false;
       for (int k = tid; k < q; k += 32) {
         const double rkk = Rc[k * q + k] * R1s[k * q + k];
         if (!(rkk > kRankTol * a.colnorm[k]) || !isfinite(rkk)) bad = true;
       }
-      if (__any_sync(0xffffffffu, bad) || !s_ok) {
+      if (__any_sync(0xffffffffu, bad) && !broke0) {
         if (tid == 0) raise_flag(a.flags, L1S_ERR_RANK_DEFICIENT);
       }
+      if (broke0 && tid == 0) *a.breakdown = 1u;
     }
     // M = R⁻¹·Π2.  q ≤ 32: R = R2·R1 first, then one right-looking back substitution;
     // wider X: R1⁻¹·(R2⁻¹·Π2) by two, which avoids the q³ product.
@@ -580,6 +590,7 @@ __global__ void __launch_bounds__(kGramThreads) cond2_kernel(const Cond2Args a) 
       a.M64[e] = m;
       a.M32[e] = static_cast<float>(m);
       if (a.M_user) a.M_user[e] = m;
+      if (!isfinite(m)) *a.breakdown = 1u;
     }
     if (a.R_user && small) {
       for (int e = tid; e < q * q; e += blockDim.x) {
@@ -631,7 +642,8 @@ size_t cond2_scratch_bytes(int r1, int q, int sms) {
 }
 
 bool launch_condition_householder(const Plan& pl, const float* pix, const l1s_params* p, double* R_user,
-                                  double* M_user, unsigned char* ws, cudaStream_t st);
+                                  double* M_user, unsigned char* ws, cudaStream_t st,
+                                  const uint32_t* only_if = nullptr);
 
 bool launch_condition(const Plan& pl, const float* pix, const l1s_params* p, double* R_user,
                       double* M_user, unsigned char* ws, cudaStream_t st, bool pi2_ready) {
@@ -675,16 +687,20 @@ bool launch_condition(const Plan& pl, const float* pix, const l1s_params* p, dou
     return false;
   if (!cuda_ok(cudaMemsetAsync(a.ticket, 0, sizeof(unsigned int) * (groups + 1), st), "reset conditioning tickets"))
     return false;
+  a.breakdown = &reinterpret_cast<StatusBlock*>(ws + pl.off_status)->qr_breakdown;
   cond2_kernel<0><<<grid, kGramThreads, smem, st>>>(a);
   cond2_kernel<1><<<grid, kGramThreads, smem, st>>>(a);
   count_launch(2);
-  return cuda_ok(cudaGetLastError(), "launch condition");
+  if (!cuda_ok(cudaGetLastError(), "launch condition")) return false;
+  // After a breakdown (Π1·X too ill-conditioned for the Gram matrices), Householder QR.
+  return launch_condition_householder(pl, pix, p, R_user, M_user, ws, st, a.breakdown);
 }
 
-// The one-block Householder variant (wide X).
+// The one-block Householder variant (wide X, or after a CholeskyQR2 breakdown when only_if is set).
 bool launch_condition_householder(const Plan& pl, const float* pix, const l1s_params* p, double* R_user,
-                                  double* M_user, unsigned char* ws, cudaStream_t st) {
+                                  double* M_user, unsigned char* ws, cudaStream_t st, const uint32_t* only_if) {
   CondArgs a;
+  a.only_if = only_if;
   a.pix = pix;
   a.r1 = pl.r1;
   a.q = pl.q;
@@ -699,6 +715,7 @@ bool launch_condition_householder(const Plan& pl, const float* pix, const l1s_pa
   a.R_user = R_user;
   a.M_user = M_user;
   a.flags = reinterpret_cast<uint32_t*>(ws + pl.off_status);
+  a.pi2_gauss = p->variant == 1 ? 1 : 0;
   const size_t bytes = sizeof(double) * static_cast<size_t>(pl.r1) * pl.q;
   a.in_smem = bytes <= kCondSmemMax ? 1 : 0;
   const size_t smem = a.in_smem ? bytes : 0;

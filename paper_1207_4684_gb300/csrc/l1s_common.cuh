@@ -44,6 +44,7 @@ struct StatusBlock {
   double irls_eta;       // IRLS smoothing floor
   int32_t irls_iters;
   uint32_t cond_ticket;  // blocks of the conditioning pass that have finished
+  uint32_t qr_breakdown; // 1: CholeskyQR2 broke down (the Householder QR then redoes the step)
 };
 
 __device__ __forceinline__ void raise_flag(uint32_t* flags, int code) {

@@ -380,13 +380,24 @@ __global__ void __launch_bounds__(kIrlsThreads) irls_polish_kernel(const IrlsArg
     s_fb = INFINITY;
   }
   __syncthreads();
-  // The d rows with the smallest |r| at the IRLS iterate (the float |r| sit in scratch).
+  // The d rows with the smallest |r| at the IRLS iterate (the float |r| sit in scratch),
+  // skipping exact copies of rows already taken: copies have equal |r|, so only ties are
+  // compared, and a vertex needs d distinct rows.
+  __shared__ float zr[kMaxD + 1];
   for (int k = 0; k < d && s_ok; ++k) {
     float best = INFINITY;
     int64_t bi = -1;
     for (int64_t i = tid; i < S; i += blockDim.x) {
       const float v = a.scratch[i];
       if (v < best) {
+        bool copy = false;
+        for (int m = 0; m < k && !copy; ++m) {
+          if (zr[m] != v) continue;
+          bool same = true;
+          for (int c = 0; c < q && same; ++c) same = a.X[i * q + c] == a.X[Z[m] * q + c];
+          copy = same;
+        }
+        if (copy) continue;
         best = v;
         bi = i;
       }
@@ -405,6 +416,7 @@ __global__ void __launch_bounds__(kIrlsThreads) irls_polish_kernel(const IrlsArg
       if (idx < 0) {
         s_ok = 0;
       } else {
+        zr[k] = a.scratch[idx];
         a.scratch[idx] = INFINITY;
         Z[k] = idx;
       }

@@ -82,6 +82,7 @@ _SIGS = {
     "fct_embed": (C.c_int, [_P, _I64, C.c_int, _P, _I64, _I32, _PP, _P, _P, _SZ, _P]),
     "l1_condition": (C.c_int, [_P, _I32, _I32, _PP, _P, _P, _P, _SZ, _P]),
     "l1_lambda": (C.c_int, [_P, _I64, C.c_int, _P, _I64, _I32, _P, _PP, _P, _P, _P, _SZ, _P]),
+    "l1_basis": (C.c_int, [_P, _I64, C.c_int, _P, _I64, _I32, _P, _P, _P, _P, _P, _SZ, _P]),
     "l1_sample": (C.c_int, [_P, _I64, C.c_int, _P, _I64, _I32, _P, _PP, _I64, _P, _P, _P, _P, _P, _P,
                             _SZ, _P]),
     "l1_sample_from_p": (C.c_int, [_P, _I64, _PP, _I64, _P, _P, _P, _SZ, _P]),
@@ -232,6 +233,15 @@ def l1_coreset_host(A, b, params: Params, capacity: int, idx, w, count, ws, stre
     n, d, lda, dt = _matrix(A)
     return load().l1_coreset_host(_ptr(A, False), lda, dt, _ptr(b), n, d, C.byref(params), capacity, _ptr(idx),
                                   _ptr(w), _ptr(count), _ptr(ws), ws.numel(), _stream(stream))
+
+
+def l1_basis(A, b, R, U=None, rownorm=None, total=None, ws=None, stream=None) -> None:
+    """U = [A, −b]·R⁻¹ (FP64), its exact ℓ1 row norms and ‖U‖₁ (device tensors, each may be None)."""
+    n, d, lda, dt = _matrix(A)
+    if ws is None:
+        ws = torch.empty(256 + 8 * 1024, dtype=torch.uint8, device=A.device)
+    _check(load().l1_basis(_ptr(A, False), lda, dt, _ptr(b), n, d, _ptr(R), _ptr(U), _ptr(rownorm), _ptr(total),
+                           _ptr(ws), ws.numel(), _stream(stream)), "l1_basis")
 
 
 def l1_solve(coreset, w, count, capacity: int, d: int, max_iter: int, x, objective, ws, stream=None) -> None:

@@ -11,5 +11,6 @@ from .inputs import (  # noqa: F401
     WORKLOADS,
     make_problem,
     make_batched_problems,
+    kappa_test_matrix,
     r1_for,
 )

@@ -232,3 +232,31 @@ def make_batched_problems(count: int = 256, seed: int = 0,
                      "laplace_outliers", seed=seed * 100003 + p + 1, problem_id=p)
         out.append(make_problem(w))
     return out
+
+
+def kappa_test_matrix(kind: str, n: int, d: int, seed: int = 0) -> np.ndarray:
+    """The randomly generated ill-conditioned test matrices of the conditioning study (§6.1),
+    as float32 (n × d):
+
+    A1 = D1·G1·D2·G2 with D1 = diag(linspace(1, 10^4, n)), G1 ∈ R^{n×d} and G2 ∈ R^{d×d}
+         standard Gaussian, D2 = diag(linspace(1, 10^4, d)): ill-conditioned, and its bottom
+         rows tend to have high leverage;
+    A2 = E·G with G ∈ R^{d×d} standard Gaussian and E ∈ R^{n×d} whose first d−1 rows are
+         e_1 … e_{d−1} and whose other n−d+1 rows are all e_d: the first d−1 rows have very
+         high leverage, the rest identical and very low.
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    if kind == "A1":
+        g1 = rng.standard_normal((n, d))
+        g2 = rng.standard_normal((d, d))
+        d1 = np.linspace(1.0, 1e4, n)
+        d2 = np.linspace(1.0, 1e4, d)
+        a = (d1[:, None] * g1) @ (d2[:, None] * g2)
+    elif kind == "A2":
+        g = rng.standard_normal((d, d))
+        a = np.empty((n, d))
+        a[: d - 1] = g[: d - 1]
+        a[d - 1:] = g[d - 1]
+    else:
+        raise ValueError(f"unknown test matrix {kind}")
+    return a.astype(np.float32)

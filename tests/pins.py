@@ -14,7 +14,7 @@ import math
 import numpy as np
 from scipy import stats
 
-from oracle import condition, fct, leverage, pipeline, rng, sampling, sct, solve
+from oracle import condition, fct, leverage, pipeline, quality, rng, sampling, sct, solve
 
 
 # ----------------------------------------------------------------- Hadamard
@@ -410,7 +410,7 @@ def check_scaled_probabilities(seed: int = 31) -> None:
 def _all_checks():
     return ALL_CHECKS + [check_bf16_round, check_gaussian_pi2, check_gaussian_lambda_distribution,
                          check_scaled_probabilities, check_multiple_regression, check_with_replacement,
-                         check_sct_draws, check_sct_stability, check_sct_embedding_bound]
+                         check_sct_draws, check_sct_stability, check_sct_embedding_bound, check_kappa_bar]
 
 
 # ----------------------------------------------------------------- slow Cauchy transform
@@ -523,3 +523,29 @@ def check_with_replacement(seed: int = 23) -> None:
         est.append(float((ww * r[ii]).sum()))
     est = np.array(est)
     assert abs(est.mean() - r.sum()) < 4 * est.std(ddof=1) / math.sqrt(len(est)), "estimator biased"
+
+
+# ----------------------------------------------------------------- conditioning quality (§6.1)
+def check_kappa_bar(seed: int = 13) -> None:
+    """κ̄₁: the identity basis I_d has α = d and min_{‖z‖∞=1} ‖z‖₁ = 1, so κ̄₁ = d (closed form);
+    κ̄₁ is scale invariant (§6.1); and for a small U with d = 2 the minimum over the boundary of
+    the unit box, found by brute force over every breakpoint of the piecewise-linear ‖U·z‖₁ on
+    each face (z = (±1, t) or (t, ±1), t at a zero of some U_i·z, or t = ±1), matches the d
+    regressions."""
+    for d in (1, 2, 5):
+        assert abs(quality.kappa_bar_1(np.eye(d)) - d) < 1e-9, f"κ̄₁(I_{d}) != {d}"
+    g = np.random.default_rng(seed)
+    U = g.standard_normal((7, 2)) * np.array([1.0, 30.0])
+    k = quality.kappa_bar_1(U)
+    assert abs(quality.kappa_bar_1(123.0 * U) - k) < 1e-9 * k, "κ̄₁ not scale invariant"
+    cands = []
+    for fixed in (0, 1):
+        free = 1 - fixed
+        ts = np.concatenate([[-1.0, 1.0], -U[:, fixed] / U[:, free]])
+        for t in ts[np.abs(ts) <= 1.0]:
+            z = np.empty(2)
+            z[fixed], z[free] = 1.0, t
+            cands.append(np.abs(U @ z).sum())
+    brute = min(cands)
+    got = quality.min_l1_on_unit_box(U)
+    assert abs(got - brute) <= 1e-9 * brute, (got, brute)
