@@ -209,6 +209,31 @@ L1S_API int l1_sample(const void* A_dev, int64_t lda, l1s_dtype dtype, const flo
               int64_t capacity, int64_t* idx_dev, double* w_dev, double* coreset_dev,
               int64_t* count_dev, float* lambda_dev, void* ws, size_t ws_bytes, void* stream);
 
+/* Figure 2, steps 6-7 from a caller-given λ (lambda_dev, n floats, e.g. from l1_lambda)
+ * and a caller-given Σλ (*lambda_total_dev, FP64 on the device), k times over:
+ * τ = m_s/Σλ, p̂_i = min(1, τ·λ_i) in FP64, and coreset j (0 ≤ j < k) keeps row i iff
+ * u_i < p̂_i with the sampling uniforms of problem id params.problem_id + j (the same
+ * exact FP64 decision as l1_sample).  Σλ being an input, row shards of one problem
+ * (each with its global_row_offset) sample with the sum of the shards' Σλ and together
+ * keep exactly the rows the unsharded call keeps; with Σλ from l1_lambda and k = 1 the
+ * result is l1_sample's.  k coresets cost one read of λ and k Philox calls per two rows
+ * (the k approximate solutions of one pass over the data, §6.3).  params.variant 1
+ * (OptimizedFastCauchyRegression) uses p̂ = min(1, sample_scale·λ_i) and ignores
+ * lambda_total_dev (may then be NULL); variant 2 (with replacement) is refused.
+ * Outputs of coreset j, rows in ascending order: idx_dev[j·capacity + t], w_dev[j·capacity
+ * + t] (1/p̂), coreset_dev[(j·capacity + t)·q + c] (FP64 [A_i, −b_i]; may be NULL, and
+ * then A_dev and b_dev are not read) for t < min(count, capacity), and count_dev[j]
+ * (the number kept; above capacity the CAPACITY status bit is set).  1 ≤ k ≤ 1024.
+ * The workspace is sized by l1s_sample_lambda_workspace_size (for k = 1 it is the
+ * l1s_workspace_size of the same arguments). */
+L1S_API int l1_sample_lambda(const void* A_dev, int64_t lda, l1s_dtype dtype, const float* b_dev,
+                             int64_t n, int32_t d, const float* lambda_dev,
+                             const double* lambda_total_dev, const l1s_params* params, int32_t k,
+                             int64_t capacity, int64_t* idx_dev, double* w_dev, double* coreset_dev,
+                             int64_t* count_dev, void* ws, size_t ws_bytes, void* stream);
+L1S_API int l1s_sample_lambda_workspace_size(const l1s_params* params, int64_t n, int32_t d,
+                                             l1s_dtype dtype, int32_t k, size_t* bytes);
+
 /* The Bernoulli step alone (Figure 2, step 7) from caller-given probabilities
  * p_dev (n FP64 values in [0,1]): row i kept iff u_i < p_i.  Writes up to
  * capacity ascending indices and *count_dev. */
@@ -238,14 +263,28 @@ L1S_API int l1_coreset_host(const void* A_host, int64_t lda, l1s_dtype dtype, co
  * Σ_k w_k·|X_k·[x; 1]| over rows X_k = [A_k, −b_k] (coreset_dev, FP64, q per
  * row, count from *count_dev, at most capacity) by FP64 iteratively
  * reweighted least squares, finished by simplex pivots of the LAD linear
- * program from the vertex of the d rows with the smallest residuals, up to a
- * vertex whose optimality the dual multipliers certify.  Writes x_dev (d
+ * program from the vertex of the d rows with the smallest residuals whose A
+ * parts are linearly independent, up to a vertex whose optimality the dual
+ * multipliers certify.  Writes x_dev (d
  * FP64) and *objective_dev (the weighted objective at x_dev).  The status bit
  * L1S_ERR_NOT_CONVERGED is raised when neither the iteration converged nor the
  * vertex was certified optimal. */
 L1S_API int l1_solve(const double* coreset_dev, const double* w_dev, const int64_t* count_dev,
              int64_t capacity, int32_t d, int32_t max_iter, double* x_dev,
              double* objective_dev, void* ws, size_t ws_bytes, void* stream);
+
+/* l1_solve for k coresets side by side (the k approximate solutions of §6.3): coreset j
+ * is rows coreset_dev + j·capacity·q, weights w_dev + j·capacity and count_dev[j], the
+ * layout l1_sample_lambda writes.  Each is solved as l1_solve solves one (its
+ * accumulation spread over fewer blocks, so sums may round differently); writes x_dev
+ * (k × d FP64), objective_dev (k) and, when flags_dev is not NULL, flags_dev[j] = the
+ * status flags of coreset j's solve (L1S_FLAG(L1S_ERR_NOT_CONVERGED) as in l1_solve).
+ * 1 ≤ k ≤ 1024; workspace sized by l1s_solve_many_workspace_size. */
+L1S_API int l1_solve_many(const double* coreset_dev, const double* w_dev, const int64_t* count_dev,
+                          int64_t capacity, int32_t d, int32_t k, int32_t max_iter, double* x_dev,
+                          double* objective_dev, uint32_t* flags_dev, void* ws, size_t ws_bytes,
+                          void* stream);
+L1S_API int l1s_solve_many_workspace_size(int64_t capacity, int32_t d, int32_t k, size_t* bytes);
 
 /* ‖A·x − b‖₁ in FP64 over all n rows (problem statement, §4.2). */
 L1S_API int l1_objective(const void* A_dev, int64_t lda, l1s_dtype dtype, const float* b_dev,

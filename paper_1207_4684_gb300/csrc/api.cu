@@ -63,6 +63,10 @@ bool launch_sample(const Plan& pl, const float* lam, const double* p, const l1s_
                    const void* A, int64_t lda, l1s_dtype dt, const float* b, int64_t capacity,
                    int64_t* idx, double* w, double* coreset, int64_t* count_out, unsigned char* ws,
                    cudaStream_t st, int lam_nsums = 0);
+size_t sample_many_extra_bytes(const Plan& pl, int k);
+bool launch_sample_many(const Plan& pl, const float* lam, const double* lam_total, const l1s_params* prm, int k,
+                        const void* A, int64_t lda, l1s_dtype dt, const float* b, int64_t capacity, int64_t* idx,
+                        double* w, double* coreset, int64_t* count_out, unsigned char* ws, cudaStream_t st);
 bool launch_debug_variates(const l1s_params* p, int64_t row_start, int64_t count, int32_t* bh,
                            int32_t* bi, int32_t* kh, int32_t* ki, float* ch, float* ci, int8_t* sg,
                            uint64_t* ub, cudaStream_t st);
@@ -71,7 +75,8 @@ size_t irls_state_bytes();
 size_t solve_scratch_bytes(int64_t capacity);
 bool launch_solve(const double* X, const double* w, const int64_t* count, int64_t capacity, int d,
                   int max_iter, double* x_out, double* obj_out, int nblocks, double* partials,
-                  void* state, float* scratch, StatusBlock* status, cudaStream_t st);
+                  void* state, float* scratch, StatusBlock* status, cudaStream_t st, int k,
+                  uint32_t* flags_out);
 bool launch_objective(const void* A, int64_t lda, l1s_dtype dt, const float* b, int64_t n, int d,
                       const double* x, double* out, int nblocks, double* partials, cudaStream_t st);
 
@@ -556,6 +561,40 @@ int l1_sample(const void* A, int64_t lda, l1s_dtype dtype, const float* b, int64
   return sample_impl(pl, A, lda, dtype, b, m32, params, capacity, idx, wts, coreset, count, lambda, w, st);
 }
 
+int l1s_sample_lambda_workspace_size(const l1s_params* params, int64_t n, int32_t d, l1s_dtype dtype, int32_t k,
+                                     size_t* bytes) {
+  Plan pl;
+  if (!bytes) return set_error("bytes must not be NULL"), L1S_ERR_INVALID_ARG;
+  if (k < 1 || k > kMaxCoresets) return set_error("k must be in [1, %d]", kMaxCoresets), L1S_ERR_INVALID_ARG;
+  if (!make_plan(params, n, d, dtype, false, &pl)) return L1S_ERR_INVALID_ARG;
+  *bytes = pl.total + sample_many_extra_bytes(pl, k);
+  return L1S_OK;
+}
+
+int l1_sample_lambda(const void* A, int64_t lda, l1s_dtype dtype, const float* b, int64_t n, int32_t d,
+                     const float* lambda, const double* lambda_total, const l1s_params* params, int32_t k,
+                     int64_t capacity, int64_t* idx, double* wts, double* coreset, int64_t* count, void* ws,
+                     size_t ws_bytes, void* stream) {
+  TraceRange trace_("l1_sample_lambda");
+  Plan pl;
+  if (!make_plan(params, n, d, dtype, false, &pl)) return L1S_ERR_INVALID_ARG;
+  if (k < 1 || k > kMaxCoresets) return set_error("k must be in [1, %d]", kMaxCoresets), L1S_ERR_INVALID_ARG;
+  if (params->variant == 2)
+    return set_error("l1_sample_lambda samples without replacement (params.variant 0 or 1)"), L1S_ERR_INVALID_ARG;
+  if (coreset && !check_a(A, lda, b, d)) return L1S_ERR_INVALID_ARG;
+  if (!lambda || (params->variant == 0 && !lambda_total))
+    return set_error("lambda (and lambda_total for variant 0) must not be NULL"), L1S_ERR_INVALID_ARG;
+  if (capacity < 0 || (capacity > 0 && (!idx || !wts)) || !count)
+    return set_error("idx, w (capacity > 0) and count must not be NULL"), L1S_ERR_INVALID_ARG;
+  const size_t need = pl.total + sample_many_extra_bytes(pl, k);
+  if (!ws || reinterpret_cast<uintptr_t>(ws) % 256 || ws_bytes < need)
+    return set_error("workspace too small for l1_sample_lambda: %zu needed", need), L1S_ERR_WORKSPACE;
+  if (!launch_sample_many(pl, lambda, lambda_total, params, k, A, lda, dtype, b, capacity, idx, wts, coreset, count,
+                          static_cast<unsigned char*>(ws), static_cast<cudaStream_t>(stream)))
+    return L1S_ERR_CUDA;
+  return L1S_OK;
+}
+
 int l1_sample_from_p(const double* p, int64_t n, const l1s_params* params, int64_t capacity, int64_t* idx,
                      int64_t* count, void* ws, size_t ws_bytes, void* stream) {
   Plan pl;
@@ -699,7 +738,66 @@ int l1_solve(const double* coreset, const double* wts, const int64_t* count, int
   unsigned char* w = static_cast<unsigned char*>(ws);
   if (!launch_solve(coreset, wts, count, capacity, d, max_iter, x, objective, di.sms,
                     reinterpret_cast<double*>(w + o_part), w + o_state, reinterpret_cast<float*>(w + o_scr),
-                    reinterpret_cast<StatusBlock*>(w + o_status), static_cast<cudaStream_t>(stream)))
+                    reinterpret_cast<StatusBlock*>(w + o_status), static_cast<cudaStream_t>(stream), 1, nullptr))
+    return L1S_ERR_CUDA;
+  return L1S_OK;
+}
+
+// Workspace layout of l1_solve_many: k status blocks, then per coreset the IRLS partials,
+// state and residual scratch.
+struct SolveManyLayout {
+  int nblocks;
+  size_t o_status, o_part, o_state, o_scr, total;
+};
+
+static SolveManyLayout solve_many_layout(int64_t capacity, int d, int k, int sms) {
+  SolveManyLayout L;
+  // About four accumulation blocks per SM over all k coresets, at most one per SM each.
+  L.nblocks = std::max(1, std::min(sms, (4 * sms + k - 1) / k));
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t o = off;
+    off = align_up(off + bytes);
+    return o;
+  };
+  const int q = d + 1;
+  L.o_status = take(std::max<size_t>(256, sizeof(StatusBlock) * static_cast<size_t>(k)));
+  L.o_part = take(sizeof(double) * static_cast<size_t>(L.nblocks) * (irls_entries(q) + 1) * k);
+  L.o_state = take(irls_state_bytes() * static_cast<size_t>(k));
+  L.o_scr = take(solve_scratch_bytes(capacity) * static_cast<size_t>(k));
+  L.total = off;
+  return L;
+}
+
+int l1s_solve_many_workspace_size(int64_t capacity, int32_t d, int32_t k, size_t* bytes) {
+  if (!bytes || d < 1 || d > kMaxD || capacity < 1 || k < 1 || k > kMaxCoresets)
+    return set_error("bad capacity, d or k"), L1S_ERR_INVALID_ARG;
+  const DeviceInfo di = device_info();
+  if (di.device < 0) return set_error("no CUDA device"), L1S_ERR_CUDA;
+  *bytes = solve_many_layout(capacity, d, k, di.sms).total;
+  return L1S_OK;
+}
+
+int l1_solve_many(const double* coreset, const double* wts, const int64_t* count, int64_t capacity, int32_t d,
+                  int32_t k, int32_t max_iter, double* x, double* objective, uint32_t* flags, void* ws,
+                  size_t ws_bytes, void* stream) {
+  TraceRange trace_("l1_solve_many");
+  if (!coreset || !wts || !count || !x || !objective) return set_error("NULL argument"), L1S_ERR_INVALID_ARG;
+  if (d < 1 || d > kMaxD || capacity < 1 || max_iter < 0 || max_iter > 100000 || k < 1 || k > kMaxCoresets)
+    return set_error("bad d, capacity, k or max_iter"), L1S_ERR_INVALID_ARG;
+  const DeviceInfo di = device_info();
+  if (di.device < 0) return set_error("no CUDA device"), L1S_ERR_CUDA;
+  const SolveManyLayout L = solve_many_layout(capacity, d, k, di.sms);
+  if (!ws || reinterpret_cast<uintptr_t>(ws) % 256 || ws_bytes < L.total)
+    return set_error("workspace too small for l1_solve_many: %zu needed", L.total), L1S_ERR_WORKSPACE;
+  unsigned char* w = static_cast<unsigned char*>(ws);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (!cuda_ok(cudaMemsetAsync(w + L.o_status, 0, sizeof(StatusBlock) * static_cast<size_t>(k), st),
+               "status reset"))
+    return L1S_ERR_CUDA;
+  if (!launch_solve(coreset, wts, count, capacity, d, max_iter, x, objective, L.nblocks,
+                    reinterpret_cast<double*>(w + L.o_part), w + L.o_state, reinterpret_cast<float*>(w + L.o_scr),
+                    reinterpret_cast<StatusBlock*>(w + L.o_status), st, k, flags))
     return L1S_ERR_CUDA;
   return L1S_OK;
 }

@@ -31,7 +31,8 @@ int coreset_impl(const Plan& pl, const void* A, int64_t lda, l1s_dtype dtype, co
                  int64_t* count, unsigned char* w, cudaStream_t st);
 bool launch_solve(const double* X, const double* w, const int64_t* count, int64_t capacity, int d,
                   int max_iter, double* x_out, double* obj_out, int nblocks, double* partials,
-                  void* state, float* scratch, StatusBlock* status, cudaStream_t st);
+                  void* state, float* scratch, StatusBlock* status, cudaStream_t st, int k,
+                  uint32_t* flags_out);
 bool launch_objective(const void* A, int64_t lda, l1s_dtype dt, const float* b, int64_t n, int d,
                       const double* x, double* out, int nblocks, double* partials, cudaStream_t st);
 
@@ -160,7 +161,7 @@ static int enqueue_member(const l1s_problem& pr, const Member& m, unsigned char*
     const DeviceInfo di = device_info();
     if (!launch_solve(core, wts, cnt, m.cap, pr.d, 100, pr.x_dev, obj_ws, di.sms,
                       reinterpret_cast<double*>(w + pl.off_irls), w + pl.off_x,
-                      reinterpret_cast<float*>(w + pl.off_objp), sb, st))
+                      reinterpret_cast<float*>(w + pl.off_objp), sb, st, 1, nullptr))
       return L1S_ERR_CUDA;
     if (pr.objective_dev &&
         !launch_objective(pr.A_dev, pr.lda, pr.dtype, pr.b_dev, pr.n, pr.d, pr.x_dev, pr.objective_dev,

@@ -21,6 +21,7 @@ namespace l1s {
 // ----------------------------------------------------------------- limits
 constexpr int kMaxLog2S = 12;       // s ≤ 4096
 constexpr int kMaxD = 128;          // d ≤ 128 (q ≤ 129)
+constexpr int kMaxCoresets = 1024;  // coresets per l1_sample_lambda / l1_solve_many call
 constexpr int kMaxR2 = 64;
 constexpr int kMaxConstM = 129 * 64;
 

@@ -161,6 +161,11 @@ struct CompactArgs {
   double* coreset;            // may be null
   int64_t* count_out;         // may be null
   StatusBlock* status_rw;
+  // Several coresets from one λ (blockIdx.y = coreset j): mask words, block counts and
+  // outputs of coreset j start j·mask_stride words, j·counts_stride counts, j·capacity
+  // rows and j counts further on.
+  int64_t mask_stride = 0;
+  int64_t counts_stride = 0;
 };
 
 // λ of one row with the operation order of the λ kernels (x_0·M_0j, then FMAs over k in
@@ -211,10 +216,17 @@ __global__ void __launch_bounds__(kSmpThreads) sample_compact_kernel(const Compa
   if constexpr (R2C > 0)
     for (int e = threadIdx.x; e < (a.d + 1) * R2C; e += blockDim.x) sM[e] = a.m32[e];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t cj = blockIdx.y;
+  const int q = a.d + 1;
+  const uint64_t* mask = a.mask + cj * a.mask_stride;
+  const int64_t* counts = a.counts + cj * a.counts_stride;
+  int64_t* idx = a.idx ? a.idx + cj * a.capacity : nullptr;
+  double* wout = a.w ? a.w + cj * a.capacity : nullptr;
+  double* cset = a.coreset ? a.coreset + cj * a.capacity * q : nullptr;
   // Offset of this block: Σ counts of the blocks before it (per-thread sums, then warp
   // shuffles and the warp totals in a fixed order).
   int64_t pre = 0;
-  for (int i = tid; i < static_cast<int>(blockIdx.x); i += blockDim.x) pre += a.counts[i];
+  for (int i = tid; i < static_cast<int>(blockIdx.x); i += blockDim.x) pre += counts[i];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) pre += __shfl_xor_sync(0xffffffffu, pre, o);
   if (lane == 0) s_warp[warp] = pre;
@@ -224,9 +236,9 @@ __global__ void __launch_bounds__(kSmpThreads) sample_compact_kernel(const Compa
     for (int w = 0; w < kWarps; ++w) t += s_warp[w];
     s_base = t;
     if (blockIdx.x == gridDim.x - 1) {
-      const int64_t total = t + a.counts[blockIdx.x];
-      if (a.count_out) *a.count_out = total;
-      a.status_rw->count = total;
+      const int64_t total = t + counts[blockIdx.x];
+      if (a.count_out) a.count_out[cj] = total;
+      if (cj == 0) a.status_rw->count = total;
       if (total > a.capacity) raise_flag(&a.status_rw->flags, L1S_ERR_CAPACITY);
     }
   }
@@ -236,10 +248,9 @@ __global__ void __launch_bounds__(kSmpThreads) sample_compact_kernel(const Compa
   const int64_t stop = min(a.n, start + a.chunk);
   const int64_t w0 = start >> 6, w1 = (stop + 63) >> 6;
   const double tau = a.status->tau;
-  const int q = a.d + 1;
   for (int64_t tile = w0; tile < w1; tile += blockDim.x) {
     const int64_t wi = tile + tid;
-    const uint64_t m = wi < w1 ? a.mask[wi] : 0ull;
+    const uint64_t m = wi < w1 ? mask[wi] : 0ull;
     const int64_t c = __popcll(m);
     // inclusive scan of c over the block: within warps by shuffles, then over warp totals
     int64_t incl = c;
@@ -265,15 +276,15 @@ __global__ void __launch_bounds__(kSmpThreads) sample_compact_kernel(const Compa
       bits &= bits - 1;
       const int64_t row = (wi << 6) + bit;
       if (pos < a.capacity) {
-        a.idx[pos] = row;
-        if (a.w) {
+        idx[pos] = row;
+        if (wout) {
           float lam;
           if constexpr (R2C > 0) lam = lambda_recompute<TA, R2C>(a, sM, row);
           else lam = a.lam[row];
-          a.w[pos] = 1.0 / p_hat(tau, lam);
+          wout[pos] = 1.0 / p_hat(tau, lam);
         }
-        if (a.coreset) {
-          double* out = a.coreset + pos * q;
+        if (cset) {
+          double* out = cset + pos * q;
           const TA* src = a.A + row * a.lda;
           for (int k = 0; k < a.d; ++k) {
             const double v = static_cast<double>(load_elem<TA>(src + k));
@@ -321,13 +332,14 @@ bool launch_sample(const Plan& pl, const float* lam, const double* p, const l1s_
   return launch_compact(pl, lam, nullptr, A, lda, dt, b, capacity, idx, w, coreset, count_out, ws, st);
 }
 
-// Ordered compaction of the keep mask (weights from λ, or from λ recomputed with M).
-bool launch_compact(const Plan& pl, const float* lam, const float* m32, const void* A, int64_t lda, l1s_dtype dt,
-                    const float* b, int64_t capacity, int64_t* idx, double* w, double* coreset, int64_t* count_out,
-                    unsigned char* ws, cudaStream_t st) {
-  const uint64_t* mask = reinterpret_cast<const uint64_t*>(ws + pl.off_mask);
-  const int64_t* counts = reinterpret_cast<const int64_t*>(ws + pl.off_counts);
+// Ordered compaction of k keep masks (weights from λ, or from λ recomputed with M).
+static bool launch_compact_many(const Plan& pl, const float* lam, const float* m32, const void* A, int64_t lda,
+                                l1s_dtype dt, const float* b, int64_t capacity, int64_t* idx, double* w,
+                                double* coreset, int64_t* count_out, unsigned char* ws, int k, const uint64_t* mask,
+                                int64_t mask_stride, const int64_t* counts, int64_t counts_stride,
+                                cudaStream_t st) {
   StatusBlock* sb = reinterpret_cast<StatusBlock*>(ws + pl.off_status);
+  const dim3 grid(pl.smp_ctas, k);
   // Weights without λ: λ recomputed from M (r2 ∈ {8, 16} and q ≤ kRecomputeMaxQ only).
   const int r2c = (lam || !w) ? 0 : pl.r2;
   if (r2c && (!m32 || (r2c != 8 && r2c != 16) || pl.q > kRecomputeMaxQ))
@@ -335,20 +347,166 @@ bool launch_compact(const Plan& pl, const float* lam, const float* m32, const vo
   if (dt == L1S_BF16) {
     CompactArgs<uint16_t> c{mask, counts, pl.smp_ctas, pl.n, pl.smp_chunk, capacity, lam, m32, pl.r2, sb,
                             static_cast<const uint16_t*>(A), lda, b, pl.d, pl.pi2_neg_lo, pl.pi2_neg_hi, idx, w,
-                            coreset, count_out, sb};
-    if (r2c == 8) sample_compact_kernel<uint16_t, 8><<<pl.smp_ctas, pl.smp_threads, 0, st>>>(c);
-    else if (r2c == 16) sample_compact_kernel<uint16_t, 16><<<pl.smp_ctas, pl.smp_threads, 0, st>>>(c);
-    else sample_compact_kernel<uint16_t, 0><<<pl.smp_ctas, pl.smp_threads, 0, st>>>(c);
+                            coreset, count_out, sb, mask_stride, counts_stride};
+    if (r2c == 8) sample_compact_kernel<uint16_t, 8><<<grid, pl.smp_threads, 0, st>>>(c);
+    else if (r2c == 16) sample_compact_kernel<uint16_t, 16><<<grid, pl.smp_threads, 0, st>>>(c);
+    else sample_compact_kernel<uint16_t, 0><<<grid, pl.smp_threads, 0, st>>>(c);
   } else {
     CompactArgs<float> c{mask, counts, pl.smp_ctas, pl.n, pl.smp_chunk, capacity, lam, m32, pl.r2, sb,
                          static_cast<const float*>(A), lda, b, pl.d, pl.pi2_neg_lo, pl.pi2_neg_hi, idx, w, coreset,
-                         count_out, sb};
-    if (r2c == 8) sample_compact_kernel<float, 8><<<pl.smp_ctas, pl.smp_threads, 0, st>>>(c);
-    else if (r2c == 16) sample_compact_kernel<float, 16><<<pl.smp_ctas, pl.smp_threads, 0, st>>>(c);
-    else sample_compact_kernel<float, 0><<<pl.smp_ctas, pl.smp_threads, 0, st>>>(c);
+                         count_out, sb, mask_stride, counts_stride};
+    if (r2c == 8) sample_compact_kernel<float, 8><<<grid, pl.smp_threads, 0, st>>>(c);
+    else if (r2c == 16) sample_compact_kernel<float, 16><<<grid, pl.smp_threads, 0, st>>>(c);
+    else sample_compact_kernel<float, 0><<<grid, pl.smp_threads, 0, st>>>(c);
   }
   count_launch(1);
   return cuda_ok(cudaGetLastError(), "launch sample_compact");
+}
+
+bool launch_compact(const Plan& pl, const float* lam, const float* m32, const void* A, int64_t lda, l1s_dtype dt,
+                    const float* b, int64_t capacity, int64_t* idx, double* w, double* coreset, int64_t* count_out,
+                    unsigned char* ws, cudaStream_t st) {
+  return launch_compact_many(pl, lam, m32, A, lda, dt, b, capacity, idx, w, coreset, count_out, ws, 1,
+                             reinterpret_cast<const uint64_t*>(ws + pl.off_mask), 0,
+                             reinterpret_cast<const int64_t*>(ws + pl.off_counts), 0, st);
+}
+
+// ----------------------------------------------------------------- k coresets from one λ
+// Figure 2, steps 6-7 from a caller-given λ and Σλ, k times over: coreset j keeps row i
+// iff u_i^(j) < p̂_i with p̂_i = min(1, τ·λ_i), τ = m_s/Σλ, and u^(j) the sampling uniforms
+// of problem id problem_id + j.  Σλ is read from device memory, so it may be a sum over
+// row shards (the one scalar a sharded problem exchanges before sampling); coreset j is
+// then the j-th call of l1_sample's sampling step with that Σλ.  Each warp reads the λ of
+// 64 rows once and decides them for all k coresets (four coresets' Philox calls at a
+// time), writing mask word j·words + ⌊i/64⌋ and adding to the block's count of coreset j.
+struct MarkManyArgs {
+  const float* lam;
+  int64_t n, chunk;
+  Key2 key;
+  uint32_t problem;
+  int64_t row_offset;
+  int k;
+  const double* lam_total;   // Σλ (device); null: τ = tau_fixed
+  double coreset;            // m_s
+  double tau_fixed;          // OptimizedFastCauchyRegression: p̂ = min(1, s·λ̂)
+  uint64_t* mask;            // [k][mask_stride]
+  int64_t mask_stride;
+  int64_t* counts;           // [k][gridDim.x]
+  StatusBlock* status;
+  int lam_pairs;
+};
+
+constexpr int kManyUnroll = 4;
+
+__global__ void __launch_bounds__(kSmpThreads) sample_mark_many_kernel(const MarkManyArgs a) {
+  __shared__ unsigned int s_cnt[kMaxCoresets];
+  for (int j = threadIdx.x; j < a.k; j += blockDim.x) s_cnt[j] = 0u;
+  double tau;
+  float tau32;
+  bool ok = true;
+  double tot = 0.0;
+  if (a.lam_total) {
+    tot = *a.lam_total;
+    ok = tau_of(tot, a.coreset, &tau, &tau32);
+  } else {
+    tau = a.tau_fixed;
+    tau32 = tau > static_cast<double>(FLT_MAX) ? FLT_MAX : static_cast<float>(tau);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    a.status->lambda_total = tot;
+    a.status->tau = tau;
+    a.status->tau32 = tau32;
+    if (!ok) raise_flag(&a.status->flags, L1S_ERR_ZERO_MASS);
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int64_t start = static_cast<int64_t>(blockIdx.x) * a.chunk;
+  const int64_t stop = min(a.n, start + a.chunk);
+  const bool odd_offset = (a.row_offset & 1) != 0;
+  for (int64_t base = start + 64 * warp; base < stop; base += 64 * static_cast<int64_t>(nwarps)) {
+    const int64_t r0 = base + 2 * lane;
+    float l0 = 0.f, l1 = 0.f;
+    if (a.lam_pairs && r0 + 1 < stop) {
+      const float2 v = *reinterpret_cast<const float2*>(a.lam + r0);
+      l0 = v.x;
+      l1 = v.y;
+    } else {
+      if (r0 < stop) l0 = a.lam[r0];
+      if (r0 + 1 < stop) l1 = a.lam[r0 + 1];
+    }
+    const uint64_t g0 = static_cast<uint64_t>(a.row_offset + r0);
+    for (int j0 = 0; j0 < a.k; j0 += kManyUnroll) {
+      uint32_t w0a[kManyUnroll], w0b[kManyUnroll], w1a[kManyUnroll], w1b[kManyUnroll];
+#pragma unroll
+      for (int u = 0; u < kManyUnroll; ++u) {
+        const uint32_t prob = a.problem + static_cast<uint32_t>(j0 + u);
+        if (!odd_offset) {
+          const uint4 o = draw_row(a.key, g0 >> 1, prob, kStreamSample);
+          w0a[u] = o.x; w0b[u] = o.y; w1a[u] = o.z; w1b[u] = o.w;
+        } else {
+          const uint4 o0 = draw_row(a.key, g0 >> 1, prob, kStreamSample);
+          const uint4 o1 = draw_row(a.key, (g0 + 1) >> 1, prob, kStreamSample);
+          w0a[u] = o0.z; w0b[u] = o0.w; w1a[u] = o1.x; w1b[u] = o1.y;
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kManyUnroll; ++u) {
+        const int j = j0 + u;
+        if (j >= a.k) break;                   // uniform across the block
+        const bool k0 = r0 < stop && keep_row(l0, tau32, tau, w0a[u], w0b[u]);
+        const bool k1 = r0 + 1 < stop && keep_row(l1, tau32, tau, w1a[u], w1b[u]);
+        const uint32_t be = __ballot_sync(0xffffffffu, k0);
+        const uint32_t bo = __ballot_sync(0xffffffffu, k1);
+        if (lane == 0) {
+          const uint64_t m = spread_bits(be) | (spread_bits(bo) << 1);
+          a.mask[j * a.mask_stride + (base >> 6)] = m;
+          if (m) atomicAdd(&s_cnt[j], static_cast<unsigned int>(__popcll(m)));
+        }
+      }
+    }
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < a.k; j += blockDim.x)
+    a.counts[static_cast<int64_t>(j) * gridDim.x + blockIdx.x] = static_cast<int64_t>(s_cnt[j]);
+}
+
+// Bytes past the plan's workspace that k > 1 coresets need (masks and block counts).
+size_t sample_many_extra_bytes(const Plan& pl, int k) {
+  if (k <= 1) return 0;
+  const size_t words = static_cast<size_t>((pl.n + 63) / 64);
+  return align_up(sizeof(uint64_t) * words * k) + align_up(sizeof(int64_t) * static_cast<size_t>(pl.smp_ctas) * k);
+}
+
+bool launch_sample_many(const Plan& pl, const float* lam, const double* lam_total, const l1s_params* prm, int k,
+                        const void* A, int64_t lda, l1s_dtype dt, const float* b, int64_t capacity, int64_t* idx,
+                        double* w, double* coreset, int64_t* count_out, unsigned char* ws, cudaStream_t st) {
+  MarkManyArgs m;
+  m.lam = lam;
+  m.n = pl.n;
+  m.chunk = pl.smp_chunk;
+  m.key = make_key(prm->seed);
+  m.problem = prm->problem_id;
+  m.row_offset = prm->global_row_offset;
+  m.k = k;
+  m.lam_total = prm->variant == 1 ? nullptr : lam_total;
+  m.coreset = prm->coreset_size;
+  m.tau_fixed = prm->variant == 1 ? prm->sample_scale : 0.0;
+  m.status = reinterpret_cast<StatusBlock*>(ws + pl.off_status);
+  m.lam_pairs = (reinterpret_cast<uintptr_t>(lam) % 8 == 0) ? 1 : 0;
+  const size_t words = static_cast<size_t>((pl.n + 63) / 64);
+  if (k == 1) {
+    m.mask = reinterpret_cast<uint64_t*>(ws + pl.off_mask);
+    m.counts = reinterpret_cast<int64_t*>(ws + pl.off_counts);
+  } else {
+    m.mask = reinterpret_cast<uint64_t*>(ws + pl.total);
+    m.counts = reinterpret_cast<int64_t*>(ws + pl.total + align_up(sizeof(uint64_t) * words * k));
+  }
+  m.mask_stride = static_cast<int64_t>(words);
+  sample_mark_many_kernel<<<pl.smp_ctas, pl.smp_threads, 0, st>>>(m);
+  count_launch(1);
+  if (!cuda_ok(cudaGetLastError(), "launch sample_mark_many")) return false;
+  return launch_compact_many(pl, lam, nullptr, A, lda, dt, b, capacity, idx, w, coreset, count_out, ws, k, m.mask,
+                             m.mask_stride, m.counts, pl.smp_ctas, st);
 }
 
 // ----------------------------------------------------------------- with replacement

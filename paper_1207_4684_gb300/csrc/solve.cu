@@ -9,7 +9,8 @@
 // loop stops early once the objective changes by less than 10⁻¹² relative.
 // An ℓ1 optimum is attained at a vertex where d residuals vanish, so the result
 // is then finished by simplex pivots of the LAD linear program, starting from the
-// d rows with the smallest |r_k|, until the dual multipliers certify the vertex
+// d rows with the smallest |r_k| whose A parts are linearly independent, until the
+// dual multipliers certify the vertex
 // optimal; the vertex replaces the iterate when its objective is not larger.
 //
 // Kernels: irls_accum (many blocks: objective and the weighted normal
@@ -47,7 +48,28 @@ struct IrlsArgs {
   double* x_out;
   double* obj_out;
   int max_iter;
+  // k coresets solved side by side (blockIdx.y = coreset j): coreset j's rows, weights,
+  // count, partials, state, status, scratch and outputs start j strides further on.
+  int64_t x_stride;       // doubles between coresets' rows (capacity·q)
+  int64_t part_stride;    // doubles between coresets' partials
+  int64_t scratch_stride; // floats between coresets' scratch
+  uint32_t* flags_out;    // per-coreset status flags (may be null)
 };
+
+__device__ __forceinline__ IrlsArgs for_coreset(IrlsArgs a) {
+  const int64_t j = blockIdx.y;
+  a.X += j * a.x_stride;
+  a.w += j * a.capacity;
+  a.count += j;
+  a.partials += j * a.part_stride;
+  a.state += j;
+  a.status += j;
+  a.scratch += j * a.scratch_stride;
+  a.x_out += j * a.d;
+  if (a.obj_out) a.obj_out += j;
+  if (a.flags_out) a.flags_out += j;
+  return a;
+}
 
 __device__ __forceinline__ int64_t coreset_rows(const IrlsArgs& a) {
   const int64_t c = *a.count;
@@ -67,7 +89,8 @@ __device__ __forceinline__ void pair_of(int e, int q, int& j, int& l) {
   l = row + left;
 }
 
-__global__ void __launch_bounds__(kIrlsThreads) irls_accum_kernel(const IrlsArgs a) {
+__global__ void __launch_bounds__(kIrlsThreads) irls_accum_kernel(const IrlsArgs a0) {
+  const IrlsArgs a = for_coreset(a0);
   if (a.status->irls_done) return;
   extern __shared__ __align__(16) double sm[];
   const int q = a.q;
@@ -142,7 +165,8 @@ __global__ void __launch_bounds__(kIrlsThreads) irls_accum_kernel(const IrlsArgs
 }
 
 // One block: totals, bookkeeping, Cholesky solve of the weighted normal equations.
-__global__ void __launch_bounds__(kIrlsThreads) irls_step_kernel(const IrlsArgs a, int nblocks, int final_pass) {
+__global__ void __launch_bounds__(kIrlsThreads) irls_step_kernel(const IrlsArgs a0, int nblocks, int final_pass) {
+  const IrlsArgs a = for_coreset(a0);
   StatusBlock* st = a.status;
   if (st->irls_done && !final_pass) return;
   extern __shared__ __align__(16) double sm[];
@@ -232,7 +256,8 @@ __global__ void __launch_bounds__(kIrlsThreads) irls_step_kernel(const IrlsArgs 
   }
 }
 
-__global__ void irls_init_kernel(const IrlsArgs a) {
+__global__ void irls_init_kernel(const IrlsArgs a0) {
+  const IrlsArgs a = for_coreset(a0);
   const int tid = threadIdx.x;
   for (int k = tid; k < a.q; k += blockDim.x) a.state->x[k] = k == a.d ? 1.0 : 0.0;
   if (tid == 0) {
@@ -244,7 +269,8 @@ __global__ void irls_init_kernel(const IrlsArgs a) {
   }
 }
 
-__global__ void irls_residuals_kernel(const IrlsArgs a) {
+__global__ void irls_residuals_kernel(const IrlsArgs a0) {
+  const IrlsArgs a = for_coreset(a0);
   const int64_t S = coreset_rows(a);
   for (int64_t k = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; k < S;
        k += static_cast<int64_t>(gridDim.x) * blockDim.x) {
@@ -353,7 +379,8 @@ constexpr int kMaxPivots = 64;
 // of the breakpoints −r_i/g_i, found by bisection on their bit patterns), where the
 // row with that breakpoint enters Z.  The better of this vertex and the IRLS iterate
 // is returned.
-__global__ void __launch_bounds__(kIrlsThreads) irls_polish_kernel(const IrlsArgs a) {
+__global__ void __launch_bounds__(kIrlsThreads) irls_polish_kernel(const IrlsArgs a0) {
+  const IrlsArgs a = for_coreset(a0);
   extern __shared__ __align__(16) double sm[];
   const int q = a.q, d = a.d, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nwarps = blockDim.x >> 5;
@@ -380,24 +407,26 @@ __global__ void __launch_bounds__(kIrlsThreads) irls_polish_kernel(const IrlsArg
     s_fb = INFINITY;
   }
   __syncthreads();
-  // The d rows with the smallest |r| at the IRLS iterate (the float |r| sit in scratch),
-  // skipping exact copies of rows already taken: copies have equal |r|, so only ties are
-  // compared, and a vertex needs d distinct rows.
-  __shared__ float zr[kMaxD + 1];
-  for (int k = 0; k < d && s_ok; ++k) {
+  // The d rows with the smallest |r| at the IRLS iterate (the float |r| sit in scratch)
+  // whose A parts are linearly independent, so that B = A_Z is invertible: rows are taken
+  // in order of |r| (ties by index), and a row whose A part lies within 1e-10 relative of
+  // the span of the rows taken so far (an exact copy, or a second canonical row e_j of the
+  // same j) is passed over.  Warp 0 keeps an orthonormal basis of the taken A parts
+  // (Gram–Schmidt, twice) in LU's space, which is free until the first vertex.
+  __shared__ int s_k, s_rounds;
+  __shared__ int64_t s_cand;
+  if (tid == 0) {
+    s_k = 0;
+    s_rounds = 0;
+  }
+  __syncthreads();
+  const int max_rounds = 9 * d + 64;
+  while (s_ok && s_k < d && s_rounds < max_rounds) {
     float best = INFINITY;
     int64_t bi = -1;
     for (int64_t i = tid; i < S; i += blockDim.x) {
       const float v = a.scratch[i];
       if (v < best) {
-        bool copy = false;
-        for (int m = 0; m < k && !copy; ++m) {
-          if (zr[m] != v) continue;
-          bool same = true;
-          for (int c = 0; c < q && same; ++c) same = a.X[i * q + c] == a.X[Z[m] * q + c];
-          copy = same;
-        }
-        if (copy) continue;
         best = v;
         bi = i;
       }
@@ -413,16 +442,60 @@ __global__ void __launch_bounds__(kIrlsThreads) irls_polish_kernel(const IrlsArg
           b = rv[t];
           idx = ri[t];
         }
-      if (idx < 0) {
-        s_ok = 0;
-      } else {
-        zr[k] = a.scratch[idx];
-        a.scratch[idx] = INFINITY;
-        Z[k] = idx;
+      s_cand = idx;
+      if (idx < 0) s_ok = 0;
+      else a.scratch[idx] = INFINITY;
+    }
+    __syncthreads();
+    if (s_ok && warp == 0) {
+      constexpr int kPer = (kMaxD + 31) / 32;
+      const int k = s_k;
+      const int64_t c = s_cand;
+      double v[kPer], n0 = 0.0;
+#pragma unroll
+      for (int t = 0; t < kPer; ++t) {
+        const int e = lane + 32 * t;
+        v[t] = e < d ? a.X[c * q + e] : 0.0;
+        n0 = fma(v[t], v[t], n0);
       }
+      for (int o = 16; o > 0; o >>= 1) n0 += __shfl_xor_sync(0xffffffffu, n0, o);
+      for (int pass = 0; pass < 2; ++pass)
+        for (int m = 0; m < k; ++m) {
+          double dot = 0.0;
+#pragma unroll
+          for (int t = 0; t < kPer; ++t) {
+            const int e = lane + 32 * t;
+            if (e < d) dot = fma(v[t], LU[m * d + e], dot);
+          }
+          for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
+#pragma unroll
+          for (int t = 0; t < kPer; ++t) {
+            const int e = lane + 32 * t;
+            if (e < d) v[t] = fma(-dot, LU[m * d + e], v[t]);
+          }
+        }
+      double n1 = 0.0;
+#pragma unroll
+      for (int t = 0; t < kPer; ++t) n1 = fma(v[t], v[t], n1);
+      for (int o = 16; o > 0; o >>= 1) n1 += __shfl_xor_sync(0xffffffffu, n1, o);
+      if (n1 > 1e-20 * n0 && n0 > 0.0) {
+        const double inv = 1.0 / sqrt(n1);
+#pragma unroll
+        for (int t = 0; t < kPer; ++t) {
+          const int e = lane + 32 * t;
+          if (e < d) LU[k * d + e] = v[t] * inv;
+        }
+        __syncwarp();
+        if (lane == 0) {
+          Z[k] = c;
+          s_k = k + 1;
+        }
+      }
+      if (lane == 0) s_rounds += 1;
     }
     __syncthreads();
   }
+  if (tid == 0 && s_k < d) s_ok = 0;
   __syncthreads();
 
   for (int piv = 0; piv < kMaxPivots && s_ok; ++piv) {
@@ -543,6 +616,7 @@ __global__ void __launch_bounds__(kIrlsThreads) irls_polish_kernel(const IrlsArg
     for (int j = 0; j < d; ++j) a.x_out[j] = use ? xb[j] : st->best_x[j];
     if (a.obj_out) *a.obj_out = use ? s_fb : st->best_f;
     if (!a.status->irls_done && !(use && s_certified)) raise_flag(&a.status->flags, L1S_ERR_NOT_CONVERGED);
+    if (a.flags_out) *a.flags_out = atomicOr(&a.status->flags, 0u);
   }
 }
 
@@ -556,9 +630,13 @@ size_t solve_scratch_bytes(int64_t capacity) { return 2 * sizeof(double) * stati
 int irls_entries(int q) { return q * (q + 1) / 2 + 1; }
 size_t irls_state_bytes() { return sizeof(IrlsState); }
 
+// k coresets at once: coreset j at X + j·capacity·q, w + j·capacity, count + j; its
+// partials, state, status block and scratch are the j-th of arrays of k; outputs
+// x_out + j·d, obj_out + j, flags_out + j.  nblocks accumulation blocks per coreset.
 bool launch_solve(const double* X, const double* w, const int64_t* count, int64_t capacity, int d,
                   int max_iter, double* x_out, double* obj_out, int nblocks, double* partials,
-                  void* state, float* scratch, StatusBlock* status, cudaStream_t st) {
+                  void* state, float* scratch, StatusBlock* status, cudaStream_t st, int k,
+                  uint32_t* flags_out) {
   IrlsArgs a;
   a.X = X;
   a.w = w;
@@ -574,6 +652,10 @@ bool launch_solve(const double* X, const double* w, const int64_t* count, int64_
   a.obj_out = obj_out;
   a.max_iter = max_iter;
   const int q = d + 1;
+  a.x_stride = capacity * q;
+  a.part_stride = static_cast<int64_t>(nblocks) * (irls_entries(q) + 1);
+  a.scratch_stride = static_cast<int64_t>(solve_scratch_bytes(capacity) / sizeof(float));
+  a.flags_out = flags_out;
   const size_t acc_smem = sizeof(double) * (kIrlsTile * q + kIrlsTile + q);
   const size_t step_smem = sizeof(double) * (irls_entries(q) + d * d + d);
   const size_t pol_smem = polish_smem_bytes(d);
@@ -587,16 +669,17 @@ bool launch_solve(const double* X, const double* w, const int64_t* count, int64_
                                     static_cast<int>(pol_smem)),
                "irls_polish smem"))
     return false;
-  irls_init_kernel<<<1, 256, 0, st>>>(a);
+  const dim3 many(nblocks, k), one(1, k);
+  irls_init_kernel<<<one, 256, 0, st>>>(a);
   for (int it = 0; it < max_iter; ++it) {
-    irls_accum_kernel<<<nblocks, kIrlsThreads, acc_smem, st>>>(a);
-    irls_step_kernel<<<1, kIrlsThreads, step_smem, st>>>(a, nblocks, 0);
+    irls_accum_kernel<<<many, kIrlsThreads, acc_smem, st>>>(a);
+    irls_step_kernel<<<one, kIrlsThreads, step_smem, st>>>(a, nblocks, 0);
   }
   // Objective of the last iterate, then the vertex polish.
-  irls_accum_kernel<<<nblocks, kIrlsThreads, acc_smem, st>>>(a);
-  irls_step_kernel<<<1, kIrlsThreads, step_smem, st>>>(a, nblocks, 1);
-  irls_residuals_kernel<<<nblocks, 256, 0, st>>>(a);
-  irls_polish_kernel<<<1, kIrlsThreads, pol_smem, st>>>(a);
+  irls_accum_kernel<<<many, kIrlsThreads, acc_smem, st>>>(a);
+  irls_step_kernel<<<one, kIrlsThreads, step_smem, st>>>(a, nblocks, 1);
+  irls_residuals_kernel<<<many, 256, 0, st>>>(a);
+  irls_polish_kernel<<<one, kIrlsThreads, pol_smem, st>>>(a);
   count_launch(2 * max_iter + 5);
   return cuda_ok(cudaGetLastError(), "launch l1_solve kernels");
 }

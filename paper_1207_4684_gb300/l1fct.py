@@ -86,6 +86,11 @@ _SIGS = {
     "l1_sample": (C.c_int, [_P, _I64, C.c_int, _P, _I64, _I32, _P, _PP, _I64, _P, _P, _P, _P, _P, _P,
                             _SZ, _P]),
     "l1_sample_from_p": (C.c_int, [_P, _I64, _PP, _I64, _P, _P, _P, _SZ, _P]),
+    "l1_sample_lambda": (C.c_int, [_P, _I64, C.c_int, _P, _I64, _I32, _P, _P, _PP, _I32, _I64, _P, _P, _P, _P, _P,
+                                   _SZ, _P]),
+    "l1s_sample_lambda_workspace_size": (C.c_int, [_PP, _I64, _I32, C.c_int, _I32, C.POINTER(_SZ)]),
+    "l1_solve_many": (C.c_int, [_P, _P, _P, _I64, _I32, _I32, _I32, _P, _P, _P, _P, _SZ, _P]),
+    "l1s_solve_many_workspace_size": (C.c_int, [_I64, _I32, _I32, C.POINTER(_SZ)]),
     "l1_coreset": (C.c_int, [_P, _I64, C.c_int, _P, _I64, _I32, _PP, _I64, _P, _P, _P, _P, _P, _SZ, _P]),
     "l1_coreset_host": (C.c_int, [_P, _I64, C.c_int, _P, _I64, _I32, _PP, _I64, _P, _P, _P, _P, _SZ, _P]),
     "l1_solve": (C.c_int, [_P, _P, _P, _I64, _I32, _I32, _P, _P, _P, _SZ, _P]),
@@ -220,6 +225,36 @@ def l1_sample(A, b, M, params: Params, capacity: int, idx, w, coreset, count, la
 def l1_sample_from_p(p, params: Params, capacity: int, idx, count, ws, stream=None) -> None:
     _check(load().l1_sample_from_p(_ptr(p), p.numel(), C.byref(params), capacity, _ptr(idx), _ptr(count),
                                    _ptr(ws), ws.numel(), _stream(stream)), "l1_sample_from_p")
+
+
+def sample_lambda_workspace_size(params: Params, n: int, d: int, dtype: int, k: int) -> int:
+    v = C.c_size_t(0)
+    _check(load().l1s_sample_lambda_workspace_size(C.byref(params), n, d, dtype, k, C.byref(v)),
+           "l1s_sample_lambda_workspace_size")
+    return v.value
+
+
+def l1_sample_lambda(A, b, lam, lam_total, params: Params, k: int, capacity: int, idx, w, coreset, count, ws,
+                     stream=None) -> None:
+    """k coresets from a given λ and Σλ (device tensors); idx/w are (k, capacity), coreset (k, capacity, q) or
+    None, count (k,)."""
+    n, d, lda, dt = _matrix(A)
+    _check(load().l1_sample_lambda(_ptr(A, False), lda, dt, _ptr(b), n, d, _ptr(lam), _ptr(lam_total),
+                                   C.byref(params), k, capacity, _ptr(idx), _ptr(w), _ptr(coreset), _ptr(count),
+                                   _ptr(ws), ws.numel(), _stream(stream)), "l1_sample_lambda")
+
+
+def solve_many_workspace_size(capacity: int, d: int, k: int) -> int:
+    v = C.c_size_t(0)
+    _check(load().l1s_solve_many_workspace_size(capacity, d, k, C.byref(v)), "l1s_solve_many_workspace_size")
+    return v.value
+
+
+def l1_solve_many(coreset, w, count, capacity: int, d: int, k: int, max_iter: int, x, objective, flags, ws,
+                  stream=None) -> None:
+    _check(load().l1_solve_many(_ptr(coreset), _ptr(w), _ptr(count), capacity, d, k, max_iter, _ptr(x),
+                                _ptr(objective), _ptr(flags), _ptr(ws), ws.numel(), _stream(stream)),
+           "l1_solve_many")
 
 
 def l1_coreset(A, b, params: Params, capacity: int, idx, w, coreset, count, ws, stream=None) -> None:

@@ -56,3 +56,74 @@ def kappa_bar(A: torch.Tensor, r1: int, s: int, seed: int = 0, problem_id: int =
     a = float(alpha.item())
     m = min(values)
     return {"kappa_bar": a / m, "alpha": a, "min_box": m, "status": flags, "R": R}
+
+
+# ----------------------------------------------------------------- §6.3: many coresets, one pass
+def many_solutions(A: torch.Tensor, b: torch.Tensor, prm: L.Params, k: int, capacity: int | None = None,
+                   max_iter: int = 100, stream=None) -> dict:
+    """The k approximate solutions of one sampling pass (§6.3): Π1·X by fct_embed, R and M
+    by l1_condition, λ and Σλ by l1_lambda (one read of A each), then k coresets from that
+    λ (l1_sample_lambda, coreset j drawn with problem id prm.problem_id + j) and their k
+    weighted ℓ1 solves side by side (l1_solve_many).  Returns the device results and the
+    CUDA-event time of each phase."""
+    n, d = A.shape
+    dev = A.device
+    q = d + 1
+    dt = L.BF16 if A.dtype == torch.bfloat16 else L.F32
+    cap = int(capacity if capacity is not None else 2 * prm.coreset_size + 64)
+    ws = torch.empty(L.sample_lambda_workspace_size(prm, n, d, dt, k), dtype=torch.uint8, device=dev)
+    pix = torch.empty((prm.r1, q), dtype=torch.float32, device=dev)
+    M = torch.empty((q, prm.r2), dtype=torch.float64, device=dev)
+    lam = torch.empty(n, dtype=torch.float32, device=dev)
+    tot = torch.empty(1, dtype=torch.float64, device=dev)
+    idx = torch.empty((k, cap), dtype=torch.int64, device=dev)
+    w = torch.empty((k, cap), dtype=torch.float64, device=dev)
+    core = torch.empty((k, cap, q), dtype=torch.float64, device=dev)
+    cnt = torch.empty(k, dtype=torch.int64, device=dev)
+    sws = torch.empty(L.solve_many_workspace_size(cap, d, k), dtype=torch.uint8, device=dev)
+    x = torch.empty((k, d), dtype=torch.float64, device=dev)
+    obj = torch.empty(k, dtype=torch.float64, device=dev)
+    flags = torch.zeros(k, dtype=torch.int32, device=dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+    st = stream if stream is not None else torch.cuda.current_stream(dev)
+    with torch.cuda.stream(st):
+        L.l1s_status_reset(ws, stream=st)
+        ev[0].record(st)
+        L.fct_embed(A, b, prm, pix, ws, stream=st)
+        ev[1].record(st)
+        L.l1_condition(pix, prm, None, M, ws, stream=st)
+        ev[2].record(st)
+        L.l1_lambda(A, b, M, prm, lam, tot, ws, stream=st)
+        ev[3].record(st)
+        L.l1_sample_lambda(A, b, lam, tot, prm, k, cap, idx, w, core, cnt, ws, stream=st)
+        ev[4].record(st)
+        L.l1_solve_many(core, w, cnt, cap, d, k, max_iter, x, obj, flags, sws, stream=st)
+        ev[5].record(st)
+    st.synchronize()
+    names = ("embed", "condition", "lambda", "sample", "solve")
+    return {"x": x, "objective": obj, "count": cnt, "solve_flags": flags, "status": L.l1s_status_read(ws, st),
+            "lambda_total": tot, "idx": idx, "w": w, "coreset": core, "capacity": cap,
+            "phase_ms": {nm: ev[i].elapsed_time(ev[i + 1]) for i, nm in enumerate(names)}}
+
+
+def canonical_box(cols: torch.Tensor, b: torch.Tensor, d: int):
+    """Lower and upper per-coordinate medians of b (FP64): the box of minimisers of ‖A·x − b‖₁
+    when row i of A is e_{cols_i} (the separable design of §6.3)."""
+    lo = torch.empty(d, dtype=torch.float64)
+    hi = torch.empty(d, dtype=torch.float64)
+    for j in range(d):
+        v = torch.sort(b[cols == j].to(torch.float64)).values
+        m = v.numel()
+        lo[j] = v[(m + 1) // 2 - 1].item()
+        hi[j] = v[m // 2].item()
+    return lo, hi
+
+
+def box_errors(x: torch.Tensor, lo: torch.Tensor, hi: torch.Tensor) -> dict:
+    """Relative 1-, 2- and ∞-norm distance of each row of x (k × d) from the optimal box,
+    relative to the same norm of lo (the columns of the §6.3 error table)."""
+    x = x.detach().cpu().to(torch.float64)
+    e = torch.clamp(torch.maximum(lo - x, x - hi), min=0.0)
+    return {"l1": (e.sum(1) / lo.abs().sum()).tolist(),
+            "l2": (e.norm(dim=1) / lo.norm()).tolist(),
+            "linf": (e.abs().amax(1) / lo.abs().max()).tolist()}

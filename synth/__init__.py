@@ -12,5 +12,6 @@ from .inputs import (  # noqa: F401
     make_problem,
     make_batched_problems,
     kappa_test_matrix,
+    canonical_design,
     r1_for,
 )

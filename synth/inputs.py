@@ -260,3 +260,30 @@ def kappa_test_matrix(kind: str, n: int, d: int, seed: int = 0) -> np.ndarray:
     else:
         raise ValueError(f"unknown test matrix {kind}")
     return a.astype(np.float32)
+
+
+def canonical_design(n: int, d: int = 15, seed: int = 0, corrupt: float = 1e-3,
+                     corrupt_scale: float = 1000.0) -> dict:
+    """The imbalanced, corrupted canonical-row design of the large-scale experiment (§6.3):
+
+    x* ∈ R^d standard Gaussian; every row of A is a canonical vector e_j, coordinate j
+    (from 0) receiving twice as many rows as coordinate j + 1 (counts ⌊n·2^{d−1−j}/(2^d − 1)⌋,
+    the rounding remainder going to coordinate 0), in a seeded random row order;
+    b_i = corrupt_scale·ε_i with probability `corrupt`, else x*_{c_i} + ε_i, ε i.i.d.
+    standard Laplace.  The paper's instance has n ≈ 5.24e9 and d = 15.
+
+    Returns {"cols": (n,) int8 coordinate of each row, "b": (n,) float32, "x_star": (d,)
+    float64, "counts": (d,) int64}; A itself (n × d, one 1 per row) is formed by the caller.
+    """
+    if not 1 <= d <= 127:
+        raise ValueError("d must be in [1, 127]")
+    rng = np.random.Generator(np.random.PCG64(seed))
+    x_star = rng.standard_normal(d)
+    counts = np.array([(n << (d - 1 - j)) // ((1 << d) - 1) for j in range(d)], dtype=np.int64)
+    counts[0] += n - int(counts.sum())
+    cols = np.repeat(np.arange(d, dtype=np.int8), counts)
+    cols = rng.permutation(cols)
+    eps = rng.laplace(0.0, 1.0, size=n)
+    bad = rng.random(n) < corrupt
+    b = np.where(bad, corrupt_scale * eps, x_star[cols] + eps).astype(np.float32)
+    return {"cols": cols, "b": b, "x_star": x_star, "counts": counts}

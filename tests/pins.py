@@ -14,7 +14,7 @@ import math
 import numpy as np
 from scipy import stats
 
-from oracle import condition, fct, leverage, pipeline, quality, rng, sampling, sct, solve
+from oracle import condition, fct, leverage, pipeline, quality, rng, sampling, sct, separable, solve
 
 
 # ----------------------------------------------------------------- Hadamard
@@ -410,7 +410,8 @@ def check_scaled_probabilities(seed: int = 31) -> None:
 def _all_checks():
     return ALL_CHECKS + [check_bf16_round, check_gaussian_pi2, check_gaussian_lambda_distribution,
                          check_scaled_probabilities, check_multiple_regression, check_with_replacement,
-                         check_sct_draws, check_sct_stability, check_sct_embedding_bound, check_kappa_bar]
+                         check_sct_draws, check_sct_stability, check_sct_embedding_bound, check_kappa_bar,
+                         check_canonical_optimum]
 
 
 # ----------------------------------------------------------------- slow Cauchy transform
@@ -549,3 +550,37 @@ def check_kappa_bar(seed: int = 13) -> None:
     brute = min(cands)
     got = quality.min_l1_on_unit_box(U)
     assert abs(got - brute) <= 1e-9 * brute, (got, brute)
+
+# ----------------------------------------------------------------- separable design (§6.3)
+def check_canonical_optimum(seed: int = 21) -> None:
+    """For canonical-vector rows the LP optimum of ‖A·x − b‖₁ (HiGHS) has the objective of
+    both corners of the oracle's box [lo, hi] and of a point inside it; moving one coordinate
+    just outside the box raises the objective; groups of odd size give lo = hi; the distance
+    to the box vanishes inside it and the relative errors follow their definitions."""
+    g = np.random.default_rng(seed)
+    d = 5
+    sizes = [7, 10, 3, 8, 1]                  # odd and even groups, one singleton
+    cols = g.permutation(np.repeat(np.arange(d), sizes))
+    b = g.laplace(size=cols.size) + cols.astype(np.float64)
+    A = np.eye(d)[cols]
+    _, f_lp = solve.lad_lp(A, b)
+    lo, hi = separable.canonical_optimum(cols, b, d)
+    for j, m in enumerate(sizes):
+        assert (lo[j] == hi[j]) == (m % 2 == 1), f"group {j} of size {m}"
+        assert lo[j] <= hi[j]
+    mid = 0.5 * (lo + hi)
+    for x in (lo, hi, mid):
+        assert math.isclose(solve.objective(A, b, x), f_lp, rel_tol=1e-12), "box point not optimal"
+    for j in range(d):
+        for x0, step in ((lo, -1e-3), (hi, 1e-3)):
+            x = x0.copy()
+            x[j] += step
+            assert solve.objective(A, b, x) > f_lp * (1 + 1e-9), f"coordinate {j} leaves the box"
+    assert np.all(separable.box_distance(mid, lo, hi) == 0.0)
+    x = hi.copy()
+    x[2] += 0.5
+    x[0] = lo[0] - 0.25
+    e = separable.relative_errors(x, lo, hi, lo)
+    assert math.isclose(e["l1"], 0.75 / np.abs(lo).sum(), rel_tol=1e-12)
+    assert math.isclose(e["l2"], math.sqrt(0.5 ** 2 + 0.25 ** 2) / np.linalg.norm(lo), rel_tol=1e-12)
+    assert math.isclose(e["linf"], 0.5 / np.abs(lo).max(), rel_tol=1e-12)

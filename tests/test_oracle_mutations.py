@@ -8,7 +8,7 @@ import numpy as np
 import pytest
 
 import pins
-from oracle import condition, fct, leverage, pipeline, rng, sampling, sct, solve
+from oracle import condition, fct, leverage, pipeline, rng, sampling, sct, separable, solve
 
 ORIG_EMBED = fct.fct1_embed
 ORIG_HAD = fct.sylvester_hadamard
@@ -26,6 +26,21 @@ ORIG_GAUSS = rng.pi2_gaussian_matrix
 ORIG_SCALED = sampling.probabilities_scaled
 ORIG_SCT = sct.sct_embed
 ORIG_SCT_MATRIX = rng.sct_matrix
+
+
+def canonical_mean(cols, b, d):
+    cols = np.asarray(cols)
+    m = np.array([np.mean(b[cols == j]) for j in range(d)])
+    return m, m
+
+
+def canonical_hi_low(cols, b, d):
+    cols = np.asarray(cols)
+    lo = np.empty(d)
+    for j in range(d):
+        v = np.sort(b[cols == j])
+        lo[j] = v[(v.size + 1) // 2 - 1]
+    return lo, lo
 
 
 def _draws_of(X, s, r1, seed, problem_id, row_offset, draws):
@@ -210,6 +225,10 @@ MUTATIONS = [
      pins.check_with_replacement),
     ("with-replacement target u, not u·Σλ", sampling, "sample_with_replacement", replace_unscaled_target,
      pins.check_with_replacement),
+    ("separable optimum: mean for median", separable, "canonical_optimum", canonical_mean,
+     pins.check_canonical_optimum),
+    ("separable optimum: upper median = lower", separable, "canonical_optimum", canonical_hi_low,
+     pins.check_canonical_optimum),
 ]
 
 
