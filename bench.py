@@ -53,11 +53,12 @@ def parse():
                     help="time eager calls instead of replays of the step captured as a CUDA graph")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the other forms (measured after the main line's timed region)")
-    ap.add_argument("--variants", default="bf16,colscale,optimized,replacement,multi,sct,t2rows_bf16,batched",
+    ap.add_argument("--variants", default="bf16,colscale,optimized,replacement,multi,sct,t2rows_bf16,batched,canonical",
                     help="comma-separated forms to measure after the main line: bf16 (the main data streamed as "
                          "BF16), colscale (n = 2^22, d = 16, FP32), optimized, replacement, multi, sct (the slow "
                          "Cauchy transform; these on the n = 2^22 data), t2rows_bf16 (n = 2^24, d = 32, BF16), "
-                         "batched")
+                         "batched, canonical (the canonical-row design of §6.3 at n = 2^26, d = 15: 100 "
+                         "coresets and solves from one pass)")
     return ap.parse_args()
 
 
@@ -351,6 +352,58 @@ def sct_variant(L, dev, stream, args, A, b, w, plain_ms: float, fct1_ms: float) 
             "variates_per_s": variates / (phase["fct_embed"] / 1e3),
             "fma_per_s": variates * q / (phase["fct_embed"] / 1e3),
             "phase1_vs_fct1": phase["fct_embed"] / fct1_ms, "speedup_vs_f32_plain": plain_ms / ms}
+
+
+# Quartiles of the Cauchy-conditioned sampling (CT) row of the relative-error table of §6.3,
+# the paper's result on its 5.24e9 × 15 instance: context for this scaled instance, not a target.
+PAPER_CT_QUARTILES = {"l1": [0.008, 0.0115], "l2": [0.00895, 0.0146], "linf": [0.0113, 0.0211]}
+
+
+def canonical_variant(L, dev, stream, args) -> dict:
+    """The large-scale experiment of §6.3 scaled to one GPU: the imbalanced, corrupted
+    canonical-row design at n = 2^26, d = 15, the slow Cauchy transform as Π1 (the paper's CT)
+    and, for comparison, FCT1; 100 coresets of about 10^5 rows from one λ and their 100 solves
+    side by side.  Reports each phase's device time, rows/s of the whole 100-solution pass, and
+    the quartiles over the 100 solutions of the 1-, 2- and ∞-norm distance from the optimal box
+    (per-coordinate medians), relative to the optimum, with entry-wise quartiles."""
+    import numpy as np
+    import torch
+
+    from paper_1207_4684_gb300 import validation
+    from synth import canonical_design, r1_for
+
+    n, d, k, m = 1 << 26, 15, 100, 1e5
+    cd = canonical_design(n, d, seed=0)
+    cols = torch.from_numpy(cd["cols"]).to(dev).long()
+    A = torch.zeros((n, d), dtype=torch.float32, device=dev)
+    A.scatter_(1, cols[:, None], 1.0)
+    b = torch.from_numpy(cd["b"]).to(dev)
+    lo, hi = validation.canonical_box(cols, b, d)
+    del cd
+    out = {"workload": "canonical_n64M_d15", "n": n, "d": d, "k": k, "coreset": m, "r1": r1_for(d), "r2": 16,
+           "paper_ct_quartiles": PAPER_CT_QUARTILES}
+    for name, prm in (("ct", L.make_params(1, r1_for(d), 16, m, seed=0, transform=1)),
+                      ("fct1", L.make_params(128, r1_for(d), 16, m, seed=0))):
+        validation.many_solutions(A, b, prm, k, stream=stream)          # warm-up
+        torch.cuda.synchronize()
+        res = validation.many_solutions(A, b, prm, k, stream=stream)
+        err = validation.box_errors(res["x"], lo, hi)
+        xs = res["x"].cpu().numpy()
+        ent = np.maximum(0.0, np.maximum(lo.numpy()[None, :] - xs, xs - hi.numpy()[None, :]))
+        total = sum(res["phase_ms"].values())
+        out[name] = {
+            "phase_ms": res["phase_ms"], "ms_per_pass": total, "rows_per_s": n / (total / 1e3),
+            "status": res["status"], "solves_flagged": int((res["solve_flags"] != 0).sum().item()),
+            "coreset_rows_median": float(res["count"].double().median().item()),
+            "quartiles": {key: [float(np.percentile(v, 25)), float(np.percentile(v, 75))] for key, v in err.items()},
+            "entrywise_abs_quartiles": [[float(np.percentile(ent[:, j], 25)), float(np.percentile(ent[:, j], 75))]
+                                        for j in range(d)],
+        }
+        del res
+        torch.cuda.empty_cache()
+    del A, b, cols
+    torch.cuda.empty_cache()
+    return out
 
 
 def bf16_variant(L, dev, stream, args, peak: float) -> dict:
@@ -835,6 +888,9 @@ def run_gpu(args) -> None:
             torch.cuda.empty_cache()
         if "batched" in want:
             variants["batched"] = batched_variant(L, dev, stream, args, peaks["hbm_gbs"])
+            torch.cuda.empty_cache()
+        if "canonical" in want:
+            variants["canonical"] = canonical_variant(L, dev, stream, args)
         variants["main_f32"] = {"workload": w.name, "value": value, "ms_per_step": ms_per_step,
                                 "step_frac": step_gbs / peaks["hbm_gbs"]}
         line["variants"] = variants

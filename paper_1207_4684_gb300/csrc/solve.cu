@@ -408,20 +408,23 @@ __global__ void __launch_bounds__(kIrlsThreads) irls_polish_kernel(const IrlsArg
   }
   __syncthreads();
   // The d rows with the smallest |r| at the IRLS iterate (the float |r| sit in scratch)
-  // whose A parts are linearly independent, so that B = A_Z is invertible: rows are taken
-  // in order of |r| (ties by index), and a row whose A part lies within 1e-10 relative of
-  // the span of the rows taken so far (an exact copy, or a second canonical row e_j of the
-  // same j) is passed over.  Warp 0 keeps an orthonormal basis of the taken A parts
-  // (Gram–Schmidt, twice) in LU's space, which is free until the first vertex.
+  // whose A parts are linearly independent, so that B = A_Z is invertible: a row whose A
+  // part lies within 1e-10 relative of the span of the rows taken so far (an exact copy,
+  // or another canonical row e_j of a j already taken) is passed over.  Where many rows
+  // are passed over (hundreds in a canonical-row design), taking one row per pass over the
+  // coreset would be slow, so each round takes every thread's smallest remaining |r|,
+  // orders these candidates by (|r|, index), and warp 0 tests them in that order, keeping
+  // an orthonormal basis of the taken A parts (Gram–Schmidt, twice) in LU's space, which
+  // is free until the first vertex.  Every tested candidate leaves the pool.
   __shared__ int s_k, s_rounds;
-  __shared__ int64_t s_cand;
+  __shared__ int64_t cand[kIrlsThreads];
   if (tid == 0) {
     s_k = 0;
     s_rounds = 0;
   }
   __syncthreads();
-  const int max_rounds = 9 * d + 64;
-  while (s_ok && s_k < d && s_rounds < max_rounds) {
+  constexpr int kMaxStartRounds = 64;
+  while (s_ok && s_k < d && s_rounds < kMaxStartRounds) {
     float best = INFINITY;
     int64_t bi = -1;
     for (int64_t i = tid; i < S; i += blockDim.x) {
@@ -433,68 +436,70 @@ __global__ void __launch_bounds__(kIrlsThreads) irls_polish_kernel(const IrlsArg
     }
     rv[tid] = best;
     ri[tid] = bi;
-    __syncthreads();
-    if (tid == 0) {
-      float b = INFINITY;
-      int64_t idx = -1;
+    const int nvalid = __syncthreads_count(bi >= 0 && best < INFINITY);
+    if (nvalid == 0) {
+      if (tid == 0) s_ok = 0;
+      break;
+    }
+    if (bi >= 0 && best < INFINITY) {
+      int rank = 0;
       for (int t = 0; t < static_cast<int>(blockDim.x); ++t)
-        if (ri[t] >= 0 && (rv[t] < b || (rv[t] == b && ri[t] < idx))) {
-          b = rv[t];
-          idx = ri[t];
-        }
-      s_cand = idx;
-      if (idx < 0) s_ok = 0;
-      else a.scratch[idx] = INFINITY;
+        rank += (ri[t] >= 0 && rv[t] < INFINITY && (rv[t] < best || (rv[t] == best && ri[t] < bi))) ? 1 : 0;
+      cand[rank] = bi;
     }
     __syncthreads();
-    if (s_ok && warp == 0) {
+    if (warp == 0) {
       constexpr int kPer = (kMaxD + 31) / 32;
-      const int k = s_k;
-      const int64_t c = s_cand;
-      double v[kPer], n0 = 0.0;
+      int k = s_k;
+      for (int t = 0; t < nvalid && k < d; ++t) {
+        const int64_t c = cand[t];
+        double v[kPer], n0 = 0.0;
 #pragma unroll
-      for (int t = 0; t < kPer; ++t) {
-        const int e = lane + 32 * t;
-        v[t] = e < d ? a.X[c * q + e] : 0.0;
-        n0 = fma(v[t], v[t], n0);
-      }
-      for (int o = 16; o > 0; o >>= 1) n0 += __shfl_xor_sync(0xffffffffu, n0, o);
-      for (int pass = 0; pass < 2; ++pass)
-        for (int m = 0; m < k; ++m) {
-          double dot = 0.0;
+        for (int u = 0; u < kPer; ++u) {
+          const int e = lane + 32 * u;
+          v[u] = e < d ? a.X[c * q + e] : 0.0;
+          n0 = fma(v[u], v[u], n0);
+        }
+        for (int o = 16; o > 0; o >>= 1) n0 += __shfl_xor_sync(0xffffffffu, n0, o);
+        for (int pass = 0; pass < 2; ++pass)
+          for (int m = 0; m < k; ++m) {
+            double dot = 0.0;
 #pragma unroll
-          for (int t = 0; t < kPer; ++t) {
-            const int e = lane + 32 * t;
-            if (e < d) dot = fma(v[t], LU[m * d + e], dot);
+            for (int u = 0; u < kPer; ++u) {
+              const int e = lane + 32 * u;
+              if (e < d) dot = fma(v[u], LU[m * d + e], dot);
+            }
+            for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
+#pragma unroll
+            for (int u = 0; u < kPer; ++u) {
+              const int e = lane + 32 * u;
+              if (e < d) v[u] = fma(-dot, LU[m * d + e], v[u]);
+            }
           }
-          for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
+        double n1 = 0.0;
 #pragma unroll
-          for (int t = 0; t < kPer; ++t) {
-            const int e = lane + 32 * t;
-            if (e < d) v[t] = fma(-dot, LU[m * d + e], v[t]);
+        for (int u = 0; u < kPer; ++u) n1 = fma(v[u], v[u], n1);
+        for (int o = 16; o > 0; o >>= 1) n1 += __shfl_xor_sync(0xffffffffu, n1, o);
+        if (n1 > 1e-20 * n0 && n0 > 0.0) {            // the same decision in every lane
+          const double inv = 1.0 / sqrt(n1);
+#pragma unroll
+          for (int u = 0; u < kPer; ++u) {
+            const int e = lane + 32 * u;
+            if (e < d) LU[k * d + e] = v[u] * inv;   // each lane reads back only its own entries
           }
+          if (lane == 0) Z[k] = c;
+          ++k;
         }
-      double n1 = 0.0;
-#pragma unroll
-      for (int t = 0; t < kPer; ++t) n1 = fma(v[t], v[t], n1);
-      for (int o = 16; o > 0; o >>= 1) n1 += __shfl_xor_sync(0xffffffffu, n1, o);
-      if (n1 > 1e-20 * n0 && n0 > 0.0) {
-        const double inv = 1.0 / sqrt(n1);
-#pragma unroll
-        for (int t = 0; t < kPer; ++t) {
-          const int e = lane + 32 * t;
-          if (e < d) LU[k * d + e] = v[t] * inv;
-        }
-        __syncwarp();
-        if (lane == 0) {
-          Z[k] = c;
-          s_k = k + 1;
-        }
+        if (lane == 0) a.scratch[c] = INFINITY;
       }
-      if (lane == 0) s_rounds += 1;
+      if (lane == 0) {
+        s_k = k;
+        s_rounds += 1;
+      }
     }
     __syncthreads();
   }
+  __syncthreads();
   if (tid == 0 && s_k < d) s_ok = 0;
   __syncthreads();
 

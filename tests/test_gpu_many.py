@@ -222,3 +222,32 @@ def test_canonical_design_many_solutions():
     for j in range(k):
         got = np.bincount(cd["cols"][idx[j, : cnt[j]]].astype(np.int64), minlength=d)
         assert got.min() > 0, got
+
+
+def test_canonical_coresets_solved_to_their_weighted_medians():
+    """At n = 2^22 and 10^5-row coresets, the solves' vertex start passes over hundreds of rows
+    of the large groups (their A parts repeat) before every coordinate has a row; each solve
+    must still end certified, at the coreset's own optimum: per coordinate a weighted median
+    of the group's responses (oracle weighted_median), objective within 1e-12."""
+    from paper_1207_4684_gb300 import validation
+
+    n, d, k, m = 1 << 22, 15, 4, 1e5
+    cd = canonical_design(n, d, seed=9)
+    cols = torch.from_numpy(cd["cols"].astype(np.int64)).to(DEV)
+    A = torch.zeros((n, d), dtype=torch.float32, device=DEV)
+    A.scatter_(1, cols[:, None], 1.0)
+    b = torch.from_numpy(cd["b"]).to(DEV)
+    prm = L.make_params(1, r1_for(d), 16, m, seed=3, transform=1)
+    out = validation.many_solutions(A, b, prm, k)
+    assert out["status"] == 0
+    assert torch.all(out["solve_flags"] == 0), out["solve_flags"]
+    for j in range(k):
+        c = int(out["count"][j].item())
+        X = out["coreset"][j, :c].cpu().numpy()
+        w = out["w"][j, :c].cpu().numpy()
+        Aj, bj = X[:, :d], -X[:, d]
+        g = Aj.argmax(1)
+        xm = np.array([solve.weighted_median(bj[g == t], w[g == t]) for t in range(d)])
+        f_opt = solve.weighted_objective(Aj, bj, w, xm)
+        f = float(out["objective"][j].item())
+        assert abs(f - f_opt) <= 1e-12 * f_opt, (j, f, f_opt)
