@@ -450,6 +450,9 @@ bool make_plan(const l1s_params* p, int64_t n, int d, l1s_dtype dt, bool host_st
   P.off_idx_tmp = take(static_cast<size_t>(cap) * (sizeof(int64_t) + sizeof(double) + sizeof(double) * P.q) +
                        2 * sizeof(double) * (P.q + 1));
   if (p->variant == 2) P.off_cdf = take(sizeof(double) * static_cast<size_t>(n));   // running sum of λ
+  // The column-sliced phase-1 kernel reads every row's draws from a per-launch table
+  // (16 bytes a row, whole 1024-row tiles).
+  if (geo[7].ok) P.off_draws = take(16 * static_cast<size_t>((n + fct_cols_tile() - 1) / fct_cols_tile()) * fct_cols_tile());
   if (host_staging) {
     P.off_stage_a = take(esz * static_cast<size_t>(n) * d);
     P.off_stage_b = take(sizeof(float) * static_cast<size_t>(n));

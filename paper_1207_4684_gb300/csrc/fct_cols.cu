@@ -75,6 +75,10 @@ struct ColsArgs {
   float* partials_b;    // b-column kernel: [its blocks][r1]
   int accumulate;       // 1: add to the partials of an earlier launch over other rows
   uint32_t* flags;      // status word (TIMEOUT)
+  // Per-row draws of this launch's tiles (fct_draws_kernel), read by the TMA form and the
+  // b-column kernel: {4·c_I, byte offset of h_I's partial row | σ·2^31, 4·c_H/√s, byte
+  // offset of h_H's partial row}, row r of the launch at index r.
+  uint4* draws;
 };
 
 __device__ __forceinline__ int col_tile_off(int row, int c) { return row * kColW + c + ((row >> 5) << 4); }
@@ -244,7 +248,90 @@ __global__ void __launch_bounds__(kColThreads, 1) fct_embed_cols_kernel(const Co
 //   pass 2: rows (w & 1) + 2i + 32h + 64(w >> 1) (i < 16): bits 1-4 in registers and
 //           bit 5 by a shuffle.
 // BF16 tiles land in the upper half of the buffer and are widened to FP32 in pass 1.
+// Pass 1 stores row r of its output at row r ^ (bit 5 of r): a warp instruction touches
+// two rows, which differ in bit 0 in pass 1 and in bit 5 in pass 2, and this placement
+// puts them in opposite halves of the 32 banks in both passes.  The identity half's draws
+// are 8 bytes a row ({4·c_I, offset of its partial row with σ in bit 31}), which a warp
+// reads in half the shared-memory wavefronts of a 16-byte record.
 constexpr int kTmaThreads = 1024;
+
+// Every row's draws, once per launch: the Philox call of the row's global id (stream 0),
+// its two Cauchy scales and buckets and σ, in the 16-byte record the phase-1 kernels read.
+// Each of the column slices and the b column would otherwise redraw every row.
+__global__ void __launch_bounds__(256) fct_draws_kernel(const ColsArgs a) {
+  const int64_t rows = a.ntiles * kColT;
+  for (int64_t r = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; r < rows;
+       r += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const uint4 o = draw_row(a.key, static_cast<uint64_t>(a.row_offset + r), a.problem, kStreamFct);
+    const bool neg = a.sign_flip && (o.w & 1u);
+    a.draws[r] = make_uint4(__float_as_uint(4.f * cauchy_f32(o.w >> 8)),
+                            (static_cast<uint32_t>(bucket_of(o.z, a.r1)) * (kColW * 4)) | (neg ? 0x80000000u : 0u),
+                            __float_as_uint(4.f * cauchy_f32(o.y >> 8) * a.inv_sqrt_s),
+                            static_cast<uint32_t>(bucket_of(o.x, a.r1)) * (kColW * 4));
+  }
+}
+
+// Two FP32 values in one 64-bit register, for the packed add/sub/fma of sm_100-class
+// parts: each lane is rounded as the scalar instruction rounds it, so a butterfly on a
+// pair gives exactly the two scalar results.
+__device__ __forceinline__ uint64_t f2_pack(float lo, float hi) {
+  uint64_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ void f2_unpack(uint64_t p, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(p));
+}
+__device__ __forceinline__ uint64_t f2_add(uint64_t a, uint64_t b) {
+  uint64_t r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ uint64_t f2_sub(uint64_t a, uint64_t b) {
+  uint64_t r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ uint64_t f2_fma(uint64_t a, uint64_t b, uint64_t c) {
+  uint64_t r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+  return r;
+}
+
+// Butterflies of a 16-value register column v[0..15] held as the pairs p[k] = (v[k], v[k+8]):
+// stages over bits 0-2 of the index run on pairs, the stage over bit 3 inside each pair.
+template <bool FULL>
+__device__ __forceinline__ void f2_butterflies(uint64_t (&p)[8], int first_bit, int lg) {
+#pragma unroll
+  for (int b = 0; b < 3; ++b)
+    if (FULL || first_bit + b < lg)
+#pragma unroll
+      for (int k = 0; k < 8; ++k)
+        if ((k & (1 << b)) == 0) {
+          const uint64_t lo = p[k], hi = p[k | (1 << b)];
+          p[k] = f2_add(lo, hi);
+          p[k | (1 << b)] = f2_sub(lo, hi);
+        }
+  if (FULL || first_bit + 3 < lg)
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      float x, y;
+      f2_unpack(p[k], x, y);
+      p[k] = f2_pack(x + y, x - y);
+    }
+}
+
+// The butterfly across the two half-warps (lane bit 4) on pairs: the lower half keeps
+// v + o, the upper o − v, as one packed fma with ±1.
+__device__ __forceinline__ void f2_cross_halves(uint64_t (&p)[8], uint64_t sgn) {
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    float x, y;
+    f2_unpack(p[k], x, y);
+    const float ox = __shfl_xor_sync(0xffffffffu, x, 16), oy = __shfl_xor_sync(0xffffffffu, y, 16);
+    p[k] = f2_fma(sgn, p[k], f2_pack(ox, oy));
+  }
+}
 constexpr int kTmaJ = 16;
 constexpr int kTmaBoxRows = 256;
 
@@ -267,26 +354,24 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
   unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
   float* tile = reinterpret_cast<float*>(base);                   // [1024][16] FP32
   float* P = tile + kColT * kColW;                                // [r1][16]
-  uint4* mI = reinterpret_cast<uint4*>(P + r1 * kColW);           // [1024]
+  uint2* mI = reinterpret_cast<uint2*>(P + r1 * kColW);           // [1024] {4·c_I, offset | σ·2^31}
   uint2* mH = reinterpret_cast<uint2*>(mI + kColT);               // padded [1024]
   unsigned char* stage = reinterpret_cast<unsigned char*>(tile) + (sizeof(TA) == 4 ? 0 : kColT * kColW * 2);
   constexpr uint32_t kTileBytes = kColT * kColW * sizeof(TA);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, h = lane >> 4, c = lane & 15;
+  const int sw = (warp >> 4) & 1;                                  // bit 5 of this thread's pass-1 rows
+  const uint64_t sgn = h ? f2_pack(-1.f, -1.f) : f2_pack(1.f, 1.f);  // cross-half butterfly sign
   const int slice = blockIdx.y;
   const bool live = c < min(kColW, a.d - slice * kColW);
   const uint32_t pc = smem_u32(P + c);
   const int lg = FULL ? 10 : a.log2s;
   const int64_t G = gridDim.x;
 
-  auto draw = [&](int64_t t, int r, uint4& mi, uint2& mh) {
-    const uint64_t grow = static_cast<uint64_t>(a.row_offset + t * kColT + r);
-    const uint4 o = draw_row(a.key, grow, a.problem, kStreamFct);
-    const bool neg = a.sign_flip && (o.w & 1u);
-    const float wI = 4.f * cauchy_f32(o.w >> 8);
-    mi = make_uint4(__float_as_uint(neg ? -wI : wI), static_cast<uint32_t>(bucket_of(o.z, r1)) * (kColW * 4),
-                    neg ? 0x80000000u : 0u, 0u);
-    mh = make_uint2(__float_as_uint(4.f * cauchy_f32(o.y >> 8) * a.inv_sqrt_s),
-                    static_cast<uint32_t>(bucket_of(o.x, r1)) * (kColW * 4));
+  // Row r of tile t's draws from the per-launch table (loaded one tile ahead, like the tile).
+  auto draw = [&](int64_t t, int r, uint2& mi, uint2& mh) {
+    const uint4 e = __ldg(a.draws + (t * kColT + r));
+    mi = make_uint2(e.x, e.y);
+    mh = make_uint2(e.z, e.w);
   };
   auto issue = [&](int64_t t) {
     mbar_arrive_expect_tx(&full_bar, kTileBytes);
@@ -304,7 +389,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
   const int64_t t0 = blockIdx.x;
   uint2 mh_next = make_uint2(0u, 0u);
   if (t0 < a.ntiles) {
-    uint4 mi;
+    uint2 mi;
     draw(t0, tid, mi, mh_next);
     mI[tid] = mi;
   }
@@ -321,7 +406,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
     }
     mH[tma_hpad(tid)] = mh_next;                         // pass 2 of the previous tile is done with mH
     const int64_t tn = t + G;
-    uint4 mi_next = make_uint4(0u, 0u, 0u, 0u);
+    uint2 mi_next = make_uint2(0u, 0u);
     float v[kTmaJ];
     // ---- pass 1: identity scatter, σ, butterflies over row bits 0 and 6-9, in place
     {
@@ -332,30 +417,24 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
         uint32_t xb;
         if constexpr (sizeof(TA) == 4) xb = __float_as_uint(tile[row * kColW + c]);
         else xb = static_cast<uint32_t>(reinterpret_cast<const uint16_t*>(stage)[row * kColW + c]) << 16;
-        const uint4 m = mI[row];
-        if (live) red_add_shared(pc + m.y, __uint_as_float(m.x) * __uint_as_float(xb));
-        v[j] = __uint_as_float(xb ^ m.z);                // z = σ·x
+        const uint2 m = mI[row];
+        const uint32_t sg = m.y & 0x80000000u;
+        v[j] = __uint_as_float(xb ^ sg);                 // z = σ·x
+        if (live) red_add_shared(pc + (m.y ^ sg), __uint_as_float(m.x) * v[j]);
       }
       if constexpr (sizeof(TA) == 2) __syncthreads();    // every BF16 value read before FP32 rows are written
-      if (FULL || lg > 0) {
+      uint64_t p[kTmaJ / 2];
 #pragma unroll
-        for (int j = 0; j < kTmaJ; ++j) {
-          const float o = __shfl_xor_sync(0xffffffffu, v[j], 16);
-          v[j] = h ? (o - v[j]) : (v[j] + o);
-        }
+      for (int q = 0; q < kTmaJ / 2; ++q) p[q] = f2_pack(v[q], v[q + 8]);
+      if (FULL || lg > 0) f2_cross_halves(p, sgn);     // row bit 0
+      f2_butterflies<FULL>(p, 6, lg);                  // row bits 6-9
+#pragma unroll
+      for (int q = 0; q < kTmaJ / 2; ++q) {
+        float x, y;
+        f2_unpack(p[q], x, y);
+        tile[((rb + 64 * q) ^ sw) * kColW + c] = x;
+        tile[((rb + 64 * (q + 8)) ^ sw) * kColW + c] = y;
       }
-#pragma unroll
-      for (int b = 0; b < 4; ++b)
-        if (FULL || 6 + b < lg)
-#pragma unroll
-          for (int j = 0; j < kTmaJ; ++j)
-            if ((j & (1 << b)) == 0) {
-              const float lo = v[j], hi = v[j | (1 << b)];
-              v[j] = lo + hi;
-              v[j | (1 << b)] = lo - hi;
-            }
-#pragma unroll
-      for (int j = 0; j < kTmaJ; ++j) tile[(rb + 64 * j) * kColW + c] = v[j];
       if (tn < a.ntiles) draw(tn, tid, mi_next, mh_next);
     }
     __syncthreads();                                     // the tile holds pass 1; mI of t is free
@@ -363,28 +442,20 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
     // ---- pass 2: butterflies over row bits 1-5, Hadamard scatter
     const int qb = (warp & 1) + 32 * h + 64 * (warp >> 1);
 #pragma unroll
-    for (int i = 0; i < kTmaJ; ++i) v[i] = tile[(qb + 2 * i) * kColW + c];
+    for (int i = 0; i < kTmaJ; ++i) v[i] = tile[((qb + 2 * i) ^ h) * kColW + c];
     __syncthreads();                                     // the tile is free: the next copy may land
     if (tid == 0 && tn < a.ntiles) {
       fence_proxy_async_smem();
       issue(tn);
     }
+    {
+      uint64_t p[kTmaJ / 2];
 #pragma unroll
-    for (int b = 0; b < 4; ++b)
-      if (FULL || 1 + b < lg)
+      for (int q = 0; q < kTmaJ / 2; ++q) p[q] = f2_pack(v[q], v[q + 8]);
+      f2_butterflies<FULL>(p, 1, lg);                  // row bits 1-4
+      if (FULL || 5 < lg) f2_cross_halves(p, sgn);     // row bit 5
 #pragma unroll
-        for (int i = 0; i < kTmaJ; ++i)
-          if ((i & (1 << b)) == 0) {
-            const float lo = v[i], hi = v[i | (1 << b)];
-            v[i] = lo + hi;
-            v[i | (1 << b)] = lo - hi;
-          }
-    if (FULL || 5 < lg) {
-#pragma unroll
-      for (int i = 0; i < kTmaJ; ++i) {
-        const float o = __shfl_xor_sync(0xffffffffu, v[i], 16);
-        v[i] = h ? (o - v[i]) : (v[i] + o);
-      }
+      for (int q = 0; q < kTmaJ / 2; ++q) f2_unpack(p[q], v[q], v[q + 8]);
     }
     if (live) {
 #pragma unroll
@@ -432,13 +503,10 @@ __global__ void __launch_bounds__(kBcolThreads) fct_embed_bcol_kernel(const Cols
     }
 #pragma unroll
     for (int k = 0; k < kColJ; ++k) {
-      const uint4 o = draw_row(a.key, static_cast<uint64_t>(a.row_offset + r0 + lane + 32 * k), a.problem, kStreamFct);
-      const bool neg = a.sign_flip && (o.w & 1u);
-      const float wI = 4.f * cauchy_f32(o.w >> 8);
-      if (neg) v[k] = -v[k];                                                 // z = σ·x
-      red_add_shared(smem_u32(Pb + bucket_of(o.z, r1)), wI * v[k]);        // identity half
-      mH[k * 32 + lane] = make_float2(4.f * cauchy_f32(o.y >> 8) * a.inv_sqrt_s,
-                                      __uint_as_float(static_cast<uint32_t>(bucket_of(o.x, r1))));
+      const uint4 e = __ldg(a.draws + (r0 + lane + 32 * k));
+      if (e.y & 0x80000000u) v[k] = -v[k];                                  // z = σ·x
+      red_add_shared(smem_u32(Pb + ((e.y & 0x7FFFFFFFu) >> 6)), __uint_as_float(e.x) * v[k]);   // identity half
+      mH[k * 32 + lane] = make_float2(__uint_as_float(e.z), __uint_as_float(e.w >> 6));
     }
 #pragma unroll
     for (int b = 0; b < 5; ++b)
@@ -546,7 +614,7 @@ static size_t bcol_smem_bytes(int r1) {
 
 static size_t cols_tma_smem_bytes(int r1) {
   return 128 + static_cast<size_t>(kColT) * kColW * 4 + static_cast<size_t>(r1) * kColW * 4 +
-         static_cast<size_t>(kColT) * sizeof(uint4) + static_cast<size_t>(kColMeta) * sizeof(uint2);
+         static_cast<size_t>(kColT) * sizeof(uint2) + static_cast<size_t>(kColMeta) * sizeof(uint2);
 }
 
 int fct_cols_slices(int log2s, int d, int r1, int max_smem) {
@@ -605,7 +673,14 @@ bool launch_fct_cols(const Plan& pl, const void* A, int64_t lda, l1s_dtype dt, c
   a.partials_b = parts + static_cast<size_t>(pl.fct_cols) * pl.fct_ctas * pl.r1 * kColW;
   a.accumulate = accumulate ? 1 : 0;
   a.flags = reinterpret_cast<uint32_t*>(ws + pl.off_status);
+  a.draws = reinterpret_cast<uint4*>(ws + pl.off_draws);
   void* args[] = {&a};
+  {
+    const int64_t rows = a.ntiles * kColT;
+    const int64_t blocks = std::min<int64_t>((rows + 255) / 256, 8 * static_cast<int64_t>(device_info().sms));
+    fct_draws_kernel<<<static_cast<int>(blocks), 256, 0, st>>>(a);
+    if (!cuda_ok(cudaGetLastError(), "launch fct_draws")) return false;
+  }
   // TMA staging needs a 16-byte aligned base and a row pitch that is a multiple of 16 bytes.
   const size_t esz = dt == L1S_BF16 ? 2 : 4;
   CUtensorMap mapA;
@@ -644,7 +719,7 @@ bool launch_fct_cols(const Plan& pl, const void* A, int64_t lda, l1s_dtype dt, c
       !cuda_ok(cudaLaunchKernel(fb, dim3(bcol_ctas(pl.n)), dim3(kBcolThreads), args, bsmem, st),
                "launch fct_embed_bcol"))
     return false;
-  count_launch(2);
+  count_launch(3);
   return true;
 }
 
