@@ -53,6 +53,8 @@ def parse():
                     help="time eager calls instead of replays of the step captured as a CUDA graph")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the other forms (measured after the main line's timed region)")
+    ap.add_argument("--kernel-case", default=None, choices=sorted(KERNEL_CASES),
+                    help="run one small case of one kernel, twice, and exit (for profiler captures; no timing)")
     ap.add_argument("--variants", default="bf16,colscale,optimized,replacement,multi,sct,t2rows_bf16,batched,canonical",
                     help="comma-separated forms to measure after the main line: bf16 (the main data streamed as "
                          "BF16), colscale (n = 2^22, d = 16, FP32), optimized, replacement, multi, sct (the slow "
@@ -902,8 +904,66 @@ def run_gpu(args) -> None:
         dist.destroy_process_group()
 
 
+# Small cases of the kernels whose profiles are kept under profiles/: each runs the call
+# twice on device-generated data (a few GB at most), so that a capture of one launch
+# (ncu -s 1 -c 1) sees a warm launch.  Sizes: phase 1 of the d = 64 headline at n = 2^22
+# (and 2^24 for its DRAM traffic), the slow transform at n = 2^21, d = 16, and the d = 64
+# tensor-core λ at n = 2^22.
+KERNEL_CASES = {"phase1_d64_n4M": (1 << 22,), "phase1_d64_n16M": (1 << 24,), "sct_d16_n2M": (1 << 21,),
+                "lambda_tc_d64_n4M": (1 << 22,)}
+
+
+def run_kernel_case(args) -> None:
+    import torch
+
+    import paper_1207_4684_gb300 as L
+
+    L.load()
+    dev = torch.device("cuda:0")
+    torch.cuda.set_device(dev)
+    g = torch.Generator(device=dev)
+    g.manual_seed(0)
+    (n,) = KERNEL_CASES[args.kernel_case]
+    if args.kernel_case.startswith("phase1"):
+        d, r1 = 64, 2130
+        A = torch.randn((n, d), generator=g, device=dev)
+        b = torch.randn(n, generator=g, device=dev)
+        prm = L.make_params(1024, r1, 32, 1e5, seed=1)
+    elif args.kernel_case.startswith("sct"):
+        d, r1 = 16, 355
+        A = torch.randn((n, d), generator=g, device=dev)
+        b = torch.randn(n, generator=g, device=dev)
+        prm = L.make_params(1, r1, 16, 2e4, seed=1, transform=1)
+    else:
+        d, r1 = 64, 2130
+        A = torch.randn((n, d), generator=g, device=dev).to(torch.bfloat16)
+        b = torch.randn(n, generator=g, device=dev)
+        prm = L.make_params(1024, r1, 32, 1e5, seed=1)
+    dt = L.BF16 if A.dtype == torch.bfloat16 else L.F32
+    ws = L.workspace(prm, n, d, dt, device=dev)
+    L.l1s_status_reset(ws)
+    if args.kernel_case.startswith("lambda"):
+        M = torch.randn((d + 1, 32), generator=g, device=dev, dtype=torch.float64) * 0.01
+        lam = torch.empty(n, device=dev)
+        tot = torch.empty(1, device=dev, dtype=torch.float64)
+        for _ in range(2):
+            L.l1_lambda(A, b, M, prm, lam, tot, ws)
+    else:
+        pix = torch.empty((r1, d + 1), device=dev)
+        for _ in range(2):
+            L.fct_embed(A, b, prm, pix, ws)
+    torch.cuda.synchronize()
+    flags = L.l1s_status_read(ws)
+    print(json.dumps({"kernel_case": args.kernel_case, "n": n, "status": flags}))
+    if flags:
+        sys.exit(1)
+
+
 def main():
     args = parse()
+    if args.kernel_case:
+        run_kernel_case(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:
