@@ -271,56 +271,6 @@ __global__ void __launch_bounds__(256) fct_draws_kernel(const ColsArgs a) {
   }
 }
 
-// Two FP32 values in one 64-bit register, for the packed add/sub/fma of sm_100-class
-// parts: each lane is rounded as the scalar instruction rounds it, so a butterfly on a
-// pair gives exactly the two scalar results.
-__device__ __forceinline__ uint64_t f2_pack(float lo, float hi) {
-  uint64_t r;
-  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
-  return r;
-}
-__device__ __forceinline__ void f2_unpack(uint64_t p, float& lo, float& hi) {
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(p));
-}
-__device__ __forceinline__ uint64_t f2_add(uint64_t a, uint64_t b) {
-  uint64_t r;
-  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-  return r;
-}
-__device__ __forceinline__ uint64_t f2_sub(uint64_t a, uint64_t b) {
-  uint64_t r;
-  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-  return r;
-}
-__device__ __forceinline__ uint64_t f2_fma(uint64_t a, uint64_t b, uint64_t c) {
-  uint64_t r;
-  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
-  return r;
-}
-
-// Butterflies of a 16-value register column v[0..15] held as the pairs p[k] = (v[k], v[k+8]):
-// stages over bits 0-2 of the index run on pairs, the stage over bit 3 inside each pair.
-template <bool FULL>
-__device__ __forceinline__ void f2_butterflies(uint64_t (&p)[8], int first_bit, int lg) {
-#pragma unroll
-  for (int b = 0; b < 3; ++b)
-    if (FULL || first_bit + b < lg)
-#pragma unroll
-      for (int k = 0; k < 8; ++k)
-        if ((k & (1 << b)) == 0) {
-          const uint64_t lo = p[k], hi = p[k | (1 << b)];
-          p[k] = f2_add(lo, hi);
-          p[k | (1 << b)] = f2_sub(lo, hi);
-        }
-  if (FULL || first_bit + 3 < lg)
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      float x, y;
-      f2_unpack(p[k], x, y);
-      p[k] = f2_pack(x + y, x - y);
-    }
-}
-
 // The butterfly across the two half-warps (lane bit 4) on pairs: the lower half keeps
 // v + o, the upper o − v, as one packed fma with ±1.
 __device__ __forceinline__ void f2_cross_halves(uint64_t (&p)[8], uint64_t sgn) {
@@ -427,7 +377,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
 #pragma unroll
       for (int q = 0; q < kTmaJ / 2; ++q) p[q] = f2_pack(v[q], v[q + 8]);
       if (FULL || lg > 0) f2_cross_halves(p, sgn);     // row bit 0
-      f2_butterflies<FULL>(p, 6, lg);                  // row bits 6-9
+      f2_butterflies<kTmaJ>(p, FULL ? 0xFu : f2_stage_mask(6, lg));   // row bits 6-9
 #pragma unroll
       for (int q = 0; q < kTmaJ / 2; ++q) {
         float x, y;
@@ -452,7 +402,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
       uint64_t p[kTmaJ / 2];
 #pragma unroll
       for (int q = 0; q < kTmaJ / 2; ++q) p[q] = f2_pack(v[q], v[q + 8]);
-      f2_butterflies<FULL>(p, 1, lg);                  // row bits 1-4
+      f2_butterflies<kTmaJ>(p, FULL ? 0xFu : f2_stage_mask(1, lg));   // row bits 1-4
       if (FULL || 5 < lg) f2_cross_halves(p, sgn);     // row bit 5
 #pragma unroll
       for (int q = 0; q < kTmaJ / 2; ++q) f2_unpack(p[q], v[q], v[q + 8]);

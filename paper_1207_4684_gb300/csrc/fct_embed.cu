@@ -316,8 +316,8 @@ __global__ void __launch_bounds__(kFctMaxThreads) fct_embed_kernel(const FctArgs
 //  * 1 b warp: 32 rows per register slot; stages over row bits ≥ 5 in registers, over
 //    bits 0-4 by shuffles; its own scatter array.
 // Hand-offs use mbarriers (bounded waits; a timeout raises the TIMEOUT status bit and
-// every role stops).  Draws of a row are packed as {32·h_I, 4·c_I·σ, sign mask, h_I}
-// and {32·h_H, 4·c_H/√s}.
+// every role stops).  Draws of a row are packed as {PST·h_I with σ in bit 31, 4·c_I} and
+// {PST·h_H, 4·c_H/√s} (8 bytes each); the butterflies run on packed FP32 pairs.
 constexpr int kWsB = 1, kWsP = 4;
 template <int W>
 struct WsCfg {
@@ -325,11 +325,9 @@ struct WsCfg {
   static constexpr int kThreads = 32 * (kA + kWsB + kWsP);      // 416 or 672
 };
 
-struct __align__(16) T16Meta {
-  int offI;           // 32·h_I: first word of row h_I of P
-  float wIs;          // 4·c_I·σ (the identity term of row i is wIs·x_i)
-  uint32_t smask;     // 0x80000000 when σ = −1 (z = x with its sign bit flipped)
-  int hI;             // h_I (the b column's own array)
+struct __align__(8) T16Meta {
+  uint32_t offs;      // PST·h_I (first word of row h_I of P), | 2^31 when σ = −1
+  float wI;           // 4·c_I (the identity term of row i is wI·z_i, z_i = σ_i·x_i)
 };
 struct __align__(8) T16MetaH {
   int offH;           // 32·h_H
@@ -439,11 +437,8 @@ __global__ void __launch_bounds__(WsCfg<W>::kThreads, LEAN ? 3 : (W == 16 ? 2 : 
         const uint4 o = draw_row(a.key, grow, a.problem, kStreamFct);
         const bool neg = a.sign_flip && (o.w & 1u);
         T16Meta m;
-        m.hI = bucket_of(o.z, r1);
-        m.offI = PST * m.hI;
-        const float wI = 4.f * cauchy_f32(o.w >> 8);
-        m.wIs = neg ? -wI : wI;
-        m.smask = neg ? 0x80000000u : 0u;
+        m.offs = static_cast<uint32_t>(PST * bucket_of(o.z, r1)) | (neg ? 0x80000000u : 0u);
+        m.wI = 4.f * cauchy_f32(o.w >> 8);
         mi[r] = m;
         T16MetaH h;
         h.offH = PST * bucket_of(o.x, r1);
@@ -493,23 +488,22 @@ __global__ void __launch_bounds__(WsCfg<W>::kThreads, LEAN ? 3 : (W == 16 ? 2 : 
             for (int j = 0; j < 16; ++j) v[j] = live ? widen<TA>(rawA[(base | j) * sd + c]) : 0.f;
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
-              const int4 m = *reinterpret_cast<const int4*>(&mi[base | j]);
-              const float x = v[j];
-              v[j] = __uint_as_float(__float_as_uint(x) ^ static_cast<uint32_t>(m.z));
-              if (live) atomicAdd(Pl + m.x, __int_as_float(m.y) * x);
+              const T16Meta m = mi[base | j];
+              const uint32_t sg = m.offs & 0x80000000u;
+              v[j] = __uint_as_float(__float_as_uint(v[j]) ^ sg);   // z = σ·x
+              if (live) atomicAdd(Pl + (m.offs ^ sg), m.wI * v[j]);
             }
+            uint64_t p[8];
 #pragma unroll
-            for (int t = 0; t < 4; ++t)
-              if (t < lg)                                       // row bit t
+            for (int k = 0; k < 8; ++k) p[k] = f2_pack(v[k], v[k + 8]);
+            f2_butterflies<16>(p, f2_stage_mask(0, lg));         // row bits 0-3
 #pragma unroll
-                for (int j = 0; j < 16; ++j)
-                  if ((j & (1 << t)) == 0) {
-                    const float lo = v[j], hi = v[j | (1 << t)];
-                    v[j] = lo + hi;
-                    v[j | (1 << t)] = lo - hi;
-                  }
-#pragma unroll
-            for (int j = 0; j < 16; ++j) tile[(base | j) * 32 + c] = v[j];
+            for (int k = 0; k < 8; ++k) {
+              float x, y;
+              f2_unpack(p[k], x, y);
+              tile[(base | k) * 32 + c] = x;
+              tile[(base | (k + 8)) * 32 + c] = y;
+            }
           }
         } else
         for (int task = tid; task < S; task += 32 * kWsA) {
@@ -524,26 +518,22 @@ __global__ void __launch_bounds__(WsCfg<W>::kThreads, LEAN ? 3 : (W == 16 ? 2 : 
           for (int j = 0; j < 16; ++j) v[j] = live ? widen<TA>(rawA[(base | (j << 1)) * sd + c]) : 0.f;
 #pragma unroll
           for (int j = 0; j < 16; ++j) {
-            const int4 m = *reinterpret_cast<const int4*>(&mi[base | (j << 1)]);
-            const float x = v[j];
-            v[j] = __uint_as_float(__float_as_uint(x) ^ static_cast<uint32_t>(m.z));
-            if (live) atomicAdd(Pl + m.x, __int_as_float(m.y) * x);
+            const T16Meta m = mi[base | (j << 1)];
+            const uint32_t sg = m.offs & 0x80000000u;
+            v[j] = __uint_as_float(__float_as_uint(v[j]) ^ sg);     // z = σ·x
+            if (live) atomicAdd(Pl + (m.offs ^ sg), m.wI * v[j]);
           }
+          uint64_t p[8];
 #pragma unroll
-          for (int t = 0; t < 4; ++t) {
-            if (t + 1 < lg) {                                   // row bit t + 1
+          for (int k = 0; k < 8; ++k) p[k] = f2_pack(v[k], v[k + 8]);
+          f2_butterflies<16>(p, f2_stage_mask(1, lg));           // row bits 1-4
 #pragma unroll
-              for (int j = 0; j < 16; ++j) {
-                if ((j & (1 << t)) == 0) {
-                  const float lo = v[j], hi = v[j | (1 << t)];
-                  v[j] = lo + hi;
-                  v[j | (1 << t)] = lo - hi;
-                }
-              }
-            }
+          for (int k = 0; k < 8; ++k) {
+            float x, y;
+            f2_unpack(p[k], x, y);
+            tile[(base | (k << 1)) * 16 + c] = x;
+            tile[(base | ((k + 8) << 1)) * 16 + c] = y;
           }
-#pragma unroll
-          for (int j = 0; j < 16; ++j) tile[(base | (j << 1)) * 16 + c] = v[j];
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&stage_free[sbuf]);
@@ -556,16 +546,14 @@ __global__ void __launch_bounds__(WsCfg<W>::kThreads, LEAN ? 3 : (W == 16 ? 2 : 
           float v[G2];
 #pragma unroll
           for (int j = 0; j < G2; ++j) v[j] = tile[(g2 | (j << 4)) * 32 + c];
+          {
+            uint64_t p[G2 / 2];
 #pragma unroll
-          for (int t = 0; t < K2; ++t)
-            if (4 + t < lg)                                     // row bit 4 + t
+            for (int k = 0; k < G2 / 2; ++k) p[k] = f2_pack(v[k], v[k + G2 / 2]);
+            f2_butterflies<G2>(p, f2_stage_mask(4, lg));         // row bits 4 and up
 #pragma unroll
-              for (int j = 0; j < G2; ++j)
-                if ((j & (1 << t)) == 0) {
-                  const float lo = v[j], hi = v[j | (1 << t)];
-                  v[j] = lo + hi;
-                  v[j | (1 << t)] = lo - hi;
-                }
+            for (int k = 0; k < G2 / 2; ++k) f2_unpack(p[k], v[k], v[k + G2 / 2]);
+          }
           if (c < d) {
             float* Pl = P + c;
 #pragma unroll
@@ -584,18 +572,13 @@ __global__ void __launch_bounds__(WsCfg<W>::kThreads, LEAN ? 3 : (W == 16 ? 2 : 
             const int jj = j ^ hb;
             v[j] = tile[((g2 << 1) | (jj & 1) | ((jj >> 1) << 5)) * 16 + c];
           }
+          {
+            uint64_t p[G2 / 2];
 #pragma unroll
-          for (int t = 0; t < K2; ++t) {
-            if (t == 0 || 4 + t < lg) {                         // row bit 0, then bits 5 and up
+            for (int k = 0; k < G2 / 2; ++k) p[k] = f2_pack(v[k], v[k + G2 / 2]);
+            f2_butterflies<G2>(p, f2_stage_mask(4, lg) | 1u);    // row bit 0, then bits 5 and up
 #pragma unroll
-              for (int j = 0; j < G2; ++j) {
-                if ((j & (1 << t)) == 0) {
-                  const float lo = v[j], hi = v[j | (1 << t)];
-                  v[j] = lo + hi;
-                  v[j | (1 << t)] = lo - hi;
-                }
-              }
-            }
+            for (int k = 0; k < G2 / 2; ++k) f2_unpack(p[k], v[k], v[k + G2 / 2]);
           }
           if (c < d) {
             float* Pl = P + (LEAN ? 0 : hb * 16) + c;
@@ -617,10 +600,10 @@ __global__ void __launch_bounds__(WsCfg<W>::kThreads, LEAN ? 3 : (W == 16 ? 2 : 
 #pragma unroll
         for (int k = 0; k < KB; ++k) {
           const int row = lane + 32 * k;
-          const int4 m = *reinterpret_cast<const int4*>(&mi[row]);
-          const float x = -rawB[row];
-          v[k] = __uint_as_float(__float_as_uint(x) ^ static_cast<uint32_t>(m.z));
-          atomicAdd(&Pb[m.w], __int_as_float(m.y) * x);
+          const T16Meta m = mi[row];
+          const uint32_t sg = m.offs & 0x80000000u;
+          v[k] = __uint_as_float(__float_as_uint(-rawB[row]) ^ sg);   // z = σ·x
+          atomicAdd(&Pb[(m.offs ^ sg) / PST], m.wI * v[k]);
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&stage_free[sbuf]);

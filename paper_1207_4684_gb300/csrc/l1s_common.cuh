@@ -134,6 +134,68 @@ __device__ __forceinline__ uint64_t u53_of(uint32_t wa, uint32_t wb) {
   return (static_cast<uint64_t>(wa >> 5) << 26) | static_cast<uint64_t>(wb >> 6);
 }
 
+// ----------------------------------------------------------------- packed FP32 pairs
+// Two FP32 values in one 64-bit register, for the packed add/sub/fma of sm_100-class
+// parts: each lane is rounded as the scalar instruction rounds it, so a butterfly on a
+// pair gives exactly the two scalar results.
+__device__ __forceinline__ uint64_t f2_pack(float lo, float hi) {
+  uint64_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ void f2_unpack(uint64_t p, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(p));
+}
+__device__ __forceinline__ uint64_t f2_add(uint64_t a, uint64_t b) {
+  uint64_t r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ uint64_t f2_sub(uint64_t a, uint64_t b) {
+  uint64_t r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ uint64_t f2_fma(uint64_t a, uint64_t b, uint64_t c) {
+  uint64_t r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+  return r;
+}
+
+// Stages t of a register butterfly run on row bit first + t, and only below log2 s: the
+// mask of the stages that run.
+__device__ __forceinline__ uint32_t f2_stage_mask(int first, int lg) {
+  const int k = lg - first;
+  return k <= 0 ? 0u : (k >= 32 ? 0xFFFFFFFFu : ((1u << k) - 1u));
+}
+
+// Radix-2 butterflies over the index bits of a register column v[0..N) held as the pairs
+// p[k] = (v[k], v[k + N/2]), in the order of the bits: stages over the low log2(N/2) bits
+// run on pairs, the top stage inside each pair.  Stage t runs when bit t of `stages` is set.
+template <int N>
+__device__ __forceinline__ void f2_butterflies(uint64_t (&p)[N / 2], uint32_t stages) {
+  constexpr int H = N / 2;
+  constexpr int LH = H >= 16 ? 4 : (H >= 8 ? 3 : (H >= 4 ? 2 : (H >= 2 ? 1 : 0)));
+  static_assert((1 << LH) == H, "N must be a power of two from 2 to 32");
+#pragma unroll
+  for (int b = 0; b < LH; ++b)
+    if ((stages >> b) & 1u)
+#pragma unroll
+      for (int k = 0; k < H; ++k)
+        if ((k & (1 << b)) == 0) {
+          const uint64_t lo = p[k], hi = p[k | (1 << b)];
+          p[k] = f2_add(lo, hi);
+          p[k | (1 << b)] = f2_sub(lo, hi);
+        }
+  if ((stages >> LH) & 1u)
+#pragma unroll
+    for (int k = 0; k < H; ++k) {
+      float x, y;
+      f2_unpack(p[k], x, y);
+      p[k] = f2_pack(x + y, x - y);
+    }
+}
+
 // ----------------------------------------------------------------- TMA bulk copies and mbarriers
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
