@@ -910,7 +910,7 @@ def run_gpu(args) -> None:
 # (and 2^24 for its DRAM traffic), the slow transform at n = 2^21, d = 16, and the d = 64
 # tensor-core λ at n = 2^22.
 KERNEL_CASES = {"phase1_d64_n4M": (1 << 22,), "phase1_d64_n16M": (1 << 24,), "sct_d16_n2M": (1 << 21,),
-                "lambda_tc_d64_n4M": (1 << 22,)}
+                "lambda_tc_d64_n4M": (1 << 22,), "batched_256": (0,)}
 
 
 def run_kernel_case(args) -> None:
@@ -924,6 +924,29 @@ def run_kernel_case(args) -> None:
     g = torch.Generator(device=dev)
     g.manual_seed(0)
     (n,) = KERNEL_CASES[args.kernel_case]
+    if args.kernel_case == "batched_256":
+        # the batched form's 256 members (default schedules), one l1_regress_batched call twice
+        from synth import make_batched_problems
+
+        probs, keep = [], []
+        for pr in make_batched_problems(256):
+            w = pr["w"]
+            A = torch.from_numpy(pr["A"]).to(dev)
+            b = torch.from_numpy(pr["b"]).to(dev)
+            prm = L.make_params(w.s, w.r1, w.r2, w.coreset, seed=w.seed, problem_id=w.problem_id)
+            cnt = torch.zeros(1, dtype=torch.int64, device=dev)
+            keep.append((A, b, cnt))
+            probs.append(L.make_problem(A, b, prm, count=cnt))
+        ws = L.batched_workspace(probs, device=dev)
+        flags = torch.zeros(len(probs), dtype=torch.int32, device=dev)
+        for _ in range(2):
+            L.l1_regress_batched(probs, ws, flags)
+        torch.cuda.synchronize()
+        bad = int((flags != 0).sum().item())
+        print(json.dumps({"kernel_case": args.kernel_case, "members": len(probs), "status_nonzero": bad}))
+        if bad:
+            sys.exit(1)
+        return
     if args.kernel_case.startswith("phase1"):
         d, r1 = 64, 2130
         A = torch.randn((n, d), generator=g, device=dev)
