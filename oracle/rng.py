@@ -57,6 +57,7 @@ STREAM_PI2 = 1
 STREAM_SAMPLE = 2
 STREAM_REPLACE = 3
 STREAM_SCT = 4
+STREAM_FJLT = 5
 
 
 def philox4x32_10(c0, c1, c2, c3, k0, k1):
@@ -213,3 +214,16 @@ def sct_matrix(seed: int, problem_id: int, rows, r1: int) -> np.ndarray:
         for w in range(4):
             out[4 * g + w] = cauchy_from_k((words[w] >> np.uint64(8)).astype(np.int64))
     return out[:r1]
+
+
+def fjlt_draws(seed: int, problem_id: int, t: int, s: int):
+    """The draws of FCT2's s × t FJLT block G (stream 5, one G for every block): call i
+    (counter (i, 0, problem_id, 5)) gives D_i = −1 when bit 0 of its word 0 is set (i < t)
+    and the Hadamard row of G's row i, ⌊word1·t / 2^32⌋ (i < s).  Returns (D as ±1
+    floats of length t, the s selected rows)."""
+    k0, k1 = _key(seed)
+    calls = np.arange(max(t, s), dtype=np.uint64)
+    o0, o1, _, _ = philox4x32_10(calls, np.uint64(0), np.uint64(problem_id), np.uint64(STREAM_FJLT), k0, k1)
+    D = np.where((o0[:t] & np.uint64(1)) == 1, -1.0, 1.0)
+    sel = ((o1[:s] * np.uint64(t)) >> np.uint64(32)).astype(np.int64)
+    return D, sel

@@ -14,7 +14,7 @@ import math
 import numpy as np
 from scipy import stats
 
-from oracle import condition, fct, leverage, pipeline, quality, rng, sampling, sct, separable, solve
+from oracle import condition, fct, fct2, leverage, pipeline, quality, rng, sampling, sct, separable, solve
 
 
 # ----------------------------------------------------------------- Hadamard
@@ -411,7 +411,8 @@ def _all_checks():
     return ALL_CHECKS + [check_bf16_round, check_gaussian_pi2, check_gaussian_lambda_distribution,
                          check_scaled_probabilities, check_multiple_regression, check_with_replacement,
                          check_sct_draws, check_sct_stability, check_sct_embedding_bound, check_kappa_bar,
-                         check_canonical_optimum]
+                         check_canonical_optimum, check_fjlt_isometry, check_fjlt_spread, check_fct2_dense,
+                         check_fct2_stability, check_fct2_embedding_bound]
 
 
 # ----------------------------------------------------------------- slow Cauchy transform
@@ -584,3 +585,85 @@ def check_canonical_optimum(seed: int = 21) -> None:
     assert math.isclose(e["l1"], 0.75 / np.abs(lo).sum(), rel_tol=1e-12)
     assert math.isclose(e["l2"], math.sqrt(0.5 ** 2 + 0.25 ** 2) / np.linalg.norm(lo), rel_tol=1e-12)
     assert math.isclose(e["linf"], 0.5 / np.abs(lo).max(), rel_tol=1e-12)
+
+
+# ----------------------------------------------------------------- FCT2 (§3.2)
+def check_fjlt_isometry(t: int = 16, s: int = 4, seeds: int = 600) -> None:
+    """The SRHT block G = √(t/s)·S·H_t·D has entries ±1/√s, so diag(GᵀG) = 1 exactly; over
+    seeds E[GᵀG] = D·H_tᵀ·H_t·D = I (off-diagonal means near 0) and, rows being sampled
+    independently, each off-diagonal entry has mean square 1/s (not 1, as for repeated rows)."""
+    acc = np.zeros((t, t))
+    acc2 = np.zeros((t, t))
+    for sd in range(seeds):
+        G = fct2.fjlt_matrix(sd, 0, t, s)
+        assert np.allclose(np.abs(G), 1.0 / math.sqrt(s)), "entries of G are not ±1/√s"
+        M = G.T @ G
+        assert np.allclose(np.diag(M), 1.0), "diag(GᵀG) != 1"
+        acc += M
+        acc2 += M * M
+    off = ~np.eye(t, dtype=bool)
+    mean = acc / seeds
+    assert np.abs(mean[off]).max() < 5.0 / math.sqrt(s * seeds), "E[GᵀG] is not I"
+    ms = (acc2 / seeds)[off]
+    assert abs(ms.mean() - 1.0 / s) < 0.1 / s, ("off-diagonal mean square", ms.mean(), 1.0 / s)
+
+
+def check_fjlt_spread(t: int = 64, s: int = 16, seeds: int = 200) -> None:
+    """The random signs spread a structured vector: for x = (1, …, 1), H_t·x = √t·e_0 alone,
+    but H_t·D·x is a ±1-sum in every row, so ‖G·x‖₂² ≈ ‖x‖₂² = t (median over seeds within a
+    factor 2)."""
+    x = np.ones(t)
+    r = [float(np.sum((fct2.fjlt_matrix(sd, 1, t, s) @ x) ** 2)) / t for sd in range(seeds)]
+    med = float(np.median(r))
+    assert 0.5 < med < 2.0, ("‖Gx‖² / ‖x‖² median", med)
+
+
+def check_fct2_dense(seed: int = 5) -> None:
+    """Π1·X from the blocks equals the explicit product of the factors,
+    (8/r1)·√(πt/(2s))·C·H̃ with H̃ = diag(G, …, G) over the zero-padded rows, C's column k
+    the Cauchys of row id (offset/t)·s + k, for a ragged n and a nonzero block offset."""
+    g = np.random.default_rng(seed)
+    t, s, r1 = 16, 6, 11
+    n, q = 3 * t + 5, 3
+    X = g.standard_normal((n, q))
+    off = 7 * t
+    got, _ = fct2.fct2_embed(X, t, s, r1, seed=seed, problem_id=2, row_offset=off)
+    nb = -(-n // t)
+    G = fct2.fjlt_matrix(seed, 2, t, s)
+    Ht = np.zeros((nb * s, nb * t))
+    for b in range(nb):
+        Ht[b * s:(b + 1) * s, b * t:(b + 1) * t] = G
+    C = rng.sct_matrix(seed, 2, (off // t) * s + np.arange(nb * s), r1)
+    Xp = np.zeros((nb * t, q))
+    Xp[:n] = X
+    want = 8.0 / r1 * math.sqrt(math.pi * t / (2 * s)) * (C @ (Ht @ Xp))
+    assert np.allclose(got, want, rtol=1e-12, atol=1e-12 * np.abs(want).max()), "FCT2 blocks != dense product"
+
+
+def check_fct2_stability(seeds: int = 400) -> None:
+    """1-stability: for a fixed y, entry r of Π1·y is (8/r1)·√(πt/(2s)) times a standard Cauchy
+    times ‖H̃y‖₁, so its ratio to scale·‖H̃y‖₁ is standard Cauchy over seeds (KS)."""
+    t, s, r1, n = 32, 8, 10, 96
+    y = np.random.default_rng(3).standard_normal((n, 1))
+    ratios = []
+    for sd in range(seeds):
+        pix, _ = fct2.fct2_embed(y, t, s, r1, seed=sd)
+        G = fct2.fjlt_matrix(sd, 0, t, s)
+        hy = np.abs(np.einsum("rt,bt->br", G, y[:, 0].reshape(-1, t))).sum()
+        ratios.append(pix[0, 0] / (8.0 / r1 * math.sqrt(math.pi * t / (2 * s)) * hy))   # §3.2's scale
+    p = stats.kstest(ratios, "cauchy").pvalue
+    assert p > 1e-3, ("Π1y is not scale·Cauchy·‖H̃y‖₁", p)
+
+
+def check_fct2_embedding_bound(seed: int = 9) -> None:
+    """The lower bound of Theorem FCT2, ‖y‖₁ ≤ ‖Π1·y‖₁ for y in the column space of X
+    (d = 4, r1 = ⌈8 d ln d⌉, s = ⌈2 d ln d⌉, t = 2^⌈log₂ 2d²⌉), for every one of 50 random y."""
+    g = np.random.default_rng(seed)
+    d, n = 4, 2048
+    r1, s, t = math.ceil(8 * d * math.log(d)), math.ceil(2 * d * math.log(d)), 32
+    X = g.standard_normal((n, d)) * np.array([1.0, 10.0, 0.1, 3.0])
+    for k in range(50):
+        z = g.standard_normal(d)
+        y = X @ z
+        pix, _ = fct2.fct2_embed(y[:, None], t, s, r1, seed=100 + k)
+        assert np.abs(pix).sum() >= np.abs(y).sum(), f"‖Π1y‖₁ < ‖y‖₁ for y {k}"

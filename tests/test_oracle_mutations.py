@@ -8,7 +8,7 @@ import numpy as np
 import pytest
 
 import pins
-from oracle import condition, fct, leverage, pipeline, rng, sampling, sct, separable, solve
+from oracle import condition, fct, fct2, leverage, pipeline, rng, sampling, sct, separable, solve
 
 ORIG_EMBED = fct.fct1_embed
 ORIG_HAD = fct.sylvester_hadamard
@@ -26,6 +26,37 @@ ORIG_GAUSS = rng.pi2_gaussian_matrix
 ORIG_SCALED = sampling.probabilities_scaled
 ORIG_SCT = sct.sct_embed
 ORIG_SCT_MATRIX = rng.sct_matrix
+ORIG_FJLT_DRAWS = rng.fjlt_draws
+ORIG_FCT2_SCALE = fct2.fct2_scale
+ORIG_FCT2 = fct2.fct2_embed
+
+
+def fjlt_no_signs(seed, problem_id, t, s):
+    D, sel = ORIG_FJLT_DRAWS(seed, problem_id, t, s)
+    return np.ones_like(D), sel
+
+
+def fjlt_one_row(seed, problem_id, t, s):
+    D, sel = ORIG_FJLT_DRAWS(seed, problem_id, t, s)
+    return D, np.full_like(sel, sel[0])
+
+
+def fct2_scale_no_sqrt(t, s, r1):
+    return 8.0 / r1
+
+
+def fct2_same_columns(X, t, s, r1, seed=0, problem_id=0, row_offset=0):
+    import math
+    X = np.asarray(X, dtype=np.float64)
+    n, q = X.shape
+    nb = -(-n // t)
+    Xp = np.zeros((nb * t, q))
+    Xp[:n] = X
+    G = fct2.fjlt_matrix(seed, problem_id, t, s)
+    Y = np.einsum("rt,btq->brq", G, Xp.reshape(nb, t, q)).reshape(nb * s, q)
+    C = rng.sct_matrix(seed, problem_id, np.arange(nb * s) % s, r1)
+    sc = fct2.fct2_scale(t, s, r1)
+    return sc * (C @ Y), sc * (np.abs(C) @ np.abs(Y))
 
 
 def canonical_mean(cols, b, d):
@@ -225,6 +256,10 @@ MUTATIONS = [
      pins.check_with_replacement),
     ("with-replacement target u, not u·Σλ", sampling, "sample_with_replacement", replace_unscaled_target,
      pins.check_with_replacement),
+    ("FJLT signs dropped", rng, "fjlt_draws", fjlt_no_signs, pins.check_fjlt_spread),
+    ("FJLT one sampled row repeated", rng, "fjlt_draws", fjlt_one_row, pins.check_fjlt_isometry),
+    ("FCT2 scale without √(πt/2s)", fct2, "fct2_scale", fct2_scale_no_sqrt, pins.check_fct2_stability),
+    ("FCT2 blocks share C's columns", fct2, "fct2_embed", fct2_same_columns, pins.check_fct2_dense),
     ("separable optimum: mean for median", separable, "canonical_optimum", canonical_mean,
      pins.check_canonical_optimum),
     ("separable optimum: upper median = lower", separable, "canonical_optimum", canonical_hi_low,
