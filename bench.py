@@ -55,10 +55,10 @@ def parse():
                     help="skip the other forms (measured after the main line's timed region)")
     ap.add_argument("--kernel-case", default=None, choices=sorted(KERNEL_CASES),
                     help="run one small case of one kernel, twice, and exit (for profiler captures; no timing)")
-    ap.add_argument("--variants", default="bf16,colscale,optimized,replacement,multi,sct,t2rows_bf16,batched,canonical",
+    ap.add_argument("--variants", default="bf16,colscale,optimized,replacement,multi,sct,fct2,t2rows_bf16,batched,canonical",
                     help="comma-separated forms to measure after the main line: bf16 (the main data streamed as "
                          "BF16), colscale (n = 2^22, d = 16, FP32), optimized, replacement, multi, sct (the slow "
-                         "Cauchy transform; these on the n = 2^22 data), t2rows_bf16 (n = 2^24, d = 32, BF16), "
+                         "Cauchy transform), fct2 (FCT2; these on the n = 2^22 data), t2rows_bf16 (n = 2^24, d = 32, BF16), "
                          "batched, canonical (the canonical-row design of §6.3 at n = 2^26, d = 15: 100 "
                          "coresets and solves from one pass)")
     return ap.parse_args()
@@ -406,6 +406,31 @@ def canonical_variant(L, dev, stream, args) -> dict:
     del A, b, cols
     torch.cuda.empty_cache()
     return out
+
+
+def fct2_variant(L, dev, stream, args, A, b, w, plain_ms: float, fct1_ms: float) -> dict:
+    """FCT2 as Π1 (§3.2) on the same data: one SRHT block G (s = ⌈2d ln d⌉ of t = 2^⌈log₂ 2d²⌉
+    rows kept) per t rows of X, then the slow Cauchy transform on the ns/t rows of H̃X."""
+    import torch
+
+    n, d = A.shape
+    q = d + 1
+    t = 1 << math.ceil(math.log2(2 * d * d))
+    sf = math.ceil(2 * d * math.log(d))
+    prm = L.make_params(t, w.r1, w.r2, w.coreset, seed=w.seed, problem_id=w.problem_id, transform=2, fjlt_rows=sf)
+    ws = L.workspace(prm, n, d, device=dev)
+    cap = int(2 * w.coreset) + 64
+    idx = torch.empty(cap, dtype=torch.int64, device=dev)
+    wts = torch.empty(cap, dtype=torch.float64, device=dev)
+    cnt = torch.zeros(1, dtype=torch.int64, device=dev)
+    ms = _time_step_ms(lambda st: L.l1_coreset(A, b, prm, cap, idx, wts, None, cnt, ws, stream=st), stream, args)
+    kept = int(cnt.item())
+    phase = _phase_ms(L, A, b, prm, cap, q, dev, stream, 2, max(3, args.steps // 4))
+    del ws
+    return {"workload": w.name, "transform": f"FCT2: SRHT blocks of t = {t} rows keeping s = {sf}, then (8/r1)*sqrt(pi*t/(2s))*C",
+            "value": n / (ms / 1e3), "ms_per_step": ms, "phase_ms": phase, "coreset_rows": kept,
+            "rows_of_HX": (-(-n // t)) * sf, "phase1_vs_fct1": phase["fct_embed"] / fct1_ms,
+            "speedup_vs_f32_plain": plain_ms / ms}
 
 
 def bf16_variant(L, dev, stream, args, peak: float) -> dict:
@@ -865,7 +890,7 @@ def run_gpu(args) -> None:
             variants["bf16"] = bf16_same_data_variant(L, dev, stream, args, A, b, w, peaks["hbm_gbs"], ws, ms_per_step)
         del ws, A, b
         torch.cuda.empty_cache()
-        if want & {"colscale", "optimized", "replacement", "multi", "sct"}:
+        if want & {"colscale", "optimized", "replacement", "multi", "sct", "fct2"}:
             line_c, A1, b1, w1 = colscale_variant(L, dev, stream, args, peaks["hbm_gbs"])
             if "colscale" in want:
                 variants["colscale"] = line_c
@@ -883,6 +908,10 @@ def run_gpu(args) -> None:
             if "sct" in want:
                 variants["sct"] = sct_variant(L, dev, stream, args, A1, b1, w1, line_c["ms_per_step"],
                                               line_c["phase_ms"]["fct_embed"])
+            torch.cuda.empty_cache()
+            if "fct2" in want:
+                variants["fct2"] = fct2_variant(L, dev, stream, args, A1, b1, w1, line_c["ms_per_step"],
+                                                line_c["phase_ms"]["fct_embed"])
             del A1, b1
             torch.cuda.empty_cache()
         if "t2rows_bf16" in want:

@@ -27,7 +27,8 @@
  * - Random draws come from Philox4x32-10 (Salmon et al., SC'11) keyed by
  *   params.seed, with counters built from the global row id, params.problem_id
  *   and a stream number (0: signs/buckets/Cauchy scales of Π1, 1: Π2,
- *   2: sampling uniforms, 3: draws with replacement, 4: the slow transform's C).  Row ids are global: row r of A has id
+ *   2: sampling uniforms, 3: draws with replacement, 4: the slow transform's C,
+ *   5: FCT2's block G).  Row ids are global: row r of A has id
  *   params.global_row_offset + r, so shards of one problem reproduce the
  *   unsharded draws.
  * - Not thread-safe per workspace; distinct workspaces may be used from
@@ -94,7 +95,17 @@ typedef struct {
                                  (§3, the theorem of Sohler and Woodruff; the conditioning of
                                  §6.3), entry (r, i), r = 4g + w, from word w of the Philox call
                                  with counter (i_lo, (i_hi mod 2^16) + g·2^16, problem_id, 4);
-                                 s and sign_flip are then unused */
+                                 s and sign_flip are then unused.  2: FCT2 (§3.2),
+                                 (8/r1)·√(πt/(2·fjlt_rows))·C·H̃ with t = s (a power of two) and
+                                 H̃ block diagonal, one fjlt_rows × t block
+                                 G = √(t/fjlt_rows)·S·H_t·D per t rows (a subsampled randomized
+                                 Hadamard transform: D_i = −1 when bit 0 of word 0 of Philox call
+                                 (i, 0, problem_id, 5) is set, G's row r the Hadamard row
+                                 ⌊word1·t/2^32⌋ of call r), then the slow transform above on the
+                                 rows of H̃X (row k of H̃X has Cauchy row id k, counted from
+                                 (global_row_offset/t)·fjlt_rows); sign_flip is unused */
+  int32_t fjlt_rows;          /* transform 2: rows of G kept per t-row block (1 ≤ fjlt_rows ≤ s);
+                                 0 takes ⌈2·d·ln d⌉ (at least 1, at most s); otherwise unused */
 } l1s_params;
 
 /* Text of the calling thread's last host-side error ("" if none). */

@@ -136,7 +136,9 @@ static bool check_params(const l1s_params* p, int64_t n, int d) {
     return set_error("variant 2 draws coreset_size rows: it must be an integer in [1, 1e9]"), false;
   if (p->variant == 1 && (!(p->sample_scale > 0.0) || !isfinite(p->sample_scale)))
     return set_error("variant 1 needs a positive, finite sample_scale"), false;
-  if (p->transform != 0 && p->transform != 1) return set_error("transform must be 0 or 1"), false;
+  if (p->transform < 0 || p->transform > 2) return set_error("transform must be 0, 1 or 2"), false;
+  if (p->transform == 2 && (p->fjlt_rows < 0 || p->fjlt_rows > p->s))
+    return set_error("transform 2: fjlt_rows must be in [0, s] (got %d)", p->fjlt_rows), false;
   return true;
 }
 
@@ -368,17 +370,25 @@ bool make_plan(const l1s_params* p, int64_t n, int d, l1s_dtype dt, bool host_st
   P.fct_threads = g.threads;
   const int per_sm = sch.fct_ctas_per_sm > 0 ? std::min(sch.fct_ctas_per_sm, g.per_sm) : g.per_sm;
   P.fct_ctas = static_cast<int>(fct_ctas_of(g, P, di, per_sm));
-  if (p->transform == 1) {
+  if (p->transform == 2) {
+    // FCT2: ⌈n/s⌉·fjlt_rows rows of H̃X, then the slow transform on them.
+    P.fjlt_rows = p->fjlt_rows > 0
+                      ? p->fjlt_rows
+                      : static_cast<int>(std::min<double>(p->s, std::max(1.0, ceil(2.0 * d * log(static_cast<double>(d))))));
+    P.fjlt_n = P.nblocks * P.fjlt_rows;
+  }
+  if (p->transform == 1 || p->transform == 2) {
     // The slow Cauchy transform: column slices of sct_width(q) columns, blocks along the rows.
+    const int64_t rows = p->transform == 2 ? P.fjlt_n : n;
     P.fct_ws = P.fct_tile_log2 = P.fct_lean = P.fct_sorted = P.fct_cols = P.fct_staged = 0;
     P.fct_width = sct_width(P.q);
     P.fct_slices = (P.q + P.fct_width - 1) / P.fct_width;
-    P.fct_ctas = sct_ctas(n, P.r1, P.q, di.sms);
+    P.fct_ctas = sct_ctas(rows, P.r1, P.q, di.sms);
   }
   // Inputs in host memory arrive in up to kMaxChunks row chunks of at least two waves of
   // tiles each, so that phase 1 on one chunk overlaps the copy of the next.
   P.fct_chunks = 1;
-  if (host_staging) {
+  if (host_staging && p->transform != 2) {       // FCT2's blocks of s rows need one chunk
     const int64_t tiles = (g.ws || g.cols) ? (n + (int64_t{1} << g.tile_log2) - 1) >> g.tile_log2 : P.nblocks;
     P.fct_chunks = static_cast<int>(
         std::max<int64_t>(1, std::min<int64_t>(kMaxChunks, tiles / (2 * static_cast<int64_t>(P.fct_ctas)))));
@@ -393,7 +403,7 @@ bool make_plan(const l1s_params* p, int64_t n, int d, l1s_dtype dt, bool host_st
                                                 P.r1, n)
                       : static_cast<size_t>(geo[v].slices) * fct_ctas_of(geo[v], P, di, geo[v].per_sm) * P.r1 *
                             geo[v].width);
-  if (p->transform == 1)
+  if (p->transform == 1 || p->transform == 2)
     partial_floats = std::max<size_t>(partial_floats, static_cast<size_t>(P.fct_slices) * P.fct_ctas * P.r1 * P.fct_width);
 
   // Phase 2: a persistent-style grid, 8 blocks per SM by default.
@@ -452,6 +462,7 @@ bool make_plan(const l1s_params* p, int64_t n, int d, l1s_dtype dt, bool host_st
   if (p->variant == 2) P.off_cdf = take(sizeof(double) * static_cast<size_t>(n));   // running sum of λ
   // The column-sliced phase-1 kernel reads every row's draws from a per-launch table
   // (16 bytes a row, whole 1024-row tiles).
+  if (p->transform == 2) P.off_fjlt = take(sizeof(float) * static_cast<size_t>(P.fjlt_n) * P.q);   // H̃X: d columns, then G·b
   if (geo[7].ok) P.off_draws = take(16 * static_cast<size_t>((n + fct_cols_tile() - 1) / fct_cols_tile()) * fct_cols_tile());
   if (host_staging) {
     P.off_stage_a = take(esz * static_cast<size_t>(n) * d);

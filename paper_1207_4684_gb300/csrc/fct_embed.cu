@@ -1256,14 +1256,19 @@ bool launch_fct_cols_reduce(const Plan& pl, const l1s_params* p, float* pix, uns
                             double* pi2_out);
 int fct_cols_tile();
 bool launch_sct(const Plan& pl, const void* A, int64_t lda, l1s_dtype dt, const float* b, int64_t n,
-                int64_t row_offset, const l1s_params* p, bool accumulate, unsigned char* ws, cudaStream_t st);
+                int64_t row_offset, const l1s_params* p, bool accumulate, unsigned char* ws, cudaStream_t st,
+                float scale);
+bool launch_fct2(const Plan& pl, const void* A, int64_t lda, l1s_dtype dt, const float* b, int64_t n,
+                 int64_t row_offset, const l1s_params* p, bool accumulate, unsigned char* ws, cudaStream_t st);
 
 // One phase-1 launch over rows [0, n) of A and b (device) whose global ids start at
 // row_offset, writing the per-block partials at `partials`.
 static bool launch_fct_part(const Plan& pl, const void* A, int64_t lda, l1s_dtype dt, const float* b, int64_t n,
                             int64_t row_offset, const l1s_params* p, bool accumulate, unsigned char* ws,
                             cudaStream_t st) {
-  if (p->transform == 1) return launch_sct(pl, A, lda, dt, b, n, row_offset, p, accumulate, ws, st);
+  if (p->transform == 1)
+    return launch_sct(pl, A, lda, dt, b, n, row_offset, p, accumulate, ws, st, static_cast<float>(4.0 / pl.r1));
+  if (p->transform == 2) return launch_fct2(pl, A, lda, dt, b, n, row_offset, p, accumulate, ws, st);
   if (pl.fct_cols) return launch_fct_cols(pl, A, lda, dt, b, n, row_offset, p, accumulate, ws, st);
   FctArgs a;
   a.A = A;

@@ -333,10 +333,12 @@ struct Plan {
   int lm_ctas;              // the fused λ-and-mark pass: blocks and rows per block (λ residency)
   int64_t lm_chunk;
   int irls_ctas;
+  int fjlt_rows;            // FCT2: rows of G kept per block of s rows
+  int64_t fjlt_n;           // FCT2: rows of H̃X, ⌈n/s⌉·fjlt_rows
   // workspace offsets (bytes)
   size_t off_status, off_partials, off_pix, off_qr, off_r, off_m64, off_m32, off_pi2,
       off_lam, off_lamsum, off_mask, off_counts, off_idx_tmp, off_irls, off_x, off_objp,
-      off_stage_a, off_stage_b, off_cdf, off_draws, total;
+      off_stage_a, off_stage_b, off_cdf, off_draws, off_fjlt, total;
 };
 
 bool make_plan(const l1s_params* p, int64_t n, int d, l1s_dtype dt, bool host_staging, Plan* plan,

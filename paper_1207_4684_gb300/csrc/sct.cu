@@ -142,9 +142,11 @@ static bool launch_sct_t(const SctArgs& a, dim3 grid, cudaStream_t st) {
 }
 
 // One slow-transform launch over rows [0, n) of A and b whose global ids start at
-// row_offset, writing (or adding to) the per-chunk partials of the plan.
+// row_offset, writing (or adding to) the per-chunk partials of the plan, the product
+// scaled by `scale` (4/r1 for the slow transform itself).
 bool launch_sct(const Plan& pl, const void* A, int64_t lda, l1s_dtype dt, const float* b, int64_t n,
-                int64_t row_offset, const l1s_params* p, bool accumulate, unsigned char* ws, cudaStream_t st) {
+                int64_t row_offset, const l1s_params* p, bool accumulate, unsigned char* ws, cudaStream_t st,
+                float scale) {
   SctArgs a;
   a.A = A;
   a.lda = lda;
@@ -155,7 +157,7 @@ bool launch_sct(const Plan& pl, const void* A, int64_t lda, l1s_dtype dt, const 
   a.key = make_key(p->seed);
   a.problem = p->problem_id;
   a.row_offset = row_offset;
-  a.scale = static_cast<float>(4.0 / pl.r1);
+  a.scale = scale;
   a.chunk = (n + pl.fct_ctas - 1) / pl.fct_ctas;
   a.partials = reinterpret_cast<float*>(ws + pl.off_partials);
   a.accumulate = accumulate ? 1 : 0;

@@ -37,17 +37,18 @@ class Params(C.Structure):
     _fields_ = [("seed", C.c_uint64), ("problem_id", C.c_uint32), ("s", C.c_int32),
                 ("r1", C.c_int32), ("r2", C.c_int32), ("coreset_size", C.c_double),
                 ("global_row_offset", C.c_int64), ("sign_flip", C.c_int32), ("variant", C.c_int32),
-                ("sample_scale", C.c_double), ("transform", C.c_int32)]
+                ("sample_scale", C.c_double), ("transform", C.c_int32), ("fjlt_rows", C.c_int32)]
 
 
 def make_params(s: int, r1: int, r2: int, coreset: float, seed: int = 0, problem_id: int = 0,
                 global_row_offset: int = 0, sign_flip: bool = True, variant: int = 0,
-                sample_scale: float = 0.0, transform: int = 0) -> Params:
+                sample_scale: float = 0.0, transform: int = 0, fjlt_rows: int = 0) -> Params:
     """variant 0: FastCauchyRegression; variant 1: OptimizedFastCauchyRegression with
     p̂ = min(1, sample_scale·λ̂) (coreset then only bounds the expected coreset size);
-    variant 2: draws with replacement.  transform 0: FCT1; 1: the slow Cauchy transform."""
+    variant 2: draws with replacement.  transform 0: FCT1; 1: the slow Cauchy transform;
+    2: FCT2 with blocks of t = s rows, fjlt_rows of them kept (0: ⌈2·d·ln d⌉)."""
     return Params(seed, problem_id, s, r1, r2, float(coreset), global_row_offset, int(bool(sign_flip)),
-                  int(variant), float(sample_scale), int(transform))
+                  int(variant), float(sample_scale), int(transform), int(fjlt_rows))
 
 
 class Schedule(C.Structure):

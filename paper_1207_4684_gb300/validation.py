@@ -21,14 +21,16 @@ from . import l1fct as L
 
 
 def kappa_bar(A: torch.Tensor, r1: int, s: int, seed: int = 0, problem_id: int = 0, transform: int = 0,
-              stream=None) -> dict:
+              fjlt_rows: int = 0, stream=None) -> dict:
     """κ̄₁ of the ℓ1 basis of A (device, n × d FP32, d ≥ 2) conditioned by Π (FCT1 with block
-    size s, or the slow Cauchy transform when transform = 1) with r1 rows."""
+    size s, the slow Cauchy transform when transform = 1, FCT2 with blocks of t = s rows of
+    which fjlt_rows are kept when transform = 2) with r1 rows."""
     n, d = A.shape
     dev = A.device
     Ap = A[:, : d - 1]                                   # rows of A with lda = d
     bp = A[:, d - 1].contiguous()
-    prm = L.make_params(s, r1, 1, n / 2.0, seed=seed, problem_id=problem_id, transform=transform)
+    prm = L.make_params(s, r1, 1, n / 2.0, seed=seed, problem_id=problem_id, transform=transform,
+                        fjlt_rows=fjlt_rows)
     ws = L.workspace(prm, n, d - 1, device=dev)         # its leading regions also serve l1_solve
     pix = torch.empty((r1, d), dtype=torch.float32, device=dev)
     R = torch.empty((d, d), dtype=torch.float64, device=dev)

@@ -71,6 +71,44 @@ def test_kappa_bar_matches_the_oracle_on_the_same_basis(kind, transform):
     assert abs(out["kappa_bar"] - ref) <= 1e-6 * ref, (out["kappa_bar"], ref)
 
 
+@pytest.mark.parametrize("kind", ["A1", "A2"])
+def test_fct2_kappa_bar_matches_the_oracle_on_the_same_basis(kind):
+    from paper_1207_4684_gb300 import validation
+
+    n, d = 1 << 12, 4
+    A = torch.from_numpy(kappa_test_matrix(kind, n, d, seed=5)).to(DEV)
+    r1 = math.ceil(2 * d * math.log(d))
+    out = validation.kappa_bar(A, r1, 32, seed=9, transform=2, fjlt_rows=math.ceil(2 * d * math.log(d)))
+    assert (out["status"] & ~L.flag(4)) == 0, out["status"]
+    Rh = out["R"].cpu().numpy()
+    Ah = A.cpu().double().numpy()
+    Ah[:, -1] = -Ah[:, -1]
+    U = np.linalg.solve(Rh.T, Ah.T).T
+    ref = quality.kappa_bar_1(U)
+    assert abs(out["kappa_bar"] - ref) <= 1e-6 * ref, (out["kappa_bar"], ref)
+
+
+@pytest.mark.parametrize("size,n,d", [("2^18x4", 1 << 18, 4)])
+def test_fct2_kappa_bar_quartiles_against_the_paper(size, n, d):
+    """FCT2 with the experiments' settings read with FCT1's and FCT2's labels swapped (§6.1):
+    r1 = ⌈2d ln d⌉, s = ⌈2d ln d⌉ rows of G kept per block of t = 2^⌈log₂ 2d²⌉ rows: the median
+    of κ̄₁ over 9 runs within a factor 3 of the published interquartile range, far below κ̄₁(A)."""
+    from paper_1207_4684_gb300 import validation
+
+    ref = json.load(open(GOLDEN))[size]
+    r1 = math.ceil(2 * d * math.log(d))
+    sf = math.ceil(2 * d * math.log(d))
+    t = 1 << math.ceil(math.log2(2 * d * d))
+    for kind in ("A1", "A2"):
+        A = torch.from_numpy(kappa_test_matrix(kind, n, d, seed=11)).to(DEV)
+        vals = [validation.kappa_bar(A, r1, t, seed=200 + k, transform=2, fjlt_rows=sf)["kappa_bar"]
+                for k in range(9)]
+        med = float(np.median(vals))
+        q1, q3 = ref["FCT2"][kind]
+        assert q1 / 3 <= med <= 3 * q3, (kind, med, q1, q3)
+        assert med < ref["kappa_bar_A"][kind] / 100, (kind, med)
+
+
 @pytest.mark.parametrize("size,n,d", [("2^18x4", 1 << 18, 4)])
 def test_kappa_bar_quartiles_against_the_paper(size, n, d):
     """FCT1 (r1 = ⌈2d ln d⌉, s = 2^⌈log₂(2d ln d)⌉) and the slow transform on A1 and A2: the
