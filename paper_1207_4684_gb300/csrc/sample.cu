@@ -662,10 +662,19 @@ __global__ void __launch_bounds__(kSmpThreads) replacement_draw_kernel(const Dra
     else lo = mid + 1;
   }
   int64_t i = lo < a.n ? lo : a.n - 1;
-  // a row of zero mass can only be met through rounding of C: take the next row with mass
-  int64_t j = i;
-  while (j < a.n && !(a.lam[j] > 0.f)) ++j;
-  if (j < a.n) i = j;
+  // A zero-mass row can only be met when u·Σλ rounds up to Σλ (no row then has C_i above
+  // the target; a zero λ_i leaves C_i = C_{i−1} exactly): take the row at which C first
+  // reaches C_i, the last row with mass (a binary search, no walk over the zero rows).
+  if (!(a.lam[i] > 0.f)) {
+    const double ci = a.cdf[i];
+    int64_t l2 = 0, h2 = i;
+    while (l2 < h2) {
+      const int64_t mid = l2 + ((h2 - l2) >> 1);
+      if (a.cdf[mid] >= ci) h2 = mid;
+      else l2 = mid + 1;
+    }
+    i = l2;
+  }
   a.idx[t] = i;
   const float li = a.lam[i];
   if (a.w) a.w[t] = li > 0.f ? total / (static_cast<double>(a.m) * static_cast<double>(li)) : 0.0;
