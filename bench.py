@@ -524,6 +524,26 @@ def batched_variant(L, dev, stream, args, peak: float) -> dict:
         graph_ms = _time_ms(g.replay, side, args.warmup, args.steps)
     torch.cuda.synchronize()
     fl = flags.cpu().numpy()
+    # The batched form against the plain FP32 path (outside the timed region): 16 members,
+    # spread over every d, solved through the batch (x̂ and ‖Ax̂ − b‖₁ per member) and one by
+    # one through l1_regress; the relative difference of their objectives.
+    pick = sorted(range(len(members)), key=lambda i: (members[i]["w"].d, members[i]["w"].n))[::16][:16]
+    xs = [torch.empty(members[i]["w"].d, dtype=torch.float64, device=dev) for i in pick]
+    objs = [torch.empty(1, dtype=torch.float64, device=dev) for _ in pick]
+    sub = [L.make_problem(members[i]["A"], members[i]["b"], members[i]["prm"], x=xs[k], objective=objs[k])
+           for k, i in enumerate(pick)]
+    sub_ws = L.batched_workspace(sub, device=dev)
+    sub_flags = torch.zeros(len(sub), dtype=torch.int32, device=dev)
+    L.l1_regress_batched(sub, sub_ws, sub_flags, stream=side)
+    torch.cuda.synchronize()
+    errs = []
+    for k, i in enumerate(pick):
+        m = members[i]
+        ws1 = L.workspace(m["prm"], m["w"].n, m["w"].d, device=dev)
+        _, f_plain, _, rc = L.l1_regress(m["A"], m["b"], m["prm"], ws1, stream=stream)
+        errs.append(abs(float(objs[k].item()) - f_plain) / f_plain)
+        del ws1
+    del sub_ws
     rows = sum(m["w"].n for m in members)
     ab = sum(algorithmic_bytes(m["w"].n, m["w"].d, 4, int(m["cnt"].item()))["step"] for m in members)
     ds = sorted({m["w"].d for m in members})
@@ -533,6 +553,8 @@ def batched_variant(L, dev, stream, args, peak: float) -> dict:
             "step_gbs": ab / (graph_ms / 1e3) / 1e9, "step_frac": ab / (graph_ms / 1e3) / 1e9 / peak,
             "algorithmic_bytes": ab, "gpu_launches_per_step": launches,
             "status_nonzero": int((fl != 0).sum()),
+            "objective_rel_err_vs_plain": {"members": len(pick), "max": max(errs), "median": float(sorted(errs)[len(errs) // 2]),
+                                           "solve_status_nonzero": int((sub_flags != 0).sum().item())},
             "d_values": ds, "s_by_d": {str(m["w"].d): m["w"].s for m in members},
             "autotuned": {f"d{k[0]}_s{k[1]}": v for k, v in sorted(tuned.items())},
             "host_s": {"generate": gen_s, "autotune": tune_s}}

@@ -6,21 +6,20 @@
 // Sylvester matrix, S the rows sel_r = ⌊word1·t/2^32⌋ of call r, so G_{r,i} =
 // D_i·(−1)^{popcount(sel_r ∧ i)}/√s and one G serves every block.
 //
-// fjlt_kernel forms H̃X directly: output (block β, row r, column c) is the ±1 sum over the
-// block's t rows of X, the sign of row i being D_i times the parity of sel_r ∧ i.  A thread
-// block walks the blocks of X in a grid stride; it stages 64 rows of X at a time in shared
-// memory and its threads own (r, c) outputs, eight a thread per pass (more passes when
-// s·q > 2048).  The direct sum costs s sign-adds per element of X, against log2 t
-// butterfly stages for all t rows of a Hadamard transform of which only s are kept;
-// s·q ≤ 2048 keeps it one pass over X.
+// fjlt_kernel forms H̃X with a fast Walsh–Hadamard transform per block: a thread block
+// stages the block's t rows (a slice of at most W columns, W·t·4 bytes ≤ 160 KB) in shared
+// memory with D applied, runs the log2 t radix-2 stages in place (one barrier a stage; the
+// threads are (pair, column) lanes, so each stage's accesses are consecutive words), then
+// writes the s rows sel_r scaled by 1/√s.  A block costs log2 t butterflies per element
+// of X, where a direct sum over the sampled rows would cost s per element.
+#include <algorithm>
+
 #include "l1s_common.cuh"
 
 namespace l1s {
 
 constexpr uint32_t kStreamFjlt = 5;
 constexpr int kFjltThreads = 256;
-constexpr int kFjltChunk = 64;   // rows of X staged per step
-constexpr int kFjltOut = 8;      // outputs a thread accumulates per pass
 
 struct FjltArgs {
   const void* A;
@@ -28,6 +27,7 @@ struct FjltArgs {
   const float* b;
   int64_t n;
   int d, q, t, sf;
+  int width;    // columns of X per slice (blockIdx.y)
   Key2 key;
   uint32_t problem;
   int64_t nblocks;
@@ -41,66 +41,58 @@ __global__ void __launch_bounds__(kFjltThreads) fjlt_kernel(const FjltArgs a) {
   extern __shared__ __align__(16) float fj_smem[];
   uint32_t* sgn = reinterpret_cast<uint32_t*>(fj_smem);   // [t]: D_i as a sign mask
   int* sel = reinterpret_cast<int*>(sgn + a.t);            // [sf]
-  float* xs = reinterpret_cast<float*>(sel + a.sf);        // [kFjltChunk][q]
+  float* xs = reinterpret_cast<float*>(sel + a.sf);        // [t][wc], this slice's columns
   const int tid = threadIdx.x;
   for (int i = tid; i < max(a.t, a.sf); i += blockDim.x) {
     const uint4 o = philox4x32_10(make_uint4(static_cast<uint32_t>(i), 0u, a.problem, kStreamFjlt), a.key);
     if (i < a.t) sgn[i] = (o.x & 1u) ? 0x80000000u : 0u;
     if (i < a.sf) sel[i] = static_cast<int>(__umulhi(o.y, static_cast<uint32_t>(a.t)));
   }
-  __syncthreads();
-  const int q = a.q, outs = a.sf * q;
+  const int c0 = blockIdx.y * a.width;
+  const int wc = min(a.width, a.q - c0);                   // columns of this slice
+  const int lanes = kFjltThreads / wc;                     // (row or pair, column) lanes
+  const int pl = tid / wc, cc = tid - pl * wc;
+  const bool active = pl < lanes;
+  const int col = c0 + cc;
   const TA* A = static_cast<const TA*>(a.A);
   for (int64_t blk = blockIdx.x; blk < a.nblocks; blk += gridDim.x) {
     const int64_t r0 = blk * a.t;
-    for (int o0 = 0; o0 < outs; o0 += kFjltThreads * kFjltOut) {
-      float acc[kFjltOut];
-      int orow[kFjltOut], ocol[kFjltOut], osel[kFjltOut];
-#pragma unroll
-      for (int k = 0; k < kFjltOut; ++k) {
-        const int o = o0 + k * kFjltThreads + tid;
-        orow[k] = o < outs ? o / q : -1;
-        ocol[k] = o < outs ? o - (o / q) * q : 0;
-        osel[k] = o < outs ? sel[orow[k]] : 0;
-        acc[k] = 0.f;
+    __syncthreads();                                       // the previous block's rows are written out
+    if (active)
+      for (int rr = pl; rr < a.t; rr += lanes) {
+        const int64_t row = r0 + rr;
+        float v = 0.f;
+        if (row < a.n) v = col < a.d ? load_elem<TA>(A + row * a.lda + col) : -__ldg(a.b + row);
+        xs[rr * wc + cc] = __uint_as_float(__float_as_uint(v) ^ sgn[rr]);   // D·x
       }
-      for (int c0 = 0; c0 < a.t; c0 += kFjltChunk) {
-        const int rows = min(kFjltChunk, a.t - c0);
-        __syncthreads();                                   // the previous chunk is consumed
-        for (int e = tid; e < rows * q; e += blockDim.x) {
-          const int rr = e / q, cc = e - rr * q;
-          const int64_t row = r0 + c0 + rr;
-          float v = 0.f;
-          if (row < a.n) v = cc < a.d ? load_elem<TA>(A + row * a.lda + cc) : -__ldg(a.b + row);
-          xs[e] = v;
+    for (int h = 1; h < a.t; h <<= 1) {
+      __syncthreads();
+      if (active)
+        for (int p = pl; p < (a.t >> 1); p += lanes) {
+          const int i = ((p & ~(h - 1)) << 1) | (p & (h - 1));
+          float* lo = xs + i * wc + cc;
+          float* hi = lo + h * wc;
+          const float x = *lo, y = *hi;
+          *lo = x + y;
+          *hi = x - y;
         }
-        __syncthreads();
-        float part[kFjltOut];
-#pragma unroll
-        for (int k = 0; k < kFjltOut; ++k) part[k] = 0.f;
-        for (int i = 0; i < rows; ++i) {
-          const int ii = c0 + i;
-          const uint32_t di = sgn[ii];
-#pragma unroll
-          for (int k = 0; k < kFjltOut; ++k) {
-            const uint32_t par = static_cast<uint32_t>(__popc(osel[k] & ii) & 1) << 31;
-            const float x = xs[i * q + ocol[k]];
-            part[k] += __uint_as_float(__float_as_uint(x) ^ di ^ par);
-          }
-        }
-#pragma unroll
-        for (int k = 0; k < kFjltOut; ++k) acc[k] += part[k];   // a chunk's sum, then the running one
-      }
-#pragma unroll
-      for (int k = 0; k < kFjltOut; ++k) {
-        if (orow[k] < 0) continue;
-        const float y = acc[k] * a.inv_sqrt_sf;
-        const int64_t yrow = blk * a.sf + orow[k];
-        if (ocol[k] < a.d) a.Y[yrow * a.d + ocol[k]] = y;
+    }
+    __syncthreads();
+    if (active)
+      for (int r = pl; r < a.sf; r += lanes) {
+        const float y = xs[sel[r] * wc + cc] * a.inv_sqrt_sf;
+        const int64_t yrow = blk * a.sf + r;
+        if (col < a.d) a.Y[yrow * a.d + col] = y;
         else a.bY[yrow] = -y;
       }
-    }
   }
+}
+
+// Columns per slice: as many as fit 160 KB of shared memory next to the draws, and no more
+// than there are threads.
+static int fjlt_width(int t, int q) {
+  const int fit = std::max(1, static_cast<int>((160 * 1024) / (4 * static_cast<int64_t>(t))));
+  return std::min(std::min(q, fit), kFjltThreads);
 }
 
 bool launch_sct(const Plan& pl, const void* A, int64_t lda, l1s_dtype dt, const float* b, int64_t n,
@@ -126,7 +118,9 @@ bool launch_fct2(const Plan& pl, const void* A, int64_t lda, l1s_dtype dt, const
   a.inv_sqrt_sf = static_cast<float>(1.0 / sqrt(static_cast<double>(pl.fjlt_rows)));
   a.Y = reinterpret_cast<float*>(ws + pl.off_fjlt);
   a.bY = a.Y + static_cast<size_t>(pl.fjlt_n) * pl.d;
-  const size_t smem = sizeof(uint32_t) * a.t + sizeof(int) * a.sf + sizeof(float) * kFjltChunk * a.q;
+  a.width = fjlt_width(a.t, a.q);
+  const int slices = (a.q + a.width - 1) / a.width;
+  const size_t smem = sizeof(uint32_t) * a.t + sizeof(int) * a.sf + sizeof(float) * static_cast<size_t>(a.t) * a.width;
   const void* fn = dt == L1S_BF16 ? reinterpret_cast<const void*>(&fjlt_kernel<uint16_t>)
                                   : reinterpret_cast<const void*>(&fjlt_kernel<float>);
   if (!cuda_ok(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)),
@@ -134,7 +128,8 @@ bool launch_fct2(const Plan& pl, const void* A, int64_t lda, l1s_dtype dt, const
     return false;
   const int grid = static_cast<int>(std::min<int64_t>(a.nblocks, 8 * static_cast<int64_t>(device_info().sms)));
   void* args[] = {&a};
-  if (!cuda_ok(cudaLaunchKernel(fn, dim3(grid), dim3(kFjltThreads), args, smem, st), "launch fjlt")) return false;
+  if (!cuda_ok(cudaLaunchKernel(fn, dim3(grid, slices), dim3(kFjltThreads), args, smem, st), "launch fjlt"))
+    return false;
   count_launch(1);
   const int64_t ny = a.nblocks * a.sf;
   const float scale = static_cast<float>(8.0 / pl.r1 * sqrt(M_PI * pl.s / (2.0 * pl.fjlt_rows)));
