@@ -79,3 +79,45 @@ def test_two_shards_equal_unsharded(n, d, dtype, s):
     common, ia, ib = np.intersect1d(got_idx, ref_idx, return_indices=True)
     assert np.allclose(got_w[ia], ref_w[ib], rtol=1e-4, atol=0)
     assert common.size >= c_ref - 3
+
+
+@pytest.mark.parametrize("transform,t,sf", [(1, 1, 0), (2, 512, 89)])
+def test_two_shards_other_transforms(transform, t, sf):
+    """The slow transform (draws keyed by global row ids) and FCT2 (blocks of t rows cut at
+    shard boundaries, H̃X rows keyed by global block): the shards' summed Π1X matches the
+    unsharded pass's within the FP32 rounding of its terms, and their kept rows are the
+    unsharded coreset's outside the 1e-4 band."""
+    n, d, m, cap = 60011, 16, 1200.0, 3000
+    pr = problem(n, d, seed=31)
+    A, b = to_device(pr)
+    prm = L.make_params(t, r1_for(d), 16, m, seed=9, transform=transform, fjlt_rows=sf)
+    ws = L.workspace(prm, n, d)
+    pix_full = torch.empty((prm.r1, d + 1), dtype=torch.float32, device=DEV)
+    L.l1s_status_reset(ws)
+    L.fct_embed(A, b, prm, pix_full, ws)
+    idx = torch.empty(cap, dtype=torch.int64, device=DEV)
+    w = torch.empty(cap, dtype=torch.float64, device=DEV)
+    cnt = torch.zeros(1, dtype=torch.int64, device=DEV)
+    L.l1_coreset(A, b, prm, cap, idx, w, None, cnt, ws)
+    assert L.l1s_status_read(ws) == 0
+    ref_idx = idx[: int(cnt.item())].cpu().numpy()
+    passes = []
+    for r in range(2):
+        lo, hi = shard_rows(n, t if transform == 2 else 64, 2, r)
+        wsr = L.workspace(prm, hi - lo, d)
+        L.l1s_status_reset(wsr)
+        passes.append(ShardPass(A[lo:hi], b[lo:hi].contiguous(), lo, prm, cap, wsr))
+    pix = sum(sp.embed() for sp in passes)
+    scale = pix_full.abs().max().item()
+    assert torch.allclose(pix, pix_full, rtol=1e-4, atol=1e-5 * scale), float((pix - pix_full).abs().max())
+    tot = sum(sp.condition_and_lambda(pix) for sp in passes)
+    outs = [sp.sample(tot) for sp in passes]
+    for sp in passes:
+        assert L.l1s_status_read(sp.ws) == 0
+    got = np.concatenate([o[0][: int(o[3].item())].cpu().numpy() for o in outs])
+    lam = torch.cat([sp.lam for sp in passes]).cpu().numpy().astype(np.float64)
+    p = np.minimum(1.0, m / float(tot.item()) * lam)
+    u = rng.sample_uniforms(9, 0, np.arange(n))
+    diff = np.setxor1d(got, ref_idx)
+    assert np.all(np.abs(u[diff] - p[diff]) <= 1e-4 * p[diff]), diff
+    assert diff.size <= 3
