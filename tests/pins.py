@@ -412,7 +412,7 @@ def _all_checks():
                          check_scaled_probabilities, check_multiple_regression, check_with_replacement,
                          check_sct_draws, check_sct_stability, check_sct_embedding_bound, check_kappa_bar,
                          check_canonical_optimum, check_fjlt_isometry, check_fjlt_spread, check_fct2_dense,
-                         check_fct2_stability, check_fct2_embedding_bound]
+                         check_fct2_stability, check_fct2_embedding_bound, check_philox_key_schedule]
 
 
 # ----------------------------------------------------------------- slow Cauchy transform
@@ -667,3 +667,23 @@ def check_fct2_embedding_bound(seed: int = 9) -> None:
         y = X @ z
         pix, _ = fct2.fct2_embed(y[:, None], t, s, r1, seed=100 + k)
         assert np.abs(pix).sum() >= np.abs(y).sum(), f"‖Π1y‖₁ < ‖y‖₁ for y {k}"
+
+
+# ----------------------------------------------------------------- Philox4x32-10 key schedule
+def check_philox_key_schedule() -> None:
+    """Philox4x32-10 bumps its two key words by Weyl constants defined in closed form (Salmon et
+    al., SC'11): ⌊2^32/φ⌋ (φ the golden ratio) and ⌊2^32·(√3 − 1)⌋, computed here with exact
+    integer square roots; and the generator uses them: advancing the key of a call by one
+    schedule step moves every one of its later round keys, so the outputs of the same counter
+    under keys (k0, k1) and (k0 + W0, k1 + W1) differ.  (The multipliers have no closed form;
+    they stay pinned by the output laws of check_draw_statistics.)"""
+    from math import isqrt
+
+    w0 = isqrt(5 << 62) - (1 << 31)        # 2^32/φ = 2^31·(√5 − 1)
+    w1 = isqrt(3 << 64) - (1 << 32)        # 2^32·(√3 − 1)
+    assert int(rng.PHILOX_W0) == w0, ("Weyl constant 0", hex(int(rng.PHILOX_W0)), hex(w0))
+    assert int(rng.PHILOX_W1) == w1, ("Weyl constant 1", hex(int(rng.PHILOX_W1)), hex(w1))
+    c = np.arange(64, dtype=np.uint64)
+    a = np.stack(rng.philox4x32_10(c, 7, 9, 11, 12345, 678))
+    b = np.stack(rng.philox4x32_10(c, 7, 9, 11, (12345 + w0) & 0xFFFFFFFF, (678 + w1) & 0xFFFFFFFF))
+    assert (a != b).any(axis=0).all()

@@ -256,6 +256,7 @@ MUTATIONS = [
      pins.check_with_replacement),
     ("with-replacement target u, not u·Σλ", sampling, "sample_with_replacement", replace_unscaled_target,
      pins.check_with_replacement),
+    ("Philox Weyl constant off by one", rng, "PHILOX_W0", np.uint64(0x9E3779B8), pins.check_philox_key_schedule),
     ("FJLT signs dropped", rng, "fjlt_draws", fjlt_no_signs, pins.check_fjlt_spread),
     ("FJLT one sampled row repeated", rng, "fjlt_draws", fjlt_one_row, pins.check_fjlt_isometry),
     ("FCT2 scale without √(πt/2s)", fct2, "fct2_scale", fct2_scale_no_sqrt, pins.check_fct2_stability),
