@@ -135,7 +135,10 @@ L1S_API int l1s_status_read(const void* ws, size_t ws_bytes, void* stream, uint3
 
 /* Phase 1 — the FCT1 embedding (§3.1; Figure 2, steps 1-2), or with
  * params.transform = 1 the slow Cauchy transform Π1·X = (4/r1)·C·X (§3), whose
- * r1·n variates are drawn inside the kernel (its cost is the drawing, not the bytes):
+ * r1·n variates are drawn inside the kernel (its cost is the drawing, not the bytes),
+ * or with params.transform = 2 FCT2 (§3.2): a subsampled randomized Hadamard block per
+ * s rows (fjlt_rows of them kept, H̃X kept in the workspace) followed by the slow
+ * transform on the rows of H̃X, scaled by (8/r1)·√(πs/(2·fjlt_rows)).  FCT1:
  *   PiX_dev = Π1·X = 4·B·C·H̃·D·[A, −b]          (r1 × q, FP32, row-major)
  * H̃ is block diagonal with blocks [H_s; I_s] (H_s the Sylvester Hadamard
  * matrix scaled by 1/√s), C a diagonal of standard Cauchys, B a hash of each
