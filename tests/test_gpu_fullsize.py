@@ -12,6 +12,11 @@ holds at any size (the sum of the two halves' embeddings, drawn with their globa
 ids, equals the embedding of all rows) and, entry by entry, against the oracle on the
 first 2^20 rows in the same launch geometry; λ on sampled rows against the oracle with
 the BF16-rounded M, the keep decision of every row, and the objective over all rows.
+
+spiky_n64M_d64 (n = 2^26, d = 64, FP32, the headline workload): the same property checks
+of Π1X (halves, and every entry on a 2^20-row prefix), R and M against the oracle's QR
+of the GPU's Π1X, λ on sampled rows, the keep decision of every row, and the objective of
+the one-call pass over all rows.
 """
 import math
 
@@ -47,8 +52,9 @@ def _phases(A, b, prm, ws, q, r1, r2):
     return pix, R, M
 
 
-def _check_sampling(A, b, M, prm, X, w, ws, n, sample_rows, tc=False):
-    """λ on sampled rows against the oracle; the keep decision of every row from the GPU's λ."""
+def _check_sampling(A, b, M, prm, x_rows, w, ws, n, sample_rows, tc=False):
+    """λ on sampled rows against the oracle; the keep decision of every row from the GPU's λ.
+    x_rows(rows) gives the FP64 rows [A_i, −b_i] of X for sorted row ids."""
     cap = int(2 * w.coreset) + 64
     idx = torch.empty(cap, dtype=torch.int64, device=DEV)
     wts = torch.empty(cap, dtype=torch.float64, device=DEV)
@@ -61,8 +67,9 @@ def _check_sampling(A, b, M, prm, X, w, ws, n, sample_rows, tc=False):
     Mh = M.cpu().numpy()
     Mm = leverage.mixed_precision_m(Mh) if tc else Mh
     rows = np.sort(np.random.default_rng(0).choice(n, sample_rows, replace=False))
-    ref = leverage.lambda_estimates(X[rows], Mm)
-    tol = lambda_tol_tc(X[rows], Mm) if tc else lambda_tol(X[rows], Mm)
+    Xr = x_rows(rows)
+    ref = leverage.lambda_estimates(Xr, Mm)
+    tol = lambda_tol_tc(Xr, Mm) if tc else lambda_tol(Xr, Mm)
     assert np.all(np.abs(lam_g[rows] - ref) <= tol), float((np.abs(lam_g[rows] - ref) / tol).max())
     p, _, _ = sampling.probabilities(lam_g, w.coreset, fsum(lam_g))
     u = rng.sample_uniforms(w.seed, w.problem_id, np.arange(n))
@@ -93,7 +100,7 @@ def test_colscale_n4M_d16_full_size():
     m_ref = condition.m_matrix(r_ref, rng.pi2_matrix(w.seed, w.problem_id, q, w.r2))
     assert np.allclose(R.cpu().numpy(), r_ref, rtol=0, atol=1e-11 * np.abs(r_ref).max())
     assert np.allclose(M.cpu().numpy(), m_ref, rtol=0, atol=1e-14 * np.linalg.cond(r_ref) * np.abs(m_ref).max())
-    p, u = _check_sampling(A, b, M, prm, X, w, ws, n, 20000)
+    p, u = _check_sampling(A, b, M, prm, lambda r: X[r], w, ws, n, 20000)
     # the one-call pass (its own Π1X: FP32 sums in another order) against those decisions
     cap = int(2 * w.coreset) + 64
     idx = torch.empty(cap, dtype=torch.int64, device=DEV)
@@ -158,9 +165,60 @@ def test_t2rows_n16M_d32_bf16_full_size():
     got_pre, flags = gpu_pix(A[:pre], b[:pre], prm)
     assert flags == 0
     check_pix(got_pre, X[:pre], prm, PIX_REL)
-    _check_sampling(A, b, M, prm, X, w, ws, n, 20000, tc=True)
+    _check_sampling(A, b, M, prm, lambda r: X[r], w, ws, n, 20000, tc=True)
     x, f, rows, rc = L.l1_regress(A, b, prm, ws)
     assert rc == 0, rc
     f_ref = solve.objective(X[:, :-1], -X[:, -1], x.numpy())
+    assert abs(f - f_ref) <= 1e-12 * f_ref
+    assert math.isfinite(f) and 0 < rows < 2 * w.coreset + 64
+
+
+def test_spiky_n64M_d64_full_size():
+    """The measured headline workload: Π1X by halves additivity and, entry by entry, on a
+    2^20-row prefix; R and M against the oracle's QR of the GPU's Π1X; λ on sampled rows;
+    every keep decision; the one-call pass's objective over all rows.  X is never formed
+    whole in FP64 (35 GB): rows are widened where they are needed."""
+    w = WORKLOADS["spiky_n64M_d64"]
+    pr = make_problem(w)
+    A, b = to_device(pr)
+    n, d = pr["A"].shape
+    q = d + 1
+
+    def x_rows(rows):
+        return np.concatenate([pr["A"][rows].astype(np.float64), -pr["b"][rows].astype(np.float64)[:, None]],
+                              axis=1)
+
+    prm = L.make_params(w.s, w.r1, w.r2, w.coreset, seed=w.seed, problem_id=w.problem_id)
+    ws = L.workspace(prm, n, d)
+    pix, R, M = _phases(A, b, prm, ws, q, w.r1, w.r2)
+    half = n // 2                                                   # a multiple of s
+    parts = []
+    for lo, hi in ((0, half), (half, n)):
+        prm_h = L.make_params(w.s, w.r1, w.r2, w.coreset, seed=w.seed, problem_id=w.problem_id,
+                              global_row_offset=lo)
+        ws_h = L.workspace(prm_h, hi - lo, d)
+        pp, _, _ = _phases(A[lo:hi], b[lo:hi], prm_h, ws_h, q, w.r1, w.r2)
+        parts.append(pp.double())
+        del ws_h
+    tot = (parts[0] + parts[1]).cpu().numpy()
+    whole = pix.double().cpu().numpy()
+    col = np.abs(whole).max(axis=0, keepdims=True)
+    err = np.abs(tot - whole) / col
+    assert np.all(err <= 2e-5), float(err.max())
+    pre = 1 << 20
+    got_pre, flags = gpu_pix(A[:pre], b[:pre], prm)
+    assert flags == 0
+    check_pix(got_pre, x_rows(np.arange(pre)), prm, PIX_REL)
+    _, r_ref = condition.qr_positive(whole)
+    m_ref = condition.m_matrix(r_ref, rng.pi2_matrix(w.seed, w.problem_id, q, w.r2))
+    assert np.allclose(R.cpu().numpy(), r_ref, rtol=0, atol=1e-11 * np.abs(r_ref).max())
+    assert np.allclose(M.cpu().numpy(), m_ref, rtol=0, atol=1e-14 * np.linalg.cond(r_ref) * np.abs(m_ref).max())
+    _check_sampling(A, b, M, prm, x_rows, w, ws, n, 20000)
+    x, f, rows, rc = L.l1_regress(A, b, prm, ws)
+    assert rc == 0, rc
+    xh = x.numpy()
+    step = 1 << 22
+    f_ref = math.fsum(solve.objective(pr["A"][lo:lo + step].astype(np.float64),
+                                      pr["b"][lo:lo + step].astype(np.float64), xh) for lo in range(0, n, step))
     assert abs(f - f_ref) <= 1e-12 * f_ref
     assert math.isfinite(f) and 0 < rows < 2 * w.coreset + 64
