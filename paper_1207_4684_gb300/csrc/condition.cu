@@ -162,22 +162,24 @@ __global__ void __launch_bounds__(kCondThreads) condition_kernel(const CondArgs 
 
 // ----------------------------------------------------------------- CholeskyQR2
 // R is also the Cholesky factor of the Gram matrix (Π1X)ᵀ(Π1X), and applying the
-// Cholesky step twice (R1 from the Gram of Π1X, R2 from the Gram of Π1X·R1⁻¹,
+// Cholesky step twice (R1 from the Gram of Π1X, R2 from the Gram of Y = Π1X·R1⁻¹,
 // R = R2·R1) gives a QR factor accurate to FP64 rounding whenever the condition
 // number is below about 1e7 — far past what an FP32-accumulated Π1X resolves (the
-// rank test flags columns dependent to 1e-5).  The Gram products spread over thread
-// blocks; the last block to finish (an atomic ticket, no waiting) sums the partials in
-// a fixed order and factors the q×q matrix.  Two launches: pass 0 (Gram of Π1X → R1),
-// pass 1 (rows of Π1X·R1⁻¹ by forward substitution, their Gram → R2, then R = R2·R1
-// and M = R⁻¹Π2).  Π2 is drawn by the phase-1 reduction when the whole pass runs.
+// rank test flags columns dependent to 1e-5).  Each Cholesky factorisation also yields
+// the inverse of its factor (the elimination's row operations applied to the identity),
+// so that everything else is a matrix product: the rows of Y = Π1X·R1⁻¹, and
+// M = R⁻¹Π2 = R1⁻¹·(R2⁻¹·Π2).  The Gram products spread over thread blocks; the last
+// block to finish (an atomic ticket, no waiting) sums the partials in a fixed order and
+// factors the q×q matrix.  Two launches: pass 0 (Gram of Π1X → R1 and R1⁻¹), pass 1
+// (rows of Y, their Gram → R2 and R2⁻¹, then M, and R = R2·R1 when the caller asks for
+// it).  Π2 is drawn by the phase-1 reduction when the whole pass runs.
 //
-// FP64 arithmetic on this part is slow (a dependent FMA takes ~64 cycles, a division
-// ~430, a square root ~670, and a full-warp FP64 instruction holds its sub-partition
-// for ~80 cycles), so the serial parts avoid divisions and square roots — reciprocals
-// and reciprocal square roots come from FP32 estimates refined by Newton steps in
-// FP64, and every division by a diagonal entry is a multiplication by its stored
-// reciprocal — and run right-looking (each step finishes one row or column and updates
-// the rest in parallel), so the dependent chain per step is a few operations long.
+// FP64 arithmetic on this part is slow (a dependent FMA takes ~64 cycles, and a full-warp
+// FP64 instruction holds its sub-partition for ~64-80 cycles however few of its lanes
+// are active), so the factorisation keeps one short chain per step — a reciprocal from the
+// hardware's FP64 approximation refined by Newton steps, no division or square root — and
+// packs each step's independent updates densely over all threads; the products and the
+// sums of the partials are independent dot products.
 constexpr int kGramThreads = 256;
 // Blocks per first-level group of the partial sums: one group (a single level) for
 // q ≤ 32, groups of 8 for wider X, whose partials are long.
@@ -192,9 +194,11 @@ struct Cond2Args {
   double* partials;      // [gridDim.x][q(q+1)/2], then the group sums
   unsigned int* ticket;  // group tickets [groups], then the final ticket (zero before each pass)
   double* R1;            // q × q (pass 0 → pass 1)
-  double* R1dinv;        // q: 1 / (R1)_kk
+  double* Z1;            // q × q: R1⁻¹ (pass 0 → pass 1)
+  double* R2;            // q × q (pass 1 → cond_m_kernel)
+  double* Z2;            // q × q: R2⁻¹ (pass 1 → cond_m_kernel)
   double* colnorm;       // q: ‖(Π1X)_:k‖₂
-  double* R;             // q × q row-major (output)
+  double* R;             // q × q row-major (output, when the caller asks for R)
   double* M64;           // q × r2
   float* M32;
   double* pi2;
@@ -205,10 +209,6 @@ struct Cond2Args {
   int pi2_ready;         // 1: Π2 is already in pi2 (drawn by the phase-1 reduction)
   int pi2_gauss;         // 1: Gaussian Π2 (OptimizedFastCauchyRegression)
 };
-
-// On this part every FP64 warp instruction occupies its SM sub-partition for tens of
-// cycles, so the serial steps below keep their FP64 chains short and spread the
-// independent work over all warps of the block.
 
 // 1/x and 1/√x for x > 0 in FP64: an FP32 estimate of the mantissa part (the exponent is
 // split off first, so any normal FP64 x works), then Newton steps in FP64 — for 1/x
@@ -235,100 +235,167 @@ __device__ __forceinline__ double rsqrt_f64(double x, int steps) {
   return y;
 }
 
-// Cholesky of the symmetric q×q matrix G (row-major, upper triangle, shared memory) by
-// all threads of the block, in the square-root-free form G = LᵀDL first: step k
-// subtracts G_ki·G_kj/d_k from the trailing triangle (warps 1 and up, a row per warp)
-// while thread 0 forms the next pivot — the same FMA the update would apply to
-// G_{k+1,k+1} — and its reciprocal, so the serial chain per step is one reciprocal.  Then R_kj = G_kj/√d_k for all
-// entries at once, and dinv[k] = 1/R_kk.  s_r holds q doubles.  Returns false when a
-// pivot is not positive.
-// chain_steps Newton steps refine the pivots' reciprocals on the serial chain (0 leaves
-// them FP32-accurate, which only perturbs G by about 1e-7 relative: enough for a
-// preconditioner); the final 1/√d_k always take two.
-// Threads [0, nt) take part (nt a multiple of 32: 128 for q ≤ 32, where four warps are
-// enough and a named barrier is cheaper, else the whole block).
+// 1/x for a positive normal FP64 x on the serial chain of the factorisation: the
+// hardware's approximate FP64 reciprocal (PTX rcp.approx.ftz.f64, far better than the
+// 2^-14 that two steps need) refined by two Newton steps y ← y + y·(1 − x·y), each of
+// which squares the relative error, to FP64 rounding.
+__device__ __forceinline__ double rcp_approx_f64(double x) {
+  double y;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+  return y;
+}
+
+__device__ __forceinline__ double rcp_newton_f64(double x) {
+  double y = rcp_approx_f64(x);
+  y = fma(y, fma(-x, y, 1.0), y);
+  return fma(y, fma(-x, y, 1.0), y);
+}
+
+// The pivot reciprocals of the two factorisations.  Pass 0 only preconditions: any r_k
+// close to 1/d_k serves, because R1 and R1⁻¹ are both formed from the same r_k (they stay
+// exact inverses of each other) and pass 1 corrects the rest — the hardware approximation
+// alone.  Pass 1 factors the Gram matrix of Y = Π1X·R1⁻¹, close to the identity, so its
+// pivots lie near 1: with e = 1 − d (exact for d in [1/2, 2]), 1/d = 1 + e + e² + e³/(1−e),
+// and 1 + (e + e²) is correctly rounded up to e³ < 2^-54 when |e| < 2^-18; any other pivot
+// takes the two Newton steps.
+template <int PASS>
+__device__ __forceinline__ double pivot_rcp(double d) {
+  if (PASS == 0) return rcp_approx_f64(d);
+  const double e = 1.0 - d;
+  if (fabs(e) < 0x1p-18) return 1.0 + fma(e, e, e);
+  return rcp_newton_f64(d);
+}
+
+// Threads [0, nt) take part in the factorisation (nt a multiple of 32: 128 for q ≤ 32,
+// where four warps are enough and a named barrier is cheaper, else the whole block).
 __device__ __forceinline__ void sync_first(int nt) {
   if (nt == static_cast<int>(blockDim.x)) __syncthreads();
   else named_barrier(1, nt);
 }
 
-__device__ bool block_cholesky(double* G, double* R, double* dinv, double* s_r, int q, int chain_steps, int nt) {
-  const int t = threadIdx.x, lane = t & 31, warp = t >> 5, nw = nt >> 5;
-  const int steps = chain_steps;
+// The entries (i, j), 1 ≤ i ≤ j < q, of an upper triangle, the rows nearest the bottom
+// first: entry e lies in row i = q − 1 − w with w the largest integer of w(w+1)/2 ≤ e, so
+// that the entries below row k form the prefix of length (q−1−k)(q−k)/2.  Packed i·2^16 + j.
+__device__ void fill_tri(uint32_t* tri, int q) {
+  for (int e = threadIdx.x; e < q * (q - 1) / 2; e += blockDim.x) {
+    int w = static_cast<int>((sqrtf(8.0f * static_cast<float>(e) + 1.0f) - 1.0f) * 0.5f);
+    while ((w + 1) * (w + 2) / 2 <= e) ++w;
+    while (w * (w + 1) / 2 > e) --w;
+    const int i = q - 1 - w;
+    tri[e] = (static_cast<uint32_t>(i) << 16) | static_cast<uint32_t>(i + e - w * (w + 1) / 2);
+  }
+}
+
+// Cholesky factor R of the symmetric positive definite q×q matrix G and its inverse Z,
+// right-looking in the square-root-free form G = L·D·Lᵀ (L unit lower triangular) by the
+// threads [0, nt).  Step k uses pivot d_k, its reciprocal r_k (pivot_rcp) and the multipliers
+// u_i = l_ik = G_ki·r_k (i > k): the trailing upper triangle loses u_i·G_kj (k < i ≤ j), and
+// the same row operations, applied to E (the identity at the start), leave E = L⁻¹ — its
+// rows i > k lose u_i times row k.  Warp 0 updates row k+1, the next pivot among it, and
+// from them forms r_{k+1} and the next step's multipliers (every lane the same values, so
+// no exchange); the other warps update the rows below and E, flat over their threads (the
+// triangle through the table of fill_tri).  One barrier per step; the serial chain per
+// step is the pivot update, one reciprocal and one product.  Then R = D^½·Lᵀ (R_kk = √d_k,
+// R_kj = √d_k·u_j of step k) overwrites the upper triangle of G, and Z = R⁻¹ = Eᵀ·D^-½ the
+// upper triangle of E (the strictly lower parts of both become zero).  G and E are
+// row-major q×q in shared memory; s_u holds 2q doubles (the multipliers of two steps), s_r,
+// s_t and s_s q each (r_k, 1/√d_k, √d_k).  Returns false when a pivot is not positive.
+template <int PASS>
+__device__ bool block_chol_inv(double* G, double* E, const uint32_t* tri, double* s_u, double* s_r,
+                               double* s_t, double* s_s, int q, int nt) {
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   bool ok = true;
-  if (t == 0) {
+  if (warp == 0) {
     const double a = G[0];
-    s_r[0] = rcp_f64(fmax(a, 1e-300), steps);
+    const double r = pivot_rcp<PASS>(fmax(a, 1e-300));
+    if (lane == 0) s_r[0] = r;
     if (!(a > 0.0) || !isfinite(a)) ok = false;
+    for (int j = 1 + lane; j < q; j += 32) s_u[j] = G[j] * r;
   }
   sync_first(nt);
   for (int k = 0; k + 1 < q; ++k) {
-    const double r = s_r[k];
-    if (t == 0) {
-      const double g = G[k * q + k + 1];
-      const double an = fma(-(g * r), g, G[(k + 1) * q + k + 1]);
-      G[(k + 1) * q + k + 1] = an;   // the one trailing entry the other warps leave to thread 0
-      s_r[k + 1] = rcp_f64(fmax(an, 1e-300), steps);
-      if (!(an > 0.0) || !isfinite(an)) ok = false;
-    } else if (warp > 0) {
-      const int w = q - k - 1;
-      if (q <= 32) {
-        // small trailing block: its w×w entries spread flat over warps 1 and up
-        for (int e = t - 32; e < w * w; e += nt - 32) {
-          const int i = k + 1 + e / w, j = k + 1 + e % w;
-          if (j >= i && (j != k + 1 || i != k + 1))
-            G[i * q + j] = fma(-(G[k * q + i] * r), G[k * q + j], G[i * q + j]);
+    const double* u = s_u + (k & 1) * q;            // multipliers of step k
+    const double* gk = G + k * q;
+    if (warp == 0) {
+      double* un = s_u + ((k + 1) & 1) * q;         // those of step k + 1
+      double* g1 = G + (k + 1) * q;
+      const double uk1 = u[k + 1];
+      const double d1 = fma(-uk1, gk[k + 1], g1[k + 1]);
+      const double r1 = pivot_rcp<PASS>(fmax(d1, 1e-300));
+      if (lane == 0) {
+        g1[k + 1] = d1;
+        s_r[k + 1] = r1;
+      }
+      if (!(d1 > 0.0) || !isfinite(d1)) ok = false;
+      for (int j = k + 2 + lane; j < q; j += 32) {
+        const double v = fma(-uk1, gk[j], g1[j]);
+        g1[j] = v;
+        un[j] = v * r1;
+      }
+    } else {
+      // Four entries per thread at a time, all loads before the stores (the entries of a step
+      // are distinct and none is read by another), so that their shared-memory and FP64
+      // latencies overlap.  E's new column k is −u_i = fma(−u_i, 1, 0).
+      const int w = q - 1 - k;
+      const int ntri = (w - 1) * w / 2;              // trailing entries below row k+1
+      const int total = ntri + w * (k + 1);          // and the entries (i, c) of E, k < i, c ≤ k
+      const int step = nt - 32;
+      for (int e0 = t - 32; e0 < total; e0 += 4 * step) {
+        double* dst[4];
+        double ua[4], bb[4], cc[4];
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+          const int e = e0 + m * step;
+          dst[m] = nullptr;
+          ua[m] = 0.0;
+          bb[m] = 0.0;
+          cc[m] = 0.0;
+          if (e < ntri) {
+            const uint32_t ij = tri[e];
+            const int i = static_cast<int>(ij >> 16), j = static_cast<int>(ij & 0xFFFFu);
+            dst[m] = G + i * q + j;
+            ua[m] = u[i];
+            bb[m] = gk[j];
+            cc[m] = *dst[m];
+          } else if (e < total) {
+            const int f = e - ntri;
+            const int di = f / (k + 1);
+            const int i = k + 1 + di, c = f - di * (k + 1);
+            dst[m] = E + i * q + c;
+            ua[m] = u[i];
+            bb[m] = c == k ? 1.0 : E[k * q + c];
+            cc[m] = c == k ? 0.0 : *dst[m];
+          }
         }
-      } else {
-        // rows i = k+1.. of the trailing upper triangle, one row per warp, lanes over j ≥ i
-        for (int i = k + warp; i < q; i += nw - 1) {
-          const double gki = G[k * q + i] * r;
-          for (int j = i + lane; j < q; j += 32)
-            if (j != k + 1 || i != k + 1) G[i * q + j] = fma(-gki, G[k * q + j], G[i * q + j]);
-        }
+#pragma unroll
+        for (int m = 0; m < 4; ++m)
+          if (dst[m]) *dst[m] = fma(-ua[m], bb[m], cc[m]);
       }
     }
     sync_first(nt);
   }
-  // R_kj = G_kj/√d_k (d_k = G_kk after its step), zero below the diagonal
-  for (int k = t; k < q; k += nt) dinv[k] = rsqrt_f64(fmax(G[k * q + k], 1e-300), 2);
+  for (int k = t; k < q; k += nt) {
+    const double d = fmax(G[k * q + k], 1e-300);
+    const double tk = rsqrt_f64(d, 2);
+    s_t[k] = tk;
+    s_s[k] = d * tk;
+  }
   sync_first(nt);
+  // R in place (each entry reads only itself); Z's upper part from E's strictly lower part
   for (int e = t; e < q * q; e += nt) {
     const int i = e / q, j = e - i * q;
-    R[e] = j < i ? 0.0 : G[e] * dinv[i];
+    if (j < i) {
+      G[e] = 0.0;
+    } else {
+      G[e] = j == i ? s_s[i] : s_s[i] * (G[e] * s_r[i]);
+      E[e] = j == i ? s_t[i] : E[j * q + i] * s_t[j];
+    }
   }
   sync_first(nt);
+  for (int e = t; e < q * q; e += nt)
+    if (e % q < e / q) E[e] = 0.0;
+  sync_first(nt);
   return ok;
-}
-
-// Right-looking back substitution in place, all threads of the block: on entry M holds
-// B (q × r2), on return R⁻¹·B for the upper-triangular R (row-major q × q) with dinv[k] =
-// 1/R_kk: step k finishes row k, then every row above subtracts R_jk·M_k·.
-__device__ void block_back_subst(const double* R, const double* dinv, double* M, int q, int r2, int nt) {
-  const int t = threadIdx.x;
-  for (int k = q - 1; k >= 0; --k) {
-    for (int c = t; c < r2; c += nt) M[k * r2 + c] *= dinv[k];
-    sync_first(nt);
-    for (int e = t; e < k * r2; e += nt) {
-      const int j = e / r2, c = e - j * r2;
-      M[e] = fma(-R[j * q + k], M[k * r2 + c], M[e]);
-    }
-    sync_first(nt);
-  }
-}
-
-// Σ_{i<count} a[i·stride] with four independent accumulators, combined in a fixed order.
-__device__ __forceinline__ double sum4(const double* a, int count, size_t stride) {
-  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-  int i = 0;
-  for (; i + 3 < count; i += 4) {
-    s0 += a[static_cast<size_t>(i) * stride];
-    s1 += a[static_cast<size_t>(i + 1) * stride];
-    s2 += a[static_cast<size_t>(i + 2) * stride];
-    s3 += a[static_cast<size_t>(i + 3) * stride];
-  }
-  for (; i < count; ++i) s0 += a[static_cast<size_t>(i) * stride];
-  return (s0 + s1) + (s2 + s3);
 }
 
 __device__ __forceinline__ void pair_index(int e, int q, int& j, int& l) {
@@ -341,20 +408,66 @@ __device__ __forceinline__ void pair_index(int e, int q, int& j, int& l) {
   l = row + left;
 }
 
-// Shared memory of a cond2 block (doubles): rows | R1 | dinv | dn | Rc | inv | R | Π2 | M.
+// out(e, Σ_{p<count} src[p·stride + e]) for every e < ne, over the whole block: a thread
+// takes RUN entries at a time and loads CHUNK partials of each before it adds them, so that
+// their L2 round trips overlap, into four accumulators (p mod 4) combined at the end — the
+// same order whatever the schedule.  The partials come from other blocks of the launch, so
+// they are read at L2.
+template <int RUN, int CHUNK, class Out>
+__device__ __forceinline__ void sum_partials_t(const double* src, int count, size_t stride, int ne, Out out) {
+  static_assert(CHUNK % 4 == 0, "chunks of whole accumulator rounds");
+  const int nb = static_cast<int>(blockDim.x);
+  for (int e0 = threadIdx.x; e0 < ne; e0 += RUN * nb) {
+    double acc[RUN][4];
+#pragma unroll
+    for (int m = 0; m < RUN; ++m)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc[m][c] = 0.0;
+    for (int p0 = 0; p0 < count; p0 += CHUNK) {
+      double v[RUN][CHUNK];
+#pragma unroll
+      for (int m = 0; m < RUN; ++m)
+#pragma unroll
+        for (int c = 0; c < CHUNK; ++c) {
+          const int e = e0 + m * nb, p = p0 + c;
+          v[m][c] = (e < ne && p < count) ? __ldcg(src + static_cast<size_t>(p) * stride + e) : 0.0;
+        }
+#pragma unroll
+      for (int m = 0; m < RUN; ++m)
+#pragma unroll
+        for (int c = 0; c < CHUNK; ++c) acc[m][c & 3] += v[m][c];
+    }
+#pragma unroll
+    for (int m = 0; m < RUN; ++m) {
+      const int e = e0 + m * nb;
+      if (e < ne) out(e, (acc[m][0] + acc[m][1]) + (acc[m][2] + acc[m][3]));
+    }
+  }
+}
+
+template <class Out>
+__device__ __forceinline__ void sum_partials(const double* src, int count, size_t stride, int ne, Out out) {
+  if (ne <= static_cast<int>(blockDim.x)) sum_partials_t<1, 32>(src, count, stride, ne, out);
+  else sum_partials_t<4, 8>(src, count, stride, ne, out);
+}
+
+// Shared memory of a cond2 block (doubles): the rows of Π1X, later the Gram matrix and R in
+// place | the rows of Y (pass 1), later E and the inverse factor in place | R1⁻¹ (pass 1) |
+// the triangle table (uint32) | the multipliers of two steps | r_k | 1/√d_k | √d_k | diag R1.
 struct Cond2Smem {
-  int rows, r1q, dinv, dn, Rc, inv, R, P, M, total;
-  __host__ __device__ Cond2Smem(int rpb, int q, int r2) {
-    rows = 0;
-    r1q = rows + (rpb > q ? rpb : q) * q;
-    dinv = r1q + q * q;
-    dn = dinv + q;
-    Rc = dn + q;
-    inv = Rc + q * q;
-    R = inv + 2 * q;
-    P = R + q * q;
-    M = P + q * r2;
-    total = M + q * r2;
+  int G, EZ, Z1, tri, su, sr, st, ss, r1d, total;
+  __host__ __device__ Cond2Smem(int rpb, int q) {
+    const int big = (rpb > q ? rpb : q) * q;
+    G = 0;
+    EZ = G + big;
+    Z1 = EZ + big;
+    tri = Z1 + q * q;
+    su = tri + (q * (q - 1) / 2 + 1) / 2;
+    sr = su + 2 * q;
+    st = sr + q;
+    ss = st + q;
+    r1d = ss + q;
+    total = r1d + q;
   }
 };
 
@@ -363,114 +476,47 @@ __global__ void __launch_bounds__(kGramThreads) cond2_kernel(const Cond2Args a) 
   extern __shared__ __align__(16) double sm2[];
   __shared__ int s_last;
   __shared__ int s_ok;
-  const int q = a.q, tid = threadIdx.x, lane = tid & 31;
+  const int q = a.q, tid = threadIdx.x;
   const int ne = q * (q + 1) / 2;
   const int r_lo = blockIdx.x * a.rows_per_block;
   const int r_hi = min(a.r1, r_lo + a.rows_per_block);
   const int nrows = r_hi - r_lo;
-  const Cond2Smem L(a.rows_per_block, q, a.r2);
-  double* rows = sm2 + L.rows;                // this block's rows, later the Gram
-  double* R1s = sm2 + L.r1q;                  // pass 1: R1
-  double* dinv = sm2 + L.dinv;                // pass 1: 1/(R1)_kk
-  double* dn = sm2 + L.dn;                    // reciprocals of this pass's factor
+  const Cond2Smem L(a.rows_per_block, q);
+  double* rows = sm2 + L.G;                   // this block's rows of Π1X, later the Gram
+  double* EZ = sm2 + L.EZ;                    // pass 1: the rows of Y; the tail: E, Z
+  double* Z1s = sm2 + L.Z1;
+  double* r1d = sm2 + L.r1d;
   if (PASS == 0) {
     // Π2, unless the phase-1 reduction drew it, spread over all blocks.
     if (!a.pi2_ready)
       for (int e = blockIdx.x * blockDim.x + tid; e < q * a.r2; e += gridDim.x * blockDim.x)
         a.pi2[e] = pi2_value(a.key, a.problem, e, a.pi2_gauss);
   } else {
-    for (int e = tid; e < q * q; e += blockDim.x) R1s[e] = a.R1[e];
-    for (int e = tid; e < q; e += blockDim.x) dinv[e] = a.R1dinv[e];
+    for (int e = tid; e < q * q; e += blockDim.x) Z1s[e] = a.Z1[e];
+    for (int e = tid; e < q; e += blockDim.x) r1d[e] = a.R1[e * q + e];
   }
   for (int e = tid; e < nrows * q; e += blockDim.x)
     rows[e] = static_cast<double>(a.pix[static_cast<size_t>(r_lo) * q + e]);
   __syncthreads();
+  const double* src = rows;
   if (PASS == 1) {
-    // y·R1 = x by forward substitution, right-looking: lane c of a warp holds the running
-    // value of column c of up to three rows; at step k the lane holding column k
-    // finishes y_k (a shuffle broadcasts it) and every later column subtracts y_k·R1_kc.
-    // The three rows of a warp are independent chains that overlap.  (q > 64: one row per
-    // thread.)
-    if (q <= 32) {
-      const int lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-      for (int i0 = warp; i0 < nrows; i0 += 3 * nw) {
-        double acc[3];
-        bool live[3];
-#pragma unroll
-        for (int u = 0; u < 3; ++u) {
-          const int i = i0 + u * nw;
-          live[u] = i < nrows;
-          acc[u] = (live[u] && lane < q) ? rows[i * q + lane] : 0.0;
-        }
-        for (int k = 0; k < q; ++k) {
-          const double rk = lane < q ? R1s[k * q + lane] : 0.0;
-          const double dk = dinv[k];
-#pragma unroll
-          for (int u = 0; u < 3; ++u) {
-            const double yk = __shfl_sync(0xffffffffu, acc[u], k) * dk;
-            if (lane == k) acc[u] = yk;
-            else if (lane > k) acc[u] = fma(-yk, rk, acc[u]);
-          }
-        }
-#pragma unroll
-        for (int u = 0; u < 3; ++u)
-          if (live[u] && lane < q) rows[(i0 + u * nw) * q + lane] = acc[u];
+    // Y = X·R1⁻¹ with R1⁻¹ upper triangular: Y_ic = Σ_{k≤c} X_ik·(R1⁻¹)_kc, an entry per thread
+    for (int e = tid; e < nrows * q; e += blockDim.x) {
+      const int i = e / q, c = e - i * q;
+      const double* x = rows + i * q;
+      double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+      int k = 0;
+      for (; k + 3 <= c; k += 4) {
+        s0 = fma(x[k], Z1s[k * q + c], s0);
+        s1 = fma(x[k + 1], Z1s[(k + 1) * q + c], s1);
+        s2 = fma(x[k + 2], Z1s[(k + 2) * q + c], s2);
+        s3 = fma(x[k + 3], Z1s[(k + 3) * q + c], s3);
       }
-    } else if (q <= 64) {
-      // lane c holds columns c and c + 32
-      const int lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-      const int c1 = lane + 32;
-      for (int i0 = warp; i0 < nrows; i0 += 3 * nw) {
-        double acc[3], acc1[3];
-        bool live[3];
-#pragma unroll
-        for (int u = 0; u < 3; ++u) {
-          const int i = i0 + u * nw;
-          live[u] = i < nrows;
-          acc[u] = (live[u] && lane < q) ? rows[i * q + lane] : 0.0;
-          acc1[u] = (live[u] && c1 < q) ? rows[i * q + c1] : 0.0;
-        }
-        for (int k = 0; k < q; ++k) {
-          const double rk = lane < q ? R1s[k * q + lane] : 0.0;
-          const double rk1 = c1 < q ? R1s[k * q + c1] : 0.0;
-          const double dk = dinv[k];
-          const bool hi = k >= 32;
-#pragma unroll
-          for (int u = 0; u < 3; ++u) {
-            const double src = hi ? acc1[u] : acc[u];
-            const double yk = __shfl_sync(0xffffffffu, src, k & 31) * dk;
-            if (!hi) {
-              if (lane == k) acc[u] = yk;
-              else if (lane > k) acc[u] = fma(-yk, rk, acc[u]);
-            }
-            if (c1 == k) acc1[u] = yk;
-            else if (c1 > k) acc1[u] = fma(-yk, rk1, acc1[u]);
-          }
-        }
-#pragma unroll
-        for (int u = 0; u < 3; ++u) {
-          if (live[u] && lane < q) rows[(i0 + u * nw) * q + lane] = acc[u];
-          if (live[u] && c1 < q) rows[(i0 + u * nw) * q + c1] = acc1[u];
-        }
-      }
-    } else {
-      for (int i = tid; i < nrows; i += blockDim.x) {
-        double* y = rows + i * q;
-        for (int c = 0; c < q; ++c) {
-          double s0 = y[c], s1 = 0.0, s2 = 0.0, s3 = 0.0;
-          int k = 0;
-          for (; k + 3 < c; k += 4) {
-            s0 = fma(-y[k], R1s[k * q + c], s0);
-            s1 = fma(-y[k + 1], R1s[(k + 1) * q + c], s1);
-            s2 = fma(-y[k + 2], R1s[(k + 2) * q + c], s2);
-            s3 = fma(-y[k + 3], R1s[(k + 3) * q + c], s3);
-          }
-          for (; k < c; ++k) s0 = fma(-y[k], R1s[k * q + c], s0);
-          y[c] = ((s0 + s1) + (s2 + s3)) * dinv[c];
-        }
-      }
+      for (; k <= c; ++k) s0 = fma(x[k], Z1s[k * q + c], s0);
+      EZ[e] = (s0 + s1) + (s2 + s3);
     }
     __syncthreads();
+    src = EZ;
   }
   for (int e = tid; e < ne; e += blockDim.x) {
     int j, l;
@@ -478,16 +524,16 @@ __global__ void __launch_bounds__(kGramThreads) cond2_kernel(const Cond2Args a) 
     double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
     int i = 0;
     for (; i + 3 < nrows; i += 4) {
-      s0 = fma(rows[i * q + j], rows[i * q + l], s0);
-      s1 = fma(rows[(i + 1) * q + j], rows[(i + 1) * q + l], s1);
-      s2 = fma(rows[(i + 2) * q + j], rows[(i + 2) * q + l], s2);
-      s3 = fma(rows[(i + 3) * q + j], rows[(i + 3) * q + l], s3);
+      s0 = fma(src[i * q + j], src[i * q + l], s0);
+      s1 = fma(src[(i + 1) * q + j], src[(i + 1) * q + l], s1);
+      s2 = fma(src[(i + 2) * q + j], src[(i + 2) * q + l], s2);
+      s3 = fma(src[(i + 3) * q + j], src[(i + 3) * q + l], s3);
     }
-    for (; i < nrows; ++i) s0 = fma(rows[i * q + j], rows[i * q + l], s0);
+    for (; i < nrows; ++i) s0 = fma(src[i * q + j], src[i * q + l], s0);
     a.partials[static_cast<size_t>(blockIdx.x) * ne + e] = (s0 + s1) + (s2 + s3);
   }
   // Two-level fixed-order sum of the partials: the last block of each group of
-  // kCondGroup blocks adds its group's partials; the last group to finish adds the
+  // cond2_group_size blocks adds its group's partials; the last group to finish adds the
   // group sums (both in block order, so the result does not depend on scheduling).
   const int gsz = cond2_group_size(q, gridDim.x);
   const int groups = (gridDim.x + gsz - 1) / gsz;
@@ -501,8 +547,8 @@ __global__ void __launch_bounds__(kGramThreads) cond2_kernel(const Cond2Args a) 
   if (!s_last) return;
   __threadfence();
   if (groups > 1) {
-    for (int e = tid; e < ne; e += blockDim.x)
-      gsum[static_cast<size_t>(g) * ne + e] = sum4(a.partials + static_cast<size_t>(g_lo) * ne + e, g_n, ne);
+    sum_partials(a.partials + static_cast<size_t>(g_lo) * ne, g_n, ne, ne,
+                 [&](int e, double v) { gsum[static_cast<size_t>(g) * ne + e] = v; });
     __threadfence();
     __syncthreads();
     if (tid == 0) s_last = (atomicAdd(a.ticket + groups, 1u) == static_cast<unsigned>(groups - 1)) ? 1 : 0;
@@ -512,42 +558,37 @@ __global__ void __launch_bounds__(kGramThreads) cond2_kernel(const Cond2Args a) 
   }
   // ---- last group: the group sums (or, with one group, the partials), then the q×q work
   double* Gs = rows;
-  const double* src = groups > 1 ? gsum : a.partials;
-  const int nsrc = groups > 1 ? groups : static_cast<int>(gridDim.x);
-  for (int e = tid; e < ne; e += blockDim.x) {
-    const double v = sum4(src + e, nsrc, ne);
-    int j, l;
-    pair_index(e, q, j, l);
-    Gs[j * q + l] = v;
-    Gs[l * q + j] = v;
-    if (PASS == 0 && j == l) a.colnorm[j] = sqrt(v);
-  }
-  double* Ps = sm2 + L.P;
-  double* Rc = sm2 + L.Rc;                    // this pass's Cholesky factor
-  if (PASS == 1)
-    for (int e = tid; e < q * a.r2; e += blockDim.x) Ps[e] = a.pi2[e];
+  sum_partials(groups > 1 ? gsum : a.partials, groups > 1 ? groups : static_cast<int>(gridDim.x), ne, ne,
+               [&](int e, double v) {
+                 int j, l;
+                 pair_index(e, q, j, l);
+                 Gs[j * q + l] = v;
+                 Gs[l * q + j] = v;
+                 if (PASS == 0 && j == l) a.colnorm[j] = sqrt(v);
+               });
+  uint32_t* tri = reinterpret_cast<uint32_t*>(sm2 + L.tri);
+  fill_tri(tri, q);
   __syncthreads();
   const int nt = q > 32 ? static_cast<int>(blockDim.x) : 128;
   if (tid < nt) {
-    // FP32-accurate pivot reciprocals suffice for R1, which only preconditions pass 1
-    const bool ok = block_cholesky(Gs, Rc, dn, sm2 + L.inv, q, PASS == 0 ? 0 : 2, nt);
+    const bool ok = block_chol_inv<PASS>(Gs, EZ, tri, sm2 + L.su, sm2 + L.sr, sm2 + L.st, sm2 + L.ss, q, nt);
     if (tid == 0) s_ok = ok ? 1 : 0;
   }
   __syncthreads();
   if (PASS == 0) {
     if (tid == 0) *a.breakdown = s_ok ? 0u : 1u;     // the Householder kernel redoes the step
-    for (int e = tid; e < q * q; e += blockDim.x) a.R1[e] = Rc[e];
-    for (int e = tid; e < q; e += blockDim.x) a.R1dinv[e] = dn[e];
+    for (int e = tid; e < q * q; e += blockDim.x) {
+      a.R1[e] = Gs[e];
+      a.Z1[e] = EZ[e];
+    }
   } else {
-    double* Rs = sm2 + L.R;
-    double* Ms = sm2 + L.M;
     const bool broke0 = *a.breakdown != 0u || !s_ok;
     if (tid < 32) {
       // rank test over the columns, one lane per column: R_kk = (R2)_kk·(R1)_kk (skipped after a
       // breakdown: the Householder kernel runs its own)
       bool bad = false;
       for (int k = tid; k < q; k += 32) {
-        const double rkk = Rc[k * q + k] * R1s[k * q + k];
+        const double rkk = Gs[k * q + k] * r1d[k];
         if (!(rkk > kRankTol * a.colnorm[k]) || !isfinite(rkk)) bad = true;
       }
       if (__any_sync(0xffffffffu, bad) && !broke0) {
@@ -555,69 +596,88 @@ __global__ void __launch_bounds__(kGramThreads) cond2_kernel(const Cond2Args a) 
       }
       if (broke0 && tid == 0) *a.breakdown = 1u;
     }
-    // M = R⁻¹·Π2.  q ≤ 32: R = R2·R1 first, then one right-looking back substitution;
-    // wider X: R1⁻¹·(R2⁻¹·Π2) by two, which avoids the q³ product.
-    const bool small = q <= 32;
-    if (small) {
-      for (int e = tid; e < q * q; e += blockDim.x) {
-        const int i = e / q, j = e - i * q;
-        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-        int k = i;
-        for (; k + 3 <= j; k += 4) {
-          s0 = fma(Rc[i * q + k], R1s[k * q + j], s0);
-          s1 = fma(Rc[i * q + k + 1], R1s[(k + 1) * q + j], s1);
-          s2 = fma(Rc[i * q + k + 2], R1s[(k + 2) * q + j], s2);
-          s3 = fma(Rc[i * q + k + 3], R1s[(k + 3) * q + j], s3);
-        }
-        for (; k <= j; ++k) s0 = fma(Rc[i * q + k], R1s[k * q + j], s0);
-        Rs[e] = j < i ? 0.0 : (s0 + s1) + (s2 + s3);
-      }
-      for (int k = tid; k < q; k += blockDim.x) dn[k] = dn[k] * dinv[k];   // 1/(R2_kk·R1_kk)
-    }
-    for (int e = tid; e < q * a.r2; e += blockDim.x) Ms[e] = Ps[e];
-    __syncthreads();
-    if (tid < nt) {
-      if (small) {
-        block_back_subst(Rs, dn, Ms, q, a.r2, nt);
-      } else {
-        block_back_subst(Rc, dn, Ms, q, a.r2, nt);
-        block_back_subst(R1s, dinv, Ms, q, a.r2, nt);
-      }
-    }
-    __syncthreads();
-    for (int e = tid; e < q * a.r2; e += blockDim.x) {
-      const double m = Ms[e];
-      a.M64[e] = m;
-      a.M32[e] = static_cast<float>(m);
-      if (a.M_user) a.M_user[e] = m;
-      if (!isfinite(m)) *a.breakdown = 1u;
-    }
-    if (a.R_user && small) {
-      for (int e = tid; e < q * q; e += blockDim.x) {
-        a.R[e] = Rs[e];
-        a.R_user[e] = Rs[e];
-      }
-    } else if (a.R_user) {
-      // R = R2·R1 (both upper triangular), only when the caller asks for it
-      for (int e = tid; e < q * q; e += blockDim.x) {
-        const int i = e / q, j = e - i * q;
-        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-        int k = i;
-        for (; k + 3 <= j; k += 4) {
-          s0 = fma(Rc[i * q + k], R1s[k * q + j], s0);
-          s1 = fma(Rc[i * q + k + 1], R1s[(k + 1) * q + j], s1);
-          s2 = fma(Rc[i * q + k + 2], R1s[(k + 2) * q + j], s2);
-          s3 = fma(Rc[i * q + k + 3], R1s[(k + 3) * q + j], s3);
-        }
-        for (; k <= j; ++k) s0 = fma(Rc[i * q + k], R1s[k * q + j], s0);
-        const double v = j < i ? 0.0 : (s0 + s1) + (s2 + s3);
-        Rs[e] = v;
-        a.R[e] = v;
-        a.R_user[e] = v;
-      }
+    for (int e = tid; e < q * q; e += blockDim.x) {
+      a.R2[e] = Gs[e];
+      a.Z2[e] = EZ[e];
     }
   }
   for (int k = tid; k <= groups; k += blockDim.x) a.ticket[k] = 0u;   // ready for the next pass
+}
+
+// After pass 1, one block per row i (Figure 2, step 3): row i of R⁻¹ = R1⁻¹·R2⁻¹, then
+// M_i = (R⁻¹)_i·Π2 and, when the caller asks for R, R_i = (R2)_i·R1 — products of upper
+// triangular factors, an entry per thread.  A non-finite entry of M records a breakdown, so
+// that the Householder kernel enqueued next redoes the step.
+constexpr int kCondMThreads = 128;
+
+__global__ void __launch_bounds__(kCondMThreads) cond_m_kernel(const Cond2Args a) {
+  // shared: R2⁻¹ (q×q), Π2 (q×r2), row i of R1⁻¹ and of R⁻¹ (q each), and for R the rows of
+  // R1 (q×q) and row i of R2 (q)
+  extern __shared__ __align__(16) double cm[];
+  const int q = a.q, r2 = a.r2, i = blockIdx.x, tid = threadIdx.x;
+  const bool want_r = a.R_user != nullptr;
+  double* z2 = cm;
+  double* pi = z2 + q * q;
+  double* z1 = pi + q * r2;
+  double* zr = z1 + q;
+  double* r1 = zr + q;
+  double* r2i = r1 + (want_r ? q * q : 0);
+  for (int e = tid; e < q * q; e += blockDim.x) z2[e] = a.Z2[e];
+  for (int e = tid; e < q * r2; e += blockDim.x) pi[e] = a.pi2[e];
+  for (int e = tid; e < q; e += blockDim.x) z1[e] = a.Z1[i * q + e];
+  if (want_r) {
+    for (int e = tid; e < q * q; e += blockDim.x) r1[e] = a.R1[e];
+    for (int e = tid; e < q; e += blockDim.x) r2i[e] = a.R2[i * q + e];
+  }
+  __syncthreads();
+  for (int j = tid; j < q; j += blockDim.x) {
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    int k = i;
+    for (; k + 3 <= j; k += 4) {
+      s0 = fma(z1[k], z2[k * q + j], s0);
+      s1 = fma(z1[k + 1], z2[(k + 1) * q + j], s1);
+      s2 = fma(z1[k + 2], z2[(k + 2) * q + j], s2);
+      s3 = fma(z1[k + 3], z2[(k + 3) * q + j], s3);
+    }
+    for (; k <= j; ++k) s0 = fma(z1[k], z2[k * q + j], s0);
+    zr[j] = j < i ? 0.0 : (s0 + s1) + (s2 + s3);
+  }
+  __syncthreads();
+  for (int c = tid; c < r2; c += blockDim.x) {
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    int k = i;
+    for (; k + 3 < q; k += 4) {
+      s0 = fma(zr[k], pi[k * r2 + c], s0);
+      s1 = fma(zr[k + 1], pi[(k + 1) * r2 + c], s1);
+      s2 = fma(zr[k + 2], pi[(k + 2) * r2 + c], s2);
+      s3 = fma(zr[k + 3], pi[(k + 3) * r2 + c], s3);
+    }
+    for (; k < q; ++k) s0 = fma(zr[k], pi[k * r2 + c], s0);
+    const double m = (s0 + s1) + (s2 + s3);
+    a.M64[i * r2 + c] = m;
+    a.M32[i * r2 + c] = static_cast<float>(m);
+    if (a.M_user) a.M_user[i * r2 + c] = m;
+    if (!isfinite(m)) *a.breakdown = 1u;
+  }
+  if (want_r) {
+    for (int j = tid; j < q; j += blockDim.x) {
+      double s0 = 0.0, s1 = 0.0;
+      int k = i;
+      for (; k + 1 <= j; k += 2) {
+        s0 = fma(r2i[k], r1[k * q + j], s0);
+        s1 = fma(r2i[k + 1], r1[(k + 1) * q + j], s1);
+      }
+      if (k <= j) s0 = fma(r2i[k], r1[k * q + j], s0);
+      const double v = j < i ? 0.0 : s0 + s1;
+      a.R[i * q + j] = v;
+      a.R_user[i * q + j] = v;
+    }
+  }
+}
+
+static size_t cond_m_smem(int q, int r2, bool want_r) {
+  return sizeof(double) * (static_cast<size_t>(q) * q + static_cast<size_t>(q) * r2 + 2 * q +
+                           (want_r ? static_cast<size_t>(q) * q + q : 0));
 }
 
 __global__ void pi2_kernel(Key2 key, uint32_t problem, int total, int gaussian, double* out) {
@@ -637,7 +697,7 @@ size_t cond2_scratch_bytes(int r1, int q, int sms) {
   const int rpb = cond2_rows_per_block(r1, q);
   const int blocks = (r1 + rpb - 1) / rpb;
   const int groups = (blocks + cond2_group_size(q, blocks) - 1) / cond2_group_size(q, blocks);
-  return sizeof(double) * (static_cast<size_t>(blocks + groups) * (q * (q + 1) / 2) + q * q + 2 * q) +
+  return sizeof(double) * (static_cast<size_t>(blocks + groups) * (q * (q + 1) / 2) + 4 * q * q + q) +
          sizeof(unsigned int) * (groups + 1) + 256;
 }
 
@@ -649,8 +709,8 @@ bool launch_condition(const Plan& pl, const float* pix, const l1s_params* p, dou
                       double* M_user, unsigned char* ws, cudaStream_t st, bool pi2_ready) {
   // Wide X (q near 129) does not fit the CholeskyQR2 blocks in shared memory: one block
   // of Householder reflections on a workspace copy handles it instead.
-  if (sizeof(double) * static_cast<size_t>(Cond2Smem(cond2_rows_per_block(pl.r1, pl.q), pl.q, pl.r2).total) >
-      static_cast<size_t>(device_info().max_smem_optin))
+  if (std::max(sizeof(double) * static_cast<size_t>(Cond2Smem(cond2_rows_per_block(pl.r1, pl.q), pl.q).total),
+               cond_m_smem(pl.q, pl.r2, R_user != nullptr)) > static_cast<size_t>(device_info().max_smem_optin))
     return launch_condition_householder(pl, pix, p, R_user, M_user, ws, st);
   Cond2Args a;
   a.pix = pix;
@@ -666,8 +726,10 @@ bool launch_condition(const Plan& pl, const float* pix, const l1s_params* p, dou
   const int groups = (grid + cond2_group_size(pl.q, grid) - 1) / cond2_group_size(pl.q, grid);
   a.partials = scratch;
   a.R1 = scratch + static_cast<size_t>(grid + groups) * ne;
-  a.R1dinv = a.R1 + pl.q * pl.q;
-  a.colnorm = a.R1dinv + pl.q;
+  a.Z1 = a.R1 + pl.q * pl.q;
+  a.R2 = a.Z1 + pl.q * pl.q;
+  a.Z2 = a.R2 + pl.q * pl.q;
+  a.colnorm = a.Z2 + pl.q * pl.q;
   a.ticket = reinterpret_cast<unsigned int*>(a.colnorm + pl.q);
   a.R = reinterpret_cast<double*>(ws + pl.off_r);
   a.M64 = reinterpret_cast<double*>(ws + pl.off_m64);
@@ -679,18 +741,22 @@ bool launch_condition(const Plan& pl, const float* pix, const l1s_params* p, dou
   a.flags = reinterpret_cast<uint32_t*>(ws + pl.off_status);
   a.pi2_ready = pi2_ready ? 1 : 0;
   a.pi2_gauss = p->variant == 1 ? 1 : 0;
-  const size_t smem = sizeof(double) * static_cast<size_t>(Cond2Smem(a.rows_per_block, pl.q, pl.r2).total);
+  const size_t smem = sizeof(double) * static_cast<size_t>(Cond2Smem(a.rows_per_block, pl.q).total);
+  const size_t msmem = cond_m_smem(pl.q, pl.r2, R_user != nullptr);
   if (!cuda_ok(cudaFuncSetAttribute(cond2_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)),
                "cond2 smem") ||
       !cuda_ok(cudaFuncSetAttribute(cond2_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)),
-               "cond2 smem"))
+               "cond2 smem") ||
+      !cuda_ok(cudaFuncSetAttribute(cond_m_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(msmem)),
+               "cond_m smem"))
     return false;
   if (!cuda_ok(cudaMemsetAsync(a.ticket, 0, sizeof(unsigned int) * (groups + 1), st), "reset conditioning tickets"))
     return false;
   a.breakdown = &reinterpret_cast<StatusBlock*>(ws + pl.off_status)->qr_breakdown;
   cond2_kernel<0><<<grid, kGramThreads, smem, st>>>(a);
   cond2_kernel<1><<<grid, kGramThreads, smem, st>>>(a);
-  count_launch(2);
+  cond_m_kernel<<<pl.q, kCondMThreads, msmem, st>>>(a);
+  count_launch(3);
   if (!cuda_ok(cudaGetLastError(), "launch condition")) return false;
   // After a breakdown (Π1·X too ill-conditioned for the Gram matrices), Householder QR.
   return launch_condition_householder(pl, pix, p, R_user, M_user, ws, st, a.breakdown);
