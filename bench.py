@@ -966,7 +966,8 @@ def run_gpu(args) -> None:
 # (and 2^24 for its DRAM traffic), the slow transform at n = 2^21, d = 16, and the d = 64
 # tensor-core λ at n = 2^22.
 KERNEL_CASES = {"phase1_d64_n4M": (1 << 22,), "phase1_d64_n16M": (1 << 24,), "sct_d16_n2M": (1 << 21,),
-                "lambda_tc_d64_n4M": (1 << 22,), "batched_256": (0,)}
+                "lambda_tc_d64_n4M": (1 << 22,), "batched_256": (0,),
+                "condition_d16": (1 << 20,), "condition_d64": (1 << 20,)}
 
 
 def run_kernel_case(args) -> None:
@@ -1001,6 +1002,28 @@ def run_kernel_case(args) -> None:
         bad = int((flags != 0).sum().item())
         print(json.dumps({"kernel_case": args.kernel_case, "members": len(probs), "status_nonzero": bad}))
         if bad:
+            sys.exit(1)
+        return
+    if args.kernel_case.startswith("condition"):
+        # the conditioning of the two measured shapes (r1 = 355, q = 17, r2 = 16 and r1 = 2130,
+        # q = 65, r2 = 32) on the embedding of 2^20 random rows, with columns scaled as in the
+        # colscale workload: two l1_condition calls as the pipeline makes them (no R copy)
+        d, r1, r2 = (16, 355, 16) if args.kernel_case.endswith("d16") else (64, 2130, 32)
+        A = torch.randn((n, d), generator=g, device=dev)
+        A *= 10.0 ** (torch.rand(d, generator=g, device=dev) * 4.0 - 2.0)
+        b = torch.randn(n, generator=g, device=dev)
+        prm = L.make_params(256 if d == 16 else 1024, r1, r2, 1e4, seed=1)
+        ws = L.workspace(prm, n, d, device=dev)
+        pix = torch.empty((r1, d + 1), device=dev)
+        M = torch.empty((d + 1, r2), device=dev, dtype=torch.float64)
+        L.l1s_status_reset(ws)
+        L.fct_embed(A, b, prm, pix, ws)
+        for _ in range(2):
+            L.l1_condition(pix, prm, None, M, ws)
+        torch.cuda.synchronize()
+        flags = L.l1s_status_read(ws)
+        print(json.dumps({"kernel_case": args.kernel_case, "r1": r1, "q": d + 1, "status": flags}))
+        if flags:
             sys.exit(1)
         return
     if args.kernel_case.startswith("phase1"):

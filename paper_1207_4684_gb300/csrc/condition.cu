@@ -177,9 +177,9 @@ __global__ void __launch_bounds__(kCondThreads) condition_kernel(const CondArgs 
 // FP64 arithmetic on this part is slow (a dependent FMA takes ~64 cycles, and a full-warp
 // FP64 instruction holds its sub-partition for ~64-80 cycles however few of its lanes
 // are active), so the factorisation keeps one short chain per step — a reciprocal from the
-// hardware's FP64 approximation refined by Newton steps, no division or square root — and
-// packs each step's independent updates densely over all threads; the products and the
-// sums of the partials are independent dot products.
+// hardware's FP64 approximation (refined by Newton steps where it enters R), no division or
+// square root — and packs each step's independent updates densely over all threads; the
+// products and the sums of the partials are independent dot products.
 constexpr int kGramThreads = 256;
 // Blocks per first-level group of the partial sums: one group (a single level) for
 // q ≤ 32, groups of 8 for wider X, whose partials are long.
@@ -236,9 +236,10 @@ __device__ __forceinline__ double rsqrt_f64(double x, int steps) {
 }
 
 // 1/x for a positive normal FP64 x on the serial chain of the factorisation: the
-// hardware's approximate FP64 reciprocal (PTX rcp.approx.ftz.f64, far better than the
-// 2^-14 that two steps need) refined by two Newton steps y ← y + y·(1 − x·y), each of
-// which squares the relative error, to FP64 rounding.
+// hardware's approximate FP64 reciprocal (PTX rcp.approx.ftz.f64; at most 2^-19.9 relative
+// error over 4M random operands spanning 1e±260 on GB300, where two Newton steps need
+// 2^-14) refined by two Newton steps y ← y + y·(1 − x·y), each of which squares the
+// relative error, to FP64 rounding.
 __device__ __forceinline__ double rcp_approx_f64(double x) {
   double y;
   asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
@@ -254,16 +255,11 @@ __device__ __forceinline__ double rcp_newton_f64(double x) {
 // The pivot reciprocals of the two factorisations.  Pass 0 only preconditions: any r_k
 // close to 1/d_k serves, because R1 and R1⁻¹ are both formed from the same r_k (they stay
 // exact inverses of each other) and pass 1 corrects the rest — the hardware approximation
-// alone.  Pass 1 factors the Gram matrix of Y = Π1X·R1⁻¹, close to the identity, so its
-// pivots lie near 1: with e = 1 − d (exact for d in [1/2, 2]), 1/d = 1 + e + e² + e³/(1−e),
-// and 1 + (e + e²) is correctly rounded up to e³ < 2^-54 when |e| < 2^-18; any other pivot
-// takes the two Newton steps.
+// alone.  Pass 1's R2 is part of R: two Newton steps.  A pivot that is not positive gives a
+// meaningless reciprocal here and is reported after the loop.
 template <int PASS>
 __device__ __forceinline__ double pivot_rcp(double d) {
-  if (PASS == 0) return rcp_approx_f64(d);
-  const double e = 1.0 - d;
-  if (fabs(e) < 0x1p-18) return 1.0 + fma(e, e, e);
-  return rcp_newton_f64(d);
+  return PASS == 0 ? rcp_approx_f64(d) : rcp_newton_f64(d);
 }
 
 // Threads [0, nt) take part in the factorisation (nt a multiple of 32: 128 for q ≤ 32,
@@ -304,12 +300,9 @@ template <int PASS>
 __device__ bool block_chol_inv(double* G, double* E, const uint32_t* tri, double* s_u, double* s_r,
                                double* s_t, double* s_s, int q, int nt) {
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  bool ok = true;
   if (warp == 0) {
-    const double a = G[0];
-    const double r = pivot_rcp<PASS>(fmax(a, 1e-300));
+    const double r = pivot_rcp<PASS>(G[0]);
     if (lane == 0) s_r[0] = r;
-    if (!(a > 0.0) || !isfinite(a)) ok = false;
     for (int j = 1 + lane; j < q; j += 32) s_u[j] = G[j] * r;
   }
   sync_first(nt);
@@ -321,12 +314,11 @@ __device__ bool block_chol_inv(double* G, double* E, const uint32_t* tri, double
       double* g1 = G + (k + 1) * q;
       const double uk1 = u[k + 1];
       const double d1 = fma(-uk1, gk[k + 1], g1[k + 1]);
-      const double r1 = pivot_rcp<PASS>(fmax(d1, 1e-300));
+      const double r1 = pivot_rcp<PASS>(d1);
       if (lane == 0) {
         g1[k + 1] = d1;
         s_r[k + 1] = r1;
       }
-      if (!(d1 > 0.0) || !isfinite(d1)) ok = false;
       for (int j = k + 2 + lane; j < q; j += 32) {
         const double v = fma(-uk1, gk[j], g1[j]);
         g1[j] = v;
@@ -374,13 +366,16 @@ __device__ bool block_chol_inv(double* G, double* E, const uint32_t* tri, double
     }
     sync_first(nt);
   }
+  bool bad = false;
   for (int k = t; k < q; k += nt) {
-    const double d = fmax(G[k * q + k], 1e-300);
+    const double d0 = G[k * q + k];
+    if (!(d0 > 0.0) || !isfinite(d0)) bad = true;
+    const double d = fmax(d0, 1e-300);
     const double tk = rsqrt_f64(d, 2);
     s_t[k] = tk;
     s_s[k] = d * tk;
   }
-  sync_first(nt);
+  const bool ok = !named_barrier_any(1, nt, bad);
   // R in place (each entry reads only itself); Z's upper part from E's strictly lower part
   for (int e = t; e < q * q; e += nt) {
     const int i = e / q, j = e - i * q;
@@ -451,6 +446,28 @@ __device__ __forceinline__ void sum_partials(const double* src, int count, size_
   else sum_partials_t<4, 8>(src, count, stride, ne, out);
 }
 
+// dst[e] = src[e] for e < count over the whole block, kStageRun loads of a thread in flight
+// before their stores (global loads at L2: the factors come from other blocks of earlier
+// launches).
+constexpr int kStageRun = 8;
+template <typename TS>
+__device__ __forceinline__ void stage_to_shared(double* dst, const TS* src, int count) {
+  const int nb = static_cast<int>(blockDim.x);
+  for (int e0 = threadIdx.x; e0 < count; e0 += kStageRun * nb) {
+    TS v[kStageRun];
+#pragma unroll
+    for (int u = 0; u < kStageRun; ++u) {
+      const int e = e0 + u * nb;
+      v[u] = e < count ? __ldcg(src + e) : TS(0);
+    }
+#pragma unroll
+    for (int u = 0; u < kStageRun; ++u) {
+      const int e = e0 + u * nb;
+      if (e < count) dst[e] = static_cast<double>(v[u]);
+    }
+  }
+}
+
 // Shared memory of a cond2 block (doubles): the rows of Π1X, later the Gram matrix and R in
 // place | the rows of Y (pass 1), later E and the inverse factor in place | R1⁻¹ (pass 1) |
 // the triangle table (uint32) | the multipliers of two steps | r_k | 1/√d_k | √d_k | diag R1.
@@ -492,11 +509,10 @@ __global__ void __launch_bounds__(kGramThreads) cond2_kernel(const Cond2Args a) 
       for (int e = blockIdx.x * blockDim.x + tid; e < q * a.r2; e += gridDim.x * blockDim.x)
         a.pi2[e] = pi2_value(a.key, a.problem, e, a.pi2_gauss);
   } else {
-    for (int e = tid; e < q * q; e += blockDim.x) Z1s[e] = a.Z1[e];
+    stage_to_shared(Z1s, a.Z1, q * q);
     for (int e = tid; e < q; e += blockDim.x) r1d[e] = a.R1[e * q + e];
   }
-  for (int e = tid; e < nrows * q; e += blockDim.x)
-    rows[e] = static_cast<double>(a.pix[static_cast<size_t>(r_lo) * q + e]);
+  stage_to_shared(rows, a.pix + static_cast<size_t>(r_lo) * q, nrows * q);
   __syncthreads();
   const double* src = rows;
   if (PASS == 1) {
@@ -622,12 +638,12 @@ __global__ void __launch_bounds__(kCondMThreads) cond_m_kernel(const Cond2Args a
   double* zr = z1 + q;
   double* r1 = zr + q;
   double* r2i = r1 + (want_r ? q * q : 0);
-  for (int e = tid; e < q * q; e += blockDim.x) z2[e] = a.Z2[e];
-  for (int e = tid; e < q * r2; e += blockDim.x) pi[e] = a.pi2[e];
-  for (int e = tid; e < q; e += blockDim.x) z1[e] = a.Z1[i * q + e];
+  stage_to_shared(z2, a.Z2, q * q);
+  stage_to_shared(pi, a.pi2, q * r2);
+  stage_to_shared(z1, a.Z1 + i * q, q);
   if (want_r) {
-    for (int e = tid; e < q * q; e += blockDim.x) r1[e] = a.R1[e];
-    for (int e = tid; e < q; e += blockDim.x) r2i[e] = a.R2[i * q + e];
+    stage_to_shared(r1, a.R1, q * q);
+    stage_to_shared(r2i, a.R2 + i * q, q);
   }
   __syncthreads();
   for (int j = tid; j < q; j += blockDim.x) {

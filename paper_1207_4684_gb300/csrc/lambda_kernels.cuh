@@ -259,11 +259,9 @@ __global__ void __launch_bounds__(kLamThreads, lambda_prefetches<D>() ? 1 : 2)
 // column d, and M's rows are padded the same way (M's b row moves to row D), so the extra
 // products are exact zeros and λ equals the unpadded FMA chain bit for bit.
 template <int D, int R2, bool SMEM_M>
-__global__ void __launch_bounds__(kLamThreads) lambda_kernel_pad(const float* __restrict__ A, int64_t lda, int d,
-                                                                 const float* __restrict__ b, int64_t n,
-                                                                 float* __restrict__ lam,
-                                                                 double* __restrict__ block_sums,
-                                                                 const float* __restrict__ mg) {
+__global__ void __launch_bounds__(kLamThreads, lambda_prefetches<D>() ? 1 : 2)
+    lambda_kernel_pad(const float* __restrict__ A, int64_t lda, int d, const float* __restrict__ b, int64_t n,
+                      float* __restrict__ lam, double* __restrict__ block_sums, const float* __restrict__ mg) {
   constexpr int Q = D + 1;
   __shared__ __align__(16) float sM[SMEM_M ? Q * R2 : 1];
   if constexpr (SMEM_M) {
@@ -276,13 +274,27 @@ __global__ void __launch_bounds__(kLamThreads) lambda_kernel_pad(const float* __
   float s = 0.f, c = 0.f;
   const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
   int64_t row = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  float nx[Q];
   auto load = [&](int64_t r, float (&x)[Q]) {
     const float* p = A + r * lda;
 #pragma unroll
     for (int k = 0; k < D; ++k) x[k] = k < d ? __ldg(p + k) : 0.f;
     x[D] = -__ldg(b + r);
   };
+  if constexpr (!lambda_prefetches<D>()) {
+    // as in lambda_kernel: wide rows are loaded when needed (a prefetched copy would double
+    // the registers a row takes), and two blocks per SM hide the latency
+    for (; row < n; row += stride) {
+      float x[Q];
+      load(row, x);
+      const float med = lambda_of_row<Q, R2, SMEM_M>(x, sM);
+      lam[row] = med;
+      two_sum_add(s, c, med);
+    }
+    const double tot = block_pair_total(s, c);
+    if (threadIdx.x == 0) block_sums[blockIdx.x] = tot;
+    return;
+  }
+  float nx[Q];
   if (row < n) load(row, nx);
   for (; row < n; row += stride) {
     float x[Q];
