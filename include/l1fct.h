@@ -158,7 +158,9 @@ L1S_API int fct_embed(const void* A_dev, int64_t lda, l1s_dtype dtype, const flo
  * q × r2 of standard Cauchys.  Outputs (device, FP64, row-major, may be NULL):
  * R_dev (q × q, upper triangular) and M_dev (q × r2).  Rank deficiency sets
  * the RANK_DEFICIENT status bit: column k counts as dependent on the columns
- * before it when |R_kk| ≤ 1e-5·‖(Π1X)_{:,k}‖₂, the resolution of an FP32 Π1X. */
+ * before it when |R_kk| ≤ 1e-5·‖(Π1X)_{:,k}‖₂, the resolution of an FP32 Π1X.
+ * Any workspace that l1s_workspace_size gives for these params, d = q − 1 and some
+ * n ≥ 1 serves. */
 L1S_API int l1_condition(const float* PiX_dev, int32_t r1, int32_t q, const l1s_params* params,
                  double* R_dev, double* M_dev, void* ws, size_t ws_bytes, void* stream);
 

@@ -532,8 +532,10 @@ int l1_condition(const float* PiX, int32_t r1, int32_t q, const l1s_params* para
   if (!params || !PiX) return set_error("params and PiX must not be NULL"), L1S_ERR_INVALID_ARG;
   if (r1 != params->r1) return set_error("r1 must equal params->r1"), L1S_ERR_INVALID_ARG;
   Plan pl;
-  if (!make_plan(params, std::max<int64_t>(1, r1), q - 1, L1S_F32, false, &pl)) return L1S_ERR_INVALID_ARG;
-  // Only the conditioning regions are used; they sit at fixed offsets for given (r1, q, r2).
+  // Only the status block and the conditioning regions are used.  The plan of one row is
+  // the smallest for these (r1, q, r2): a workspace that l1s_workspace_size gave for any
+  // n ≥ 1 holds it (a plan of n = r1 rows asked more than one sized for n < r1 rows had).
+  if (!make_plan(params, 1, q - 1, L1S_F32, false, &pl)) return L1S_ERR_INVALID_ARG;
   if (!check_ws(pl, ws, ws_bytes)) return L1S_ERR_WORKSPACE;
   if (!launch_condition(pl, PiX, params, R, M, static_cast<unsigned char*>(ws),
                         static_cast<cudaStream_t>(stream)))

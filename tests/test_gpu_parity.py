@@ -83,6 +83,11 @@ FCT_CASES = [
     ((1 << 17) + 1000, 64, 1024, "f32", 1, 0, None),
     ((1 << 17) + 1000, 64, 1024, "bf16", 1, 1024 * 5, None),
     (50000, 48, 1024, "f32", 0, 0, None),        # 32 < d < 64
+    # the widest X: r1 = ⌈8 d ln d⌉ beyond the column-sliced kernel's partial (r1 ≤ 2280)
+    (4000, 80, 1024, "f32", 1, 0, None),
+    (3000, 100, 256, "f32", 1, 0, None),
+    (2500, 128, 1024, "f32", 1, 1024 * 3, None),  # d at its maximum, global row offset
+    (2500, 128, 512, "bf16", 0, 0, None),
 ]
 
 
@@ -137,7 +142,12 @@ def test_fct_nonfinite_flag():
 # ----------------------------------------------------------------- conditioning
 @pytest.mark.parametrize("n,d,s,r2,design", [(65536, 8, 64, 16, "gauss"), (30000, 32, 256, 32, "gauss"),
                                              (5000, 64, 64, 32, "gauss"), (4000, 1, 16, 5, "gauss"),
-                                             (65536, 16, 256, 16, "gauss_colscale")])
+                                             (65536, 16, 256, 16, "gauss_colscale"),
+                                             # CholeskyQR2 at q = 81 (r1 = 2805); the one-block
+                                             # Householder QR for the widest X (q = 101, 129)
+                                             (4000, 80, 256, 32, "gauss_colscale"),
+                                             (3000, 100, 256, 16, "gauss"),
+                                             (2500, 128, 1024, 32, "gauss")])
 def test_condition_parity(n, d, s, r2, design):
     pr = problem(n, d, seed=d, design=design)
     A, b = to_device(pr)
@@ -186,7 +196,10 @@ def test_condition_rank_deficient_flag():
                                               # tensor-core form for 16 < d <= 64, r2 in {16, 32}
                                               (70001, 64, 32, "bf16", None), (30000, 48, 16, "bf16", None),
                                               (20000, 24, 16, "bf16", None), (5000, 64, 16, "bf16", 72),
-                                              (129, 33, 32, "bf16", None)])
+                                              (129, 33, 32, "bf16", None),
+                                              # the generic kernel for the widest X (q ≤ 129)
+                                              (20000, 100, 16, "f32", None), (8000, 128, 32, "bf16", None),
+                                              (5000, 80, 32, "f32", 84)])
 def test_lambda_parity(n, d, r2, dtype, lda):
     pr = problem(n, d, seed=r2 + d, dtype=dtype, design="gauss")
     A, b = to_device(pr, lda)
