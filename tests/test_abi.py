@@ -90,6 +90,18 @@ def test_version_and_argument_errors_without_gpu(lib):
     with pytest.raises(L.L1SError) as e:
         L.l1s_workspace_size(L.make_params(s=64, r1=40, r2=16, coreset=100.0, global_row_offset=10), 1000, 4)
     assert e.value.code == 1 and "global_row_offset" in str(e.value)
+    # empty input and the width limits are argument errors, decided before any device work
+    prm = L.make_params(s=64, r1=300, r2=16, coreset=100.0)
+    with pytest.raises(L.L1SError) as e:
+        L.l1s_workspace_size(prm, 0, 4)
+    assert e.value.code == 1 and "n must be" in str(e.value)
+    for d in (0, 129):
+        with pytest.raises(L.L1SError) as e:
+            L.l1s_workspace_size(prm, 1000, d)
+        assert e.value.code == 1 and "d must be" in str(e.value)
+    with pytest.raises(L.L1SError) as e:
+        L.l1s_workspace_size(L.make_params(s=64, r1=300, r2=0, coreset=100.0), 1000, 4)
+    assert e.value.code == 1 and "r2" in str(e.value)
 
 
 def test_product_code_never_touches_the_oracle():
