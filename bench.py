@@ -967,7 +967,7 @@ def run_gpu(args) -> None:
 # tensor-core λ at n = 2^22.
 KERNEL_CASES = {"phase1_d64_n4M": (1 << 22,), "phase1_d64_n16M": (1 << 24,), "sct_d16_n2M": (1 << 21,),
                 "lambda_tc_d64_n4M": (1 << 22,), "batched_256": (0,),
-                "condition_d16": (1 << 20,), "condition_d64": (1 << 20,)}
+                "condition_d16": (1 << 20,), "condition_d64": (1 << 20,), "lambda_f32_d64_n4M": (1 << 22,)}
 
 
 def run_kernel_case(args) -> None:
@@ -1038,7 +1038,9 @@ def run_kernel_case(args) -> None:
         prm = L.make_params(1, r1, 16, 2e4, seed=1, transform=1)
     else:
         d, r1 = 64, 2130
-        A = torch.randn((n, d), generator=g, device=dev).to(torch.bfloat16)
+        A = torch.randn((n, d), generator=g, device=dev)
+        if "_tc_" in args.kernel_case:
+            A = A.to(torch.bfloat16)
         b = torch.randn(n, generator=g, device=dev)
         prm = L.make_params(1024, r1, 32, 1e5, seed=1)
     dt = L.BF16 if A.dtype == torch.bfloat16 else L.F32
