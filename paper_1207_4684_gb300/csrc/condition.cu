@@ -4,14 +4,15 @@
 // phase 2 multiplies X by one skinny matrix, the order the paper's running-time
 // argument uses (proof of the fast ℓ1 regression theorem: R⁻¹Π2 before X·(R⁻¹Π2)).
 //
-// The QR is CholeskyQR2 (below) in two launches over many thread blocks.  When
-// its blocks do not fit in shared memory (q near 129), a single thread block runs
+// The QR is CholeskyQR2 (below) in two launches over many thread blocks, and M comes
+// from a third, one block per row of M.  When the blocks do not fit in shared memory
+// (q above about 93), a single thread block runs
 // Householder reflections on a column-major FP64 copy of Π1·X instead, held in
 // shared memory when it fits (r1·q·8 bytes ≤ 160 KB) and in the workspace
 // (L2-resident) otherwise.  CholeskyQR2 squares the condition number in its Gram
 // matrices and breaks down when Π1·X is conditioned worse than about 1e7-1e8; a
 // breakdown (a Cholesky pivot that is not positive, or a non-finite R or M) is recorded
-// in the status block, and the Householder kernel, enqueued after the two passes, then
+// in the status block, and the Householder kernel, enqueued after those launches, then
 // redoes the step (it returns at once otherwise), so the decision stays on the device.
 #include <stddef.h>
 
@@ -210,18 +211,10 @@ struct Cond2Args {
   int pi2_gauss;         // 1: Gaussian Π2 (OptimizedFastCauchyRegression)
 };
 
-// 1/x and 1/√x for x > 0 in FP64: an FP32 estimate of the mantissa part (the exponent is
-// split off first, so any normal FP64 x works), then Newton steps in FP64 — for 1/x
-// y ← y + y·(1 − x·y), for 1/√x y ← y·(3/2 − (x/2)·y²).  Each step doubles the number of
-// correct bits: one leaves a relative error near 1e-13, two reach FP64 rounding.
-__device__ __forceinline__ double rcp_f64(double x, int steps) {
-  int e;
-  const double m = frexp(x, &e);                         // x = m·2^e, m ∈ [1/2, 1)
-  double y = ldexp(static_cast<double>(__frcp_rn(static_cast<float>(m))), -e);
-  for (int i = 0; i < steps; ++i) y = fma(y, fma(-x, y, 1.0), y);
-  return y;
-}
-
+// 1/√x for x > 0 in FP64: an FP32 estimate of the mantissa part (the exponent is split
+// off first, so any normal FP64 x works), then Newton steps y ← y·(3/2 − (x/2)·y²) in FP64.
+// Each step doubles the number of correct bits: one leaves a relative error near 1e-13,
+// two reach FP64 rounding.
 __device__ __forceinline__ double rsqrt_f64(double x, int steps) {
   int e;
   double m = frexp(x, &e);
@@ -723,7 +716,7 @@ bool launch_condition_householder(const Plan& pl, const float* pix, const l1s_pa
 
 bool launch_condition(const Plan& pl, const float* pix, const l1s_params* p, double* R_user,
                       double* M_user, unsigned char* ws, cudaStream_t st, bool pi2_ready) {
-  // Wide X (q near 129) does not fit the CholeskyQR2 blocks in shared memory: one block
+  // Wide X (q above about 93) does not fit the CholeskyQR2 blocks in shared memory: one block
   // of Householder reflections on a workspace copy handles it instead.
   if (std::max(sizeof(double) * static_cast<size_t>(Cond2Smem(cond2_rows_per_block(pl.r1, pl.q), pl.q).total),
                cond_m_smem(pl.q, pl.r2, R_user != nullptr)) > static_cast<size_t>(device_info().max_smem_optin))
