@@ -8,7 +8,7 @@ import numpy as np
 import pytest
 
 import pins
-from oracle import condition, fct, fct2, leverage, pipeline, rng, sampling, sct, separable, solve
+from oracle import condition, fct, fct2, leverage, pipeline, quality, rng, sampling, sct, separable, solve
 
 ORIG_EMBED = fct.fct1_embed
 ORIG_HAD = fct.sylvester_hadamard
@@ -29,6 +29,22 @@ ORIG_SCT_MATRIX = rng.sct_matrix
 ORIG_FJLT_DRAWS = rng.fjlt_draws
 ORIG_FCT2_SCALE = fct2.fct2_scale
 ORIG_FCT2 = fct2.fct2_embed
+ORIG_MINBOX = quality.min_l1_on_unit_box
+
+
+def minbox_last_coordinate_only(U):
+    """Only the faces z_{d−1} = ±1 of the unit box searched (the other d − 1 regressions skipped)."""
+    U = np.asarray(U, dtype=np.float64)
+    if U.shape[1] == 1:
+        return ORIG_MINBOX(U)
+    _, v = solve.lad_lp(U[:, :-1], -U[:, -1])
+    return v
+
+
+def kappa_alpha_row_max(U):
+    """α as the largest row ℓ1 norm instead of the entrywise ℓ1 norm of U."""
+    U = np.asarray(U, dtype=np.float64)
+    return float(np.abs(U).sum(axis=1).max()) / quality.min_l1_on_unit_box(U)
 
 
 def fjlt_no_signs(seed, problem_id, t, s):
@@ -261,6 +277,9 @@ MUTATIONS = [
     ("FJLT one sampled row repeated", rng, "fjlt_draws", fjlt_one_row, pins.check_fjlt_isometry),
     ("FCT2 scale without √(πt/2s)", fct2, "fct2_scale", fct2_scale_no_sqrt, pins.check_fct2_stability),
     ("FCT2 blocks share C's columns", fct2, "fct2_embed", fct2_same_columns, pins.check_fct2_dense),
+    ("κ̄₁: one face of the unit box searched", quality, "min_l1_on_unit_box", minbox_last_coordinate_only,
+     pins.check_kappa_bar),
+    ("κ̄₁: α as the largest row norm", quality, "kappa_bar_1", kappa_alpha_row_max, pins.check_kappa_bar),
     ("separable optimum: mean for median", separable, "canonical_optimum", canonical_mean,
      pins.check_canonical_optimum),
     ("separable optimum: upper median = lower", separable, "canonical_optimum", canonical_hi_low,
