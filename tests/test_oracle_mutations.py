@@ -30,6 +30,7 @@ ORIG_FJLT_DRAWS = rng.fjlt_draws
 ORIG_FCT2_SCALE = fct2.fct2_scale
 ORIG_FCT2 = fct2.fct2_embed
 ORIG_MINBOX = quality.min_l1_on_unit_box
+ORIG_WOBJ = solve.weighted_objective
 
 
 def minbox_last_coordinate_only(U):
@@ -260,6 +261,8 @@ MUTATIONS = [
     ("p̂ not capped at 1", sampling, "probabilities", prob_no_cap, pins.check_sampling),
     ("weight p̂ for 1/p̂", sampling, "bernoulli_sample", bern_weights_p, pins.check_sampling),
     ("LP ignores weights", solve, "lad_lp", lp_unweighted, pins.check_solver),
+    ("objective ignores weights", solve, "weighted_objective", lambda A, b, w, x: ORIG_WOBJ(A, b, None, x),
+     pins.check_solver),
     ("X = [A, +b]", pipeline, "form_x", formx_plus_b, pins.check_solver),
     ("Gaussian Π2 variance 2", rng, "pi2_gaussian_matrix", gauss_var2, pins.check_gaussian_pi2),
     ("Box–Muller pair copied", rng, "pi2_gaussian_matrix", gauss_pair_copy, pins.check_gaussian_pi2),
