@@ -33,6 +33,16 @@ ORIG_MINBOX = quality.min_l1_on_unit_box
 ORIG_WOBJ = solve.weighted_objective
 
 
+def lambda_mean(X, M, chunk=1 << 20):
+    """The mean of |X·M| over the r2 columns instead of their median."""
+    return np.abs(np.asarray(X, dtype=np.float64) @ np.asarray(M, dtype=np.float64)).mean(axis=1)
+
+
+def pi2_gaussian_entries(seed, problem_id, q, r2):
+    """Π2 with standard Gaussian entries where FastCauchyRegression draws Cauchys."""
+    return np.random.default_rng(seed + 7 * problem_id).standard_normal((q, r2))
+
+
 def minbox_last_coordinate_only(U):
     """Only the faces z_{d−1} = ±1 of the unit box searched (the other d − 1 regressions skipped)."""
     U = np.asarray(U, dtype=np.float64)
@@ -256,6 +266,8 @@ MUTATIONS = [
     ("R transposed", condition, "qr_positive", qr_transposed, pins.check_qr),
     ("R·Π2 for R⁻¹·Π2", condition, "m_matrix", m_times_r, pins.check_qr),
     ("upper median", leverage, "lambda_estimates", lambda_upper_median, pins.check_lambda_distribution),
+    ("mean for median", leverage, "lambda_estimates", lambda_mean, pins.check_lambda_distribution),
+    ("Gaussian Π2 in FastCauchyRegression", rng, "pi2_matrix", pi2_gaussian_entries, pins.check_lambda_distribution),
     ("R⁻¹ distorted", condition, "m_matrix", lambda r, p: ORIG_M(r, p) * np.linspace(0.2, 5, r.shape[0])[:, None],
      pins.check_lambda_distribution),
     ("p̂ not capped at 1", sampling, "probabilities", prob_no_cap, pins.check_sampling),
