@@ -146,6 +146,27 @@ def check_fct_blocks(seed: int = 11) -> None:
         assert np.allclose(tsum[0::2], 4.0 * blocksum / math.sqrt(s), rtol=1e-13), "T of a Hadamard row"
 
 
+def check_fct_row_offset(seed: int = 29) -> None:
+    """Π1 is one linear map of all n rows whose variates (D, C, B) belong to global row ids,
+    so cutting X at a multiple of s and embedding the two parts with their row offsets gives
+    two matrices that add up to the embedding of the whole, and so do their Σ|terms|; the
+    ragged tail pads with zero rows either way (§3.1; row ids as the shards' reading)."""
+    g = np.random.default_rng(seed)
+    for s in (1, 4, 64):
+        n = 7 * s + s // 2 + 1
+        cut = 3 * s
+        X = g.standard_normal((n, 4))
+        r1 = 37
+        whole, tw = fct.fct1_embed(X, s, r1, seed=5, problem_id=1)
+        top, tt = fct.fct1_embed(X[:cut], s, r1, seed=5, problem_id=1, row_offset=0)
+        bot, tb = fct.fct1_embed(X[cut:], s, r1, seed=5, problem_id=1, row_offset=cut)
+        assert np.all(np.abs(top + bot - whole) <= 1e-12 * tw + 1e-300), f"additivity at s = {s}"
+        assert np.allclose(tt + tb, tw, rtol=1e-12, atol=0), f"Σ|terms| additivity at s = {s}"
+        # the offset matters: the bottom part embedded as if its rows came first differs
+        wrong, _ = fct.fct1_embed(X[cut:], s, r1, seed=5, problem_id=1, row_offset=0)
+        assert np.abs(top + wrong - whole).max() > 1e-6 * np.abs(whole).max(), "row ids ignored"
+
+
 def check_fct_mass(seed: int = 5) -> None:
     """With C ≡ 1 and random buckets, Σ_rows Π1X = 4·Σ g per column (the hashed sums add
     up, proof of FCT1), and Σ_rows T = 4·(1 + √s)·‖z‖₁: every input entry enters one identity
@@ -412,7 +433,8 @@ def _all_checks():
                          check_scaled_probabilities, check_multiple_regression, check_with_replacement,
                          check_sct_draws, check_sct_stability, check_sct_embedding_bound, check_kappa_bar,
                          check_canonical_optimum, check_fjlt_isometry, check_fjlt_spread, check_fct2_dense,
-                         check_fct2_stability, check_fct2_embedding_bound, check_philox_key_schedule]
+                         check_fct2_stability, check_fct2_embedding_bound, check_philox_key_schedule,
+                         check_fct_row_offset]
 
 
 # ----------------------------------------------------------------- slow Cauchy transform

@@ -33,6 +33,11 @@ ORIG_MINBOX = quality.min_l1_on_unit_box
 ORIG_WOBJ = solve.weighted_objective
 
 
+def embed_offset_ignored(X, s, r1, seed=0, problem_id=0, row_offset=0, sign_flip=True, draws=None):
+    """FCT1 with the rows' variates drawn from local row ids (the global offset dropped)."""
+    return ORIG_EMBED(X, s, r1, seed, problem_id, 0, sign_flip, draws)
+
+
 def lambda_mean(X, M, chunk=1 << 20):
     """The mean of |X·M| over the r2 columns instead of their median."""
     return np.abs(np.asarray(X, dtype=np.float64) @ np.asarray(M, dtype=np.float64)).mean(axis=1)
@@ -250,6 +255,7 @@ def sct_last_block_dropped(X, r1, seed=0, problem_id=0, row_offset=0, block=1 <<
 
 MUTATIONS = [
     ("identity half dropped", fct, "fct1_embed", embed_no_identity, pins.check_fct_dense),
+    ("row offset ignored", fct, "fct1_embed", embed_offset_ignored, pins.check_fct_row_offset),
     ("slow transform scaled by 1/r1", sct, "sct_embed", sct_scale_one_over_r1, pins.check_sct_stability),
     ("slow transform: one call for all groups", rng, "sct_matrix", sct_group_ignored, pins.check_sct_draws),
     ("slow transform: last rows dropped", sct, "sct_embed", sct_last_block_dropped, pins.check_sct_stability),
