@@ -38,6 +38,13 @@ def embed_offset_ignored(X, s, r1, seed=0, problem_id=0, row_offset=0, sign_flip
     return ORIG_EMBED(X, s, r1, seed, problem_id, 0, sign_flip, draws)
 
 
+def embed_ragged_tail_dropped(X, s, r1, seed=0, problem_id=0, row_offset=0, sign_flip=True, draws=None):
+    """FCT1 that drops the last, partial block of s rows instead of padding it with zeros."""
+    X = np.asarray(X)
+    m = X.shape[0] - X.shape[0] % s
+    return ORIG_EMBED(X[:m] if m else X, s, r1, seed, problem_id, row_offset, sign_flip, draws)
+
+
 def lambda_mean(X, M, chunk=1 << 20):
     """The mean of |X·M| over the r2 columns instead of their median."""
     return np.abs(np.asarray(X, dtype=np.float64) @ np.asarray(M, dtype=np.float64)).mean(axis=1)
@@ -256,6 +263,7 @@ def sct_last_block_dropped(X, r1, seed=0, problem_id=0, row_offset=0, block=1 <<
 MUTATIONS = [
     ("identity half dropped", fct, "fct1_embed", embed_no_identity, pins.check_fct_dense),
     ("row offset ignored", fct, "fct1_embed", embed_offset_ignored, pins.check_fct_row_offset),
+    ("ragged tail dropped", fct, "fct1_embed", embed_ragged_tail_dropped, pins.check_fct_dense),
     ("slow transform scaled by 1/r1", sct, "sct_embed", sct_scale_one_over_r1, pins.check_sct_stability),
     ("slow transform: one call for all groups", rng, "sct_matrix", sct_group_ignored, pins.check_sct_draws),
     ("slow transform: last rows dropped", sct, "sct_embed", sct_last_block_dropped, pins.check_sct_stability),
