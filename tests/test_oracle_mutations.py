@@ -45,6 +45,15 @@ def embed_ragged_tail_dropped(X, s, r1, seed=0, problem_id=0, row_offset=0, sign
     return ORIG_EMBED(X[:m] if m else X, s, r1, seed, problem_id, row_offset, sign_flip, draws)
 
 
+def replace_next_row(lam, m, u):
+    """Each draw takes the row after the one whose interval of the running sum holds it."""
+    idx, _, cdf = ORIG_REPLACE(lam, m, u)
+    lam = np.asarray(lam, dtype=np.float64)
+    idx = np.minimum(idx + 1, lam.size - 1)
+    with np.errstate(divide="ignore"):
+        return idx, cdf[-1] / (m * lam[idx]), cdf
+
+
 def lambda_mean(X, M, chunk=1 << 20):
     """The mean of |X·M| over the r2 columns instead of their median."""
     return np.abs(np.asarray(X, dtype=np.float64) @ np.asarray(M, dtype=np.float64)).mean(axis=1)
@@ -297,6 +306,8 @@ MUTATIONS = [
     ("Gaussian Π2 variance 2 in λ̂", rng, "pi2_gaussian_matrix", gauss_var2, pins.check_gaussian_lambda_distribution),
     ("scaled p̂ not capped", sampling, "probabilities_scaled", scaled_no_cap, pins.check_scaled_probabilities),
     ("X = [A, +B] (multiple)", pipeline, "form_x_multi", formx_multi_plus_b, pins.check_multiple_regression),
+    ("with-replacement draw one row late", sampling, "sample_with_replacement", replace_next_row,
+     pins.check_with_replacement),
     ("with-replacement weight m·p̂", sampling, "sample_with_replacement", replace_weight_mp,
      pins.check_with_replacement),
     ("with-replacement target u, not u·Σλ", sampling, "sample_with_replacement", replace_unscaled_target,
