@@ -32,11 +32,8 @@
  *   params.global_row_offset + r, so shards of one problem reproduce the
  *   unsharded draws.
  * - Not thread-safe per workspace; distinct workspaces may be used from
- *   distinct threads when the calls have the same shapes (n, d, dtype and
- *   params): each call sets its kernels' dynamic shared-memory limit for its own
- *   shapes just before it launches, so calls of different shapes from several
- *   host threads must be serialised by the caller (a launch that meets another
- *   thread's lower limit fails with L1S_ERR_CUDA; nothing runs out of bounds).
+ *   distinct threads (the kernels' dynamic shared-memory limits only ever rise,
+ *   under a lock, so calls of different shapes do not undo each other's).
  *   l1_lambda, l1_sample, l1_coreset, l1_coreset_host and
  *   l1_regress load M into a per-device constant bank: calls of these on
  *   different streams of one device must not overlap (l1_regress_batched

@@ -7,6 +7,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <map>
 #include <mutex>
 
 #include "l1s_common.cuh"
@@ -96,6 +97,20 @@ bool cuda_ok(cudaError_t e, const char* what) {
   if (e == cudaSuccess) return true;
   set_error("%s: %s", what, cudaGetErrorString(e));
   return false;
+}
+
+bool allow_dynamic_smem(const void* fn, size_t bytes, const char* what) {
+  static std::mutex mu;
+  static std::map<std::pair<int, const void*>, size_t> granted;
+  int dev = 0;
+  if (!cuda_ok(cudaGetDevice(&dev), "cudaGetDevice")) return false;
+  std::lock_guard<std::mutex> lock(mu);
+  size_t& g = granted[std::make_pair(dev, fn)];
+  if (bytes <= g) return true;
+  if (!cuda_ok(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(bytes)), what))
+    return false;
+  g = bytes;
+  return true;
 }
 
 DeviceInfo device_info() {
@@ -246,8 +261,7 @@ static FctGeometry fct_geometry(int variant, const Plan& P, l1s_dtype dt, const 
     g.smem = fct_cols_smem_bytes(P.r1);
     g.threads = fct_cols_threads();
     const void* fn = fct_cols_kernel(dt, P.log2s == 10);
-    if (!cuda_ok(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(g.smem)),
-                 "cudaFuncSetAttribute(fct_embed_cols)"))
+    if (!allow_dynamic_smem(reinterpret_cast<const void*>(fn), g.smem, "cudaFuncSetAttribute(fct_embed_cols)"))
       return g;
     int per_sm = 0;
     if (!cuda_ok(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, g.threads, g.smem), "occupancy(fct_cols)") ||
@@ -302,8 +316,7 @@ static FctGeometry fct_geometry(int variant, const Plan& P, l1s_dtype dt, const 
   const void* fn = g.sorted ? fct_sorted_kernel(P.log2s, dt, g.sorted)
                             : (g.ws ? fct_ws_kernel(g.tile_log2, P.log2s, dt, g.ws, g.lean)
                                     : fct_kernel(P.log2s, dt, staged));
-  if (!cuda_ok(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(g.smem)),
-               "cudaFuncSetAttribute(fct_embed)"))
+  if (!allow_dynamic_smem(reinterpret_cast<const void*>(fn), g.smem, "cudaFuncSetAttribute(fct_embed)"))
     return g;
   int per_sm = 0;
   if (!cuda_ok(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, g.threads, g.smem),

@@ -69,16 +69,12 @@ bool launch_basis(const void* A, int64_t lda, l1s_dtype dt, const float* b, int6
   double* sums = reinterpret_cast<double*>(ws + 256);
   const size_t smem = sizeof(double) * q * q;
   if (dt == L1S_BF16) {
-    if (!cuda_ok(cudaFuncSetAttribute(l1_basis_kernel<uint16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      static_cast<int>(smem)),
-                 "cudaFuncSetAttribute(l1_basis)"))
+    if (!allow_dynamic_smem(reinterpret_cast<const void*>(l1_basis_kernel<uint16_t>), smem, "cudaFuncSetAttribute(l1_basis)"))
       return false;
     l1_basis_kernel<uint16_t><<<blocks, kBasisThreads, smem, st>>>(static_cast<const uint16_t*>(A), lda, b, n, d, R,
                                                                     U, rownorm, sums);
   } else {
-    if (!cuda_ok(cudaFuncSetAttribute(l1_basis_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      static_cast<int>(smem)),
-                 "cudaFuncSetAttribute(l1_basis)"))
+    if (!allow_dynamic_smem(reinterpret_cast<const void*>(l1_basis_kernel<float>), smem, "cudaFuncSetAttribute(l1_basis)"))
       return false;
     l1_basis_kernel<float><<<blocks, kBasisThreads, smem, st>>>(static_cast<const float*>(A), lda, b, n, d, R, U,
                                                                  rownorm, sums);

@@ -752,12 +752,9 @@ bool launch_condition(const Plan& pl, const float* pix, const l1s_params* p, dou
   a.pi2_gauss = p->variant == 1 ? 1 : 0;
   const size_t smem = sizeof(double) * static_cast<size_t>(Cond2Smem(a.rows_per_block, pl.q).total);
   const size_t msmem = cond_m_smem(pl.q, pl.r2, R_user != nullptr);
-  if (!cuda_ok(cudaFuncSetAttribute(cond2_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)),
-               "cond2 smem") ||
-      !cuda_ok(cudaFuncSetAttribute(cond2_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)),
-               "cond2 smem") ||
-      !cuda_ok(cudaFuncSetAttribute(cond_m_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(msmem)),
-               "cond_m smem"))
+  if (!allow_dynamic_smem(reinterpret_cast<const void*>(cond2_kernel<0>), smem, "cond2 smem") ||
+      !allow_dynamic_smem(reinterpret_cast<const void*>(cond2_kernel<1>), smem, "cond2 smem") ||
+      !allow_dynamic_smem(reinterpret_cast<const void*>(cond_m_kernel), msmem, "cond_m smem"))
     return false;
   if (!cuda_ok(cudaMemsetAsync(a.ticket, 0, sizeof(unsigned int) * (groups + 1), st), "reset conditioning tickets"))
     return false;
@@ -794,9 +791,7 @@ bool launch_condition_householder(const Plan& pl, const float* pix, const l1s_pa
   const size_t bytes = sizeof(double) * static_cast<size_t>(pl.r1) * pl.q;
   a.in_smem = bytes <= kCondSmemMax ? 1 : 0;
   const size_t smem = a.in_smem ? bytes : 0;
-  if (!cuda_ok(cudaFuncSetAttribute(condition_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    static_cast<int>(smem)),
-               "condition smem"))
+  if (!allow_dynamic_smem(reinterpret_cast<const void*>(condition_kernel), smem, "condition smem"))
     return false;
   condition_kernel<<<1, kCondThreads, smem, st>>>(a);
   count_launch(1);

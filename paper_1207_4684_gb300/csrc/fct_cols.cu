@@ -646,8 +646,7 @@ bool launch_fct_cols(const Plan& pl, const void* A, int64_t lda, l1s_dtype dt, c
                                             : reinterpret_cast<const void*>(&fct_embed_cols_tma_kernel<float, false>));
     const size_t smem = cols_tma_smem_bytes(pl.r1);
     void* targs[] = {&mapA, &a};
-    if (!cuda_ok(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)),
-                 "cudaFuncSetAttribute(fct_embed_cols_tma)") ||
+    if (!allow_dynamic_smem(reinterpret_cast<const void*>(fn), smem, "cudaFuncSetAttribute(fct_embed_cols_tma)") ||
         !cuda_ok(cudaLaunchKernel(fn, dim3(pl.fct_ctas, pl.fct_cols), dim3(kTmaThreads), targs, smem, st),
                  "launch fct_embed_cols_tma"))
       return false;
@@ -655,8 +654,7 @@ bool launch_fct_cols(const Plan& pl, const void* A, int64_t lda, l1s_dtype dt, c
     set_error("");
     const void* fn = fct_cols_kernel(dt, pl.log2s == 10);
     const size_t smem = fct_cols_smem_bytes(pl.r1);
-    if (!cuda_ok(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)),
-                 "cudaFuncSetAttribute(fct_embed_cols)") ||
+    if (!allow_dynamic_smem(reinterpret_cast<const void*>(fn), smem, "cudaFuncSetAttribute(fct_embed_cols)") ||
         !cuda_ok(cudaLaunchKernel(fn, dim3(pl.fct_ctas, pl.fct_cols), dim3(kColThreads), args, smem, st),
                  "launch fct_embed_cols"))
       return false;
@@ -664,8 +662,7 @@ bool launch_fct_cols(const Plan& pl, const void* A, int64_t lda, l1s_dtype dt, c
   // The b column: its blocks are a function of this launch's n (the reduction reads them).
   const size_t bsmem = bcol_smem_bytes(pl.r1);
   const void* fb = reinterpret_cast<const void*>(&fct_embed_bcol_kernel);
-  if (!cuda_ok(cudaFuncSetAttribute(fb, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(bsmem)),
-               "cudaFuncSetAttribute(fct_embed_bcol)") ||
+  if (!allow_dynamic_smem(reinterpret_cast<const void*>(fb), bsmem, "cudaFuncSetAttribute(fct_embed_bcol)") ||
       !cuda_ok(cudaLaunchKernel(fb, dim3(bcol_ctas(pl.n)), dim3(kBcolThreads), args, bsmem, st),
                "launch fct_embed_bcol"))
     return false;

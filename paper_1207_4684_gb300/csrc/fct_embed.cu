@@ -1314,8 +1314,7 @@ static bool launch_fct_part(const Plan& pl, const void* A, int64_t lda, l1s_dtyp
       const size_t s1 = fct_ws_smem_bytes(tile, static_cast<int>(lda), dt, pl.r1, wsw, pl.fct_lean != 0);
       int o0 = 0, o1 = 0;
       if (s1 <= device_info().max_smem_optin &&
-          cuda_ok(cudaFuncSetAttribute(fw, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(s1)),
-                  "cudaFuncSetAttribute(fct_embed)") &&
+          allow_dynamic_smem(reinterpret_cast<const void*>(fw), s1, "cudaFuncSetAttribute(fct_embed)") &&
           cuda_ok(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o0, fw, pl.fct_threads, s0), "occupancy") &&
           cuda_ok(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o1, fw, pl.fct_threads, s1), "occupancy") &&
           o1 >= o0 && o1 > 0)
@@ -1331,8 +1330,7 @@ static bool launch_fct_part(const Plan& pl, const void* A, int64_t lda, l1s_dtyp
   const size_t smem = srt ? fct_sorted_smem_bytes(pl.s, pl.d, dt, pl.r1, srt)
                           : (wsw ? fct_ws_smem_bytes(tile, a.sd, dt, pl.r1, wsw, pl.fct_lean != 0)
                                  : fct_smem_bytes(pl.s, pl.d, dt, pl.r1, pl.fct_width, staged));
-  if (!cuda_ok(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)),
-               "cudaFuncSetAttribute(fct_embed)"))
+  if (!allow_dynamic_smem(reinterpret_cast<const void*>(fn), smem, "cudaFuncSetAttribute(fct_embed)"))
     return false;
   void* args[] = {&a};
   dim3 grid(pl.fct_ctas, pl.fct_slices);

@@ -123,8 +123,7 @@ bool launch_fct2(const Plan& pl, const void* A, int64_t lda, l1s_dtype dt, const
   const size_t smem = sizeof(uint32_t) * a.t + sizeof(int) * a.sf + sizeof(float) * static_cast<size_t>(a.t) * a.width;
   const void* fn = dt == L1S_BF16 ? reinterpret_cast<const void*>(&fjlt_kernel<uint16_t>)
                                   : reinterpret_cast<const void*>(&fjlt_kernel<float>);
-  if (!cuda_ok(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)),
-               "cudaFuncSetAttribute(fjlt)"))
+  if (!allow_dynamic_smem(reinterpret_cast<const void*>(fn), smem, "cudaFuncSetAttribute(fjlt)"))
     return false;
   const int grid = static_cast<int>(std::min<int64_t>(a.nblocks, 8 * static_cast<int64_t>(device_info().sms)));
   void* args[] = {&a};

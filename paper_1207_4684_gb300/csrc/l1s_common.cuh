@@ -300,6 +300,11 @@ struct TraceRange {
   TraceRange& operator=(const TraceRange&) = delete;
 };
 bool cuda_ok(cudaError_t e, const char* what);
+// Raises fn's dynamic shared-memory limit on the current device to at least `bytes` and
+// never lowers it, under a lock, so that calls of different shapes from several host
+// threads cannot lower the limit another call has set for its own launch.  False (with
+// the CUDA error recorded) when the runtime refuses.
+bool allow_dynamic_smem(const void* fn, size_t bytes, const char* what);
 
 inline size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }
 

@@ -404,9 +404,7 @@ static bool launch_tc(const TcArgs& args, const void* A, int64_t lda, int d, con
       !encode_bf16_2d(&mapB, mt, N, K, K * 2, K, N, sw))
     return false;
   const size_t smem = tc_smem_bytes<K, N>();
-  if (!cuda_ok(cudaFuncSetAttribute(lambda_tc_kernel<K, N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    static_cast<int>(smem)),
-               "lambda_tc smem"))
+  if (!allow_dynamic_smem(reinterpret_cast<const void*>(lambda_tc_kernel<K, N>), smem, "lambda_tc smem"))
     return false;
   lambda_tc_kernel<K, N><<<blocks, kTcThreads, smem, st>>>(mapA, mapB, args);
   return true;

@@ -134,8 +134,7 @@ template <int QW, typename TA>
 static bool launch_sct_t(const SctArgs& a, dim3 grid, cudaStream_t st) {
   const size_t smem = sct_smem_floats<QW>() * sizeof(float);
   const void* fn = reinterpret_cast<const void*>(&sct_embed_kernel<QW, TA>);
-  if (!cuda_ok(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)),
-               "cudaFuncSetAttribute(sct_embed)"))
+  if (!allow_dynamic_smem(reinterpret_cast<const void*>(fn), smem, "cudaFuncSetAttribute(sct_embed)"))
     return false;
   void* args[] = {const_cast<SctArgs*>(&a)};
   return cuda_ok(cudaLaunchKernel(fn, grid, dim3(kSctThreads), args, smem, st), "launch sct_embed");

@@ -664,15 +664,9 @@ bool launch_solve(const double* X, const double* w, const int64_t* count, int64_
   const size_t acc_smem = sizeof(double) * (kIrlsTile * q + kIrlsTile + q);
   const size_t step_smem = sizeof(double) * (irls_entries(q) + d * d + d);
   const size_t pol_smem = polish_smem_bytes(d);
-  if (!cuda_ok(cudaFuncSetAttribute(irls_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    static_cast<int>(step_smem)),
-               "irls_step smem") ||
-      !cuda_ok(cudaFuncSetAttribute(irls_accum_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    static_cast<int>(acc_smem)),
-               "irls_accum smem") ||
-      !cuda_ok(cudaFuncSetAttribute(irls_polish_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    static_cast<int>(pol_smem)),
-               "irls_polish smem"))
+  if (!allow_dynamic_smem(reinterpret_cast<const void*>(irls_step_kernel), step_smem, "irls_step smem") ||
+      !allow_dynamic_smem(reinterpret_cast<const void*>(irls_accum_kernel), acc_smem, "irls_accum smem") ||
+      !allow_dynamic_smem(reinterpret_cast<const void*>(irls_polish_kernel), pol_smem, "irls_polish smem"))
     return false;
   const dim3 many(nblocks, k), one(1, k);
   irls_init_kernel<<<one, 256, 0, st>>>(a);
